@@ -1,0 +1,226 @@
+"""Dynamical ortho-symplectic reduced model in the paper's real form, float64.
+
+R(t) ~ U(t) Z(t), U in St(2n, R^2N) cap Sp(2n, R^2N) (2N x 2n), Z (2n x p)
+(Sec. 3.2, eqs. dynManifold, UZred).  Everything here keeps the real
+2N x 2n / 2n x p matrices of the paper and applies the Poisson tensors
+J_2N, J_2n literally; matrices of size 2N x 2N are formed only by the
+``*_dense`` variants used on tiny inputs.
+
+Time stepping (Sec. 5, eqs. PRK-ZV and discrete_dynROM), with the tableau
+read as: explicit midpoint for the basis (a^_21 = 1/2, b^ = (0, 1)) and the
+implicit midpoint rule padded to the same two stages for the coefficients
+(a = [[0, 0], [0, 1/2]], b = (0, 1), c = (0, 1/2)).  Stage 1 is the basis-only
+stage at the beginning of the interval; the nonlinear stage is solved by
+fixed-point iteration from k = 0, stopped when the Frobenius norm of the
+update to k is below tol times the norm of k (Sec. 6.1, tol = 1e-9).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import pic
+
+
+class NoConvergence(RuntimeError):
+    pass
+
+
+# --------------------------------------------------------------------------
+# Poisson tensors
+# --------------------------------------------------------------------------
+def J(m2: int) -> np.ndarray:
+    """J_{2m} = [[0, I_m], [-I_m, 0]]."""
+    m = m2 // 2
+    out = np.zeros((m2, m2))
+    out[:m, m:] = np.eye(m)
+    out[m:, :m] = -np.eye(m)
+    return out
+
+
+def apply_J(M: np.ndarray) -> np.ndarray:
+    """J_{2m} @ M for M with 2m rows: [M_bottom; -M_top]."""
+    m = M.shape[0] // 2
+    return np.vstack([M[m:], -M[:m]])
+
+
+def split(U: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """U_X = first N rows, U_V = last N rows."""
+    N = U.shape[0] // 2
+    return U[:N], U[N:]
+
+
+# --------------------------------------------------------------------------
+# reconstruction and gradients (eqs. grads, grH-full, UZred_coeff)
+# --------------------------------------------------------------------------
+def reconstruct(U: np.ndarray, Z: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """X_r^i = U_X Z_i, V_r^i = U_V Z_i, returned as (p, N) arrays."""
+    UX, UV = split(U)
+    return (UX @ Z).T, (UV @ Z).T
+
+
+def full_gradient(U: np.ndarray, Z: np.ndarray, g: pic.Grid):
+    """G = [G_X; V_r] (2N x p) at R = U Z, the electric potentials Phi (p x Nx)
+    and the electric energies E_i (p)."""
+    Xr, Vr = reconstruct(U, Z)
+    rho, Phi, GX = pic.field(Xr, g)
+    return np.vstack([GX.T, Vr.T]), Phi, pic.electric_energy(Phi, g)
+
+
+def reduced_gradient(U: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """g = U^T G (2n x p)."""
+    return U.T @ G
+
+
+def coefficient_velocity(U: np.ndarray, Z: np.ndarray, g: pic.Grid) -> np.ndarray:
+    """Zdot = J_2n U^T G(UZ)."""
+    G, _, _ = full_gradient(U, Z, g)
+    return apply_J(U.T @ G)
+
+
+def S_of(Z: np.ndarray) -> np.ndarray:
+    """S(Z) = Z Z^T + J_2n^T Z Z^T J_2n."""
+    J2n = J(Z.shape[0])
+    ZZ = Z @ Z.T
+    return ZZ + J2n.T @ ZZ @ J2n
+
+
+def basis_velocity_from_G(U: np.ndarray, Z: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """X(U, Z) = (I - U U^T)(J_2N G Z^T - G Z^T J_2n^T) S(Z)^-1 (eq. UZred_basis)."""
+    GZ = G @ Z.T
+    A = apply_J(GZ) - GZ @ J(Z.shape[0]).T
+    A = A - U @ (U.T @ A)
+    S = S_of(Z)
+    return np.linalg.solve(S.T, A.T).T
+
+
+def basis_velocity(U: np.ndarray, Z: np.ndarray, g: pic.Grid) -> np.ndarray:
+    G, _, _ = full_gradient(U, Z, g)
+    return basis_velocity_from_G(U, Z, G)
+
+
+# --------------------------------------------------------------------------
+# Cayley retraction (Sec. 5, Proposition 5.6 of the cited tangent method)
+# --------------------------------------------------------------------------
+def cayley(Omega: np.ndarray) -> np.ndarray:
+    """cay(Omega) = (I - Omega/2)^-1 (I + Omega/2)."""
+    I = np.eye(Omega.shape[0])
+    return np.linalg.solve(I - 0.5 * Omega, I + 0.5 * Omega)
+
+
+def W_of(U0: np.ndarray, xi: np.ndarray) -> np.ndarray:
+    """W with 2W = (2I - U0 U0^T) xi."""
+    return xi - 0.5 * U0 @ (U0.T @ xi)
+
+
+def retraction_dense(U0: np.ndarray, xi: np.ndarray) -> np.ndarray:
+    """R_U0(xi) = cay(W U0^T - U0 W^T) U0 with the 2N x 2N matrix formed."""
+    W = W_of(U0, xi)
+    return cayley(W @ U0.T - U0 @ W.T) @ U0
+
+
+def retraction(U0: np.ndarray, xi: np.ndarray) -> np.ndarray:
+    """R_U0(xi) in O(N n^2): W U0^T - U0 W^T = C D^T with C = [W, -U0],
+    D = [U0, W], so cay(C D^T) U0 = U0 + C (I_4n - D^T C / 2)^-1 D^T U0
+    (Sherman-Morrison-Woodbury on the rank-4n Cayley transform)."""
+    W = W_of(U0, xi)
+    C = np.hstack([W, -U0])
+    D = np.hstack([U0, W])
+    K = D.T @ C
+    return U0 + C @ np.linalg.solve(np.eye(K.shape[0]) - 0.5 * K, D.T @ U0)
+
+
+def _gradient(U, Z, g, grad_fn):
+    """G at R = U Z: the PIC gradient, or grad_fn(R) for a given Hamiltonian."""
+    if grad_fn is None:
+        return full_gradient(U, Z, g)[0]
+    return grad_fn(U @ Z)
+
+
+def tangent_velocity(U0: np.ndarray, xi: np.ndarray, Z: np.ndarray, g: pic.Grid,
+                     retract=retraction, grad_fn=None):
+    """Y(xi, Z) of the local flow in the tangent space at U0 (Sec. 5):
+        Y = -U0 (R^T U0 + I)^-1 (R + U0)^T Ups + Ups - U0 Ups^T U0,
+        Ups = (2 X(R, Z) - (W U0^T - U0 W^T) X(R, Z)) (U0^T R + I)^-1,
+    with R = R_U0(xi), 2W = (2I - U0 U0^T) xi.  Returns (Y, R, G(R, Z))."""
+    I = np.eye(U0.shape[1])
+    W = W_of(U0, xi)
+    R = retract(U0, xi)
+    G = _gradient(R, Z, g, grad_fn)
+    Xc = basis_velocity_from_G(R, Z, G)
+    OmX = W @ (U0.T @ Xc) - U0 @ (W.T @ Xc)
+    Ups = np.linalg.solve((U0.T @ R + I).T, (2.0 * Xc - OmX).T).T
+    Y = -U0 @ np.linalg.solve(R.T @ U0 + I, (R + U0).T @ Ups) + Ups - U0 @ (Ups.T @ U0)
+    return Y, R, G
+
+
+# --------------------------------------------------------------------------
+# partitioned RK2 step (eqs. pRK_Z, pRK_U, pRK_Z_k1, pRK_Z_ki, pRK_U_ktilde)
+# --------------------------------------------------------------------------
+def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
+              tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
+              retract=retraction, grad_fn=None):
+    """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
+
+    info: 'iters' (fixed-point evaluations), 'U_half', 'k2', 'E0' (electric
+    energies at (U0, Z0); PIC gradient only), 'kh1' (basis velocity at the start).
+    grad_fn: optional map R -> G replacing the PIC gradient (any Hamiltonian).
+    """
+    info = {}
+    if grad_fn is None:
+        G0, _, E0 = full_gradient(U0, Z0, g)
+        info["E0"] = E0
+    else:
+        G0 = grad_fn(U0 @ Z0)
+    if freeze_basis:
+        kh1 = np.zeros_like(U0)
+        U_half = U0
+    else:
+        kh1 = basis_velocity_from_G(U0, Z0, G0)
+        U_half = retract(U0, 0.5 * dt * kh1)
+    info["kh1"] = kh1
+    info["U_half"] = U_half
+    k = np.zeros_like(Z0)
+    for it in range(1, maxit + 1):
+        G = _gradient(U_half, Z0 + 0.5 * dt * k, g, grad_fn)
+        k_new = apply_J(U_half.T @ G)
+        diff = np.linalg.norm(k_new - k)
+        k = k_new
+        if diff <= tol * np.linalg.norm(k):
+            break
+    else:
+        raise NoConvergence(f"fixed point did not converge in {maxit} iterations")
+    info["iters"] = it
+    info["k2"] = k
+    Z1 = Z0 + dt * k
+    if freeze_basis:
+        return U0.copy(), Z1, info
+    Y, _, _ = tangent_velocity(U0, 0.5 * dt * kh1, Z0 + 0.5 * dt * k, g, retract, grad_fn)
+    U1 = retract(U0, dt * Y)
+    return U1, Z1, info
+
+
+def energies(U: np.ndarray, Z: np.ndarray, g: pic.Grid) -> tuple[np.ndarray, np.ndarray]:
+    """(E_i, H_i) with H_i = 1/2 |V_r^i|^2 + E(X_r^i) (eqs. nonlinear_hamiltonian, HamEE)."""
+    Xr, Vr = reconstruct(U, Z)
+    return pic.hamiltonian(Xr, Vr, g)
+
+
+def run(U: np.ndarray, Z: np.ndarray, dt: float, nsteps: int, g: pic.Grid, **kw):
+    """nsteps PRK2 steps; returns U, Z, the (E, H) trace (nsteps, p, 2), iterations."""
+    tr = np.zeros((nsteps, Z.shape[1], 2))
+    its = []
+    for t in range(nsteps):
+        U, Z, info = prk2_step(U, Z, dt, g, **kw)
+        its.append(info["iters"])
+        E, H = energies(U, Z, g)
+        tr[t, :, 0] = E
+        tr[t, :, 1] = H
+    return U, Z, tr, its
+
+
+def manifold_residuals(U: np.ndarray) -> tuple[float, float]:
+    """(||U^T U - I||_F, ||U^T J_2N U - J_2n||_F)."""
+    n2 = U.shape[1]
+    ortho = np.linalg.norm(U.T @ U - np.eye(n2))
+    symp = np.linalg.norm(U.T @ apply_J(U) - J(n2))
+    return float(ortho), float(symp)

@@ -1,0 +1,187 @@
+"""Pins of the oracle's dynamical reduced model (Sec. 3.2, Sec. 5)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import csvd, pic, reduced
+
+
+def small_state(N=40, p=8, n=3, Nx=8, seed=1, L=4 * np.pi):
+    g = pic.make_grid(N, Nx, L)
+    X0 = W.random_positions(p, N, L, seed=seed)
+    V0 = W.random_velocities(p, N, seed=seed + 1)
+    U0, Z0, _ = csvd.csvd_init(X0, V0, n)
+    return g, U0, Z0
+
+
+def test_csvd_eckart_young_and_manifold():
+    N, p, n = 60, 10, 4
+    X0 = W.random_positions(p, N, 5.0, seed=2)
+    V0 = W.random_velocities(p, N, seed=3)
+    U0, Z0, sigma = csvd.csvd_init(X0, V0, n)
+    R0 = np.vstack([X0.T, V0.T])
+    # singular values from an independent route: eigenvalues of R^H R
+    Rc = (X0 + 1j * V0).T
+    ev = np.sort(np.linalg.eigvalsh(Rc.conj().T @ Rc))[::-1]
+    np.testing.assert_allclose(np.linalg.norm(R0 - U0 @ Z0) ** 2, ev[n:].sum(), rtol=1e-10)
+    o, s = reduced.manifold_residuals(U0)
+    assert o < 1e-13 and s < 1e-13
+    np.testing.assert_allclose(Z0, U0.T @ R0, atol=1e-12)
+
+
+def test_basis_velocity_is_tangent():
+    g, U0, Z0 = small_state()
+    Xc = reduced.basis_velocity(U0, Z0, g)
+    # gauge U^T X = 0 (eq. UZred_basis projects with I - U U^T)
+    assert np.linalg.norm(U0.T @ Xc) < 1e-12 * np.linalg.norm(Xc)
+    # tangent to Sp: X^T J U + U^T J X = 0; tangent to St: X^T U + U^T X = 0
+    JU, JX = reduced.apply_J(U0), reduced.apply_J(Xc)
+    assert np.linalg.norm(Xc.T @ JU + U0.T @ JX) < 1e-12 * np.linalg.norm(Xc)
+
+
+def test_S_of_Z_real_form_of_gram():
+    Z = np.random.default_rng(0).standard_normal((6, 9))
+    zeta = csvd.zeta_from_Z(Z)
+    np.testing.assert_allclose(reduced.S_of(Z), csvd.U_from_Q(zeta @ zeta.conj().T), atol=1e-12)
+
+
+def test_retraction_woodbury_equals_dense_and_stays_on_manifold():
+    g, U0, Z0 = small_state(N=30, n=4)
+    xi = 0.3 * reduced.basis_velocity(U0, Z0, g)
+    R1 = reduced.retraction(U0, xi)
+    R2 = reduced.retraction_dense(U0, xi)
+    np.testing.assert_allclose(R1, R2, atol=1e-13)
+    o, s = reduced.manifold_residuals(R1)
+    assert o < 1e-13 and s < 1e-13
+    # retraction property R(0) = U0 and dR_0[xi] = xi for tangent xi
+    np.testing.assert_allclose(reduced.retraction(U0, 0 * xi), U0, atol=1e-15)
+    eps = 1e-6
+    fd = (reduced.retraction(U0, eps * xi) - reduced.retraction(U0, -eps * xi)) / (2 * eps)
+    np.testing.assert_allclose(fd, xi, atol=1e-8 * np.abs(xi).max())
+
+
+def test_cayley_of_skew_hamiltonian_is_orthosymplectic():
+    g, U0, Z0 = small_state(N=12, n=2)
+    W_ = reduced.W_of(U0, 0.5 * reduced.basis_velocity(U0, Z0, g))
+    Om = W_ @ U0.T - U0 @ W_.T
+    C = reduced.cayley(Om)
+    J = reduced.J(C.shape[0])
+    np.testing.assert_allclose(C.T @ C, np.eye(C.shape[0]), atol=1e-13)
+    np.testing.assert_allclose(C.T @ J @ C, J, atol=1e-13)
+
+
+def test_tangent_velocity_is_inverse_differential_of_retraction():
+    # the local flow xi' = Y(xi, Z) must satisfy d/dt R(xi(t)) = X(R(xi), Z)
+    g, U0, Z0 = small_state()
+    Xc0 = reduced.basis_velocity(U0, Z0, g)
+    xi = 0.05 * Xc0
+    Y, R, G = reduced.tangent_velocity(U0, xi, Z0, g)
+    XR = reduced.basis_velocity_from_G(R, Z0, G)
+    errs = []
+    for eps in (1e-3, 1e-4):
+        fd = (reduced.retraction(U0, xi + eps * Y) - reduced.retraction(U0, xi - eps * Y)) / (2 * eps)
+        errs.append(np.linalg.norm(fd - XR) / np.linalg.norm(XR))
+    assert errs[1] < 1e-8 and errs[0] / errs[1] > 50  # O(eps^2) agreement
+    Y0, _, _ = reduced.tangent_velocity(U0, 0 * xi, Z0, g)
+    np.testing.assert_allclose(Y0, Xc0, atol=1e-13 * np.abs(Xc0).max())
+
+
+def implicit_midpoint_pic(X, V, dt, g, tol=1e-14):
+    """Independent implicit midpoint step of the full-order system (eq. VPHamEqn)."""
+    X1, V1 = X.copy(), V.copy()
+    for _ in range(200):
+        Xm, Vm = 0.5 * (X + X1), 0.5 * (V + V1)
+        GX = pic.field(Xm, g)[2]
+        X1n, V1n = X + dt * Vm, V - dt * GX
+        d = np.linalg.norm(X1n - X1) + np.linalg.norm(V1n - V1)
+        X1, V1 = X1n, V1n
+        if d < tol * (np.linalg.norm(X1) + np.linalg.norm(V1)):
+            break
+    return X1, V1
+
+
+def test_full_basis_reduces_to_implicit_midpoint_pic():
+    # 2n = 2N with U = I: (I - U U^T) = 0 freezes U and the coefficient stage
+    # is the implicit midpoint rule on the full-order system.
+    N, p, Nx = 4, 6, 5
+    L = 3.0
+    g = pic.make_grid(N, Nx, L)
+    X = W.random_positions(p, N, L, seed=21)
+    V = 0.5 * W.random_velocities(p, N, seed=22)
+    U = csvd.U_from_Q(np.eye(N, dtype=complex))
+    Z = np.vstack([X.T, V.T])
+    U1, Z1, info = reduced.prk2_step(U, Z, 0.05, g, tol=1e-15, maxit=400)
+    np.testing.assert_allclose(U1, U, atol=1e-13)
+    X1, V1 = implicit_midpoint_pic(X, V, 0.05, g)
+    np.testing.assert_allclose(Z1[:N].T, X1, atol=1e-12)
+    np.testing.assert_allclose(Z1[N:].T, V1, atol=1e-12)
+
+
+def test_frozen_basis_coefficient_map_is_symplectic():
+    g, U0, Z0 = small_state(N=30, p=3, n=2, Nx=6)
+    dt, eps = 0.05, 1e-7
+    n2 = Z0.shape[0]
+
+    def step(z):
+        Z = Z0.copy()
+        Z[:, 0] = z
+        return reduced.prk2_step(U0, Z, dt, g, tol=1e-15, maxit=400, freeze_basis=True)[1][:, 0]
+
+    M = np.zeros((n2, n2))
+    for c in range(n2):
+        e = np.zeros(n2)
+        e[c] = eps * max(1.0, abs(Z0[c, 0]))
+        M[:, c] = (step(Z0[:, 0] + e) - step(Z0[:, 0] - e)) / (2 * e[c])
+    J = reduced.J(n2)
+    np.testing.assert_allclose(M.T @ J @ M, J, atol=1e-5)
+
+
+def test_sample_permutation_equivariance():
+    g, U0, Z0 = small_state(p=6)
+    perm = np.array([3, 0, 5, 1, 4, 2])
+    U1, Z1, _ = reduced.prk2_step(U0, Z0, 0.05, g)
+    U2, Z2, _ = reduced.prk2_step(U0, Z0[:, perm], 0.05, g)
+    np.testing.assert_allclose(Z2, Z1[:, perm], rtol=0, atol=1e-11 * np.abs(Z1).max())
+    np.testing.assert_allclose(U2, U1, atol=1e-11)
+
+
+def test_prk2_keeps_manifold_on_pic():
+    g, U0, Z0 = small_state(N=60, p=10, n=3, Nx=16, L=10 * np.pi)
+    U, Z = U0, Z0
+    for _ in range(50):
+        U, Z, _ = reduced.prk2_step(U, Z, 0.05, g)
+    o, s = reduced.manifold_residuals(U)
+    assert o < 1e-12 and s < 1e-12
+
+
+def test_prk2_is_second_order_for_smooth_hamiltonian():
+    # The PIC force jumps at nodes, which limits any integrator to first order;
+    # the scheme itself is pinned on H = 1/2 V^T V + 1/2 X^T K X (smooth, and
+    # not reducible by a fixed basis since K mixes the particles).
+    N, p, n = 30, 8, 3
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((N, N))
+    K = A @ A.T / N + np.eye(N)
+
+    def grad_fn(R):
+        return np.vstack([K @ R[:N], R[N:]])
+
+    X0 = rng.standard_normal((p, N))
+    V0 = rng.standard_normal((p, N))
+    U0, Z0, _ = csvd.csvd_init(X0, V0, n)
+    g = pic.make_grid(N, 8, 1.0)
+
+    def run(dt, T=0.8):
+        U, Z = U0, Z0
+        for _ in range(int(round(T / dt))):
+            U, Z, _ = reduced.prk2_step(U, Z, dt, g, tol=1e-14, maxit=400, grad_fn=grad_fn)
+        return U, Z
+
+    Uref, Zref = run(0.0125)
+    errs = []
+    for dt in (0.1, 0.05):
+        U, Z = run(dt)
+        errs.append(np.linalg.norm(U @ Z - Uref @ Zref))
+        o, s = reduced.manifold_residuals(U)
+        assert o < 1e-13 and s < 1e-13
+    assert 3.2 < errs[0] / errs[1] < 5.0, errs
