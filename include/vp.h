@@ -1,0 +1,219 @@
+/*
+ * vp.h -- C ABI of the GB300 library for the data-parallel hot path of the
+ * adaptive symplectic dynamical reduced model of the parametric particle-based
+ * 1D1V Vlasov-Poisson system (Hesthaven, Pagliantini, Ripamonti,
+ * arXiv 2201.05555).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns a vp_status.  No call aborts, prints or exits.  The
+ *   message of the last failure on a context is vp_last_error(ctx).
+ * - Pointers named *_dev are device pointers owned by the caller; the library
+ *   never frees them.  Host pointers are named *_host.  The library owns only
+ *   its context and the workspace it allocates (on demand, within the byte
+ *   budget given to vp_ctx_create).
+ * - Device work is asynchronous on the caller's CUDA stream (`stream`, a
+ *   cudaStream_t passed as void*; NULL = legacy default stream).  Arguments
+ *   are validated on the host before any launch (VP_EINVAL).  Errors found on
+ *   the device (non-convergence, non-finite energies, a singular small
+ *   system) are written to a device status word and reported by
+ *   vp_ctx_sync_status.
+ * - Floating point: every entry point below computes in FP64 (dtype "f64").
+ *   Fixed-point int64 charge accumulation makes deposits independent of the
+ *   order of particles: repeated calls give bit-identical results.
+ *
+ * Data layouts (row-major, C order)
+ * ---------------------------------
+ * - Particles of p samples: X, V, GX are p x N arrays (sample i occupies
+ *   elements [i*ld, i*ld + N)).  Positions are unwrapped (they are reduced
+ *   modulo L only inside the particle-to-grid maps).
+ * - The ortho-symplectic basis U = [[A, -B], [B, A]] (2N x 2n, Sec. 3.2,
+ *   eq. dynManifold) is stored as the complex N x n matrix Q = A + iB,
+ *   row l = [A_l0 .. A_l(n-1), B_l0 .. B_l(n-1)] (N x 2n doubles).  Tangent
+ *   vectors xi, X(U,Z), Y(xi,Z) (2N x 2n) use the same storage.
+ * - Coefficients Z = [a; b] (2n x p) exactly as in the paper (zeta = a + ib).
+ * - Grid arrays rho, phi, F are p x Nx.  F_j = (phi_{j+1} - phi_j)/h is the
+ *   derivative of the P1 potential on cell j = [x_j, x_{j+1}).
+ *
+ * Mesh conventions: nodes x_j = j h, h = L/Nx, periodic P1 hats; a particle
+ * at wrapped position x lies in cell floor(x/h); the Poisson gauge is
+ * sum_j phi_j = 0.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vp_status {
+  VP_OK = 0,
+  VP_EINVAL = 1,       /* invalid argument (checked on the host) */
+  VP_ENOMEM = 2,       /* workspace over the context budget or cudaMalloc failed */
+  VP_EBUSY = 3,        /* server full / admission refused */
+  VP_EAGAIN = 4,       /* result not ready yet */
+  VP_ETIMEDOUT = 5,    /* a bounded wait ran out */
+  VP_ENOCONV = 6,      /* fixed-point iteration did not converge */
+  VP_ENUMERIC = 7,     /* non-finite value or singular small system */
+  VP_EDRIFT = 8,       /* basis left the ortho-symplectic manifold */
+  VP_ECUDA = 9,        /* a CUDA runtime call failed */
+  VP_EUNSUPPORTED = 10 /* size outside the compiled limits */
+} vp_status;
+
+typedef struct vp_ctx vp_ctx;
+
+/* Mesh and particle constants (Sec. 2.1).  With q = -1, m = 1 and weights
+ * omega = L/N (mean density 1): Mq = -L/N, mp = L/N, background = 1. */
+typedef struct vp_grid {
+  int32_t Nx;        /* nodes of the periodic P1 mesh, 3 <= Nx <= 1024 */
+  double L;          /* domain length */
+  double Mq;         /* charge of one macro-particle, q*omega (eq. PoissonSystem) */
+  double mp;         /* mass of one macro-particle, m*omega (eq. HamEEfull) */
+  double background; /* neutralising background density; P1 load background*h */
+} vp_grid;
+
+/* Options of the partitioned RK2 step (Sec. 5). */
+typedef struct vp_step_opts {
+  double tol;      /* fixed-point stop: |k_{m+1} - k_m|_F <= tol |k_{m+1}|_F (Sec. 6.1: 1e-9) */
+  int32_t maxit;   /* iteration cap; exceeding it gives VP_ENOCONV */
+  int32_t freeze_basis; /* 1: keep U fixed (global symplectic reduced basis, Sec. 3.1) */
+} vp_step_opts;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context on `device`.  scratch_bytes bounds the workspace the
+ * library may allocate for itself (0 = 4 GiB). */
+vp_status vp_ctx_create(vp_ctx** ctx_out, int device, size_t scratch_bytes);
+vp_status vp_ctx_destroy(vp_ctx* ctx);
+const char* vp_last_error(const vp_ctx* ctx);
+const char* vp_status_string(vp_status s);
+/* Synchronise `stream`, then return and clear the device status word. */
+vp_status vp_ctx_sync_status(vp_ctx* ctx, void* stream);
+/* Bytes of workspace currently held by the context. */
+size_t vp_ctx_workspace_bytes(const vp_ctx* ctx);
+int32_t vp_version(void);
+
+/* ------------------------------------------------------ particle-grid maps */
+/* a2. rho = Lambda^0(X)^T M_q + b for each of p samples (Sec. 2.1,
+ * eq. PoissonSystem): cloud-in-cell (P1 hat) deposit plus the background
+ * load background*h per node.  X_dev: p x N with leading dimension ldx >= N.
+ * rho_dev: p x Nx.  1 <= N < 2^31, 1 <= p <= 65535. */
+vp_status vp_deposit_cic(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p,
+                         const double* X_dev, int64_t ldx, double* rho_dev, void* stream);
+
+/* a3. Solve L phi = rho with sum(phi) = 0 for each sample, L = (1/h)
+ * circ(-1, 2, -1) the periodic P1 stiffness matrix (eq. PoissonSystem), by
+ * two prefix sums.  Writes the cell derivative F (p x Nx), optionally phi
+ * (p x Nx) and the electric energy E = (1/(2 mp)) phi^T L phi = (h/(2 mp))
+ * sum_j F_j^2 (p, eq. HamEEfull).  Null outputs are skipped.  Requires
+ * sum_j rho_j = 0 (neutral system); the solve uses the consistent part. */
+vp_status vp_poisson_periodic(vp_ctx* ctx, const vp_grid* grid, int32_t p, const double* rho_dev,
+                              double* phi_dev, double* F_dev, double* energy_dev, void* stream);
+
+/* a4. Gradient of the electric energy at the particles,
+ * GX = m_p^-1 diag(M_q) grad Lambda^0(X) phi = (Mq/mp) F_{cell(X)} (eq. VPHamEqn);
+ * the accelerations of eq. sv_full_order are -GX.  idx_dev == NULL: all N
+ * particles, GX_dev p x N.  Otherwise only the d particles idx_dev[0..d)
+ * (DEIM rows, Sec. 4.2), GX_dev p x d.  F_dev: p x Nx from vp_poisson_periodic. */
+vp_status vp_gather_E(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const double* X_dev,
+                      int64_t ldx, const double* F_dev, const int32_t* idx_dev, int64_t d,
+                      double* GX_dev, void* stream);
+
+/* a10. nsteps Stormer-Verlet steps of the full-order model for each sample
+ * (Sec. 5, eq. sv_full_order), in place on X_dev, V_dev (p x N, ld N).
+ * trace_dev (nullable): (nsteps x p x 2) electric energy and Hamiltonian
+ * H = 1/2 V^T V + E after each step (eq. high_fidelity_Hamiltonian).
+ * One thread-block cluster per sample runs all steps in one launch. */
+vp_status vp_full_step(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, double* X_dev,
+                       double* V_dev, double dt, int32_t nsteps, double* trace_dev, void* stream);
+
+/* -------------------------------------------------------- reduced model */
+/* a1. X_r = U_X Z, V_r = U_V Z (Sec. 3.2): X_dev, V_dev p x N (V_dev nullable).
+ * Q_dev N x 2n, Z_dev 2n x p.  1 <= n <= 40 for every reduced-model call. */
+vp_status vp_reconstruct(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q_dev,
+                         const double* Z_dev, double* X_dev, double* V_dev, void* stream);
+
+/* a5. g = U^T [GX; V_r] with V_r = U_V Z (eq. grads): the X part by a
+ * projection of GX (p x N) onto the basis, the V part through the Gram
+ * matrix U_V^T U_V (Sec. 4.3, cost item 1).  g_dev: 2n x p.  GX_dev == NULL
+ * gives the V part alone. */
+vp_status vp_project_grad(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q_dev,
+                          const double* GX_dev, const double* Z_dev, double* g_dev, void* stream);
+
+/* a6. Basis velocity X(U, Z) = (I - UU^T)(J G Z^T - G Z^T J^T) S(Z)^-1
+ * (eq. UZred_basis), with G = [GX; V_r] evaluated at R = UZ (deposit,
+ * Poisson, gather inside).  Xi_dev: N x 2n (complex storage). */
+vp_status vp_basis_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q_dev, const double* Z_dev, double* Xi_dev, void* stream);
+
+/* a7. Cayley retraction R_U0(xi) = cay(W U0^T - U0 W^T) U0, 2W = (2I -
+ * U0 U0^T) xi (Sec. 5), evaluated in O(N n^2) with the Woodbury identity.
+ * Qout_dev may alias Q0_dev. */
+vp_status vp_cayley_retract(vp_ctx* ctx, int64_t N, int32_t n, const double* Q0_dev,
+                            const double* xi_dev, double* Qout_dev, void* stream);
+
+/* a8. Tangent velocity Y(xi, Z) of the local flow at U0 (Sec. 5), with the
+ * basis velocity evaluated at R_U0(xi).  Y_dev: N x 2n. */
+vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                              const double* Q0_dev, const double* xi_dev, const double* Z_dev,
+                              double* Y_dev, void* stream);
+
+/* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
+ * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
+ * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
+ * opts NULL = {1e-9, 100, 0}.  trace_dev (nullable): ((nsteps+1) x p x 2)
+ * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
+ * nonlinear_hamiltonian) of the state before step 1 and after each step.
+ * iters_dev (nullable): fixed-point iterations of each step (int32, nsteps).
+ * Synchronises `stream` once per step to steer the fixed point. */
+vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          double* Q_dev, double* Z_dev, double dt, int32_t nsteps,
+                          const vp_step_opts* opts, double* trace_dev, int32_t* iters_dev,
+                          void* stream);
+
+/* a11. FP64 diagnostics of a reduced state: electric energy E_i and
+ * Hamiltonian H_i = 1/2 |U_V Z_i|^2 + E_i (p each, eq. nonlinear_hamiltonian),
+ * and the manifold residual |Q^H Q - I|_F (= |U^T U - I|_F / sqrt 2; U^T J U = J
+ * holds exactly for the block form).  Any output may be NULL. */
+vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q_dev, const double* Z_dev, double* E_dev, double* H_dev,
+                            double* resid_dev, void* stream);
+
+/* a12. DEIM-indexed nonlinear gradient (Sec. 4.3, eq. grHDD):
+ * gX = m_p^-1 U_X^T diag(grad Lambda^0(X_r) Phi_DMD) P c, evaluated at the d
+ * rows idx_dev of X_r = U_X Z only.  c_dev: the d DEIM weights
+ * c = (P^T Psi)^-T Psi^T M_q.  phi_dev: p x Nx potentials Phi_DMD.
+ * gX_dev: 2n x p.  Add the linear part U_V^T V_r (vp_project_grad with GX = 0)
+ * for the full g^DD. */
+vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                                 const double* Q_dev, const double* Z_dev, int64_t d,
+                                 const int32_t* idx_dev, const double* c_dev,
+                                 const double* phi_dev, double* gX_dev, void* stream);
+
+/* ------------------------------------------------------------ profiling */
+/* Kernels of the library, for launch counts and event timing. */
+typedef enum vp_kernel {
+  VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
+  VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
+  VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
+  VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_COUNT
+} vp_kernel;
+
+/* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is
+ * set in `mask` are also timed: a CUDA event pair is recorded around each
+ * launch on the launch stream and resolved at the next synchronisation
+ * point (vp_profile_read synchronises the context's device).  mask = 0
+ * stops timing. */
+vp_status vp_profile_enable(vp_ctx* ctx, uint64_t mask);
+/* Launch count, timed launches and summed event time (ms) of one kernel. */
+vp_status vp_profile_read(vp_ctx* ctx, int32_t kernel, int64_t* launches, int64_t* timed,
+                          double* ms_total);
+vp_status vp_profile_reset(vp_ctx* ctx);
+const char* vp_kernel_name(int32_t kernel);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VP_H */

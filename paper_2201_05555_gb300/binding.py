@@ -1,0 +1,276 @@
+"""ctypes binding of libvp (include/vp.h): argument marshalling only.
+
+Every method takes torch CUDA float64 tensors (C-contiguous), passes their
+device pointers and the current torch stream to the C ABI, and raises
+VPError on a non-zero status.  No computation happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from .build import LIB
+
+_P = C.c_void_p
+_I32, _I64, _D, _SZ = C.c_int32, C.c_int64, C.c_double, C.c_size_t
+
+STATUS = {0: "VP_OK", 1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_EBUSY", 4: "VP_EAGAIN",
+          5: "VP_ETIMEDOUT", 6: "VP_ENOCONV", 7: "VP_ENUMERIC", 8: "VP_EDRIFT", 9: "VP_ECUDA",
+          10: "VP_EUNSUPPORTED"}
+
+
+class VPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    """vp_grid: mesh and macro-particle constants (Sec. 2.1)."""
+    _fields_ = [("Nx", _I32), ("L", _D), ("Mq", _D), ("mp", _D), ("background", _D)]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32)]
+
+
+def make_grid(N: int, Nx: int, L: float, q: float = -1.0, m: float = 1.0,
+              omega: float | None = None) -> Grid:
+    """q = -1, m = 1, weights omega = L/N (mean density 1); the background
+    density neutralises the N particles."""
+    w = L / N if omega is None else omega
+    Mq = q * w
+    return Grid(Nx, L, Mq, m * w, -Mq * N / L)
+
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("vp_ctx_create", _I32, [C.POINTER(_P), C.c_int, _SZ]),
+    ("vp_ctx_destroy", _I32, [_P]),
+    ("vp_last_error", C.c_char_p, [_P]),
+    ("vp_status_string", C.c_char_p, [_I32]),
+    ("vp_ctx_sync_status", _I32, [_P, _P]),
+    ("vp_ctx_workspace_bytes", _SZ, [_P]),
+    ("vp_version", _I32, []),
+    ("vp_deposit_cic", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P]),
+    ("vp_poisson_periodic", _I32, [_P, C.POINTER(Grid), _I32, _P, _P, _P, _P, _P]),
+    ("vp_gather_E", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P, _I64, _P, _P]),
+    ("vp_full_step", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _P, _D, _I32, _P, _P]),
+    ("vp_reconstruct", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P]),
+    ("vp_project_grad", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P]),
+    ("vp_basis_velocity", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P]),
+    ("vp_cayley_retract", _I32, [_P, _I64, _I32, _P, _P, _P, _P]),
+    ("vp_tangent_velocity", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P, _P]),
+    ("vp_basis_update", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _D, _I32,
+                               C.POINTER(StepOpts), _P, _P, _P]),
+    ("vp_reduced_energy", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
+    ("vp_deim_gather_project", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I64, _P,
+                                      _P, _P, _P, _P]),
+]
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load_library() -> C.CDLL:
+    """Load libvp.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise ImportError(f"{LIB} is missing: build it with __graft_entry__.build() "
+                                  "(the CUDA library is the only implementation)")
+            lib = C.CDLL(LIB)
+            for name, res, args in _SIGS:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float64, name: str = "tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Context:
+    """A vp_ctx on one device, with one method per C entry point."""
+
+    def __init__(self, device: int = 0, scratch_bytes: int = 0):
+        self.lib = load_library()
+        self.device = device
+        h = _P()
+        s = self.lib.vp_ctx_create(C.byref(h), device, scratch_bytes)
+        if s != 0:
+            raise VPError(s, f"vp_ctx_create(device={device}) failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers
+    def _stream(self):
+        return C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, s: int, what: str):
+        if s != 0:
+            msg = self.lib.vp_last_error(self.h).decode()
+            raise VPError(s, f"{what}: {msg}")
+
+    def _empty(self, *shape, dtype=torch.float64):
+        return torch.empty(*shape, dtype=dtype, device=f"cuda:{self.device}")
+
+    def sync_status(self):
+        self._check(self.lib.vp_ctx_sync_status(self.h, self._stream()), "device status")
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.vp_ctx_workspace_bytes(self.h))
+
+    # -- particle <-> grid
+    def deposit_cic(self, grid: Grid, X: torch.Tensor, rho: torch.Tensor | None = None):
+        p, N = X.shape
+        rho = self._empty(p, grid.Nx) if rho is None else rho
+        self._check(self.lib.vp_deposit_cic(self.h, C.byref(grid), N, p, _ptr(X, name="X"), N,
+                                            _ptr(rho, name="rho"), self._stream()), "deposit")
+        return rho
+
+    def poisson(self, grid: Grid, rho: torch.Tensor, want_phi: bool = True):
+        p = rho.shape[0]
+        F = self._empty(p, grid.Nx)
+        phi = self._empty(p, grid.Nx) if want_phi else None
+        E = self._empty(p)
+        self._check(self.lib.vp_poisson_periodic(self.h, C.byref(grid), p, _ptr(rho, name="rho"),
+                                                 _ptr(phi), _ptr(F), _ptr(E), self._stream()),
+                    "poisson")
+        return F, phi, E
+
+    def gather(self, grid: Grid, X: torch.Tensor, F: torch.Tensor, idx: torch.Tensor | None = None):
+        p, N = X.shape
+        d = 0 if idx is None else idx.numel()
+        GX = self._empty(p, N if idx is None else d)
+        self._check(self.lib.vp_gather_E(self.h, C.byref(grid), N, p, _ptr(X, name="X"), N,
+                                         _ptr(F, name="F"), _ptr(idx, torch.int32, "idx"), d,
+                                         _ptr(GX), self._stream()), "gather")
+        return GX
+
+    def full_step(self, grid: Grid, X: torch.Tensor, V: torch.Tensor, dt: float, nsteps: int,
+                  trace: bool = True):
+        p, N = X.shape
+        tr = self._empty(nsteps, p, 2) if trace else None
+        self._check(self.lib.vp_full_step(self.h, C.byref(grid), N, p, _ptr(X, name="X"),
+                                          _ptr(V, name="V"), dt, nsteps, _ptr(tr),
+                                          self._stream()), "full_step")
+        return tr
+
+    # -- reduced model
+    def reconstruct(self, Q: torch.Tensor, Z: torch.Tensor, want_v: bool = True):
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        X = self._empty(p, N)
+        V = self._empty(p, N) if want_v else None
+        self._check(self.lib.vp_reconstruct(self.h, N, n2 // 2, p, _ptr(Q, name="Q"),
+                                            _ptr(Z, name="Z"), _ptr(X), _ptr(V), self._stream()),
+                    "reconstruct")
+        return X, V
+
+    def project_grad(self, Q: torch.Tensor, GX: torch.Tensor | None, Z: torch.Tensor):
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        g = self._empty(n2, p)
+        self._check(self.lib.vp_project_grad(self.h, N, n2 // 2, p, _ptr(Q, name="Q"),
+                                             _ptr(GX, name="GX"), _ptr(Z, name="Z"), _ptr(g),
+                                             self._stream()), "project_grad")
+        return g
+
+    def basis_velocity(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor):
+        N, n2 = Q.shape
+        Xi = self._empty(N, n2)
+        self._check(self.lib.vp_basis_velocity(self.h, C.byref(grid), N, n2 // 2, Z.shape[1],
+                                               _ptr(Q, name="Q"), _ptr(Z, name="Z"), _ptr(Xi),
+                                               self._stream()), "basis_velocity")
+        return Xi
+
+    def cayley_retract(self, Q0: torch.Tensor, xi: torch.Tensor, out: torch.Tensor | None = None):
+        N, n2 = Q0.shape
+        out = self._empty(N, n2) if out is None else out
+        self._check(self.lib.vp_cayley_retract(self.h, N, n2 // 2, _ptr(Q0, name="Q0"),
+                                               _ptr(xi, name="xi"), _ptr(out, name="out"),
+                                               self._stream()), "cayley_retract")
+        return out
+
+    def tangent_velocity(self, grid: Grid, Q0: torch.Tensor, xi: torch.Tensor, Z: torch.Tensor):
+        N, n2 = Q0.shape
+        Y = self._empty(N, n2)
+        self._check(self.lib.vp_tangent_velocity(self.h, C.byref(grid), N, n2 // 2, Z.shape[1],
+                                                 _ptr(Q0, name="Q0"), _ptr(xi, name="xi"),
+                                                 _ptr(Z, name="Z"), _ptr(Y), self._stream()),
+                    "tangent_velocity")
+        return Y
+
+    def basis_update(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int,
+                     tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
+                     trace: bool = True, iters: bool = True):
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        tr = self._empty(nsteps + 1, p, 2) if trace else None
+        it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
+        opts = StepOpts(tol, maxit, int(freeze_basis))
+        self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,
+                                             _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
+                                             C.byref(opts), _ptr(tr),
+                                             _ptr(it, torch.int32), self._stream()),
+                    "basis_update")
+        return tr, it
+
+    def reduced_energy(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor):
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        E, H, r = self._empty(p), self._empty(p), self._empty(1)
+        self._check(self.lib.vp_reduced_energy(self.h, C.byref(grid), N, n2 // 2, p,
+                                               _ptr(Q, name="Q"), _ptr(Z, name="Z"), _ptr(E),
+                                               _ptr(H), _ptr(r), self._stream()), "reduced_energy")
+        return E, H, r
+
+    def deim_gather_project(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, idx: torch.Tensor,
+                            c: torch.Tensor, phi: torch.Tensor):
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        g = self._empty(n2, p)
+        self._check(self.lib.vp_deim_gather_project(self.h, C.byref(grid), N, n2 // 2, p,
+                                                    _ptr(Q, name="Q"), _ptr(Z, name="Z"),
+                                                    idx.numel(), _ptr(idx, torch.int32, "idx"),
+                                                    _ptr(c, name="c"), _ptr(phi, name="phi"),
+                                                    _ptr(g), self._stream()), "deim_gather_project")
+        return g
+
+
+_default: dict[int, Context] = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]

@@ -1,0 +1,431 @@
+// Single-block FP64 kernels for the small dense algebra of the reduced model:
+// n x n complex matrices (n <= 40) built from Gram matrices over the N rows,
+// Gauss-Jordan solves with partial pivoting, and the per-step coefficient
+// updates.  Complex n x n matrices are row-major double2 in global memory.
+#include "vp_internal.cuh"
+
+namespace vpk {
+
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// out = alpha * op(A) op(B) + beta * out (all n x n); op = 0 plain, 1 conj-transpose.
+// out must not alias A or B.  Ends with __syncthreads().
+__device__ void cmm(double2* out, const double2* A, int opA, const double2* B, int opB,
+                    double2 alpha, double beta, int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) {
+      double2 a = opA ? cconj(A[k * n + r]) : A[r * n + k];
+      double2 b = opB ? cconj(B[c * n + k]) : B[k * n + c];
+      s = cadd(s, cmul(a, b));
+    }
+    double2 v = cmul(alpha, s);
+    out[e] = beta == 0.0 ? v : cadd(v, cscale(out[e], beta));
+  }
+  __syncthreads();
+}
+
+// out = a*A + b*op(B) + d*I (elementwise), n x n.  out may alias A.
+__device__ void cadd_mat(double2* out, double a, const double2* A, double b, const double2* B,
+                         int opB, double d, int n) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    double2 x = A ? cscale(A[e], a) : make_double2(0.0, 0.0);
+    if (B) x = cadd(x, cscale(opB ? cconj(B[c * n + r]) : B[e], b));
+    if (r == c) x.x += d;
+    out[e] = x;
+  }
+  __syncthreads();
+}
+
+// Solve A X = B in place (A: n x n, lda; B: n x m, ldb; both in shared
+// memory) by Gauss-Jordan with partial pivoting.  Returns false if a pivot
+// vanishes.  Pivot ties resolve to the lowest row (deterministic).
+__device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m, double2* col) {
+  __shared__ int piv;
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = 1;
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = c;
+      for (int r = c + threadIdx.x; r < n; r += 32) {
+        double v = cabs2(A[r * lda + c]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        piv = bi;
+        if (!(best > 0.0) || !isfinite(best)) ok = 0;
+      }
+    }
+    __syncthreads();
+    if (!ok) return false;
+    const int pr = piv;
+    if (pr != c) {
+      for (int j = threadIdx.x; j < n + m; j += blockDim.x) {
+        double2* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
+        double2* b = j < n ? &A[pr * lda + j] : &B[pr * ldb + j - n];
+        double2 t = *a;
+        *a = *b;
+        *b = t;
+      }
+      __syncthreads();
+    }
+    const double2 pv = A[c * lda + c];
+    const double2 inv = cscale(cconj(pv), 1.0 / cabs2(pv));
+    __syncthreads();
+    for (int j = threadIdx.x; j < n + m; j += blockDim.x) {
+      double2* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
+      *a = cmul(*a, inv);
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = A[r * lda + c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * (n + m); e += blockDim.x) {
+      int r = e / (n + m), j = e - r * (n + m);
+      if (r == c) continue;
+      double2 f = col[r];
+      if (j < n) A[r * lda + j] = csub(A[r * lda + j], cmul(f, A[c * lda + j]));
+      else B[r * ldb + j - n] = csub(B[r * ldb + j - n], cmul(f, B[c * ldb + j - n]));
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Hermitian H = zeta zeta^H (n x n) from Z = [a; b] (2n x p).
+__device__ void zeta_gram(double2* H, const double* Z, int n, int p) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = 0; i < p; ++i) {
+      double2 zr = make_double2(Z[(int64_t)r * p + i], Z[(int64_t)(n + r) * p + i]);
+      double2 zc = make_double2(Z[(int64_t)c * p + i], Z[(int64_t)(n + c) * p + i]);
+      s = cadd(s, cmul(zr, cconj(zc)));
+    }
+    H[e] = s;
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------- basis velocity
+// X(Q, zeta) = -i (M - Q (Q^H M)) H^-1 = M C0 + Q C1 (times scale), with
+// H = zeta zeta^H, C0 = -i scale H^-1, C1 = i scale (Q^H M) H^-1.
+// Shared: aug n x 3n.  Output C (2 x n x n).
+__global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ QhM,
+                                     const double* __restrict__ Z, double scale, double2* C,
+                                     double2* tmp, int* status) {
+  extern __shared__ double2 aug[];
+  const int ld = 3 * n;
+  double2* H = tmp;  // n x n (global scratch)
+  zeta_gram(H, Z, n, p);
+  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+    int r = e / ld, c = e - r * ld;
+    double2 v;
+    if (c < n) v = H[r * n + c];
+    else if (c < 2 * n) v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
+    else v = cconj(QhM[(c - 2 * n) * n + r]);  // (Q^H M)^H
+    aug[e] = v;
+  }
+  __syncthreads();
+  __shared__ double2 col[64];
+  if (!gj_solve(aug, ld, aug + n, ld, n, 2 * n, col)) {
+    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+    return;
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    double2 hinv = aug[r * ld + n + c];              // H^-1
+    double2 y = cconj(aug[c * ld + 2 * n + r]);      // ((H^-1 (Q^H M)^H)^H)[r][c] = (Q^H M H^-1)[r][c]
+    C[e] = make_double2(scale * hinv.y, -scale * hinv.x);          // -i s H^-1
+    C[n * n + e] = make_double2(-scale * y.y, scale * y.x);        // +i s (Q^H M) H^-1
+  }
+}
+
+void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
+                        double2* C, double2* tmp, int* status, cudaStream_t st) {
+  size_t smem = sizeof(double2) * n * 3 * n;
+  k_small_basis_coeffs<<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status);
+}
+
+// ------------------------------------------------------- Cayley retraction
+// Inputs G0 = Q0^H Q0, P = Q0^H xi, XX = xi^H xi.  With W = xi - Q0 P / 2,
+// C = [W, -Q0], D = [Q0, W]:  R = Q0 + C (I - D^H C / 2)^-1 D^H Q0
+//   = Q0 (I - P Yt / 2 - Yb) + xi Yt,   [Yt; Yb] = (I - K/2)^-1 [G0; W^H Q0],
+// K = D^H C = [[Q0^H W, -G0], [W^H W, -W^H Q0]],
+// Q0^H W = P - G0 P / 2,  W^H W = XX - P^H P + P^H G0 P / 4.
+// Output C (2 x n x n): coefficient of Q0, coefficient of xi.
+__global__ void k_small_cayley(int n, const double2* __restrict__ G0, const double2* __restrict__ P,
+                               const double2* __restrict__ XX, double2* C, double2* tmp,
+                               int* status) {
+  extern __shared__ double2 aug[];  // 2n x 3n
+  const int nn = n * n, ld = 3 * n;
+  double2* T = tmp;            // G0 P
+  double2* QW = tmp + nn;      // Q0^H W
+  double2* WW = tmp + 2 * nn;  // W^H W
+  const double2 one = make_double2(1.0, 0.0);
+  cmm(T, G0, 0, P, 0, one, 0.0, n);
+  cadd_mat(QW, 1.0, P, -0.5, T, 0, 0.0, n);
+  cmm(WW, P, 1, P, 0, make_double2(-1.0, 0.0), 0.0, n);
+  cmm(WW, P, 1, T, 0, make_double2(0.25, 0.0), 1.0, n);
+  cadd_mat(WW, 1.0, WW, 1.0, XX, 0, 0.0, n);
+  for (int e = threadIdx.x; e < 2 * n * ld; e += blockDim.x) {
+    int r = e / ld, c = e - r * ld;
+    int rb = r >= n, cb = c / n, rr = r - rb * n, cc = c - cb * n;
+    double2 v;
+    double d = (rr == cc) ? 1.0 : 0.0;
+    if (!rb && cb == 0) v = make_double2(d - 0.5 * QW[rr * n + cc].x, -0.5 * QW[rr * n + cc].y);
+    else if (!rb && cb == 1) v = cscale(G0[rr * n + cc], 0.5);
+    else if (!rb && cb == 2) v = G0[rr * n + cc];
+    else if (rb && cb == 0) v = cscale(WW[rr * n + cc], -0.5);
+    else {  // W^H Q0 = (Q0^H W)^H
+      double2 wq = cconj(QW[cc * n + rr]);
+      v = (cb == 1) ? make_double2(d + 0.5 * wq.x, 0.5 * wq.y) : wq;
+    }
+    aug[e] = v;
+  }
+  __syncthreads();
+  __shared__ double2 col[128];
+  if (!gj_solve(aug, ld, aug + 2 * n, ld, 2 * n, n, col)) {
+    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+    return;
+  }
+  // copy Yt, Yb to global scratch (reuse T, QW)
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    T[e] = aug[r * ld + 2 * n + c];         // Yt
+    QW[e] = aug[(n + r) * ld + 2 * n + c];  // Yb
+  }
+  __syncthreads();
+  // alpha = I - P Yt / 2 - Yb ; beta = Yt
+  cmm(C, P, 0, T, 0, make_double2(-0.5, 0.0), 0.0, n);
+  cadd_mat(C, 1.0, C, -1.0, QW, 0, 1.0, n);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) C[nn + e] = T[e];
+}
+
+void small_cayley_coeffs(int n, const double2* G0, const double2* P, const double2* XX, double2* C,
+                         double2* tmp, int* status, cudaStream_t st) {
+  size_t smem = sizeof(double2) * 2 * n * 3 * n;
+  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status);
+}
+
+// ------------------------------------------------------- tangent velocity
+// Y(xi, Z) (Sec. 5) with R = R_Q0(xi), Xp = X(R, Z), W = xi - Q0 P / 2:
+//   Ups = (2 Xp - W (Q0^H Xp) + Q0 (W^H Xp)) T1,   T1 = (Q0^H R + I)^-1
+//   Y   = -Q0 T2 (R + Q0)^H Ups + Ups - Q0 (Ups^H Q0),   T2 = (R^H Q0 + I)^-1 = T1^H
+// Written as Ups = Xp u1 + xi u2 + Q0 u3 and Y = Xp u1 + xi u2 + Q0 c with
+//   u1 = 2 T1, u2 = -A1 T1, u3 = (P A1 / 2 + A2 - P^H A1 / 2) T1,
+//   Q0^H Ups = A1 u1 + P u2 + G0 u3,  R^H Ups = A4 u1 + A5 u2 + A3^H u3,
+//   c = u3 - T2 (R^H Ups + Q0^H Ups) - (Q0^H Ups)^H,
+// where A1 = Q0^H Xp, A2 = xi^H Xp, A3 = Q0^H R, A4 = R^H Xp, A5 = R^H xi.
+// grams: [A1, A2, A3, A4, A5] (5 x n x n); output C = scale * [u1, u2, c]
+// (coefficients of Xp, xi, Q0).
+__global__ void k_small_tangent(int n, const double2* __restrict__ grams,
+                                const double2* __restrict__ G0, const double2* __restrict__ P,
+                                double scale, double2* C, double2* tmp, int* status) {
+  extern __shared__ double2 aug[];  // n x 2n
+  const int nn = n * n, ld = 2 * n;
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  const double2 *A1 = grams, *A2 = grams + nn, *A3 = grams + 2 * nn, *A4 = grams + 3 * nn,
+                *A5 = grams + 4 * nn;
+  double2 *T1 = tmp, *u1 = tmp + nn, *u2 = tmp + 2 * nn, *u3 = tmp + 3 * nn, *W1 = tmp + 4 * nn,
+          *QU = tmp + 5 * nn, *RU = tmp + 6 * nn, *W2 = tmp + 7 * nn;
+  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+    int r = e / ld, c = e - r * ld;
+    double2 v;
+    if (c < n) { v = A3[r * n + c]; if (r == c) v.x += 1.0; }
+    else v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
+    aug[e] = v;
+  }
+  __syncthreads();
+  __shared__ double2 col[64];
+  if (!gj_solve(aug, ld, aug + n, ld, n, n, col)) {
+    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+    return;
+  }
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    T1[e] = aug[r * ld + n + c];
+  }
+  __syncthreads();
+  cadd_mat(u1, 2.0, T1, 0.0, nullptr, 0, 0.0, n);
+  cmm(u2, A1, 0, T1, 0, mone, 0.0, n);
+  // W1 = P A1 / 2 + A2 - P^H A1 / 2
+  cmm(W1, P, 0, A1, 0, make_double2(0.5, 0.0), 0.0, n);
+  cmm(W1, P, 1, A1, 0, make_double2(-0.5, 0.0), 1.0, n);
+  cadd_mat(W1, 1.0, W1, 1.0, A2, 0, 0.0, n);
+  cmm(u3, W1, 0, T1, 0, one, 0.0, n);
+  // QU = A1 u1 + P u2 + G0 u3
+  cmm(QU, A1, 0, u1, 0, one, 0.0, n);
+  cmm(QU, P, 0, u2, 0, one, 1.0, n);
+  cmm(QU, G0, 0, u3, 0, one, 1.0, n);
+  // RU = A4 u1 + A5 u2 + A3^H u3
+  cmm(RU, A4, 0, u1, 0, one, 0.0, n);
+  cmm(RU, A5, 0, u2, 0, one, 1.0, n);
+  cmm(RU, A3, 1, u3, 0, one, 1.0, n);
+  // c = u3 - T1^H (RU + QU) - QU^H
+  cadd_mat(W2, 1.0, RU, 1.0, QU, 0, 0.0, n);
+  cmm(W1, T1, 1, W2, 0, one, 0.0, n);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    double2 cc = csub(csub(u3[e], W1[e]), cconj(QU[c * n + r]));
+    C[e] = cscale(u1[e], scale);
+    C[nn + e] = cscale(u2[e], scale);
+    C[2 * nn + e] = cscale(cc, scale);
+  }
+}
+
+void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
+                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st) {
+  size_t smem = sizeof(double2) * n * 2 * n;
+  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status);
+}
+
+// ------------------------------------------------- fixed-point iteration
+// g = gX + G_V Ze, G_V = U_V^T U_V from the raw Gram of the stored rows
+// [A | B] (U_V = [B, A]); k_new = J_2n g; |k_new - k| <= tol |k_new| stops.
+__device__ __forceinline__ int vperm(int k, int n) { return k < n ? n + k : k - n; }
+
+__device__ double block_sum2(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
+                               const double* __restrict__ GVraw, const double* __restrict__ Z0,
+                               double* k, double* Ze, double dt, double tol, int maxit, int* done,
+                               int* iters, int* status) {
+  if (*done) return;
+  __shared__ double red[32];
+  const int n2 = 2 * n;
+  const int64_t tot = (int64_t)n2 * p;
+  double d2 = 0.0, k2 = 0.0;
+  // k_new[r] = g[n + r] (r < n), k_new[n + r] = -g[r]; compute g rows on demand
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    int r = (int)(e / p), i = (int)(e - (int64_t)r * p);
+    int gr = r < n ? n + r : r - n;
+    double sgn = r < n ? 1.0 : -1.0;
+    double g = gX[(int64_t)gr * p + i];
+    const int pr = vperm(gr, n);
+    for (int c = 0; c < n2; ++c) g = fma(GVraw[pr * n2 + vperm(c, n)], Ze[(int64_t)c * p + i], g);
+    double kn = sgn * g;
+    double dk = kn - k[e];
+    d2 = fma(dk, dk, d2);
+    k2 = fma(kn, kn, k2);
+    k[e] = kn;  // element e of k is read only by this thread
+  }
+  __syncthreads();  // every read of Ze above precedes the update below
+  double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red);
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) Ze[e] = fma(0.5 * dt, k[e], Z0[e]);
+  if (threadIdx.x == 0) {
+    int it = *iters + 1;
+    *iters = it;
+    bool conv = sqrt(D2) <= tol * sqrt(K2);
+    if (!isfinite(D2) || !isfinite(K2)) {
+      vp_set_status(status, VP_ENUMERIC);
+      *done = 1;
+    } else if (conv) {
+      *done = 1;
+    } else if (it >= maxit) {
+      vp_set_status(status, VP_ENOCONV);
+      *done = 1;
+    }
+  }
+}
+
+void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
+                  double* Ze, double dt, double tol, int maxit, int* done, int* iters, int* status,
+                  cudaStream_t st) {
+  k_coeff_update<<<1, 1024, 0, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, done, iters, status);
+}
+
+// Z1 = Z0 + dt k
+__global__ void k_axpy(int64_t m, double a, const double* x, const double* y, double* out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < m) out[e] = fma(a, x[e], y[e]);
+}
+void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st) {
+  k_axpy<<<ceil_div(m, 256), 256, 0, st>>>(m, a, x, y, out);
+}
+
+// g = gX + G_V Z (2n x p), G_V = U_V^T U_V from the raw Gram; gX may be null.
+__global__ void k_add_linear(int n, int p, const double* __restrict__ gX,
+                             const double* __restrict__ GVraw, const double* __restrict__ Z,
+                             double* __restrict__ g) {
+  const int n2 = 2 * n;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n2 * p) return;
+  int r = (int)(e / p), i = (int)(e - (int64_t)r * p);
+  double s = gX ? gX[e] : 0.0;
+  const int pr = vperm(r, n);
+  for (int c = 0; c < n2; ++c) s = fma(GVraw[pr * n2 + vperm(c, n)], Z[(int64_t)c * p + i], s);
+  g[e] = s;
+}
+void add_linear(int n, int p, const double* gX, const double* GVraw, const double* Z, double* g,
+                cudaStream_t st) {
+  int64_t m = (int64_t)2 * n * p;
+  k_add_linear<<<ceil_div(m, 256), 256, 0, st>>>(n, p, gX, GVraw, Z, g);
+}
+
+// --------------------------------------------------------------- energies
+// E_out[i] = Efield[i], H_out[i] = 1/2 Z_i^T G_V Z_i + Efield[i];
+// resid = |Q^H Q - I|_F from the complex Gram QhQ (nullable).
+__global__ void k_energies(int n, int p, const double* __restrict__ GVraw,
+                           const double* __restrict__ Z, const double* __restrict__ Efield,
+                           double* E_out, double* H_out, int64_t stride,
+                           const double2* __restrict__ QhQ, double* resid, int* status) {
+  const int n2 = 2 * n;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    double kin = 0.0;
+    for (int a = 0; a < n2; ++a) {
+      double za = Z[(int64_t)a * p + i];
+      double s = 0.0;
+      for (int b = 0; b < n2; ++b) s = fma(GVraw[vperm(a, n) * n2 + vperm(b, n)], Z[(int64_t)b * p + i], s);
+      kin = fma(za, s, kin);
+    }
+    double E = Efield[i];
+    double H = 0.5 * kin + E;
+    if (E_out) E_out[i * stride] = E;
+    if (H_out) H_out[i * stride] = H;
+    if (!isfinite(H)) vp_set_status(status, VP_ENUMERIC);
+  }
+  if (QhQ && resid) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int r = e / n, c = e - r * n;
+      double2 v = QhQ[e];
+      if (r == c) v.x -= 1.0;
+      s += cabs2(v);
+    }
+    double tot = block_sum2(s, red);
+    if (threadIdx.x == 0) *resid = sqrt(tot);
+  }
+}
+
+void energies(int n, int p, const double* GVraw, const double* Z, const double* Efield,
+              double* E_out, double* H_out, int64_t stride, const double2* QhQ, double* resid,
+              int* status, cudaStream_t st) {
+  k_energies<<<1, 256, 0, st>>>(n, p, GVraw, Z, Efield, E_out, H_out, stride, QhQ, resid, status);
+}
+
+void dense_init() {
+  cudaFuncSetAttribute(k_small_basis_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_cayley, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+}  // namespace vpk

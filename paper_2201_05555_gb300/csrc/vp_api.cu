@@ -1,0 +1,667 @@
+// C ABI of libvp: argument checks, workspace, and the composition of the
+// kernels into the calls declared in include/vp.h.
+#include "vp_internal.cuh"
+
+#include <cstdarg>
+#include <cmath>
+#include <vector>
+
+using namespace vpk;
+
+// ------------------------------------------------------------ context glue
+vp_status vp_fail(vp_ctx* ctx, vp_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return s;
+}
+
+vp_status vp_cuda_check(vp_ctx* ctx, cudaError_t e, const char* what) {
+  return vp_fail(ctx, e == cudaErrorMemoryAllocation ? VP_ENOMEM : VP_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+vp_status vp_workspace(vp_ctx* ctx, size_t bytes, void** out) {
+  if (bytes > ctx->budget)
+    return vp_fail(ctx, VP_ENOMEM, "workspace of %zu bytes exceeds the context budget %zu", bytes,
+                   ctx->budget);
+  if (bytes > ctx->ws_bytes) {
+    if (ctx->ws) {
+      VP_CUDA(cudaDeviceSynchronize());
+      VP_CUDA(cudaFree(ctx->ws));
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4;
+    if (want > ctx->budget) want = bytes;
+    VP_CUDA(cudaMalloc(&ctx->ws, want));
+    ctx->ws_bytes = want;
+  }
+  *out = ctx->ws;
+  return VP_OK;
+}
+
+namespace {
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define VP_ENTER()                                              \
+  if (!ctx) return VP_EINVAL;                                   \
+  std::lock_guard<std::mutex> lock_(ctx->mu);                   \
+  DeviceGuard guard_(ctx->device);                              \
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);     \
+  (void)st;
+
+vp_status check_grid(vp_ctx* ctx, const vp_grid* g) {
+  if (!g) return vp_fail(ctx, VP_EINVAL, "grid is NULL");
+  if (g->Nx < 3 || g->Nx > VP_MAX_NX)
+    return vp_fail(ctx, VP_EINVAL, "Nx = %d outside [3, %d]", g->Nx, VP_MAX_NX);
+  if (!(g->L > 0.0) || !std::isfinite(g->L)) return vp_fail(ctx, VP_EINVAL, "L must be > 0");
+  if (!(g->mp > 0.0) || !std::isfinite(g->mp)) return vp_fail(ctx, VP_EINVAL, "mp must be > 0");
+  if (!std::isfinite(g->Mq) || !std::isfinite(g->background))
+    return vp_fail(ctx, VP_EINVAL, "Mq and background must be finite");
+  return VP_OK;
+}
+
+vp_status check_np(vp_ctx* ctx, int64_t N, int32_t p) {
+  if (N < 1 || N >= (int64_t(1) << 31)) return vp_fail(ctx, VP_EINVAL, "N = %lld outside [1, 2^31)", (long long)N);
+  if (p < 1 || p > 65535) return vp_fail(ctx, VP_EINVAL, "p = %d outside [1, 65535]", p);
+  return VP_OK;
+}
+
+vp_status check_n(vp_ctx* ctx, int32_t n, int64_t N) {
+  if (n < 1 || n > 40) return vp_fail(ctx, VP_EUNSUPPORTED, "n = %d outside [1, 40] (2n <= 80)", n);
+  if (n > N) return vp_fail(ctx, VP_EINVAL, "n = %d exceeds N = %lld", n, (long long)N);
+  return VP_OK;
+}
+
+#define VP_TRY(x)                      \
+  do {                                 \
+    vp_status s_ = (x);                \
+    if (s_ != VP_OK) return s_;        \
+  } while (0)
+
+// Workspace of the reduced-model calls.
+struct RedWS {
+  unsigned long long* counts;
+  double *F, *Efield, *part, *gX, *k, *Ze, *Z0, *Z1, *GVraw, *aux;
+  double2 *grams, *cay, *C, *tmp;
+  int* flags;  // [0] done, [1] iters
+  double* rows[5];
+  int gx_proj, gx_gram;
+};
+
+vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w) {
+  const int n2 = 2 * n, nn = n * n;
+  const int sms = ctx->num_sms;
+  w.gx_proj = tile_grid_x(N, project_chunks(p, Nx > 0 ? Nx : 3), sms);
+  w.gx_gram = gram_grid_x(N, sms);
+  size_t part_d = std::max<size_t>((size_t)w.gx_proj * n2 * p,
+                                   std::max<size_t>((size_t)w.gx_gram * 12 * nn * 2,
+                                                    (size_t)w.gx_gram * n2 * n2));
+  size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
+  size_t bytes = arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
+                 arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)n2 * n2, 8) +
+                 arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) +
+                 arena_bytes(4 * nn, 16) + arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) +
+                 arena_bytes(8, 4) + (size_t)nrows * arena_bytes((size_t)N * n2, 8);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, bytes, &base));
+  Arena a{(char*)base, 0, bytes};
+  w.counts = a.take<unsigned long long>(pn);
+  w.F = a.take<double>(pn);
+  w.Efield = a.take<double>(p);
+  w.part = a.take<double>(part_d);
+  w.gX = a.take<double>((size_t)n2 * p);
+  w.k = a.take<double>((size_t)n2 * p);
+  w.Ze = a.take<double>((size_t)n2 * p);
+  w.Z0 = a.take<double>((size_t)n2 * p);
+  w.Z1 = a.take<double>((size_t)n2 * p);
+  w.GVraw = a.take<double>((size_t)n2 * n2);
+  w.aux = a.take<double>((size_t)n2 * p + 64);
+  w.grams = a.take<double2>(12 * nn);
+  w.cay = a.take<double2>(4 * nn);
+  w.C = a.take<double2>(4 * nn);
+  w.tmp = a.take<double2>(10 * nn);
+  w.flags = a.take<int>(8);
+  for (int r = 0; r < 5; ++r) w.rows[r] = r < nrows ? a.take<double>((size_t)N * n2) : nullptr;
+  return VP_OK;
+}
+
+// ------------------------------------------------------- reduced building blocks
+struct Red {
+  vp_ctx* ctx;
+  GridC g;
+  int64_t N;
+  int n, p;
+  RedWS w;
+  cudaStream_t st;
+
+  // deposit X_r = Re(Q Z) and solve: F, Efield (counts zeroed again by the solve)
+  void field(const double* Q, const double* Z, const int* skip = nullptr) {
+    VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
+    VP_K(VP_K_POISSON, poisson(g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip, ctx->d_status, st));
+  }
+  // Grams out_s = blk[pa]^H blk[pb] into `out` (npairs x n x n double2)
+  void grams(std::initializer_list<const double*> blks,
+             std::initializer_list<std::pair<int, int>> pairs, double2* out) {
+    GramArgs a{};
+    a.nblk = 0;
+    for (const double* b : blks) a.blk[a.nblk++] = b;
+    a.npairs = 0;
+    for (auto pr : pairs) {
+      a.pa[a.npairs] = pr.first;
+      a.pb[a.npairs] = pr.second;
+      ++a.npairs;
+    }
+    VP_K(VP_K_GRAM, gram(N, n, a, reinterpret_cast<double2*>(w.part), w.gx_gram, st));
+    VP_K(VP_K_REDUCE, reduce_partials(w.gx_gram, (int64_t)a.npairs * n * n * 2, w.part,
+                    reinterpret_cast<double*>(out), nullptr, st));
+  }
+  void gv(const double* Q, double* GVraw) {
+    VP_K(VP_K_GRAM_REAL, gram_real(N, 2 * n, Q, w.part, w.gx_gram, st));
+    VP_K(VP_K_REDUCE, reduce_partials(w.gx_gram, (int64_t)4 * n * n, w.part, GVraw, nullptr, st));
+  }
+  void comb(std::initializer_list<const double*> xs, const double2* C, double* out) {
+    AffineArgs a{};
+    a.nterms = 0;
+    for (const double* x : xs) a.X[a.nterms++] = x;
+    VP_K(VP_K_AFFINE, affine(N, n, a, C, out, ctx->num_sms, st));
+  }
+  // X(Q, Z) * scale into out, using M as scratch (F must hold the field at (Q, Z))
+  void basis_velocity_from_field(const double* Q, const double* Z, double scale, double* M,
+                                 double* out) {
+    VP_K(VP_K_BASIS_M, basis_M(g, N, n, p, Q, Z, w.F, M, ctx->num_sms, st));
+    grams({Q, M}, {{0, 1}}, w.grams);
+    VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
+    comb({M, Q}, w.C, out);
+  }
+  // Qout = R_Q0(xi); leaves G0, P, XX in w.cay[0..3n^2)
+  void cayley(const double* Q0, const double* xi, double* Qout) {
+    grams({Q0, xi}, {{0, 0}, {0, 1}, {1, 1}}, w.cay);
+    const int nn = n * n;
+    VP_K(VP_K_SMALL_CAYLEY, small_cayley_coeffs(n, w.cay, w.cay + nn, w.cay + 2 * nn, w.C, w.tmp, ctx->d_status, st));
+    comb({Q0, xi}, w.C, Qout);
+  }
+  // Y(xi, Z) * scale with Qh = R_Q0(xi) and Xp = X(Qh, Z) given; w.cay must hold
+  // the Cayley Grams of (Q0, xi).
+  void tangent(const double* Q0, const double* xi, const double* Qh, const double* Xp, double scale,
+               double* out) {
+    grams({Q0, xi, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
+    const int nn = n * n;
+    VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, scale, w.C, w.tmp, ctx->d_status, st));
+    comb({Xp, xi, Q0}, w.C, out);
+  }
+};
+
+vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, int nrows,
+                    cudaStream_t st, Red& R) {
+  R.ctx = ctx;
+  R.N = N;
+  R.n = n;
+  R.p = p;
+  R.st = st;
+  if (grid) R.g = make_gridc(*grid, N);
+  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w));
+  if (grid) VP_CUDA(cudaMemsetAsync(R.w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
+  return VP_OK;
+}
+}  // namespace
+
+// ============================================================== profiling
+static const char* kKernelNames[VP_K_COUNT] = {
+    "k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step", "k_reconstruct",
+    "k_deposit_reduced", "k_project", "k_basis_M", "k_gram", "k_gram_real", "k_reduce_partials",
+    "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
+    "k_coeff_update", "k_axpy", "k_add_linear", "k_energies"};
+
+static cudaEvent_t take_event(vp_ctx* ctx) {
+  if (ctx->event_pool.empty()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = ctx->event_pool.back();
+  ctx->event_pool.pop_back();
+  return e;
+}
+
+void vp_prof_begin(vp_ctx* ctx, int id, cudaStream_t st, cudaEvent_t* a) {
+  ctx->launches[id] += 1;
+  *a = nullptr;
+  if (!(ctx->prof_mask >> id & 1ull)) return;
+  if (ctx->pending.size() > 4096) vp_prof_collect(ctx);
+  *a = take_event(ctx);
+  if (*a) cudaEventRecord(*a, st);
+}
+
+void vp_prof_end(vp_ctx* ctx, int id, cudaStream_t st, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b = take_event(ctx);
+  if (!b) {
+    ctx->event_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, st);
+  ctx->pending.push_back({id, a, b});
+}
+
+void vp_prof_collect(vp_ctx* ctx) {
+  for (auto& q : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      ctx->ms[q.id] += ms;
+      ctx->timed[q.id] += 1;
+    }
+    ctx->event_pool.push_back(q.a);
+    ctx->event_pool.push_back(q.b);
+  }
+  ctx->pending.clear();
+  (void)cudaGetLastError();
+}
+
+// ================================================================ context
+extern "C" {
+
+vp_status vp_profile_enable(vp_ctx* ctx, uint64_t mask) {
+  if (!ctx) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->prof_mask = mask;
+  return VP_OK;
+}
+
+vp_status vp_profile_read(vp_ctx* ctx, int32_t kernel, int64_t* launches, int64_t* timed,
+                          double* ms_total) {
+  if (!ctx || kernel < 0 || kernel >= VP_K_COUNT) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard guard(ctx->device);
+  vp_prof_collect(ctx);
+  if (launches) *launches = ctx->launches[kernel];
+  if (timed) *timed = ctx->timed[kernel];
+  if (ms_total) *ms_total = ctx->ms[kernel];
+  return VP_OK;
+}
+
+vp_status vp_profile_reset(vp_ctx* ctx) {
+  if (!ctx) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  DeviceGuard guard(ctx->device);
+  vp_prof_collect(ctx);
+  for (int k = 0; k < VP_K_COUNT; ++k) {
+    ctx->launches[k] = 0;
+    ctx->timed[k] = 0;
+    ctx->ms[k] = 0.0;
+  }
+  return VP_OK;
+}
+
+const char* vp_kernel_name(int32_t kernel) {
+  return (kernel >= 0 && kernel < VP_K_COUNT) ? kKernelNames[kernel] : "unknown";
+}
+
+
+int32_t vp_version(void) { return 10000; }
+
+const char* vp_status_string(vp_status s) {
+  switch (s) {
+    case VP_OK: return "ok";
+    case VP_EINVAL: return "invalid argument";
+    case VP_ENOMEM: return "out of memory / over budget";
+    case VP_EBUSY: return "busy";
+    case VP_EAGAIN: return "not ready";
+    case VP_ETIMEDOUT: return "timed out";
+    case VP_ENOCONV: return "fixed point did not converge";
+    case VP_ENUMERIC: return "non-finite value or singular system";
+    case VP_EDRIFT: return "basis left the ortho-symplectic manifold";
+    case VP_ECUDA: return "CUDA error";
+    case VP_EUNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
+  if (!out) return VP_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VP_ECUDA;
+  vp_ctx* ctx = new vp_ctx();
+  ctx->device = device;
+  ctx->budget = scratch_bytes ? scratch_bytes : (size_t(4) << 30);
+  DeviceGuard guard(device);
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&ctx->d_status, 64) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_pinned, 64) != cudaSuccess) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return VP_ENOMEM;
+  }
+  cudaMemset(ctx->d_status, 0, 64);
+  memset(ctx->h_pinned, 0, 64);
+  pic_init();
+  reduced_init();
+  dense_init();
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return VP_ECUDA;
+  }
+  *out = ctx;
+  return VP_OK;
+}
+
+vp_status vp_ctx_destroy(vp_ctx* ctx) {
+  if (!ctx) return VP_EINVAL;
+  {
+    DeviceGuard guard(ctx->device);
+    cudaDeviceSynchronize();
+    vp_prof_collect(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  }
+  delete ctx;
+  return VP_OK;
+}
+
+const char* vp_last_error(const vp_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+size_t vp_ctx_workspace_bytes(const vp_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+vp_status vp_ctx_sync_status(vp_ctx* ctx, void* stream) {
+  VP_ENTER();
+  VP_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VP_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  VP_CUDA(cudaStreamSynchronize(st));
+  int s = ctx->h_pinned[0];
+  if (s != 0) return vp_fail(ctx, (vp_status)s, "device reported: %s", vp_status_string((vp_status)s));
+  return VP_OK;
+}
+
+// ======================================================= particle-grid maps
+vp_status vp_deposit_cic(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const double* X,
+                         int64_t ldx, double* rho, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  if (!X || !rho || ldx < N) return vp_fail(ctx, VP_EINVAL, "null pointer or ldx < N");
+  GridC g = make_gridc(*grid, N);
+  void* base;
+  size_t cb = sizeof(unsigned long long) * p * grid->Nx;
+  VP_TRY(vp_workspace(ctx, cb, &base));
+  auto* counts = (unsigned long long*)base;
+  VP_CUDA(cudaMemsetAsync(counts, 0, cb, st));
+  VP_K(VP_K_DEPOSIT, deposit_samples(g, N, p, X, ldx, counts, ctx->num_sms, st));
+  VP_K(VP_K_RHO, counts_to_rho(g, p, counts, rho, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_poisson_periodic(vp_ctx* ctx, const vp_grid* grid, int32_t p, const double* rho,
+                              double* phi, double* F, double* energy, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, 1, p));
+  if (!rho || !F) return vp_fail(ctx, VP_EINVAL, "rho and F are required");
+  GridC g = make_gridc(*grid, 1);
+  VP_K(VP_K_POISSON, poisson(g, p, rho, nullptr, phi, F, energy, nullptr, nullptr, ctx->d_status, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_gather_E(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const double* X,
+                      int64_t ldx, const double* F, const int32_t* idx, int64_t d, double* GX,
+                      void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  if (!X || !F || !GX || ldx < N) return vp_fail(ctx, VP_EINVAL, "null pointer or ldx < N");
+  if (idx && (d < 1 || d > N)) return vp_fail(ctx, VP_EINVAL, "d = %lld outside [1, N]", (long long)d);
+  GridC g = make_gridc(*grid, N);
+  VP_K(VP_K_GATHER, gather(g, N, p, X, ldx, F, idx, d, GX, ctx->num_sms, ctx->d_status, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_full_step(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, double* X, double* V,
+                       double dt, int32_t nsteps, double* trace, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  if (!X || !V) return vp_fail(ctx, VP_EINVAL, "X and V are required");
+  if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
+  if (nsteps == 0) return VP_OK;
+  GridC g = make_gridc(*grid, N);
+  cudaError_t fe = cudaSuccess;
+  VP_K(VP_K_FULL_STEP, fe = full_step(g, N, p, X, V, dt, nsteps, trace, ctx->d_status, st));
+  VP_CUDA(fe);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+// ============================================================ reduced model
+vp_status vp_reconstruct(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q,
+                         const double* Z, double* X, double* V, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !X) return vp_fail(ctx, VP_EINVAL, "Q, Z and X are required");
+  VP_K(VP_K_RECONSTRUCT, reconstruct(N, n, p, Q, Z, X, V, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_project_grad(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q,
+                          const double* GX, const double* Z, double* g_out, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !g_out) return vp_fail(ctx, VP_EINVAL, "Q, Z and g are required");
+  Red R;
+  vp_grid dummy{3, 1.0, 0.0, 1.0, 0.0};
+  VP_TRY(red_setup(ctx, &dummy, N, n, p, 0, st, R));
+  if (GX) {
+    VP_K(VP_K_PROJECT, project(R.g, N, n, p, Q, Z, nullptr, GX, N, nullptr, nullptr, N, R.w.part, R.w.gx_proj,
+            nullptr, ctx->d_status, st));
+    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_proj, (int64_t)2 * n * p, R.w.part, R.w.gX, nullptr, st));
+  }
+  R.gv(Q, R.w.GVraw);
+  VP_K(VP_K_ADD_LINEAR, add_linear(n, p, GX ? R.w.gX : nullptr, R.w.GVraw, Z, g_out, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_basis_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q, const double* Z, double* Xi, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !Xi) return vp_fail(ctx, VP_EINVAL, "Q, Z and Xi are required");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 1, st, R));
+  R.field(Q, Z);
+  R.basis_velocity_from_field(Q, Z, 1.0, R.w.rows[0], Xi);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_cayley_retract(vp_ctx* ctx, int64_t N, int32_t n, const double* Q0, const double* xi,
+                            double* Qout, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, 1));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q0 || !xi || !Qout) return vp_fail(ctx, VP_EINVAL, "Q0, xi and Qout are required");
+  Red R;
+  VP_TRY(red_setup(ctx, nullptr, N, n, 1, 0, st, R));
+  R.cayley(Q0, xi, Qout);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                              const double* Q0, const double* xi, const double* Z, double* Y,
+                              void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q0 || !xi || !Z || !Y) return vp_fail(ctx, VP_EINVAL, "Q0, xi, Z and Y are required");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 3, st, R));
+  double *Qh = R.w.rows[0], *M = R.w.rows[1], *Xp = R.w.rows[2];
+  R.cayley(Q0, xi, Qh);
+  R.field(Qh, Z);
+  R.basis_velocity_from_field(Qh, Z, 1.0, M, Xp);
+  R.tangent(Q0, xi, Qh, Xp, 1.0, Y);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q, const double* Z, double* E, double* H, double* resid,
+                            void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 0, st, R));
+  R.field(Q, Z);
+  R.gv(Q, R.w.GVraw);
+  if (resid) R.grams({Q}, {{0, 0}}, R.w.grams);
+  VP_K(VP_K_ENERGIES, energies(n, p, R.w.GVraw, Z, R.w.Efield, E, H, 1, resid ? R.w.grams : nullptr, resid,
+           ctx->d_status, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                                 const double* Q, const double* Z, int64_t d, const int32_t* idx,
+                                 const double* c, const double* phi, double* gX, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !idx || !c || !phi || !gX) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  if (d < 1 || d > N) return vp_fail(ctx, VP_EINVAL, "d = %lld outside [1, N]", (long long)d);
+  Red R;
+  VP_TRY(red_setup(ctx, grid, d, n, p, 0, st, R));
+  R.g = make_gridc(*grid, N);
+  VP_K(VP_K_CELL_GRADIENT, cell_gradient(R.g, p, phi, R.w.F, st));
+  VP_K(VP_K_PROJECT, project(R.g, d, n, p, Q, Z, R.w.F, nullptr, 0, idx, c, N, R.w.part, R.w.gx_proj, nullptr,
+          ctx->d_status, st));
+  VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_proj, (int64_t)2 * n * p, R.w.part, gX, nullptr, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+// One partitioned RK2 step per iteration (Sec. 5; stage structure as in the
+// oracle's prk2_step).  Buffers: rows[0] = M / M', rows[1] = xi_half,
+// rows[2] = Q_half, rows[3] = X(Q_half, Z_mid), rows[4] = xi_1 = dt Y.
+vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          double* Q, double* Z, double dt, int32_t nsteps, const vp_step_opts* opts,
+                          double* trace, int32_t* iters, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
+  if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
+  vp_step_opts o{1e-9, 100, 0};
+  if (opts) o = *opts;
+  if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 5, st, R));
+  RedWS& w = R.w;
+  double *M = w.rows[0], *xih = w.rows[1], *Qh = w.rows[2], *Xp = w.rows[3], *xi1 = w.rows[4];
+  const int64_t zsz = (int64_t)2 * n * p;
+  const int64_t tstride = (int64_t)p * 2;
+  int round = 4;
+  for (int step = 0; step < nsteps; ++step) {
+    // stage 1: field at (Q0, Z0); energies of the entering state
+    R.field(Q, Z);
+    if (trace) {
+      R.gv(Q, w.GVraw);
+      VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride, trace + step * tstride + 1, 2,
+               nullptr, nullptr, ctx->d_status, st));
+    }
+    const double* Qmid = Q;
+    if (!o.freeze_basis) {
+      R.basis_velocity_from_field(Q, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
+      R.cayley(Q, xih, Qh);                                 // Q_half = R_Q0(xi_half)
+      Qmid = Qh;
+    }
+    // stage 2: fixed point for k2 at Q_half
+    R.gv(Qmid, w.GVraw);
+    VP_CUDA(cudaMemcpyAsync(w.Z0, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
+    VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+    int done_h = 0, total = 0;
+    while (!done_h) {
+      for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
+        R.field(Qmid, w.Ze, w.flags);
+        VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N, w.part, w.gx_proj,
+                w.flags, ctx->d_status, st));
+        VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
+        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit, w.flags, w.flags + 1,
+                     ctx->d_status, st));
+      }
+      VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      VP_CUDA(cudaStreamSynchronize(st));
+      if (!ctx->pending.empty()) vp_prof_collect(ctx);
+      done_h = ctx->h_pinned[1];
+      if (!done_h && total >= o.maxit) break;
+      round = 2;
+    }
+    const int its = ctx->h_pinned[2];
+    round = its > 2 ? its : 2;
+    if (iters) VP_CUDA(cudaMemcpyAsync(iters + step, w.flags + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    if (!done_h || its >= o.maxit) {
+      // status word carries VP_ENOCONV or VP_ENUMERIC
+      VP_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      VP_CUDA(cudaStreamSynchronize(st));
+      if (ctx->h_pinned[0] != 0 || !done_h)
+        return vp_fail(ctx, VP_ENOCONV, "fixed point did not converge in %d iterations (step %d)",
+                       o.maxit, step);
+    }
+    // Z_mid = w.Ze (= Z0 + dt/2 k2), Z1 = Z0 + dt k2
+    VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
+    if (!o.freeze_basis) {
+      // stage 3: basis velocity at (Q_half, Z_mid), tangent velocity, retraction
+      R.field(Qh, w.Ze);
+      R.basis_velocity_from_field(Qh, w.Ze, 1.0, M, Xp);
+      R.tangent(Q, xih, Qh, Xp, dt, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
+      R.cayley(Q, xi1, Q);                 // Q_1 = R_Q0(xi_1), in place
+    }
+    VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+  }
+  if (trace) {
+    R.field(Q, Z);
+    R.gv(Q, w.GVraw);
+    VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + nsteps * tstride, trace + nsteps * tstride + 1, 2,
+             nullptr, nullptr, ctx->d_status, st));
+  }
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+}  // extern "C"

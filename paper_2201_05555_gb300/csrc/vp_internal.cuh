@@ -1,0 +1,211 @@
+// Internal definitions shared by the translation units of libvp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <mutex>
+#include <vector>
+
+#include "../../include/vp.h"
+
+#define VP_MAX_NX 1024
+#define VP_MAX_N2 128  // 2n <= 128
+#define VP_NSM_DEFAULT 152
+
+// ----------------------------------------------------------------- context
+struct vp_ctx {
+  int device = 0;
+  int num_sms = VP_NSM_DEFAULT;
+  size_t budget = 0;
+  // workspace arena: one device allocation, grown on demand within budget
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // device status word (int32) and a pinned mirror used by host-steered loops
+  int* d_status = nullptr;
+  int* h_pinned = nullptr;  // pinned host ints: [0] status, [1] done flag, [2] iterations
+  std::string last_error;
+  std::mutex mu;
+  // profiling: launch counters and event timers per kernel (vp_kernel ids)
+  uint64_t prof_mask = 0;
+  int64_t launches[VP_K_COUNT] = {};
+  int64_t timed[VP_K_COUNT] = {};
+  double ms[VP_K_COUNT] = {};
+  struct Pending { int id; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// Count (and, if enabled, event-time) one kernel launch made by `expr`.
+void vp_prof_begin(vp_ctx* ctx, int id, cudaStream_t st, cudaEvent_t* a);
+void vp_prof_end(vp_ctx* ctx, int id, cudaStream_t st, cudaEvent_t a);
+void vp_prof_collect(vp_ctx* ctx);  // resolve pending event pairs (synchronises them)
+#define VP_K(id, expr)                               \
+  do {                                               \
+    cudaEvent_t ev_a_ = nullptr;                     \
+    vp_prof_begin(ctx, id, st, &ev_a_);              \
+    expr;                                            \
+    vp_prof_end(ctx, id, st, ev_a_);                 \
+  } while (0)
+
+vp_status vp_fail(vp_ctx* ctx, vp_status s, const char* fmt, ...);
+vp_status vp_cuda_check(vp_ctx* ctx, cudaError_t e, const char* what);
+// Ensure the arena holds at least `bytes`; grows (synchronously) if needed.
+vp_status vp_workspace(vp_ctx* ctx, size_t bytes, void** out);
+
+#define VP_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return vp_cuda_check(ctx, e_, #call);   \
+  } while (0)
+
+#define VP_LAUNCHED()                                              \
+  do {                                                             \
+    cudaError_t e_ = cudaGetLastError();                           \
+    if (e_ != cudaSuccess) return vp_cuda_check(ctx, e_, "launch"); \
+  } while (0)
+
+// Device status word: the first error wins.
+__device__ __forceinline__ void vp_set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// Sub-allocation inside the arena (256-byte aligned).
+struct Arena {
+  char* base;
+  size_t off;
+  size_t cap;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+inline size_t arena_bytes(size_t count, size_t elem) { return (count * elem + 255) & ~size_t(255); }
+
+// ------------------------------------------------------- fixed-point charge
+// Deposit weights lambda in [0,1] are accumulated as integers lambda*2^S.
+// A node receives at most N*2^S < 2^62 (S = 62 - bitlength(N), capped at 52),
+// so the int64 sums never overflow and do not depend on the summation order.
+inline int fixed_point_bits(int64_t N) {
+  int b = 0;
+  while ((int64_t(1) << b) <= N) ++b;  // bitlength(N)
+  int S = 62 - b;
+  return S > 52 ? 52 : S;
+}
+
+// Wrapped cell index and fraction of an unwrapped position x (cell units
+// t = x/h, periodic with period Nx).
+__device__ __forceinline__ void cell_of(double x, double inv_h, int Nx, double dNx, double inv_Nx,
+                                        int& j, double& s) {
+  double t = x * inv_h;
+  double w = floor(t * inv_Nx);
+  double tt = fma(-w, dNx, t);
+  if (tt < 0.0) tt += dNx;
+  if (tt >= dNx) tt -= dNx;
+  double fl = floor(tt);
+  j = (int)fl;
+  if (j > Nx - 1) j = Nx - 1;
+  if (j < 0) j = 0;
+  s = tt - (double)j;
+}
+
+// ----------------------------------------------------------- launch helpers
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Complex FP64 helpers (double2 = re, im).
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// ------------------------------------------------------------ shared state
+// Launch configuration shared by the reduced-model tile kernels.
+#define TILE_ROWS 64     // particles (rows of Q) per tile
+#define TILE_THREADS 256 // threads per block of the tile kernels
+
+// -------------------------------------------------------- internal entry
+// (implemented in the .cu files; used by the API layer)
+namespace vpk {
+
+struct GridC {
+  int Nx;
+  double L, h, inv_h, inv_Nx, dNx, Mq, mp, qm, bg_load, fp_scale, fp_inv;  // fp_*: 2^S, 2^-S
+  int S;
+};
+GridC make_gridc(const vp_grid& g, int64_t N);
+
+struct GramArgs {  // out_s = blk[pa[s]]^H blk[pb[s]]
+  const double* blk[6];
+  int pa[12], pb[12];
+  int nblk, npairs;
+};
+struct AffineArgs {  // out = sum_t X[t] C_t
+  const double* X[4];
+  int nterms;
+};
+
+// pic_kernels.cu
+void deposit_samples(const GridC& g, int64_t N, int p, const double* X, int64_t ldx,
+                     unsigned long long* counts, int num_sms, cudaStream_t st);
+void counts_to_rho(const GridC& g, int p, const unsigned long long* counts, double* rho,
+                   cudaStream_t st);
+void poisson(const GridC& g, int p, const double* rho, const unsigned long long* counts,
+             double* phi, double* F, double* energy, unsigned long long* zero_counts,
+             const int* skip, int* status, cudaStream_t st);
+void gather(const GridC& g, int64_t N, int p, const double* X, int64_t ldx, const double* F,
+            const int32_t* idx, int64_t d, double* GX, int num_sms, int* status, cudaStream_t st);
+cudaError_t full_step(const GridC& g, int64_t N, int p, double* X, double* V, double dt,
+                      int nsteps, double* trace, int* status, cudaStream_t st);
+
+// reduced_kernels.cu
+int tile_grid_x(int64_t N, int chunks, int num_sms);
+int gram_grid_x(int64_t N, int num_sms);
+int project_chunks(int p, int Nx);
+void reconstruct(int64_t N, int n, int p, const double* Q, const double* Z, double* X, double* V,
+                 cudaStream_t st);
+void deposit_reduced(const GridC& g, int64_t N, int n, int p, const double* Q, const double* Z,
+                     unsigned long long* counts, const int* skip, int num_sms, cudaStream_t st);
+void project(const GridC& g, int64_t count, int n, int p, const double* Q, const double* Z,
+             const double* F, const double* GX, int64_t ldg, const int32_t* idx, const double* cw,
+             int64_t nrows, double* part, int gridx, const int* skip, int* status,
+             cudaStream_t st);
+void basis_M(const GridC& g, int64_t N, int n, int p, const double* Q, const double* Z,
+             const double* F, double* M, int num_sms, cudaStream_t st);
+void gram(int64_t N, int n, const GramArgs& a, double2* part, int gridx, cudaStream_t st);
+void gram_real(int64_t N, int m, const double* X, double* part, int gridx, cudaStream_t st);
+void reduce_partials(int nparts, int64_t elems, const double* part, double* out, const int* skip,
+                     cudaStream_t st);
+void affine(int64_t N, int n, const AffineArgs& a, const double2* C, double* out, int num_sms,
+            cudaStream_t st);
+void cell_gradient(const GridC& g, int p, const double* phi, double* F, cudaStream_t st);
+void reduced_init();
+
+// dense.cu (single-block FP64 small dense algebra)
+void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
+                        double2* C, double2* tmp, int* status, cudaStream_t st);
+void small_cayley_coeffs(int n, const double2* G0, const double2* P, const double2* XX, double2* C,
+                         double2* tmp, int* status, cudaStream_t st);
+void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
+                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
+void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
+                  double* Ze, double dt, double tol, int maxit, int* done, int* iters, int* status,
+                  cudaStream_t st);
+void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st);
+void add_linear(int n, int p, const double* gX, const double* GVraw, const double* Z, double* g,
+                cudaStream_t st);
+void energies(int n, int p, const double* GVraw, const double* Z, const double* Efield,
+              double* E_out, double* H_out, int64_t stride, const double2* QhQ, double* resid,
+              int* status, cudaStream_t st);
+void dense_init();
+void pic_init();
+
+}  // namespace vpk
