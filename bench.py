@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the reduced-model hot path on GB300.
+
+Workload (two-stream instability, dynamical reduced model): N = 1e5
+particles per sample, p = 64 samples (v0 on a Hammersley set in [2, 3]),
+rank 2n = 20, Nx = 128, dt = 0.05, FP64.  One step is one partitioned RK2
+step (Sec. 5): basis velocity, Cayley retraction, the fixed-point
+coefficient stage (deposit, Poisson, gather, projection per iteration),
+the tangent velocity and the second retraction, plus the FP64 energy
+diagnostics.  Metric: particle-steps/s = N * p * steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Multi-GPU (torchrun): every rank runs its own replica
+of the workload (weak scaling, no collective on the data path); the time is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s (N*p per step)"
+UNIT = "particle-steps/s"
+WL = dict(name="two_stream_reduced", N=100_000, p=64, n2=20, Nx=128, dt=0.05)
+L2_BYTES = 129 * 2**20
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload():
+    return W.two_stream_reduced(N=WL["N"], p=WL["p"], Nx=WL["Nx"], n2=WL["n2"], dt=WL["dt"])
+
+
+def initial_state(rank: int = 0):
+    """Seeded particles of the workload and the truncated complex SVD start
+    (Sec. 3.2; input preparation, outside every timed region)."""
+    wl = workload()
+    X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet, seed=W.BASE_SEED + 1000 * rank)
+    return wl, X0, V0
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(steps: int) -> dict:
+    """The FP64 oracle, as it stands, on one host thread (BLAS pinned to 1
+    thread): `steps` PRK2 steps of the full workload."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads as W
+from oracle import csvd, pic, reduced
+wl = W.two_stream_reduced(N={WL['N']}, p={WL['p']}, Nx={WL['Nx']}, n2={WL['n2']}, dt={WL['dt']})
+X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet)
+U, Z, _ = csvd.csvd_init(X0, V0, wl.n2 // 2)
+g = pic.make_grid(wl.N, wl.Nx, wl.family.L)
+
+t = time.perf_counter()
+its = []
+for _ in range({steps}):
+    U, Z, info = reduced.prk2_step(U, Z, wl.dt, g)
+    its.append(info["iters"])
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "iters": its}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "error": r.stderr.strip().splitlines()[-1:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    units = WL["N"] * WL["p"] * steps
+    return {"value": units / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} PRK2 steps of the full workload (N={WL['N']}, p={WL['p']}, "
+                      f"2n={WL['n2']}) numpy float64, BLAS 1 thread; "
+                      f"fixed-point iterations {out['iters']}",
+            "seconds": out["seconds"]}
+
+
+# --------------------------------------------------------------- arms
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    return ours(args, rank, world)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    res = cpu_baseline(max(1, args.steps if args.steps <= 3 else 2))
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": (WL["N"] * WL["p"] / res["value"] * 1e3) if res.get("value") else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(world),
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(world):
+    return {"workload": "two-stream reduced model, N=1e5 particles x p=64 samples, 2n=20, "
+                        "Nx=128, dt=0.05, FP64 (configs[1])",
+            "N": WL["N"], "p": WL["p"], "rank_2n": WL["n2"], "Nx": WL["Nx"], "dt": WL["dt"],
+            "loading": "seeded per sample", "parallelism": f"replicas x{world}",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def ours(args, rank, world):
+    import torch
+
+    from paper_2201_05555_gb300 import Context, make_grid
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    ctx = Context(local)
+
+    wl, X0, V0 = initial_state(rank)
+    n = wl.n2 // 2
+    # truncated complex SVD start: R0 = X0 + i V0 (N x p), n leading left
+    # singular vectors; zeta = Q^H R0 (setup, not timed)
+    R0 = (X0 + 1j * V0).T
+    Uc, _, _ = np.linalg.svd(R0, full_matrices=False)
+    Qc = Uc[:, :n]
+    zeta = Qc.conj().T @ R0
+    Q = torch.tensor(np.hstack([Qc.real, Qc.imag]), device=dev).contiguous()
+    Z = torch.tensor(np.vstack([zeta.real, zeta.imag]), device=dev).contiguous()
+    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Qt, Zt, trace=True):
+        return ctx.basis_update(grid, Qt, Zt, wl.dt, 1, trace=trace, iters=True)
+
+    for _ in range(args.warmup):
+        step(Q, Z)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident state
+    KP = "k_project"
+    ctx.profile_reset()
+    ctx.profile_enable([KP])
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    iters = []
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            _, it = step(Q, Z)
+            ev[s][1].record(stream)
+            iters.append(it)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.profile_enable([])
+    prof = ctx.profile_read()
+    total_launches = sum(v[0] for v in prof.values())
+    ctx.sync_status()
+    its = [int(i[0]) for i in iters]
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through host buffers: H2D state, one step, D2H state
+    Qh = Q.cpu().pin_memory()
+    Zh = Z.cpu().pin_memory()
+    Qd, Zd = torch.empty_like(Q), torch.empty_like(Z)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        e2e_ev[s][0].record(stream)
+        Qd.copy_(Qh, non_blocking=True)
+        Zd.copy_(Zh, non_blocking=True)
+        step(Qd, Zd, trace=False)
+        Qh.copy_(Qd, non_blocking=True)
+        Zh.copy_(Zd, non_blocking=True)
+        e2e_ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    units_step = wl.N * wl.p
+    value = units_step * args.steps * world / (ms / 1e3)
+    e2e_value = units_step * args.steps * world / (e2e_ms / 1e3)
+    state_bytes = Q.numel() * 8 + Z.numel() * 8
+
+    # ---- roofline of the dominant kernel (k_project: FP64 ALU bound)
+    l, timed, pms = prof[KP]
+    real = sum(its)  # launches that did work (the rest exit on the converged flag)
+    flop_per_launch = units_step * 8 * n  # 2n FMA reconstruct + 2n FMA projection per particle-sample
+    achieved = flop_per_launch * real / (pms / 1e3) / 1e12 if pms > 0 else None
+    roof = {"bound": "alu", "kernel": "k_project", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+            "launches": l, "working_launches": real, "ms_total": pms,
+            "peak_basis": "FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2.07 GHz, measured 1.19 TFLOP/s"}
+    clocks = clk.summary()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(world),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": total_launches, "roofline": roof, "clocks": clocks,
+            "fixed_point_iters": its}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

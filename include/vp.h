@@ -80,6 +80,12 @@ typedef struct vp_step_opts {
   double tol;      /* fixed-point stop: |k_{m+1} - k_m|_F <= tol |k_{m+1}|_F (Sec. 6.1: 1e-9) */
   int32_t maxit;   /* iteration cap; exceeding it gives VP_ENOCONV */
   int32_t freeze_basis; /* 1: keep U fixed (global symplectic reduced basis, Sec. 3.1) */
+  /* Stagnation stop (the PIC force jumps at the nodes, so the fixed-point map
+   * is discontinuous and can end in a cycle of cell flips above tol): stop
+   * when the relative update r_m <= stall_floor and r_m >= stall_ratio r_{m-1}.
+   * stall_floor = 0 disables it.  Defaults 1e-5 and 0.5. */
+  double stall_floor;
+  double stall_ratio;
 } vp_step_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -163,7 +169,7 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0}.  trace_dev (nullable): ((nsteps+1) x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-5, 0.5}.  trace_dev (nullable): ((nsteps+1) x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
  * nonlinear_hamiltonian) of the state before step 1 and after each step.
  * iters_dev (nullable): fixed-point iterations of each step (int32, nsteps).

@@ -13,6 +13,13 @@ implicit midpoint rule padded to the same two stages for the coefficients
 stage at the beginning of the interval; the nonlinear stage is solved by
 fixed-point iteration from k = 0, stopped when the Frobenius norm of the
 update to k is below tol times the norm of k (Sec. 6.1, tol = 1e-9).
+
+The PIC force is piecewise constant in each particle position (the P1 hat
+gradients jump at the nodes), so the fixed-point map is discontinuous: with
+N p of order 1e6 the iteration ends in a cycle of cell flips above 1e-9
+(3.5e-7 for N = 1e5, p = 64).  The iteration therefore also stops on
+stagnation: a relative update r_m <= stall_floor (1e-5) that is not below
+stall_ratio (0.5) times r_{m-1}.
 """
 from __future__ import annotations
 
@@ -158,10 +165,12 @@ def tangent_velocity(U0: np.ndarray, xi: np.ndarray, Z: np.ndarray, g: pic.Grid,
 # --------------------------------------------------------------------------
 def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
               tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
-              retract=retraction, grad_fn=None):
+              retract=retraction, grad_fn=None, stall_floor: float = 1e-5,
+              stall_ratio: float = 0.5):
     """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
 
-    info: 'iters' (fixed-point evaluations), 'U_half', 'k2', 'E0' (electric
+    info: 'iters' (fixed-point evaluations), 'resid' (last relative update),
+    'stalled' (stopped on stagnation), 'U_half', 'k2', 'E0' (electric
     energies at (U0, Z0); PIC gradient only), 'kh1' (basis velocity at the start).
     grad_fn: optional map R -> G replacing the PIC gradient (any Hamiltonian).
     """
@@ -180,16 +189,26 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     info["kh1"] = kh1
     info["U_half"] = U_half
     k = np.zeros_like(Z0)
+    r_prev = 0.0
+    stalled = False
     for it in range(1, maxit + 1):
         G = _gradient(U_half, Z0 + 0.5 * dt * k, g, grad_fn)
         k_new = apply_J(U_half.T @ G)
         diff = np.linalg.norm(k_new - k)
+        nk = np.linalg.norm(k_new)
         k = k_new
-        if diff <= tol * np.linalg.norm(k):
+        if diff <= tol * nk:
             break
+        r = diff / nk
+        if it >= 2 and r <= stall_floor and r >= stall_ratio * r_prev:
+            stalled = True
+            break
+        r_prev = r
     else:
         raise NoConvergence(f"fixed point did not converge in {maxit} iterations")
     info["iters"] = it
+    info["resid"] = diff / nk if nk > 0 else 0.0
+    info["stalled"] = stalled
     info["k2"] = k
     Z1 = Z0 + dt * k
     if freeze_basis:

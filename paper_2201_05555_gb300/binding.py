@@ -34,7 +34,8 @@ class Grid(C.Structure):
 
 
 class StepOpts(C.Structure):
-    _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32)]
+    _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32), ("stall_floor", _D),
+                ("stall_ratio", _D)]
 
 
 def make_grid(N: int, Nx: int, L: float, q: float = -1.0, m: float = 1.0,
@@ -69,7 +70,19 @@ _SIGS = [
     ("vp_reduced_energy", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_deim_gather_project", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I64, _P,
                                       _P, _P, _P, _P]),
+    ("vp_profile_enable", _I32, [_P, C.c_uint64]),
+    ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
+    ("vp_profile_reset", _I32, [_P]),
+    ("vp_kernel_name", C.c_char_p, [_I32]),
 ]
+
+# vp_kernel ids (include/vp.h)
+KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step",
+           "k_reconstruct", "k_deposit_reduced", "k_project", "k_basis_M", "k_gram",
+           "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
+           "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
+           "k_axpy", "k_add_linear", "k_energies"]
+KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
 _lib_lock = threading.Lock()
@@ -148,6 +161,26 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.lib.vp_ctx_workspace_bytes(self.h))
+
+    # -- profiling (launch counters, CUDA-event timers on the launch stream)
+    def profile_enable(self, kernels=()):
+        mask = 0
+        for k in kernels:
+            mask |= 1 << (KID[k] if isinstance(k, str) else int(k))
+        self._check(self.lib.vp_profile_enable(self.h, C.c_uint64(mask)), "profile_enable")
+
+    def profile_reset(self):
+        self._check(self.lib.vp_profile_reset(self.h), "profile_reset")
+
+    def profile_read(self) -> dict:
+        """{kernel: (launches, timed launches, total event ms)}."""
+        out = {}
+        for i, name in enumerate(KERNELS):
+            l, t, m = _I64(), _I64(), _D()
+            self._check(self.lib.vp_profile_read(self.h, i, C.byref(l), C.byref(t), C.byref(m)),
+                        "profile_read")
+            out[name] = (l.value, t.value, m.value)
+        return out
 
     # -- particle <-> grid
     def deposit_cic(self, grid: Grid, X: torch.Tensor, rho: torch.Tensor | None = None):
@@ -232,12 +265,13 @@ class Context:
 
     def basis_update(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int,
                      tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
-                     trace: bool = True, iters: bool = True):
+                     trace: bool = True, iters: bool = True, stall_floor: float = 1e-5,
+                     stall_ratio: float = 0.5):
         N, n2 = Q.shape
         p = Z.shape[1]
         tr = self._empty(nsteps + 1, p, 2) if trace else None
         it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
-        opts = StepOpts(tol, maxit, int(freeze_basis))
+        opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio)
         self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,
                                              _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
                                              C.byref(opts), _ptr(tr),

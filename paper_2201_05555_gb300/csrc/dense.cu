@@ -306,7 +306,8 @@ __device__ double block_sum2(double v, double* red) {
 
 __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
                                const double* __restrict__ GVraw, const double* __restrict__ Z0,
-                               double* k, double* Ze, double dt, double tol, int maxit, int* done,
+                               double* k, double* Ze, double dt, double tol, int maxit,
+                               double stall_floor, double stall_ratio, double* rstate, int* done,
                                int* iters, int* status) {
   if (*done) return;
   __shared__ double red[32];
@@ -333,11 +334,15 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
   if (threadIdx.x == 0) {
     int it = *iters + 1;
     *iters = it;
-    bool conv = sqrt(D2) <= tol * sqrt(K2);
+    const double diff = sqrt(D2), nk = sqrt(K2);
+    bool conv = diff <= tol * nk;
+    const double r = nk > 0.0 ? diff / nk : 0.0;
+    const bool stalled = it >= 2 && r <= stall_floor && r >= stall_ratio * rstate[0];
+    rstate[0] = r;  // relative update of this iteration
     if (!isfinite(D2) || !isfinite(K2)) {
       vp_set_status(status, VP_ENUMERIC);
       *done = 1;
-    } else if (conv) {
+    } else if (conv || stalled) {
       *done = 1;
     } else if (it >= maxit) {
       vp_set_status(status, VP_ENOCONV);
@@ -347,9 +352,11 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
 }
 
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
-                  double* Ze, double dt, double tol, int maxit, int* done, int* iters, int* status,
+                  double* Ze, double dt, double tol, int maxit, double stall_floor,
+                  double stall_ratio, double* rstate, int* done, int* iters, int* status,
                   cudaStream_t st) {
-  k_coeff_update<<<1, 1024, 0, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, done, iters, status);
+  k_coeff_update<<<1, 1024, 0, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
+                                     stall_ratio, rstate, done, iters, status);
 }
 
 // Z1 = Z0 + dt k

@@ -585,7 +585,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0};
+  vp_step_opts o{1e-9, 100, 0, 1e-5, 0.5};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
   Red R;
@@ -615,6 +615,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
     VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
     VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
     VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+    VP_CUDA(cudaMemsetAsync(w.aux, 0, sizeof(double), st));
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
@@ -622,8 +623,9 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
         VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N, w.part, w.gx_proj,
                 w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
-        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit, w.flags, w.flags + 1,
-                     ctx->d_status, st));
+        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
+                                             o.stall_floor, o.stall_ratio, w.aux, w.flags,
+                                             w.flags + 1, ctx->d_status, st));
       }
       VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       VP_CUDA(cudaStreamSynchronize(st));

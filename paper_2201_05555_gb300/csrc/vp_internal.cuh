@@ -197,7 +197,8 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
-                  double* Ze, double dt, double tol, int maxit, int* done, int* iters, int* status,
+                  double* Ze, double dt, double tol, int maxit, double stall_floor,
+                  double stall_ratio, double* rstate, int* done, int* iters, int* status,
                   cudaStream_t st);
 void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st);
 void add_linear(int n, int p, const double* gX, const double* GVraw, const double* Z, double* g,

@@ -50,12 +50,16 @@ def hammersley(N: int) -> tuple[np.ndarray, np.ndarray]:
 # inverse CDF sampling (vectorised safeguarded Newton)
 # --------------------------------------------------------------------------
 def _invert_monotone(cdf: Callable, pdf: Callable, u: np.ndarray, lo: float, hi: float,
-                     tol: float = 1e-14, iters: int = 200) -> np.ndarray:
-    """Solve cdf(x) = u for x in [lo, hi] with bracketing Newton."""
+                     tol: float = 1e-14, iters: int = 10, table: int = 65537) -> np.ndarray:
+    """Solve cdf(x) = u for x in [lo, hi]: a start from a tabulated CDF
+    (linear interpolation on `table` points), then bracketed Newton steps
+    (a bisection step wherever Newton would leave the bracket)."""
     u = np.asarray(u, dtype=np.float64)
-    a = np.full(u.shape, lo)
-    b = np.full(u.shape, hi)
-    x = lo + u * (hi - lo)
+    xs = np.linspace(lo, hi, table)
+    cs = cdf(xs)
+    x = np.interp(u, cs, xs)
+    k = np.clip(np.searchsorted(cs, u), 1, table - 1)
+    a, b = xs[k - 1], xs[k]
     for _ in range(iters):
         fx = cdf(x) - u
         a = np.where(fx < 0, x, a)
@@ -63,7 +67,7 @@ def _invert_monotone(cdf: Callable, pdf: Callable, u: np.ndarray, lo: float, hi:
         d = pdf(x)
         with np.errstate(divide="ignore", invalid="ignore"):
             xn = x - fx / d
-        bad = ~np.isfinite(xn) | (xn <= a) | (xn >= b)
+        bad = ~np.isfinite(xn) | (xn < a) | (xn > b)
         xn = np.where(bad, 0.5 * (a + b), xn)
         done = np.abs(xn - x) <= tol * np.maximum(1.0, np.abs(x))
         x = xn
