@@ -198,6 +198,26 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
                                  const int32_t* idx_dev, const double* c_dev,
                                  const double* phi_dev, double* gX_dev, void* stream);
 
+/* -------------------------------------------------- deposit, no allocation */
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory (their pool or fixed memory plan owns it all,
+ * or the device-wide synchronisation of cudaFree is unacceptable).
+ * Same result as vp_deposit_cic (bit-identical counts), without a context:
+ * the fixed-point charge counts live in one device array that the library
+ * declares at file scope, 131072 int64 (1 MiB), held by every GPU that loads
+ * the library until the process exits.  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ * - Limit: p * Nx <= 131072; larger requests return VP_EUNSUPPORTED and
+ *   launch nothing.  Invalid arguments return VP_EINVAL.
+ * - Works on the caller's current device.  The first call on each device
+ *   looks up the array's device address (cudaGetSymbolAddress); make that
+ *   first call before any stream capture.
+ * - All calls on a device share the array.  Each call clears the part it uses
+ *   before depositing, but calls whose work overlaps on the GPU (two streams,
+ *   two host threads) race on it and give wrong results: serialise them. */
+vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int32_t p, const double* X_dev,
+                                 int64_t ldx, double* rho_dev, void* stream);
+
 /* ------------------------------------------------------------ profiling */
 /* Kernels of the library, for launch counts and event timing. */
 typedef enum vp_kernel {

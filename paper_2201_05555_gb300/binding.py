@@ -70,6 +70,7 @@ _SIGS = [
     ("vp_reduced_energy", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_deim_gather_project", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I64, _P,
                                       _P, _P, _P, _P]),
+    ("vp_deposit_cic_noalloc", _I32, [C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P]),
     ("vp_profile_enable", _I32, [_P, C.c_uint64]),
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
@@ -299,6 +300,21 @@ class Context:
                                                     _ptr(c, name="c"), _ptr(phi, name="phi"),
                                                     _ptr(g), self._stream()), "deim_gather_project")
         return g
+
+
+def deposit_cic_noalloc(grid: Grid, X: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
+    """vp_deposit_cic_noalloc: the deposit of vp_deposit_cic for callers that
+    may not allocate device memory (no context; rho must be given).  Runs on
+    X's device and the current torch stream of that device."""
+    lib = load_library()
+    p, N = X.shape
+    with torch.cuda.device(X.device):
+        st = C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream)
+        s = lib.vp_deposit_cic_noalloc(C.byref(grid), N, p, _ptr(X, name="X"), N,
+                                       _ptr(rho, name="rho"), st)
+    if s != 0:
+        raise VPError(s, "vp_deposit_cic_noalloc")
+    return rho
 
 
 _default: dict[int, Context] = {}
