@@ -86,6 +86,11 @@ typedef struct vp_step_opts {
    * stall_floor = 0 disables it.  Defaults 1e-5 and 0.5. */
   double stall_floor;
   double stall_ratio;
+  /* Arithmetic of the particle loops (deposit, projection, Gamma zeta^H):
+   * 0 = FP64; 1 = double-float (each FP64 operand as a sum of two floats,
+   * compensated dot products, about 48 significant bits; storage and every
+   * other step stay FP64).  Default 0. */
+  int32_t arith;
 } vp_step_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -169,15 +174,18 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0, 1e-5, 0.5}.  trace_dev (nullable): ((nsteps+1) x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-5, 0.5, 0}.  trace_dev (nullable): ((nsteps+1) x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
  * nonlinear_hamiltonian) of the state before step 1 and after each step.
  * iters_dev (nullable): fixed-point iterations of each step (int32, nsteps).
+ * kstate_dev (nullable, 2n x p, in/out): initial guess of the fixed point
+ * (the paper leaves it unstated); on return it holds the last step's k2, so
+ * passing it back warm-starts the next call.  NULL: start from k = 0 each step.
  * Synchronises `stream` once per step to steer the fixed point. */
 vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                           double* Q_dev, double* Z_dev, double dt, int32_t nsteps,
                           const vp_step_opts* opts, double* trace_dev, int32_t* iters_dev,
-                          void* stream);
+                          double* kstate_dev, void* stream);
 
 /* a11. FP64 diagnostics of a reduced state: electric energy E_i and
  * Hamiltonian H_i = 1/2 |U_V Z_i|^2 + E_i (p each, eq. nonlinear_hamiltonian),
@@ -224,7 +232,8 @@ typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
-  VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_COUNT
+  VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_DF,
+  VP_K_PROJECT_DF, VP_K_BASIS_M_DF, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

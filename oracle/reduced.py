@@ -166,13 +166,15 @@ def tangent_velocity(U0: np.ndarray, xi: np.ndarray, Z: np.ndarray, g: pic.Grid,
 def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
               tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
               retract=retraction, grad_fn=None, stall_floor: float = 1e-5,
-              stall_ratio: float = 0.5):
+              stall_ratio: float = 0.5, k_init: np.ndarray | None = None):
     """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
 
     info: 'iters' (fixed-point evaluations), 'resid' (last relative update),
     'stalled' (stopped on stagnation), 'U_half', 'k2', 'E0' (electric
     energies at (U0, Z0); PIC gradient only), 'kh1' (basis velocity at the start).
     grad_fn: optional map R -> G replacing the PIC gradient (any Hamiltonian).
+    k_init: initial guess of the fixed point (the paper leaves it unstated);
+    None starts from k = 0, a warm start passes the previous step's k2.
     """
     info = {}
     if grad_fn is None:
@@ -188,7 +190,7 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
         U_half = retract(U0, 0.5 * dt * kh1)
     info["kh1"] = kh1
     info["U_half"] = U_half
-    k = np.zeros_like(Z0)
+    k = np.zeros_like(Z0) if k_init is None else np.array(k_init, dtype=np.float64, copy=True)
     r_prev = 0.0
     stalled = False
     for it in range(1, maxit + 1):
@@ -224,12 +226,16 @@ def energies(U: np.ndarray, Z: np.ndarray, g: pic.Grid) -> tuple[np.ndarray, np.
     return pic.hamiltonian(Xr, Vr, g)
 
 
-def run(U: np.ndarray, Z: np.ndarray, dt: float, nsteps: int, g: pic.Grid, **kw):
-    """nsteps PRK2 steps; returns U, Z, the (E, H) trace (nsteps, p, 2), iterations."""
+def run(U: np.ndarray, Z: np.ndarray, dt: float, nsteps: int, g: pic.Grid,
+        warm_start: bool = False, **kw):
+    """nsteps PRK2 steps; returns U, Z, the (E, H) trace (nsteps, p, 2), iterations.
+    warm_start: each step's fixed point starts from the previous step's k2."""
     tr = np.zeros((nsteps, Z.shape[1], 2))
     its = []
+    k = None
     for t in range(nsteps):
-        U, Z, info = prk2_step(U, Z, dt, g, **kw)
+        U, Z, info = prk2_step(U, Z, dt, g, k_init=k if warm_start else None, **kw)
+        k = info["k2"]
         its.append(info["iters"])
         E, H = energies(U, Z, g)
         tr[t, :, 0] = E

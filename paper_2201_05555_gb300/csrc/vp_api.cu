@@ -103,10 +103,13 @@ struct RedWS {
   double2 *grams, *cay, *C, *tmp;
   int* flags;  // [0] done, [1] iters
   double* rows[5];
+  float2 *Q2a, *Q2b;  // double-float shadows of Q0 and Q_half
+  uint16_t* jcell;    // cell index per (particle, sample), N x p
   int gx_proj, gx_gram;
 };
 
-vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w) {
+vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w,
+                 bool df = false) {
   const int n2 = 2 * n, nn = n * n;
   const int sms = ctx->num_sms;
   w.gx_proj = tile_grid_x(N, project_chunks(p, Nx > 0 ? Nx : 3), sms);
@@ -119,7 +122,8 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
                  arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)n2 * n2, 8) +
                  arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) +
                  arena_bytes(4 * nn, 16) + arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) +
-                 arena_bytes(8, 4) + (size_t)nrows * arena_bytes((size_t)N * n2, 8);
+                 arena_bytes(8, 4) + (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
+                 (df ? 2 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) : 0);
   void* base = nullptr;
   VP_TRY(vp_workspace(ctx, bytes, &base));
   Arena a{(char*)base, 0, bytes};
@@ -140,6 +144,9 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.tmp = a.take<double2>(10 * nn);
   w.flags = a.take<int>(8);
   for (int r = 0; r < 5; ++r) w.rows[r] = r < nrows ? a.take<double>((size_t)N * n2) : nullptr;
+  w.Q2a = df ? a.take<float2>((size_t)N * n2) : nullptr;
+  w.Q2b = df ? a.take<float2>((size_t)N * n2) : nullptr;
+  w.jcell = df ? a.take<uint16_t>((size_t)N * p) : nullptr;
   return VP_OK;
 }
 
@@ -151,10 +158,16 @@ struct Red {
   int n, p;
   RedWS w;
   cudaStream_t st;
+  bool df = false;
 
-  // deposit X_r = Re(Q Z) and solve: F, Efield (counts zeroed again by the solve)
-  void field(const double* Q, const double* Z, const int* skip = nullptr) {
-    VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
+  // deposit X_r = Re(Q Z) and solve: F, Efield (counts zeroed again by the solve).
+  // With df, Q2 is the double-float shadow of Q and the cell indices are kept.
+  void field(const double* Q, const double* Z, const int* skip = nullptr,
+             const float2* Q2 = nullptr) {
+    if (df && Q2)
+      VP_K(VP_K_DEPOSIT_DF, deposit_df(g, N, n, p, Q2, Z, w.counts, w.jcell, skip, ctx->num_sms, st));
+    else
+      VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
     VP_K(VP_K_POISSON, poisson(g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip, ctx->d_status, st));
   }
   // Grams out_s = blk[pa]^H blk[pb] into `out` (npairs x n x n double2)
@@ -185,8 +198,11 @@ struct Red {
   }
   // X(Q, Z) * scale into out, using M as scratch (F must hold the field at (Q, Z))
   void basis_velocity_from_field(const double* Q, const double* Z, double scale, double* M,
-                                 double* out) {
-    VP_K(VP_K_BASIS_M, basis_M(g, N, n, p, Q, Z, w.F, M, ctx->num_sms, st));
+                                 double* out, const float2* Q2 = nullptr) {
+    if (df && Q2)
+      VP_K(VP_K_BASIS_M_DF, basis_M_df(g, N, n, p, Q2, Z, w.F, w.jcell, M, ctx->num_sms, st));
+    else
+      VP_K(VP_K_BASIS_M, basis_M(g, N, n, p, Q, Z, w.F, M, ctx->num_sms, st));
     grams({Q, M}, {{0, 1}}, w.grams);
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
     comb({M, Q}, w.C, out);
@@ -210,14 +226,15 @@ struct Red {
 };
 
 vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, int nrows,
-                    cudaStream_t st, Red& R) {
+                    cudaStream_t st, Red& R, bool df = false) {
   R.ctx = ctx;
+  R.df = df;
   R.N = N;
   R.n = n;
   R.p = p;
   R.st = st;
   if (grid) R.g = make_gridc(*grid, N);
-  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w));
+  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df));
   if (grid) VP_CUDA(cudaMemsetAsync(R.w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
   return VP_OK;
 }
@@ -228,7 +245,8 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step", "k_reconstruct",
     "k_deposit_reduced", "k_project", "k_basis_M", "k_gram", "k_gram_real", "k_reduce_partials",
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
-    "k_coeff_update", "k_axpy", "k_add_linear", "k_energies"};
+    "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df",
+    "k_project_df", "k_basis_M_df"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -355,6 +373,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   pic_init();
   reduced_init();
   dense_init();
+  df_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_pinned);
@@ -578,50 +597,68 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
 // rows[2] = Q_half, rows[3] = X(Q_half, Z_mid), rows[4] = xi_1 = dt Y.
 vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                           double* Q, double* Z, double dt, int32_t nsteps, const vp_step_opts* opts,
-                          double* trace, int32_t* iters, void* stream) {
+                          double* trace, int32_t* iters, double* kstate, void* stream) {
   VP_ENTER();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0, 1e-5, 0.5};
+  vp_step_opts o{1e-9, 100, 0, 1e-5, 0.5, 0};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
+  if (o.arith != 0 && o.arith != 1) return vp_fail(ctx, VP_EINVAL, "arith must be 0 or 1");
+  const bool df = o.arith == 1;
   Red R;
-  VP_TRY(red_setup(ctx, grid, N, n, p, 5, st, R));
+  VP_TRY(red_setup(ctx, grid, N, n, p, 5, st, R, df));
   RedWS& w = R.w;
   double *M = w.rows[0], *xih = w.rows[1], *Qh = w.rows[2], *Xp = w.rows[3], *xi1 = w.rows[4];
   const int64_t zsz = (int64_t)2 * n * p;
   const int64_t tstride = (int64_t)p * 2;
   int round = 4;
+  const int64_t qsz = N * 2 * n;
   for (int step = 0; step < nsteps; ++step) {
     // stage 1: field at (Q0, Z0); energies of the entering state
-    R.field(Q, Z);
+    if (df) VP_K(VP_K_SPLIT, split_df(qsz, Q, w.Q2a, st));
+    R.field(Q, Z, nullptr, w.Q2a);
     if (trace) {
       R.gv(Q, w.GVraw);
       VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride, trace + step * tstride + 1, 2,
                nullptr, nullptr, ctx->d_status, st));
     }
     const double* Qmid = Q;
+    const float2* Q2mid = w.Q2a;
     if (!o.freeze_basis) {
-      R.basis_velocity_from_field(Q, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
-      R.cayley(Q, xih, Qh);                                 // Q_half = R_Q0(xi_half)
+      R.basis_velocity_from_field(Q, Z, 0.5 * dt, M, xih, w.Q2a);  // xi_half = dt/2 X(Q0, Z0)
+      R.cayley(Q, xih, Qh);                                        // Q_half = R_Q0(xi_half)
       Qmid = Qh;
+      if (df) {
+        VP_K(VP_K_SPLIT, split_df(qsz, Qh, w.Q2b, st));
+        Q2mid = w.Q2b;
+      }
     }
     // stage 2: fixed point for k2 at Q_half
     R.gv(Qmid, w.GVraw);
     VP_CUDA(cudaMemcpyAsync(w.Z0, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-    VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-    VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
+    if (kstate) {  // warm start: k^0 = previous k2, Ze = Z0 + dt/2 k^0
+      VP_CUDA(cudaMemcpyAsync(w.k, kstate, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+      VP_K(VP_K_AXPY, axpy(zsz, 0.5 * dt, w.k, w.Z0, w.Ze, st));
+    } else {
+      VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+      VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
+    }
     VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
     VP_CUDA(cudaMemsetAsync(w.aux, 0, sizeof(double), st));
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
-        R.field(Qmid, w.Ze, w.flags);
-        VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N, w.part, w.gx_proj,
-                w.flags, ctx->d_status, st));
+        R.field(Qmid, w.Ze, w.flags, Q2mid);
+        if (df)
+          VP_K(VP_K_PROJECT_DF, project_df(R.g, N, n, p, Q2mid, w.F, w.jcell, w.part, w.gx_proj,
+                                           w.flags, st));
+        else
+          VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
+                                     w.part, w.gx_proj, w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
         VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
                                              o.stall_floor, o.stall_ratio, w.aux, w.flags,
@@ -647,10 +684,12 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
     }
     // Z_mid = w.Ze (= Z0 + dt/2 k2), Z1 = Z0 + dt k2
     VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
+    if (kstate)
+      VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
     if (!o.freeze_basis) {
       // stage 3: basis velocity at (Q_half, Z_mid), tangent velocity, retraction
-      R.field(Qh, w.Ze);
-      R.basis_velocity_from_field(Qh, w.Ze, 1.0, M, Xp);
+      R.field(Qh, w.Ze, nullptr, Q2mid);
+      R.basis_velocity_from_field(Qh, w.Ze, 1.0, M, Xp, Q2mid);
       R.tangent(Q, xih, Qh, Xp, dt, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
       R.cayley(Q, xi1, Q);                 // Q_1 = R_Q0(xi_1), in place
     }

@@ -209,4 +209,15 @@ void energies(int n, int p, const double* GVraw, const double* Z, const double* 
 void dense_init();
 void pic_init();
 
+// reduced_df.cu (double-float particle loops)
+void split_df(int64_t m, const double* x, float2* out, cudaStream_t st);
+void deposit_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* Z,
+                unsigned long long* counts, uint16_t* jout, const int* skip, int num_sms,
+                cudaStream_t st);
+void project_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* F,
+                const uint16_t* jin, double* part, int gridx, const int* skip, cudaStream_t st);
+void basis_M_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* Z,
+                const double* F, const uint16_t* jin, double* M, int num_sms, cudaStream_t st);
+void df_init();
+
 }  // namespace vpk

@@ -16,22 +16,27 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_full_size_prk2_step():
+@pytest.fixture(scope="module")
+def reference():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2201_05555_gb300 import Context, make_grid
-
     wl = W.two_stream_reduced()
     X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet)
-    n = wl.n2 // 2
-    U, Z, _ = csvd.csvd_init(X0, V0, n)
+    U, Z, _ = csvd.csvd_init(X0, V0, wl.n2 // 2)
     g = pic.make_grid(wl.N, wl.Nx, wl.family.L)
     U1, Z1, info = reduced.prk2_step(U, Z, wl.dt, g)
+    return wl, g, U, Z, U1, Z1, info
 
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_full_size_prk2_step(reference, arith):
+    from paper_2201_05555_gb300 import Context, make_grid
+
+    wl, g, U, Z, U1, Z1, info = reference
     ctx = Context(0)
     Qd = torch.tensor(q_storage(U), device="cuda:0")
     Zd = torch.tensor(Z, device="cuda:0")
-    tr, it = ctx.basis_update(make_grid(wl.N, wl.Nx, wl.family.L), Qd, Zd, wl.dt, 1)
+    tr, it = ctx.basis_update(make_grid(wl.N, wl.Nx, wl.family.L), Qd, Zd, wl.dt, 1, arith=arith)
     ctx.sync_status()
     assert int(it[0]) == info["iters"]
     Ug, Zg = U_of(Qd.cpu().numpy()), Zd.cpu().numpy()

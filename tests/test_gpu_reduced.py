@@ -103,12 +103,14 @@ def test_reduced_energy_parity(ctx, sh):
     assert float(r.cpu()) < 1e-12
 
 
+@pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("sh,steps", [(SHAPES[0], 3), (SHAPES[1], 5), (SHAPES[2], 2)])
-def test_prk2_step_parity(ctx, sh, steps):
+def test_prk2_step_parity(ctx, sh, steps, arith):
+    """arith 0: FP64 particle loops; 1: double-float particle loops."""
     g, grid, U, Z = state(**sh)
     dt = 0.05
     Qd, Zd = T(q_storage(U)), T(Z)
-    tr, it = ctx.basis_update(grid, Qd, Zd, dt, steps)
+    tr, it = ctx.basis_update(grid, Qd, Zd, dt, steps, arith=arith)
     ctx.sync_status()
     Uo, Zo = U, Z
     its = []
@@ -124,6 +126,24 @@ def test_prk2_step_parity(ctx, sh, steps):
     assert rel(Ug @ Zd.cpu().numpy(), Uo @ Zo) < TOL
     assert list(it.cpu().numpy()[:steps]) == its
     assert rel(tr.cpu().numpy(), np.stack(tro)) < TOL
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_warm_start_parity(ctx, arith):
+    """Fixed point started from the previous step's k2 on both sides, carried
+    across calls in a caller-owned buffer."""
+    g, grid, U, Z = state(N=5000, p=40, n=6, Nx=64)
+    dt = 0.05
+    Qd, Zd = T(q_storage(U)), T(Z)
+    kst = torch.zeros_like(Zd)
+    its = []
+    for _ in range(3):  # one step per call, state carried in kst
+        _, it = ctx.basis_update(grid, Qd, Zd, dt, 1, trace=False, arith=arith, kstate=kst)
+        its.append(int(it[0]))
+    Uo, Zo, tro, itso = reduced.run(U, Z, dt, 3, g, warm_start=True)
+    assert its == itso
+    assert rel(U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy(), Uo @ Zo) < TOL
+    assert rel(Zd.cpu().numpy(), Zo) < TOL
 
 
 def test_quiet_start_low_rank_parity(ctx):
