@@ -273,7 +273,7 @@ def ours(args, rank, world):
     Qh = Q.cpu().pin_memory()
     Zh = Z.cpu().pin_memory()
     Qd, Zd = torch.empty_like(Q), torch.empty_like(Z)
-    trh = torch.empty((2, wl.p, 2), dtype=torch.float64).pin_memory()
+    trh = torch.empty((1, wl.p, 2), dtype=torch.float64).pin_memory()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
     torch.cuda.synchronize()

@@ -174,9 +174,11 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0, 1e-5, 0.5, 0}.  trace_dev (nullable): ((nsteps+1) x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-5, 0.5, 0}.  trace_dev (nullable): (nsteps x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
- * nonlinear_hamiltonian) of the state before step 1 and after each step.
+ * nonlinear_hamiltonian) of the state entering each step, taken from the
+ * step's first field evaluation (no extra work); vp_reduced_energy gives the
+ * same diagnostics for the final state.
  * iters_dev (nullable): fixed-point iterations of each step (int32, nsteps).
  * kstate_dev (nullable, 2n x p, in/out): initial guess of the fixed point
  * (the paper leaves it unstated); on return it holds the last step's k2, so
@@ -233,7 +235,8 @@ typedef enum vp_kernel {
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_DF,
-  VP_K_PROJECT_DF, VP_K_BASIS_M_DF, VP_K_COUNT
+  VP_K_PROJECT_DF, VP_K_BASIS_M_DF, VP_K_PREP_DF, VP_K_GRAM_DF, VP_K_GRAM_REAL_DF, VP_K_AFFINE_DF,
+  VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

@@ -83,7 +83,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df", "k_project_df",
-           "k_basis_M_df"]
+           "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -275,7 +275,7 @@ class Context:
         warm start of the fixed point, updated with the last k2."""
         N, n2 = Q.shape
         p = Z.shape[1]
-        tr = self._empty(nsteps + 1, p, 2) if trace else None
+        tr = self._empty(max(nsteps, 1), p, 2) if trace else None
         it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
         opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio, int(arith))
         self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,

@@ -122,10 +122,10 @@ __device__ void zeta_gram(double2* H, const double* Z, int n, int p) {
 // Shared: aug n x 3n.  Output C (2 x n x n).
 __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ QhM,
                                      const double* __restrict__ Z, double scale, double2* C,
-                                     double2* tmp, int* status) {
+                                     double2* tmp, int* status, int in_smem) {
   extern __shared__ double2 aug[];
   const int ld = 3 * n;
-  double2* H = tmp;  // n x n (global scratch)
+  double2* H = in_smem ? aug + n * ld : tmp;  // n x n
   zeta_gram(H, Z, n, p);
   for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
     int r = e / ld, c = e - r * ld;
@@ -152,8 +152,8 @@ __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ Q
 
 void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
                         double2* C, double2* tmp, int* status, cudaStream_t st) {
-  size_t smem = sizeof(double2) * n * 3 * n;
-  k_small_basis_coeffs<<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status);
+  size_t smem = sizeof(double2) * n * 4 * n;
+  k_small_basis_coeffs<<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status, 1);
 }
 
 // ------------------------------------------------------- Cayley retraction
@@ -163,14 +163,29 @@ void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, doubl
 // K = D^H C = [[Q0^H W, -G0], [W^H W, -W^H Q0]],
 // Q0^H W = P - G0 P / 2,  W^H W = XX - P^H P + P^H G0 P / 4.
 // Output C (2 x n x n): coefficient of Q0, coefficient of xi.
-__global__ void k_small_cayley(int n, const double2* __restrict__ G0, const double2* __restrict__ P,
-                               const double2* __restrict__ XX, double2* C, double2* tmp,
-                               int* status) {
-  extern __shared__ double2 aug[];  // 2n x 3n
+__global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const double2* __restrict__ Pg,
+                               const double2* __restrict__ XXg, double2* C, double2* tmp,
+                               int* status, int in_smem) {
+  extern __shared__ double2 aug[];  // 2n x 3n, then (in_smem) G0, P, XX, T, QW, WW
   const int nn = n * n, ld = 3 * n;
-  double2* T = tmp;            // G0 P
-  double2* QW = tmp + nn;      // Q0^H W
-  double2* WW = tmp + 2 * nn;  // W^H W
+  double2* sb = aug + 6 * nn;
+  const double2* G0 = G0g;
+  const double2* P = Pg;
+  const double2* XX = XXg;
+  double2* T = in_smem ? sb + 3 * nn : tmp;            // G0 P
+  double2* QW = in_smem ? sb + 4 * nn : tmp + nn;      // Q0^H W
+  double2* WW = in_smem ? sb + 5 * nn : tmp + 2 * nn;  // W^H W
+  if (in_smem) {
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      sb[e] = G0g[e];
+      sb[nn + e] = Pg[e];
+      sb[2 * nn + e] = XXg[e];
+    }
+    __syncthreads();
+    G0 = sb;
+    P = sb + nn;
+    XX = sb + 2 * nn;
+  }
   const double2 one = make_double2(1.0, 0.0);
   cmm(T, G0, 0, P, 0, one, 0.0, n);
   cadd_mat(QW, 1.0, P, -0.5, T, 0, 0.0, n);
@@ -213,8 +228,10 @@ __global__ void k_small_cayley(int n, const double2* __restrict__ G0, const doub
 
 void small_cayley_coeffs(int n, const double2* G0, const double2* P, const double2* XX, double2* C,
                          double2* tmp, int* status, cudaStream_t st) {
-  size_t smem = sizeof(double2) * 2 * n * 3 * n;
-  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status);
+  size_t full = sizeof(double2) * 12 * n * n;
+  int in_smem = full <= 200 * 1024;
+  size_t smem = in_smem ? full : sizeof(double2) * 6 * n * n;
+  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem);
 }
 
 // ------------------------------------------------------- tangent velocity
@@ -228,16 +245,32 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 // where A1 = Q0^H Xp, A2 = xi^H Xp, A3 = Q0^H R, A4 = R^H Xp, A5 = R^H xi.
 // grams: [A1, A2, A3, A4, A5] (5 x n x n); output C = scale * [u1, u2, c]
 // (coefficients of Xp, xi, Q0).
-__global__ void k_small_tangent(int n, const double2* __restrict__ grams,
-                                const double2* __restrict__ G0, const double2* __restrict__ P,
-                                double scale, double2* C, double2* tmp, int* status) {
-  extern __shared__ double2 aug[];  // n x 2n
+__global__ void k_small_tangent(int n, const double2* __restrict__ grams_g,
+                                const double2* __restrict__ G0g, const double2* __restrict__ Pg,
+                                double scale, double2* C, double2* tmp, int* status, int in_smem) {
+  extern __shared__ double2 aug[];  // n x 2n, then (in_smem) 7 inputs and 8 temporaries
   const int nn = n * n, ld = 2 * n;
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+  double2* sb = aug + 2 * nn;
+  const double2* grams = grams_g;
+  const double2* G0 = G0g;
+  const double2* P = Pg;
+  double2* tb = in_smem ? sb + 7 * nn : tmp;
+  if (in_smem) {
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      for (int q = 0; q < 5; ++q) sb[q * nn + e] = grams_g[q * nn + e];
+      sb[5 * nn + e] = G0g[e];
+      sb[6 * nn + e] = Pg[e];
+    }
+    __syncthreads();
+    grams = sb;
+    G0 = sb + 5 * nn;
+    P = sb + 6 * nn;
+  }
   const double2 *A1 = grams, *A2 = grams + nn, *A3 = grams + 2 * nn, *A4 = grams + 3 * nn,
                 *A5 = grams + 4 * nn;
-  double2 *T1 = tmp, *u1 = tmp + nn, *u2 = tmp + 2 * nn, *u3 = tmp + 3 * nn, *W1 = tmp + 4 * nn,
-          *QU = tmp + 5 * nn, *RU = tmp + 6 * nn, *W2 = tmp + 7 * nn;
+  double2 *T1 = tb, *u1 = tb + nn, *u2 = tb + 2 * nn, *u3 = tb + 3 * nn, *W1 = tb + 4 * nn,
+          *QU = tb + 5 * nn, *RU = tb + 6 * nn, *W2 = tb + 7 * nn;
   for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
     int r = e / ld, c = e - r * ld;
     double2 v;
@@ -285,8 +318,10 @@ __global__ void k_small_tangent(int n, const double2* __restrict__ grams,
 
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st) {
-  size_t smem = sizeof(double2) * n * 2 * n;
-  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status);
+  size_t full = sizeof(double2) * 17 * n * n;
+  int in_smem = full <= 200 * 1024;
+  size_t smem = in_smem ? full : sizeof(double2) * 2 * n * n;
+  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem);
 }
 
 // ------------------------------------------------- fixed-point iteration
@@ -310,27 +345,34 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
                                double stall_floor, double stall_ratio, double* rstate, int* done,
                                int* iters, int* status) {
   if (*done) return;
+  extern __shared__ double cu_sm[];
   __shared__ double red[32];
   const int n2 = 2 * n;
   const int64_t tot = (int64_t)n2 * p;
+  double* GV = cu_sm;             // n2 x n2, G_V = U_V^T U_V
+  double* Zs = cu_sm + n2 * n2;   // n2 x p, current evaluation point
+  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+    int a = e / n2, b = e - a * n2;
+    GV[e] = GVraw[vperm(a, n) * n2 + vperm(b, n)];
+  }
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) Zs[e] = Ze[e];
+  __syncthreads();
   double d2 = 0.0, k2 = 0.0;
-  // k_new[r] = g[n + r] (r < n), k_new[n + r] = -g[r]; compute g rows on demand
+  // k_new[r] = g[n + r] (r < n), k_new[n + r] = -g[r], g = gX + G_V Ze
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     int r = (int)(e / p), i = (int)(e - (int64_t)r * p);
     int gr = r < n ? n + r : r - n;
     double sgn = r < n ? 1.0 : -1.0;
     double g = gX[(int64_t)gr * p + i];
-    const int pr = vperm(gr, n);
-    for (int c = 0; c < n2; ++c) g = fma(GVraw[pr * n2 + vperm(c, n)], Ze[(int64_t)c * p + i], g);
+    for (int c = 0; c < n2; ++c) g = fma(GV[gr * n2 + c], Zs[(int64_t)c * p + i], g);
     double kn = sgn * g;
     double dk = kn - k[e];
     d2 = fma(dk, dk, d2);
     k2 = fma(kn, kn, k2);
-    k[e] = kn;  // element e of k is read only by this thread
+    k[e] = kn;
+    Ze[e] = fma(0.5 * dt, kn, Z0[e]);
   }
-  __syncthreads();  // every read of Ze above precedes the update below
   double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red);
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) Ze[e] = fma(0.5 * dt, k[e], Z0[e]);
   if (threadIdx.x == 0) {
     int it = *iters + 1;
     *iters = it;
@@ -355,8 +397,9 @@ void coeff_update(int n, int p, const double* gX, const double* GVraw, const dou
                   double* Ze, double dt, double tol, int maxit, double stall_floor,
                   double stall_ratio, double* rstate, int* done, int* iters, int* status,
                   cudaStream_t st) {
-  k_coeff_update<<<1, 1024, 0, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
-                                     stall_ratio, rstate, done, iters, status);
+  size_t smem = sizeof(double) * (4 * n * n + 2 * (size_t)n * p);
+  k_coeff_update<<<1, 1024, smem, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
+                                        stall_ratio, rstate, done, iters, status);
 }
 
 // Z1 = Z0 + dt k
@@ -433,6 +476,7 @@ void dense_init() {
   cudaFuncSetAttribute(k_small_basis_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_small_cayley, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_small_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_coeff_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace vpk

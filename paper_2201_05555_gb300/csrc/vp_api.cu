@@ -105,6 +105,8 @@ struct RedWS {
   double* rows[5];
   float2 *Q2a, *Q2b;  // double-float shadows of Q0 and Q_half
   uint16_t* jcell;    // cell index per (particle, sample), N x p
+  float2* frows[5];   // double-float row blocks of the double-float step
+  float2 *Z2, *Zh2, *F2;
   int gx_proj, gx_gram;
 };
 
@@ -123,7 +125,8 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
                  arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) +
                  arena_bytes(4 * nn, 16) + arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) +
                  arena_bytes(8, 4) + (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
-                 (df ? 2 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) : 0);
+                 (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) +
+                           2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) : 0);
   void* base = nullptr;
   VP_TRY(vp_workspace(ctx, bytes, &base));
   Arena a{(char*)base, 0, bytes};
@@ -147,6 +150,10 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.Q2a = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.Q2b = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.jcell = df ? a.take<uint16_t>((size_t)N * p) : nullptr;
+  for (int r = 0; r < 5; ++r) w.frows[r] = df ? a.take<float2>((size_t)N * n2) : nullptr;
+  w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
+  w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
+  w.F2 = df ? a.take<float2>(pn) : nullptr;
   return VP_OK;
 }
 
@@ -164,10 +171,8 @@ struct Red {
   // With df, Q2 is the double-float shadow of Q and the cell indices are kept.
   void field(const double* Q, const double* Z, const int* skip = nullptr,
              const float2* Q2 = nullptr) {
-    if (df && Q2)
-      VP_K(VP_K_DEPOSIT_DF, deposit_df(g, N, n, p, Q2, Z, w.counts, w.jcell, skip, ctx->num_sms, st));
-    else
-      VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
+    (void)Q2;
+    VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
     VP_K(VP_K_POISSON, poisson(g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip, ctx->d_status, st));
   }
   // Grams out_s = blk[pa]^H blk[pb] into `out` (npairs x n x n double2)
@@ -199,10 +204,8 @@ struct Red {
   // X(Q, Z) * scale into out, using M as scratch (F must hold the field at (Q, Z))
   void basis_velocity_from_field(const double* Q, const double* Z, double scale, double* M,
                                  double* out, const float2* Q2 = nullptr) {
-    if (df && Q2)
-      VP_K(VP_K_BASIS_M_DF, basis_M_df(g, N, n, p, Q2, Z, w.F, w.jcell, M, ctx->num_sms, st));
-    else
-      VP_K(VP_K_BASIS_M, basis_M(g, N, n, p, Q, Z, w.F, M, ctx->num_sms, st));
+    (void)Q2;
+    VP_K(VP_K_BASIS_M, basis_M(g, N, n, p, Q, Z, w.F, M, ctx->num_sms, st));
     grams({Q, M}, {{0, 1}}, w.grams);
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
     comb({M, Q}, w.C, out);
@@ -240,13 +243,159 @@ vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, i
 }
 }  // namespace
 
+// ------------------------------------------- double-float partitioned RK2
+// The same stage structure as the FP64 path: every N-row intermediate (M,
+// xi_half, Q_half, X(Q_half, Z_mid), xi_1) is kept as double-float rows,
+// Gram matrices and the small dense algebra are FP64, and Q is written back
+// in FP64.
+namespace {
+struct RedDF {
+  Red& R;
+  vp_ctx* ctx;
+  cudaStream_t st;
+  int64_t N;
+  int n, p;
+  void field(const float2* Q2, const double* Z, const int* skip) {
+    RedWS& w = R.w;
+    VP_K(VP_K_PREP_DF, prep_df(R.g, n, p, Z, w.Z2, w.Zh2, nullptr, nullptr, skip, st));
+    VP_K(VP_K_DEPOSIT_DF, deposit_df(R.g, N, n, p, Q2, w.Zh2, w.counts, w.jcell, skip, ctx->num_sms, st));
+    VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip,
+                               ctx->d_status, st));
+    VP_K(VP_K_PREP_DF, prep_df(R.g, n, p, nullptr, nullptr, nullptr, w.F, w.F2, skip, st));
+  }
+  void grams(std::initializer_list<const float2*> blks,
+             std::initializer_list<std::pair<int, int>> pairs, double2* out) {
+    GramArgsDF a{};
+    for (const float2* b : blks) a.blk[a.nblk++] = b;
+    for (auto pr : pairs) {
+      a.pa[a.npairs] = pr.first;
+      a.pb[a.npairs] = pr.second;
+      ++a.npairs;
+    }
+    VP_K(VP_K_GRAM_DF, gram_df(N, n, a, reinterpret_cast<double2*>(R.w.part), R.w.gx_gram, st));
+    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)a.npairs * n * n * 2, R.w.part,
+                                      reinterpret_cast<double*>(out), nullptr, st));
+  }
+  void gv(const float2* Q2, double* GVraw) {
+    VP_K(VP_K_GRAM_REAL_DF, gram_real_df(N, 2 * n, Q2, R.w.part, R.w.gx_gram, st));
+    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
+  }
+  void comb(std::initializer_list<const float2*> xs, const double2* C, double* out_d, float2* out_f) {
+    AffineArgsDF a{};
+    for (const float2* x : xs) a.X[a.nterms++] = x;
+    VP_K(VP_K_AFFINE_DF, affine_df(N, n, a, C, out_d, out_f, ctx->num_sms, st));
+  }
+  // scale * X(Q, Z) into out (F2, jcell, Z2 must hold the field at (Q, Z))
+  void basis_velocity(const float2* Q2, const double* Z, double scale, float2* M, float2* out) {
+    RedWS& w = R.w;
+    VP_K(VP_K_BASIS_M_DF, basis_M_df(R.g, N, n, p, Q2, w.Z2, w.F2, w.jcell, M, ctx->num_sms, st));
+    grams({Q2, M}, {{0, 1}}, w.grams);
+    VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
+    comb({M, Q2}, w.C, nullptr, out);
+  }
+  // Cayley retraction of Q0 along xi; leaves G0, P, XX in w.cay
+  void cayley(const float2* Q0, const float2* xi, double* out_d, float2* out_f) {
+    RedWS& w = R.w;
+    grams({Q0, xi}, {{0, 0}, {0, 1}, {1, 1}}, w.cay);
+    const int nn = n * n;
+    VP_K(VP_K_SMALL_CAYLEY, small_cayley_coeffs(n, w.cay, w.cay + nn, w.cay + 2 * nn, w.C, w.tmp,
+                                                ctx->d_status, st));
+    comb({Q0, xi}, w.C, out_d, out_f);
+  }
+};
+}  // namespace
+
+static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, double dt,
+                                 int nsteps, const vp_step_opts& o, double* trace, int32_t* iters,
+                                 double* kstate, cudaStream_t st) {
+  RedWS& w = R.w;
+  const int64_t N = R.N;
+  const int n = R.n, p = R.p;
+  RedDF D{R, ctx, st, N, n, p};
+  float2 *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2], *Xp = w.frows[3],
+         *xi1 = w.frows[4];
+  const int64_t zsz = (int64_t)2 * n * p, qsz = N * 2 * n;
+  const int64_t tstride = (int64_t)p * 2;
+  int round = 4;
+  for (int step = 0; step < nsteps; ++step) {
+    VP_K(VP_K_SPLIT, split_df(qsz, Q, Q0, st));
+    D.field(Q0, Z, nullptr);
+    if (trace) {
+      D.gv(Q0, w.GVraw);
+      VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride,
+                                   trace + step * tstride + 1, 2, nullptr, nullptr, ctx->d_status, st));
+    }
+    const float2* Qm = Q0;
+    if (!o.freeze_basis) {
+      D.basis_velocity(Q0, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
+      D.cayley(Q0, xih, nullptr, Qh);             // Q_half = R_Q0(xi_half)
+      Qm = Qh;
+    }
+    D.gv(Qm, w.GVraw);
+    VP_CUDA(cudaMemcpyAsync(w.Z0, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    if (kstate) {
+      VP_CUDA(cudaMemcpyAsync(w.k, kstate, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+      VP_K(VP_K_AXPY, axpy(zsz, 0.5 * dt, w.k, w.Z0, w.Ze, st));
+    } else {
+      VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+      VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
+    }
+    VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+    VP_CUDA(cudaMemsetAsync(w.aux, 0, sizeof(double), st));
+    int done_h = 0, total = 0;
+    while (!done_h) {
+      for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
+        D.field(Qm, w.Ze, w.flags);
+        VP_K(VP_K_PROJECT_DF, project_df(R.g, N, n, p, Qm, w.F2, w.jcell, w.part, w.gx_proj,
+                                         w.flags, st));
+        VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
+        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol,
+                                             o.maxit, o.stall_floor, o.stall_ratio, w.aux, w.flags,
+                                             w.flags + 1, ctx->d_status, st));
+      }
+      VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      VP_CUDA(cudaStreamSynchronize(st));
+      if (!ctx->pending.empty()) vp_prof_collect(ctx);
+      done_h = ctx->h_pinned[1];
+      if (!done_h && total >= o.maxit) break;
+      round = 2;
+    }
+    const int its = ctx->h_pinned[2];
+    round = its > 2 ? its : 2;
+    if (iters) VP_CUDA(cudaMemcpyAsync(iters + step, w.flags + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    if (!done_h || its >= o.maxit) {
+      VP_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      VP_CUDA(cudaStreamSynchronize(st));
+      if (ctx->h_pinned[0] != 0 || !done_h)
+        return vp_fail(ctx, VP_ENOCONV, "fixed point did not converge in %d iterations (step %d)",
+                       o.maxit, step);
+    }
+    VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
+    if (kstate)
+      VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    if (!o.freeze_basis) {
+      D.field(Qh, w.Ze, nullptr);
+      D.basis_velocity(Qh, w.Ze, 1.0, M, Xp);  // X(Q_half, Z_mid)
+      D.grams({Q0, xih, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
+      const int nn = n * n;
+      VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
+                                                    ctx->d_status, st));
+      D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
+      D.cayley(Q0, xi1, Q, nullptr);             // Q_1 = R_Q0(xi_1) in FP64
+    }
+    VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+  }
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
 // ============================================================== profiling
 static const char* kKernelNames[VP_K_COUNT] = {
     "k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step", "k_reconstruct",
     "k_deposit_reduced", "k_project", "k_basis_M", "k_gram", "k_gram_real", "k_reduce_partials",
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df",
-    "k_project_df", "k_basis_M_df"};
+    "k_project_df", "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -608,9 +757,13 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
   if (o.arith != 0 && o.arith != 1) return vp_fail(ctx, VP_EINVAL, "arith must be 0 or 1");
+  if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p = %lld exceeds 25600 (shared memory of the "
+                   "fixed-point update)", (long long)(4 * n * n + 2 * n * p));
   const bool df = o.arith == 1;
   Red R;
-  VP_TRY(red_setup(ctx, grid, N, n, p, 5, st, R, df));
+  VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df));
+  if (df) return basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st);
   RedWS& w = R.w;
   double *M = w.rows[0], *xih = w.rows[1], *Qh = w.rows[2], *Xp = w.rows[3], *xi1 = w.rows[4];
   const int64_t zsz = (int64_t)2 * n * p;
@@ -619,23 +772,18 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   const int64_t qsz = N * 2 * n;
   for (int step = 0; step < nsteps; ++step) {
     // stage 1: field at (Q0, Z0); energies of the entering state
-    if (df) VP_K(VP_K_SPLIT, split_df(qsz, Q, w.Q2a, st));
-    R.field(Q, Z, nullptr, w.Q2a);
+    R.field(Q, Z);
     if (trace) {
       R.gv(Q, w.GVraw);
       VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride, trace + step * tstride + 1, 2,
                nullptr, nullptr, ctx->d_status, st));
     }
     const double* Qmid = Q;
-    const float2* Q2mid = w.Q2a;
     if (!o.freeze_basis) {
-      R.basis_velocity_from_field(Q, Z, 0.5 * dt, M, xih, w.Q2a);  // xi_half = dt/2 X(Q0, Z0)
+      R.basis_velocity_from_field(Q, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
       R.cayley(Q, xih, Qh);                                        // Q_half = R_Q0(xi_half)
       Qmid = Qh;
-      if (df) {
-        VP_K(VP_K_SPLIT, split_df(qsz, Qh, w.Q2b, st));
-        Q2mid = w.Q2b;
-      }
+
     }
     // stage 2: fixed point for k2 at Q_half
     R.gv(Qmid, w.GVraw);
@@ -652,13 +800,9 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
-        R.field(Qmid, w.Ze, w.flags, Q2mid);
-        if (df)
-          VP_K(VP_K_PROJECT_DF, project_df(R.g, N, n, p, Q2mid, w.F, w.jcell, w.part, w.gx_proj,
-                                           w.flags, st));
-        else
-          VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
-                                     w.part, w.gx_proj, w.flags, ctx->d_status, st));
+        R.field(Qmid, w.Ze, w.flags);
+        VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
+                                   w.part, w.gx_proj, w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
         VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
                                              o.stall_floor, o.stall_ratio, w.aux, w.flags,
@@ -688,18 +832,12 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
       VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
     if (!o.freeze_basis) {
       // stage 3: basis velocity at (Q_half, Z_mid), tangent velocity, retraction
-      R.field(Qh, w.Ze, nullptr, Q2mid);
-      R.basis_velocity_from_field(Qh, w.Ze, 1.0, M, Xp, Q2mid);
+      R.field(Qh, w.Ze);
+      R.basis_velocity_from_field(Qh, w.Ze, 1.0, M, Xp);
       R.tangent(Q, xih, Qh, Xp, dt, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
       R.cayley(Q, xi1, Q);                 // Q_1 = R_Q0(xi_1), in place
     }
     VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-  }
-  if (trace) {
-    R.field(Q, Z);
-    R.gv(Q, w.GVraw);
-    VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + nsteps * tstride, trace + nsteps * tstride + 1, 2,
-             nullptr, nullptr, ctx->d_status, st));
   }
   VP_LAUNCHED();
   return VP_OK;

@@ -152,6 +152,15 @@ struct AffineArgs {  // out = sum_t X[t] C_t
   const double* X[4];
   int nterms;
 };
+struct GramArgsDF {  // double-float rows
+  const float2* blk[4];
+  int pa[8], pb[8];
+  int nblk, npairs;
+};
+struct AffineArgsDF {
+  const float2* X[4];
+  int nterms;
+};
 
 // pic_kernels.cu
 void deposit_samples(const GridC& g, int64_t N, int p, const double* X, int64_t ldx,
@@ -211,13 +220,19 @@ void pic_init();
 
 // reduced_df.cu (double-float particle loops)
 void split_df(int64_t m, const double* x, float2* out, cudaStream_t st);
-void deposit_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* Z,
+void prep_df(const GridC& g, int n, int p, const double* Z, float2* Z2, float2* Zh2,
+             const double* F, float2* F2, const int* skip, cudaStream_t st);
+void deposit_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Zh2,
                 unsigned long long* counts, uint16_t* jout, const int* skip, int num_sms,
                 cudaStream_t st);
-void project_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* F,
+void project_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* F2,
                 const uint16_t* jin, double* part, int gridx, const int* skip, cudaStream_t st);
-void basis_M_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const double* Z,
-                const double* F, const uint16_t* jin, double* M, int num_sms, cudaStream_t st);
+void basis_M_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Z2,
+                const float2* F2, const uint16_t* jin, float2* M, int num_sms, cudaStream_t st);
+void gram_df(int64_t N, int n, const GramArgsDF& a, double2* part, int gridx, cudaStream_t st);
+void gram_real_df(int64_t N, int m, const float2* X, double* part, int gridx, cudaStream_t st);
+void affine_df(int64_t N, int n, const AffineArgsDF& a, const double2* C, double* out_d,
+               float2* out_f, int num_sms, cudaStream_t st);
 void df_init();
 
 }  // namespace vpk
