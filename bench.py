@@ -216,14 +216,9 @@ def ours(args, rank, world):
 
     wl, X0, V0 = initial_state(rank)
     n = wl.n2 // 2
-    # truncated complex SVD start: R0 = X0 + i V0 (N x p), n leading left
-    # singular vectors; zeta = Q^H R0 (setup, not timed)
-    R0 = (X0 + 1j * V0).T
-    Uc, _, _ = np.linalg.svd(R0, full_matrices=False)
-    Qc = Uc[:, :n]
-    zeta = Qc.conj().T @ R0
-    Q = torch.tensor(np.hstack([Qc.real, Qc.imag]), device=dev).contiguous()
-    Z = torch.tensor(np.vstack([zeta.real, zeta.imag]), device=dev).contiguous()
+    # truncated complex SVD start on the device (setup, not timed)
+    Q, Z, _ = ctx.init_csvd(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev), n)
+    ctx.sync_status()
     grid = make_grid(wl.N, wl.Nx, wl.family.L)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -189,6 +189,18 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
                           const vp_step_opts* opts, double* trace_dev, int32_t* iters_dev,
                           double* kstate_dev, void* stream);
 
+/* Start of the reduced model (Sec. 3.2, Algorithm 2): truncated complex SVD
+ * of R0 = X0 + i V0 (N x p), through the Gram matrix R0^H R0 = W S^2 W^H
+ * (cyclic Jacobi on the device): Q = R0 W_n S_n^-1 re-orthonormalised as
+ * Q (Q^H Q)^-1/2, zeta = Q^H R0.  X0_dev, V0_dev: p x N (ld N).  Outputs
+ * Q_dev (N x 2n), Z_dev (2n x p), sigma_dev (p singular values, descending;
+ * nullable).  The phase of each column of Q is free and not normalised.
+ * 1 <= n <= min(p, 40), p <= 256.  Singular values below 1e-14 sigma_1 in the
+ * first n give VP_ENUMERIC through the status word (S(Z) would be singular). */
+vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0_dev,
+                       const double* V0_dev, double* Q_dev, double* Z_dev, double* sigma_dev,
+                       void* stream);
+
 /* a11. FP64 diagnostics of a reduced state: electric energy E_i and
  * Hamiltonian H_i = 1/2 |U_V Z_i|^2 + E_i (p each, eq. nonlinear_hamiltonian),
  * and the manifold residual |Q^H Q - I|_F (= |U^T U - I|_F / sqrt 2; U^T J U = J
@@ -236,7 +248,7 @@ typedef enum vp_kernel {
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_DF,
   VP_K_PROJECT_DF, VP_K_BASIS_M_DF, VP_K_PREP_DF, VP_K_GRAM_DF, VP_K_GRAM_REAL_DF, VP_K_AFFINE_DF,
-  VP_K_COUNT
+  VP_K_INIT, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

@@ -71,6 +71,7 @@ _SIGS = [
     ("vp_deim_gather_project", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I64, _P,
                                       _P, _P, _P, _P]),
     ("vp_deposit_cic_noalloc", _I32, [C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P]),
+    ("vp_init_csvd", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_profile_enable", _I32, [_P, C.c_uint64]),
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
@@ -83,7 +84,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df", "k_project_df",
-           "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df"]
+           "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df", "k_init"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -285,6 +286,17 @@ class Context:
                                              self._stream()),
                     "basis_update")
         return tr, it
+
+    def init_csvd(self, X0: torch.Tensor, V0: torch.Tensor, n: int):
+        """(Q, Z, sigma): truncated complex SVD start from particles (p x N each)."""
+        p, N = X0.shape
+        Q = self._empty(N, 2 * n)
+        Z = self._empty(2 * n, p)
+        sig = self._empty(p)
+        self._check(self.lib.vp_init_csvd(self.h, N, p, n, _ptr(X0, name="X0"),
+                                          _ptr(V0, name="V0"), _ptr(Q), _ptr(Z), _ptr(sig),
+                                          self._stream()), "init_csvd")
+        return Q, Z, sig
 
     def reduced_energy(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor):
         N, n2 = Q.shape

@@ -430,6 +430,14 @@ void add_linear(int n, int p, const double* gX, const double* GVraw, const doubl
   k_add_linear<<<ceil_div(m, 256), 256, 0, st>>>(n, p, gX, GVraw, Z, g);
 }
 
+__global__ void k_sqrt_nonneg(int m, const double* x, double* out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) out[e] = sqrt(fmax(x[e], 0.0));
+}
+void sqrt_nonneg(int m, const double* x, double* out, cudaStream_t st) {
+  k_sqrt_nonneg<<<ceil_div(m, 256), 256, 0, st>>>(m, x, out);
+}
+
 // --------------------------------------------------------------- energies
 // E_out[i] = Efield[i], H_out[i] = 1/2 Z_i^T G_V Z_i + Efield[i];
 // resid = |Q^H Q - I|_F from the complex Gram QhQ (nullable).

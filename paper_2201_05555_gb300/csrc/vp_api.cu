@@ -395,7 +395,8 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_deposit_reduced", "k_project", "k_basis_M", "k_gram", "k_gram_real", "k_reduce_partials",
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df",
-    "k_project_df", "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df"};
+    "k_project_df", "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df",
+    "k_init"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -737,6 +738,83 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
   VP_K(VP_K_PROJECT, project(R.g, d, n, p, Q, Z, R.w.F, nullptr, 0, idx, c, N, R.w.part, R.w.gx_proj, nullptr,
           ctx->d_status, st));
   VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_proj, (int64_t)2 * n * p, R.w.part, gX, nullptr, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0,
+                       const double* V0, double* Q, double* Z, double* sigma, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  if (p > 256) return vp_fail(ctx, VP_EUNSUPPORTED, "p = %d > 256", p);
+  if (n < 1 || n > 40 || n > p || n > N)
+    return vp_fail(ctx, VP_EINVAL, "n = %d outside [1, min(p, N, 40)]", n);
+  if (!X0 || !V0 || !Q || !Z) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  const int64_t pp = (int64_t)p * p;
+  int gx = ceil_div(N, 32);
+  int gmax = (int)std::max<int64_t>(1, (64ll << 20) / (pp * 16));  // partials <= 64 MiB
+  gx = std::min(gx, std::min(2 * ctx->num_sms, gmax));
+  const int nn = n * n;
+  size_t bytes = arena_bytes((size_t)gx * pp, 16) + 4 * arena_bytes(pp, 16) + arena_bytes(p, 8) +
+                 arena_bytes((size_t)p * n, 16) + 2 * arena_bytes(nn, 16) + arena_bytes(n, 8) +
+                 arena_bytes((size_t)gx * n * p, 16) + arena_bytes((size_t)n * p, 16) +
+                 arena_bytes((size_t)N * 2 * n, 8) + arena_bytes(4 * nn, 16) +
+                 arena_bytes((size_t)2 * ctx->num_sms * 4 * nn, 16);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, bytes, &base));
+  Arena a{(char*)base, 0, bytes};
+  double2* part = a.take<double2>((size_t)gx * pp);
+  double2* A = a.take<double2>(pp);
+  double2* Wj = a.take<double2>(pp);
+  double2* Ws = a.take<double2>(pp);
+  double* lam = a.take<double>(p);
+  double2* Cn = a.take<double2>((size_t)p * n);
+  double2* G = a.take<double2>(nn);
+  double2* Gs = a.take<double2>(nn);
+  double* lamG = a.take<double>(n);
+  double2* zpart = a.take<double2>((size_t)gx * n * p);
+  double2* zeta = a.take<double2>((size_t)n * p);
+  double* Q0 = a.take<double>((size_t)N * 2 * n);
+  double2* WG = a.take<double2>(4 * nn);
+  double2* gpart = a.take<double2>((size_t)2 * ctx->num_sms * 4 * nn);
+  (void)gpart;
+  // 1. A = R0^H R0
+  VP_K(VP_K_INIT, init_launch_rgram(N, p, X0, V0, part, gx, st));
+  VP_K(VP_K_REDUCE, reduce_partials(gx, pp * 2, reinterpret_cast<double*>(part),
+                                    reinterpret_cast<double*>(A), nullptr, st));
+  // 2. A = W diag(lambda) W^H, lambda descending
+  VP_K(VP_K_INIT, init_launch_jacobi(p, A, Wj, lam, Ws, ctx->d_status, st));
+  // 3. Q0 = R0 W_n diag(lambda_n)^-1/2
+  VP_K(VP_K_INIT, init_launch_coeff(p, n, Ws, lam, Cn, ctx->d_status, st));
+  VP_K(VP_K_INIT, init_launch_r_times(N, p, n, X0, V0, Cn, Q0, ctx->num_sms, st));
+  // 4. Q = Q0 (Q0^H Q0)^-1/2
+  {
+    GramArgs ga{};
+    ga.blk[0] = Q0;
+    ga.nblk = 1;
+    ga.pa[0] = 0;
+    ga.pb[0] = 0;
+    ga.npairs = 1;
+    int ggx = gram_grid_x(N, ctx->num_sms);
+    VP_K(VP_K_GRAM, gram(N, n, ga, gpart, ggx, st));
+    VP_K(VP_K_REDUCE, reduce_partials(ggx, (int64_t)nn * 2, reinterpret_cast<double*>(gpart),
+                                      reinterpret_cast<double*>(G), nullptr, st));
+    VP_K(VP_K_INIT, init_launch_jacobi(n, G, WG, lamG, WG + nn, ctx->d_status, st));
+    VP_K(VP_K_INIT, init_launch_inv_sqrt(n, WG + nn, lamG, Gs, ctx->d_status, st));
+    AffineArgs aa{};
+    aa.X[0] = Q0;
+    aa.nterms = 1;
+    VP_K(VP_K_AFFINE, affine(N, n, aa, Gs, Q, ctx->num_sms, st));
+  }
+  // 5. zeta = Q^H R0
+  VP_K(VP_K_INIT, init_launch_zeta(N, p, n, Q, X0, V0, zpart, gx, st));
+  VP_K(VP_K_REDUCE, reduce_partials(gx, (int64_t)n * p * 2, reinterpret_cast<double*>(zpart),
+                                    reinterpret_cast<double*>(zeta), nullptr, st));
+  VP_K(VP_K_INIT, init_launch_zeta_to_Z(n, p, zeta, Z, st));
+  if (sigma) {
+    // sigma = sqrt(max(lambda, 0)), computed on the device
+    VP_K(VP_K_INIT, sqrt_nonneg(p, lam, sigma, st));
+  }
   VP_LAUNCHED();
   return VP_OK;
 }

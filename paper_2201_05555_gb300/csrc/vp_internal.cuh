@@ -210,6 +210,7 @@ void coeff_update(int n, int p, const double* gX, const double* GVraw, const dou
                   double stall_ratio, double* rstate, int* done, int* iters, int* status,
                   cudaStream_t st);
 void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st);
+void sqrt_nonneg(int m, const double* x, double* out, cudaStream_t st);
 void add_linear(int n, int p, const double* gX, const double* GVraw, const double* Z, double* g,
                 cudaStream_t st);
 void energies(int n, int p, const double* GVraw, const double* Z, const double* Efield,
@@ -234,5 +235,20 @@ void gram_real_df(int64_t N, int m, const float2* X, double* part, int gridx, cu
 void affine_df(int64_t N, int n, const AffineArgsDF& a, const double2* C, double* out_d,
                float2* out_f, int num_sms, cudaStream_t st);
 void df_init();
+
+// init.cu (complex SVD start)
+void init_launch_rgram(int64_t N, int p, const double* X, const double* V, double2* part, int gx,
+                       cudaStream_t st);
+void init_launch_jacobi(int m, double2* A, double2* W, double* lambda, double2* Wout, int* status,
+                        cudaStream_t st);
+void init_launch_coeff(int p, int n, const double2* W, const double* lambda, double2* C, int* status,
+                       cudaStream_t st);
+void init_launch_r_times(int64_t N, int p, int n, const double* X, const double* V, const double2* C,
+                         double* Q, int num_sms, cudaStream_t st);
+void init_launch_inv_sqrt(int n, const double2* W, const double* lambda, double2* out, int* status,
+                          cudaStream_t st);
+void init_launch_zeta(int64_t N, int p, int n, const double* Q, const double* X, const double* V,
+                      double2* part, int gx, cudaStream_t st);
+void init_launch_zeta_to_Z(int n, int p, const double2* zeta, double* Z, cudaStream_t st);
 
 }  // namespace vpk
