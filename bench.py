@@ -196,7 +196,7 @@ def config_dict(world):
             "loading": "seeded per sample", "parallelism": f"replicas x{world}",
             "arithmetic": ("FP64 storage; particle loops in double-float (Dot2), small dense "
                            "and reductions FP64" if ARITH == 1 else "FP64"),
-            "fixed_point": "tol 1e-9 or stagnation (r<=1e-5, ratio>=0.5), warm start from k2",
+            "fixed_point": "tol 1e-9 or stagnation (r<=1e-3, no halving over 2 iterations), warm start from k2",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -234,7 +234,7 @@ def ours(args, rank, world):
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident state
-    KP = "k_project_df" if ARITH == 1 else "k_project"
+    KP = "k_project_lp" if ARITH else "k_project"
     ctx.profile_reset()
     ctx.profile_enable([KP])
     if dist:

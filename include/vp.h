@@ -81,16 +81,26 @@ typedef struct vp_step_opts {
   int32_t maxit;   /* iteration cap; exceeding it gives VP_ENOCONV */
   int32_t freeze_basis; /* 1: keep U fixed (global symplectic reduced basis, Sec. 3.1) */
   /* Stagnation stop (the PIC force jumps at the nodes, so the fixed-point map
-   * is discontinuous and can end in a cycle of cell flips above tol): stop
-   * when the relative update r_m <= stall_floor and r_m >= stall_ratio r_{m-1}.
-   * stall_floor = 0 disables it.  Defaults 1e-5 and 0.5. */
+   * is discontinuous and can end in a cycle of cell flips above tol): stop at
+   * iteration m >= 3 when the relative update r_m <= stall_floor and
+   * r_m >= stall_ratio min(r_{m-1}, r_{m-2}).  stall_floor = 0 disables it.
+   * Defaults 1e-3 and 0.5. */
   double stall_floor;
   double stall_ratio;
-  /* Arithmetic of the particle loops (deposit, projection, Gamma zeta^H):
-   * 0 = FP64; 1 = double-float (each FP64 operand as a sum of two floats,
-   * compensated dot products, about 48 significant bits; storage and every
-   * other step stay FP64).  Default 0. */
+  /* Arithmetic of the N-row work (deposit, projection, Gamma zeta^H, Gram
+   * matrices, affine row updates):
+   * 0 = FP64;
+   * 1 = double-float (each FP64 operand as a sum of two floats, compensated
+   *     dot products, about 48 significant bits);
+   * 2 = FP32 (the precision form: FP32 row storage and accumulation).
+   * Q and Z stay FP64 in memory; reductions across blocks, the small dense
+   * algebra and the energies are FP64 in every mode.  Default 0. */
   int32_t arith;
+  /* 1: after every step re-orthonormalise Q <- Q (Q^H Q)^-1/2 (the block
+   * form keeps U symplectic): Gram and update in double-float, the n x n
+   * eigen-decomposition in FP64.  Not in the paper; a safeguard against the
+   * drift of U^T U = I in the precision form.  Default 0. */
+  int32_t reortho;
 } vp_step_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -174,11 +184,12 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0, 1e-5, 0.5, 0}.  trace_dev (nullable): (nsteps x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-3, 0.5, 0, 0}.  trace_dev (nullable): (nsteps x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
  * nonlinear_hamiltonian) of the state entering each step, taken from the
- * step's first field evaluation (no extra work); vp_reduced_energy gives the
- * same diagnostics for the final state.
+ * step's first field evaluation (no extra work; with arith = 2 from an extra
+ * double-float evaluation, so the diagnostic keeps FP64 accuracy);
+ * vp_reduced_energy gives the same diagnostics for the final state.
  * iters_dev (nullable): fixed-point iterations of each step (int32, nsteps).
  * kstate_dev (nullable, 2n x p, in/out): initial guess of the fixed point
  * (the paper leaves it unstated); on return it holds the last step's k2, so
@@ -246,8 +257,8 @@ typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
-  VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_DF,
-  VP_K_PROJECT_DF, VP_K_BASIS_M_DF, VP_K_PREP_DF, VP_K_GRAM_DF, VP_K_GRAM_REAL_DF, VP_K_AFFINE_DF,
+  VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
+  VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_COUNT
 } vp_kernel;
 

@@ -35,7 +35,7 @@ class Grid(C.Structure):
 
 class StepOpts(C.Structure):
     _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32), ("stall_floor", _D),
-                ("stall_ratio", _D), ("arith", _I32)]
+                ("stall_ratio", _D), ("arith", _I32), ("reortho", _I32)]
 
 
 def make_grid(N: int, Nx: int, L: float, q: float = -1.0, m: float = 1.0,
@@ -83,8 +83,8 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_reconstruct", "k_deposit_reduced", "k_project", "k_basis_M", "k_gram",
            "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
-           "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df", "k_project_df",
-           "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df", "k_init"]
+           "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
+           "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -268,17 +268,18 @@ class Context:
 
     def basis_update(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int,
                      tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
-                     trace: bool = True, iters: bool = True, stall_floor: float = 1e-5,
+                     trace: bool = True, iters: bool = True, stall_floor: float = 1e-3,
                      stall_ratio: float = 0.5, arith: int = 0,
-                     kstate: torch.Tensor | None = None):
+                     kstate: torch.Tensor | None = None, reortho: bool = False):
         """nsteps partitioned RK2 steps in place on Q (N x 2n) and Z (2n x p).
-        arith: 0 FP64, 1 double-float particle loops.  kstate (2n x p, in/out):
+        arith: 0 FP64, 1 double-float, 2 FP32 (precision form) for the N-row work.  kstate (2n x p, in/out):
         warm start of the fixed point, updated with the last k2."""
         N, n2 = Q.shape
         p = Z.shape[1]
         tr = self._empty(max(nsteps, 1), p, 2) if trace else None
         it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
-        opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio, int(arith))
+        opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio, int(arith),
+                        int(reortho))
         self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,
                                              _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
                                              C.byref(opts), _ptr(tr),

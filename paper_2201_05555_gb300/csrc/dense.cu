@@ -379,8 +379,11 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
     const double diff = sqrt(D2), nk = sqrt(K2);
     bool conv = diff <= tol * nk;
     const double r = nk > 0.0 ? diff / nk : 0.0;
-    const bool stalled = it >= 2 && r <= stall_floor && r >= stall_ratio * rstate[0];
-    rstate[0] = r;  // relative update of this iteration
+    // rstate: relative updates of the two previous iterations
+    const bool stalled =
+        it >= 3 && r <= stall_floor && r >= stall_ratio * fmin(rstate[0], rstate[1]);
+    rstate[1] = rstate[0];
+    rstate[0] = r;
     if (!isfinite(D2) || !isfinite(K2)) {
       vp_set_status(status, VP_ENUMERIC);
       *done = 1;

@@ -1,23 +1,25 @@
-// Particle-loop kernels of the reduced model in double-float arithmetic.
+// Particle-loop, Gram and affine kernels of the reduced model in FP32-based
+// arithmetic, for two arithmetic policies:
 //
-// GB300 executes FP32 at 58x its FP64 rate (measured 68.8 vs 1.19 TFLOP/s),
-// so the three particle loops (deposit of X_r = Re(Q zeta), projection
-// U_X^T G, and Gamma zeta^H) represent every FP64 operand as an unevaluated
-// sum hi + lo of two floats (|lo| <= ulp(hi)/2, about 48 significant bits)
-// and form each dot product with the compensated algorithm "Dot2" of Ogita,
-// Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): an error-free product
-// (FMA) and an error-free sum (TwoSum) per term, with the rounding errors
-// accumulated separately, which gives the result as if computed in twice
-// the working precision.  Storage stays FP64; results are FP64.  The cell
-// index of every (particle, sample) is written by the deposit and reused by
-// the projection and the basis kernel at the same (Q, zeta).
+// ArithDF  double-float: every FP64 operand is an unevaluated sum hi + lo of
+//          two floats (|lo| <= ulp(hi)/2, about 48 significant bits) and every
+//          dot product uses the compensated algorithm "Dot2" of Ogita, Rump
+//          and Oishi (SIAM J. Sci. Comput. 26, 2005): an error-free product
+//          (FMA) and an error-free sum (TwoSum) per term, the rounding errors
+//          accumulated separately, as if computed in twice the precision.
+//          GB300 executes FP32 at 58x its FP64 rate (measured 68.8 vs 1.19
+//          TFLOP/s), so this meets the FP64 tolerance several times faster.
+// ArithF32 plain FP32 storage of the N-row quantities and FP32 accumulation
+//          (the precision form); per-block partial sums, reductions, the small
+//          dense algebra and the energies stay FP64.
+//
+// Storage of Q and zeta stays FP64 in both; Q is split once per change into
+// the policy's row format.  The cell index of every (particle, sample) is
+// written by the deposit and reused by the projection and the basis kernel
+// at the same (Q, zeta).
 #include "vp_internal.cuh"
 
 namespace vpk {
-
-struct DF {
-  float hi, lo;
-};
 
 __device__ __forceinline__ float2 df_split(double d) {
   float h = __double2float_rn(d);
@@ -25,38 +27,50 @@ __device__ __forceinline__ float2 df_split(double d) {
   return make_float2(h, l);
 }
 
-// Running compensated sum: value = s + c.
-struct Acc {
-  float s, c;
-  __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
-  // += a * b with a, b double-float
-  __device__ __forceinline__ void fma2(float2 a, float2 b) {
-    float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, e);
-    e = fmaf(a.y, b.x, e);
-    float t = s + p;
-    float bp = t - s;
-    float es = (s - (t - bp)) + (p - bp);
-    s = t;
-    c += es + e;
-  }
-  // += a * b with a double-float, b a plain float
-  __device__ __forceinline__ void fma1(float2 a, float b) {
-    float p = a.x * b;
-    float e = fmaf(a.x, b, -p);
-    e = fmaf(a.y, b, e);
-    float t = s + p;
-    float bp = t - s;
-    float es = (s - (t - bp)) + (p - bp);
-    s = t;
-    c += es + e;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-  __device__ __forceinline__ float2 df() const {
-    float h = s + c;
-    return make_float2(h, c - (h - s));
-  }
+struct ArithDF {
+  using V = float2;
+  static __device__ __forceinline__ V from(double d) { return df_split(d); }
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
+  static __device__ __forceinline__ float hi(V a) { return a.x; }
+  static __device__ __forceinline__ float lo(V a) { return a.y; }
+  // running compensated sum s + c
+  struct A {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void fma2(V a, V b) {
+      float p = a.x * b.x;
+      float e = fmaf(a.x, b.x, -p);
+      e = fmaf(a.x, b.y, e);
+      e = fmaf(a.y, b.x, e);
+      float t = s + p;
+      float bp = t - s;
+      float es = (s - (t - bp)) + (p - bp);
+      s = t;
+      c += es + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    __device__ __forceinline__ V out() const {
+      float h = s + c;
+      return make_float2(h, c - (h - s));
+    }
+  };
+};
+
+struct ArithF32 {
+  using V = float;
+  static __device__ __forceinline__ V from(double d) { return __double2float_rn(d); }
+  static __device__ __forceinline__ V zero() { return 0.f; }
+  static __device__ __forceinline__ V neg(V a) { return -a; }
+  static __device__ __forceinline__ float hi(V a) { return a; }
+  static __device__ __forceinline__ float lo(V) { return 0.f; }
+  struct A {
+    float s;
+    __device__ __forceinline__ void zero() { s = 0.f; }
+    __device__ __forceinline__ void fma2(V a, V b) { s = fmaf(a, b, s); }
+    __device__ __forceinline__ double value() const { return (double)s; }
+    __device__ __forceinline__ V out() const { return s; }
+  };
 };
 
 // Cell index and fixed-point fraction of t = th + tl (cell units,
@@ -88,78 +102,72 @@ __device__ __forceinline__ void cell_fixed(float th, float tl, int Nx, float inv
   w1 = q;
 }
 
-// Split Q (N x 2n doubles) into its double-float shadow (N x 2n float2).
-__global__ void k_split(int64_t m, const double* __restrict__ x, float2* __restrict__ out) {
+static inline int chunk_w(int p, int Nx) {
+  int pc = 1;
+  while (pc < p && pc < 32) pc <<= 1;
+  while (pc > 1 && (size_t)pc * Nx * 8 > 96 * 1024) pc >>= 1;
+  return pc;
+}
+
+// ------------------------------------------------------------- conversions
+template <class AR>
+__global__ void k_split(int64_t m, const double* __restrict__ x, typename AR::V* __restrict__ out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < m) out[e] = df_split(x[e]);
+  if (e < m) out[e] = AR::from(x[e]);
 }
 
-void split_df(int64_t m, const double* x, float2* out, cudaStream_t st) {
-  k_split<<<ceil_div(m, 256), 256, 0, st>>>(m, x, out);
+// once per field evaluation: Z2 = Z, Zh2 = Z / h (2n x p), F2 = q/m F (p x Nx)
+template <class AR>
+__global__ void k_prep(GridC g, int64_t nz, const double* __restrict__ Z, typename AR::V* Z2,
+                       typename AR::V* Zh2, int64_t nf, const double* __restrict__ F,
+                       typename AR::V* F2, const int* skip) {
+  if (skip && *skip) return;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nz) {
+    double z = Z[e];
+    if (Z2) Z2[e] = AR::from(z);
+    if (Zh2) Zh2[e] = AR::from(z * g.inv_h);
+  } else if (F && e - nz < nf) {
+    F2[e - nz] = AR::from(g.qm * F[e - nz]);
+  }
 }
 
-__device__ __forceinline__ void load_q2(float2* Qs, int ldq, const float2* __restrict__ Q2, int n2,
-                                        int64_t base, int rows) {
+template <class V>
+__device__ __forceinline__ void load_rows(V* Qs, int ldq, const V* __restrict__ Q2, int n2,
+                                          int64_t base, int rows) {
   for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
     int r = e / n2, k = e - r * n2;
     Qs[r * ldq + k] = Q2[(base + r) * n2 + k];
   }
 }
 
-// z chunk as double-float, optionally scaled (1/h for positions in cells)
-__device__ __forceinline__ void load_z2(float2* Zs, int ldz, const double* __restrict__ Z, int n2,
-                                        int p, int c0, int PC, double scale) {
+template <class AR>
+__device__ __forceinline__ void load_zc(typename AR::V* Zs, int ldz,
+                                        const typename AR::V* __restrict__ Z2, int n2, int p,
+                                        int c0, int PC) {
   for (int e = threadIdx.x; e < n2 * PC; e += blockDim.x) {
     int k = e / PC, ii = e - k * PC;
-    Zs[k * ldz + ii] = df_split((c0 + ii < p) ? scale * Z[(int64_t)k * p + c0 + ii] : 0.0);
+    Zs[k * ldz + ii] = (c0 + ii < p) ? Z2[(int64_t)k * p + c0 + ii] : AR::zero();
   }
 }
 
-// z chunk from a pre-split (2n x p) float2 array, zero padded
-__device__ __forceinline__ void load_zc(float2* Zs, int ldz, const float2* __restrict__ Z2, int n2,
-                                        int p, int c0, int PC) {
-  for (int e = threadIdx.x; e < n2 * PC; e += blockDim.x) {
-    int k = e / PC, ii = e - k * PC;
-    Zs[k * ldz + ii] = (c0 + ii < p) ? Z2[(int64_t)k * p + c0 + ii] : make_float2(0.f, 0.f);
-  }
-}
-
-// Split, once per field evaluation: Z2 = df(Z), Zh2 = df(Z / h) (2n x p) and
-// F2 = df(q/m F) (p x Nx).
-__global__ void k_prep_df(GridC g, int64_t nz, const double* __restrict__ Z, float2* Z2,
-                          float2* Zh2, int64_t nf, const double* __restrict__ F, float2* F2,
-                          const int* skip) {
-  if (skip && *skip) return;
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < nz) {
-    double z = Z[e];
-    if (Z2) Z2[e] = df_split(z);
-    if (Zh2) Zh2[e] = df_split(z * g.inv_h);
-  } else if (F && e - nz < nf) {
-    F2[e - nz] = df_split(g.qm * F[e - nz]);
-  }
-}
-
-void prep_df(const GridC& g, int n, int p, const double* Z, float2* Z2, float2* Zh2,
-             const double* F, float2* F2, const int* skip, cudaStream_t st) {
-  int64_t nz = Z ? (int64_t)2 * n * p : 0, nf = F ? (int64_t)p * g.Nx : 0;
-  if (nz + nf == 0) return;
-  k_prep_df<<<ceil_div(nz + nf, 256), 256, 0, st>>>(g, nz, Z, Z2, Zh2, nf, F, F2, skip);
-}
-
-// ------------------------------------------------ deposit (double-float)
-__global__ void k_deposit_df(GridC g, int64_t N, int n, int p, int PC,
-                             const float2* __restrict__ Q2, const float2* __restrict__ Zh2,
+// ------------------------------------------------------------------ deposit
+template <class AR>
+__global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
+                             const typename AR::V* __restrict__ Q2,
+                             const typename AR::V* __restrict__ Zh2,
                              unsigned long long* __restrict__ counts, uint16_t* __restrict__ jout,
                              const int* skip) {
+  using V = typename AR::V;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n2 = 2 * n, ldq = n2 + 1, ldz = PC + 1, Nx = g.Nx;
-  float2* Qs = reinterpret_cast<float2*>(smraw);
-  float2* Zs = Qs + TILE_ROWS * ldq;
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(Zs + ((n2 * ldz + 1) & ~1));
+  V* Qs = reinterpret_cast<V*>(smraw);
+  V* Zs = Qs + TILE_ROWS * ldq;
+  const size_t zoff = (sizeof(V) * (TILE_ROWS * ldq + n2 * ldz) + 15) & ~size_t(15);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smraw + zoff);
   const int c0 = blockIdx.y * PC;
-  load_zc(Zs, ldz, Zh2, n2, p, c0, PC);
+  load_zc<AR>(Zs, ldz, Zh2, n2, p, c0, PC);
   for (int e = threadIdx.x; e < PC * Nx; e += blockDim.x) cnt[e] = 0ull;
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
   const bool active = c0 + ii < p;
@@ -170,22 +178,21 @@ __global__ void k_deposit_df(GridC g, int64_t N, int n, int p, int PC,
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
     __syncthreads();
-    load_q2(Qs, ldq, Q2, n2, base, rows);
+    load_rows(Qs, ldq, Q2, n2, base, rows);
     __syncthreads();
     if (active) {
       for (int r = rsub; r < rows; r += RP) {
-        const float2* q = Qs + r * ldq;
-        Acc x;
+        const V* q = Qs + r * ldq;
+        typename AR::A x;
         x.zero();
         for (int k = 0; k < n; ++k) {
           x.fma2(q[k], Zs[k * ldz + ii]);
-          float2 mb = make_float2(-q[n + k].x, -q[n + k].y);
-          x.fma2(mb, Zs[(n + k) * ldz + ii]);
+          x.fma2(AR::neg(q[n + k]), Zs[(n + k) * ldz + ii]);
         }
-        float2 tt = x.df();
+        const V tt = x.out();
         int j;
         long long w1;
-        cell_fixed(tt.x, tt.y, Nx, inv_Nx, scale, g.S, one, j, w1);
+        cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
         int j1 = (j + 1 == Nx) ? 0 : j + 1;
         atomicAdd(mycnt + j, (unsigned long long)(one - w1));
         atomicAdd(mycnt + j1, (unsigned long long)w1);
@@ -200,60 +207,40 @@ __global__ void k_deposit_df(GridC g, int64_t N, int n, int p, int PC,
   }
 }
 
-static inline int chunk_w(int p, int Nx) {
-  int pc = 1;
-  while (pc < p && pc < 32) pc <<= 1;
-  while (pc > 1 && (size_t)pc * Nx * 8 > 96 * 1024) pc >>= 1;
-  return pc;
-}
-
-void deposit_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Zh2,
-                unsigned long long* counts, uint16_t* jout, const int* skip, int num_sms,
-                cudaStream_t st) {
-  int PC = chunk_w(p, g.Nx);
-  int ch = ceil_div(p, PC);
-  int n2 = 2 * n;
-  size_t smem = sizeof(float2) * (TILE_ROWS * (n2 + 1) + ((n2 * (PC + 1) + 1) & ~1)) +
-                sizeof(unsigned long long) * PC * g.Nx;
-  int gx = tile_grid_x(N, ch, 2 * num_sms);  // 4 blocks per SM hide the atomic latency
-  k_deposit_df<<<dim3(gx, ch), TILE_THREADS, smem, st>>>(g, N, n, p, PC, Q2, Zh2, counts, jout, skip);
-}
-
-// --------------------------------------- projection g_X = U_X^T G (double-float)
+// ---------------------------------------------- projection g_X = U_X^T G
 // G_li = (q/m) F_i[j_li] with j from the deposit at the same (Q, zeta).
-template <int PDF_MAXACC>
+// Thread t owns sample column c = t % PC and rows k = t / PC + a (256 / PC).
+template <class AR, int MAXACC>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_project_df(GridC g, int64_t N, int n, int p, int PC,
-                             const float2* __restrict__ Q2, const float2* __restrict__ F2,
-                             const uint16_t* __restrict__ jin, double* __restrict__ part,
-                             const int* skip) {
+k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
+             const typename AR::V* __restrict__ F2, const uint16_t* __restrict__ jin,
+             double* __restrict__ part, const int* skip) {
+  using V = typename AR::V;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n2 = 2 * n, ldq = n2 + 1, Nx = g.Nx, ldG = PC + 1;
-  float2* Qs = reinterpret_cast<float2*>(smraw);
-  float2* Fs = Qs + TILE_ROWS * ldq;  // PC x Nx, q/m F split
-  float2* Gs = Fs + PC * Nx;          // TILE_ROWS x ldG
+  V* Qs = reinterpret_cast<V*>(smraw);
+  V* Fs = Qs + TILE_ROWS * ldq;  // PC x Nx
+  V* Gs = Fs + PC * Nx;          // TILE_ROWS x ldG
   const int c0 = blockIdx.y * PC;
   const int t = threadIdx.x;
   for (int e = t; e < PC * Nx; e += blockDim.x) {
     int c = e / Nx;
-    Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : make_float2(0.f, 0.f);
+    Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : AR::zero();
   }
-  const int npairs = n2 * PC;
-  // thread t owns sample column c = t % PC and rows k = t / PC + a (blockDim / PC)
   const int cc = t % PC, kk0 = t / PC, kstep = blockDim.x / PC;
-  Acc acc[PDF_MAXACC];
+  typename AR::A acc[MAXACC];
 #pragma unroll
-  for (int a = 0; a < PDF_MAXACC; ++a) acc[a].zero();
+  for (int a = 0; a < MAXACC; ++a) acc[a].zero();
   const int pc_eff = min(PC, p - c0);
   for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
     __syncthreads();
-    load_q2(Qs, ldq, Q2, n2, base, rows);
+    load_rows(Qs, ldq, Q2, n2, base, rows);
     for (int e = t; e < rows * PC; e += blockDim.x) {
       int r = e / PC, c = e - r * PC;
-      float2 G = make_float2(0.f, 0.f);
+      V G = AR::zero();
       if (c < pc_eff) G = Fs[c * Nx + jin[(base + r) * p + c0 + c]];
       Gs[r * ldG + c] = G;
     }
@@ -261,14 +248,14 @@ k_project_df(GridC g, int64_t N, int n, int p, int PC,
     // rows in groups of four: the loads of a group are issued together
     int r = 0;
     for (; r + 4 <= rows; r += 4) {
-      const float2 G0 = Gs[r * ldG + cc], G1 = Gs[(r + 1) * ldG + cc];
-      const float2 G2 = Gs[(r + 2) * ldG + cc], G3 = Gs[(r + 3) * ldG + cc];
+      const V G0 = Gs[r * ldG + cc], G1 = Gs[(r + 1) * ldG + cc];
+      const V G2 = Gs[(r + 2) * ldG + cc], G3 = Gs[(r + 3) * ldG + cc];
 #pragma unroll
-      for (int a = 0; a < PDF_MAXACC; ++a) {
+      for (int a = 0; a < MAXACC; ++a) {
         int k = kk0 + a * kstep;
         if (k < n2) {
-          const float2 q0 = Qs[r * ldq + k], q1 = Qs[(r + 1) * ldq + k];
-          const float2 q2 = Qs[(r + 2) * ldq + k], q3 = Qs[(r + 3) * ldq + k];
+          const V q0 = Qs[r * ldq + k], q1 = Qs[(r + 1) * ldq + k];
+          const V q2 = Qs[(r + 2) * ldq + k], q3 = Qs[(r + 3) * ldq + k];
           acc[a].fma2(q0, G0);
           acc[a].fma2(q1, G1);
           acc[a].fma2(q2, G2);
@@ -277,17 +264,16 @@ k_project_df(GridC g, int64_t N, int n, int p, int PC,
       }
     }
     for (; r < rows; ++r) {
-      const float2 G = Gs[r * ldG + cc];
+      const V G = Gs[r * ldG + cc];
 #pragma unroll
-      for (int a = 0; a < PDF_MAXACC; ++a) {
+      for (int a = 0; a < MAXACC; ++a) {
         int k = kk0 + a * kstep;
         if (k < n2) acc[a].fma2(Qs[r * ldq + k], G);
       }
     }
   }
-  (void)npairs;
 #pragma unroll
-  for (int a = 0; a < PDF_MAXACC; ++a) {
+  for (int a = 0; a < MAXACC; ++a) {
     int k = kk0 + a * kstep;
     if (k < n2 && c0 + cc < p) {
       double v = acc[a].value();
@@ -296,64 +282,52 @@ k_project_df(GridC g, int64_t N, int n, int p, int PC,
   }
 }
 
-void project_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* F2,
-                const uint16_t* jin, double* part, int gridx, const int* skip, cudaStream_t st) {
-  int PC = chunk_w(p, g.Nx);
-  int ch = ceil_div(p, PC);
-  int n2 = 2 * n;
-  size_t smem = sizeof(float2) * (TILE_ROWS * (n2 + 1) + PC * g.Nx + TILE_ROWS * (PC + 1));
-  if (n2 <= 4 * (TILE_THREADS / PC))
-    k_project_df<4><<<dim3(gridx, ch), TILE_THREADS, smem, st>>>(g, N, n, p, PC, Q2, F2, jin, part, skip);
-  else
-    k_project_df<16><<<dim3(gridx, ch), TILE_THREADS, smem, st>>>(g, N, n, p, PC, Q2, F2, jin, part, skip);
-}
-
-// -------------------------------------- M = Gamma zeta^H (double-float)
+// -------------------------------------------------------- M = Gamma zeta^H
 // Gamma_li = (q/m) F_i[j_li] + i Im(Q_l zeta_i); M_lk = sum_i Gamma_li conj(zeta_ki).
-// Z2, F2: pre-split zeta and q/m F; M written as double-float rows.
-template <int MAXACC>
+template <class AR, int MAXACC>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_basis_M_df(GridC g, int64_t N, int n, int p, int PC, const float2* __restrict__ Q2,
-             const float2* __restrict__ Z2, const float2* __restrict__ F2,
-             const uint16_t* __restrict__ jin, float2* __restrict__ M) {
+k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
+             const typename AR::V* __restrict__ Z2, const typename AR::V* __restrict__ F2,
+             const uint16_t* __restrict__ jin, typename AR::V* __restrict__ M) {
+  using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n2 = 2 * n, ldq = n2 + 1, ldz = PC + 1, Nx = g.Nx, ldG = PC + 1;
-  float2* Qs = reinterpret_cast<float2*>(smraw);
-  float2* Zs = Qs + TILE_ROWS * ldq;
-  float2* Fs = Zs + n2 * ldz;
-  float2* Gr = Fs + PC * Nx;             // TILE_ROWS x ldG, real part of Gamma
-  float2* Gi = Gr + TILE_ROWS * ldG;     // imaginary part
+  V* Qs = reinterpret_cast<V*>(smraw);
+  V* Zs = Qs + TILE_ROWS * ldq;
+  V* Fs = Zs + n2 * ldz;
+  V* Gr = Fs + PC * Nx;          // TILE_ROWS x ldG, real part of Gamma
+  V* Gi = Gr + TILE_ROWS * ldG;  // imaginary part
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
   const int npairs = TILE_ROWS * n;
   for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
-    Acc ar[MAXACC], ai[MAXACC];
+    typename AR::A ar[MAXACC], ai[MAXACC];
 #pragma unroll
     for (int a = 0; a < MAXACC; ++a) { ar[a].zero(); ai[a].zero(); }
     __syncthreads();
-    load_q2(Qs, ldq, Q2, n2, base, rows);
+    load_rows(Qs, ldq, Q2, n2, base, rows);
     for (int c0 = 0; c0 < p; c0 += PC) {
       __syncthreads();
-      load_zc(Zs, ldz, Z2, n2, p, c0, PC);
+      load_zc<AR>(Zs, ldz, Z2, n2, p, c0, PC);
       for (int e = t; e < PC * Nx; e += blockDim.x) {
         int c = e / Nx;
-        Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : make_float2(0.f, 0.f);
+        Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : AR::zero();
       }
       __syncthreads();
       const bool active = c0 + ii < p;
       for (int r = rsub; r < rows; r += RP) {
-        float2 gr = make_float2(0.f, 0.f), gi = make_float2(0.f, 0.f);
+        V gr = AR::zero(), gi = AR::zero();
         if (active) {
-          const float2* q = Qs + r * ldq;
-          Acc v;
+          const V* q = Qs + r * ldq;
+          typename AR::A v;
           v.zero();
           for (int k = 0; k < n; ++k) {
             v.fma2(q[n + k], Zs[k * ldz + ii]);   // B a
             v.fma2(q[k], Zs[(n + k) * ldz + ii]); // A b
           }
           gr = Fs[ii * Nx + jin[(base + r) * p + c0 + ii]];
-          gi = v.df();
+          gi = v.out();
         }
         Gr[r * ldG + ii] = gr;
         Gi[r * ldG + ii] = gi;
@@ -367,13 +341,13 @@ k_basis_M_df(GridC g, int64_t N, int n, int p, int PC, const float2* __restrict_
           int r = e / n, k = e - r * n;
           if (r < rows) {
             for (int c = 0; c < pc_eff; ++c) {
-              float2 za = Zs[k * ldz + c], zb = Zs[(n + k) * ldz + c];
-              float2 grc = Gr[r * ldG + c], gic = Gi[r * ldG + c];
+              V za = Zs[k * ldz + c], zb = Zs[(n + k) * ldz + c];
+              V grc = Gr[r * ldG + c], gic = Gi[r * ldG + c];
               // Gamma conj(zeta) = (Gr a + Gi b) + i (Gi a - Gr b)
               ar[a].fma2(grc, za);
               ar[a].fma2(gic, zb);
               ai[a].fma2(gic, za);
-              ai[a].fma2(make_float2(-grc.x, -grc.y), zb);
+              ai[a].fma2(AR::neg(grc), zb);
             }
           }
         }
@@ -385,66 +359,56 @@ k_basis_M_df(GridC g, int64_t N, int n, int p, int PC, const float2* __restrict_
       if (e < npairs) {
         int r = e / n, k = e - r * n;
         if (r < rows) {
-          M[(base + r) * n2 + k] = ar[a].df();
-          M[(base + r) * n2 + n + k] = ai[a].df();
+          M[(base + r) * n2 + k] = ar[a].out();
+          M[(base + r) * n2 + n + k] = ai[a].out();
         }
       }
     }
   }
 }
 
-void basis_M_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Z2,
-                const float2* F2, const uint16_t* jin, float2* M, int num_sms, cudaStream_t st) {
-  int PC = chunk_w(p, g.Nx);
-  int n2 = 2 * n;
-  size_t smem = sizeof(float2) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + PC * g.Nx +
-                                  2 * TILE_ROWS * (PC + 1));
-  int gx = tile_grid_x(N, 1, num_sms);
-  if (TILE_ROWS * n <= 4 * TILE_THREADS)
-    k_basis_M_df<4><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, Q2, Z2, F2, jin, M);
-  else
-    k_basis_M_df<16><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, Q2, Z2, F2, jin, M);
-}
-
-// ------------------------------------------------------ Gram (double-float)
-// out_s = blk[pa[s]]^H blk[pb[s]] (n x n complex) from double-float rows;
-// part[blockIdx.x][s][k1][k2] as double2.
+// -------------------------------------------------------------------- Gram
+// out_s = blk[pa[s]]^H blk[pb[s]] (n x n complex); part[blockIdx.x][s][k1][k2].
 #define GDF_ROWS 32
 #define GDF_EPT 4
-__global__ void k_gram_df(int64_t N, int n, GramArgsDF a, double2* __restrict__ part) {
+template <class AR>
+__global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ part) {
+  using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);
+  V* sm = reinterpret_cast<V*>(smraw);
   const int n2 = 2 * n, ldb = n2 + 1;
   const int total = a.npairs * n * n;
   const int e0 = blockIdx.y * blockDim.x * GDF_EPT;
-  Acc re[GDF_EPT], im[GDF_EPT];
+  typename AR::A re[GDF_EPT], im[GDF_EPT];
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) { re[q].zero(); im[q].zero(); }
   for (int64_t tile = blockIdx.x; tile * GDF_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * GDF_ROWS;
     const int rows = (int)((int64_t)GDF_ROWS < N - base ? (int64_t)GDF_ROWS : N - base);
     __syncthreads();
-    for (int b = 0; b < a.nblk; ++b)
+    for (int b = 0; b < a.nblk; ++b) {
+      const V* src = reinterpret_cast<const V*>(a.blk[b]);
       for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         int r = e / n2, k = e - r * n2;
-        sm[(b * GDF_ROWS + r) * ldb + k] = a.blk[b][(base + r) * n2 + k];
+        sm[(b * GDF_ROWS + r) * ldb + k] = src[(base + r) * n2 + k];
       }
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < GDF_EPT; ++q) {
       int e = e0 + q * blockDim.x + threadIdx.x;
       if (e < total) {
         int s = e / (n * n), rem = e - s * n * n, k1 = rem / n, k2 = rem - k1 * n;
-        const float2* X = sm + a.pa[s] * GDF_ROWS * ldb;
-        const float2* Y = sm + a.pb[s] * GDF_ROWS * ldb;
+        const V* X = sm + a.pa[s] * GDF_ROWS * ldb;
+        const V* Y = sm + a.pb[s] * GDF_ROWS * ldb;
         for (int r = 0; r < rows; ++r) {
-          float2 xr = X[r * ldb + k1], xi = X[r * ldb + n + k1];
-          float2 yr = Y[r * ldb + k2], yi = Y[r * ldb + n + k2];
+          V xr = X[r * ldb + k1], xi = X[r * ldb + n + k1];
+          V yr = Y[r * ldb + k2], yi = Y[r * ldb + n + k2];
           // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
           re[q].fma2(xr, yr);
           re[q].fma2(xi, yi);
           im[q].fma2(xr, yi);
-          im[q].fma2(make_float2(-xi.x, -xi.y), yr);
+          im[q].fma2(AR::neg(xi), yr);
         }
       }
     }
@@ -456,21 +420,16 @@ __global__ void k_gram_df(int64_t N, int n, GramArgsDF a, double2* __restrict__ 
   }
 }
 
-void gram_df(int64_t N, int n, const GramArgsDF& a, double2* part, int gridx, cudaStream_t st) {
-  int total = a.npairs * n * n;
-  int gy = ceil_div(total, TILE_THREADS * GDF_EPT);
-  size_t smem = sizeof(float2) * a.nblk * GDF_ROWS * (2 * n + 1);
-  k_gram_df<<<dim3(gridx, gy), TILE_THREADS, smem, st>>>(N, n, a, part);
-}
-
-// Real Gram X^T X of N x m double-float rows (G_V of the stored [A | B]).
-__global__ void k_gram_real_df(int64_t N, int m, const float2* __restrict__ X,
+// Real Gram X^T X of N x m rows (G_V of the stored [A | B]).
+template <class AR>
+__global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restrict__ X,
                                double* __restrict__ part) {
+  using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);
+  V* sm = reinterpret_cast<V*>(smraw);
   const int ldb = m + 1, total = m * m;
   const int e0 = blockIdx.y * blockDim.x * GDF_EPT;
-  Acc acc[GDF_EPT];
+  typename AR::A acc[GDF_EPT];
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) acc[q].zero();
   for (int64_t tile = blockIdx.x; tile * GDF_ROWS < N; tile += gridDim.x) {
@@ -498,51 +457,49 @@ __global__ void k_gram_real_df(int64_t N, int m, const float2* __restrict__ X,
   }
 }
 
-void gram_real_df(int64_t N, int m, const float2* X, double* part, int gridx, cudaStream_t st) {
-  int gy = ceil_div(m * m, TILE_THREADS * GDF_EPT);
-  size_t smem = sizeof(float2) * GDF_ROWS * (m + 1);
-  k_gram_real_df<<<dim3(gridx, gy), TILE_THREADS, smem, st>>>(N, m, X, part);
-}
-
-// --------------------------------------------------- affine (double-float)
+// ------------------------------------------------------------------ affine
 // out_l = sum_t X_t,l C_t (C_t n x n complex FP64, converted once per block);
-// written as FP64 rows (out_d) and/or double-float rows (out_f).
-__global__ void k_affine_df(int64_t N, int n, AffineArgsDF a, const double2* __restrict__ C,
-                            double* __restrict__ out_d, float2* __restrict__ out_f) {
+// written as FP64 rows (out_d) and/or rows of the policy (out_v).
+template <class AR>
+__global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __restrict__ C,
+                            double* __restrict__ out_d, typename AR::V* __restrict__ out_v) {
+  using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n2 = 2 * n, ldb = n2 + 1, nn = n * n;
-  float2* Cr = reinterpret_cast<float2*>(smraw);  // nterms x n x n
-  float2* Ci = Cr + a.nterms * nn;
-  float2* Xs = Ci + a.nterms * nn;
+  V* Cr = reinterpret_cast<V*>(smraw);  // nterms x n x n
+  V* Ci = Cr + a.nterms * nn;
+  V* Xs = Ci + a.nterms * nn;
   for (int e = threadIdx.x; e < a.nterms * nn; e += blockDim.x) {
     double2 c = C[e];
-    Cr[e] = df_split(c.x);
-    Ci[e] = df_split(c.y);
+    Cr[e] = AR::from(c.x);
+    Ci[e] = AR::from(c.y);
   }
   for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
     __syncthreads();
-    for (int b = 0; b < a.nterms; ++b)
+    for (int b = 0; b < a.nterms; ++b) {
+      const V* src = reinterpret_cast<const V*>(a.X[b]);
       for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
         int r = e / n2, k = e - r * n2;
-        Xs[(b * TILE_ROWS + r) * ldb + k] = a.X[b][(base + r) * n2 + k];
+        Xs[(b * TILE_ROWS + r) * ldb + k] = src[(base + r) * n2 + k];
       }
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
       int r = e / n, k = e - r * n;
-      Acc re, im;
+      typename AR::A re, im;
       re.zero();
       im.zero();
       for (int b = 0; b < a.nterms; ++b) {
-        const float2* x = Xs + (b * TILE_ROWS + r) * ldb;
-        const float2* cr = Cr + b * nn;
-        const float2* ci = Ci + b * nn;
+        const V* x = Xs + (b * TILE_ROWS + r) * ldb;
+        const V* cr = Cr + b * nn;
+        const V* ci = Ci + b * nn;
         for (int q = 0; q < n; ++q) {
-          float2 xr = x[q], xi = x[n + q], c_r = cr[q * n + k], c_i = ci[q * n + k];
+          V xr = x[q], xi = x[n + q], c_r = cr[q * n + k], c_i = ci[q * n + k];
           // (xr + i xi)(cr + i ci) = (xr cr - xi ci) + i (xr ci + xi cr)
           re.fma2(xr, c_r);
-          re.fma2(make_float2(-xi.x, -xi.y), c_i);
+          re.fma2(AR::neg(xi), c_i);
           im.fma2(xr, c_i);
           im.fma2(xi, c_r);
         }
@@ -552,31 +509,111 @@ __global__ void k_affine_df(int64_t N, int n, AffineArgsDF a, const double2* __r
         out_d[o + k] = re.value();
         out_d[o + n + k] = im.value();
       }
-      if (out_f) {
-        out_f[o + k] = re.df();
-        out_f[o + n + k] = im.df();
+      if (out_v) {
+        out_v[o + k] = re.out();
+        out_v[o + n + k] = im.out();
       }
     }
   }
 }
 
-void affine_df(int64_t N, int n, const AffineArgsDF& a, const double2* C, double* out_d,
-               float2* out_f, int num_sms, cudaStream_t st) {
-  size_t smem = sizeof(float2) * (2 * a.nterms * n * n + a.nterms * TILE_ROWS * (2 * n + 1));
-  int gx = tile_grid_x(N, 1, num_sms);
-  k_affine_df<<<gx, TILE_THREADS, smem, st>>>(N, n, a, C, out_d, out_f);
+// ============================================================ host wrappers
+template <class AR>
+static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
+  using V = typename AR::V;
+  const GridC& g = *A.g;
+  const int n = A.n, p = A.p, n2 = 2 * n;
+  const int64_t N = A.N;
+  switch (op) {
+    case LP_SPLIT:
+      k_split<AR><<<ceil_div(A.m, 256), 256, 0, st>>>(A.m, A.dsrc, (V*)A.v0);
+      break;
+    case LP_PREP: {
+      int64_t nz = A.dsrc ? (int64_t)n2 * p : 0, nf = A.F ? (int64_t)p * g.Nx : 0;
+      if (nz + nf == 0) break;
+      k_prep<AR><<<ceil_div(nz + nf, 256), 256, 0, st>>>(g, nz, A.dsrc, (V*)A.v0, (V*)A.v1, nf, A.F,
+                                                          (V*)A.v2, A.skip);
+      break;
+    }
+    case LP_DEPOSIT: {
+      int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
+      size_t smem = ((sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1)) + 15) & ~size_t(15)) +
+                    sizeof(unsigned long long) * PC * g.Nx;
+      int gx = tile_grid_x(N, ch, 2 * A.num_sms);
+      k_deposit_lp<AR><<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
+          g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.counts, A.j, A.skip);
+      break;
+    }
+    case LP_PROJECT: {
+      int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
+      size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + PC * g.Nx + TILE_ROWS * (PC + 1));
+      if (n2 <= 4 * (TILE_THREADS / PC))
+        k_project_lp<AR, 4><<<dim3(A.gridx, ch), TILE_THREADS, smem, st>>>(
+            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip);
+      else
+        k_project_lp<AR, 16><<<dim3(A.gridx, ch), TILE_THREADS, smem, st>>>(
+            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip);
+      break;
+    }
+    case LP_BASIS_M: {
+      int PC = chunk_w(p, g.Nx);
+      size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + PC * g.Nx +
+                                 2 * TILE_ROWS * (PC + 1));
+      int gx = tile_grid_x(N, 1, A.num_sms);
+      if (TILE_ROWS * n <= 4 * TILE_THREADS)
+        k_basis_M_lp<AR, 4><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
+                                                            (const V*)A.v1, (const V*)A.v2, A.j,
+                                                            (V*)A.v3);
+      else
+        k_basis_M_lp<AR, 16><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
+                                                             (const V*)A.v1, (const V*)A.v2, A.j,
+                                                             (V*)A.v3);
+      break;
+    }
+    case LP_GRAM: {
+      int total = A.gram.npairs * n * n;
+      int gy = ceil_div(total, TILE_THREADS * GDF_EPT);
+      size_t smem = sizeof(V) * A.gram.nblk * GDF_ROWS * (n2 + 1);
+      k_gram_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, n, A.gram, (double2*)A.part);
+      break;
+    }
+    case LP_GRAM_REAL: {
+      int m = n2;
+      int gy = ceil_div(m * m, TILE_THREADS * GDF_EPT);
+      size_t smem = sizeof(V) * GDF_ROWS * (m + 1);
+      k_gram_real_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, m, (const V*)A.v0, A.part);
+      break;
+    }
+    case LP_AFFINE: {
+      size_t smem = sizeof(V) * (2 * A.aff.nterms * n * n + A.aff.nterms * TILE_ROWS * (n2 + 1));
+      int gx = tile_grid_x(N, 1, A.num_sms);
+      k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0);
+      break;
+    }
+  }
+}
+
+void lp_launch(int arith, LpOp op, const LpArgs& a, cudaStream_t st) {
+  if (arith == 2) launch_all<ArithF32>(op, a, st);
+  else launch_all<ArithDF>(op, a, st);
+}
+
+template <class AR>
+static void set_attrs() {
+  const int big = 220 * 1024;
+  cudaFuncSetAttribute(k_deposit_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_project_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_project_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_basis_M_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_basis_M_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_gram_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_gram_real_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_affine_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 void df_init() {
-  const int big = 220 * 1024;
-  cudaFuncSetAttribute(k_deposit_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_project_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_project_df<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_basis_M_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_basis_M_df<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_gram_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_gram_real_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_affine_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  set_attrs<ArithDF>();
+  set_attrs<ArithF32>();
 }
 
 }  // namespace vpk

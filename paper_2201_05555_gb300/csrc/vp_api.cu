@@ -103,9 +103,9 @@ struct RedWS {
   double2 *grams, *cay, *C, *tmp;
   int* flags;  // [0] done, [1] iters
   double* rows[5];
-  float2 *Q2a, *Q2b;  // double-float shadows of Q0 and Q_half
+  float2 *Q2a, *Q2b;  // row-format shadows of Q0 and Q_half (float2 or float)
   uint16_t* jcell;    // cell index per (particle, sample), N x p
-  float2* frows[5];   // double-float row blocks of the double-float step
+  float2* frows[5];   // row blocks of the FP32-based step
   float2 *Z2, *Zh2, *F2;
   int gx_proj, gx_gram;
 };
@@ -249,58 +249,116 @@ vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, i
 // Gram matrices and the small dense algebra are FP64, and Q is written back
 // in FP64.
 namespace {
+// FP32-based composition (arith 1 double-float, 2 FP32); rows are stored in
+// buffers sized for double-float and used as float2 or float.
 struct RedDF {
   Red& R;
   vp_ctx* ctx;
   cudaStream_t st;
   int64_t N;
-  int n, p;
-  void field(const float2* Q2, const double* Z, const int* skip) {
+  int n, p, arith;
+  LpArgs base() const {
+    LpArgs a;
+    a.g = &R.g;
+    a.N = N;
+    a.n = n;
+    a.p = p;
+    a.num_sms = ctx->num_sms;
+    return a;
+  }
+  void field(const void* Q2, const double* Z, const int* skip) {
     RedWS& w = R.w;
-    VP_K(VP_K_PREP_DF, prep_df(R.g, n, p, Z, w.Z2, w.Zh2, nullptr, nullptr, skip, st));
-    VP_K(VP_K_DEPOSIT_DF, deposit_df(R.g, N, n, p, Q2, w.Zh2, w.counts, w.jcell, skip, ctx->num_sms, st));
+    LpArgs a = base();
+    a.dsrc = Z;
+    a.v0 = w.Z2;
+    a.v1 = w.Zh2;
+    a.skip = skip;
+    VP_K(VP_K_PREP_LP, lp_launch(arith, LP_PREP, a, st));
+    a = base();
+    a.v0 = const_cast<void*>(Q2);
+    a.v1 = w.Zh2;
+    a.counts = w.counts;
+    a.j = w.jcell;
+    a.skip = skip;
+    VP_K(VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
     VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip,
                                ctx->d_status, st));
-    VP_K(VP_K_PREP_DF, prep_df(R.g, n, p, nullptr, nullptr, nullptr, w.F, w.F2, skip, st));
+    a = base();
+    a.F = w.F;
+    a.v2 = w.F2;
+    a.skip = skip;
+    VP_K(VP_K_PREP_LP, lp_launch(arith, LP_PREP, a, st));
   }
-  void grams(std::initializer_list<const float2*> blks,
+  void project(const void* Q2, const int* skip) {
+    LpArgs a = base();
+    a.v0 = const_cast<void*>(Q2);
+    a.v1 = R.w.F2;
+    a.j = R.w.jcell;
+    a.part = R.w.part;
+    a.gridx = R.w.gx_proj;
+    a.skip = skip;
+    VP_K(VP_K_PROJECT_LP, lp_launch(arith, LP_PROJECT, a, st));
+  }
+  void grams(std::initializer_list<const void*> blks,
              std::initializer_list<std::pair<int, int>> pairs, double2* out) {
-    GramArgsDF a{};
-    for (const float2* b : blks) a.blk[a.nblk++] = b;
+    LpArgs a = base();
+    for (const void* b : blks) a.gram.blk[a.gram.nblk++] = b;
     for (auto pr : pairs) {
-      a.pa[a.npairs] = pr.first;
-      a.pb[a.npairs] = pr.second;
-      ++a.npairs;
+      a.gram.pa[a.gram.npairs] = pr.first;
+      a.gram.pb[a.gram.npairs] = pr.second;
+      ++a.gram.npairs;
     }
-    VP_K(VP_K_GRAM_DF, gram_df(N, n, a, reinterpret_cast<double2*>(R.w.part), R.w.gx_gram, st));
-    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)a.npairs * n * n * 2, R.w.part,
+    a.part = R.w.part;
+    a.gridx = R.w.gx_gram;
+    VP_K(VP_K_GRAM_LP, lp_launch(arith, LP_GRAM, a, st));
+    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)a.gram.npairs * n * n * 2, R.w.part,
                                       reinterpret_cast<double*>(out), nullptr, st));
   }
-  void gv(const float2* Q2, double* GVraw) {
-    VP_K(VP_K_GRAM_REAL_DF, gram_real_df(N, 2 * n, Q2, R.w.part, R.w.gx_gram, st));
+  void gv(const void* Q2, double* GVraw) {
+    LpArgs a = base();
+    a.v0 = const_cast<void*>(Q2);
+    a.part = R.w.part;
+    a.gridx = R.w.gx_gram;
+    VP_K(VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
   }
-  void comb(std::initializer_list<const float2*> xs, const double2* C, double* out_d, float2* out_f) {
-    AffineArgsDF a{};
-    for (const float2* x : xs) a.X[a.nterms++] = x;
-    VP_K(VP_K_AFFINE_DF, affine_df(N, n, a, C, out_d, out_f, ctx->num_sms, st));
+  void comb(std::initializer_list<const void*> xs, const double2* C, double* out_d, void* out_v) {
+    LpArgs a = base();
+    for (const void* x : xs) a.aff.X[a.aff.nterms++] = x;
+    a.C = C;
+    a.dout = out_d;
+    a.v0 = out_v;
+    VP_K(VP_K_AFFINE_LP, lp_launch(arith, LP_AFFINE, a, st));
+  }
+  void split(const double* Q, void* Q2) {
+    LpArgs a = base();
+    a.m = N * 2 * n;
+    a.dsrc = Q;
+    a.v0 = Q2;
+    VP_K(VP_K_SPLIT, lp_launch(arith, LP_SPLIT, a, st));
   }
   // scale * X(Q, Z) into out (F2, jcell, Z2 must hold the field at (Q, Z))
-  void basis_velocity(const float2* Q2, const double* Z, double scale, float2* M, float2* out) {
+  void basis_velocity(const void* Q2, const double* Z, double scale, void* M, void* out) {
     RedWS& w = R.w;
-    VP_K(VP_K_BASIS_M_DF, basis_M_df(R.g, N, n, p, Q2, w.Z2, w.F2, w.jcell, M, ctx->num_sms, st));
+    LpArgs a = base();
+    a.v0 = const_cast<void*>(Q2);
+    a.v1 = w.Z2;
+    a.v2 = w.F2;
+    a.v3 = M;
+    a.j = w.jcell;
+    VP_K(VP_K_BASIS_M_LP, lp_launch(arith, LP_BASIS_M, a, st));
     grams({Q2, M}, {{0, 1}}, w.grams);
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
     comb({M, Q2}, w.C, nullptr, out);
   }
   // Cayley retraction of Q0 along xi; leaves G0, P, XX in w.cay
-  void cayley(const float2* Q0, const float2* xi, double* out_d, float2* out_f) {
+  void cayley(const void* Q0, const void* xi, double* out_d, void* out_v) {
     RedWS& w = R.w;
     grams({Q0, xi}, {{0, 0}, {0, 1}, {1, 1}}, w.cay);
     const int nn = n * n;
     VP_K(VP_K_SMALL_CAYLEY, small_cayley_coeffs(n, w.cay, w.cay + nn, w.cay + 2 * nn, w.C, w.tmp,
                                                 ctx->d_status, st));
-    comb({Q0, xi}, w.C, out_d, out_f);
+    comb({Q0, xi}, w.C, out_d, out_v);
   }
 };
 }  // namespace
@@ -311,21 +369,29 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
   RedWS& w = R.w;
   const int64_t N = R.N;
   const int n = R.n, p = R.p;
-  RedDF D{R, ctx, st, N, n, p};
-  float2 *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2], *Xp = w.frows[3],
-         *xi1 = w.frows[4];
-  const int64_t zsz = (int64_t)2 * n * p, qsz = N * 2 * n;
+  RedDF D{R, ctx, st, N, n, p, o.arith};
+  RedDF DD{R, ctx, st, N, n, p, 1};  // double-float diagnostics and re-orthonormalisation
+  void *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2], *Xp = w.frows[3],
+       *xi1 = w.frows[4];
+  const int64_t zsz = (int64_t)2 * n * p;
   const int64_t tstride = (int64_t)p * 2;
   int round = 4;
   for (int step = 0; step < nsteps; ++step) {
-    VP_K(VP_K_SPLIT, split_df(qsz, Q, Q0, st));
+    if (trace && o.arith == 2) {  // FP64-accurate diagnostic in the precision form
+      DD.split(Q, w.Q2b);
+      DD.field(w.Q2b, Z, nullptr);
+      DD.gv(w.Q2b, w.GVraw);
+      VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride,
+                                   trace + step * tstride + 1, 2, nullptr, nullptr, ctx->d_status, st));
+    }
+    D.split(Q, Q0);
     D.field(Q0, Z, nullptr);
-    if (trace) {
+    if (trace && o.arith != 2) {
       D.gv(Q0, w.GVraw);
       VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride,
                                    trace + step * tstride + 1, 2, nullptr, nullptr, ctx->d_status, st));
     }
-    const float2* Qm = Q0;
+    const void* Qm = Q0;
     if (!o.freeze_basis) {
       D.basis_velocity(Q0, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
       D.cayley(Q0, xih, nullptr, Qh);             // Q_half = R_Q0(xi_half)
@@ -341,13 +407,12 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
       VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
     }
     VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
-    VP_CUDA(cudaMemsetAsync(w.aux, 0, sizeof(double), st));
+    VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
         D.field(Qm, w.Ze, w.flags);
-        VP_K(VP_K_PROJECT_DF, project_df(R.g, N, n, p, Qm, w.F2, w.jcell, w.part, w.gx_proj,
-                                         w.flags, st));
+        D.project(Qm, w.flags);
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
         VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol,
                                              o.maxit, o.stall_floor, o.stall_ratio, w.aux, w.flags,
@@ -382,6 +447,17 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
                                                     ctx->d_status, st));
       D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
       D.cayley(Q0, xi1, Q, nullptr);             // Q_1 = R_Q0(xi_1) in FP64
+      if (o.reortho) {                           // Q <- Q (Q^H Q)^-1/2
+        const int nn = n * n;
+        DD.split(Q, w.Q2b);
+        DD.grams({w.Q2b}, {{0, 0}}, w.grams);
+        double2* Wj = w.tmp;
+        double2* Ws = w.tmp + nn;
+        double* lam = reinterpret_cast<double*>(w.tmp + 2 * nn);
+        VP_K(VP_K_INIT, init_launch_jacobi(n, w.grams, Wj, lam, Ws, ctx->d_status, st));
+        VP_K(VP_K_INIT, init_launch_inv_sqrt(n, Ws, lam, w.C, ctx->d_status, st));
+        DD.comb({w.Q2b}, w.C, Q, nullptr);
+      }
     }
     VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
   }
@@ -394,8 +470,8 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step", "k_reconstruct",
     "k_deposit_reduced", "k_project", "k_basis_M", "k_gram", "k_gram_real", "k_reduce_partials",
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
-    "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_df",
-    "k_project_df", "k_basis_M_df", "k_prep_df", "k_gram_df", "k_gram_real_df", "k_affine_df",
+    "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
+    "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
@@ -831,14 +907,14 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0, 1e-5, 0.5, 0};
+  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 0, 0};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
-  if (o.arith != 0 && o.arith != 1) return vp_fail(ctx, VP_EINVAL, "arith must be 0 or 1");
+  if (o.arith < 0 || o.arith > 2) return vp_fail(ctx, VP_EINVAL, "arith must be 0, 1 or 2");
   if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
     return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p = %lld exceeds 25600 (shared memory of the "
                    "fixed-point update)", (long long)(4 * n * n + 2 * n * p));
-  const bool df = o.arith == 1;
+  const bool df = o.arith != 0;
   Red R;
   VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df));
   if (df) return basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st);
@@ -874,7 +950,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
       VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
     }
     VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
-    VP_CUDA(cudaMemsetAsync(w.aux, 0, sizeof(double), st));
+    VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {

@@ -152,14 +152,34 @@ struct AffineArgs {  // out = sum_t X[t] C_t
   const double* X[4];
   int nterms;
 };
-struct GramArgsDF {  // double-float rows
-  const float2* blk[4];
+// FP32-based row kernels (reduced_df.cu): rows stored as float2 (double-float)
+// or float (FP32), selected by the arithmetic policy at launch.
+struct GramArgsLP {
+  const void* blk[4];
   int pa[8], pb[8];
   int nblk, npairs;
 };
-struct AffineArgsDF {
-  const float2* X[4];
+struct AffineArgsLP {
+  const void* X[4];
   int nterms;
+};
+enum LpOp { LP_SPLIT, LP_PREP, LP_DEPOSIT, LP_PROJECT, LP_BASIS_M, LP_GRAM, LP_GRAM_REAL, LP_AFFINE };
+struct LpArgs {
+  const GridC* g = nullptr;
+  int64_t N = 0;
+  int n = 0, p = 0, num_sms = 0, gridx = 0;
+  int64_t m = 0;
+  const double* dsrc = nullptr;
+  const double* F = nullptr;
+  void *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;
+  unsigned long long* counts = nullptr;
+  uint16_t* j = nullptr;
+  double* part = nullptr;
+  const int* skip = nullptr;
+  GramArgsLP gram{};
+  AffineArgsLP aff{};
+  const double2* C = nullptr;
+  double* dout = nullptr;
 };
 
 // pic_kernels.cu
@@ -219,21 +239,8 @@ void energies(int n, int p, const double* GVraw, const double* Z, const double* 
 void dense_init();
 void pic_init();
 
-// reduced_df.cu (double-float particle loops)
-void split_df(int64_t m, const double* x, float2* out, cudaStream_t st);
-void prep_df(const GridC& g, int n, int p, const double* Z, float2* Z2, float2* Zh2,
-             const double* F, float2* F2, const int* skip, cudaStream_t st);
-void deposit_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Zh2,
-                unsigned long long* counts, uint16_t* jout, const int* skip, int num_sms,
-                cudaStream_t st);
-void project_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* F2,
-                const uint16_t* jin, double* part, int gridx, const int* skip, cudaStream_t st);
-void basis_M_df(const GridC& g, int64_t N, int n, int p, const float2* Q2, const float2* Z2,
-                const float2* F2, const uint16_t* jin, float2* M, int num_sms, cudaStream_t st);
-void gram_df(int64_t N, int n, const GramArgsDF& a, double2* part, int gridx, cudaStream_t st);
-void gram_real_df(int64_t N, int m, const float2* X, double* part, int gridx, cudaStream_t st);
-void affine_df(int64_t N, int n, const AffineArgsDF& a, const double2* C, double* out_d,
-               float2* out_f, int num_sms, cudaStream_t st);
+// reduced_df.cu: arith 1 = double-float, 2 = FP32
+void lp_launch(int arith, LpOp op, const LpArgs& a, cudaStream_t st);
 void df_init();
 
 // init.cu (complex SVD start)

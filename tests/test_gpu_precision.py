@@ -1,0 +1,103 @@
+"""Precision form (arith = 2): FP32 storage and accumulation of the N-row work,
+FP64 reductions, small dense algebra and energies.  Its error against the
+FP64 oracle is measured per result and bounded here; the bounds are the
+stated accuracy of this form (the FP64 and double-float forms meet 1e-10)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import csvd, pic, reduced
+from tests.helpers import U_of, q_storage, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# stated per-result bounds of the precision form after one step (relative)
+BOUNDS = {"Z": 1e-6, "UZ": 1e-5, "E": 1e-6, "H": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_05555_gb300 import Context
+    return Context(0)
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda:0")
+
+
+@pytest.mark.parametrize("family,N,p,n,Nx", [("two_stream", 20_000, 64, 10, 128),
+                                            ("bump_on_tail", 20_000, 32, 8, 256)])
+def test_precision_form_one_step(ctx, family, N, p, n, Nx):
+    from paper_2201_05555_gb300 import make_grid
+    fam = W.FAMILIES[family]
+    if family == "two_stream":
+        etas = W.hammersley_params(p, {"v0": (2.0, 3.0)}, {"alpha": 1e-3, "sigma": 1.0})
+    else:
+        etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
+    X0, V0 = W.load_batch(fam, etas, N, quiet=False)
+    U, Z, _ = csvd.csvd_init(X0, V0, n)
+    g = pic.make_grid(N, Nx, fam.L)
+    dt = 0.05
+    U1, Z1, info = reduced.prk2_step(U, Z, dt, g)
+    E1, H1 = reduced.energies(U1, Z1, g)
+    Qd, Zd = T(q_storage(U)), T(Z)
+    grid = make_grid(N, Nx, fam.L)
+    ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, trace=False)
+    ctx.sync_status()
+    Eg, Hg, r = ctx.reduced_energy(grid, Qd, Zd)
+    Ug, Zg = U_of(Qd.cpu().numpy()), Zd.cpu().numpy()
+    err = {"Z": rel(Zg, Z1), "UZ": rel(Ug @ Zg, U1 @ Z1),
+           "E": float(np.max(np.abs(Eg.cpu().numpy() - E1) / np.abs(E1))),
+           "H": float(np.max(np.abs(Hg.cpu().numpy() - H1) / np.abs(H1))),
+           "manifold": float(r.cpu())}
+    print("precision-form errors", family, json.dumps(err))
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open(os.path.join("gpurun_out", f"precision_errors_{family}.json"), "w") as f:
+        json.dump(err, f)
+    for k, b in BOUNDS.items():
+        assert err[k] < b, (k, err[k])
+    assert err["manifold"] < 1e-5
+
+
+# 20-step bounds: FP32 drifts from the FP64 trajectory by about 1.5e-7 per
+# step on the (unstable) two-stream state (3.4e-6 measured after 20 steps);
+# double-float stays at the FP64 level.
+STEP20 = {2: {"H": 1e-5, "E": 1e-5}, 1: {"H": 1e-10, "E": 1e-9}}
+
+
+@pytest.mark.parametrize("arith", [2, 1])
+def test_precision_form_twenty_steps_with_reortho(ctx, arith):
+    """20 steps of the two-stream workload (t = 1): energies of the FP32 and
+    double-float forms (FP64-accurate trace, FP64 re-orthonormalisation every
+    step) against the FP64 oracle, and the manifold residual at FP64 level."""
+    from paper_2201_05555_gb300 import make_grid
+    N, p, n, Nx, dt, steps = 10_000, 32, 6, 64, 0.05, 20
+    etas = W.hammersley_params(p, {"v0": (2.0, 3.0)}, {"alpha": 1e-3, "sigma": 1.0})
+    X0, V0 = W.load_batch(W.TWO_STREAM, etas, N, quiet=False)
+    U, Z, _ = csvd.csvd_init(X0, V0, n)
+    g = pic.make_grid(N, Nx, W.TWO_STREAM.L)
+    Uo, Zo, tro, _ = reduced.run(U, Z, dt, steps, g)
+    Qd, Zd = T(q_storage(U)), T(Z)
+    grid = make_grid(N, Nx, W.TWO_STREAM.L)
+    tr, _ = ctx.basis_update(grid, Qd, Zd, dt, steps, arith=arith, reortho=True)
+    Eg, Hg, r = ctx.reduced_energy(grid, Qd, Zd)
+    ctx.sync_status()
+    trg = tr.cpu().numpy()
+    # trace entry s is the state entering step s = the oracle's state after step s-1
+    eE = np.max(np.abs(trg[1:, :, 0] - tro[:-1, :, 0]) / np.abs(tro[:-1, :, 0]))
+    eH = np.max(np.abs(trg[1:, :, 1] - tro[:-1, :, 1]) / np.abs(tro[:-1, :, 1]))
+    eHf = float(np.max(np.abs(Hg.cpu().numpy() - tro[-1, :, 1]) / np.abs(tro[-1, :, 1])))
+    err = {"E_max_rel": float(eE), "H_max_rel": float(eH), "H_final_rel": eHf,
+           "manifold": float(r.cpu())}
+    print("precision-form 20 steps arith", arith, json.dumps(err))
+    with open(os.path.join("gpurun_out", f"precision_errors_20steps_arith{arith}.json"), "w") as f:
+        json.dump(err, f)
+    assert err["H_max_rel"] < STEP20[arith]["H"] and err["H_final_rel"] < STEP20[arith]["H"]
+    assert err["E_max_rel"] < STEP20[arith]["E"]
+    assert err["manifold"] < 1e-12
