@@ -191,7 +191,7 @@ def reference_arm(args, rank, world):
 
 def config_dict(world):
     return {"workload": "two-stream reduced model, N=1e5 particles x p=64 samples, 2n=20, "
-                        "Nx=128, dt=0.05, FP64 (configs[1])",
+                        "Nx=128, dt=0.05, FP64",
             "N": WL["N"], "p": WL["p"], "rank_2n": WL["n2"], "Nx": WL["Nx"], "dt": WL["dt"],
             "loading": "seeded per sample", "parallelism": f"replicas x{world}",
             "arithmetic": ("FP64 storage; particle loops in double-float (Dot2), small dense "
