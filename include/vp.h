@@ -251,6 +251,101 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
 vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int32_t p, const double* X_dev,
                                  int64_t ldx, double* rho_dev, void* stream);
 
+/* ------------------------------------------------------- quiet-start load */
+/* Quiet-start macro-particles of p samples on the device (Sec. 6.1, eq.
+ * initial_distribution): particle l of sample i sits at
+ * x = F_x^-1(phi_2(l)), v = F_v^-1((l + 1/2)/N), phi_2 the base-2 radical
+ * inverse (2-D Hammersley set), F_x the CDF of (1 + alpha cos kx)/L on [0, L),
+ * F_v the CDF of the family's Gaussian mixture truncated to [-10, 10].
+ * family: 0 Landau damping (k = 0.5; eta_i = {alpha, sigma, unused}),
+ * 1 two-stream (k = 0.2; eta_i = {v0, sigma, alpha}: streams at +-v0, weights
+ * 1/2), 2 bump-on-tail (k = 0.5; eta_i = {vb, alpha, sigma_b}: 0.9 N(0,1) +
+ * 0.1 N(vb, sigma_b^2)).  eta_dev: p x 3 doubles; X_dev, V_dev: p x N.
+ * Inverses are solved to ~1e-14 relative; values agree with an FP64 host
+ * evaluation of the same inverse CDFs to that level, not bit for bit. */
+vp_status vp_load_quiet(vp_ctx* ctx, int32_t family, int64_t N, int32_t p, const double* eta_dev,
+                        double* X_dev, double* V_dev, void* stream);
+
+/* ------------------------------------------------------------ checkpoint */
+/* A reduced state as one host byte image: a header of 8 int64 {magic
+ * "VPSTATE1", version 1, N, n, p, step, has_k, 0}, then Q (N x 2n), Z (2n x p)
+ * and, with has_k, the fixed-point state k (2n x p) that warm-starts
+ * vp_basis_update.  Restarting from an image continues bit for bit: the step
+ * reads nothing else (the grid and options are the caller's). */
+size_t vp_state_bytes(int64_t N, int32_t n, int32_t p, int32_t with_k);
+/* Copies device Q, Z, K (K nullable) into `host` (host_bytes >= vp_state_bytes)
+ * and synchronises `stream`. */
+vp_status vp_state_export(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q_dev,
+                          const double* Z_dev, const double* K_dev, int64_t step, void* host,
+                          size_t host_bytes, void* stream);
+/* Checks magic, version and sizes against (N, n, p), copies the image into
+ * device Q, Z and (if K_dev is given; the image must then hold k) K, returns
+ * the step count in *step (nullable) and synchronises `stream`.  Mismatch or
+ * truncation: VP_EINVAL, nothing copied. */
+vp_status vp_state_import(vp_ctx* ctx, const void* host, size_t host_bytes, int64_t N, int32_t n,
+                          int32_t p, double* Q_dev, double* Z_dev, double* K_dev, int64_t* step,
+                          void* stream);
+
+/* --------------------------------------------------------------- serving */
+/* Many-query serving of the parametric reduced model (Sec. 6: one query = one
+ * parameter set of p samples, evolved from its own start).  A server owns one
+ * device, an HBM budget and a number of slots.  Queries wait in FIFO order
+ * and are admitted while a slot is free and their device bytes fit in what
+ * the budget has left; each admitted query runs on its own context, stream and
+ * host thread: quiet-start load (vp_load_quiet), truncated complex SVD start
+ * (vp_init_csvd) with n = the largest k <= n_max whose sigma_k >= rank_tol
+ * sigma_1, then nsteps partitioned RK2 steps (vp_basis_update, warm-started,
+ * in chunks of 16 steps; arith 2 re-orthonormalises each step).  The grid is
+ * q = -1, m = 1, omega = L/N with a neutralising background.  Every kernel is
+ * deterministic, so a query's result is the same alone or beside others. */
+typedef struct vp_server vp_server;
+
+typedef struct vp_query {
+  int32_t family;   /* as vp_load_quiet */
+  int32_t p;        /* samples, 1..256 */
+  int64_t N;        /* particles per sample, 2..2^31-1 */
+  int32_t Nx;       /* grid nodes, 3..1024 */
+  int32_t n_max;    /* largest reduced rank n (2n columns), 1..min(p, 40) */
+  double rank_tol;  /* keep sigma_k >= rank_tol sigma_1 (e.g. 1e-6) */
+  double dt;
+  int32_t nsteps;
+  int32_t arith;        /* as vp_step_opts.arith */
+  const double* eta;    /* host, p x 3; copied at submit */
+  double* trace_host;   /* host (nullable), nsteps x p x 2: E and H entering each step */
+  double* zeta_host;    /* host (nullable), 2 n_max x p: final Z (first 2n x p written) */
+} vp_query;
+
+typedef struct vp_result {
+  int32_t status;     /* VP_OK, VP_EAGAIN (cancelled) or the first error */
+  int32_t n;          /* reduced rank chosen */
+  int32_t steps_done;
+  int32_t max_iters;  /* largest fixed-point iteration count of a step */
+  double t_submit, t_admit, t_start, t_done; /* seconds since server creation;
+                                                t_start: end of the start phase */
+} vp_result;
+
+/* hbm_budget: device bytes all running queries may hold together;
+ * max_slots >= 1 queries run at once. */
+vp_status vp_server_create(vp_server** out, int device, size_t hbm_budget, int max_slots);
+/* Queue a query.  The caller's output buffers must stay valid until the poll
+ * that returns it.  VP_EINVAL: bad sizes; VP_EUNSUPPORTED: 4 n_max^2 +
+ * 2 n_max p > 25600; VP_ENOMEM: the query alone exceeds the budget; VP_EBUSY:
+ * 4096 queries waiting or the server is stopping. */
+vp_status vp_serve_submit(vp_server* srv, const vp_query* q, uint64_t* ticket);
+/* Wait up to timeout_ms (0: do not wait) for a query.  VP_OK: done, *res
+ * filled (res->status is the query's own status) and the ticket released;
+ * VP_EAGAIN (timeout_ms = 0) / VP_ETIMEDOUT: not done yet, ticket kept;
+ * VP_EINVAL: unknown or released ticket. */
+vp_status vp_serve_poll(vp_server* srv, uint64_t ticket, vp_result* res, int32_t timeout_ms);
+/* Cancel a query: a waiting query finishes at once with status VP_EAGAIN; a
+ * running one stops at its next 16-step boundary with VP_EAGAIN. */
+vp_status vp_serve_cancel(vp_server* srv, uint64_t ticket);
+/* Counters (each nullable). */
+vp_status vp_server_stats(vp_server* srv, int64_t* submitted, int64_t* completed, int32_t* active,
+                          int32_t* pending, size_t* used_bytes);
+/* Drop waiting queries, cancel running ones, join every thread, free. */
+vp_status vp_server_destroy(vp_server* srv);
+
 /* ------------------------------------------------------------ profiling */
 /* Kernels of the library, for launch counts and event timing. */
 typedef enum vp_kernel {
@@ -259,7 +354,7 @@ typedef enum vp_kernel {
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
-  VP_K_INIT, VP_K_COUNT
+  VP_K_INIT, VP_K_LOAD, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

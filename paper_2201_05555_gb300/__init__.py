@@ -15,4 +15,8 @@ from .binding import (  # noqa: F401
     lib_path,
     load_library,
     make_grid,
+    Server,
+    Query,
+    Result,
+    deposit_cic_noalloc,
 )

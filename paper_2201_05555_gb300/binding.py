@@ -10,6 +10,7 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
 import torch
 
 from .build import LIB
@@ -76,6 +77,17 @@ _SIGS = [
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
     ("vp_kernel_name", C.c_char_p, [_I32]),
+    ("vp_load_quiet", _I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
+    ("vp_state_bytes", _SZ, [_I64, _I32, _I32, _I32]),
+    ("vp_state_export", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _I64, _P, _SZ, _P]),
+    ("vp_state_import", _I32, [_P, _P, _SZ, _I64, _I32, _I32, _P, _P, _P, C.POINTER(_I64), _P]),
+    ("vp_server_create", _I32, [C.POINTER(_P), C.c_int, _SZ, C.c_int]),
+    ("vp_serve_submit", _I32, [_P, _P, C.POINTER(C.c_uint64)]),
+    ("vp_serve_poll", _I32, [_P, C.c_uint64, _P, _I32]),
+    ("vp_serve_cancel", _I32, [_P, C.c_uint64]),
+    ("vp_server_stats", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32),
+                               C.POINTER(_I32), C.POINTER(_SZ)]),
+    ("vp_server_destroy", _I32, [_P]),
 ]
 
 # vp_kernel ids (include/vp.h)
@@ -84,7 +96,8 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
-           "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init"]
+           "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
+           "k_load_quiet"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -320,6 +333,37 @@ class Context:
                                                     _ptr(g), self._stream()), "deim_gather_project")
         return g
 
+    def load_quiet(self, family: int, N: int, eta: torch.Tensor):
+        """(X, V), p x N each: quiet-start particles of p samples (eta: p x 3)."""
+        p = eta.shape[0]
+        X, V = self._empty(p, N), self._empty(p, N)
+        self._check(self.lib.vp_load_quiet(self.h, family, N, p, _ptr(eta, name="eta"), _ptr(X),
+                                           _ptr(V), self._stream()), "load_quiet")
+        return X, V
+
+    def state_export(self, Q: torch.Tensor, Z: torch.Tensor, kstate: torch.Tensor | None = None,
+                     step: int = 0) -> bytes:
+        """Checkpoint image (bytes) of a reduced state Q (N x 2n), Z (2n x p), k."""
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        nb = self.lib.vp_state_bytes(N, n2 // 2, p, int(kstate is not None))
+        buf = (C.c_char * nb)()
+        self._check(self.lib.vp_state_export(self.h, N, n2 // 2, p, _ptr(Q, name="Q"),
+                                             _ptr(Z, name="Z"), _ptr(kstate, name="kstate"), step,
+                                             C.cast(buf, _P), nb, self._stream()), "state_export")
+        return bytes(buf)
+
+    def state_import(self, image: bytes, N: int, n: int, p: int, with_k: bool = False):
+        """(Q, Z, kstate or None, step) from a checkpoint image."""
+        Q, Z = self._empty(N, 2 * n), self._empty(2 * n, p)
+        K = self._empty(2 * n, p) if with_k else None
+        step = _I64(0)
+        buf = C.create_string_buffer(image, len(image))
+        self._check(self.lib.vp_state_import(self.h, C.cast(buf, _P), len(image), N, n, p,
+                                             _ptr(Q), _ptr(Z), _ptr(K), C.byref(step),
+                                             self._stream()), "state_import")
+        return Q, Z, K, step.value
+
 
 def deposit_cic_noalloc(grid: Grid, X: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
     """vp_deposit_cic_noalloc: the deposit of vp_deposit_cic for callers that
@@ -343,3 +387,96 @@ def default_context(device: int = 0) -> Context:
     if device not in _default:
         _default[device] = Context(device)
     return _default[device]
+
+
+# ------------------------------------------------------------------ serving
+class Query(C.Structure):
+    """vp_query (include/vp.h)."""
+    _fields_ = [("family", _I32), ("p", _I32), ("N", _I64), ("Nx", _I32), ("n_max", _I32),
+                ("rank_tol", _D), ("dt", _D), ("nsteps", _I32), ("arith", _I32),
+                ("eta", _P), ("trace_host", _P), ("zeta_host", _P)]
+
+
+class Result(C.Structure):
+    """vp_result (include/vp.h)."""
+    _fields_ = [("status", _I32), ("n", _I32), ("steps_done", _I32), ("max_iters", _I32),
+                ("t_submit", _D), ("t_admit", _D), ("t_start", _D), ("t_done", _D)]
+
+
+FAMILY_ID = {"landau": 0, "two_stream": 1, "bump_on_tail": 2}
+
+
+class Server:
+    """vp_server: queued reduced solves on one device within an HBM budget.
+
+    submit() copies eta and allocates the host outputs (numpy trace
+    nsteps x p x 2 and zeta 2n_max x p); poll() returns them with the
+    vp_result once the query is done."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 8 << 30, max_slots: int = 4):
+        self.lib = load_library()
+        h = _P()
+        s = self.lib.vp_server_create(C.byref(h), device, hbm_budget, max_slots)
+        if s != 0:
+            raise VPError(s, "vp_server_create")
+        self.h = h
+        self._held: dict[int, tuple] = {}
+
+    def submit(self, family: int | str, eta, N: int, Nx: int, n_max: int, dt: float,
+               nsteps: int, arith: int = 1, rank_tol: float = 1e-6) -> int:
+        fam = FAMILY_ID[family] if isinstance(family, str) else int(family)
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        p = eta.shape[0]
+        trace = np.zeros((nsteps, p, 2))
+        zeta = np.zeros((2 * n_max, p))
+        q = Query(fam, p, N, Nx, n_max, rank_tol, dt, nsteps, arith, eta.ctypes.data,
+                  trace.ctypes.data, zeta.ctypes.data)
+        t = C.c_uint64(0)
+        s = self.lib.vp_serve_submit(self.h, C.addressof(q), C.byref(t))
+        if s != 0:
+            raise VPError(s, "vp_serve_submit")
+        self._held[t.value] = (eta, trace, zeta)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """None while the query runs; else (Result, trace, zeta[:2n])."""
+        r = Result()
+        s = self.lib.vp_serve_poll(self.h, ticket, C.addressof(r), timeout_ms)
+        if s in (4, 5):
+            return None
+        if s != 0:
+            raise VPError(s, "vp_serve_poll")
+        _, trace, zeta = self._held.pop(ticket)
+        return r, trace, zeta[: 2 * max(r.n, 0)]
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        out = self.poll(ticket, timeout_ms)
+        if out is None:
+            raise VPError(5, f"query {ticket} not done after {timeout_ms} ms")
+        return out
+
+    def cancel(self, ticket: int):
+        s = self.lib.vp_serve_cancel(self.h, ticket)
+        if s != 0:
+            raise VPError(s, "vp_serve_cancel")
+
+    def stats(self) -> dict:
+        sub, com = _I64(0), _I64(0)
+        act, pen = _I32(0), _I32(0)
+        used = _SZ(0)
+        self.lib.vp_server_stats(self.h, C.byref(sub), C.byref(com), C.byref(act), C.byref(pen),
+                                 C.byref(used))
+        return {"submitted": sub.value, "completed": com.value, "active": act.value,
+                "pending": pen.value, "used_bytes": used.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vp_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -110,23 +110,34 @@ struct RedWS {
   int gx_proj, gx_gram;
 };
 
+size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df, int* gx_proj,
+                    int* gx_gram) {
+  const int n2 = 2 * n, nn = n * n;
+  const int gp = tile_grid_x(N, project_chunks(p, Nx > 0 ? Nx : 3), sms);
+  const int gg = gram_grid_x(N, sms);
+  if (gx_proj) *gx_proj = gp;
+  if (gx_gram) *gx_gram = gg;
+  size_t part_d = std::max<size_t>((size_t)gp * n2 * p,
+                                   std::max<size_t>((size_t)gg * 12 * nn * 2, (size_t)gg * n2 * n2));
+  size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
+  return arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
+         arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)n2 * n2, 8) +
+         arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
+         arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
+         (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
+         (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) +
+                   2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8)
+             : 0);
+}
+
 vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w,
                  bool df = false) {
   const int n2 = 2 * n, nn = n * n;
-  const int sms = ctx->num_sms;
-  w.gx_proj = tile_grid_x(N, project_chunks(p, Nx > 0 ? Nx : 3), sms);
-  w.gx_gram = gram_grid_x(N, sms);
+  size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
+  size_t bytes = red_ws_bytes(ctx->num_sms, N, n, p, Nx, nrows, df, &w.gx_proj, &w.gx_gram);
   size_t part_d = std::max<size_t>((size_t)w.gx_proj * n2 * p,
                                    std::max<size_t>((size_t)w.gx_gram * 12 * nn * 2,
                                                     (size_t)w.gx_gram * n2 * n2));
-  size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
-  size_t bytes = arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
-                 arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)n2 * n2, 8) +
-                 arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) +
-                 arena_bytes(4 * nn, 16) + arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) +
-                 arena_bytes(8, 4) + (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
-                 (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) +
-                           2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) : 0);
   void* base = nullptr;
   VP_TRY(vp_workspace(ctx, bytes, &base));
   Arena a{(char*)base, 0, bytes};
@@ -472,7 +483,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
-    "k_init"};
+    "k_init", "k_load_quiet"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -520,6 +531,39 @@ void vp_prof_collect(vp_ctx* ctx) {
 }
 
 // ================================================================ context
+namespace {
+size_t init_ws_bytes(int sms, int64_t N, int p, int n, int* gx_out) {
+  const int64_t pp = (int64_t)p * p;
+  int gx = ceil_div(N, 32);
+  int gmax = (int)std::max<int64_t>(1, (64ll << 20) / (pp * 16));  // partials <= 64 MiB
+  gx = std::min(gx, std::min(2 * sms, gmax));
+  if (gx_out) *gx_out = gx;
+  const int nn = n * n;
+  return arena_bytes((size_t)gx * pp, 16) + 4 * arena_bytes(pp, 16) + arena_bytes(p, 8) +
+         arena_bytes((size_t)p * n, 16) + 2 * arena_bytes(nn, 16) + arena_bytes(n, 8) +
+         arena_bytes((size_t)gx * n * p, 16) + arena_bytes((size_t)n * p, 16) +
+         arena_bytes((size_t)N * 2 * n, 8) + arena_bytes(4 * nn, 16) +
+         arena_bytes((size_t)2 * sms * 4 * nn, 16);
+}
+}  // namespace
+
+// Workspace one serving query needs: the larger of the start and the steps.
+size_t vp_query_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int arith) {
+  const bool df = arith != 0;
+  return std::max(init_ws_bytes(sms, N, p, n, nullptr),
+                  red_ws_bytes(sms, N, n, p, Nx, df ? 0 : 5, df, nullptr, nullptr));
+}
+
+// Free a context's workspace arena (synchronises the device).
+void vp_workspace_release(vp_ctx* ctx) {
+  if (!ctx || !ctx->ws) return;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+}
+
 extern "C" {
 
 vp_status vp_profile_enable(vp_ctx* ctx, uint64_t mask) {
@@ -827,15 +871,9 @@ vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const doubl
     return vp_fail(ctx, VP_EINVAL, "n = %d outside [1, min(p, N, 40)]", n);
   if (!X0 || !V0 || !Q || !Z) return vp_fail(ctx, VP_EINVAL, "null pointer");
   const int64_t pp = (int64_t)p * p;
-  int gx = ceil_div(N, 32);
-  int gmax = (int)std::max<int64_t>(1, (64ll << 20) / (pp * 16));  // partials <= 64 MiB
-  gx = std::min(gx, std::min(2 * ctx->num_sms, gmax));
+  int gx = 0;
   const int nn = n * n;
-  size_t bytes = arena_bytes((size_t)gx * pp, 16) + 4 * arena_bytes(pp, 16) + arena_bytes(p, 8) +
-                 arena_bytes((size_t)p * n, 16) + 2 * arena_bytes(nn, 16) + arena_bytes(n, 8) +
-                 arena_bytes((size_t)gx * n * p, 16) + arena_bytes((size_t)n * p, 16) +
-                 arena_bytes((size_t)N * 2 * n, 8) + arena_bytes(4 * nn, 16) +
-                 arena_bytes((size_t)2 * ctx->num_sms * 4 * nn, 16);
+  size_t bytes = init_ws_bytes(ctx->num_sms, N, p, n, &gx);
   void* base = nullptr;
   VP_TRY(vp_workspace(ctx, bytes, &base));
   Arena a{(char*)base, 0, bytes};
