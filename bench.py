@@ -43,6 +43,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM cl
 # instructions, so the derived peak is 152 SMs x 128 lanes x 2.07 GHz x 2 / 11.
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 11 / 1e12
 ARITH = 1
+# served form: Poisson arrivals; N log-uniform, p uniform in [1, 64], horizon T
+SERVE = dict(rate=50.0, seconds=10.0, N=(1e3, 1e4), T=4.0, slots=16, arith=2,
+             budget=150 << 30)
 
 
 def parse():
@@ -53,6 +56,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the full-order, precision-form and served measurements")
+    ap.add_argument("--serve-rate", type=float, default=SERVE["rate"])
+    ap.add_argument("--serve-seconds", type=float, default=SERVE["seconds"])
+    ap.add_argument("--serve-n", type=float, nargs=2, default=SERVE["N"])
+    ap.add_argument("--serve-horizon", type=float, default=SERVE["T"])
+    ap.add_argument("--serve-slots", type=int, default=SERVE["slots"])
+    ap.add_argument("--serve-arith", type=int, default=SERVE["arith"])
     return ap.parse_args()
 
 
@@ -66,6 +77,26 @@ def initial_state(rank: int = 0):
     wl = workload()
     X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet, seed=W.BASE_SEED + 1000 * rank)
     return wl, X0, V0
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel's source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) < 4 or line.startswith("#") or f[0] != kernel:
+            continue
+        src = os.path.join(ROOT, f[2])
+        if not os.path.exists(src):
+            return None
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != f[3]:
+            return None
+        return int(f[1])
+    return None
 
 
 # ----------------------------------------------------------------- clocks
@@ -161,6 +192,170 @@ print(json.dumps({{"seconds": dt, "iters": its}}))
                       f"2n={WL['n2']}) numpy float64, BLAS 1 thread; "
                       f"fixed-point iterations {out['iters']}",
             "seconds": out["seconds"]}
+
+
+# ------------------------------------------------------ extra measurements
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+def full_order_measure(ctx, torch, dev, flush, reps: int = 5) -> dict:
+    """Full-order Landau damping: N = 1e4, p = 4, Nx = 64, dt = 0.1, 200
+    Stormer-Verlet steps per launch sequence (seeded loading)."""
+    from paper_2201_05555_gb300 import make_grid
+    wl = W.landau_full_order()
+    X0, V0 = W.particles(wl)
+    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    Xd, Vd = torch.tensor(X0, device=dev), torch.tensor(V0, device=dev)
+    X, V = Xd.clone(), Vd.clone()
+    ctx.full_step(grid, X, V, wl.dt, wl.steps)  # warm-up
+    stream = torch.cuda.current_stream(dev)
+    ev = _events(torch, reps)
+    for r in range(reps):
+        X.copy_(Xd)
+        V.copy_(Vd)
+        flush.zero_()
+        ev[r][0].record(stream)
+        ctx.full_step(grid, X, V, wl.dt, wl.steps)
+        ev[r][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    med = ms[len(ms) // 2]
+    units = wl.N * wl.p * wl.steps
+    return {"workload": "full-order Landau damping, N=1e4 x p=4, Nx=64, dt=0.1, 200 steps, FP64",
+            "value": units / (med / 1e3), "unit": UNIT, "us_per_step": med * 1e3 / wl.steps,
+            "ms_per_200_steps_median": med, "reps": reps,
+            "bound": "latency (state 640 KB, on-chip); HBM fraction not meaningful"}
+
+
+def precision_measure(ctx, torch, dev, flush, steps: int = 4, warm: int = 1) -> dict:
+    """Precision form on the bump-on-tail workload: N = 1e6, p = 256,
+    Nx = 256, dt = 0.1, Philox-seeded loading on the device, rank 2n in [16, 64] chosen
+    at t = 0 by tail energy < 1e-8.  The same start is stepped with FP32 row
+    work (arith 2, FP64 re-orthonormalisation and energies) and with
+    double-float row work (arith 1, FP64-accurate); errors compare the two
+    energy traces."""
+    from paper_2201_05555_gb300 import make_grid
+    N, p, Nx, dt = 1_000_000, 256, 256, 0.1
+    etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
+    rows = torch.tensor([[e["vb"], e["alpha"], e["sigma_b"]] for e in etas], device=dev)
+    X, V = ctx.load_particles(2, N, rows, mode=1, seed=W.BASE_SEED)
+    Q, Z, sig, n = ctx.init_csvd_rank(X, V, 8, 32, 1e-8)
+    Q, Z = Q.clone(), Z.clone()
+    ctx.sync_status()
+    del X, V
+    torch.cuda.empty_cache()
+    grid = make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+    stream = torch.cuda.current_stream(dev)
+    out, traces = {}, {}
+    for arith in (1, 2):
+        Qa, Za, Ka = Q.clone(), Z.clone(), torch.zeros_like(Z)
+        trs = []
+        for _ in range(warm):
+            tr, _ = ctx.basis_update(grid, Qa, Za, dt, 1, arith=arith, kstate=Ka,
+                                     reortho=arith == 2)
+            trs.append(tr)
+        ev = _events(torch, steps)
+        its = []
+        for s_ in range(steps):
+            flush.zero_()
+            ev[s_][0].record(stream)
+            tr, it = ctx.basis_update(grid, Qa, Za, dt, 1, arith=arith, kstate=Ka,
+                                      reortho=arith == 2)
+            ev[s_][1].record(stream)
+            trs.append(tr)
+            its.append(it)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        traces[arith] = torch.cat(trs).cpu().numpy()
+        out[arith] = {"value": N * p * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                      "fixed_point_iters": [int(i[0]) for i in its]}
+        del Qa, Za, Ka
+    ref, lo = traces[1], traces[2]
+    errE = float(np.max(np.abs(lo[..., 0] - ref[..., 0]) / np.abs(ref[..., 0])))
+    errH = float(np.max(np.abs(lo[..., 1] - ref[..., 1]) / np.abs(ref[..., 1])))
+    return {"workload": f"bump-on-tail precision form, N=1e6 x p=256, Nx=256, dt=0.1, "
+                        f"Philox-seeded loading, 2n={2 * n} (tail energy < 1e-8 in [16, 64])",
+            "value": out[2]["value"], "unit": UNIT, "ms_per_step": out[2]["ms_per_step"],
+            "arith": "FP32 N-row work, FP64 Grams/small dense/re-orthonormalisation/energies",
+            "fixed_point_iters": out[2]["fixed_point_iters"],
+            "fp64_form": {"value": out[1]["value"], "ms_per_step": out[1]["ms_per_step"],
+                          "arith": "double-float N-row work (FP64-accurate)",
+                          "fixed_point_iters": out[1]["fixed_point_iters"]},
+            "speedup_vs_fp64_form": out[2]["value"] / out[1]["value"],
+            "max_rel_err_E": errE, "max_rel_err_H": errH,
+            "err_steps": warm + steps, "rank_2n": 2 * n}
+
+
+def served_measure(args, dev_index: int) -> dict:
+    """Served form: Poisson arrivals of reduced-solve queries.  Each query:
+    family uniform over {Landau, two-stream, bump-on-tail}, p uniform in
+    [1, 64] samples with eta uniform over the family's range, N log-uniform,
+    horizon T (dt 0.1 Landau/bump-on-tail, 0.05 two-stream), rank by tail
+    energy < 1e-8 with 2n <= 20, admitted by an HBM budget."""
+    import threading
+    from paper_2201_05555_gb300 import Server
+    rng = np.random.Generator(np.random.PCG64(W.BASE_SEED + 5))
+    rate, secs = args.serve_rate, args.serve_seconds
+    lo, hi = args.serve_n
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * secs * 2) + 10))
+    arrivals = arrivals[arrivals < secs]
+    queries = []
+    for _ in arrivals:
+        fam = int(rng.integers(0, 3))
+        p = int(rng.integers(1, 65))
+        N = int(round(10 ** rng.uniform(np.log10(lo), np.log10(hi))))
+        if fam == 0:
+            eta = np.stack([rng.uniform(0.01, 0.05, p), np.ones(p), np.zeros(p)], 1)
+        elif fam == 1:
+            eta = np.stack([rng.uniform(2.0, 3.0, p), np.ones(p), np.full(p, 1e-3)], 1)
+        else:
+            eta = np.stack([rng.uniform(4.0, 5.0, p), np.full(p, 0.04), np.full(p, 0.5)], 1)
+        dt = 0.05 if fam == 1 else 0.1
+        nsteps = int(round(args.serve_horizon / dt))
+        queries.append(dict(family=fam, eta=eta, N=N, Nx=128, n_max=min(10, p), dt=dt,
+                            nsteps=nsteps, arith=args.serve_arith, rank_tol=1e-8, loading=1,
+                            seed=int(rng.integers(0, 2**63))))
+    srv = Server(dev_index, hbm_budget=SERVE["budget"], max_slots=args.serve_slots)
+    # warm the slots (first use of each context builds its workspace)
+    warm = [srv.submit(**dict(queries[0], nsteps=2)) for _ in range(args.serve_slots)]
+    for t in warm:
+        srv.wait(t)
+    tickets = [None] * len(queries)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, (ta, q) in enumerate(zip(arrivals, queries)):
+            d = ta - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = srv.submit(**q)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = [srv.wait(t, 600_000)[0] for t in tickets]
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
+    ok = [r.status == 0 for r in res]
+    units = sum(q["N"] * q["eta"].shape[0] * r.steps_done for q, r in zip(queries, res))
+    first = min(r.t_submit for r in res)
+    last = max(r.t_done for r in res)
+    return {"workload": (f"served reduced solves, Poisson arrivals {rate:g}/s for {secs:g} s, "
+                         f"N log-uniform [{lo:.0e}, {hi:.0e}], p uniform [1, 64], Nx=128, "
+                         f"horizon T={args.serve_horizon:g}, 2n<=20, arith {args.serve_arith}, "
+                         f"{args.serve_slots} slots, 150 GB budget"),
+            "queries": len(res), "ok": int(sum(ok)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "value": units / (last - first), "unit": UNIT, "wall_s": wall,
+            "queue_wait_p50_ms": float(np.percentile([(r.t_admit - r.t_submit) * 1e3
+                                                      for r in res], 50)),
+            "error": ("FP32 row work with FP64 re-orthonormalisation and energies: one-step "
+                      "|dE|/E, |dH|/H <= 1e-6, 20 steps <= 1e-5 against the FP64 oracle"
+                      if args.serve_arith == 2 else "FP64-accurate (parity 1e-10)")}
 
 
 # --------------------------------------------------------------- arms
@@ -306,7 +501,7 @@ def ours(args, rank, world):
              "instructions per emulated FP64 FMA" if ARITH == 1 else
              "FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2.07 GHz, measured 1.19 TFLOP/s")
     roof = {"bound": "alu", "kernel": KP, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(KP),
             "launches": l, "working_launches": real, "ms_total": pms, "peak_basis": basis,
             "flop_per_launch": flop_per_launch}
     clocks = clk.summary()
@@ -320,6 +515,10 @@ def ours(args, rank, world):
                     "d2h_bytes_per_step": state_bytes + trh.numel() * 8},
             "gpu_launches": total_launches, "roofline": roof, "clocks": clocks,
             "fixed_point_iters": its}
+    if not args.no_extras and world == 1:
+        line["full_order"] = full_order_measure(ctx, torch, dev, flush)
+        line["precision_form"] = precision_measure(ctx, torch, dev, flush)
+        line["served"] = served_measure(args, local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     print(json.dumps(line))

@@ -212,6 +212,19 @@ vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const doubl
                        const double* V0_dev, double* Q_dev, double* Z_dev, double* sigma_dev,
                        void* stream);
 
+/* The same start with the rank chosen at t = 0 from the singular values (the
+ * paper observes that a constant rank suffices; the rule is a reading): n =
+ * the smallest k in [n_min, n_max] whose relative tail energy
+ * sum_{j>k} sigma_j^2 / sum_j sigma_j^2 < tail_tol (n_max if none), lowered
+ * while sigma_n < 1e-6 sigma_1, even below n_min (cond S(Z) <= 1e12; singular
+ * values from the Gram matrix resolve ~1e-8 sigma_1).  Q_dev must hold N x 2 n_max; Q (N x 2n) and
+ * Z (2n x p) are written densely for the chosen n, returned in *n_out.
+ * Synchronises `stream` once (the eigenvalues go to the host for the rule). */
+vp_status vp_init_csvd_rank(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, int32_t n_max,
+                            double tail_tol, const double* X0_dev, const double* V0_dev,
+                            double* Q_dev, double* Z_dev, double* sigma_dev, int32_t* n_out,
+                            void* stream);
+
 /* a11. FP64 diagnostics of a reduced state: electric energy E_i and
  * Hamiltonian H_i = 1/2 |U_V Z_i|^2 + E_i (p each, eq. nonlinear_hamiltonian),
  * and the manifold residual |Q^H Q - I|_F (= |U^T U - I|_F / sqrt 2; U^T J U = J
@@ -251,20 +264,26 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
 vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int32_t p, const double* X_dev,
                                  int64_t ldx, double* rho_dev, void* stream);
 
-/* ------------------------------------------------------- quiet-start load */
-/* Quiet-start macro-particles of p samples on the device (Sec. 6.1, eq.
- * initial_distribution): particle l of sample i sits at
- * x = F_x^-1(phi_2(l)), v = F_v^-1((l + 1/2)/N), phi_2 the base-2 radical
- * inverse (2-D Hammersley set), F_x the CDF of (1 + alpha cos kx)/L on [0, L),
- * F_v the CDF of the family's Gaussian mixture truncated to [-10, 10].
+/* ---------------------------------------------------------------- loading */
+/* Macro-particles of p samples on the device (Sec. 6.1, eq.
+ * initial_distribution): particle l of sample i sits at x = F_x^-1(u_x),
+ * v = F_v^-1(u_v), F_x the CDF of (1 + alpha cos kx)/L on [0, L), F_v the CDF
+ * of the family's Gaussian mixture truncated to [-10, 10].
+ * mode 0, quiet start: u_x = phi_2(l) (base-2 radical inverse), u_v =
+ * (l + 1/2)/N (2-D Hammersley set); seed unused.
+ * mode 1, seeded: one Philox4x32-10 block per particle (Salmon et al. 2011)
+ * with counter (l mod 2^32, l div 2^32, i, 0) and key (seed mod 2^32,
+ * seed div 2^32); u_x = (w0 >> 5, w1 >> 6) and u_v = (w2 >> 5, w3 >> 6) as
+ * 53-bit fractions.
  * family: 0 Landau damping (k = 0.5; eta_i = {alpha, sigma, unused}),
  * 1 two-stream (k = 0.2; eta_i = {v0, sigma, alpha}: streams at +-v0, weights
  * 1/2), 2 bump-on-tail (k = 0.5; eta_i = {vb, alpha, sigma_b}: 0.9 N(0,1) +
  * 0.1 N(vb, sigma_b^2)).  eta_dev: p x 3 doubles; X_dev, V_dev: p x N.
  * Inverses are solved to ~1e-14 relative; values agree with an FP64 host
  * evaluation of the same inverse CDFs to that level, not bit for bit. */
-vp_status vp_load_quiet(vp_ctx* ctx, int32_t family, int64_t N, int32_t p, const double* eta_dev,
-                        double* X_dev, double* V_dev, void* stream);
+vp_status vp_load_particles(vp_ctx* ctx, int32_t family, int32_t mode, uint64_t seed, int64_t N,
+                            int32_t p, const double* eta_dev, double* X_dev, double* V_dev,
+                            void* stream);
 
 /* ------------------------------------------------------------ checkpoint */
 /* A reduced state as one host byte image: a header of 8 int64 {magic
@@ -292,21 +311,27 @@ vp_status vp_state_import(vp_ctx* ctx, const void* host, size_t host_bytes, int6
  * device, an HBM budget and a number of slots.  Queries wait in FIFO order
  * and are admitted while a slot is free and their device bytes fit in what
  * the budget has left; each admitted query runs on its own context, stream and
- * host thread: quiet-start load (vp_load_quiet), truncated complex SVD start
- * (vp_init_csvd) with n = the largest k <= n_max whose sigma_k >= rank_tol
- * sigma_1, then nsteps partitioned RK2 steps (vp_basis_update, warm-started,
- * in chunks of 16 steps; arith 2 re-orthonormalises each step).  The grid is
+ * host thread: particle load (vp_load_particles), truncated complex SVD start
+ * (vp_init_csvd) with the rank chosen at t = 0 from the singular values:
+ * n = the smallest k in [n_min, n_max] whose relative tail energy
+ * sum_{j>k} sigma_j^2 / sum_j sigma_j^2 < rank_tol (n_max if none), lowered
+ * while sigma_n < 1e-6 sigma_1 so that S(Z) stays invertible; then nsteps
+ * partitioned RK2 steps (vp_basis_update, warm-started, in chunks of 16
+ * steps; arith 2 re-orthonormalises each step).  The grid is
  * q = -1, m = 1, omega = L/N with a neutralising background.  Every kernel is
  * deterministic, so a query's result is the same alone or beside others. */
 typedef struct vp_server vp_server;
 
 typedef struct vp_query {
-  int32_t family;   /* as vp_load_quiet */
+  int32_t family;   /* as vp_load_particles */
+  int32_t loading;  /* vp_load_particles mode: 0 quiet start, 1 Philox-seeded */
+  uint64_t seed;    /* key of the seeded loading */
   int32_t p;        /* samples, 1..256 */
   int64_t N;        /* particles per sample, 2..2^31-1 */
   int32_t Nx;       /* grid nodes, 3..1024 */
   int32_t n_max;    /* largest reduced rank n (2n columns), 1..min(p, 40) */
-  double rank_tol;  /* keep sigma_k >= rank_tol sigma_1 (e.g. 1e-6) */
+  int32_t n_min;    /* smallest reduced rank, 1..n_max */
+  double rank_tol;  /* relative tail energy left out by the rank (e.g. 1e-8) */
   double dt;
   int32_t nsteps;
   int32_t arith;        /* as vp_step_opts.arith */

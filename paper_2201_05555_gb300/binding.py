@@ -77,7 +77,9 @@ _SIGS = [
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
     ("vp_kernel_name", C.c_char_p, [_I32]),
-    ("vp_load_quiet", _I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
+    ("vp_init_csvd_rank", _I32, [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P,
+                                 C.POINTER(_I32), _P]),
+    ("vp_load_particles", _I32, [_P, _I32, _I32, C.c_uint64, _I64, _I32, _P, _P, _P, _P]),
     ("vp_state_bytes", _SZ, [_I64, _I32, _I32, _I32]),
     ("vp_state_export", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _I64, _P, _SZ, _P]),
     ("vp_state_import", _I32, [_P, _P, _SZ, _I64, _I32, _I32, _P, _P, _P, C.POINTER(_I64), _P]),
@@ -97,7 +99,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
-           "k_load_quiet"]
+           "k_load"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -312,6 +314,22 @@ class Context:
                                           self._stream()), "init_csvd")
         return Q, Z, sig
 
+    def init_csvd_rank(self, X0: torch.Tensor, V0: torch.Tensor, n_min: int, n_max: int,
+                       tail_tol: float):
+        """(Q, Z, sigma, n): the start with n chosen from the singular values."""
+        p, N = X0.shape
+        Q = self._empty(N, 2 * n_max)
+        Z = self._empty(2 * n_max, p)
+        sig = self._empty(p)
+        n = _I32(0)
+        self._check(self.lib.vp_init_csvd_rank(self.h, N, p, n_min, n_max, tail_tol,
+                                               _ptr(X0, name="X0"), _ptr(V0, name="V0"),
+                                               _ptr(Q), _ptr(Z), _ptr(sig), C.byref(n),
+                                               self._stream()), "init_csvd_rank")
+        k = n.value
+        return (Q.view(-1)[: N * 2 * k].view(N, 2 * k), Z.view(-1)[: 2 * k * p].view(2 * k, p),
+                sig, k)
+
     def reduced_energy(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor):
         N, n2 = Q.shape
         p = Z.shape[1]
@@ -333,12 +351,15 @@ class Context:
                                                     _ptr(g), self._stream()), "deim_gather_project")
         return g
 
-    def load_quiet(self, family: int, N: int, eta: torch.Tensor):
-        """(X, V), p x N each: quiet-start particles of p samples (eta: p x 3)."""
+    def load_particles(self, family: int, N: int, eta: torch.Tensor, mode: int = 0,
+                       seed: int = 0):
+        """(X, V), p x N each: particles of p samples (eta: p x 3); mode 0 quiet
+        start, 1 Philox-seeded with key `seed`."""
         p = eta.shape[0]
         X, V = self._empty(p, N), self._empty(p, N)
-        self._check(self.lib.vp_load_quiet(self.h, family, N, p, _ptr(eta, name="eta"), _ptr(X),
-                                           _ptr(V), self._stream()), "load_quiet")
+        self._check(self.lib.vp_load_particles(self.h, family, mode, seed, N, p,
+                                               _ptr(eta, name="eta"), _ptr(X), _ptr(V),
+                                               self._stream()), "load_particles")
         return X, V
 
     def state_export(self, Q: torch.Tensor, Z: torch.Tensor, kstate: torch.Tensor | None = None,
@@ -392,8 +413,9 @@ def default_context(device: int = 0) -> Context:
 # ------------------------------------------------------------------ serving
 class Query(C.Structure):
     """vp_query (include/vp.h)."""
-    _fields_ = [("family", _I32), ("p", _I32), ("N", _I64), ("Nx", _I32), ("n_max", _I32),
-                ("rank_tol", _D), ("dt", _D), ("nsteps", _I32), ("arith", _I32),
+    _fields_ = [("family", _I32), ("loading", _I32), ("seed", C.c_uint64), ("p", _I32),
+                ("N", _I64), ("Nx", _I32), ("n_max", _I32),
+                ("n_min", _I32), ("rank_tol", _D), ("dt", _D), ("nsteps", _I32), ("arith", _I32),
                 ("eta", _P), ("trace_host", _P), ("zeta_host", _P)]
 
 
@@ -423,13 +445,15 @@ class Server:
         self._held: dict[int, tuple] = {}
 
     def submit(self, family: int | str, eta, N: int, Nx: int, n_max: int, dt: float,
-               nsteps: int, arith: int = 1, rank_tol: float = 1e-6) -> int:
+               nsteps: int, arith: int = 1, rank_tol: float = 1e-8, n_min: int = 1,
+               loading: int = 0, seed: int = 0) -> int:
         fam = FAMILY_ID[family] if isinstance(family, str) else int(family)
         eta = np.ascontiguousarray(eta, dtype=np.float64)
         p = eta.shape[0]
         trace = np.zeros((nsteps, p, 2))
         zeta = np.zeros((2 * n_max, p))
-        q = Query(fam, p, N, Nx, n_max, rank_tol, dt, nsteps, arith, eta.ctypes.data,
+        q = Query(fam, loading, seed, p, N, Nx, n_max, n_min, rank_tol, dt, nsteps, arith,
+                  eta.ctypes.data,
                   trace.ctypes.data, zeta.ctypes.data)
         t = C.c_uint64(0)
         s = self.lib.vp_serve_submit(self.h, C.addressof(q), C.byref(t))

@@ -70,6 +70,7 @@ __global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2*
   __shared__ double2 rot_c[128], rot_s[128];
   __shared__ int pj[128], pk[128];
   __shared__ double off_s, tot_s;
+  __shared__ int nrot;
   __shared__ int order[256];
   const int t = threadIdx.x, nt = blockDim.x;
   for (int e = t; e < m * m; e += nt) W[e] = make_double2((e / m) == (e % m) ? 1.0 : 0.0, 0.0);
@@ -78,7 +79,7 @@ __global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2*
   const int npair = slots / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence: off-diagonal mass against the whole
-    if (t == 0) { off_s = 0.0; tot_s = 0.0; }
+    if (t == 0) { off_s = 0.0; tot_s = 0.0; nrot = 0; }
     __syncthreads();
     double off = 0.0, tot = 0.0;
     for (int e = t; e < m * m; e += nt) {
@@ -106,8 +107,11 @@ __global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2*
         if (k < m) {
           double2 ajk = A[j * m + k];
           double mag = sqrt(ajk.x * ajk.x + ajk.y * ajk.y);
-          if (mag > 0.0) {
-            double ajj = A[j * m + j].x, akk = A[k * m + k].x;
+          double ajj = A[j * m + j].x, akk = A[k * m + k].x;
+          // rotate unless a_jk is below rounding of the diagonal pair (the
+          // classical threshold |a_jk| <= eps sqrt|a_jj a_kk|)
+          if (mag > 1e-15 * sqrt(fabs(ajj * akk)) && mag > 1e-300) {
+            atomicAdd(&nrot, 1);
             double tau = (akk - ajj) / (2.0 * mag);
             double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
@@ -160,6 +164,10 @@ __global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2*
       }
       __syncthreads();
     }
+    // a sweep without rotations: every pair is below the threshold
+    const int nr = nrot;
+    __syncthreads();
+    if (nr == 0) break;
     if (sweep == max_sweeps - 1 && t == 0) vp_set_status(status, VP_ENOCONV);
   }
   // sort eigenvalues descending (m <= 256, one thread: selection order)
@@ -302,6 +310,14 @@ __global__ void k_zeta_to_Z(int n, int p, const double2* zeta, double* Z) {
     Z[(int64_t)k * p + i] = zeta[e].x;
     Z[(int64_t)(n + k) * p + i] = zeta[e].y;
   }
+}
+
+// Dynamic shared memory above 48 KB (p up to 256: 2 p IG_ROWS doubles = 128 KB).
+void init_kernels_init() {
+  const int lim = 227 * 1024;
+  cudaFuncSetAttribute(k_rgram, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_r_times, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_zeta, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 void init_launch_rgram(int64_t N, int p, const double* X, const double* V, double2* part, int gx,

@@ -1,9 +1,12 @@
-// Quiet-start loading of macro-particles on the device (Sec. 6.1, eq.
-// initial_distribution): particle l of sample i takes x = F_x^-1(phi_2(l)) and
-// v = F_v^-1((l + 1/2)/N), with phi_2 the base-2 radical inverse (the 2-D
-// Hammersley set), F_x the CDF of (1 + alpha cos kx)/L on [0, L) and F_v the
-// CDF of a Gaussian mixture truncated to [-10, 10].  Inverses by bisection on
-// the bracket, finished by safeguarded Newton steps.
+// Loading of macro-particles on the device (Sec. 6.1, eq.
+// initial_distribution): particle l of sample i takes x = F_x^-1(u_x) and
+// v = F_v^-1(u_v), with F_x the CDF of (1 + alpha cos kx)/L on [0, L) and F_v
+// the CDF of a Gaussian mixture truncated to [-10, 10].  Quiet start: u_x =
+// phi_2(l) (base-2 radical inverse), u_v = (l + 1/2)/N (the 2-D Hammersley
+// set).  Seeded: one Philox4x32-10 block per particle (Salmon et al., SC 2011),
+// counter (l mod 2^32, l div 2^32, i, 0), key (seed mod 2^32, seed div 2^32);
+// u_x from words 0-1 and u_v from words 2-3 as 53-bit doubles.  Inverses by
+// bisection on the bracket, finished by safeguarded Newton steps.
 #include "vp_internal.cuh"
 
 namespace vpk {
@@ -53,8 +56,28 @@ __device__ void family_params(int family, const double* eta, double& alpha, Mix&
   M.norm = hi - lo;
 }
 
-__global__ void k_load_quiet(int family, double k, int64_t N, const double* __restrict__ eta,
-                             double* __restrict__ X, double* __restrict__ V) {
+// Philox4x32 with 10 rounds: round constants 0xD2511F53, 0xCD9E8D57, key
+// increments 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// mode 0: quiet start; mode 1: Philox with key `seed`.
+__global__ void k_load(int family, int mode, unsigned long long seed, double k, int64_t N,
+                       const double* __restrict__ eta, double* __restrict__ X,
+                       double* __restrict__ V) {
   const int i = blockIdx.y;
   double alpha;
   Mix M;
@@ -62,15 +85,25 @@ __global__ void k_load_quiet(int family, double k, int64_t N, const double* __re
   const double L = 2.0 * 3.141592653589793 / k;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N;
        l += (int64_t)gridDim.x * blockDim.x) {
-    // radical inverse base 2 of l
-    unsigned long long b = (unsigned long long)l;
-    double ux = 0.0, f = 0.5;
-    while (b) {
-      if (b & 1ull) ux += f;
-      b >>= 1;
-      f *= 0.5;
+    double ux, uv;
+    if (mode == 0) {
+      // radical inverse base 2 of l
+      unsigned long long b = (unsigned long long)l;
+      double f = 0.5;
+      ux = 0.0;
+      while (b) {
+        if (b & 1ull) ux += f;
+        b >>= 1;
+        f *= 0.5;
+      }
+      uv = ((double)l + 0.5) / (double)N;
+    } else {
+      const unsigned long long ul = (unsigned long long)l;
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)ul, (uint32_t)(ul >> 32), (uint32_t)i, 0u),
+                                    make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+      ux = u53(w.x, w.y);
+      uv = u53(w.z, w.w);
     }
-    const double uv = ((double)l + 0.5) / (double)N;
     // x: solve x + (alpha/k) sin(kx) = ux L on [0, L]
     double a = 0.0, c = L, x = ux * L;
     for (int it = 0; it < 60; ++it) {
@@ -107,13 +140,13 @@ __global__ void k_load_quiet(int family, double k, int64_t N, const double* __re
   }
 }
 
-void load_quiet(int family, double k, int64_t N, int p, const double* eta, double* X, double* V,
-                int num_sms, cudaStream_t st) {
+void load_particles(int family, int mode, unsigned long long seed, double k, int64_t N, int p,
+                    const double* eta, double* X, double* V, int num_sms, cudaStream_t st) {
   int bx = ceil_div(N, 256);
   int want = (4 * num_sms + p - 1) / p;
   if (bx > want) bx = want;
   if (bx < 1) bx = 1;
-  k_load_quiet<<<dim3(bx, p), 256, 0, st>>>(family, k, N, eta, X, V);
+  k_load<<<dim3(bx, p), 256, 0, st>>>(family, mode, seed, k, N, eta, X, V);
 }
 
 }  // namespace vpk

@@ -7,7 +7,7 @@
 // own context, CUDA stream and host thread, so steps of concurrent queries
 // overlap on the device; a finished query frees its slot and its memory and
 // the next waiting query is admitted.  A query's work on the device:
-// quiet-start particles (load.cu), the truncated complex SVD start with n
+// particles (load.cu: quiet start or Philox-seeded), the truncated complex SVD start with n
 // chosen from the singular values, then the partitioned RK2 steps (FP64,
 // double-float or FP32 row work) in chunks, with the energy trace and the
 // final coefficients copied to the caller's host buffers.  All kernels are
@@ -118,27 +118,19 @@ void vp_server::run(Job* j, Slot* sl) {
   // start: particles, complex SVD, rank from the singular values
   if (s == VP_OK) {
     cudaMemcpyAsync(eta, j->eta.data(), sizeof(double) * 3 * p, cudaMemcpyHostToDevice, st);
-    vp_status s1 = vp_load_quiet(ctx, q.family, N, p, eta, X, V, st);
+    vp_status s1 = vp_load_particles(ctx, q.family, q.loading, q.seed, N, p, eta, X, V, st);
     if (s1 != VP_OK) fail(s1);
-    vp_status s2 = s1 != VP_OK ? s1 : vp_init_csvd(ctx, N, p, n, X, V, Q, Z, sig, st);
+    int32_t nsel = 0;
+    vp_status s2 = s1 != VP_OK ? s1
+                               : vp_init_csvd_rank(ctx, N, p, q.n_min, q.n_max, q.rank_tol, X, V, Q,
+                                                   Z, sig, &nsel, st);
     if (s2 != VP_OK) fail(s2);
+    n = nsel;
   }
   if (s == VP_OK) {
-    std::vector<double> sh(p);
-    cudaMemcpyAsync(sh.data(), sig, sizeof(double) * p, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) fail(VP_ECUDA);
     vp_status s2 = vp_ctx_sync_status(ctx, st);
     if (s2 != VP_OK) fail(s2);
-    // largest n <= n_max with sigma_n >= rank_tol sigma_1 keeps S(Z) invertible
-    int nn = 0;
-    for (int k = 0; k < std::min(q.n_max, p); ++k)
-      if (sh[k] >= q.rank_tol * sh[0] && sh[k] > 0.0) nn = k + 1;
-    if (nn < 1) fail(VP_ENUMERIC);
-    if (s == VP_OK && nn < n) {
-      n = nn;
-      vp_status s3 = vp_init_csvd(ctx, N, p, n, X, V, Q, Z, nullptr, st);
-      if (s3 != VP_OK) fail(s3);
-    }
   }
   if (X) cudaFreeAsync(X, st);
   if (V) cudaFreeAsync(V, st);
@@ -311,8 +303,9 @@ vp_status vp_server_create(vp_server** out, int device, size_t hbm_budget, int m
 
 vp_status vp_serve_submit(vp_server* s, const vp_query* q, uint64_t* ticket) {
   if (!s || !q || !ticket) return VP_EINVAL;
-  if (q->family < 0 || q->family > 2 || q->N < 2 || q->N >= (int64_t(1) << 31) || q->p < 1 ||
-      q->p > 256 || q->n_max < 1 || q->n_max > 40 || q->n_max > q->p || q->Nx < 3 ||
+  if (q->family < 0 || q->family > 2 || q->loading < 0 || q->loading > 1 || q->N < 2 || q->N >= (int64_t(1) << 31) || q->p < 1 ||
+      q->p > 256 || q->n_max < 1 || q->n_max > 40 || q->n_max > q->p || q->n_min < 1 ||
+      q->n_min > q->n_max || q->Nx < 3 ||
       q->Nx > VP_MAX_NX || !(q->dt > 0.0) || q->nsteps < 1 || q->arith < 0 || q->arith > 2 ||
       !(q->rank_tol >= 0.0) || !q->eta)
     return VP_EINVAL;
@@ -473,13 +466,16 @@ vp_status vp_state_import(vp_ctx* ctx, const void* host, size_t host_bytes, int6
   return VP_OK;
 }
 
-vp_status vp_load_quiet(vp_ctx* ctx, int32_t family, int64_t N, int32_t p, const double* eta_dev,
-                        double* X_dev, double* V_dev, void* stream) {
-  if (!ctx || !eta_dev || !X_dev || !V_dev || family < 0 || family > 2 || N < 1 || p < 1 || p > 65535)
+vp_status vp_load_particles(vp_ctx* ctx, int32_t family, int32_t mode, uint64_t seed, int64_t N,
+                            int32_t p, const double* eta_dev, double* X_dev, double* V_dev,
+                            void* stream) {
+  if (!ctx || !eta_dev || !X_dev || !V_dev || family < 0 || family > 2 || mode < 0 || mode > 1 ||
+      N < 1 || p < 1 || p > 65535)
     return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_LOAD, vpk::load_quiet(family, family_k(family), N, p, eta_dev, X_dev, V_dev, ctx->num_sms, st));
+  VP_K(VP_K_LOAD, vpk::load_particles(family, mode, seed, family_k(family), N, p, eta_dev, X_dev,
+                                      V_dev, ctx->num_sms, st));
   VP_LAUNCHED();
   return VP_OK;
 }

@@ -483,7 +483,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
-    "k_init", "k_load_quiet"};
+    "k_init", "k_load"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -531,6 +531,31 @@ void vp_prof_collect(vp_ctx* ctx) {
 }
 
 // ================================================================ context
+// Rank at t = 0 (reading of the paper's constant-rank observation): the
+// smallest n in [n_min, n_max] whose relative tail energy
+// sum_{j>n} sigma_j^2 / sum_j sigma_j^2 is below tol (n_max if none), then
+// lowered while sigma_n < 1e-6 sigma_1 (even below n_min): S(Z) = Z Z^T then
+// has condition number <= 1e12, and sigma_n stays above the resolution of
+// singular values taken from the Gram matrix R0^H R0 (~1e-8 sigma_1).
+// Returns 0 when all singular values vanish.
+int vp_choose_rank(const double* sig, int p, int n_min, int n_max, double tol) {
+  n_max = std::min(n_max, p);
+  double total = 0.0;
+  for (int k = 0; k < p; ++k) total += sig[k] * sig[k];
+  if (!(total > 0.0)) return 0;
+  int n = n_max;
+  double tail = total;
+  for (int k = 1; k <= n_max; ++k) {
+    tail -= sig[k - 1] * sig[k - 1];
+    if (k >= n_min && tail < tol * total) {
+      n = k;
+      break;
+    }
+  }
+  while (n > 0 && !(sig[n - 1] >= 1e-6 * sig[0])) --n;
+  return n;
+}
+
 namespace {
 size_t init_ws_bytes(int sms, int64_t N, int p, int n, int* gx_out) {
   const int64_t pp = (int64_t)p * p;
@@ -644,6 +669,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   reduced_init();
   dense_init();
   df_init();
+  init_kernels_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_pinned);
@@ -862,35 +888,39 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
   return VP_OK;
 }
 
-vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0,
-                       const double* V0, double* Q, double* Z, double* sigma, void* stream) {
-  VP_ENTER();
+// Truncated complex SVD start.  rank_tol < 0: n = n_max as given; otherwise
+// the eigenvalues of R0^H R0 are copied to the host after the Jacobi sweep
+// (one stream synchronisation) and n is chosen by vp_choose_rank.
+static vp_status init_csvd_impl(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, int32_t n_max,
+                                double rank_tol, const double* X0, const double* V0, double* Q,
+                                double* Z, double* sigma, int32_t* n_out, cudaStream_t st) {
   VP_TRY(check_np(ctx, N, p));
   if (p > 256) return vp_fail(ctx, VP_EUNSUPPORTED, "p = %d > 256", p);
-  if (n < 1 || n > 40 || n > p || n > N)
-    return vp_fail(ctx, VP_EINVAL, "n = %d outside [1, min(p, N, 40)]", n);
+  if (n_max < 1 || n_max > 40 || n_max > p || n_max > N)
+    return vp_fail(ctx, VP_EINVAL, "n = %d outside [1, min(p, N, 40)]", n_max);
+  if (n_min < 1 || n_min > n_max) return vp_fail(ctx, VP_EINVAL, "n_min = %d outside [1, n_max]", n_min);
   if (!X0 || !V0 || !Q || !Z) return vp_fail(ctx, VP_EINVAL, "null pointer");
   const int64_t pp = (int64_t)p * p;
   int gx = 0;
-  const int nn = n * n;
-  size_t bytes = init_ws_bytes(ctx->num_sms, N, p, n, &gx);
+  size_t bytes = init_ws_bytes(ctx->num_sms, N, p, n_max, &gx);
   void* base = nullptr;
   VP_TRY(vp_workspace(ctx, bytes, &base));
   Arena a{(char*)base, 0, bytes};
+  const int nnx = n_max * n_max;
   double2* part = a.take<double2>((size_t)gx * pp);
   double2* A = a.take<double2>(pp);
   double2* Wj = a.take<double2>(pp);
   double2* Ws = a.take<double2>(pp);
   double* lam = a.take<double>(p);
-  double2* Cn = a.take<double2>((size_t)p * n);
-  double2* G = a.take<double2>(nn);
-  double2* Gs = a.take<double2>(nn);
-  double* lamG = a.take<double>(n);
-  double2* zpart = a.take<double2>((size_t)gx * n * p);
-  double2* zeta = a.take<double2>((size_t)n * p);
-  double* Q0 = a.take<double>((size_t)N * 2 * n);
-  double2* WG = a.take<double2>(4 * nn);
-  double2* gpart = a.take<double2>((size_t)2 * ctx->num_sms * 4 * nn);
+  double2* Cn = a.take<double2>((size_t)p * n_max);
+  double2* G = a.take<double2>(nnx);
+  double2* Gs = a.take<double2>(nnx);
+  double* lamG = a.take<double>(n_max);
+  double2* zpart = a.take<double2>((size_t)gx * n_max * p);
+  double2* zeta = a.take<double2>((size_t)n_max * p);
+  double* Q0 = a.take<double>((size_t)N * 2 * n_max);
+  double2* WG = a.take<double2>(4 * nnx);
+  double2* gpart = a.take<double2>((size_t)2 * ctx->num_sms * 4 * nnx);
   (void)gpart;
   // 1. A = R0^H R0
   VP_K(VP_K_INIT, init_launch_rgram(N, p, X0, V0, part, gx, st));
@@ -898,6 +928,17 @@ vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const doubl
                                     reinterpret_cast<double*>(A), nullptr, st));
   // 2. A = W diag(lambda) W^H, lambda descending
   VP_K(VP_K_INIT, init_launch_jacobi(p, A, Wj, lam, Ws, ctx->d_status, st));
+  int n = n_max;
+  if (rank_tol >= 0.0) {
+    std::vector<double> lh(p), sh(p);
+    VP_CUDA(cudaMemcpyAsync(lh.data(), lam, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
+    VP_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < p; ++k) sh[k] = lh[k] > 0.0 ? std::sqrt(lh[k]) : 0.0;
+    n = vp_choose_rank(sh.data(), p, n_min, n_max, rank_tol);
+    if (n < 1) return vp_fail(ctx, VP_ENUMERIC, "no usable rank: the snapshot matrix is zero");
+  }
+  if (n_out) *n_out = n;
+  const int nn = n * n;
   // 3. Q0 = R0 W_n diag(lambda_n)^-1/2
   VP_K(VP_K_INIT, init_launch_coeff(p, n, Ws, lam, Cn, ctx->d_status, st));
   VP_K(VP_K_INIT, init_launch_r_times(N, p, n, X0, V0, Cn, Q0, ctx->num_sms, st));
@@ -931,6 +972,20 @@ vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const doubl
   }
   VP_LAUNCHED();
   return VP_OK;
+}
+
+vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0,
+                       const double* V0, double* Q, double* Z, double* sigma, void* stream) {
+  VP_ENTER();
+  return init_csvd_impl(ctx, N, p, 1, n, -1.0, X0, V0, Q, Z, sigma, nullptr, st);
+}
+
+vp_status vp_init_csvd_rank(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, int32_t n_max,
+                            double tail_tol, const double* X0, const double* V0, double* Q,
+                            double* Z, double* sigma, int32_t* n_out, void* stream) {
+  VP_ENTER();
+  if (!(tail_tol >= 0.0)) return vp_fail(ctx, VP_EINVAL, "tail_tol must be >= 0");
+  return init_csvd_impl(ctx, N, p, n_min, n_max, tail_tol, X0, V0, Q, Z, sigma, n_out, st);
 }
 
 // One partitioned RK2 step per iteration (Sec. 5; stage structure as in the

@@ -57,6 +57,8 @@ vp_status vp_workspace(vp_ctx* ctx, size_t bytes, void** out);
 // Workspace bytes of one serving query (start + steps) and arena release.
 size_t vp_query_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int arith);
 void vp_workspace_release(vp_ctx* ctx);
+// Rank at t = 0 from the singular values (tail energy rule).
+int vp_choose_rank(const double* sig, int p, int n_min, int n_max, double tol);
 
 #define VP_CUDA(call)                                              \
   do {                                                             \
@@ -260,8 +262,10 @@ void init_launch_inv_sqrt(int n, const double2* W, const double* lambda, double2
 void init_launch_zeta(int64_t N, int p, int n, const double* Q, const double* X, const double* V,
                       double2* part, int gx, cudaStream_t st);
 void init_launch_zeta_to_Z(int n, int p, const double2* zeta, double* Z, cudaStream_t st);
-// Quiet-start loading (load.cu): eta p x 3, X and V p x N.
-void load_quiet(int family, double k, int64_t N, int p, const double* eta, double* X, double* V,
-                int num_sms, cudaStream_t st);
+void init_kernels_init();  // kernel attributes of init.cu
+// Particle loading (load.cu): eta p x 3, X and V p x N; mode 0 quiet start,
+// mode 1 Philox4x32-10 keyed by seed.
+void load_particles(int family, int mode, unsigned long long seed, double k, int64_t N, int p,
+                    const double* eta, double* X, double* V, int num_sms, cudaStream_t st);
 
 }  // namespace vpk

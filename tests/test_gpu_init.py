@@ -24,7 +24,8 @@ def T(a):
 
 
 @pytest.mark.parametrize("N,p,n,quiet", [(3001, 37, 5, False), (20_000, 64, 10, False),
-                                         (4000, 16, 3, True), (501, 7, 7, False)])
+                                         (4000, 16, 3, True), (501, 7, 7, False),
+                                         (3000, 256, 16, False), (2000, 200, 40, False)])
 def test_init_csvd(ctx, N, p, n, quiet):
     etas = W.hammersley_params(p, {"v0": (2.0, 3.0)}, {"alpha": 1e-3, "sigma": 1.0})
     X0, V0 = W.load_batch(W.TWO_STREAM, etas, N, quiet=quiet)
@@ -49,3 +50,31 @@ def test_init_csvd(ctx, N, p, n, quiet):
         # well separated spectrum: the subspace, hence U Z, is unique
         Uo, Zo, _ = csvd.csvd_init(X0, V0, n)
         assert rel(U @ Zg, Uo @ Zo) < 1e-10
+
+
+@pytest.mark.parametrize("family,quiet,n_min,n_max,tol", [
+    (W.TWO_STREAM, True, 1, 10, 1e-8), (W.LANDAU, True, 2, 12, 1e-12),
+    (W.BUMP_ON_TAIL, False, 3, 8, 1e-3), (W.BUMP_ON_TAIL, True, 8, 16, 1e-30)])
+def test_init_csvd_rank(ctx, family, quiet, n_min, n_max, tol):
+    """Rank chosen from the singular values: the smallest n in [n_min, n_max]
+    with relative tail energy < tol, lowered while sigma_n < 1e-6 sigma_1;
+    the state equals the fixed-rank start with that n, bit for bit."""
+    N, p = 4000, 16
+    if family is W.LANDAU:
+        etas = [{"alpha": a, "sigma": 1.0} for a in np.linspace(0.01, 0.05, p)]
+    elif family is W.TWO_STREAM:
+        etas = W.hammersley_params(p, {"v0": (2.0, 3.0)}, {"alpha": 1e-3, "sigma": 1.0})
+    else:
+        etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
+    X0, V0 = W.load_batch(family, etas, N, quiet=quiet)
+    Q, Z, sig, n = ctx.init_csvd_rank(T(X0), T(V0), n_min, n_max, tol)
+    ctx.sync_status()
+    s = np.linalg.svd((X0 + 1j * V0).T, compute_uv=False)
+    e = s ** 2
+    tail = 1.0 - np.cumsum(e) / e.sum()
+    want = next((k + 1 for k in range(n_min - 1, n_max) if tail[k] < tol), n_max)
+    while s[want - 1] < 1e-6 * s[0]:
+        want -= 1
+    assert n == want
+    Qf, Zf, _ = ctx.init_csvd(T(X0), T(V0), n)
+    assert torch.equal(Q, Qf) and torch.equal(Z, Zf)

@@ -1,6 +1,7 @@
 """Quiet-start loader, checkpoint image and the serving loop on the GPU.
 
-- vp_load_quiet against the FP64 host loader of the same inverse CDFs.
+- vp_load_particles (quiet start and Philox-seeded) against the FP64 host
+  loader of the same uniforms and inverse CDFs.
 - vp_state_export / vp_state_import: a run split at a checkpoint continues
   bit for bit.
 - vp_serve_*: a served query matches the FP64 oracle pipeline (quiet start,
@@ -48,11 +49,16 @@ def eta_rows(family: int, p: int) -> np.ndarray:
 
 @pytest.mark.parametrize("family", [0, 1, 2])
 @pytest.mark.parametrize("N", [1, 3001, 65_537])
-def test_load_quiet_parity(ctx, family, N):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_load_particles_parity(ctx, family, N, mode):
     p = 5
     rows, recs = eta_rows(family, p)
-    X, V = ctx.load_quiet(family, N, torch.tensor(rows, device="cuda:0"))
-    Xo, Vo = W.load_batch(FAM[family], recs, N, quiet=True)
+    seed = W.BASE_SEED + 77
+    X, V = ctx.load_particles(family, N, torch.tensor(rows, device="cuda:0"), mode=mode, seed=seed)
+    if mode == 0:
+        Xo, Vo = W.load_batch(FAM[family], recs, N, quiet=True)
+    else:
+        Xo, Vo = W.load_batch(FAM[family], recs, N, quiet=False, seed=seed, rng="philox")
     # both sides solve the same monotone equations to ~1e-14 relative
     assert np.max(np.abs(X.cpu().numpy() - Xo)) < 1e-11
     assert np.max(np.abs(V.cpu().numpy() - Vo)) < 1e-11
@@ -103,15 +109,22 @@ def server():
     s.close()
 
 
-def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps):
+def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps, loading=0, seed=0):
     """The served pipeline on the oracle: quiet start, complex SVD start with
-    n = the largest k <= n_max with sigma_k >= rank_tol sigma_1, then warm-
-    started PRK2 steps; returns n, the (E, H) trace of the states entering
-    each step and the final Z."""
+    n = the smallest k <= n_max whose relative tail energy is below rank_tol,
+    then warm-started PRK2 steps; returns n, the (E, H) trace of the states
+    entering each step and the final Z."""
     fam = FAM[family]
-    X0, V0 = W.load_batch(fam, recs, N, quiet=True)
+    if loading == 0:
+        X0, V0 = W.load_batch(fam, recs, N, quiet=True)
+    else:
+        X0, V0 = W.load_batch(fam, recs, N, quiet=False, seed=seed, rng="philox")
     U, Z, sig = csvd.csvd_init(X0, V0, n_max)
-    n = int(np.sum(sig[:n_max] >= rank_tol * sig[0]))
+    e = sig ** 2
+    tail = 1.0 - np.cumsum(e) / e.sum()
+    n = next((k + 1 for k in range(n_max) if tail[k] < rank_tol), n_max)
+    while sig[n - 1] < 1e-6 * sig[0]:
+        n -= 1
     if n < n_max:
         U, Z, sig = csvd.csvd_init(X0, V0, n)
     g = pic.make_grid(N, Nx, fam.L)
@@ -121,14 +134,17 @@ def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps):
     return n, entering, Z
 
 
-@pytest.mark.parametrize("family", [0, 1, 2])
-def test_serve_matches_oracle(server, family):
-    N, p, Nx, n_max, tol_rank, dt, nsteps = 3001, 6, 64, 3, 1e-6, 0.05, 5
+@pytest.mark.parametrize("family,loading", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1)])
+def test_serve_matches_oracle(server, family, loading):
+    N, p, Nx, n_max, tol_rank, dt, nsteps = 3001, 6, 64, 3, 1e-7, 0.05, 5
     rows, recs = eta_rows(family, p)
-    t = server.submit(family, rows, N, Nx, n_max, dt, nsteps, arith=0, rank_tol=tol_rank)
+    seed = W.BASE_SEED + 9
+    t = server.submit(family, rows, N, Nx, n_max, dt, nsteps, arith=0, rank_tol=tol_rank,
+                      loading=loading, seed=seed)
     r, tr, zeta = server.wait(t)
     assert r.status == 0 and r.steps_done == nsteps
-    n, tr_o, Z_o = oracle_query(family, rows, recs, N, Nx, n_max, tol_rank, dt, nsteps)
+    n, tr_o, Z_o = oracle_query(family, rows, recs, N, Nx, n_max, tol_rank, dt, nsteps,
+                                loading, seed)
     assert r.n == n
     # loader values agree to ~1e-14, not bitwise; the rest is the FP64 path
     assert rel(tr, tr_o) < 1e-9
@@ -140,7 +156,7 @@ def test_serve_alone_equals_mix(server):
     """The same query, alone and among three others running at the same time,
     gives bit-identical traces and coefficients (deterministic kernels,
     per-query context and stream)."""
-    base = dict(N=20_000, Nx=128, n_max=5, dt=0.05, nsteps=40, rank_tol=1e-6)
+    base = dict(N=20_000, Nx=128, n_max=5, dt=0.05, nsteps=40, rank_tol=1e-12)
     rowsA, _ = eta_rows(1, 16)
     for arith in (0, 1):
         ta = server.submit(1, rowsA, arith=arith, **base)

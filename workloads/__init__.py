@@ -47,6 +47,50 @@ def hammersley(N: int) -> tuple[np.ndarray, np.ndarray]:
 
 
 # --------------------------------------------------------------------------
+# counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+# "Parallel random numbers: as easy as 1, 2, 3", SC 2011)
+# --------------------------------------------------------------------------
+_PHILOX_M = (np.uint64(0xD2511F53), np.uint64(0xCD9E8D57))
+_PHILOX_W = (np.uint64(0x9E3779B9), np.uint64(0xBB67AE85))
+_U32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32(ctr, key, rounds: int = 10):
+    """Philox4x32 block: ctr = 4 arrays, key = 2 arrays of 32-bit words (held
+    in uint64); returns the 4 output words.  Each round multiplies words 0 and
+    2 by the two round constants, mixes the high halves with words 1, 3 and the
+    key, and bumps the key by the Weyl constants."""
+    c = [np.asarray(x, dtype=np.uint64) & _U32 for x in ctr]
+    k0 = np.asarray(key[0], dtype=np.uint64) & _U32
+    k1 = np.asarray(key[1], dtype=np.uint64) & _U32
+    for _ in range(rounds):
+        p0 = _PHILOX_M[0] * c[0]
+        p1 = _PHILOX_M[1] * c[2]
+        c = [((p1 >> np.uint64(32)) ^ c[1] ^ k0) & _U32, p1 & _U32,
+             ((p0 >> np.uint64(32)) ^ c[3] ^ k1) & _U32, p0 & _U32]
+        k0 = (k0 + _PHILOX_W[0]) & _U32
+        k1 = (k1 + _PHILOX_W[1]) & _U32
+    return c
+
+
+def _u53(a, b):
+    """Double in [0, 1) from the top 27 bits of a and 26 bits of b."""
+    return ((a >> np.uint64(5)).astype(np.float64) * 67108864.0
+            + (b >> np.uint64(6)).astype(np.float64)) * (1.0 / 9007199254740992.0)
+
+
+def philox_uniforms(N: int, sample: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """(u_x, u_v) of particles l = 0..N-1 of one sample: one Philox4x32-10 block
+    per particle with counter (l mod 2^32, l div 2^32, sample, 0) and key
+    (seed mod 2^32, seed div 2^32); u_x from words 0-1, u_v from words 2-3."""
+    l = np.arange(N, dtype=np.uint64)
+    z = np.zeros(N, dtype=np.uint64)
+    w = philox4x32([l & _U32, l >> np.uint64(32), z + np.uint64(sample), z],
+                   [np.uint64(seed) & _U32, np.uint64(seed) >> np.uint64(32)])
+    return _u53(w[0], w[1]), _u53(w[2], w[3])
+
+
+# --------------------------------------------------------------------------
 # inverse CDF sampling (vectorised safeguarded Newton)
 # --------------------------------------------------------------------------
 def _invert_monotone(cdf: Callable, pdf: Callable, u: np.ndarray, lo: float, hi: float,
@@ -146,32 +190,41 @@ FAMILIES = {f.name: f for f in (LANDAU, TWO_STREAM, BUMP_ON_TAIL)}
 
 
 def load_particles(family: Family, eta: dict, N: int, quiet: bool = True,
-                   seed: int = BASE_SEED) -> tuple[np.ndarray, np.ndarray]:
+                   seed: int = BASE_SEED, rng: str = "pcg64",
+                   sample: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """Positions and velocities (each length N, float64) of one sample.
 
     quiet=True: quiet start on the Hammersley set, x from the base-2 radical
-    inverse of l and v from (l + 1/2)/N.  quiet=False: seeded uniform numbers
-    (numpy PCG64 stream ``seed``).
+    inverse of l and v from (l + 1/2)/N.  quiet=False: seeded uniform numbers,
+    rng="pcg64" (numpy PCG64 stream ``seed``) or rng="philox" (Philox4x32-10
+    keyed by ``seed``, counter = (particle, sample); the CUDA loader draws the
+    same numbers).
     """
     alpha, w, m, s = family.params(eta)
     if quiet:
         uv, ux = hammersley(N)
+    elif rng == "philox":
+        ux, uv = philox_uniforms(N, sample, seed)
     else:
-        rng = np.random.Generator(np.random.PCG64(seed))
-        ux = rng.random(N)
-        uv = rng.random(N)
+        gen = np.random.Generator(np.random.PCG64(seed))
+        ux = gen.random(N)
+        uv = gen.random(N)
     x = sample_positions(ux, alpha, family.k)
     v = sample_velocities(uv, w, m, s)
     return x, v
 
 
 def load_batch(family: Family, etas: list[dict], N: int, quiet: bool = True,
-               seed: int = BASE_SEED) -> tuple[np.ndarray, np.ndarray]:
-    """X, V of shape (p, N): sample i uses parameters etas[i] and seed+i."""
+               seed: int = BASE_SEED, rng: str = "pcg64") -> tuple[np.ndarray, np.ndarray]:
+    """X, V of shape (p, N): sample i uses parameters etas[i] and seed+i
+    (rng="pcg64"), or key seed and counter sample i (rng="philox")."""
     X = np.empty((len(etas), N))
     V = np.empty((len(etas), N))
     for i, eta in enumerate(etas):
-        X[i], V[i] = load_particles(family, eta, N, quiet=quiet, seed=seed + i)
+        if rng == "philox":
+            X[i], V[i] = load_particles(family, eta, N, quiet=quiet, seed=seed, rng=rng, sample=i)
+        else:
+            X[i], V[i] = load_particles(family, eta, N, quiet=quiet, seed=seed + i)
     return X, V
 
 
