@@ -371,6 +371,54 @@ vp_status vp_server_stats(vp_server* srv, int64_t* submitted, int64_t* completed
 /* Drop waiting queries, cancel running ones, join every thread, free. */
 vp_status vp_server_destroy(vp_server* srv);
 
+/* --------------------------------------------------------------- batched */
+/* Many independent reduced models advanced together (each its own grid, N,
+ * n, p, dt and state; Sec. 5 steps).  The three phases of a step (field,
+ * energies and basis stage with the first fixed-point rounds; further
+ * rounds; Z update, tangent velocity and Cayley retraction) are captured
+ * once for all instances into three CUDA graphs whose instances are parallel
+ * branches.  A step launches the first graph, checks every instance's
+ * convergence with one small kernel and one synchronisation of `stream`,
+ * launches the rounds graph until all have converged (converged instances
+ * return at once), then the last graph.  Per instance the kernels and their
+ * order are those of vp_basis_update with arith 1 or 2 and a warm-started
+ * fixed point, so each instance's state equals (bit for bit) that of its own
+ * vp_basis_update call with kstate.  The paper has no batched form. */
+typedef struct vp_batch vp_batch;
+
+typedef struct vp_batch_item {
+  vp_grid grid;
+  int64_t N;
+  int32_t n, p;
+  double dt;
+  double* Q_dev;       /* N x 2n, advanced in place */
+  double* Z_dev;       /* 2n x p, advanced in place */
+  double* kstate_dev;  /* 2n x p warm start (nullable: internal, zero at creation) */
+  double* trace_dev;   /* nullable: trace_capacity x p x 2, E and H entering each step */
+  int32_t trace_capacity;
+  int32_t* iters_dev;  /* nullable: trace_capacity fixed-point iteration counts */
+} vp_batch_item;
+
+/* opts: arith 1 or 2 (others as vp_basis_update; reortho honoured).
+ * rounds_first / rounds_more: fixed-point rounds in the first and in the
+ * repeated graph.  scratch_per_instance: workspace budget of each instance's
+ * context (0: 4 GiB).  The items' buffers must stay valid until destroy.
+ * Synchronises the device. */
+vp_status vp_batch_create(vp_batch** out, int device, const vp_batch_item* items, int32_t count,
+                          const vp_step_opts* opts, int32_t rounds_first, int32_t rounds_more,
+                          size_t scratch_per_instance);
+/* nsteps steps of every instance on `stream` (one synchronisation per
+ * convergence check; returns after the last step has finished).  The first
+ * instance error found is returned (vp_batch_last_error names the instance). */
+vp_status vp_batch_step(vp_batch* b, int32_t nsteps, void* stream);
+/* Steps done, kernel launches made so far, kernel nodes of the three graphs. */
+vp_status vp_batch_info(const vp_batch* b, int64_t* steps_done, int64_t* launches,
+                        int64_t* graph_nodes);
+/* Message of the last error of b; b = NULL: of the last failed vp_batch_create
+ * on the calling thread. */
+const char* vp_batch_last_error(const vp_batch* b);
+vp_status vp_batch_destroy(vp_batch* b);
+
 /* ------------------------------------------------------------ profiling */
 /* Kernels of the library, for launch counts and event timing. */
 typedef enum vp_kernel {

@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     load_library,
     make_grid,
     Server,
+    Batch,
     Query,
     Result,
     deposit_cic_noalloc,

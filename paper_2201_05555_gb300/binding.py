@@ -90,6 +90,12 @@ _SIGS = [
     ("vp_server_stats", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32),
                                C.POINTER(_I32), C.POINTER(_SZ)]),
     ("vp_server_destroy", _I32, [_P]),
+    ("vp_batch_create", _I32, [C.POINTER(_P), C.c_int, _P, _I32, C.POINTER(StepOpts), _I32, _I32,
+                               _SZ]),
+    ("vp_batch_step", _I32, [_P, _I32, _P]),
+    ("vp_batch_info", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
+    ("vp_batch_last_error", C.c_char_p, [_P]),
+    ("vp_batch_destroy", _I32, [_P]),
 ]
 
 # vp_kernel ids (include/vp.h)
@@ -498,6 +504,71 @@ class Server:
             self.lib.vp_server_destroy(self.h)
             self.h = None
             self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batched
+class BatchItem(C.Structure):
+    """vp_batch_item (include/vp.h)."""
+    _fields_ = [("grid", Grid), ("N", _I64), ("n", _I32), ("p", _I32), ("dt", _D),
+                ("Q_dev", _P), ("Z_dev", _P), ("kstate_dev", _P), ("trace_dev", _P),
+                ("trace_capacity", _I32), ("iters_dev", _P)]
+
+
+class Batch:
+    """vp_batch: many reduced models stepped together by CUDA graphs.
+
+    instances: list of dicts with grid, Q (N x 2n), Z (2n x p), dt and
+    optionally kstate, trace (cap x p x 2), iters (cap, int32) torch CUDA
+    tensors; the tensors are advanced in place."""
+
+    def __init__(self, instances, arith: int = 2, rounds_first: int = 8, rounds_more: int = 2,
+                 tol: float = 1e-9, maxit: int = 100, reortho: bool | None = None,
+                 scratch_per_instance: int = 0, device: int = 0):
+        self.lib = load_library()
+        self._keep = instances
+        arr = (BatchItem * len(instances))()
+        for i, d in enumerate(instances):
+            Q, Z = d["Q"], d["Z"]
+            N, n2 = Q.shape
+            tr, it = d.get("trace"), d.get("iters")
+            arr[i] = BatchItem(d["grid"], N, n2 // 2, Z.shape[1], d["dt"], _ptr(Q, name="Q"),
+                               _ptr(Z, name="Z"), _ptr(d.get("kstate"), name="kstate"),
+                               _ptr(tr, name="trace"), tr.shape[0] if tr is not None else 0,
+                               _ptr(it, torch.int32, "iters"))
+        self._arr = arr
+        ro = (arith == 2) if reortho is None else reortho
+        opts = StepOpts(tol, maxit, 0, 1e-3, 0.5, arith, int(ro))
+        h = _P()
+        s = self.lib.vp_batch_create(C.byref(h), device, C.cast(arr, _P), len(instances),
+                                     C.byref(opts), rounds_first, rounds_more,
+                                     scratch_per_instance)
+        if s != 0:
+            raise VPError(s, "vp_batch_create: " + self.lib.vp_batch_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def step(self, nsteps: int = 1):
+        st = C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        s = self.lib.vp_batch_step(self.h, nsteps, st)
+        if s != 0:
+            raise VPError(s, self.lib.vp_batch_last_error(self.h).decode())
+
+    def info(self) -> dict:
+        sd, la = _I64(0), _I64(0)
+        nodes = (_I64 * 3)()
+        self.lib.vp_batch_info(self.h, C.byref(sd), C.byref(la), nodes)
+        return {"steps_done": sd.value, "launches": la.value, "graph_kernels": list(nodes)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vp_batch_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

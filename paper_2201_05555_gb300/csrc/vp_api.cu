@@ -374,61 +374,142 @@ struct RedDF {
 };
 }  // namespace
 
+namespace {
+struct DFStep {
+  vp_ctx* ctx;
+  Red& R;
+  double* Q;
+  double* Z;
+  double dt;
+  vp_step_opts o;
+  double* kstate;
+  cudaStream_t st;
+  const void* Qm = nullptr;  // rows the fixed point evaluates at (Q_half, or Q0 when frozen)
+  DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt, double* ks,
+         cudaStream_t s);
+  vp_status pre(double* trace_step);
+  vp_status rounds(int count);
+  vp_status post();
+};
+}  // namespace
+
+// One step of the FP32-based path in three phases, so that the host-steered
+// loop below and the batched engine (batch.cu, CUDA graphs) issue the same
+// kernel sequence: pre (field at the entering state, energies, basis stage,
+// fixed-point set-up), rounds (fixed-point iterations; after convergence the
+// kernels see the done flag and return at once), post (Z update, tangent
+// velocity, Cayley retraction, re-orthonormalisation).
+DFStep::DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt,
+               double* ks, cudaStream_t s)
+    : ctx(c), R(r), Q(q), Z(z), dt(d), o(opt), kstate(ks), st(s) {}
+
+vp_status DFStep::pre(double* trace_step) {
+  RedWS& w = R.w;
+  const int n = R.n, p = R.p;
+  const int64_t N = R.N;
+  RedDF D{R, ctx, st, N, n, p, o.arith};
+  RedDF DD{R, ctx, st, N, n, p, 1};  // double-float diagnostics
+  void *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2];
+  const int64_t zsz = (int64_t)2 * n * p;
+  if (trace_step && o.arith == 2) {  // FP64-accurate diagnostic in the precision form
+    DD.split(Q, w.Q2b);
+    DD.field(w.Q2b, Z, nullptr);
+    DD.gv(w.Q2b, w.GVraw);
+    VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace_step, trace_step + 1, 2, nullptr,
+                                 nullptr, ctx->d_status, st));
+  }
+  D.split(Q, Q0);
+  D.field(Q0, Z, nullptr);
+  if (trace_step && o.arith != 2) {
+    D.gv(Q0, w.GVraw);
+    VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace_step, trace_step + 1, 2, nullptr,
+                                 nullptr, ctx->d_status, st));
+  }
+  Qm = Q0;
+  if (!o.freeze_basis) {
+    D.basis_velocity(Q0, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
+    D.cayley(Q0, xih, nullptr, Qh);             // Q_half = R_Q0(xi_half)
+    Qm = Qh;
+  }
+  D.gv(Qm, w.GVraw);
+  VP_CUDA(cudaMemcpyAsync(w.Z0, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+  if (kstate) {
+    VP_CUDA(cudaMemcpyAsync(w.k, kstate, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    VP_K(VP_K_AXPY, axpy(zsz, 0.5 * dt, w.k, w.Z0, w.Ze, st));
+  } else {
+    VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
+  }
+  VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+  VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
+  return VP_OK;
+}
+
+vp_status DFStep::rounds(int count) {
+  RedWS& w = R.w;
+  const int n = R.n, p = R.p;
+  RedDF D{R, ctx, st, R.N, n, p, o.arith};
+  const int64_t zsz = (int64_t)2 * n * p;
+  for (int r = 0; r < count; ++r) {
+    D.field(Qm, w.Ze, w.flags);
+    D.project(Qm, w.flags);
+    VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
+    VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
+                                         o.stall_floor, o.stall_ratio, w.aux, w.flags, w.flags + 1,
+                                         ctx->d_status, st));
+  }
+  return VP_OK;
+}
+
+vp_status DFStep::post() {
+  RedWS& w = R.w;
+  const int n = R.n, p = R.p;
+  const int64_t N = R.N;
+  RedDF D{R, ctx, st, N, n, p, o.arith};
+  RedDF DD{R, ctx, st, N, n, p, 1};
+  void *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2], *Xp = w.frows[3],
+       *xi1 = w.frows[4];
+  const int64_t zsz = (int64_t)2 * n * p;
+  VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
+  if (kstate) VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+  if (!o.freeze_basis) {
+    D.field(Qh, w.Ze, nullptr);
+    D.basis_velocity(Qh, w.Ze, 1.0, M, Xp);  // X(Q_half, Z_mid)
+    D.grams({Q0, xih, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
+    const int nn = n * n;
+    VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
+                                                  ctx->d_status, st));
+    D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
+    D.cayley(Q0, xi1, Q, nullptr);             // Q_1 = R_Q0(xi_1) in FP64
+    if (o.reortho) {                           // Q <- Q (Q^H Q)^-1/2
+      DD.split(Q, w.Q2b);
+      DD.grams({w.Q2b}, {{0, 0}}, w.grams);
+      double2* Wj = w.tmp;
+      double2* Ws = w.tmp + nn;
+      double* lam = reinterpret_cast<double*>(w.tmp + 2 * nn);
+      VP_K(VP_K_INIT, init_launch_jacobi(n, w.grams, Wj, lam, Ws, ctx->d_status, st));
+      VP_K(VP_K_INIT, init_launch_inv_sqrt(n, Ws, lam, w.C, ctx->d_status, st));
+      DD.comb({w.Q2b}, w.C, Q, nullptr);
+    }
+  }
+  VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+  return VP_OK;
+}
+
 static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, double dt,
                                  int nsteps, const vp_step_opts& o, double* trace, int32_t* iters,
                                  double* kstate, cudaStream_t st) {
   RedWS& w = R.w;
-  const int64_t N = R.N;
-  const int n = R.n, p = R.p;
-  RedDF D{R, ctx, st, N, n, p, o.arith};
-  RedDF DD{R, ctx, st, N, n, p, 1};  // double-float diagnostics and re-orthonormalisation
-  void *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2], *Xp = w.frows[3],
-       *xi1 = w.frows[4];
-  const int64_t zsz = (int64_t)2 * n * p;
-  const int64_t tstride = (int64_t)p * 2;
+  const int64_t tstride = (int64_t)R.p * 2;
+  DFStep S(ctx, R, Q, Z, dt, o, kstate, st);
   int round = 4;
   for (int step = 0; step < nsteps; ++step) {
-    if (trace && o.arith == 2) {  // FP64-accurate diagnostic in the precision form
-      DD.split(Q, w.Q2b);
-      DD.field(w.Q2b, Z, nullptr);
-      DD.gv(w.Q2b, w.GVraw);
-      VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride,
-                                   trace + step * tstride + 1, 2, nullptr, nullptr, ctx->d_status, st));
-    }
-    D.split(Q, Q0);
-    D.field(Q0, Z, nullptr);
-    if (trace && o.arith != 2) {
-      D.gv(Q0, w.GVraw);
-      VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace + step * tstride,
-                                   trace + step * tstride + 1, 2, nullptr, nullptr, ctx->d_status, st));
-    }
-    const void* Qm = Q0;
-    if (!o.freeze_basis) {
-      D.basis_velocity(Q0, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
-      D.cayley(Q0, xih, nullptr, Qh);             // Q_half = R_Q0(xi_half)
-      Qm = Qh;
-    }
-    D.gv(Qm, w.GVraw);
-    VP_CUDA(cudaMemcpyAsync(w.Z0, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-    if (kstate) {
-      VP_CUDA(cudaMemcpyAsync(w.k, kstate, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-      VP_K(VP_K_AXPY, axpy(zsz, 0.5 * dt, w.k, w.Z0, w.Ze, st));
-    } else {
-      VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-      VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
-    }
-    VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
-    VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
+    VP_TRY(S.pre(trace ? trace + step * tstride : nullptr));
     int done_h = 0, total = 0;
     while (!done_h) {
-      for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
-        D.field(Qm, w.Ze, w.flags);
-        D.project(Qm, w.flags);
-        VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
-        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol,
-                                             o.maxit, o.stall_floor, o.stall_ratio, w.aux, w.flags,
-                                             w.flags + 1, ctx->d_status, st));
-      }
+      const int r = std::min(round, o.maxit - total);
+      VP_TRY(S.rounds(r));
+      total += r;
       VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       VP_CUDA(cudaStreamSynchronize(st));
       if (!ctx->pending.empty()) vp_prof_collect(ctx);
@@ -446,34 +527,51 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
         return vp_fail(ctx, VP_ENOCONV, "fixed point did not converge in %d iterations (step %d)",
                        o.maxit, step);
     }
-    VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
-    if (kstate)
-      VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
-    if (!o.freeze_basis) {
-      D.field(Qh, w.Ze, nullptr);
-      D.basis_velocity(Qh, w.Ze, 1.0, M, Xp);  // X(Q_half, Z_mid)
-      D.grams({Q0, xih, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
-      const int nn = n * n;
-      VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
-                                                    ctx->d_status, st));
-      D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
-      D.cayley(Q0, xi1, Q, nullptr);             // Q_1 = R_Q0(xi_1) in FP64
-      if (o.reortho) {                           // Q <- Q (Q^H Q)^-1/2
-        const int nn = n * n;
-        DD.split(Q, w.Q2b);
-        DD.grams({w.Q2b}, {{0, 0}}, w.grams);
-        double2* Wj = w.tmp;
-        double2* Ws = w.tmp + nn;
-        double* lam = reinterpret_cast<double*>(w.tmp + 2 * nn);
-        VP_K(VP_K_INIT, init_launch_jacobi(n, w.grams, Wj, lam, Ws, ctx->d_status, st));
-        VP_K(VP_K_INIT, init_launch_inv_sqrt(n, Ws, lam, w.C, ctx->d_status, st));
-        DD.comb({w.Q2b}, w.C, Q, nullptr);
-      }
-    }
-    VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
+    VP_TRY(S.post());
   }
   VP_LAUNCHED();
   return VP_OK;
+}
+
+// ------------------------------------------------ per-instance step objects
+// The batched engine (batch.cu) drives one of these per instance; each owns
+// its workspace (in its context) and issues the same kernels as
+// vp_basis_update with arith 1 or 2.
+struct InstanceStep {
+  Red R;
+  DFStep* S = nullptr;
+};
+
+vp_status step_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, double* Q,
+                     double* Z, double dt, const vp_step_opts* opts, double* kstate,
+                     cudaStream_t st, InstanceStep** out) {
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !out) return vp_fail(ctx, VP_EINVAL, "Q, Z and out are required");
+  if (!std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "dt not finite");
+  if (!opts || opts->arith < 1 || opts->arith > 2)
+    return vp_fail(ctx, VP_EINVAL, "batched steps need arith 1 or 2");
+  if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p exceeds 25600");
+  InstanceStep* is = new InstanceStep();
+  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, is->R, true);
+  if (s != VP_OK) {
+    delete is;
+    return s;
+  }
+  is->S = new DFStep(ctx, is->R, Q, Z, dt, *opts, kstate, st);
+  *out = is;
+  return VP_OK;
+}
+vp_status step_pre(InstanceStep* is, double* trace_step) { return is->S->pre(trace_step); }
+vp_status step_rounds(InstanceStep* is, int count) { return is->S->rounds(count); }
+vp_status step_post(InstanceStep* is) { return is->S->post(); }
+int* step_flags(InstanceStep* is) { return is->R.w.flags; }
+void step_free(InstanceStep* is) {
+  if (!is) return;
+  delete is->S;
+  delete is;
 }
 
 // ============================================================== profiling

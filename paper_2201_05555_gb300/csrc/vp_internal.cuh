@@ -57,6 +57,17 @@ vp_status vp_workspace(vp_ctx* ctx, size_t bytes, void** out);
 // Workspace bytes of one serving query (start + steps) and arena release.
 size_t vp_query_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int arith);
 void vp_workspace_release(vp_ctx* ctx);
+// One reduced step of one instance in phases (vp_api.cu), for the batched
+// engine: the kernel sequence of vp_basis_update with arith 1 or 2.
+struct InstanceStep;
+vp_status step_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, double* Q,
+                     double* Z, double dt, const vp_step_opts* opts, double* kstate,
+                     cudaStream_t st, InstanceStep** out);
+vp_status step_pre(InstanceStep* is, double* trace_step);
+vp_status step_rounds(InstanceStep* is, int count);
+vp_status step_post(InstanceStep* is);
+int* step_flags(InstanceStep* is);  // device [done, iterations]
+void step_free(InstanceStep* is);
 // Rank at t = 0 from the singular values (tail energy rule).
 int vp_choose_rank(const double* sig, int p, int n_min, int n_max, double tol);
 
