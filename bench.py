@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--serve-horizon", type=float, default=SERVE["T"])
     ap.add_argument("--serve-slots", type=int, default=SERVE["slots"])
     ap.add_argument("--serve-arith", type=int, default=SERVE["arith"])
+    ap.add_argument("--batch-size", type=int, default=512)
+    ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
+    ap.add_argument("--batch-steps", type=int, default=4)
+    ap.add_argument("--batch-rounds", type=int, default=8)
     return ap.parse_args()
 
 
@@ -286,6 +290,83 @@ def precision_measure(ctx, torch, dev, flush, steps: int = 4, warm: int = 1) -> 
             "speedup_vs_fp64_form": out[2]["value"] / out[1]["value"],
             "max_rel_err_E": errE, "max_rel_err_H": errH,
             "err_steps": warm + steps, "rank_2n": 2 * n}
+
+
+def batched_measure(args, ctx, torch, dev, flush) -> dict:
+    """Batched form: B instances, family uniform, N log-uniform, Nx in
+    {64, 128, 256}, 2n in {8, 10, ..., 80} clamped to 2n <= 2p, p uniform in
+    [1, 64], Philox-seeded loading, FP32 row work (arith 2) with FP64
+    re-orthonormalisation.  All instances advance together through the
+    captured graphs; the same instances stepped one after another through
+    vp_basis_update give the comparison."""
+    from paper_2201_05555_gb300 import Batch, make_grid
+    rng = np.random.Generator(np.random.PCG64(W.BASE_SEED + 7))
+    B, (lo, hi), S = args.batch_size, args.batch_n, args.batch_steps
+    fams = (W.LANDAU, W.TWO_STREAM, W.BUMP_ON_TAIL)
+    items, units = [], 0
+    for k in range(B):
+        f = int(rng.integers(0, 3))
+        N = int(round(10 ** rng.uniform(np.log10(lo), np.log10(hi))))
+        Nx = int(rng.choice([64, 128, 256]))
+        p = int(rng.integers(1, 65))
+        n = min(int(rng.integers(4, 41)), p)
+        if f == 0:
+            eta = np.stack([rng.uniform(0.01, 0.05, p), np.ones(p), np.zeros(p)], 1)
+        elif f == 1:
+            eta = np.stack([rng.uniform(2.0, 3.0, p), np.ones(p), np.full(p, 1e-3)], 1)
+        else:
+            eta = np.stack([rng.uniform(4.0, 5.0, p), np.full(p, 0.04), np.full(p, 0.5)], 1)
+        X, V = ctx.load_particles(f, N, torch.tensor(eta, device=dev), mode=1,
+                                  seed=W.BASE_SEED + 1000 + k)
+        Q, Z, _ = ctx.init_csvd(X, V, n)
+        del X, V
+        items.append(dict(grid=make_grid(N, Nx, fams[f].L), Q=Q, Z=Z,
+                          dt=0.05 if f == 1 else 0.1, kstate=torch.zeros_like(Z)))
+        units += N * p
+    ctx.sync_status()
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream(dev)
+    # one after another (each instance's own vp_basis_update)
+    seq = [dict(d, Q=d["Q"].clone(), Z=d["Z"].clone(), kstate=d["kstate"].clone()) for d in items]
+
+    def seq_step():
+        for d in seq:
+            ctx.basis_update(d["grid"], d["Q"], d["Z"], d["dt"], 1, trace=False, iters=False,
+                             arith=2, kstate=d["kstate"], reortho=True)
+
+    seq_step()  # warm-up (grows the workspace to the largest instance)
+    torch.cuda.synchronize()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record(stream)
+    for _ in range(S):
+        seq_step()
+    b_.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b_) / S
+    del seq
+    torch.cuda.empty_cache()
+    bt = Batch(items, arith=2, rounds_first=args.batch_rounds, rounds_more=2)
+    bt.step(1)  # warm-up
+    l0 = bt.info()["launches"]
+    flush.zero_()
+    a.record(stream)
+    bt.step(S)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    bat_ms = a.elapsed_time(b_) / S
+    info = bt.info()
+    bt.close()
+    return {"workload": (f"batched form: {B} instances, family uniform, N log-uniform "
+                         f"[{lo:.0e}, {hi:.0e}], Nx in {{64,128,256}}, 2n in [8, 80] clamped to "
+                         f"2n <= 2p, p uniform [1, 64], FP32 row work, Philox-seeded loading"),
+            "value": units / (bat_ms / 1e3), "unit": UNIT, "ms_per_step": bat_ms,
+            "steps": S, "instances": B, "particle_samples_per_step": units,
+            "sequential": {"value": units / (seq_ms / 1e3), "ms_per_step": seq_ms,
+                           "how": "same instances, one vp_basis_update call each per step"},
+            "speedup_vs_sequential": seq_ms / bat_ms,
+            "graph_kernels": info["graph_kernels"],
+            "kernel_launches_per_step": (info["launches"] - l0) / S}
 
 
 def served_measure(args, dev_index: int) -> dict:
@@ -518,6 +599,7 @@ def ours(args, rank, world):
     if not args.no_extras and world == 1:
         line["full_order"] = full_order_measure(ctx, torch, dev, flush)
         line["precision_form"] = precision_measure(ctx, torch, dev, flush)
+        line["batched"] = batched_measure(args, ctx, torch, dev, flush)
         line["served"] = served_measure(args, local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
