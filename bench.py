@@ -499,6 +499,8 @@ def ours(args, rank, world):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # launch shapes of the particle kernels chosen on this state (setup, not timed)
+    tuned = ctx.autotune(grid, Q, Z, arith=ARITH, reps=5) if ARITH else None
     kstate = torch.zeros_like(Z)  # warm start of the fixed point (previous step's k2)
 
     def step(Qt, Zt, trace=True, arith=ARITH):
@@ -595,6 +597,7 @@ def ours(args, rank, world):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + trh.numel() * 8},
             "gpu_launches": total_launches, "roofline": roof, "clocks": clocks,
+            "autotuned_blocks_per_sm": tuned,
             "fixed_point_iters": its}
     if not args.no_extras and world == 1:
         line["full_order"] = full_order_measure(ctx, torch, dev, flush)

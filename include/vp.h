@@ -371,6 +371,26 @@ vp_status vp_server_stats(vp_server* srv, int64_t* submitted, int64_t* completed
 /* Drop waiting queries, cancel running ones, join every thread, free. */
 vp_status vp_server_destroy(vp_server* srv);
 
+/* ---------------------------------------------------------------- tuning */
+/* Launch shape of the FP32-based particle kernels (arith 1 and 2): each
+ * knob sizes its kernel's grid for this many resident blocks per SM (1..32).
+ * Defaults {4, 4, 4, 8, 8} (measured on the two-stream workload).  The paper
+ * has no counterpart. */
+typedef enum vp_tune_knob {
+  VP_TUNE_DEPOSIT_LP = 0, VP_TUNE_PROJECT_LP, VP_TUNE_BASIS_M_LP, VP_TUNE_GRAM_LP,
+  VP_TUNE_AFFINE_LP, VP_TUNE_COUNT
+} vp_tune_knob;
+vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm);
+vp_status vp_tune_get(vp_ctx* ctx, int32_t knob, int32_t* blocks_per_sm);
+/* Autotuner: on the caller's state (Q N x 2n, Z 2n x p; read only) times
+ * every knob's kernel at 1, 2, 3, 4, 6 and 8 blocks per SM (`reps` launches
+ * each, CUDA events on `stream`), keeps the fastest in the context and
+ * writes the choices to chosen[VP_TUNE_COUNT] (nullable).  Results of later
+ * calls change only by the order of partial sums.  Synchronises `stream`. */
+vp_status vp_autotune(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                      const double* Q_dev, const double* Z_dev, int32_t arith, int32_t reps,
+                      int32_t* chosen, void* stream);
+
 /* --------------------------------------------------------------- batched */
 /* Many independent reduced models advanced together (each its own grid, N,
  * n, p, dt and state; Sec. 5 steps).  The three phases of a step (field,

@@ -90,6 +90,10 @@ _SIGS = [
     ("vp_server_stats", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32),
                                C.POINTER(_I32), C.POINTER(_SZ)]),
     ("vp_server_destroy", _I32, [_P]),
+    ("vp_tune_set", _I32, [_P, _I32, _I32]),
+    ("vp_tune_get", _I32, [_P, _I32, C.POINTER(_I32)]),
+    ("vp_autotune", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I32, _I32,
+                           C.POINTER(_I32), _P]),
     ("vp_batch_create", _I32, [C.POINTER(_P), C.c_int, _P, _I32, C.POINTER(StepOpts), _I32, _I32,
                                _SZ]),
     ("vp_batch_step", _I32, [_P, _I32, _P]),
@@ -356,6 +360,31 @@ class Context:
                                                     _ptr(c, name="c"), _ptr(phi, name="phi"),
                                                     _ptr(g), self._stream()), "deim_gather_project")
         return g
+
+    TUNE_KNOBS = ("deposit", "project", "basis_M", "gram", "affine")
+
+    def tune_set(self, **blocks_per_sm):
+        for name, v in blocks_per_sm.items():
+            self._check(self.lib.vp_tune_set(self.h, self.TUNE_KNOBS.index(name), int(v)),
+                        "tune_set")
+
+    def tune_get(self) -> dict:
+        out = {}
+        for i, name in enumerate(self.TUNE_KNOBS):
+            v = _I32(0)
+            self._check(self.lib.vp_tune_get(self.h, i, C.byref(v)), "tune_get")
+            out[name] = v.value
+        return out
+
+    def autotune(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, arith: int = 1,
+                 reps: int = 5) -> dict:
+        """Pick the grid size of each FP32-based particle kernel on this state."""
+        N, n2 = Q.shape
+        ch = (_I32 * 5)()
+        self._check(self.lib.vp_autotune(self.h, C.byref(grid), N, n2 // 2, Z.shape[1],
+                                         _ptr(Q, name="Q"), _ptr(Z, name="Z"), arith, reps, ch,
+                                         self._stream()), "autotune")
+        return dict(zip(self.TUNE_KNOBS, list(ch)))
 
     def load_particles(self, family: int, N: int, eta: torch.Tensor, mode: int = 0,
                        seed: int = 0):

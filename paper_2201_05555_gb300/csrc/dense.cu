@@ -101,6 +101,60 @@ __device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m,
   return true;
 }
 
+// Solve in place M = [A | B] (n x w, leading dimension ld; A is n x n) by
+// Gauss-Jordan elimination without pivoting, for the systems of this file:
+// Hermitian positive definite (zeta zeta^H) or close to the identity
+// (Cayley and tangent factors with small steps), where elimination in the
+// natural order is stable.  Per pivot c: the scaled pivot row (columns > c)
+// goes to shared memory, then every row is updated from `src` into `dst`
+// (ping-pong with `work`, n x w), two barriers per pivot.  Only columns > c
+// are kept current, so on return the B part of M holds A^-1 B and the A part
+// is undefined.  Returns false (M undefined) when a pivot falls below 1e-14
+// times the largest initial diagonal entry or is not finite; callers then
+// rebuild M and use gj_solve.
+__device__ bool gj_np(double2* M, int ld, int n, int w, double2* work, double2* rowc) {
+  __shared__ int bad;
+  __shared__ double dscale;
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int r = 0; r < n; ++r) d = fmax(d, cabs2(M[r * ld + r]));
+    dscale = d;
+    bad = !(d > 0.0) || !isfinite(d);
+  }
+  __syncthreads();
+  double2* src = M;
+  double2* dst = work;
+  int lds = ld, ldd = w;
+  for (int c = 0; c < n; ++c) {
+    const double2 pv = src[c * lds + c];
+    const double a2 = cabs2(pv);
+    if (threadIdx.x == 0 && (!(a2 > 1e-28 * dscale) || !isfinite(a2))) bad = 1;
+    const double2 inv = cscale(cconj(pv), 1.0 / a2);
+    const int w1 = w - c - 1;  // columns c+1 .. w-1
+    for (int j = threadIdx.x; j < w1; j += blockDim.x) rowc[j] = cmul(src[c * lds + c + 1 + j], inv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * w1; e += blockDim.x) {
+      const int r = e / w1, jj = e - r * w1, j = c + 1 + jj;
+      dst[r * ldd + j] = (r == c) ? rowc[jj] : csub(src[r * lds + j], cmul(src[r * lds + c], rowc[jj]));
+    }
+    __syncthreads();
+    double2* t = src;
+    src = dst;
+    dst = t;
+    const int tl = lds;
+    lds = ldd;
+    ldd = tl;
+  }
+  if (src != M) {  // result of an odd number of pivots sits in work: copy the B part
+    for (int e = threadIdx.x; e < n * (w - n); e += blockDim.x) {
+      const int r = e / (w - n), j = n + e - r * (w - n);
+      M[r * ld + j] = src[r * lds + j];
+    }
+    __syncthreads();
+  }
+  return !bad;
+}
+
 // Hermitian H = zeta zeta^H (n x n) from Z = [a; b] (2n x p).
 __device__ void zeta_gram(double2* H, const double* Z, int n, int p) {
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -126,20 +180,29 @@ __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ Q
   extern __shared__ double2 aug[];
   const int ld = 3 * n;
   double2* H = in_smem ? aug + n * ld : tmp;  // n x n
+  double2* work = aug + n * ld + n * n;        // n x 3n (in_smem)
+  __shared__ double2 rowc[128];
   zeta_gram(H, Z, n, p);
-  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
-    int r = e / ld, c = e - r * ld;
-    double2 v;
-    if (c < n) v = H[r * n + c];
-    else if (c < 2 * n) v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
-    else v = cconj(QhM[(c - 2 * n) * n + r]);  // (Q^H M)^H
-    aug[e] = v;
-  }
-  __syncthreads();
+  auto build = [&]() {
+    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+      int r = e / ld, c = e - r * ld;
+      double2 v;
+      if (c < n) v = H[r * n + c];
+      else if (c < 2 * n) v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
+      else v = cconj(QhM[(c - 2 * n) * n + r]);  // (Q^H M)^H
+      aug[e] = v;
+    }
+    __syncthreads();
+  };
+  build();
   __shared__ double2 col[64];
-  if (!gj_solve(aug, ld, aug + n, ld, n, 2 * n, col)) {
-    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
-    return;
+  bool ok = in_smem && gj_np(aug, ld, n, ld, work, rowc);
+  if (!ok) {
+    build();
+    if (!gj_solve(aug, ld, aug + n, ld, n, 2 * n, col)) {
+      if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+      return;
+    }
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int r = e / n, c = e - r * n;
@@ -152,7 +215,7 @@ __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ Q
 
 void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
                         double2* C, double2* tmp, int* status, cudaStream_t st) {
-  size_t smem = sizeof(double2) * n * 4 * n;
+  size_t smem = sizeof(double2) * n * 7 * n;
   k_small_basis_coeffs<<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status, 1);
 }
 
@@ -165,7 +228,7 @@ void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, doubl
 // Output C (2 x n x n): coefficient of Q0, coefficient of xi.
 __global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const double2* __restrict__ Pg,
                                const double2* __restrict__ XXg, double2* C, double2* tmp,
-                               int* status, int in_smem) {
+                               int* status, int in_smem, int fast) {
   extern __shared__ double2 aug[];  // 2n x 3n, then (in_smem) G0, P, XX, T, QW, WW
   const int nn = n * n, ld = 3 * n;
   double2* sb = aug + 6 * nn;
@@ -192,26 +255,34 @@ __global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const dou
   cmm(WW, P, 1, P, 0, make_double2(-1.0, 0.0), 0.0, n);
   cmm(WW, P, 1, T, 0, make_double2(0.25, 0.0), 1.0, n);
   cadd_mat(WW, 1.0, WW, 1.0, XX, 0, 0.0, n);
-  for (int e = threadIdx.x; e < 2 * n * ld; e += blockDim.x) {
-    int r = e / ld, c = e - r * ld;
-    int rb = r >= n, cb = c / n, rr = r - rb * n, cc = c - cb * n;
-    double2 v;
-    double d = (rr == cc) ? 1.0 : 0.0;
-    if (!rb && cb == 0) v = make_double2(d - 0.5 * QW[rr * n + cc].x, -0.5 * QW[rr * n + cc].y);
-    else if (!rb && cb == 1) v = cscale(G0[rr * n + cc], 0.5);
-    else if (!rb && cb == 2) v = G0[rr * n + cc];
-    else if (rb && cb == 0) v = cscale(WW[rr * n + cc], -0.5);
-    else {  // W^H Q0 = (Q0^H W)^H
-      double2 wq = cconj(QW[cc * n + rr]);
-      v = (cb == 1) ? make_double2(d + 0.5 * wq.x, 0.5 * wq.y) : wq;
+  auto build = [&]() {
+    for (int e = threadIdx.x; e < 2 * n * ld; e += blockDim.x) {
+      int r = e / ld, c = e - r * ld;
+      int rb = r >= n, cb = c / n, rr = r - rb * n, cc = c - cb * n;
+      double2 v;
+      double d = (rr == cc) ? 1.0 : 0.0;
+      if (!rb && cb == 0) v = make_double2(d - 0.5 * QW[rr * n + cc].x, -0.5 * QW[rr * n + cc].y);
+      else if (!rb && cb == 1) v = cscale(G0[rr * n + cc], 0.5);
+      else if (!rb && cb == 2) v = G0[rr * n + cc];
+      else if (rb && cb == 0) v = cscale(WW[rr * n + cc], -0.5);
+      else {  // W^H Q0 = (Q0^H W)^H
+        double2 wq = cconj(QW[cc * n + rr]);
+        v = (cb == 1) ? make_double2(d + 0.5 * wq.x, 0.5 * wq.y) : wq;
+      }
+      aug[e] = v;
     }
-    aug[e] = v;
-  }
-  __syncthreads();
+    __syncthreads();
+  };
+  build();
   __shared__ double2 col[128];
-  if (!gj_solve(aug, ld, aug + 2 * n, ld, 2 * n, n, col)) {
-    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
-    return;
+  __shared__ double2 rowc[256];
+  bool ok = fast && gj_np(aug, ld, 2 * n, ld, aug + 12 * nn, rowc);
+  if (!ok) {
+    build();
+    if (!gj_solve(aug, ld, aug + 2 * n, ld, 2 * n, n, col)) {
+      if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+      return;
+    }
   }
   // copy Yt, Yb to global scratch (reuse T, QW)
   for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -230,8 +301,9 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
                          double2* tmp, int* status, cudaStream_t st) {
   size_t full = sizeof(double2) * 12 * n * n;
   int in_smem = full <= 200 * 1024;
-  size_t smem = in_smem ? full : sizeof(double2) * 6 * n * n;
-  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem);
+  int fast = in_smem && sizeof(double2) * 18 * n * n <= 200 * 1024;  // + work for gj_np
+  size_t smem = fast ? sizeof(double2) * 18 * n * n : in_smem ? full : sizeof(double2) * 6 * n * n;
+  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem, fast);
 }
 
 // ------------------------------------------------------- tangent velocity
@@ -247,7 +319,8 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 // (coefficients of Xp, xi, Q0).
 __global__ void k_small_tangent(int n, const double2* __restrict__ grams_g,
                                 const double2* __restrict__ G0g, const double2* __restrict__ Pg,
-                                double scale, double2* C, double2* tmp, int* status, int in_smem) {
+                                double scale, double2* C, double2* tmp, int* status, int in_smem,
+                                int fast) {
   extern __shared__ double2 aug[];  // n x 2n, then (in_smem) 7 inputs and 8 temporaries
   const int nn = n * n, ld = 2 * n;
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
@@ -271,18 +344,26 @@ __global__ void k_small_tangent(int n, const double2* __restrict__ grams_g,
                 *A5 = grams + 4 * nn;
   double2 *T1 = tb, *u1 = tb + nn, *u2 = tb + 2 * nn, *u3 = tb + 3 * nn, *W1 = tb + 4 * nn,
           *QU = tb + 5 * nn, *RU = tb + 6 * nn, *W2 = tb + 7 * nn;
-  for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
-    int r = e / ld, c = e - r * ld;
-    double2 v;
-    if (c < n) { v = A3[r * n + c]; if (r == c) v.x += 1.0; }
-    else v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
-    aug[e] = v;
-  }
-  __syncthreads();
+  auto build = [&]() {
+    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+      int r = e / ld, c = e - r * ld;
+      double2 v;
+      if (c < n) { v = A3[r * n + c]; if (r == c) v.x += 1.0; }
+      else v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
+      aug[e] = v;
+    }
+    __syncthreads();
+  };
+  build();
   __shared__ double2 col[64];
-  if (!gj_solve(aug, ld, aug + n, ld, n, n, col)) {
-    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
-    return;
+  __shared__ double2 rowc[128];
+  bool ok = fast && gj_np(aug, ld, n, ld, aug + 17 * nn, rowc);
+  if (!ok) {
+    build();
+    if (!gj_solve(aug, ld, aug + n, ld, n, n, col)) {
+      if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+      return;
+    }
   }
   for (int e = threadIdx.x; e < nn; e += blockDim.x) {
     int r = e / n, c = e - r * n;
@@ -320,8 +401,9 @@ void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const 
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st) {
   size_t full = sizeof(double2) * 17 * n * n;
   int in_smem = full <= 200 * 1024;
-  size_t smem = in_smem ? full : sizeof(double2) * 2 * n * n;
-  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem);
+  int fast = in_smem && sizeof(double2) * 19 * n * n <= 200 * 1024;  // + work for gj_np
+  size_t smem = fast ? sizeof(double2) * 19 * n * n : in_smem ? full : sizeof(double2) * 2 * n * n;
+  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem, fast);
 }
 
 // ------------------------------------------------- fixed-point iteration
@@ -339,70 +421,160 @@ __device__ double block_sum2(double v, double* red) {
   return s;
 }
 
+// Fixed-point update of the coefficient stage, spread over blocks of
+// sample columns: block b owns columns [b CW, (b+1) CW) and writes
+// k_new = J (gX + G_V Ze) and Ze = Z0 + dt/2 k_new for them (a column depends
+// only on its own column of Ze).  Each block leaves its sums |k_new - k|^2,
+// |k_new|^2 in `partials`; the last block to finish (ticket counter) adds them
+// in block order (deterministic), counts the iteration and decides: converged
+// (relative update <= tol), stalled (see vp_step_opts), non-finite
+// (VP_ENUMERIC) or out of iterations (VP_ENOCONV).  Every later launch of the
+// step returns at once through `done`.
+#define CU_CW 8
 __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
                                const double* __restrict__ GVraw, const double* __restrict__ Z0,
                                double* k, double* Ze, double dt, double tol, int maxit,
                                double stall_floor, double stall_ratio, double* rstate, int* done,
-                               int* iters, int* status) {
+                               int* iters, int* ticket, double* partials, int* status) {
   if (*done) return;
   extern __shared__ double cu_sm[];
   __shared__ double red[32];
+  __shared__ int last;
   const int n2 = 2 * n;
-  const int64_t tot = (int64_t)n2 * p;
-  double* GV = cu_sm;             // n2 x n2, G_V = U_V^T U_V
-  double* Zs = cu_sm + n2 * n2;   // n2 x p, current evaluation point
+  const int i0 = blockIdx.x * CU_CW, cw = min(CU_CW, p - i0);
+  double* GV = cu_sm;            // n2 x n2, G_V = U_V^T U_V
+  double* Zs = cu_sm + n2 * n2;  // n2 x CU_CW, this block's columns of Ze
   for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
     int a = e / n2, b = e - a * n2;
     GV[e] = GVraw[vperm(a, n) * n2 + vperm(b, n)];
   }
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) Zs[e] = Ze[e];
+  for (int e = threadIdx.x; e < n2 * cw; e += blockDim.x) {
+    int r = e / cw, c = e - r * cw;
+    Zs[r * CU_CW + c] = Ze[(int64_t)r * p + i0 + c];
+  }
   __syncthreads();
   double d2 = 0.0, k2 = 0.0;
   // k_new[r] = g[n + r] (r < n), k_new[n + r] = -g[r], g = gX + G_V Ze
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    int r = (int)(e / p), i = (int)(e - (int64_t)r * p);
+  for (int e = threadIdx.x; e < n2 * cw; e += blockDim.x) {
+    int r = e / cw, c = e - r * cw;
+    const int64_t o = (int64_t)r * p + i0 + c;
     int gr = r < n ? n + r : r - n;
     double sgn = r < n ? 1.0 : -1.0;
-    double g = gX[(int64_t)gr * p + i];
-    for (int c = 0; c < n2; ++c) g = fma(GV[gr * n2 + c], Zs[(int64_t)c * p + i], g);
+    double g = gX[(int64_t)gr * p + i0 + c];
+    for (int m = 0; m < n2; ++m) g = fma(GV[gr * n2 + m], Zs[m * CU_CW + c], g);
     double kn = sgn * g;
-    double dk = kn - k[e];
+    double dk = kn - k[o];
     d2 = fma(dk, dk, d2);
     k2 = fma(kn, kn, k2);
-    k[e] = kn;
-    Ze[e] = fma(0.5 * dt, kn, Z0[e]);
+    k[o] = kn;
+    Ze[o] = fma(0.5 * dt, kn, Z0[o]);
   }
   double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red);
   if (threadIdx.x == 0) {
-    int it = *iters + 1;
-    *iters = it;
-    const double diff = sqrt(D2), nk = sqrt(K2);
-    bool conv = diff <= tol * nk;
-    const double r = nk > 0.0 ? diff / nk : 0.0;
-    // rstate: relative updates of the two previous iterations
-    const bool stalled =
-        it >= 3 && r <= stall_floor && r >= stall_ratio * fmin(rstate[0], rstate[1]);
-    rstate[1] = rstate[0];
-    rstate[0] = r;
-    if (!isfinite(D2) || !isfinite(K2)) {
-      vp_set_status(status, VP_ENUMERIC);
-      *done = 1;
-    } else if (conv || stalled) {
-      *done = 1;
-    } else if (it >= maxit) {
-      vp_set_status(status, VP_ENOCONV);
-      *done = 1;
-    }
+    partials[2 * blockIdx.x] = D2;
+    partials[2 * blockIdx.x + 1] = K2;
+    __threadfence();
+    last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  D2 = 0.0;
+  K2 = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    D2 += ((volatile double*)partials)[2 * b];
+    K2 += ((volatile double*)partials)[2 * b + 1];
+  }
+  *ticket = 0;
+  int it = *iters + 1;
+  *iters = it;
+  const double diff = sqrt(D2), nk = sqrt(K2);
+  bool conv = diff <= tol * nk;
+  const double r = nk > 0.0 ? diff / nk : 0.0;
+  // rstate: relative updates of the two previous iterations
+  const bool stalled =
+      it >= 3 && r <= stall_floor && r >= stall_ratio * fmin(rstate[0], rstate[1]);
+  rstate[1] = rstate[0];
+  rstate[0] = r;
+  if (!isfinite(D2) || !isfinite(K2)) {
+    vp_set_status(status, VP_ENUMERIC);
+    *done = 1;
+  } else if (conv || stalled) {
+    *done = 1;
+  } else if (it >= maxit) {
+    vp_set_status(status, VP_ENOCONV);
+    *done = 1;
   }
 }
 
+// flags: [0] done, [1] iterations, [2] ticket (zero between launches);
+// rstate: [0..1] previous relative updates, then 2 doubles per block.
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
                   double* Ze, double dt, double tol, int maxit, double stall_floor,
                   double stall_ratio, double* rstate, int* done, int* iters, int* status,
                   cudaStream_t st) {
-  size_t smem = sizeof(double) * (4 * n * n + 2 * (size_t)n * p);
-  k_coeff_update<<<1, 1024, smem, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
-                                        stall_ratio, rstate, done, iters, status);
+  const int nb = (p + CU_CW - 1) / CU_CW;
+  size_t smem = sizeof(double) * (4 * n * n + 2 * (size_t)n * CU_CW);
+  k_coeff_update<<<nb, 256, smem, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
+                                        stall_ratio, rstate, done, iters, done + 2, rstate + 2,
+                                        status);
+}
+
+// Loewdin factor G^{-1/2} of a Hermitian positive definite G close to I
+// (G = Q^H Q of a basis that left the manifold by rounding only), by the
+// coupled Newton-Schulz iteration Y <- Y T / 2, Zm <- T Zm / 2 with
+// T = 3 I - Zm Y, from Y = G, Zm = I (Higham, Functions of Matrices, 2008,
+// Sec. 6.3): Zm -> G^{-1/2} quadratically while |I - G| < 1.  Stops when
+// |Zm Y - I|_F <= 1e-15 sqrt(n) (two or three iterations at a deviation of
+// 1e-7).  |G - I|_F >= 0.9 sets VP_EDRIFT and returns C = I.
+__global__ void k_lowdin(int n, const double2* __restrict__ G, double2* __restrict__ C,
+                         int* status) {
+  extern __shared__ double2 lw[];
+  __shared__ double red[32];
+  __shared__ int stop;
+  const int nn = n * n;
+  double2 *Y = lw, *Zm = lw + nn, *T = lw + 2 * nn, *U = lw + 3 * nn;
+  double e2 = 0.0;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const bool d = (e / n) == (e % n);
+    Y[e] = G[e];
+    Zm[e] = make_double2(d ? 1.0 : 0.0, 0.0);
+    const double2 dv = make_double2(G[e].x - (d ? 1.0 : 0.0), G[e].y);
+    e2 += cabs2(dv);
+  }
+  const double dev = sqrt(block_sum2(e2, red));
+  if (!(dev < 0.9)) {
+    if (threadIdx.x == 0) vp_set_status(status, VP_EDRIFT);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) C[e] = Zm[e];
+    return;
+  }
+  const double2 one = make_double2(1.0, 0.0), half = make_double2(0.5, 0.0);
+  for (int it = 0; it < 12; ++it) {
+    cmm(T, Zm, 0, Y, 0, one, 0.0, n);  // T = Zm Y
+    double r2 = 0.0;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const bool d = (e / n) == (e % n);
+      r2 += cabs2(make_double2(T[e].x - (d ? 1.0 : 0.0), T[e].y));
+    }
+    const double res = sqrt(block_sum2(r2, red));
+    if (threadIdx.x == 0) stop = !(res > 1e-15 * sqrt((double)n));
+    __syncthreads();
+    if (stop) break;
+    cadd_mat(T, -1.0, T, 0.0, nullptr, 0, 3.0, n);  // T = 3 I - Zm Y
+    cmm(U, Y, 0, T, 0, half, 0.0, n);               // Y T / 2
+    double2* t = Y;
+    Y = U;
+    U = t;
+    cmm(U, T, 0, Zm, 0, half, 0.0, n);  // T Zm / 2
+    t = Zm;
+    Zm = U;
+    U = t;
+  }
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) C[e] = Zm[e];
+}
+
+void lowdin(int n, const double2* G, double2* C, int* status, cudaStream_t st) {
+  k_lowdin<<<1, 256, sizeof(double2) * 4 * n * n, st>>>(n, G, C, status);
 }
 
 // Z1 = Z0 + dt k
@@ -488,6 +660,7 @@ void dense_init() {
   cudaFuncSetAttribute(k_small_cayley, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_small_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_coeff_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_lowdin, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace vpk

@@ -196,7 +196,7 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
         int j1 = (j + 1 == Nx) ? 0 : j + 1;
         atomicAdd(mycnt + j, (unsigned long long)(one - w1));
         atomicAdd(mycnt + j1, (unsigned long long)w1);
-        if (jout) jout[(base + r) * p + c0 + ii] = (uint16_t)j;
+        if (jout) jout[jt_block(tile, blockIdx.y, gridDim.y, PC) + r * PC + ii] = (uint16_t)j;
       }
     }
   }
@@ -210,39 +210,73 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
 // ---------------------------------------------- projection g_X = U_X^T G
 // G_li = (q/m) F_i[j_li] with j from the deposit at the same (Q, zeta).
 // Thread t owns sample column c = t % PC and rows k = t / PC + a (256 / PC).
+// Full tiles of Q rows and of cell indices arrive by bulk copies into two
+// shared-memory stages: the copy of the block's next tile runs while the
+// current one is used.  A partial last tile is read with plain loads.
 template <class AR, int MAXACC>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
-             const typename AR::V* __restrict__ F2, const uint16_t* __restrict__ jin,
-             double* __restrict__ part, const int* skip) {
+             const typename AR::V* __restrict__ F2, const uint16_t* __restrict__ jt,
+             double* __restrict__ part, const int* skip, int* status) {
   using V = typename AR::V;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n2 = 2 * n, ldq = n2 + 1, Nx = g.Nx, ldG = PC + 1;
-  V* Qs = reinterpret_cast<V*>(smraw);
-  V* Fs = Qs + TILE_ROWS * ldq;  // PC x Nx
-  V* Gs = Fs + PC * Nx;          // TILE_ROWS x ldG
-  const int c0 = blockIdx.y * PC;
+  const int n2 = 2 * n, Nx = g.Nx, ldG = PC + 1;
+  const int nch = gridDim.y, chunk = blockIdx.y, c0 = chunk * PC;
+  const uint32_t qbytes = (uint32_t)(sizeof(V) * TILE_ROWS * n2);
+  const uint32_t jbytes = (uint32_t)(sizeof(uint16_t) * TILE_ROWS * PC);
+  const size_t qst = (qbytes + 15) & ~size_t(15), jst = (jbytes + 15) & ~size_t(15);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);  // 2 stages
+  V* Qs0 = reinterpret_cast<V*>(smraw + 16);
+  uint16_t* Js0 = reinterpret_cast<uint16_t*>(smraw + 16 + 2 * qst);
+  V* Fs = reinterpret_cast<V*>(smraw + 16 + 2 * qst + 2 * jst);  // PC x Nx
+  V* Gs = Fs + PC * Nx;                                           // TILE_ROWS x ldG
   const int t = threadIdx.x;
+  const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
   for (int e = t; e < PC * Nx; e += blockDim.x) {
     int c = e / Nx;
     Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : AR::zero();
   }
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: start the bulk copies of full tile `tl` into stage `st`
+  auto issue = [&](int64_t tl, int st) {
+    if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[st], qbytes + jbytes);
+    bulk_g2s(reinterpret_cast<unsigned char*>(Qs0) + st * qst, Q2 + tl * TILE_ROWS * n2, qbytes, &bar[st]);
+    bulk_g2s(reinterpret_cast<unsigned char*>(Js0) + st * jst, jt + jt_block(tl, chunk, nch, PC),
+             jbytes, &bar[st]);
+  };
   const int cc = t % PC, kk0 = t / PC, kstep = blockDim.x / PC;
   typename AR::A acc[MAXACC];
 #pragma unroll
   for (int a = 0; a < MAXACC; ++a) acc[a].zero();
   const int pc_eff = min(PC, p - c0);
-  for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
+  int it = 0;
+  issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
-    __syncthreads();
-    load_rows(Qs, ldq, Q2, n2, base, rows);
+    V* Qs = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(Qs0) + stg * qst);
+    uint16_t* Js = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(Js0) + stg * jst);
+    issue(tile + gridDim.x, stg ^ 1);  // stage stg^1 was released by the barrier ending the last tile
+    if (rows == TILE_ROWS) {
+      mbar_wait(&bar[stg], (it >> 1) & 1, status);
+    } else {  // partial last tile: plain loads
+      for (int e = t; e < rows * n2; e += blockDim.x) Qs[e] = Q2[base * n2 + e];
+      const uint16_t* js = jt + jt_block(tile, chunk, nch, PC);
+      for (int e = t; e < rows * PC; e += blockDim.x) Js[e] = js[e];
+      __syncthreads();
+    }
     for (int e = t; e < rows * PC; e += blockDim.x) {
       int r = e / PC, c = e - r * PC;
-      V G = AR::zero();
-      if (c < pc_eff) G = Fs[c * Nx + jin[(base + r) * p + c0 + c]];
-      Gs[r * ldG + c] = G;
+      Gs[r * ldG + c] = (c < pc_eff) ? Fs[c * Nx + Js[e]] : AR::zero();
     }
     __syncthreads();
     // rows in groups of four: the loads of a group are issued together
@@ -254,8 +288,8 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
       for (int a = 0; a < MAXACC; ++a) {
         int k = kk0 + a * kstep;
         if (k < n2) {
-          const V q0 = Qs[r * ldq + k], q1 = Qs[(r + 1) * ldq + k];
-          const V q2 = Qs[(r + 2) * ldq + k], q3 = Qs[(r + 3) * ldq + k];
+          const V q0 = Qs[r * n2 + k], q1 = Qs[(r + 1) * n2 + k];
+          const V q2 = Qs[(r + 2) * n2 + k], q3 = Qs[(r + 3) * n2 + k];
           acc[a].fma2(q0, G0);
           acc[a].fma2(q1, G1);
           acc[a].fma2(q2, G2);
@@ -268,9 +302,10 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
 #pragma unroll
       for (int a = 0; a < MAXACC; ++a) {
         int k = kk0 + a * kstep;
-        if (k < n2) acc[a].fma2(Qs[r * ldq + k], G);
+        if (k < n2) acc[a].fma2(Qs[r * n2 + k], G);
       }
     }
+    __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < MAXACC; ++a) {
@@ -299,6 +334,7 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
   V* Gi = Gr + TILE_ROWS * ldG;  // imaginary part
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
   const int npairs = TILE_ROWS * n;
+  const int nch = (p + PC - 1) / PC;
   for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
@@ -326,7 +362,7 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
             v.fma2(q[n + k], Zs[k * ldz + ii]);   // B a
             v.fma2(q[k], Zs[(n + k) * ldz + ii]); // A b
           }
-          gr = Fs[ii * Nx + jin[(base + r) * p + c0 + ii]];
+          gr = Fs[ii * Nx + jin[jt_block(tile, c0 / PC, nch, PC) + r * PC + ii]];
           gi = v.out();
         }
         Gr[r * ldG + ii] = gr;
@@ -364,6 +400,132 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
         }
       }
     }
+  }
+}
+
+// M = Gamma zeta^H in the split form used when all p field rows fit in
+// shared memory.  With Gamma = G + i V_r and V_r = Im(Q zeta):
+//   Re M_k = sum_i G_i a_ki + [x | y] W[:, k],  Im M_k = -sum_i G_i b_ki + [x | y] W[:, n+k],
+// where zeta = a + i b, Q_l = x + i y and W = Y Y^T with Y = [b; a] (2n x p), because
+// sum_i V_i b_ki = sum_m x_m (b b^T)_mk + y_m (a b^T)_mk and likewise for a.
+// Per row this is 2 n p + 4 n^2 multiply-adds instead of 6 n p, and V_r is
+// never formed.  W is computed by every block from zeta in shared memory.
+// Threads: TPR = 4 per row of a 64-row tile; thread (r, s) owns k = s, s+4, ...
+// Q rows and the tile's cell indices (all chunks) arrive by bulk copies into
+// two stages, the next tile's copies running during the current tile.
+template <class AR, int KPT>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_basis_M2_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
+              const typename AR::V* __restrict__ Z2, const typename AR::V* __restrict__ F2,
+              const uint16_t* __restrict__ jt, typename AR::V* __restrict__ M, int* status) {
+  using V = typename AR::V;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n2 = 2 * n, Nx = g.Nx, ldz = p + 1, ldg = p + 1;
+  const int nch = (p + PC - 1) / PC;
+  const uint32_t qbytes = (uint32_t)(sizeof(V) * TILE_ROWS * n2);
+  const uint32_t jbytes = (uint32_t)(sizeof(uint16_t) * TILE_ROWS * nch * PC);
+  const size_t qst = (qbytes + 15) & ~size_t(15), jst = (jbytes + 15) & ~size_t(15);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  unsigned char* Qs0 = smraw + 16;
+  unsigned char* Js0 = Qs0 + 2 * qst;
+  V* Fs = reinterpret_cast<V*>(Js0 + 2 * jst);  // p x Nx
+  V* Zs = Fs + (size_t)p * Nx;                  // n2 x ldz: [a; b]
+  V* Ws = Zs + (size_t)n2 * ldz;                // n2 x n2
+  V* Gt = Ws + (size_t)n2 * n2;                 // TILE_ROWS x ldg
+  const int t = threadIdx.x;
+  const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
+  for (int e = t; e < p * Nx; e += blockDim.x) Fs[e] = F2[e];
+  for (int e = t; e < n2 * p; e += blockDim.x) {
+    int k = e / p, i = e - k * p;
+    Zs[k * ldz + i] = Z2[e];
+  }
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // W = Y Y^T, Y = [b; a]: row m of Y is row (m + n) mod 2n of Z
+  for (int e = t; e < n2 * n2; e += blockDim.x) {
+    int m = e / n2, k = e - m * n2;
+    const V* ym = Zs + ((m + n) % n2) * ldz;
+    const V* yk = Zs + ((k + n) % n2) * ldz;
+    typename AR::A acc;
+    acc.zero();
+    for (int i = 0; i < p; ++i) acc.fma2(ym[i], yk[i]);
+    Ws[e] = acc.out();
+  }
+  auto issue = [&](int64_t tl, int st) {
+    if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[st], qbytes + jbytes);
+    bulk_g2s(Qs0 + st * qst, Q2 + tl * TILE_ROWS * n2, qbytes, &bar[st]);
+    bulk_g2s(Js0 + st * jst, jt + jt_block(tl, 0, nch, PC), jbytes, &bar[st]);
+  };
+  const int r = t >> 2, sub = t & 3;
+  int it = 0;
+  issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
+    const int64_t base = tile * TILE_ROWS;
+    const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
+    const V* Qs = reinterpret_cast<const V*>(Qs0 + stg * qst);
+    uint16_t* Js = reinterpret_cast<uint16_t*>(Js0 + stg * jst);
+    issue(tile + gridDim.x, stg ^ 1);
+    if (rows == TILE_ROWS) {
+      mbar_wait(&bar[stg], (it >> 1) & 1, status);
+    } else {  // partial last tile: plain loads
+      V* Qw = reinterpret_cast<V*>(Qs0 + stg * qst);
+      for (int e = t; e < rows * n2; e += blockDim.x) Qw[e] = Q2[base * n2 + e];
+      const uint16_t* js = jt + jt_block(tile, 0, nch, PC);
+      for (int e = t; e < TILE_ROWS * nch * PC; e += blockDim.x) Js[e] = js[e];
+      __syncthreads();
+    }
+    // G_ri = (q/m) F_i[j_ri] of the tile
+    for (int e = t; e < rows * p; e += blockDim.x) {
+      int rr = e / p, i = e - rr * p;
+      int c = i / PC, ci = i - c * PC;
+      Gt[rr * ldg + i] = Fs[i * Nx + Js[(c * TILE_ROWS + rr) * PC + ci]];
+    }
+    __syncthreads();
+    if (r < rows) {
+      typename AR::A ar[KPT], ai[KPT];
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) { ar[q].zero(); ai[q].zero(); }
+      const V* gr = Gt + r * ldg;
+      for (int i = 0; i < p; ++i) {
+        const V gv = gr[i];
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) {
+          const int k = sub + 4 * q;
+          if (k < n) {
+            ar[q].fma2(gv, Zs[k * ldz + i]);
+            ai[q].fma2(AR::neg(gv), Zs[(n + k) * ldz + i]);
+          }
+        }
+      }
+      const V* qr = Qs + r * n2;
+      for (int m = 0; m < n2; ++m) {
+        const V qm = qr[m];
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) {
+          const int k = sub + 4 * q;
+          if (k < n) {
+            ar[q].fma2(qm, Ws[m * n2 + k]);
+            ai[q].fma2(qm, Ws[m * n2 + n + k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) {
+        const int k = sub + 4 * q;
+        if (k < n) {
+          M[(base + r) * n2 + k] = ar[q].out();
+          M[(base + r) * n2 + n + k] = ai[q].out();
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -539,27 +701,53 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
       size_t smem = ((sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1)) + 15) & ~size_t(15)) +
                     sizeof(unsigned long long) * PC * g.Nx;
-      int gx = tile_grid_x(N, ch, 2 * A.num_sms);
+      int gx = grid_bps(ceil_div(N, TILE_ROWS), ch, (A.tune ? A.tune : kTuneDefault)[TUNE_DEPOSIT], A.num_sms);
       k_deposit_lp<AR><<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
           g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.counts, A.j, A.skip);
       break;
     }
     case LP_PROJECT: {
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
-      size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + PC * g.Nx + TILE_ROWS * (PC + 1));
+      const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
+      const size_t jst = (sizeof(uint16_t) * TILE_ROWS * PC + 15) & ~size_t(15);
+      size_t smem = 16 + 2 * qst + 2 * jst + sizeof(V) * (PC * g.Nx + TILE_ROWS * (PC + 1));
       if (n2 <= 4 * (TILE_THREADS / PC))
         k_project_lp<AR, 4><<<dim3(A.gridx, ch), TILE_THREADS, smem, st>>>(
-            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip);
+            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip, A.status);
       else
         k_project_lp<AR, 16><<<dim3(A.gridx, ch), TILE_THREADS, smem, st>>>(
-            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip);
+            g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.j, A.part, A.skip, A.status);
       break;
     }
     case LP_BASIS_M: {
       int PC = chunk_w(p, g.Nx);
+      {
+        const int nch = ceil_div(p, PC);
+        const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
+        const size_t jst = (sizeof(uint16_t) * TILE_ROWS * nch * PC + 15) & ~size_t(15);
+        const size_t smem2 = 16 + 2 * qst + 2 * jst +
+                             sizeof(V) * ((size_t)p * g.Nx + (size_t)n2 * (p + 1) + (size_t)n2 * n2 +
+                                          (size_t)TILE_ROWS * (p + 1));
+        // split form when all p field rows are resident and two blocks fit an SM
+        // (with one block per SM the double-float form measured slower than
+        // the chunked kernel below)
+        if (smem2 <= 112 * 1024) {
+          int gx = grid_bps(ceil_div(N, TILE_ROWS), 1,
+                            (A.tune ? A.tune : kTuneDefault)[TUNE_BASIS_M], A.num_sms);
+          if (n <= 12)
+            k_basis_M2_lp<AR, 3><<<gx, TILE_THREADS, smem2, st>>>(
+                g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, (const V*)A.v2, A.j, (V*)A.v3,
+                A.status);
+          else
+            k_basis_M2_lp<AR, 10><<<gx, TILE_THREADS, smem2, st>>>(
+                g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, (const V*)A.v2, A.j, (V*)A.v3,
+                A.status);
+          break;
+        }
+      }
       size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + PC * g.Nx +
                                  2 * TILE_ROWS * (PC + 1));
-      int gx = tile_grid_x(N, 1, A.num_sms);
+      int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_BASIS_M], A.num_sms);
       if (TILE_ROWS * n <= 4 * TILE_THREADS)
         k_basis_M_lp<AR, 4><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
                                                             (const V*)A.v1, (const V*)A.v2, A.j,
@@ -586,7 +774,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_AFFINE: {
       size_t smem = sizeof(V) * (2 * A.aff.nterms * n * n + A.aff.nterms * TILE_ROWS * (n2 + 1));
-      int gx = tile_grid_x(N, 1, A.num_sms);
+      int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_AFFINE], A.num_sms);
       k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0);
       break;
     }
@@ -606,6 +794,8 @@ static void set_attrs() {
   cudaFuncSetAttribute(k_project_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_basis_M_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_basis_M_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_basis_M2_lp<AR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_basis_M2_lp<AR, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_gram_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_gram_real_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_affine_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

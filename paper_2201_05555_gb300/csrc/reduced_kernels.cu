@@ -262,6 +262,7 @@ void project(const GridC& g, int64_t count, int n, int p, const double* Q, const
 }
 
 int project_chunks(int p, int Nx) { return ceil_div(p, chunk_width(p, Nx)); }
+int chunk_pc(int p, int Nx) { return chunk_width(p, Nx); }
 
 // ------------------------------------------------ M = Gamma zeta^H (N x n)
 // Gamma_li = GX_li + i V_r,li at R = Q zeta; M_lk = sum_i Gamma_li conj(zeta_ki).

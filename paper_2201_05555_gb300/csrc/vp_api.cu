@@ -110,11 +110,22 @@ struct RedWS {
   int gx_proj, gx_gram;
 };
 
+// Cell-index entries of the tile-by-tile layout (jt_block): whole tiles and
+// whole sample chunks.
+static size_t jcell_count(int64_t N, int p, int Nx) {
+  const int pc = chunk_pc(p, Nx > 0 ? Nx : 3);
+  return (size_t)ceil_div(N, TILE_ROWS) * ceil_div(p, pc) * TILE_ROWS * pc;
+}
+
 size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df, int* gx_proj,
-                    int* gx_gram) {
+                    int* gx_gram, const int* tune = nullptr) {
   const int n2 = 2 * n, nn = n * n;
-  const int gp = tile_grid_x(N, project_chunks(p, Nx > 0 ? Nx : 3), sms);
-  const int gg = gram_grid_x(N, sms);
+  const int chunks = project_chunks(p, Nx > 0 ? Nx : 3);
+  // the FP32-based path sizes its grids by the context's launch-shape knobs
+  const int* tn = tune ? tune : kTuneDefault;
+  const int gp = df ? grid_bps(ceil_div(N, TILE_ROWS), chunks, tn[TUNE_PROJECT], sms)
+                    : tile_grid_x(N, chunks, sms);
+  const int gg = df ? grid_bps(ceil_div(N, 32), 1, tn[TUNE_GRAM], sms) : gram_grid_x(N, sms);
   if (gx_proj) *gx_proj = gp;
   if (gx_gram) *gx_gram = gg;
   size_t part_d = std::max<size_t>((size_t)gp * n2 * p,
@@ -125,7 +136,7 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
          arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
          arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
-         (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes((size_t)N * p, 2) +
+         (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
                    2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8)
              : 0);
 }
@@ -134,7 +145,8 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
                  bool df = false) {
   const int n2 = 2 * n, nn = n * n;
   size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
-  size_t bytes = red_ws_bytes(ctx->num_sms, N, n, p, Nx, nrows, df, &w.gx_proj, &w.gx_gram);
+  size_t bytes = red_ws_bytes(ctx->num_sms, N, n, p, Nx, nrows, df, &w.gx_proj, &w.gx_gram,
+                              ctx->tune);
   size_t part_d = std::max<size_t>((size_t)w.gx_proj * n2 * p,
                                    std::max<size_t>((size_t)w.gx_gram * 12 * nn * 2,
                                                     (size_t)w.gx_gram * n2 * n2));
@@ -160,7 +172,7 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   for (int r = 0; r < 5; ++r) w.rows[r] = r < nrows ? a.take<double>((size_t)N * n2) : nullptr;
   w.Q2a = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.Q2b = df ? a.take<float2>((size_t)N * n2) : nullptr;
-  w.jcell = df ? a.take<uint16_t>((size_t)N * p) : nullptr;
+  w.jcell = df ? a.take<uint16_t>(jcell_count(N, p, Nx)) : nullptr;
   for (int r = 0; r < 5; ++r) w.frows[r] = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
@@ -275,6 +287,8 @@ struct RedDF {
     a.n = n;
     a.p = p;
     a.num_sms = ctx->num_sms;
+    a.tune = ctx->tune;
+    a.status = ctx->d_status;
     return a;
   }
   void field(const void* Q2, const double* Z, const int* skip) {
@@ -440,7 +454,7 @@ vp_status DFStep::pre(double* trace_step) {
     VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
     VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
   }
-  VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+  VP_CUDA(cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), st));
   VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
   return VP_OK;
 }
@@ -484,11 +498,7 @@ vp_status DFStep::post() {
     if (o.reortho) {                           // Q <- Q (Q^H Q)^-1/2
       DD.split(Q, w.Q2b);
       DD.grams({w.Q2b}, {{0, 0}}, w.grams);
-      double2* Wj = w.tmp;
-      double2* Ws = w.tmp + nn;
-      double* lam = reinterpret_cast<double*>(w.tmp + 2 * nn);
-      VP_K(VP_K_INIT, init_launch_jacobi(n, w.grams, Wj, lam, Ws, ctx->d_status, st));
-      VP_K(VP_K_INIT, init_launch_inv_sqrt(n, Ws, lam, w.C, ctx->d_status, st));
+      VP_K(VP_K_INIT, lowdin(n, w.grams, w.C, ctx->d_status, st));
       DD.comb({w.Q2b}, w.C, Q, nullptr);
     }
   }
@@ -530,6 +540,138 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
     VP_TRY(S.post());
   }
   VP_LAUNCHED();
+  return VP_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm) {
+  if (!ctx || knob < 0 || knob >= TUNE_COUNT || blocks_per_sm < 1 || blocks_per_sm > 32)
+    return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->tune[knob] = blocks_per_sm;
+  return VP_OK;
+}
+
+vp_status vp_tune_get(vp_ctx* ctx, int32_t knob, int32_t* blocks_per_sm) {
+  if (!ctx || knob < 0 || knob >= TUNE_COUNT || !blocks_per_sm) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  *blocks_per_sm = ctx->tune[knob];
+  return VP_OK;
+}
+
+// Times each FP32-based particle kernel at candidate grid sizes on the
+// caller's state (one field evaluation sets up the cell indices and the
+// field) and keeps the fastest per knob.  Reads Q and Z only.
+vp_status vp_autotune(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                      const double* Q, const double* Z, int32_t arith, int32_t reps,
+                      int32_t* chosen, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
+  if (arith < 1 || arith > 2) return vp_fail(ctx, VP_EINVAL, "arith must be 1 or 2");
+  if (reps < 1 || reps > 1000) return vp_fail(ctx, VP_EINVAL, "reps outside [1, 1000]");
+  static const int cand[] = {1, 2, 3, 4, 6, 8};
+  const int ncand = 6;
+  const int saved[TUNE_COUNT] = {ctx->tune[0], ctx->tune[1], ctx->tune[2], ctx->tune[3], ctx->tune[4]};
+  const uint64_t mask = ctx->prof_mask;
+  ctx->prof_mask = 0;
+  // workspace for the largest grids
+  for (int k = 0; k < TUNE_COUNT; ++k) ctx->tune[k] = cand[ncand - 1];
+  Red R;
+  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, R, true);
+  for (int k = 0; k < TUNE_COUNT; ++k) ctx->tune[k] = saved[k];
+  if (s != VP_OK) {
+    ctx->prof_mask = mask;
+    return s;
+  }
+  RedWS& w = R.w;
+  RedDF D{R, ctx, st, N, n, p, arith};
+  D.split(Q, w.Q2a);
+  D.field(w.Q2a, Z, nullptr);  // cell indices, (q/m) F, Z2, Zh2 at (Q, Z)
+  VP_CUDA(cudaMemsetAsync(w.C, 0, sizeof(double2) * 4 * n * n, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VP_CUDA(cudaEventCreate(&e0));
+  VP_CUDA(cudaEventCreate(&e1));
+  const int chunks = project_chunks(p, grid->Nx);
+  int best_all[TUNE_COUNT];
+  for (int knob = 0; knob < TUNE_COUNT; ++knob) {
+    float best = 1e30f;
+    int bestc = saved[knob];
+    for (int ci = 0; ci < ncand; ++ci) {
+      ctx->tune[knob] = cand[ci];
+      LpArgs a = D.base();
+      auto launch = [&]() {
+        switch (knob) {
+          case TUNE_DEPOSIT:
+            a.v0 = w.Q2a;
+            a.v1 = w.Zh2;
+            a.counts = w.counts;
+            a.j = w.jcell;
+            lp_launch(arith, LP_DEPOSIT, a, st);
+            break;
+          case TUNE_PROJECT:
+            a.v0 = w.Q2a;
+            a.v1 = w.F2;
+            a.j = w.jcell;
+            a.part = w.part;
+            a.gridx = grid_bps(ceil_div(N, TILE_ROWS), chunks, cand[ci], ctx->num_sms);
+            lp_launch(arith, LP_PROJECT, a, st);
+            break;
+          case TUNE_BASIS_M:
+            a.v0 = w.Q2a;
+            a.v1 = w.Z2;
+            a.v2 = w.F2;
+            a.v3 = w.frows[0];
+            a.j = w.jcell;
+            lp_launch(arith, LP_BASIS_M, a, st);
+            break;
+          case TUNE_GRAM:
+            a.gram.blk[0] = w.Q2a;
+            a.gram.blk[1] = w.frows[1];
+            a.gram.nblk = 2;
+            a.gram.pa[0] = 0;
+            a.gram.pb[0] = 1;
+            a.gram.pa[1] = 1;
+            a.gram.pb[1] = 1;
+            a.gram.npairs = 2;
+            a.part = w.part;
+            a.gridx = grid_bps(ceil_div(N, 32), 1, cand[ci], ctx->num_sms);
+            lp_launch(arith, LP_GRAM, a, st);
+            break;
+          default:
+            a.aff.X[0] = w.Q2a;
+            a.aff.X[1] = w.frows[1];
+            a.aff.nterms = 2;
+            a.C = w.C;
+            a.v0 = w.frows[2];
+            lp_launch(arith, LP_AFFINE, a, st);
+            break;
+        }
+      };
+      launch();  // warm-up
+      VP_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) launch();
+      VP_CUDA(cudaEventRecord(e1, st));
+      VP_CUDA(cudaEventSynchronize(e1));
+      VP_LAUNCHED();
+      float ms = 0.f;
+      VP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bestc = cand[ci];
+      }
+    }
+    ctx->tune[knob] = bestc;
+    best_all[knob] = bestc;
+  }
+  VP_CUDA(cudaMemsetAsync(w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->prof_mask = mask;
+  if (chosen)
+    for (int k = 0; k < TUNE_COUNT; ++k) chosen[k] = best_all[k];
   return VP_OK;
 }
 
@@ -1140,7 +1282,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
       VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
       VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
     }
-    VP_CUDA(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), st));
+    VP_CUDA(cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), st));
     VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
     int done_h = 0, total = 0;
     while (!done_h) {

@@ -15,6 +15,11 @@
 #define VP_MAX_N2 128  // 2n <= 128
 #define VP_NSM_DEFAULT 152
 
+// Launch-shape knobs of the FP32-based particle kernels: resident blocks per
+// SM the grid is sized for (vp_tune_set / vp_autotune).
+enum TuneKnob { TUNE_DEPOSIT = 0, TUNE_PROJECT, TUNE_BASIS_M, TUNE_GRAM, TUNE_AFFINE, TUNE_COUNT };
+constexpr int kTuneDefault[TUNE_COUNT] = {4, 4, 4, 8, 8};
+
 // ----------------------------------------------------------------- context
 struct vp_ctx {
   int device = 0;
@@ -36,7 +41,17 @@ struct vp_ctx {
   struct Pending { int id; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
+  int tune[TUNE_COUNT] = {kTuneDefault[0], kTuneDefault[1], kTuneDefault[2], kTuneDefault[3],
+                         kTuneDefault[4]};
 };
+
+// Blocks of a grid sized for `bps` resident blocks per SM over `chunks`
+// column chunks, at most one per tile.
+inline int grid_bps(int64_t tiles, int chunks, int bps, int num_sms) {
+  int64_t want = ((int64_t)bps * num_sms + chunks - 1) / chunks;
+  int64_t g = tiles < want ? tiles : want;
+  return g < 1 ? 1 : (int)g;
+}
 
 // Count (and, if enabled, event-time) one kernel launch made by `expr`.
 void vp_prof_begin(vp_ctx* ctx, int id, cudaStream_t st, cudaEvent_t* a);
@@ -86,6 +101,57 @@ int vp_choose_rank(const double* sig, int p, int n_min, int n_max, double tol);
 // Device status word: the first error wins.
 __device__ __forceinline__ void vp_set_status(int* st, int code) {
   if (st) atomicCAS(st, 0, code);
+}
+
+// ------------------------------------------------- bulk copies (TMA engine)
+// One-dimensional bulk copies global -> shared completed on an mbarrier
+// (cp.async.bulk with complete_tx).  Addresses and sizes must be multiples of
+// 16 bytes.  Waits are bounded: after kMbarSpins polls the waiting thread sets
+// VP_ETIMEDOUT in the status word and goes on, so every thread still reaches
+// the same barriers and the kernel ends.
+constexpr int kMbarSpins = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make initialised barriers visible to the bulk-copy engine
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this CTA's earlier generic-proxy accesses of shared memory before
+// later bulk-copy writes into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  for (int i = 0; i < kMbarSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  vp_set_status(status, VP_ETIMEDOUT);
+  return false;
 }
 
 // Sub-allocation inside the arena (256-byte aligned).
@@ -196,7 +262,17 @@ struct LpArgs {
   AffineArgsLP aff{};
   const double2* C = nullptr;
   double* dout = nullptr;
+  const int* tune = nullptr;  // vp_ctx::tune (null: defaults)
+  int* status = nullptr;      // device status word
 };
+
+// Cell indices of the FP32-based path are stored tile by tile: for row tile
+// t (TILE_ROWS particles) and sample chunk c (PC samples) one contiguous
+// TILE_ROWS x PC block, so a kernel fetches its (tile, chunk) indices, or all
+// chunks of a tile, with one bulk copy.  Entries past N or p are padding.
+__host__ __device__ __forceinline__ int64_t jt_block(int64_t tile, int chunk, int nchunks, int PC) {
+  return (tile * nchunks + chunk) * (int64_t)TILE_ROWS * PC;
+}
 
 // pic_kernels.cu
 void deposit_samples(const GridC& g, int64_t N, int p, const double* X, int64_t ldx,
@@ -215,6 +291,7 @@ cudaError_t full_step(const GridC& g, int64_t N, int p, double* X, double* V, do
 int tile_grid_x(int64_t N, int chunks, int num_sms);
 int gram_grid_x(int64_t N, int num_sms);
 int project_chunks(int p, int Nx);
+int chunk_pc(int p, int Nx);  // samples per column chunk of the particle kernels
 void reconstruct(int64_t N, int n, int p, const double* Q, const double* Z, double* X, double* V,
                  cudaStream_t st);
 void deposit_reduced(const GridC& g, int64_t N, int n, int p, const double* Q, const double* Z,
@@ -252,6 +329,7 @@ void add_linear(int n, int p, const double* gX, const double* GVraw, const doubl
 void energies(int n, int p, const double* GVraw, const double* Z, const double* Efield,
               double* E_out, double* H_out, int64_t stride, const double2* QhQ, double* resid,
               int* status, cudaStream_t st);
+void lowdin(int n, const double2* G, double2* C, int* status, cudaStream_t st);
 void dense_init();
 void pic_init();
 
