@@ -152,19 +152,28 @@ __device__ __forceinline__ void load_zc(typename AR::V* Zs, int ldz,
 }
 
 // ------------------------------------------------------------------ deposit
+// X_r = Re(Q zeta) / h per (particle, sample) in the policy's arithmetic,
+// then the cell index and fixed-point weights: charge counts accumulate in
+// shared memory (int64, order-free) and go to the global counts once per
+// block.  Full tiles of Q rows arrive by bulk copies into two stages, the
+// copy of the block's next tile running during the current one; a partial
+// last tile is read with plain loads.
 template <class AR>
 __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
                              const typename AR::V* __restrict__ Q2,
                              const typename AR::V* __restrict__ Zh2,
                              unsigned long long* __restrict__ counts, uint16_t* __restrict__ jout,
-                             const int* skip) {
+                             const int* skip, int* status) {
   using V = typename AR::V;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n2 = 2 * n, ldq = n2 + 1, ldz = PC + 1, Nx = g.Nx;
-  V* Qs = reinterpret_cast<V*>(smraw);
-  V* Zs = Qs + TILE_ROWS * ldq;
-  const size_t zoff = (sizeof(V) * (TILE_ROWS * ldq + n2 * ldz) + 15) & ~size_t(15);
+  const int n2 = 2 * n, ldz = PC + 1, Nx = g.Nx;
+  const uint32_t qbytes = (uint32_t)(sizeof(V) * TILE_ROWS * n2);
+  const size_t qst = (qbytes + 15) & ~size_t(15);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  unsigned char* Qs0 = smraw + 16;
+  V* Zs = reinterpret_cast<V*>(Qs0 + 2 * qst);
+  const size_t zoff = (16 + 2 * qst + sizeof(V) * n2 * ldz + 15) & ~size_t(15);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smraw + zoff);
   const int c0 = blockIdx.y * PC;
   load_zc<AR>(Zs, ldz, Zh2, n2, p, c0, PC);
@@ -174,15 +183,36 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
   const long long one = 1ll << g.S;
   const float scale = (float)g.fp_scale, inv_Nx = (float)g.inv_Nx;
   unsigned long long* mycnt = cnt + ii * Nx;
-  for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
+  const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tl, int st) {
+    if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[st], qbytes);
+    bulk_g2s(Qs0 + st * qst, Q2 + tl * TILE_ROWS * n2, qbytes, &bar[st]);
+  };
+  int it = 0;
+  issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
-    __syncthreads();
-    load_rows(Qs, ldq, Q2, n2, base, rows);
-    __syncthreads();
+    V* Qs = reinterpret_cast<V*>(Qs0 + stg * qst);
+    issue(tile + gridDim.x, stg ^ 1);
+    if (rows == TILE_ROWS) {
+      mbar_wait(&bar[stg], (it >> 1) & 1, status);
+    } else {  // partial last tile: plain loads
+      for (int e = t; e < rows * n2; e += blockDim.x) Qs[e] = Q2[base * n2 + e];
+      __syncthreads();
+    }
     if (active) {
       for (int r = rsub; r < rows; r += RP) {
-        const V* q = Qs + r * ldq;
+        const V* q = Qs + r * n2;
         typename AR::A x;
         x.zero();
         for (int k = 0; k < n; ++k) {
@@ -199,8 +229,8 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
         if (jout) jout[jt_block(tile, blockIdx.y, gridDim.y, PC) + r * PC + ii] = (uint16_t)j;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = threadIdx.x; e < PC * Nx; e += blockDim.x) {
     int c = e / Nx;
     if (c0 + c < p && cnt[e]) atomicAdd(&counts[(int64_t)(c0 + c) * Nx + (e - c * Nx)], cnt[e]);
@@ -410,6 +440,7 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
 // sum_i V_i b_ki = sum_m x_m (b b^T)_mk + y_m (a b^T)_mk and likewise for a.
 // Per row this is 2 n p + 4 n^2 multiply-adds instead of 6 n p, and V_r is
 // never formed.  W is computed by every block from zeta in shared memory.
+// F_i[j] is gathered from global memory (p x Nx values, cached in L1).
 // Threads: TPR = 4 per row of a 64-row tile; thread (r, s) owns k = s, s+4, ...
 // Q rows and the tile's cell indices (all chunks) arrive by bulk copies into
 // two stages, the next tile's copies running during the current tile.
@@ -428,13 +459,11 @@ k_basis_M2_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   unsigned char* Qs0 = smraw + 16;
   unsigned char* Js0 = Qs0 + 2 * qst;
-  V* Fs = reinterpret_cast<V*>(Js0 + 2 * jst);  // p x Nx
-  V* Zs = Fs + (size_t)p * Nx;                  // n2 x ldz: [a; b]
+  V* Zs = reinterpret_cast<V*>(Js0 + 2 * jst);  // n2 x ldz: [a; b]
   V* Ws = Zs + (size_t)n2 * ldz;                // n2 x n2
   V* Gt = Ws + (size_t)n2 * n2;                 // TILE_ROWS x ldg
   const int t = threadIdx.x;
   const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
-  for (int e = t; e < p * Nx; e += blockDim.x) Fs[e] = F2[e];
   for (int e = t; e < n2 * p; e += blockDim.x) {
     int k = e / p, i = e - k * p;
     Zs[k * ldz + i] = Z2[e];
@@ -481,11 +510,12 @@ k_basis_M2_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __
       for (int e = t; e < TILE_ROWS * nch * PC; e += blockDim.x) Js[e] = js[e];
       __syncthreads();
     }
-    // G_ri = (q/m) F_i[j_ri] of the tile
+    // G_ri = (q/m) F_i[j_ri] of the tile, gathered from the p x Nx field
+    // rows (read-only path; they stay in L1 next to this block's shared memory)
     for (int e = t; e < rows * p; e += blockDim.x) {
       int rr = e / p, i = e - rr * p;
       int c = i / PC, ci = i - c * PC;
-      Gt[rr * ldg + i] = Fs[i * Nx + Js[(c * TILE_ROWS + rr) * PC + ci]];
+      Gt[rr * ldg + i] = __ldg(F2 + (size_t)i * Nx + Js[(c * TILE_ROWS + rr) * PC + ci]);
     }
     __syncthreads();
     if (r < rows) {
@@ -533,39 +563,66 @@ k_basis_M2_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __
 // out_s = blk[pa[s]]^H blk[pb[s]] (n x n complex); part[blockIdx.x][s][k1][k2].
 #define GDF_ROWS 32
 #define GDF_EPT 4
+// Full 32-row tiles of every block arrive by bulk copies into two stages (the
+// next tile's copies run during the current tile); a partial last tile is
+// read with plain loads.
 template <class AR>
-__global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ part) {
+__global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ part, int* status) {
   using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int n2 = 2 * n, ldb = n2 + 1;
+  const int n2 = 2 * n;
+  const uint32_t bbytes = (uint32_t)(sizeof(V) * GDF_ROWS * n2);  // one block's tile
+  const size_t sst = (size_t)bbytes * a.nblk;                     // one stage, 16-aligned
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  unsigned char* S0 = smraw + 16;
   const int total = a.npairs * n * n;
   const int e0 = blockIdx.y * blockDim.x * GDF_EPT;
+  const int t = threadIdx.x;
+  const int64_t ntiles = (N + GDF_ROWS - 1) / GDF_ROWS;
   typename AR::A re[GDF_EPT], im[GDF_EPT];
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) { re[q].zero(); im[q].zero(); }
-  for (int64_t tile = blockIdx.x; tile * GDF_ROWS < N; tile += gridDim.x) {
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tl, int st) {
+    if (t != 0 || tl >= ntiles || (tl + 1) * GDF_ROWS > N) return;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[st], (uint32_t)sst);
+    for (int b = 0; b < a.nblk; ++b)
+      bulk_g2s(S0 + st * sst + b * bbytes,
+               reinterpret_cast<const V*>(a.blk[b]) + tl * GDF_ROWS * n2, bbytes, &bar[st]);
+  };
+  int it = 0;
+  issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
     const int64_t base = tile * GDF_ROWS;
     const int rows = (int)((int64_t)GDF_ROWS < N - base ? (int64_t)GDF_ROWS : N - base);
-    __syncthreads();
-    for (int b = 0; b < a.nblk; ++b) {
-      const V* src = reinterpret_cast<const V*>(a.blk[b]);
-      for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
-        int r = e / n2, k = e - r * n2;
-        sm[(b * GDF_ROWS + r) * ldb + k] = src[(base + r) * n2 + k];
+    V* sm = reinterpret_cast<V*>(S0 + stg * sst);
+    issue(tile + gridDim.x, stg ^ 1);
+    if (rows == GDF_ROWS) {
+      mbar_wait(&bar[stg], (it >> 1) & 1, status);
+    } else {
+      for (int b = 0; b < a.nblk; ++b) {
+        const V* src = reinterpret_cast<const V*>(a.blk[b]);
+        for (int e = t; e < rows * n2; e += blockDim.x) sm[b * GDF_ROWS * n2 + e] = src[base * n2 + e];
       }
+      __syncthreads();
     }
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < GDF_EPT; ++q) {
-      int e = e0 + q * blockDim.x + threadIdx.x;
+      int e = e0 + q * blockDim.x + t;
       if (e < total) {
         int s = e / (n * n), rem = e - s * n * n, k1 = rem / n, k2 = rem - k1 * n;
-        const V* X = sm + a.pa[s] * GDF_ROWS * ldb;
-        const V* Y = sm + a.pb[s] * GDF_ROWS * ldb;
+        const V* X = sm + a.pa[s] * GDF_ROWS * n2;
+        const V* Y = sm + a.pb[s] * GDF_ROWS * n2;
         for (int r = 0; r < rows; ++r) {
-          V xr = X[r * ldb + k1], xi = X[r * ldb + n + k1];
-          V yr = Y[r * ldb + k2], yi = Y[r * ldb + n + k2];
+          V xr = X[r * n2 + k1], xi = X[r * n2 + n + k1];
+          V yr = Y[r * n2 + k2], yi = Y[r * n2 + n + k2];
           // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
           re[q].fma2(xr, yr);
           re[q].fma2(xi, yi);
@@ -574,10 +631,11 @@ __global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ 
         }
       }
     }
+    __syncthreads();
   }
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) {
-    int e = e0 + q * blockDim.x + threadIdx.x;
+    int e = e0 + q * blockDim.x + t;
     if (e < total) part[(int64_t)blockIdx.x * total + e] = make_double2(re[q].value(), im[q].value());
   }
 }
@@ -624,37 +682,62 @@ __global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restric
 // written as FP64 rows (out_d) and/or rows of the policy (out_v).
 template <class AR>
 __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __restrict__ C,
-                            double* __restrict__ out_d, typename AR::V* __restrict__ out_v) {
+                            double* __restrict__ out_d, typename AR::V* __restrict__ out_v,
+                            int* status) {
   using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n2 = 2 * n, ldb = n2 + 1, nn = n * n;
-  V* Cr = reinterpret_cast<V*>(smraw);  // nterms x n x n
+  const int n2 = 2 * n, nn = n * n;
+  const uint32_t tbytes = (uint32_t)(sizeof(V) * TILE_ROWS * n2);  // one term's tile
+  const size_t sst = (size_t)tbytes * a.nterms;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  unsigned char* S0 = smraw + 16;
+  V* Cr = reinterpret_cast<V*>(S0 + 2 * sst);  // nterms x n x n
   V* Ci = Cr + a.nterms * nn;
-  V* Xs = Ci + a.nterms * nn;
-  for (int e = threadIdx.x; e < a.nterms * nn; e += blockDim.x) {
+  const int t = threadIdx.x;
+  const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
+  for (int e = t; e < a.nterms * nn; e += blockDim.x) {
     double2 c = C[e];
     Cr[e] = AR::from(c.x);
     Ci[e] = AR::from(c.y);
   }
-  for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tl, int st) {
+    if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[st], (uint32_t)sst);
+    for (int b = 0; b < a.nterms; ++b)
+      bulk_g2s(S0 + st * sst + b * tbytes,
+               reinterpret_cast<const V*>(a.X[b]) + tl * TILE_ROWS * n2, tbytes, &bar[st]);
+  };
+  int it = 0;
+  issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
-    __syncthreads();
-    for (int b = 0; b < a.nterms; ++b) {
-      const V* src = reinterpret_cast<const V*>(a.X[b]);
-      for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) {
-        int r = e / n2, k = e - r * n2;
-        Xs[(b * TILE_ROWS + r) * ldb + k] = src[(base + r) * n2 + k];
+    V* Xs = reinterpret_cast<V*>(S0 + stg * sst);
+    issue(tile + gridDim.x, stg ^ 1);
+    if (rows == TILE_ROWS) {
+      mbar_wait(&bar[stg], (it >> 1) & 1, status);
+    } else {
+      for (int b = 0; b < a.nterms; ++b) {
+        const V* src = reinterpret_cast<const V*>(a.X[b]);
+        for (int e = t; e < rows * n2; e += blockDim.x) Xs[b * TILE_ROWS * n2 + e] = src[base * n2 + e];
       }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+    for (int e = t; e < rows * n; e += blockDim.x) {
       int r = e / n, k = e - r * n;
       typename AR::A re, im;
       re.zero();
       im.zero();
       for (int b = 0; b < a.nterms; ++b) {
-        const V* x = Xs + (b * TILE_ROWS + r) * ldb;
+        const V* x = Xs + (b * TILE_ROWS + r) * n2;
         const V* cr = Cr + b * nn;
         const V* ci = Ci + b * nn;
         for (int q = 0; q < n; ++q) {
@@ -676,6 +759,7 @@ __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __r
         out_v[o + n + k] = im.out();
       }
     }
+    __syncthreads();
   }
 }
 
@@ -699,11 +783,12 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_DEPOSIT: {
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
-      size_t smem = ((sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1)) + 15) & ~size_t(15)) +
+      const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
+      size_t smem = ((16 + 2 * qst + sizeof(V) * n2 * (PC + 1) + 15) & ~size_t(15)) +
                     sizeof(unsigned long long) * PC * g.Nx;
       int gx = grid_bps(ceil_div(N, TILE_ROWS), ch, (A.tune ? A.tune : kTuneDefault)[TUNE_DEPOSIT], A.num_sms);
       k_deposit_lp<AR><<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
-          g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.counts, A.j, A.skip);
+          g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.counts, A.j, A.skip, A.status);
       break;
     }
     case LP_PROJECT: {
@@ -726,11 +811,10 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
         const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
         const size_t jst = (sizeof(uint16_t) * TILE_ROWS * nch * PC + 15) & ~size_t(15);
         const size_t smem2 = 16 + 2 * qst + 2 * jst +
-                             sizeof(V) * ((size_t)p * g.Nx + (size_t)n2 * (p + 1) + (size_t)n2 * n2 +
+                             sizeof(V) * ((size_t)n2 * (p + 1) + (size_t)n2 * n2 +
                                           (size_t)TILE_ROWS * (p + 1));
-        // split form when all p field rows are resident and two blocks fit an SM
-        // (with one block per SM the double-float form measured slower than
-        // the chunked kernel below)
+        // split form when two blocks fit an SM (with one block per SM the
+        // double-float form measured slower than the chunked kernel below)
         if (smem2 <= 112 * 1024) {
           int gx = grid_bps(ceil_div(N, TILE_ROWS), 1,
                             (A.tune ? A.tune : kTuneDefault)[TUNE_BASIS_M], A.num_sms);
@@ -761,8 +845,9 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     case LP_GRAM: {
       int total = A.gram.npairs * n * n;
       int gy = ceil_div(total, TILE_THREADS * GDF_EPT);
-      size_t smem = sizeof(V) * A.gram.nblk * GDF_ROWS * (n2 + 1);
-      k_gram_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, n, A.gram, (double2*)A.part);
+      size_t smem = 16 + 2 * sizeof(V) * A.gram.nblk * GDF_ROWS * n2;
+      k_gram_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, n, A.gram, (double2*)A.part,
+                                                                   A.status);
       break;
     }
     case LP_GRAM_REAL: {
@@ -773,9 +858,9 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_AFFINE: {
-      size_t smem = sizeof(V) * (2 * A.aff.nterms * n * n + A.aff.nterms * TILE_ROWS * (n2 + 1));
+      size_t smem = 16 + sizeof(V) * (2 * A.aff.nterms * n * n + 2 * A.aff.nterms * TILE_ROWS * n2);
       int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_AFFINE], A.num_sms);
-      k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0);
+      k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0, A.status);
       break;
     }
   }
