@@ -105,7 +105,7 @@ typedef struct vp_step_opts {
 
 /* ------------------------------------------------------------------ context */
 /* Create a context on `device`.  scratch_bytes bounds the workspace the
- * library may allocate for itself (0 = 4 GiB). */
+ * library may allocate for itself (0 = 16 GiB). */
 vp_status vp_ctx_create(vp_ctx** ctx_out, int device, size_t scratch_bytes);
 vp_status vp_ctx_destroy(vp_ctx* ctx);
 const char* vp_last_error(const vp_ctx* ctx);
@@ -422,7 +422,7 @@ typedef struct vp_batch_item {
 /* opts: arith 1 or 2 (others as vp_basis_update; reortho honoured).
  * rounds_first / rounds_more: fixed-point rounds in the first and in the
  * repeated graph.  scratch_per_instance: workspace budget of each instance's
- * context (0: 4 GiB).  The items' buffers must stay valid until destroy.
+ * context (0: 16 GiB).  The items' buffers must stay valid until destroy.
  * Synchronises the device. */
 vp_status vp_batch_create(vp_batch** out, int device, const vp_batch_item* items, int32_t count,
                           const vp_step_opts* opts, int32_t rounds_first, int32_t rounds_more,

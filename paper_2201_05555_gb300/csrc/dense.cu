@@ -430,20 +430,24 @@ __device__ double block_sum2(double v, double* red) {
 // (relative update <= tol), stalled (see vp_step_opts), non-finite
 // (VP_ENUMERIC) or out of iterations (VP_ENOCONV).  Every later launch of the
 // step returns at once through `done`.
-#define CU_CW 8
+#define CU_CW 1
 __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
                                const double* __restrict__ GVraw, const double* __restrict__ Z0,
                                double* k, double* Ze, double dt, double tol, int maxit,
                                double stall_floor, double stall_ratio, double* rstate, int* done,
-                               int* iters, int* ticket, double* partials, int* status) {
+                               int* iters, int* ticket, double* partials, int* status,
+                               const double* __restrict__ part, int nparts, void* Z2, void* Zh2,
+                               double inv_h, int zmode) {
   if (*done) return;
   extern __shared__ double cu_sm[];
   __shared__ double red[32];
   __shared__ int last;
   const int n2 = 2 * n;
   const int i0 = blockIdx.x * CU_CW, cw = min(CU_CW, p - i0);
-  double* GV = cu_sm;            // n2 x n2, G_V = U_V^T U_V
-  double* Zs = cu_sm + n2 * n2;  // n2 x CU_CW, this block's columns of Ze
+  double* GV = cu_sm;                 // n2 x n2, G_V = U_V^T U_V
+  double* Zs = cu_sm + n2 * n2;       // n2 x CU_CW, this block's columns of Ze
+  double* Gs = Zs + n2 * CU_CW;       // n2 x CU_CW, projection of this block's columns
+  double* Sl = Gs + n2 * CU_CW;       // slice sums of the partials
   for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
     int a = e / n2, b = e - a * n2;
     GV[e] = GVraw[vperm(a, n) * n2 + vperm(b, n)];
@@ -451,6 +455,41 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
   for (int e = threadIdx.x; e < n2 * cw; e += blockDim.x) {
     int r = e / cw, c = e - r * cw;
     Zs[r * CU_CW + c] = Ze[(int64_t)r * p + i0 + c];
+  }
+  if (part) {
+    // slice sl of output o sums partials sl, sl + S, ... with eight
+    // independent accumulators (many loads in flight); the slices are then
+    // added in slice order (deterministic)
+    const int64_t tot = (int64_t)n2 * p;
+    const int nout = n2 * cw;
+    const int S = max(1, (int)blockDim.x / nout);
+    for (int e = threadIdx.x; e < nout * S; e += blockDim.x) {
+      const int o = e % nout, sl = e / nout;
+      const int r = o / cw, c = o - r * cw;
+      const double* src = part + (int64_t)r * p + i0 + c;
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = 0.0;
+      int b = sl;
+      for (; b + 7 * S < nparts; b += 8 * S) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += __ldcg(src + (int64_t)(b + u * S) * tot);
+      }
+      for (; b < nparts; b += S) a[0] += __ldcg(src + (int64_t)b * tot);
+      Sl[o * S + sl] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      const int r = o / cw, c = o - r * cw;
+      double g = 0.0;
+      for (int sl = 0; sl < S; ++sl) g += Sl[o * S + sl];
+      Gs[r * CU_CW + c] = g;
+    }
+  } else {
+    for (int e = threadIdx.x; e < n2 * cw; e += blockDim.x) {
+      int r = e / cw, c = e - r * cw;
+      Gs[r * CU_CW + c] = gX[(int64_t)r * p + i0 + c];
+    }
   }
   __syncthreads();
   double d2 = 0.0, k2 = 0.0;
@@ -460,14 +499,17 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
     const int64_t o = (int64_t)r * p + i0 + c;
     int gr = r < n ? n + r : r - n;
     double sgn = r < n ? 1.0 : -1.0;
-    double g = gX[(int64_t)gr * p + i0 + c];
+    double g = Gs[gr * CU_CW + c];
     for (int m = 0; m < n2; ++m) g = fma(GV[gr * n2 + m], Zs[m * CU_CW + c], g);
     double kn = sgn * g;
     double dk = kn - k[o];
     d2 = fma(dk, dk, d2);
     k2 = fma(kn, kn, k2);
     k[o] = kn;
-    Ze[o] = fma(0.5 * dt, kn, Z0[o]);
+    const double ze = fma(0.5 * dt, kn, Z0[o]);
+    Ze[o] = ze;
+    if (Z2) store_lp(Z2, o, ze, zmode);
+    if (Zh2) store_lp(Zh2, o, ze * inv_h, zmode);
   }
   double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red);
   if (threadIdx.x == 0) {
@@ -477,14 +519,21 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
     last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last || threadIdx.x >= 32) return;
   __threadfence();
+  // warp 0 of the last block: lane l adds blocks l, l + 32, ...; lane 0 then
+  // adds the lanes by a fixed butterfly (its order does not depend on timing)
   D2 = 0.0;
   K2 = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) {
-    D2 += ((volatile double*)partials)[2 * b];
-    K2 += ((volatile double*)partials)[2 * b + 1];
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+    D2 += __ldcg(partials + 2 * b);
+    K2 += __ldcg(partials + 2 * b + 1);
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    D2 += __shfl_xor_sync(0xffffffffu, D2, o);
+    K2 += __shfl_xor_sync(0xffffffffu, K2, o);
+  }
+  if (threadIdx.x != 0) return;
   *ticket = 0;
   int it = *iters + 1;
   *iters = it;
@@ -512,12 +561,14 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
                   double* Ze, double dt, double tol, int maxit, double stall_floor,
                   double stall_ratio, double* rstate, int* done, int* iters, int* status,
-                  cudaStream_t st) {
+                  cudaStream_t st, const double* part, int nparts, void* Z2, void* Zh2,
+                  double inv_h, int zmode) {
   const int nb = (p + CU_CW - 1) / CU_CW;
-  size_t smem = sizeof(double) * (4 * n * n + 2 * (size_t)n * CU_CW);
+  // GV, Zs, Gs and the slice sums (at most max(blockDim, 2n CU_CW) of them)
+  size_t smem = sizeof(double) * (4 * n * n + 4 * (size_t)n * CU_CW + 256 + 2 * (size_t)n * CU_CW);
   k_coeff_update<<<nb, 256, smem, st>>>(n, p, gX, GVraw, Z0, k, Ze, dt, tol, maxit, stall_floor,
                                         stall_ratio, rstate, done, iters, done + 2, rstate + 2,
-                                        status);
+                                        status, part, nparts, Z2, Zh2, inv_h, zmode);
 }
 
 // Loewdin factor G^{-1/2} of a Hermitian positive definite G close to I

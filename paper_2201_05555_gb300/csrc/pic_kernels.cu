@@ -149,10 +149,12 @@ void counts_to_rho(const GridC& g, int p, const unsigned long long* counts, doub
 
 // ---------------------------------------------------------------- Poisson
 // One block per sample.  Input either rho (double) or fixed-point counts.
+// F2 (nullable): (q/m) F also in the row format f2mode of the FP32-based
+// forms (1 double-float, 2 FP32), for their projection and basis kernels.
 __global__ void k_poisson(GridC g, const double* __restrict__ rho,
                           const unsigned long long* __restrict__ counts, double* phi, double* F,
                           double* energy, unsigned long long* zero_counts, const int* skip,
-                          int* status) {
+                          int* status, void* F2, int f2mode) {
   if (skip && *skip) return;
   __shared__ double a[VP_MAX_NX];
   __shared__ double tmp[VP_MAX_NX];
@@ -168,6 +170,8 @@ __global__ void k_poisson(GridC g, const double* __restrict__ rho,
     for (int c = threadIdx.x; c < Nx; c += blockDim.x) zero_counts[base + c] = 0ull;
   double e = poisson_inplace(g, a, tmp, red, phi ? phi + base : nullptr);
   for (int c = threadIdx.x; c < Nx; c += blockDim.x) F[base + c] = a[c];
+  if (F2)
+    for (int c = threadIdx.x; c < Nx; c += blockDim.x) store_lp(F2, base + c, g.qm * a[c], f2mode);
   if (threadIdx.x == 0) {
     if (energy) energy[i] = e;
     if (!isfinite(e)) vp_set_status(status, VP_ENUMERIC);
@@ -176,8 +180,9 @@ __global__ void k_poisson(GridC g, const double* __restrict__ rho,
 
 void poisson(const GridC& g, int p, const double* rho, const unsigned long long* counts,
              double* phi, double* F, double* energy, unsigned long long* zero_counts,
-             const int* skip, int* status, cudaStream_t st) {
-  k_poisson<<<p, 256, 0, st>>>(g, rho, counts, phi, F, energy, zero_counts, skip, status);
+             const int* skip, int* status, cudaStream_t st, void* F2, int f2mode) {
+  k_poisson<<<p, 256, 0, st>>>(g, rho, counts, phi, F, energy, zero_counts, skip, status, F2,
+                               f2mode);
 }
 
 // ----------------------------------------------------------------- gather

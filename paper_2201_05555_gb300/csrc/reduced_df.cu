@@ -21,12 +21,6 @@
 
 namespace vpk {
 
-__device__ __forceinline__ float2 df_split(double d) {
-  float h = __double2float_rn(d);
-  float l = __double2float_rn(d - (double)h);
-  return make_float2(h, l);
-}
-
 struct ArithDF {
   using V = float2;
   static __device__ __forceinline__ V from(double d) { return df_split(d); }
@@ -683,18 +677,18 @@ __global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restric
 template <class AR>
 __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __restrict__ C,
                             double* __restrict__ out_d, typename AR::V* __restrict__ out_v,
-                            int* status) {
+                            int* status, int TR) {
   using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n2 = 2 * n, nn = n * n;
-  const uint32_t tbytes = (uint32_t)(sizeof(V) * TILE_ROWS * n2);  // one term's tile
+  const uint32_t tbytes = (uint32_t)(sizeof(V) * TR * n2);  // one term's tile of TR rows
   const size_t sst = (size_t)tbytes * a.nterms;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   unsigned char* S0 = smraw + 16;
   V* Cr = reinterpret_cast<V*>(S0 + 2 * sst);  // nterms x n x n
   V* Ci = Cr + a.nterms * nn;
   const int t = threadIdx.x;
-  const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
+  const int64_t ntiles = (N + TR - 1) / TR;
   for (int e = t; e < a.nterms * nn; e += blockDim.x) {
     double2 c = C[e];
     Cr[e] = AR::from(c.x);
@@ -707,27 +701,27 @@ __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __r
   }
   __syncthreads();
   auto issue = [&](int64_t tl, int st) {
-    if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
+    if (t != 0 || tl >= ntiles || (tl + 1) * TR > N) return;
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[st], (uint32_t)sst);
     for (int b = 0; b < a.nterms; ++b)
       bulk_g2s(S0 + st * sst + b * tbytes,
-               reinterpret_cast<const V*>(a.X[b]) + tl * TILE_ROWS * n2, tbytes, &bar[st]);
+               reinterpret_cast<const V*>(a.X[b]) + tl * TR * n2, tbytes, &bar[st]);
   };
   int it = 0;
   issue(blockIdx.x, 0);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int stg = it & 1;
-    const int64_t base = tile * TILE_ROWS;
-    const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
+    const int64_t base = tile * TR;
+    const int rows = (int)((int64_t)TR < N - base ? (int64_t)TR : N - base);
     V* Xs = reinterpret_cast<V*>(S0 + stg * sst);
     issue(tile + gridDim.x, stg ^ 1);
-    if (rows == TILE_ROWS) {
+    if (rows == TR) {
       mbar_wait(&bar[stg], (it >> 1) & 1, status);
     } else {
       for (int b = 0; b < a.nterms; ++b) {
         const V* src = reinterpret_cast<const V*>(a.X[b]);
-        for (int e = t; e < rows * n2; e += blockDim.x) Xs[b * TILE_ROWS * n2 + e] = src[base * n2 + e];
+        for (int e = t; e < rows * n2; e += blockDim.x) Xs[b * TR * n2 + e] = src[base * n2 + e];
       }
       __syncthreads();
     }
@@ -737,7 +731,7 @@ __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __r
       re.zero();
       im.zero();
       for (int b = 0; b < a.nterms; ++b) {
-        const V* x = Xs + (b * TILE_ROWS + r) * n2;
+        const V* x = Xs + (b * TR + r) * n2;
         const V* cr = Cr + b * nn;
         const V* ci = Ci + b * nn;
         for (int q = 0; q < n; ++q) {
@@ -858,9 +852,15 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_AFFINE: {
-      size_t smem = 16 + sizeof(V) * (2 * A.aff.nterms * n * n + 2 * A.aff.nterms * TILE_ROWS * n2);
-      int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_AFFINE], A.num_sms);
-      k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0, A.status);
+      // rows per tile: 64, or fewer when two stages of every term would not fit
+      int TR = TILE_ROWS;
+      auto smem_for = [&](int tr) {
+        return 16 + sizeof(V) * (2 * (size_t)A.aff.nterms * n * n + 2 * (size_t)A.aff.nterms * tr * n2);
+      };
+      while (TR > 16 && smem_for(TR) > 200 * 1024) TR /= 2;
+      size_t smem = smem_for(TR);
+      int gx = grid_bps(ceil_div(N, TR), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_AFFINE], A.num_sms);
+      k_affine_lp<AR><<<gx, TILE_THREADS, smem, st>>>(N, n, A.aff, A.C, A.dout, (V*)A.v0, A.status, TR);
       break;
     }
   }

@@ -291,14 +291,18 @@ struct RedDF {
     a.status = ctx->d_status;
     return a;
   }
-  void field(const void* Q2, const double* Z, const int* skip) {
+  // field at (Q2, Z): Z2 = Z and Zh2 = Z / h in row format (skipped when the
+  // caller already wrote them), deposit, Poisson writing F and (q/m) F in row format
+  void field(const void* Q2, const double* Z, const int* skip, bool z_ready = false) {
     RedWS& w = R.w;
     LpArgs a = base();
-    a.dsrc = Z;
-    a.v0 = w.Z2;
-    a.v1 = w.Zh2;
-    a.skip = skip;
-    VP_K(VP_K_PREP_LP, lp_launch(arith, LP_PREP, a, st));
+    if (!z_ready) {
+      a.dsrc = Z;
+      a.v0 = w.Z2;
+      a.v1 = w.Zh2;
+      a.skip = skip;
+      VP_K(VP_K_PREP_LP, lp_launch(arith, LP_PREP, a, st));
+    }
     a = base();
     a.v0 = const_cast<void*>(Q2);
     a.v1 = w.Zh2;
@@ -307,12 +311,7 @@ struct RedDF {
     a.skip = skip;
     VP_K(VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
     VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip,
-                               ctx->d_status, st));
-    a = base();
-    a.F = w.F;
-    a.v2 = w.F2;
-    a.skip = skip;
-    VP_K(VP_K_PREP_LP, lp_launch(arith, LP_PREP, a, st));
+                               ctx->d_status, st, w.F2, arith));
   }
   void project(const void* Q2, const int* skip) {
     LpArgs a = base();
@@ -456,6 +455,11 @@ vp_status DFStep::pre(double* trace_step) {
   }
   VP_CUDA(cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), st));
   VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
+  LpArgs a = D.base();  // Ze in row format for the first round's deposit
+  a.dsrc = w.Ze;
+  a.v0 = w.Z2;
+  a.v1 = w.Zh2;
+  VP_K(VP_K_PREP_LP, lp_launch(o.arith, LP_PREP, a, st));
   return VP_OK;
 }
 
@@ -464,13 +468,16 @@ vp_status DFStep::rounds(int count) {
   const int n = R.n, p = R.p;
   RedDF D{R, ctx, st, R.N, n, p, o.arith};
   const int64_t zsz = (int64_t)2 * n * p;
+  (void)zsz;
+  // Ze in row format (Z2, Zh2) comes from pre() for the first round and from
+  // the coefficient update (which also sums the projection partials) after it
   for (int r = 0; r < count; ++r) {
-    D.field(Qm, w.Ze, w.flags);
+    D.field(Qm, w.Ze, w.flags, true);
     D.project(Qm, w.flags);
-    VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
-    VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
-                                         o.stall_floor, o.stall_ratio, w.aux, w.flags, w.flags + 1,
-                                         ctx->d_status, st));
+    VP_K(VP_K_COEFF_UPDATE,
+         coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit, o.stall_floor,
+                      o.stall_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st, w.part,
+                      w.gx_proj, w.Z2, w.Zh2, R.g.inv_h, o.arith));
   }
   return VP_OK;
 }
@@ -894,7 +901,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VP_ECUDA;
   vp_ctx* ctx = new vp_ctx();
   ctx->device = device;
-  ctx->budget = scratch_bytes ? scratch_bytes : (size_t(4) << 30);
+  ctx->budget = scratch_bytes ? scratch_bytes : (size_t(16) << 30);
   DeviceGuard guard(device);
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&ctx->d_status, 64) != cudaSuccess ||

@@ -154,6 +154,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
   return false;
 }
 
+// Double-float split of an FP64 value: hi = rn(d), lo = rn(d - hi).
+__device__ __forceinline__ float2 df_split(double d) {
+  float h = __double2float_rn(d);
+  float l = __double2float_rn(d - (double)h);
+  return make_float2(h, l);
+}
+// Store d in the row format of the FP32-based forms: mode 1 double-float
+// (float2), mode 2 FP32 (float).
+__device__ __forceinline__ void store_lp(void* base, int64_t e, double d, int mode) {
+  if (mode == 1) reinterpret_cast<float2*>(base)[e] = df_split(d);
+  else reinterpret_cast<float*>(base)[e] = __double2float_rn(d);
+}
+
 // Sub-allocation inside the arena (256-byte aligned).
 struct Arena {
   char* base;
@@ -281,7 +294,7 @@ void counts_to_rho(const GridC& g, int p, const unsigned long long* counts, doub
                    cudaStream_t st);
 void poisson(const GridC& g, int p, const double* rho, const unsigned long long* counts,
              double* phi, double* F, double* energy, unsigned long long* zero_counts,
-             const int* skip, int* status, cudaStream_t st);
+             const int* skip, int* status, cudaStream_t st, void* F2 = nullptr, int f2mode = 0);
 void gather(const GridC& g, int64_t N, int p, const double* X, int64_t ldx, const double* F,
             const int32_t* idx, int64_t d, double* GX, int num_sms, int* status, cudaStream_t st);
 cudaError_t full_step(const GridC& g, int64_t N, int p, double* X, double* V, double dt,
@@ -318,10 +331,15 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
                          double2* tmp, int* status, cudaStream_t st);
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
+// gX: the projection (2n x p), or nullptr with `part` (nparts x 2n x p block
+// partials of it, summed here in block order).  Z2/Zh2 (nullable): the new
+// evaluation point Ze and Ze / h in the row format `zmode` (1 double-float,
+// 2 FP32) for the next deposit.
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
                   double* Ze, double dt, double tol, int maxit, double stall_floor,
                   double stall_ratio, double* rstate, int* done, int* iters, int* status,
-                  cudaStream_t st);
+                  cudaStream_t st, const double* part = nullptr, int nparts = 0,
+                  void* Z2 = nullptr, void* Zh2 = nullptr, double inv_h = 0.0, int zmode = 0);
 void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st);
 void sqrt_nonneg(int m, const double* x, double* out, cudaStream_t st);
 void add_linear(int n, int p, const double* gX, const double* GVraw, const double* Z, double* g,

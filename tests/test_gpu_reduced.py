@@ -203,3 +203,20 @@ def test_deim_all_rows_equals_full_projection(ctx):
     gx = ctx.deim_gather_project(grid, T(q_storage(U)), T(Z), T(idx), T(c), T(Phi)).cpu().numpy()
     UX = U[:N]
     assert rel(gx, UX.T @ G[:N]) < TOL
+
+
+@pytest.mark.parametrize("arith", [0, 1, 2])
+@pytest.mark.parametrize("sh", [dict(N=2000, p=80, n=40, Nx=256), dict(N=1500, p=70, n=32, Nx=1024),
+                                dict(N=3001, p=256, n=16, Nx=256)])
+def test_prk2_large_rank_parity(ctx, sh, arith):
+    """Largest ranks, sample counts and grids the shared-memory stages allow:
+    one step against the oracle (FP64 and double-float at 1e-10; FP32 row
+    work at the precision form's one-step bound 1e-5 on UZ)."""
+    g, grid, U, Z = state(**sh)
+    dt = 0.05
+    Qd, Zd = T(q_storage(U)), T(Z)
+    ctx.basis_update(grid, Qd, Zd, dt, 1, arith=arith, reortho=arith == 2)
+    ctx.sync_status()
+    Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
+    UZ = U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy()
+    assert rel(UZ, Uo @ Zo) < (TOL if arith < 2 else 1e-5)
