@@ -439,6 +439,14 @@ vp_status vp_batch_info(const vp_batch* b, int64_t* steps_done, int64_t* launche
 const char* vp_batch_last_error(const vp_batch* b);
 vp_status vp_batch_destroy(vp_batch* b);
 
+/* ------------------------------------------------------------ self-test */
+/* Failure-detection check of the bounded waits: launches one block that waits
+ * on an mbarrier nothing completes, `spins` polls (1 .. 2^22), after which it
+ * records VP_ETIMEDOUT in the status word (read by vp_ctx_sync_status) and
+ * ends.  The library's own waits (bulk copies completing on mbarriers) use
+ * 2^22 polls and report the same way.  The paper has no counterpart. */
+vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
+
 /* ------------------------------------------------------------ profiling */
 /* Kernels of the library, for launch counts and event timing. */
 typedef enum vp_kernel {

@@ -90,6 +90,7 @@ _SIGS = [
     ("vp_server_stats", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32),
                                C.POINTER(_I32), C.POINTER(_SZ)]),
     ("vp_server_destroy", _I32, [_P]),
+    ("vp_selftest_wait", _I32, [_P, _I32, _P]),
     ("vp_tune_set", _I32, [_P, _I32, _I32]),
     ("vp_tune_get", _I32, [_P, _I32, C.POINTER(_I32)]),
     ("vp_autotune", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I32, _I32,
@@ -360,6 +361,10 @@ class Context:
                                                     _ptr(c, name="c"), _ptr(phi, name="phi"),
                                                     _ptr(g), self._stream()), "deim_gather_project")
         return g
+
+    def selftest_wait(self, spins: int = 1000):
+        """Launch a bounded wait that runs out (VP_ETIMEDOUT via sync_status)."""
+        self._check(self.lib.vp_selftest_wait(self.h, spins, self._stream()), "selftest_wait")
 
     TUNE_KNOBS = ("deposit", "project", "basis_M", "gram", "affine")
 

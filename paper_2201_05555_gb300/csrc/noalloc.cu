@@ -77,3 +77,27 @@ extern "C" vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int3
   if (cudaGetLastError() != cudaSuccess) return VP_ECUDA;
   return VP_OK;
 }
+
+// ------------------------------------------------------------- self-test
+// A bounded wait that runs out: one block waits on an mbarrier that no copy
+// and no thread ever completes, `spins` polls per thread, then records
+// VP_ETIMEDOUT in the context's status word and returns.  Nothing is in
+// flight when it ends, so the context stays usable.
+namespace {
+__global__ void k_selftest_wait(int spins, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0, status, spins);
+}
+}  // namespace
+
+extern "C" vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream) {
+  if (!ctx || spins < 1 || spins > (1 << 22)) return VP_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_selftest_wait<<<1, 64, 0, st>>>(spins, ctx->d_status);
+  return cudaGetLastError() == cudaSuccess ? VP_OK : VP_ECUDA;
+}

@@ -147,8 +147,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-  for (int i = 0; i < kMbarSpins; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
+                                          int spins = kMbarSpins) {
+  for (int i = 0; i < spins; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   vp_set_status(status, VP_ETIMEDOUT);
   return false;

@@ -131,3 +131,34 @@ def test_invalid_arguments_rejected_on_host(ctx):
     assert e.value.status == 1
     with pytest.raises(VPError):
         ctx.deposit_cic(make_grid(10, 5000, 1.0), X)  # Nx > 1024
+
+
+def test_bounded_wait_reports_timeout(ctx):
+    """A wait that nothing completes ends after its poll limit with
+    VP_ETIMEDOUT in the status word; the context keeps working."""
+    from paper_2201_05555_gb300 import VPError, make_grid
+    ctx.selftest_wait(2000)
+    with pytest.raises(VPError) as e:
+        ctx.sync_status()
+    assert e.value.status == 5  # VP_ETIMEDOUT
+    ctx.sync_status()  # reading the status cleared it
+    N, p, Nx = 1000, 3, 16
+    g = pic.make_grid(N, Nx, 4 * np.pi)
+    X = W.random_positions(p, N, g.L, seed=3)
+    rho = ctx.deposit_cic(make_grid(N, Nx, g.L), T(X)).cpu().numpy()
+    assert rel(rho, pic.deposit(X, g)) < 1e-12
+
+
+def test_drift_reported(ctx):
+    """Re-orthonormalisation of a basis far off the manifold (Q^H Q = 4 I)
+    reports VP_EDRIFT instead of correcting it silently."""
+    from paper_2201_05555_gb300 import VPError, make_grid
+    N, p, n, Nx = 2000, 8, 3, 32
+    etas = W.hammersley_params(p, {"v0": (2.0, 3.0)}, {"alpha": 1e-3, "sigma": 1.0})
+    X0, V0 = W.load_batch(W.TWO_STREAM, etas, N, quiet=False)
+    Q, Z, _ = ctx.init_csvd(T(X0), T(V0), n)
+    Q *= 2.0
+    with pytest.raises(VPError) as e:
+        ctx.basis_update(make_grid(N, Nx, W.TWO_STREAM.L), Q, Z, 0.05, 1, arith=2, reortho=True)
+        ctx.sync_status()
+    assert e.value.status == 8  # VP_EDRIFT
