@@ -164,10 +164,39 @@ def tangent_velocity(U0: np.ndarray, xi: np.ndarray, Z: np.ndarray, g: pic.Grid,
 # --------------------------------------------------------------------------
 # partitioned RK2 step (eqs. pRK_Z, pRK_U, pRK_Z_k1, pRK_Z_ki, pRK_U_ktilde)
 # --------------------------------------------------------------------------
+def param_subsample(Z0: np.ndarray, p_max: int, tol: float = 0.0) -> np.ndarray:
+    """Greedy parameter subsample of Sec. 4.1 (eq. pSampl) on the columns of Z0.
+
+    Each iteration adds the index i outside the subset whose distance
+    min_j |Z0_i - Z0_j|_2 to the subset (j in the subset) is largest.  Readings:
+    the printed minimum runs over the subset (over all indices it would be
+    zero); the first index is the column of largest norm; ties go to the lowest
+    index; the loop stops at p_max indices or when the largest distance falls
+    to tol times the one found for the second index."""
+    p = Z0.shape[1]
+    p_max = min(p_max, p)
+    norms = np.linalg.norm(Z0, axis=0)
+    sel = [int(np.argmax(norms))]
+    dmin = np.linalg.norm(Z0 - Z0[:, [sel[0]]], axis=0)
+    d_first = None
+    while len(sel) < p_max:
+        cand = dmin.copy()
+        cand[sel] = -1.0
+        i = int(np.argmax(cand))
+        if d_first is None:
+            d_first = cand[i]
+        elif cand[i] <= tol * d_first:
+            break
+        sel.append(i)
+        dmin = np.minimum(dmin, np.linalg.norm(Z0 - Z0[:, [i]], axis=0))
+    return np.array(sel, dtype=np.int64)
+
+
 def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
               tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
               retract=retraction, grad_fn=None, stall_floor: float = 1e-3,
-              stall_ratio: float = 0.5, k_init: np.ndarray | None = None):
+              stall_ratio: float = 0.5, k_init: np.ndarray | None = None,
+              sub: np.ndarray | None = None):
     """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
 
     info: 'iters' (fixed-point evaluations), 'resid' (last relative update),
@@ -176,7 +205,10 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     grad_fn: optional map R -> G replacing the PIC gradient (any Hamiltonian).
     k_init: initial guess of the fixed point (the paper leaves it unstated);
     None starts from k = 0, a warm start passes the previous step's k2.
+    sub: parameter subsample (Sec. 4.1): the basis velocities use only the
+    columns sub of Z (and of the gradient); the coefficients use all columns.
     """
+    cols = slice(None) if sub is None else np.asarray(sub)
     info = {}
     if grad_fn is None:
         G0, _, E0 = full_gradient(U0, Z0, g)
@@ -187,7 +219,7 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
         kh1 = np.zeros_like(U0)
         U_half = U0
     else:
-        kh1 = basis_velocity_from_G(U0, Z0, G0)
+        kh1 = basis_velocity_from_G(U0, Z0[:, cols], G0[:, cols])
         U_half = retract(U0, 0.5 * dt * kh1)
     info["kh1"] = kh1
     info["U_half"] = U_half
@@ -216,7 +248,8 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     Z1 = Z0 + dt * k
     if freeze_basis:
         return U0.copy(), Z1, info
-    Y, _, _ = tangent_velocity(U0, 0.5 * dt * kh1, Z0 + 0.5 * dt * k, g, retract, grad_fn)
+    Y, _, _ = tangent_velocity(U0, 0.5 * dt * kh1, (Z0 + 0.5 * dt * k)[:, cols], g, retract,
+                               grad_fn)
     U1 = retract(U0, dt * Y)
     return U1, Z1, info
 

@@ -185,3 +185,45 @@ def test_prk2_is_second_order_for_smooth_hamiltonian():
         o, s = reduced.manifold_residuals(U)
         assert o < 1e-13 and s < 1e-13
     assert 3.2 < errs[0] / errs[1] < 5.0, errs
+
+
+# ------------------------------------------------------- parameter subsample
+def test_param_subsample_line():
+    """Points 0, 1, ..., 9 on a line: the largest norm first (9), then the
+    farthest from it (0), then the midpoint with the lower index on the tie
+    (4 and 5 are both 4 away), then the points halfway again."""
+    Z = np.zeros((2, 10))
+    Z[0] = np.arange(10.0)
+    sel = reduced.param_subsample(Z, 5)
+    assert list(sel[:3]) == [9, 0, 4]
+    # 4th: distance 2 to {0, 4, 9} for 2, 6 and 7; the lowest index wins
+    assert sel[3] == 2
+
+
+def test_param_subsample_brute_force():
+    """Each greedy choice maximises the distance to the chosen set (checked by
+    enumerating every candidate), distances never increase, and p_max = p
+    selects every column once."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    Z = rng.standard_normal((6, 23))
+    sel = list(reduced.param_subsample(Z, 23))
+    assert sorted(sel) == list(range(23))
+    prev = np.inf
+    for k in range(1, 23):
+        chosen = sel[:k]
+        d = [min(np.linalg.norm(Z[:, i] - Z[:, j]) for j in chosen) if i not in chosen else -1
+             for i in range(23)]
+        assert sel[k] == int(np.argmax(d))
+        assert d[sel[k]] <= prev + 1e-15
+        prev = d[sel[k]]
+    # a tolerance stops early: the largest remaining distance falls below it
+    short = reduced.param_subsample(Z, 23, tol=0.9)
+    assert 2 <= len(short) < 23 and list(short) == sel[:len(short)]
+
+
+def test_prk2_with_full_subsample_is_unchanged():
+    """The subsampled basis evolution with every column selected is the full one."""
+    g, U, Z = small_state(N=300, p=7, n=2, Nx=16)
+    a = reduced.prk2_step(U, Z, 0.05, g)
+    b = reduced.prk2_step(U, Z, 0.05, g, sub=np.arange(7))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
