@@ -97,10 +97,17 @@ typedef struct vp_step_opts {
    * algebra and the energies are FP64 in every mode.  Default 0. */
   int32_t arith;
   /* 1: after every step re-orthonormalise Q <- Q (Q^H Q)^-1/2 (the block
-   * form keeps U symplectic): Gram and update in double-float, the n x n
-   * eigen-decomposition in FP64.  Not in the paper; a safeguard against the
-   * drift of U^T U = I in the precision form.  Default 0. */
+   * form keeps U symplectic): Gram and update in double-float, the factor by
+   * a coupled Newton-Schulz iteration in FP64 (|Q^H Q - I|_F >= 0.9 reports
+   * VP_EDRIFT).  Not in the paper; a safeguard against the drift of
+   * U^T U = I in the precision form.  Default 0. */
   int32_t reortho;
+  /* Parameter subsample of the basis evolution (Sec. 4.1): 0 = all samples;
+   * otherwise the basis velocities use only the nsub columns sub_idx (device,
+   * int32, from vp_param_subsample; n <= nsub <= p) of Z and of the gradient,
+   * while every coefficient column is advanced.  arith 1 or 2 only. */
+  int32_t nsub;
+  const int32_t* sub_idx;
 } vp_step_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -184,7 +191,7 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0, 1e-3, 0.5, 0, 0}.  trace_dev (nullable): (nsteps x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-3, 0.5, 0, 0, 0, NULL}.  trace_dev (nullable): (nsteps x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
  * nonlinear_hamiltonian) of the state entering each step, taken from the
  * step's first field evaluation (no extra work; with arith = 2 from an extra
@@ -211,6 +218,17 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
 vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0_dev,
                        const double* V0_dev, double* Q_dev, double* Z_dev, double* sigma_dev,
                        void* stream);
+
+/* Greedy parameter subsample (Sec. 4.1, eq. pSampl) on the columns of Z0
+ * (2n x p, device): the first index is the column of largest norm, then each
+ * step adds the column whose distance min_j |Z0_i - Z0_j|_2 to the chosen set
+ * is largest (ties to the lowest index), until p_max columns or until that
+ * distance falls to tol times the one of the second choice.  idx_dev (device,
+ * int32, p_max entries) receives the indices in order of choice, *count the
+ * number chosen.  p <= 1024.  Synchronises `stream`. */
+vp_status vp_param_subsample(vp_ctx* ctx, int32_t n, int32_t p, const double* Z0_dev,
+                             int32_t p_max, double tol, int32_t* idx_dev, int32_t* count,
+                             void* stream);
 
 /* The same start with the rank chosen at t = 0 from the singular values (the
  * paper observes that a constant rank suffices; the rule is a reading): n =
@@ -455,7 +473,7 @@ typedef enum vp_kernel {
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
-  VP_K_INIT, VP_K_LOAD, VP_K_COUNT
+  VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

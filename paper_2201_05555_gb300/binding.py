@@ -36,7 +36,8 @@ class Grid(C.Structure):
 
 class StepOpts(C.Structure):
     _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32), ("stall_floor", _D),
-                ("stall_ratio", _D), ("arith", _I32), ("reortho", _I32)]
+                ("stall_ratio", _D), ("arith", _I32), ("reortho", _I32), ("nsub", _I32),
+                ("sub_idx", _P)]
 
 
 def make_grid(N: int, Nx: int, L: float, q: float = -1.0, m: float = 1.0,
@@ -77,6 +78,7 @@ _SIGS = [
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
     ("vp_kernel_name", C.c_char_p, [_I32]),
+    ("vp_param_subsample", _I32, [_P, _I32, _I32, _P, _I32, _D, _P, C.POINTER(_I32), _P]),
     ("vp_init_csvd_rank", _I32, [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P,
                                  C.POINTER(_I32), _P]),
     ("vp_load_particles", _I32, [_P, _I32, _I32, C.c_uint64, _I64, _I32, _P, _P, _P, _P]),
@@ -110,7 +112,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
-           "k_load"]
+           "k_load", "k_subset"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -296,7 +298,8 @@ class Context:
                      tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
                      trace: bool = True, iters: bool = True, stall_floor: float = 1e-3,
                      stall_ratio: float = 0.5, arith: int = 0,
-                     kstate: torch.Tensor | None = None, reortho: bool = False):
+                     kstate: torch.Tensor | None = None, reortho: bool = False,
+                     sub: torch.Tensor | None = None):
         """nsteps partitioned RK2 steps in place on Q (N x 2n) and Z (2n x p).
         arith: 0 FP64, 1 double-float, 2 FP32 (precision form) for the N-row work.  kstate (2n x p, in/out):
         warm start of the fixed point, updated with the last k2."""
@@ -305,7 +308,8 @@ class Context:
         tr = self._empty(max(nsteps, 1), p, 2) if trace else None
         it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
         opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio, int(arith),
-                        int(reortho))
+                        int(reortho), 0 if sub is None else sub.numel(),
+                        _ptr(sub, torch.int32, "sub"))
         self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,
                                              _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
                                              C.byref(opts), _ptr(tr),
@@ -324,6 +328,16 @@ class Context:
                                           _ptr(V0, name="V0"), _ptr(Q), _ptr(Z), _ptr(sig),
                                           self._stream()), "init_csvd")
         return Q, Z, sig
+
+    def param_subsample(self, Z0: torch.Tensor, p_max: int, tol: float = 0.0) -> torch.Tensor:
+        """Greedy parameter subsample (int32 device indices, in order of choice)."""
+        n2, p = Z0.shape
+        idx = torch.empty(min(p_max, p), dtype=torch.int32, device=Z0.device)
+        cnt = _I32(0)
+        self._check(self.lib.vp_param_subsample(self.h, n2 // 2, p, _ptr(Z0, name="Z0"), p_max,
+                                                tol, _ptr(idx, torch.int32, "idx"), C.byref(cnt),
+                                                self._stream()), "param_subsample")
+        return idx[: cnt.value]
 
     def init_csvd_rank(self, X0: torch.Tensor, V0: torch.Tensor, n_min: int, n_max: int,
                        tail_tol: float):
@@ -577,7 +591,7 @@ class Batch:
                                _ptr(it, torch.int32, "iters"))
         self._arr = arr
         ro = (arith == 2) if reortho is None else reortho
-        opts = StepOpts(tol, maxit, 0, 1e-3, 0.5, arith, int(ro))
+        opts = StepOpts(tol, maxit, 0, 1e-3, 0.5, arith, int(ro), 0, None)
         h = _P()
         s = self.lib.vp_batch_create(C.byref(h), device, C.cast(arr, _P), len(instances),
                                      C.byref(opts), rounds_first, rounds_more,

@@ -628,6 +628,108 @@ void lowdin(int n, const double2* G, double2* C, int* status, cudaStream_t st) {
   k_lowdin<<<1, 256, sizeof(double2) * 4 * n * n, st>>>(n, G, C, status);
 }
 
+// Zs (rows x nsub) = columns idx of Z (rows x p); an index outside [0, p)
+// records VP_EINVAL and gives a zero column.
+__global__ void k_gather_cols(int rows, int p, const double* __restrict__ Z,
+                              const int32_t* __restrict__ idx, int nsub, double* __restrict__ Zs,
+                              int* status) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * nsub) return;
+  const int r = (int)(e / nsub), j = (int)(e - (int64_t)r * nsub);
+  const int c = idx[j];
+  if (c < 0 || c >= p) {
+    vp_set_status(status, VP_EINVAL);
+    Zs[e] = 0.0;
+    return;
+  }
+  Zs[e] = Z[(int64_t)r * p + c];
+}
+
+void gather_cols(int rows, int p, const double* Z, const int32_t* idx, int nsub, double* Zs,
+                 int* status, cudaStream_t st) {
+  k_gather_cols<<<ceil_div((int64_t)rows * nsub, 256), 256, 0, st>>>(rows, p, Z, idx, nsub, Zs,
+                                                                     status);
+}
+
+// Greedy parameter subsample (Sec. 4.1, eq. pSampl), one block: dmin holds
+// each column's distance to the chosen set; the chosen column and ties are
+// resolved by a block arg-max that prefers the lowest index.
+__global__ void k_param_subsample(int rows, int p, const double* __restrict__ Z, int p_max,
+                                  double tol, int32_t* __restrict__ idx, int32_t* count) {
+  extern __shared__ double ps_sm[];
+  double* dmin = ps_sm;  // p
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int pick;
+  __shared__ double dfirst;
+  __shared__ int stop;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = (blockDim.x + 31) >> 5;
+  auto argmax = [&](const double* v) {  // largest v, lowest index on ties
+    double best = -1.0;
+    int bidx = 0x7fffffff;
+    for (int i = t; i < p; i += blockDim.x)
+      if (v[i] > best) { best = v[i]; bidx = i; }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { bv[wid] = best; bi[wid] = bidx; }
+    __syncthreads();
+    if (t == 0) {
+      double b = -1.0;
+      int k = 0x7fffffff;
+      for (int w = 0; w < nw; ++w)
+        if (bv[w] > b || (bv[w] == b && bi[w] < k)) { b = bv[w]; k = bi[w]; }
+      pick = k;
+      bv[0] = b;
+    }
+    __syncthreads();
+  };
+  auto dist = [&](int i, int j) {
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) {
+      const double d = Z[(int64_t)r * p + i] - Z[(int64_t)r * p + j];
+      s = fma(d, d, s);
+    }
+    return sqrt(s);
+  };
+  for (int i = t; i < p; i += blockDim.x) {  // norms first
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s = fma(Z[(int64_t)r * p + i], Z[(int64_t)r * p + i], s);
+    dmin[i] = sqrt(s);
+  }
+  __syncthreads();
+  argmax(dmin);
+  int k = pick;
+  if (t == 0) { idx[0] = k; stop = 0; dfirst = -1.0; }
+  for (int i = t; i < p; i += blockDim.x) dmin[i] = (i == k) ? -1.0 : dist(i, k);
+  __syncthreads();
+  int chosen = 1;
+  while (chosen < p_max) {
+    argmax(dmin);
+    if (t == 0) {
+      const double d = bv[0];
+      if (dfirst < 0.0) dfirst = d;
+      else if (d <= tol * dfirst) stop = 1;
+      if (!stop) idx[chosen] = pick;
+    }
+    __syncthreads();
+    if (stop) break;
+    k = pick;
+    for (int i = t; i < p; i += blockDim.x)
+      if (dmin[i] >= 0.0) dmin[i] = (i == k) ? -1.0 : fmin(dmin[i], dist(i, k));
+    ++chosen;
+    __syncthreads();
+  }
+  if (t == 0) *count = chosen;
+}
+
+void param_subsample(int rows, int p, const double* Z, int p_max, double tol, int32_t* idx,
+                     int32_t* count, cudaStream_t st) {
+  k_param_subsample<<<1, 256, sizeof(double) * p, st>>>(rows, p, Z, p_max, tol, idx, count);
+}
+
 // Z1 = Z0 + dt k
 __global__ void k_axpy(int64_t m, double a, const double* x, const double* y, double* out) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -108,6 +108,16 @@ struct RedWS {
   float2* frows[5];   // row blocks of the FP32-based step
   float2 *Z2, *Zh2, *F2;
   int gx_proj, gx_gram;
+  // parameter subsample of the basis stages (Sec. 4.1): per-sample buffers
+  // for the nsub selected columns; N-row buffers are shared
+  struct Sub {
+    int nsub = 0;
+    const int32_t* idx = nullptr;
+    unsigned long long* counts = nullptr;
+    double *F = nullptr, *Efield = nullptr, *Zs = nullptr;
+    float2 *Z2 = nullptr, *Zh2 = nullptr, *F2 = nullptr;
+    uint16_t* jcell = nullptr;
+  } sub;
 };
 
 // Cell-index entries of the tile-by-tile layout (jt_block): whole tiles and
@@ -117,8 +127,16 @@ static size_t jcell_count(int64_t N, int p, int Nx) {
   return (size_t)ceil_div(N, TILE_ROWS) * ceil_div(p, pc) * TILE_ROWS * pc;
 }
 
+// Bytes of the subsample buffers (RedWS::Sub) for nsub columns.
+static size_t sub_ws_bytes(int64_t N, int n, int nsub, int Nx) {
+  if (nsub <= 0) return 0;
+  const size_t pn = (size_t)nsub * (Nx > 0 ? Nx : 1), zn = (size_t)2 * n * nsub;
+  return arena_bytes(pn, 8) * 2 + arena_bytes(nsub, 8) + arena_bytes(zn, 8) +
+         2 * arena_bytes(zn, 8) + arena_bytes(pn, 8) + arena_bytes(jcell_count(N, nsub, Nx), 2);
+}
+
 size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df, int* gx_proj,
-                    int* gx_gram, const int* tune = nullptr) {
+                    int* gx_gram, const int* tune = nullptr, int nsub = 0) {
   const int n2 = 2 * n, nn = n * n;
   const int chunks = project_chunks(p, Nx > 0 ? Nx : 3);
   // the FP32-based path sizes its grids by the context's launch-shape knobs
@@ -137,16 +155,17 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
          arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
-                   2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8)
+                   2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) +
+                   sub_ws_bytes(N, n, nsub, Nx)
              : 0);
 }
 
 vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w,
-                 bool df = false) {
+                 bool df = false, int nsub = 0) {
   const int n2 = 2 * n, nn = n * n;
   size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
   size_t bytes = red_ws_bytes(ctx->num_sms, N, n, p, Nx, nrows, df, &w.gx_proj, &w.gx_gram,
-                              ctx->tune);
+                              ctx->tune, df ? nsub : 0);
   size_t part_d = std::max<size_t>((size_t)w.gx_proj * n2 * p,
                                    std::max<size_t>((size_t)w.gx_gram * 12 * nn * 2,
                                                     (size_t)w.gx_gram * n2 * n2));
@@ -177,6 +196,19 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.F2 = df ? a.take<float2>(pn) : nullptr;
+  w.sub = RedWS::Sub();
+  if (df && nsub > 0) {
+    const size_t ps = (size_t)nsub * (Nx > 0 ? Nx : 1), zs = (size_t)n2 * nsub;
+    w.sub.nsub = nsub;
+    w.sub.counts = a.take<unsigned long long>(ps);
+    w.sub.F = a.take<double>(ps);
+    w.sub.Efield = a.take<double>(nsub);
+    w.sub.Zs = a.take<double>(zs);
+    w.sub.Z2 = a.take<float2>(zs);
+    w.sub.Zh2 = a.take<float2>(zs);
+    w.sub.F2 = a.take<float2>(ps);
+    w.sub.jcell = a.take<uint16_t>(jcell_count(N, nsub, Nx));
+  }
   return VP_OK;
 }
 
@@ -252,7 +284,7 @@ struct Red {
 };
 
 vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, int nrows,
-                    cudaStream_t st, Red& R, bool df = false) {
+                    cudaStream_t st, Red& R, bool df = false, int nsub = 0) {
   R.ctx = ctx;
   R.df = df;
   R.N = N;
@@ -260,9 +292,26 @@ vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, i
   R.p = p;
   R.st = st;
   if (grid) R.g = make_gridc(*grid, N);
-  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df));
+  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df, nsub));
   if (grid) VP_CUDA(cudaMemsetAsync(R.w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
+  if (grid && R.w.sub.nsub)
+    VP_CUDA(cudaMemsetAsync(R.w.sub.counts, 0, sizeof(unsigned long long) * nsub * grid->Nx, st));
   return VP_OK;
+}
+
+// The Red of the subsample: the subset's per-sample buffers, the rest shared.
+Red sub_red(const Red& R) {
+  Red Rs = R;
+  const RedWS::Sub& b = R.w.sub;
+  Rs.p = b.nsub;
+  Rs.w.counts = b.counts;
+  Rs.w.F = b.F;
+  Rs.w.Efield = b.Efield;
+  Rs.w.Z2 = b.Z2;
+  Rs.w.Zh2 = b.Zh2;
+  Rs.w.F2 = b.F2;
+  Rs.w.jcell = b.jcell;
+  return Rs;
 }
 }  // namespace
 
@@ -398,6 +447,7 @@ struct DFStep {
   double* kstate;
   cudaStream_t st;
   const void* Qm = nullptr;  // rows the fixed point evaluates at (Q_half, or Q0 when frozen)
+  Red Rs;                    // parameter subsample of the basis stages (Rs.p = 0: none)
   DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt, double* ks,
          cudaStream_t s);
   vp_status pre(double* trace_step);
@@ -414,7 +464,31 @@ struct DFStep {
 // velocity, Cayley retraction, re-orthonormalisation).
 DFStep::DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt,
                double* ks, cudaStream_t s)
-    : ctx(c), R(r), Q(q), Z(z), dt(d), o(opt), kstate(ks), st(s) {}
+    : ctx(c), R(r), Q(q), Z(z), dt(d), o(opt), kstate(ks), st(s) {
+  Rs = sub_red(R);
+  Rs.w.sub.idx = opt.sub_idx;
+}
+
+// scale X(Q2, Zsrc) of the basis stage into out, on all samples or on the
+// parameter subsample (field and basis kernels on the selected columns)
+static vp_status basis_stage(DFStep& S, const void* Q2, const double* Zsrc, double scale,
+                             void* M, void* out, bool field_ready) {
+  vp_ctx* ctx = S.ctx;
+  cudaStream_t st = S.st;
+  const int n = S.R.n;
+  if (S.Rs.p > 0) {
+    RedDF Ds{S.Rs, ctx, st, S.R.N, n, S.Rs.p, S.o.arith};
+    VP_K(VP_K_SUBSET, gather_cols(2 * n, S.R.p, Zsrc, S.o.sub_idx, S.Rs.p, S.R.w.sub.Zs,
+                                  ctx->d_status, st));
+    Ds.field(Q2, S.R.w.sub.Zs, nullptr);
+    Ds.basis_velocity(Q2, S.R.w.sub.Zs, scale, M, out);
+  } else {
+    RedDF D{S.R, ctx, st, S.R.N, n, S.R.p, S.o.arith};
+    if (!field_ready) D.field(Q2, Zsrc, nullptr);
+    D.basis_velocity(Q2, Zsrc, scale, M, out);
+  }
+  return VP_OK;
+}
 
 vp_status DFStep::pre(double* trace_step) {
   RedWS& w = R.w;
@@ -432,7 +506,10 @@ vp_status DFStep::pre(double* trace_step) {
                                  nullptr, ctx->d_status, st));
   }
   D.split(Q, Q0);
-  D.field(Q0, Z, nullptr);
+  // the field of all samples at the entering state serves the energies and,
+  // without a subsample, the basis stage
+  const bool full_field = Rs.p == 0 || (trace_step && o.arith != 2);
+  if (full_field) D.field(Q0, Z, nullptr);
   if (trace_step && o.arith != 2) {
     D.gv(Q0, w.GVraw);
     VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Z, w.Efield, trace_step, trace_step + 1, 2, nullptr,
@@ -440,8 +517,8 @@ vp_status DFStep::pre(double* trace_step) {
   }
   Qm = Q0;
   if (!o.freeze_basis) {
-    D.basis_velocity(Q0, Z, 0.5 * dt, M, xih);  // xi_half = dt/2 X(Q0, Z0)
-    D.cayley(Q0, xih, nullptr, Qh);             // Q_half = R_Q0(xi_half)
+    VP_TRY(basis_stage(*this, Q0, Z, 0.5 * dt, M, xih, full_field));  // xi_half = dt/2 X(Q0, Z0)
+    D.cayley(Q0, xih, nullptr, Qh);                                   // Q_half = R_Q0(xi_half)
     Qm = Qh;
   }
   D.gv(Qm, w.GVraw);
@@ -494,8 +571,7 @@ vp_status DFStep::post() {
   VP_K(VP_K_AXPY, axpy(zsz, dt, w.k, w.Z0, w.Z1, st));
   if (kstate) VP_CUDA(cudaMemcpyAsync(kstate, w.k, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
   if (!o.freeze_basis) {
-    D.field(Qh, w.Ze, nullptr);
-    D.basis_velocity(Qh, w.Ze, 1.0, M, Xp);  // X(Q_half, Z_mid)
+    VP_TRY(basis_stage(*this, Qh, w.Ze, 1.0, M, Xp, false));  // X(Q_half, Z_mid)
     D.grams({Q0, xih, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
     const int nn = n * n;
     VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
@@ -704,7 +780,11 @@ vp_status step_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, 
   if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
     return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p exceeds 25600");
   InstanceStep* is = new InstanceStep();
-  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, is->R, true);
+  if (opts->nsub != 0 && (opts->nsub < n || opts->nsub > p || !opts->sub_idx)) {
+    delete is;
+    return vp_fail(ctx, VP_EINVAL, "subsample outside [n, p] or no indices");
+  }
+  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, is->R, true, opts->nsub);
   if (s != VP_OK) {
     delete is;
     return s;
@@ -730,7 +810,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
-    "k_init", "k_load"};
+    "k_init", "k_load", "k_subset"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1227,6 +1307,20 @@ vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const doubl
   return init_csvd_impl(ctx, N, p, 1, n, -1.0, X0, V0, Q, Z, sigma, nullptr, st);
 }
 
+vp_status vp_param_subsample(vp_ctx* ctx, int32_t n, int32_t p, const double* Z0, int32_t p_max,
+                             double tol, int32_t* idx, int32_t* count, void* stream) {
+  VP_ENTER();
+  if (n < 1 || p < 1 || p > 1024 || p_max < 1 || !Z0 || !idx || !count || !(tol >= 0.0))
+    return vp_fail(ctx, VP_EINVAL, "subsample arguments (n %d, p %d, p_max %d)", n, p, p_max);
+  int32_t* d_count = reinterpret_cast<int32_t*>(ctx->d_status) + 4;  // spare words of the status block
+  VP_K(VP_K_SUBSET, param_subsample(2 * n, p, Z0, std::min(p_max, p), tol, idx, d_count, st));
+  VP_LAUNCHED();
+  VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 4, d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  VP_CUDA(cudaStreamSynchronize(st));
+  *count = ctx->h_pinned[4];
+  return VP_OK;
+}
+
 vp_status vp_init_csvd_rank(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, int32_t n_max,
                             double tail_tol, const double* X0, const double* V0, double* Q,
                             double* Z, double* sigma, int32_t* n_out, void* stream) {
@@ -1247,16 +1341,23 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 0, 0};
+  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 0, 0, 0, nullptr};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
   if (o.arith < 0 || o.arith > 2) return vp_fail(ctx, VP_EINVAL, "arith must be 0, 1 or 2");
   if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
     return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p = %lld exceeds 25600 (shared memory of the "
                    "fixed-point update)", (long long)(4 * n * n + 2 * n * p));
+  if (o.nsub != 0) {
+    if (o.arith == 0)
+      return vp_fail(ctx, VP_EUNSUPPORTED, "the parameter subsample needs arith 1 or 2");
+    if (o.nsub < n || o.nsub > p || !o.sub_idx)
+      return vp_fail(ctx, VP_EINVAL, "subsample of %d columns outside [n, p] = [%d, %d] or no indices",
+                     o.nsub, n, p);
+  }
   const bool df = o.arith != 0;
   Red R;
-  VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df));
+  VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df, o.nsub));
   if (df) return basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st);
   RedWS& w = R.w;
   double *M = w.rows[0], *xih = w.rows[1], *Qh = w.rows[2], *Xp = w.rows[3], *xi1 = w.rows[4];

@@ -349,6 +349,10 @@ void energies(int n, int p, const double* GVraw, const double* Z, const double* 
               double* E_out, double* H_out, int64_t stride, const double2* QhQ, double* resid,
               int* status, cudaStream_t st);
 void lowdin(int n, const double2* G, double2* C, int* status, cudaStream_t st);
+void gather_cols(int rows, int p, const double* Z, const int32_t* idx, int nsub, double* Zs,
+                 int* status, cudaStream_t st);
+void param_subsample(int rows, int p, const double* Z, int p_max, double tol, int32_t* idx,
+                     int32_t* count, cudaStream_t st);
 void dense_init();
 void pic_init();
 

@@ -220,3 +220,36 @@ def test_prk2_large_rank_parity(ctx, sh, arith):
     Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
     UZ = U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy()
     assert rel(UZ, Uo @ Zo) < (TOL if arith < 2 else 1e-5)
+
+
+# ------------------------------------------------------- parameter subsample
+@pytest.mark.parametrize("p,pmax,tol", [(37, 9, 0.0), (64, 64, 0.0), (200, 50, 0.3), (5, 3, 0.0)])
+def test_param_subsample_parity(ctx, p, pmax, tol):
+    """Greedy subsample of Sec. 4.1 on the device = the oracle's (indices exact)."""
+    rng = np.random.Generator(np.random.PCG64(p))
+    Z = rng.standard_normal((12, p))
+    idx = ctx.param_subsample(T(Z), pmax, tol).cpu().numpy()
+    ref = reduced.param_subsample(Z, pmax, tol)
+    assert list(idx) == list(ref)
+
+
+@pytest.mark.parametrize("arith", [1, 2])
+def test_prk2_subsample_parity(ctx, arith):
+    """Basis evolution on a parameter subsample (Sec. 4.1), coefficients on all
+    samples: two steps against the oracle's subset step."""
+    g, grid, U, Z = state(N=3001, p=37, n=5, Nx=64)
+    sub = reduced.param_subsample(Z, 12)
+    dt = 0.05
+    Qd, Zd = T(q_storage(U)), T(Z)
+    subd = torch.tensor(sub, dtype=torch.int32, device="cuda:0")
+    tr, it = ctx.basis_update(grid, Qd, Zd, dt, 2, arith=arith, sub=subd, reortho=arith == 2)
+    ctx.sync_status()
+    Uo, Zo = U, Z
+    for _ in range(2):
+        Uo, Zo, _ = reduced.prk2_step(Uo, Zo, dt, g, sub=sub)
+    UZ = U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy()
+    assert rel(UZ, Uo @ Zo) < (TOL if arith == 1 else 1e-5)
+    # the subsample changes the basis velocity: the full step differs
+    a = reduced.prk2_step(U, Z, dt, g)
+    b = reduced.prk2_step(U, Z, dt, g, sub=sub)
+    assert rel(a[0] @ a[1], b[0] @ b[1]) > 1e-8
