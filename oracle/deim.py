@@ -4,8 +4,10 @@ g^DD_i = U_V^T V_r^i
        + m_p^-1 U_X^T diag(grad Lambda^0(X_r^i) Phi^i_DMD) P (P^T Psi)^-T Psi^T M_q.
 
 The DEIM basis Psi (N x d), the selection matrix P (N x d, columns e_idx) and
-the DMD potentials Phi_DMD (p x Nx) are inputs; their construction (DMD,
-DEIM snapshots, greedy indices) is outside this function.
+the DMD potentials Phi_DMD (p x Nx) are inputs of the gradient.  The DEIM
+construction of Sec. 4.2 is below: snapshot columns Lambda^0(X_r) Phi (eq.
+Ydeim), the basis of the first d left singular vectors, and the greedy
+interpolation indices.
 """
 from __future__ import annotations
 
@@ -48,3 +50,37 @@ def deim_gradient(U, Z, idx, c, Phi_dmd, g):
     """Full g^DD = U_V^T V_r + nonlinear part."""
     _, UV = reduced.split(U)
     return UV.T @ (UV @ Z) + deim_gradient_X(U, Z, idx, c, Phi_dmd, g)
+
+
+# --------------------------------------------------------------------------
+# DEIM construction (Sec. 4.2, eq. Ydeim and the greedy index selection)
+# --------------------------------------------------------------------------
+def potential_at_particles(X: np.ndarray, Phi: np.ndarray, g: pic.Grid) -> np.ndarray:
+    """Lambda^0(X) Phi: the P1 interpolant of the nodal potential Phi at every
+    particle (a column of eq. Ydeim).  X (N,) or (p, N), Phi (Nx,) or (p, Nx)."""
+    X = np.atleast_2d(X)
+    Phi = np.atleast_2d(Phi)
+    j, s = pic.cell_and_fraction(X, g)
+    j1 = (j + 1) % g.Nx
+    return np.take_along_axis(Phi, j, axis=1) * (1.0 - s) + np.take_along_axis(Phi, j1, axis=1) * s
+
+
+def deim_basis(Y: np.ndarray, d: int) -> tuple[np.ndarray, np.ndarray]:
+    """First d left singular vectors of the snapshot matrix Y (N x m) and all
+    singular values."""
+    Usv, sv, _ = np.linalg.svd(Y, full_matrices=False)
+    return Usv[:, :d], sv
+
+
+def deim_indices(Psi: np.ndarray) -> np.ndarray:
+    """Greedy DEIM interpolation indices for the ordered basis Psi (N x d): the
+    first index is where |psi_1| is largest; index k is where the residual of
+    psi_k after interpolating it from the first k-1 basis vectors at the first
+    k-1 indices is largest in magnitude (ties: lowest row)."""
+    N, d = Psi.shape
+    idx = [int(np.argmax(np.abs(Psi[:, 0])))]
+    for k in range(1, d):
+        c = np.linalg.solve(Psi[idx, :k], Psi[idx, k])
+        r = Psi[:, k] - Psi[:, :k] @ c
+        idx.append(int(np.argmax(np.abs(r))))
+    return np.array(idx, dtype=np.int64)
