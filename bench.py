@@ -370,6 +370,58 @@ def batched_measure(args, ctx, torch, dev, flush) -> dict:
             "kernel_launches_per_step": (info["launches"] - l0) / S}
 
 
+def subsample_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
+    """The bench workload with the basis evolution on a greedy parameter
+    subsample of 16 of the 64 samples (Sec. 4.1), double-float row work."""
+    from paper_2201_05555_gb300 import make_grid
+    wl, X0, V0 = initial_state(0)
+    Q, Z, _ = ctx.init_csvd(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev),
+                            wl.n2 // 2)
+    sub = ctx.param_subsample(Z, 16)
+    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    K = torch.zeros_like(Z)
+    for _ in range(3):
+        ctx.basis_update(grid, Q, Z, wl.dt, 1, arith=ARITH, kstate=K, sub=sub)
+    stream = torch.cuda.current_stream(dev)
+    ev = _events(torch, steps)
+    for s_ in range(steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        ctx.basis_update(grid, Q, Z, wl.dt, 1, arith=ARITH, kstate=K, sub=sub)
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return {"workload": "two-stream reduced model as the main line, basis evolution on a greedy "
+                        "parameter subsample of 16 of 64 samples",
+            "value": wl.N * wl.p / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "subsample": [int(i) for i in sub.cpu()]}
+
+
+def deim_build_measure(ctx, torch, dev, reps: int = 5) -> dict:
+    """DEIM construction (Sec. 4.2) at N = 1e5 particles: m = 8 x 11 snapshot
+    columns (8 sampled parameters over a window of 11 steps), d = 32: basis,
+    greedy indices and weights."""
+    N, m, d = 100_000, 88, 32
+    g = torch.Generator(device=dev)
+    g.manual_seed(W.BASE_SEED)
+    A = torch.linalg.qr(torch.randn(N, m, generator=g, device=dev, dtype=torch.float64))[0]
+    Y = (A * (0.85 ** torch.arange(m, device=dev, dtype=torch.float64))).T.contiguous()
+    Psi, _ = ctx.deim_basis(Y, d)  # warm-up
+    ctx.deim_indices(Psi)
+    stream = torch.cuda.current_stream(dev)
+    ev = _events(torch, reps)
+    for r in range(reps):
+        ev[r][0].record(stream)
+        Psi, _ = ctx.deim_basis(Y, d)
+        idx = ctx.deim_indices(Psi)
+        ctx.deim_weights(Psi, idx, -1.0 / N)
+        ev[r][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+    return {"workload": f"DEIM construction, N=1e5, m={m} snapshot columns, d={d}",
+            "ms_per_construction": ms, "snapshot_values_per_s": N * m / (ms / 1e3)}
+
+
 def served_measure(args, dev_index: int) -> dict:
     """Served form: Poisson arrivals of reduced-solve queries.  Each query:
     family uniform over {Landau, two-stream, bump-on-tail}, p uniform in
@@ -604,6 +656,8 @@ def ours(args, rank, world):
         line["full_order"] = full_order_measure(ctx, torch, dev, flush)
         line["precision_form"] = precision_measure(ctx, torch, dev, flush)
         line["batched"] = batched_measure(args, ctx, torch, dev, flush)
+        line["subsampled"] = subsample_measure(ctx, torch, dev, flush)
+        line["deim_build"] = deim_build_measure(ctx, torch, dev)
         line["served"] = served_measure(args, local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)

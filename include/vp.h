@@ -262,6 +262,34 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
                                  const int32_t* idx_dev, const double* c_dev,
                                  const double* phi_dev, double* gX_dev, void* stream);
 
+/* ------------------------------------------------------ DEIM construction */
+/* Sec. 4.2, eq. Ydeim: the snapshot columns Lambda^0(X) Phi, i.e. the P1
+ * interpolant of each sample's nodal potential at its particles.
+ * X_dev: p x N (ld ldx) positions (unwrapped), phi_dev: p x Nx potentials,
+ * Y_dev: p columns of length N (ld ldy). */
+vp_status vp_potential_at_particles(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p,
+                                    const double* X_dev, int64_t ldx, const double* phi_dev,
+                                    double* Y_dev, int64_t ldy, void* stream);
+/* DEIM basis: the first d left singular vectors of the snapshot matrix
+ * Y (N x m, stored as m columns of length N, ld ldy), written as d columns of
+ * length N (Psi_dev, d x N), from the Gram matrix Y^T Y (Jacobi): directions
+ * with singular values below ~1e-8 sigma_1 are not resolved.  sigma_dev
+ * (nullable): the m singular values, descending.  m <= 256, d <= min(m, 128),
+ * m d <= 25600.  A vanishing singular value among the first d gives
+ * VP_ENUMERIC through the status word. */
+vp_status vp_deim_basis(vp_ctx* ctx, int64_t N, int32_t m, const double* Y_dev, int64_t ldy,
+                        int32_t d, double* Psi_dev, double* sigma_dev, void* stream);
+/* Greedy DEIM interpolation indices for the ordered basis Psi (d x N): the
+ * first is the row where |psi_1| is largest, the k-th where the residual of
+ * psi_k interpolated from the first k-1 vectors at the first k-1 indices is
+ * largest (ties to the lowest row).  idx_dev: d int32.  d <= 128. */
+vp_status vp_deim_indices(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
+                          int32_t* idx_dev, void* stream);
+/* Weights of the DEIM-indexed gradient (eq. grHDD): c = (P^T Psi)^-T Psi^T M_q
+ * with equal particle charges M_q (all entries Mq).  c_dev: d doubles. */
+vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
+                          const int32_t* idx_dev, double Mq, double* c_dev, void* stream);
+
 /* -------------------------------------------------- deposit, no allocation */
 /* The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory (their pool or fixed memory plan owns it all,

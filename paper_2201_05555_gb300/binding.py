@@ -78,6 +78,11 @@ _SIGS = [
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     ("vp_profile_reset", _I32, [_P]),
     ("vp_kernel_name", C.c_char_p, [_I32]),
+    ("vp_potential_at_particles", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P, _I64,
+                                         _P]),
+    ("vp_deim_basis", _I32, [_P, _I64, _I32, _P, _I64, _I32, _P, _P, _P]),
+    ("vp_deim_indices", _I32, [_P, _I64, _I32, _P, _P, _P]),
+    ("vp_deim_weights", _I32, [_P, _I64, _I32, _P, _P, _D, _P, _P]),
     ("vp_param_subsample", _I32, [_P, _I32, _I32, _P, _I32, _D, _P, C.POINTER(_I32), _P]),
     ("vp_init_csvd_rank", _I32, [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P,
                                  C.POINTER(_I32), _P]),
@@ -328,6 +333,40 @@ class Context:
                                           _ptr(V0, name="V0"), _ptr(Q), _ptr(Z), _ptr(sig),
                                           self._stream()), "init_csvd")
         return Q, Z, sig
+
+    def potential_at_particles(self, grid: Grid, X: torch.Tensor, phi: torch.Tensor):
+        """Lambda^0(X) Phi per sample (p x N)."""
+        p, N = X.shape
+        Y = self._empty(p, N)
+        self._check(self.lib.vp_potential_at_particles(self.h, C.byref(grid), N, p,
+                                                       _ptr(X, name="X"), N, _ptr(phi, name="phi"),
+                                                       _ptr(Y), N, self._stream()),
+                    "potential_at_particles")
+        return Y
+
+    def deim_basis(self, Y: torch.Tensor, d: int):
+        """(Psi (d x N), sigma (m)) from the snapshot columns Y (m x N)."""
+        m, N = Y.shape
+        Psi, sig = self._empty(d, N), self._empty(m)
+        self._check(self.lib.vp_deim_basis(self.h, N, m, _ptr(Y, name="Y"), N, d, _ptr(Psi),
+                                           _ptr(sig), self._stream()), "deim_basis")
+        return Psi, sig
+
+    def deim_indices(self, Psi: torch.Tensor) -> torch.Tensor:
+        d, N = Psi.shape
+        idx = torch.empty(d, dtype=torch.int32, device=Psi.device)
+        self._check(self.lib.vp_deim_indices(self.h, N, d, _ptr(Psi, name="Psi"),
+                                             _ptr(idx, torch.int32, "idx"), self._stream()),
+                    "deim_indices")
+        return idx
+
+    def deim_weights(self, Psi: torch.Tensor, idx: torch.Tensor, Mq: float) -> torch.Tensor:
+        d, N = Psi.shape
+        c = self._empty(d)
+        self._check(self.lib.vp_deim_weights(self.h, N, d, _ptr(Psi, name="Psi"),
+                                             _ptr(idx, torch.int32, "idx"), Mq, _ptr(c),
+                                             self._stream()), "deim_weights")
+        return c
 
     def param_subsample(self, Z0: torch.Tensor, p_max: int, tol: float = 0.0) -> torch.Tensor:
         """Greedy parameter subsample (int32 device indices, in order of choice)."""

@@ -90,11 +90,6 @@ vp_status check_n(vp_ctx* ctx, int32_t n, int64_t N) {
   return VP_OK;
 }
 
-#define VP_TRY(x)                      \
-  do {                                 \
-    vp_status s_ = (x);                \
-    if (s_ != VP_OK) return s_;        \
-  } while (0)
 
 // Workspace of the reduced-model calls.
 struct RedWS {
@@ -997,6 +992,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   dense_init();
   df_init();
   init_kernels_init();
+  deim_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_pinned);
@@ -1364,7 +1360,6 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   const int64_t zsz = (int64_t)2 * n * p;
   const int64_t tstride = (int64_t)p * 2;
   int round = 4;
-  const int64_t qsz = N * 2 * n;
   for (int step = 0; step < nsteps; ++step) {
     // stage 1: field at (Q0, Z0); energies of the entering state
     R.field(Q, Z);

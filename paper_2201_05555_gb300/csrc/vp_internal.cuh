@@ -92,6 +92,12 @@ int vp_choose_rank(const double* sig, int p, int n_min, int n_max, double tol);
     if (e_ != cudaSuccess) return vp_cuda_check(ctx, e_, #call);   \
   } while (0)
 
+#define VP_TRY(x)               \
+  do {                          \
+    vp_status s_ = (x);         \
+    if (s_ != VP_OK) return s_; \
+  } while (0)
+
 #define VP_LAUNCHED()                                              \
   do {                                                             \
     cudaError_t e_ = cudaGetLastError();                           \
@@ -375,6 +381,7 @@ void init_launch_zeta(int64_t N, int p, int n, const double* Q, const double* X,
                       double2* part, int gx, cudaStream_t st);
 void init_launch_zeta_to_Z(int n, int p, const double2* zeta, double* Z, cudaStream_t st);
 void init_kernels_init();  // kernel attributes of init.cu
+void deim_init();          // kernel attributes of deim.cu
 // Particle loading (load.cu): eta p x 3, X and V p x N; mode 0 quiet start,
 // mode 1 Philox4x32-10 keyed by seed.
 void load_particles(int family, int mode, unsigned long long seed, double k, int64_t N, int p,
