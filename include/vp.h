@@ -290,6 +290,45 @@ vp_status vp_deim_indices(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_d
 vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
                           const int32_t* idx_dev, double Mq, double* c_dev, void* stream);
 
+/* ------------------------------------------------------------------- DMD */
+/* DMD of the electric potential (Sec. 4.2, Algorithm 1) on window data of
+ * the sampled parameters: Y, Y' (nx x m, stored as m columns of length nx;
+ * eq. DMD_potential_Y_time_parameter).  Truncated SVD Y = U S V^T with the
+ * singular values above max(tol, 1e-7) sigma_1 (at most r_max <= 64; *r_out
+ * receives r), from the Gram matrix Y^T Y (Jacobi), which resolves singular
+ * values down to ~1e-8 sigma_1 only.  Outputs (device, sized for r_max):
+ *   B = Y' V S^-1 (r columns of length nx) - the exact-DMD modes are B W;
+ *   Bpinv = (B^T B)^-1 B^T (r x nx, row-major);
+ *   A = U^T B (r x r), whose eigenvalues are the DMD eigenvalues;
+ *   S = A^1/2, the principal square root (Denman-Beavers), for half steps;
+ *   sigma (nullable): the m singular values of Y.
+ * Since Theta^+ = W^-1 Bpinv, the DMD potential Theta (Pi (.) lambda^(s/dt))
+ * with Pi = Theta^+ Phi equals B A^(s/dt) Bpinv Phi: whole and half steps use
+ * real powers of A and S.  An eigenvalue of A on the closed negative real
+ * axis (no real principal square root) gives VP_ENUMERIC.  nx <= 4096,
+ * m <= 256.  Synchronises `stream` (the rank goes to the host). */
+vp_status vp_dmd_fit(vp_ctx* ctx, int32_t nx, int32_t m, const double* Y_dev, const double* Yp_dev,
+                     double tol, int32_t r_max, int32_t* r_out, double* B_dev, double* Bpinv_dev,
+                     double* A_dev, double* S_dev, double* sigma_dev, void* stream);
+/* DMD coordinates beta_i = Bpinv Phi_i of q potentials (q x nx) -> beta (q x r);
+ * Pi_i = W^-1 beta_i. */
+vp_status vp_dmd_coords(vp_ctx* ctx, int32_t nx, int32_t r, const double* Bpinv_dev, int32_t q,
+                        const double* Phi_dev, double* beta_dev, void* stream);
+/* Gaussian radial basis interpolation (Sec. 4.2, coordinates of parameters
+ * outside the sample): through q points eta_s (q x dim) with values (q x K),
+ * kernel exp(-(eps |eta - eta_j|)^2), evaluated at p points eta (p x dim)
+ * into out (p x K).  q (q + K) doubles must fit in 200 KB. */
+vp_status vp_rbf_interpolate(vp_ctx* ctx, int32_t dim, int32_t q, const double* eta_s_dev,
+                             int32_t K, const double* values_dev, int32_t p, const double* eta_dev,
+                             double eps, double* out_dev, void* stream);
+/* DMD potential (eq. DMD_approx_potential_subset) at s = (ksteps + half / 2) dt
+ * after the last window state: Phi_i = B A^ksteps S^half beta_i for p
+ * coordinate rows beta (p x r) -> Phi (p x nx). */
+vp_status vp_dmd_potential(vp_ctx* ctx, int32_t nx, int32_t r, const double* B_dev,
+                           const double* A_dev, const double* S_dev, int32_t p,
+                           const double* beta_dev, int32_t ksteps, int32_t half, double* Phi_dev,
+                           void* stream);
+
 /* -------------------------------------------------- deposit, no allocation */
 /* The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory (their pool or fixed memory plan owns it all,

@@ -83,6 +83,11 @@ _SIGS = [
     ("vp_deim_basis", _I32, [_P, _I64, _I32, _P, _I64, _I32, _P, _P, _P]),
     ("vp_deim_indices", _I32, [_P, _I64, _I32, _P, _P, _P]),
     ("vp_deim_weights", _I32, [_P, _I64, _I32, _P, _P, _D, _P, _P]),
+    ("vp_dmd_fit", _I32, [_P, _I32, _I32, _P, _P, _D, _I32, C.POINTER(_I32), _P, _P, _P, _P, _P,
+                          _P]),
+    ("vp_dmd_coords", _I32, [_P, _I32, _I32, _P, _I32, _P, _P, _P]),
+    ("vp_rbf_interpolate", _I32, [_P, _I32, _I32, _P, _I32, _P, _I32, _P, _D, _P, _P]),
+    ("vp_dmd_potential", _I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _I32, _I32, _P, _P]),
     ("vp_param_subsample", _I32, [_P, _I32, _I32, _P, _I32, _D, _P, C.POINTER(_I32), _P]),
     ("vp_init_csvd_rank", _I32, [_P, _I64, _I32, _I32, _I32, _D, _P, _P, _P, _P, _P,
                                  C.POINTER(_I32), _P]),
@@ -367,6 +372,49 @@ class Context:
                                              _ptr(idx, torch.int32, "idx"), Mq, _ptr(c),
                                              self._stream()), "deim_weights")
         return c
+
+    def dmd_fit(self, Y: torch.Tensor, Yp: torch.Tensor, tol: float, r_max: int = 64) -> dict:
+        """DMD of window data Y, Y' (m x nx: m columns of length nx)."""
+        m, nx = Y.shape
+        B, Bp = self._empty(r_max, nx), self._empty(r_max, nx)
+        A, S, sig = self._empty(r_max * r_max), self._empty(r_max * r_max), self._empty(m)
+        r = _I32(0)
+        self._check(self.lib.vp_dmd_fit(self.h, nx, m, _ptr(Y, name="Y"), _ptr(Yp, name="Yp"), tol,
+                                        r_max, C.byref(r), _ptr(B), _ptr(Bp), _ptr(A), _ptr(S),
+                                        _ptr(sig), self._stream()), "dmd_fit")
+        k = r.value
+        return {"r": k, "B": B[:k].contiguous(), "Bpinv": Bp[:k].contiguous(),
+                "A": A[:k * k].view(k, k).contiguous(), "S": S[:k * k].view(k, k).contiguous(),
+                "sigma": sig}
+
+    def dmd_coords(self, fit: dict, Phi: torch.Tensor) -> torch.Tensor:
+        q, nx = Phi.shape
+        beta = self._empty(q, fit["r"])
+        self._check(self.lib.vp_dmd_coords(self.h, nx, fit["r"], _ptr(fit["Bpinv"]), q,
+                                           _ptr(Phi, name="Phi"), _ptr(beta), self._stream()),
+                    "dmd_coords")
+        return beta
+
+    def rbf_interpolate(self, eta_s: torch.Tensor, values: torch.Tensor, eta: torch.Tensor,
+                        eps: float) -> torch.Tensor:
+        q, dim = eta_s.shape
+        K = values.shape[1]
+        p = eta.shape[0]
+        out = self._empty(p, K)
+        self._check(self.lib.vp_rbf_interpolate(self.h, dim, q, _ptr(eta_s, name="eta_s"), K,
+                                                _ptr(values, name="values"), p,
+                                                _ptr(eta, name="eta"), eps, _ptr(out),
+                                                self._stream()), "rbf_interpolate")
+        return out
+
+    def dmd_potential(self, fit: dict, beta: torch.Tensor, ksteps: int, half: int) -> torch.Tensor:
+        p = beta.shape[0]
+        nx = fit["B"].shape[1]
+        Phi = self._empty(p, nx)
+        self._check(self.lib.vp_dmd_potential(self.h, nx, fit["r"], _ptr(fit["B"]), _ptr(fit["A"]),
+                                              _ptr(fit["S"]), p, _ptr(beta, name="beta"), ksteps,
+                                              half, _ptr(Phi), self._stream()), "dmd_potential")
+        return Phi
 
     def param_subsample(self, Z0: torch.Tensor, p_max: int, tol: float = 0.0) -> torch.Tensor:
         """Greedy parameter subsample (int32 device indices, in order of choice)."""
