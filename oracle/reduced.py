@@ -196,7 +196,7 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
               tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
               retract=retraction, grad_fn=None, stall_floor: float = 1e-3,
               stall_ratio: float = 0.5, k_init: np.ndarray | None = None,
-              sub: np.ndarray | None = None):
+              sub: np.ndarray | None = None, coeff_grad=None):
     """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
 
     info: 'iters' (fixed-point evaluations), 'resid' (last relative update),
@@ -207,6 +207,9 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     None starts from k = 0, a warm start passes the previous step's k2.
     sub: parameter subsample (Sec. 4.1): the basis velocities use only the
     columns sub of Z (and of the gradient); the coefficients use all columns.
+    coeff_grad: optional map (U, Z) -> g (2n x p) replacing U^T G in the
+    coefficient stage (the DMD-DEIM gradient of eq. grHDD, Sec. 4.3); the
+    basis stages keep the gradient of the field.
     """
     cols = slice(None) if sub is None else np.asarray(sub)
     info = {}
@@ -227,8 +230,11 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     r_prev = [np.inf, np.inf]  # r_{m-1}, r_{m-2}
     stalled = False
     for it in range(1, maxit + 1):
-        G = _gradient(U_half, Z0 + 0.5 * dt * k, g, grad_fn)
-        k_new = apply_J(U_half.T @ G)
+        if coeff_grad is None:
+            G = _gradient(U_half, Z0 + 0.5 * dt * k, g, grad_fn)
+            k_new = apply_J(U_half.T @ G)
+        else:
+            k_new = apply_J(coeff_grad(U_half, Z0 + 0.5 * dt * k))
         diff = np.linalg.norm(k_new - k)
         nk = np.linalg.norm(k_new)
         k = k_new
