@@ -285,6 +285,20 @@ vp_status vp_deim_basis(vp_ctx* ctx, int64_t N, int32_t m, const double* Y_dev, 
  * largest (ties to the lowest row).  idx_dev: d int32.  d <= 128. */
 vp_status vp_deim_indices(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
                           int32_t* idx_dev, void* stream);
+/* Adaptive update of the DEIM indices (Sec. 4.2, eq. indices_adaptive_DEIM).
+ * On entry idx_dev holds the indices of the previous basis Psi_prev (d x N);
+ * the n_up positions k whose vectors rotated most, i.e. with the smallest
+ * |psi_k . psi_prev_k| (absolute value: singular vectors carry an arbitrary
+ * sign; ties to the lowest k), are renewed in increasing k by the greedy rule
+ * of vp_deim_indices (interpolation residual of psi_k from psi_1..psi_{k-1}
+ * at the indices then held), never taking a row held at another position;
+ * the other positions keep their rows.  The printed arg-max of the inner
+ * products would pick the least-rotated vectors while the paper's text asks
+ * for the most-rotated; this reading follows the text.  n_up = d is the
+ * greedy procedure, n_up = 0 keeps the indices.  0 <= n_up <= d <= 128. */
+vp_status vp_deim_indices_update(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
+                                 const double* Psi_prev_dev, int32_t n_up, int32_t* idx_dev,
+                                 void* stream);
 /* Weights of the DEIM-indexed gradient (eq. grHDD): c = (P^T Psi)^-T Psi^T M_q
  * with equal particle charges M_q (all entries Mq).  c_dev: d doubles. */
 vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_dev,
@@ -300,13 +314,15 @@ vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi_d
  *   B = Y' V S^-1 (r columns of length nx) - the exact-DMD modes are B W;
  *   Bpinv = (B^T B)^-1 B^T (r x nx, row-major);
  *   A = U^T B (r x r), whose eigenvalues are the DMD eigenvalues;
- *   S = A^1/2, the principal square root (Denman-Beavers), for half steps;
+ *   S = Re(A^1/2) with the principal power of every eigenvalue (complex
+ *     Schur form of A, triangular square root), for half steps;
  *   sigma (nullable): the m singular values of Y.
- * Since Theta^+ = W^-1 Bpinv, the DMD potential Theta (Pi (.) lambda^(s/dt))
- * with Pi = Theta^+ Phi equals B A^(s/dt) Bpinv Phi: whole and half steps use
- * real powers of A and S.  An eigenvalue of A on the closed negative real
- * axis (no real principal square root) gives VP_ENUMERIC.  nx <= 4096,
- * m <= 256.  Synchronises `stream` (the rank goes to the host). */
+ * Since Theta^+ = W^-1 Bpinv, the real part of the DMD potential
+ * Theta (Pi (.) lambda^(s/dt)) with Pi = Theta^+ Phi equals
+ * B Re(A^(s/dt)) Bpinv Phi: whole steps use real powers of A, half steps S.
+ * An eigenvalue on the negative real axis (a mode that changes sign every
+ * step) contributes zero at half steps on either side of the branch cut.
+ * nx <= 4096, m <= 256.  Synchronises `stream` (the rank goes to the host). */
 vp_status vp_dmd_fit(vp_ctx* ctx, int32_t nx, int32_t m, const double* Y_dev, const double* Yp_dev,
                      double tol, int32_t r_max, int32_t* r_out, double* B_dev, double* Bpinv_dev,
                      double* A_dev, double* S_dev, double* sigma_dev, void* stream);
@@ -328,6 +344,59 @@ vp_status vp_dmd_potential(vp_ctx* ctx, int32_t nx, int32_t r, const double* B_d
                            const double* A_dev, const double* S_dev, int32_t p,
                            const double* beta_dev, int32_t ksteps, int32_t half, double* Phi_dev,
                            void* stream);
+
+/* ------------------------------------------ DMD-DEIM reduced dynamics */
+/* The DMD-DEIM reduced model of eq. UZredhyp integrated by the partitioned
+ * Runge-Kutta scheme of Sec. 5 (eq. discrete_dynROM) following Algorithm 2.
+ * A vp_hyper object owns the sliding windows and the DMD and DEIM operators
+ * of one reduced problem (grid, N, n, p) with a parameter subsample.  Each
+ * interval tau (one call step):
+ *  1. the field of the sampled parameters at the entering state (U, Z_sub)
+ *     gives the potentials Phi^i_{tau-1} and the DEIM data columns
+ *     Lambda^0(X_r^i) Phi^i (eq. Ydeim); both enter windows of T + 1 entries;
+ *  2. while the windows hold T entries or fewer the interval is the
+ *     subsampled reduced step (vp_basis_update with the subsample);
+ *  3. afterwards: DMD of the potential windows (vp_dmd_fit, tolerance
+ *     dmd_tol), coordinates of the sampled parameters from Phi_{tau-1},
+ *     Gaussian RBF interpolation to all p parameters (width 0.3 / mean
+ *     nearest-neighbour distance of the sampled parameters), the DMD potential
+ *     at the coefficient stage time t_{tau-1} + dt/2; the DEIM basis of the
+ *     data window (d vectors), its indices (all of them on the first DMD-DEIM
+ *     interval and every k_deim intervals after it, else n_up of them by
+ *     vp_deim_indices_update) and weights; then the PRK2 step whose
+ *     coefficient stage uses the DMD-DEIM gradient g^DD of eq. grHDD (its X
+ *     part needs the d DEIM rows of U only, independent of N), while the basis
+ *     stages keep the field of the sampled parameters (eq. UZhypred_basis).
+ * The FP32-based forms only (arith 1 or 2).  The DMD rank is read on the
+ * host once per interval (one stream synchronisation). */
+typedef struct vp_hyper vp_hyper;
+typedef struct vp_hyper_opts {
+  int32_t nsub;            /* sampled parameters p* (n <= p* <= p) */
+  const int32_t* sub_idx;  /* device, p* column indices (e.g. vp_param_subsample) */
+  int32_t dim;             /* parameter dimension */
+  const double* eta;       /* device, p x dim parameters (RBF coordinates) */
+  int32_t T;               /* window length (T >= 1, p* T <= 256) */
+  int32_t d;               /* DEIM points (d <= min(p* (T + 1), 128)) */
+  int32_t n_up;            /* renewed indices per interval (0 .. d) */
+  int32_t k_deim;          /* all indices renewed every k_deim intervals (>= 1) */
+  double dmd_tol;          /* Algorithm 1 tolerance relative to sigma_1 */
+  int32_t r_max;           /* DMD rank cap (<= 64) */
+} vp_hyper_opts;
+vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          const vp_hyper_opts* opts, vp_hyper** out);
+/* nsteps intervals from (Q, Z) in place; opts, trace, iters and kstate as in
+ * vp_basis_update (opts->nsub / sub_idx are ignored: the object's subsample
+ * is used).  Intervals continue the object's windows across calls. */
+vp_status vp_hyper_step(vp_hyper* h, double* Q_dev, double* Z_dev, double dt, int32_t nsteps,
+                        const vp_step_opts* opts, double* trace_dev, int32_t* iters_dev,
+                        double* kstate_dev, void* stream);
+/* State of the last interval: intervals done, DMD-DEIM intervals done, DMD
+ * rank (0 before the first DMD-DEIM interval); idx_dev (nullable, d int32)
+ * receives the current DEIM indices, Phi_dev (nullable, p x Nx) the DMD
+ * potentials at the last coefficient stage time. */
+vp_status vp_hyper_info(vp_hyper* h, int32_t* intervals, int32_t* hyper_intervals, int32_t* r_dmd,
+                        int32_t* idx_dev, double* Phi_dev, void* stream);
+vp_status vp_hyper_destroy(vp_hyper* h);
 
 /* -------------------------------------------------- deposit, no allocation */
 /* The paper has no counterpart to this call; it exists for callers that may
@@ -540,7 +609,7 @@ typedef enum vp_kernel {
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
-  VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_COUNT
+  VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

@@ -17,6 +17,8 @@ from .binding import (  # noqa: F401
     make_grid,
     Server,
     Batch,
+    Hyper,
+    HyperOpts,
     Query,
     Result,
     deposit_cic_noalloc,

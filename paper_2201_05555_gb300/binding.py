@@ -40,6 +40,11 @@ class StepOpts(C.Structure):
                 ("sub_idx", _P)]
 
 
+class HyperOpts(C.Structure):
+    _fields_ = [("nsub", _I32), ("sub_idx", _P), ("dim", _I32), ("eta", _P), ("T", _I32),
+                ("d", _I32), ("n_up", _I32), ("k_deim", _I32), ("dmd_tol", _D), ("r_max", _I32)]
+
+
 def make_grid(N: int, Nx: int, L: float, q: float = -1.0, m: float = 1.0,
               omega: float | None = None) -> Grid:
     """q = -1, m = 1, weights omega = L/N (mean density 1); the background
@@ -82,6 +87,12 @@ _SIGS = [
                                          _P]),
     ("vp_deim_basis", _I32, [_P, _I64, _I32, _P, _I64, _I32, _P, _P, _P]),
     ("vp_deim_indices", _I32, [_P, _I64, _I32, _P, _P, _P]),
+    ("vp_deim_indices_update", _I32, [_P, _I64, _I32, _P, _P, _I32, _P, _P]),
+    ("vp_hyper_create", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, C.POINTER(HyperOpts),
+                               C.POINTER(_P)]),
+    ("vp_hyper_step", _I32, [_P, _P, _P, _D, _I32, C.POINTER(StepOpts), _P, _P, _P, _P]),
+    ("vp_hyper_info", _I32, [_P, _P, _P, _P, _P, _P, _P]),
+    ("vp_hyper_destroy", _I32, [_P]),
     ("vp_deim_weights", _I32, [_P, _I64, _I32, _P, _P, _D, _P, _P]),
     ("vp_dmd_fit", _I32, [_P, _I32, _I32, _P, _P, _D, _I32, C.POINTER(_I32), _P, _P, _P, _P, _P,
                           _P]),
@@ -122,7 +133,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
-           "k_load", "k_subset"]
+           "k_load", "k_subset", "k_hyper", "k_deim_round"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -364,6 +375,23 @@ class Context:
                                              _ptr(idx, torch.int32, "idx"), self._stream()),
                     "deim_indices")
         return idx
+
+    def deim_indices_update(self, Psi: torch.Tensor, Psi_prev: torch.Tensor, idx_prev: torch.Tensor,
+                            n_up: int) -> torch.Tensor:
+        """Indices of Psi inheriting idx_prev except at the n_up most rotated positions."""
+        d, N = Psi.shape
+        idx = idx_prev.to(torch.int32).clone()
+        self._check(self.lib.vp_deim_indices_update(self.h, N, d, _ptr(Psi, name="Psi"),
+                                                    _ptr(Psi_prev, name="Psi_prev"), n_up,
+                                                    _ptr(idx, torch.int32, "idx"), self._stream()),
+                    "deim_indices_update")
+        return idx
+
+    def hyper(self, grid: Grid, N: int, n: int, p: int, sub: torch.Tensor, eta: torch.Tensor,
+              T: int = 3, d: int = 32, n_up: int = 12, k_deim: int = 3, dmd_tol: float = 1e-5,
+              r_max: int = 64) -> "Hyper":
+        """DMD-DEIM reduced dynamics (Algorithm 2) of one reduced problem."""
+        return Hyper(self, grid, N, n, p, sub, eta, T, d, n_up, k_deim, dmd_tol, r_max)
 
     def deim_weights(self, Psi: torch.Tensor, idx: torch.Tensor, Mq: float) -> torch.Tensor:
         d, N = Psi.shape
@@ -653,6 +681,63 @@ class BatchItem(C.Structure):
     _fields_ = [("grid", Grid), ("N", _I64), ("n", _I32), ("p", _I32), ("dt", _D),
                 ("Q_dev", _P), ("Z_dev", _P), ("kstate_dev", _P), ("trace_dev", _P),
                 ("trace_capacity", _I32), ("iters_dev", _P)]
+
+
+class Hyper:
+    """vp_hyper: sliding windows and DMD / DEIM operators of one reduced
+    problem, stepped by vp_hyper_step (Algorithm 2)."""
+
+    def __init__(self, ctx: "Context", grid: Grid, N: int, n: int, p: int, sub: torch.Tensor,
+                 eta: torch.Tensor, T: int, d: int, n_up: int, k_deim: int, dmd_tol: float,
+                 r_max: int):
+        self.ctx = ctx
+        self.grid = grid
+        self.p, self.Nx, self.d = p, grid.Nx, d
+        self._sub = sub.to(torch.int32).contiguous()
+        eta = eta.to(torch.float64).reshape(p, -1).contiguous()
+        self._eta = eta
+        opts = HyperOpts(self._sub.numel(), _ptr(self._sub, torch.int32, "sub"), eta.shape[1],
+                         _ptr(eta, name="eta"), T, d, n_up, k_deim, dmd_tol, r_max)
+        h = _P()
+        ctx._check(ctx.lib.vp_hyper_create(ctx.h, C.byref(grid), N, n, p, C.byref(opts),
+                                           C.byref(h)), "hyper_create")
+        self.h = h
+
+    def step(self, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int, tol: float = 1e-9,
+             maxit: int = 100, arith: int = 1, reortho: bool = False, trace: bool = True,
+             iters: bool = True, kstate: torch.Tensor | None = None, stall_floor: float = 1e-3,
+             stall_ratio: float = 0.5):
+        """nsteps intervals in place on Q (N x 2n) and Z (2n x p); returns (trace, iters)."""
+        ctx = self.ctx
+        tr = ctx._empty(max(nsteps, 1), self.p, 2) if trace else None
+        it = ctx._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
+        opts = StepOpts(tol, maxit, 0, stall_floor, stall_ratio, int(arith), int(reortho), 0, None)
+        ctx._check(ctx.lib.vp_hyper_step(self.h, _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
+                                         C.byref(opts), _ptr(tr), _ptr(it, torch.int32),
+                                         _ptr(kstate, name="kstate"), ctx._stream()), "hyper_step")
+        return tr, it
+
+    def info(self) -> dict:
+        ctx = self.ctx
+        a, b, r = _I32(0), _I32(0), _I32(0)
+        idx = ctx._empty(self.d, dtype=torch.int32)
+        phi = ctx._empty(self.p, self.Nx)
+        ctx._check(ctx.lib.vp_hyper_info(self.h, C.byref(a), C.byref(b), C.byref(r),
+                                         _ptr(idx, torch.int32), _ptr(phi), ctx._stream()),
+                   "hyper_info")
+        return {"intervals": a.value, "hyper_intervals": b.value, "r": r.value, "idx": idx,
+                "phi_half": phi}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.vp_hyper_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -6,9 +6,9 @@
 // DMD of the potential (Algorithm 1): with the truncated SVD Y = U S V^T of
 // the window data, B = Y' V S^-1 and A = U^T B, the exact-DMD prediction
 // Theta (Pi (.) lambda^(s/dt)) with Theta = B W, A W = W Lambda, equals
-// B A^(s/dt) B^+ Phi (Theta^+ = W^-1 B^+), so whole and half steps need only
-// real powers of A and its principal square root (Denman-Beavers iteration),
-// no complex eigen-decomposition.
+// B A^(s/dt) B^+ Phi (Theta^+ = W^-1 B^+), so whole steps need only real
+// powers of A and half steps the real part of its principal square root
+// (from the complex Schur form of the small r x r matrix A).
 //
 // Layouts: snapshot matrix Y stored column by column (m x N, leading
 // dimension ldy >= N); basis Psi column by column (d x N).  FP64 throughout.
@@ -118,7 +118,8 @@ __global__ void k_psi(int64_t N, int m, int d, const double* __restrict__ Y, int
 // (Gauss-Jordan with partial pivoting, one block, k <= 128): c -> cvec.
 __global__ void k_deim_small(int64_t N, int k, const double* __restrict__ Psi,
                              const int32_t* __restrict__ idx, double* __restrict__ cvec,
-                             int* status) {
+                             int* status, const int* __restrict__ renew) {
+  if (renew && !renew[k]) return;
   extern __shared__ double ab[];  // k x (k + 1)
   __shared__ int piv, ok;
   const int w = k + 1;
@@ -170,19 +171,35 @@ __global__ void k_deim_small(int64_t N, int k, const double* __restrict__ Psi,
   for (int i = threadIdx.x; i < k; i += blockDim.x) cvec[i] = ab[i * w + k];
 }
 
-// |psi_k - sum_{j<k} c_j psi_j| per row; block partial arg-max (lowest row on ties)
+// |psi_k - sum_{j<k} c_j psi_j| per row; block partial arg-max (lowest row on ties).
+// With renew (the index update): nothing unless position k is renewed, and
+// rows held at another position (inherited, or renewed before k) are skipped.
 __global__ void k_deim_resid(int64_t N, int k, const double* __restrict__ Psi,
                              const double* __restrict__ cvec, double* __restrict__ pval,
-                             int64_t* __restrict__ pidx) {
+                             int64_t* __restrict__ pidx, const int32_t* __restrict__ idx, int d,
+                             const int* __restrict__ renew) {
+  if (renew && !renew[k]) return;
   __shared__ double cs[128];
   __shared__ double bv[32];
   __shared__ int64_t bi[32];
+  __shared__ int32_t held[128];
+  __shared__ int nheld;
   for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = cvec[j];
+  if (threadIdx.x == 0) {
+    int c = 0;
+    if (renew)
+      for (int j = 0; j < d; ++j)
+        if (j != k && (j < k || !renew[j])) held[c++] = idx[j];
+    nheld = c;
+  }
   __syncthreads();
   double best = -1.0;
   int64_t bidx = INT64_MAX;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N;
        l += (int64_t)gridDim.x * blockDim.x) {
+    bool skip = false;
+    for (int j = 0; j < nheld; ++j) skip |= held[j] == (int32_t)l;
+    if (skip) continue;
     double r = Psi[(int64_t)k * N + l];
     for (int j = 0; j < k; ++j) r = fma(-cs[j], Psi[(int64_t)j * N + l], r);
     const double a = fabs(r);
@@ -222,8 +239,9 @@ __global__ void k_deim_resid(int64_t N, int k, const double* __restrict__ Psi,
 }
 
 __global__ void k_deim_pick(int nb, const double* __restrict__ pval,
-                            const int64_t* __restrict__ pidx, int32_t* __restrict__ idx, int k) {
-  if (threadIdx.x != 0) return;
+                            const int64_t* __restrict__ pidx, int32_t* __restrict__ idx, int k,
+                            const int* __restrict__ renew) {
+  if (threadIdx.x != 0 || (renew && !renew[k])) return;
   double best = -1.0;
   int64_t b = INT64_MAX;
   for (int i = 0; i < nb; ++i)
@@ -232,6 +250,47 @@ __global__ void k_deim_pick(int nb, const double* __restrict__ pval,
       b = pidx[i];
     }
   idx[k] = (int32_t)b;
+}
+
+// block partial dot products psi_k . prev_k (d x N each): part[blockIdx.x][k]
+__global__ void k_rot_dots(int64_t N, int d, const double* __restrict__ Psi,
+                           const double* __restrict__ Prev, double* __restrict__ part) {
+  __shared__ double red[32];
+  for (int k = 0; k < d; ++k) {
+    double s = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N;
+         l += (int64_t)gridDim.x * blockDim.x)
+      s = fma(Psi[(int64_t)k * N + l], Prev[(int64_t)k * N + l], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      part[(int64_t)blockIdx.x * d + k] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// renew[k] = 1 for the n_up positions with the smallest |psi_k . prev_k| (the
+// most rotated basis vectors; ties to the lowest position), else 0
+__global__ void k_renew(int d, const double* __restrict__ dots, int n_up, int* __restrict__ renew) {
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < d; ++k) renew[k] = 0;
+  for (int t = 0; t < n_up && t < d; ++t) {
+    int b = -1;
+    double best = 0.0;
+    for (int k = 0; k < d; ++k) {
+      if (renew[k]) continue;
+      const double a = fabs(dots[k]);
+      if (b < 0 || a < best) {
+        best = a;
+        b = k;
+      }
+    }
+    renew[b] = 1;
+  }
 }
 
 // block partial column sums of Psi (d x N): part[blockIdx.x][k]
@@ -406,69 +465,221 @@ __global__ void k_inverse(int r, const double* __restrict__ G, double* __restric
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) Inv[e] = aug[(e / r) * w + r + e % r];
 }
 
-// Principal square root S of A (r x r) by the Denman-Beavers iteration
-// Y <- (Y + Z^-1) / 2, Z <- (Z + Y^-1) / 2 from Y = A, Z = I (Y -> A^1/2); at
-// most 60 iterations, stop when |dY|_F <= 1e-15 |Y|_F.  Needs no eigenvalue of
-// A on the closed negative real axis; otherwise VP_ENUMERIC.
+// ---------------------------------------------- half-step power of A
+__device__ __forceinline__ double c_abs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 c_div(double2 a, double2 b) {  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double q = b.y / b.x, den = b.x + b.y * q;
+    return make_double2((a.x + a.y * q) / den, (a.y - a.x * q) / den);
+  }
+  const double q = b.x / b.y, den = b.x * q + b.y;
+  return make_double2((a.x * q + a.y) / den, (a.y * q - a.x) / den);
+}
+// principal square root, branch cut on the negative real axis (the sign of
+// the imaginary part, zero included, picks the side)
+__device__ __forceinline__ double2 c_sqrt(double2 z) {
+  if (z.x == 0.0 && z.y == 0.0) return make_double2(0.0, 0.0);
+  const double t = sqrt(0.5 * (c_abs(z) + fabs(z.x)));
+  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
+  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+// S = Re(A^{1/2}) with the principal power of every eigenvalue (A real, r x r,
+// r <= 64), i.e. Re(W Lambda^{1/2} W^-1) for A = W Lambda W^-1: the half-step
+// factor of exact DMD.  An eigenvalue on the negative real axis (a mode that
+// changes sign every step) contributes +-i |lambda|^{1/2} times a real
+// projector, whose real part is zero on either side of the cut.
+// Method: complex Schur form A = Q T Q^H (Householder reduction to Hessenberg
+// form, then implicit single-shift QR sweeps with Wilkinson shifts, Givens
+// rotations and deflation; every tenth sweep of an eigenvalue uses an ad hoc
+// shift), the upper-triangular square root R of T by the recurrence
+// R_ii = T_ii^{1/2}, (R_ii + R_jj) R_ij = T_ij - sum_{i<k<j} R_ik R_kj (Bjorck
+// and Hammarling, 1983), then S = Re(Q R Q^H).  One warp; the QR sweeps stop
+// after 40 r in total (VP_ENOCONV).
 __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict__ S, int* status) {
-  extern __shared__ double sm[];
-  const int rr = r * r, w = 2 * r;
-  double* Yk = sm;
-  double* Zk = Yk + rr;
-  double* aug = Zk + rr;  // r x 2r
-  double* Yi = aug + r * w;
-  __shared__ double red[2];
-  __shared__ int done;
-  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
-    Yk[e] = A[e];
-    Zk[e] = (e / r == e % r) ? 1.0 : 0.0;
+  extern __shared__ double2 sq[];
+  double2* H = sq;           // r x r, becomes T, then Q R
+  double2* Qm = H + r * r;   // r x r
+  double2* R = Qm + r * r;   // r x r
+  __shared__ double v[64];
+  __shared__ double vv;
+  const int lane = threadIdx.x;
+  const double eps = 2.220446049250313e-16;
+  for (int e = lane; e < r * r; e += 32) {
+    H[e] = make_double2(A[e], 0.0);
+    Qm[e] = make_double2((e / r == e % r) ? 1.0 : 0.0, 0.0);
   }
-  if (threadIdx.x == 0) done = 0;
-  __syncthreads();
-  int it = 0;
-  for (; it < 60 && !done; ++it) {
-    // Yi = Y^-1
-    for (int e = threadIdx.x; e < r * w; e += blockDim.x) {
-      const int i = e / w, j = e - i * w;
-      aug[e] = j < r ? Yk[i * r + j] : (j - r == i ? 1.0 : 0.0);
+  __syncwarp();
+  // 1. Hessenberg form (A is real: real reflectors)
+  for (int k = 0; k + 2 < r; ++k) {
+    const int m = r - k - 1;
+    double sx = 0.0, x0 = H[(k + 1) * r + k].x;
+    for (int i = 1; i < m; ++i) {
+      const double t = H[(k + 1 + i) * r + k].x;
+      sx = fma(t, t, sx);
     }
-    __syncthreads();
-    if (!small_inverse(aug, r)) break;
-    for (int e = threadIdx.x; e < rr; e += blockDim.x) Yi[e] = aug[(e / r) * w + r + e % r];
-    __syncthreads();
-    // aug <- Z^-1
-    for (int e = threadIdx.x; e < r * w; e += blockDim.x) {
-      const int i = e / w, j = e - i * w;
-      aug[e] = j < r ? Zk[i * r + j] : (j - r == i ? 1.0 : 0.0);
+    if (sx == 0.0) continue;  // column already reduced (same value in every lane)
+    const double alpha = -copysign(sqrt(fma(x0, x0, sx)), x0);
+    for (int i = lane; i < m; i += 32) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * r + k].x;
+    __syncwarp();
+    if (lane == 0) {
+      double t = 0.0;
+      for (int i = 0; i < m; ++i) t = fma(v[i], v[i], t);
+      vv = t;
     }
-    __syncthreads();
-    if (!small_inverse(aug, r)) break;
-    if (threadIdx.x == 0) {
-      red[0] = 0.0;
-      red[1] = 0.0;
+    __syncwarp();
+    const double f = 2.0 / vv;
+    for (int j = lane; j < r; j += 32) {  // H <- P H (rows k+1..)
+      double w = 0.0;
+      for (int i = 0; i < m; ++i) w = fma(v[i], H[(k + 1 + i) * r + j].x, w);
+      w *= f;
+      for (int i = 0; i < m; ++i) H[(k + 1 + i) * r + j].x -= v[i] * w;
     }
-    __syncthreads();
-    double dn = 0.0, yn = 0.0;
-    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
-      const double yn_e = 0.5 * (Yk[e] + aug[(e / r) * w + r + e % r]);
-      const double zn_e = 0.5 * (Zk[e] + Yi[e]);
-      dn += (yn_e - Yk[e]) * (yn_e - Yk[e]);
-      yn += yn_e * yn_e;
-      Yk[e] = yn_e;
-      Zk[e] = zn_e;
+    __syncwarp();
+    for (int i = lane; i < r; i += 32) {  // H <- H P, Q <- Q P (columns k+1..)
+      double w = 0.0, wq = 0.0;
+      for (int j = 0; j < m; ++j) {
+        w = fma(H[i * r + k + 1 + j].x, v[j], w);
+        wq = fma(Qm[i * r + k + 1 + j].x, v[j], wq);
+      }
+      w *= f;
+      wq *= f;
+      for (int j = 0; j < m; ++j) {
+        H[i * r + k + 1 + j].x -= w * v[j];
+        Qm[i * r + k + 1 + j].x -= wq * v[j];
+      }
     }
-    atomicAdd(&red[0], dn);
-    atomicAdd(&red[1], yn);
-    __syncthreads();
-    if (threadIdx.x == 0 && red[0] <= 1e-30 * red[1]) done = 1;
-    __syncthreads();
+    __syncwarp();
+    for (int i = k + 2 + lane; i < r; i += 32) H[i * r + k] = make_double2(0.0, 0.0);
+    __syncwarp();
   }
-  __syncthreads();
-  if (!done) {
-    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+  // 2. complex Schur form by implicit single-shift QR sweeps
+  int hi = r - 1, it = 0, total = 0;
+  bool failed = false;
+  while (hi > 0) {
+    int l = hi;
+    for (; l > 0; --l) {
+      double sc = c_abs(H[(l - 1) * r + l - 1]) + c_abs(H[l * r + l]);
+      if (sc == 0.0) sc = 1.0;
+      if (c_abs(H[l * r + l - 1]) <= eps * sc) break;
+    }
+    __syncwarp();
+    if (l > 0 && lane == 0) H[l * r + l - 1] = make_double2(0.0, 0.0);
+    __syncwarp();
+    if (l == hi) {
+      --hi;
+      it = 0;
+      continue;
+    }
+    if (total > 40 * r) {
+      failed = true;
+      break;
+    }
+    const double2 a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi], c = H[hi * r + hi - 1],
+                  d = H[hi * r + hi];
+    double2 mu;
+    if (it % 11 == 10) {
+      mu = make_double2(d.x + 0.75 * c_abs(c), d.y);
+    } else {
+      const double2 h = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
+      const double2 disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
+      const double2 m0 = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
+      const double2 m1 = cadd(m0, disc), m2 = csub(m0, disc);
+      mu = c_abs(csub(m1, d)) < c_abs(csub(m2, d)) ? m1 : m2;
+    }
+    for (int k = l; k < hi; ++k) {
+      double2 x, y;
+      if (k == l) {
+        x = csub(H[l * r + l], mu);
+        y = H[(l + 1) * r + l];
+      } else {
+        x = H[k * r + k - 1];
+        y = H[(k + 1) * r + k - 1];
+      }
+      // G = [[cg, sg], [-conj(sg), cg]] with G [x; y] = [rho; 0]
+      double cg;
+      double2 sg;
+      if (y.x == 0.0 && y.y == 0.0) {
+        cg = 1.0;
+        sg = make_double2(0.0, 0.0);
+      } else if (x.x == 0.0 && x.y == 0.0) {
+        cg = 0.0;
+        sg = make_double2(1.0, 0.0);
+      } else {
+        const double ax = c_abs(x), nrm = hypot(ax, c_abs(y));
+        cg = ax / nrm;
+        sg = cmul(make_double2(x.x / ax, x.y / ax), make_double2(y.x / nrm, -y.y / nrm));
+      }
+      __syncwarp();
+      const int j0 = k == l ? l : k - 1;
+      for (int j = j0 + lane; j < r; j += 32) {  // rows k, k+1 <- G [rows]
+        const double2 h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
+        H[k * r + j] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(sg, h1));
+        H[(k + 1) * r + j] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(make_double2(sg.x, -sg.y), h0));
+      }
+      __syncwarp();
+      if (k > l && lane == 0) H[(k + 1) * r + k - 1] = make_double2(0.0, 0.0);
+      const int i1 = min(k + 2, hi) + 1;
+      const double2 sc = make_double2(sg.x, -sg.y);
+      for (int i = lane; i < r; i += 32) {  // columns k, k+1 <- [columns] G^H
+        if (i < i1) {
+          const double2 h0 = H[i * r + k], h1 = H[i * r + k + 1];
+          H[i * r + k] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(h1, sc));
+          H[i * r + k + 1] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(h0, sg));
+        }
+        const double2 q0 = Qm[i * r + k], q1 = Qm[i * r + k + 1];
+        Qm[i * r + k] = cadd(make_double2(cg * q0.x, cg * q0.y), cmul(q1, sc));
+        Qm[i * r + k + 1] = csub(make_double2(cg * q1.x, cg * q1.y), cmul(q0, sg));
+      }
+      __syncwarp();
+    }
+    ++it;
+    ++total;
+  }
+  if (failed) {
+    if (lane == 0) vp_set_status(status, VP_ENOCONV);
     return;
   }
-  for (int e = threadIdx.x; e < rr; e += blockDim.x) S[e] = Yk[e];
+  // 3. R = T^{1/2} (upper triangular), superdiagonal by superdiagonal
+  bool singular = false;
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e / r, j = e - i * r;
+    R[e] = i == j ? c_sqrt(H[e]) : make_double2(0.0, 0.0);
+  }
+  __syncwarp();
+  for (int dd = 1; dd < r; ++dd) {
+    for (int i = lane; i + dd < r; i += 32) {
+      const int j = i + dd;
+      double2 s = H[i * r + j];
+      for (int k = i + 1; k < j; ++k) s = csub(s, cmul(R[i * r + k], R[k * r + j]));
+      const double2 den = cadd(R[i * r + i], R[j * r + j]);
+      if (den.x == 0.0 && den.y == 0.0) {
+        singular = true;
+        R[i * r + j] = make_double2(0.0, 0.0);
+      } else {
+        R[i * r + j] = c_div(s, den);
+      }
+    }
+    __syncwarp();
+  }
+  if (singular) vp_set_status(status, VP_ENUMERIC);
+  // 4. S = Re(Q R Q^H): H <- Q R, then S_ij = Re sum_k H_ik conj(Q_jk)
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e / r, j = e - i * r;
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k <= j; ++k) s = cadd(s, cmul(Qm[i * r + k], R[k * r + j]));
+    H[e] = s;
+  }
+  __syncwarp();
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e / r, j = e - i * r;
+    double s = 0.0;
+    for (int k = 0; k < r; ++k) {
+      const double2 h = H[i * r + k], q = Qm[j * r + k];
+      s = fma(h.x, q.x, fma(h.y, q.y, s));  // Re(h conj(q))
+    }
+    S[e] = s;
+  }
 }
 
 // out (q x cols) = A (q x K) B (K x cols), row-major
@@ -486,10 +697,12 @@ __global__ void k_mm(int q, int K, int cols, const double* __restrict__ A,
 // out (p x K) = E (K_ss^-1 values), K_ss = exp(-(eps |eta_i - eta_j|)^2).
 __global__ void k_rbf(int dim, int q, const double* __restrict__ eta_s, int K,
                       const double* __restrict__ values, int p, const double* __restrict__ eta,
-                      double eps, double* __restrict__ out, int* status) {
+                      double eps_h, const double* __restrict__ eps_dev, double* __restrict__ out,
+                      int* status) {
   extern __shared__ double aug[];  // q x (q + K)
   __shared__ int piv, ok;
   const int w = q + K;
+  const double eps = eps_dev ? *eps_dev : eps_h;
   for (int e = threadIdx.x; e < q * w; e += blockDim.x) {
     const int i = e / w, j = e - i * w;
     if (j < q) {
@@ -587,6 +800,134 @@ __global__ void k_dmd_eval(int nx, int r, const double* __restrict__ B, const do
   }
 }
 
+// ------------------------------------------- DMD-DEIM reduced dynamics
+// Y_i[l] = Lambda^0(x_il) Phi_i with x_il = sum_m A_lm a_mi - B_lm b_mi, the
+// position of particle l under sample i (U_X = [A, -B], Z_i = [a; b]): the
+// DEIM data column of eq. Ydeim, straight from Q (N x 2n rows [A | B]) and
+// the 2n x q coefficients Zs.  Row tiles of 32 particles go to shared memory.
+#define PQ_ROWS 32
+__global__ void k_phi_at_qz(GridC g, int64_t N, int n, int q, const double* __restrict__ Q,
+                            const double* __restrict__ Zs, const double* __restrict__ phi,
+                            double* __restrict__ Y) {
+  extern __shared__ double pq[];
+  const int n2 = 2 * n;
+  double* zs = pq;                // n2 x q
+  double* qt = pq + n2 * q;       // PQ_ROWS x n2
+  for (int e = threadIdx.x; e < n2 * q; e += blockDim.x) zs[e] = Zs[e];
+  for (int64_t tile = blockIdx.x; tile * PQ_ROWS < N; tile += gridDim.x) {
+    const int64_t base = tile * PQ_ROWS;
+    const int rows = (int)min((int64_t)PQ_ROWS, N - base);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * n2; e += blockDim.x) qt[e] = Q[base * n2 + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < q * PQ_ROWS; e += blockDim.x) {
+      const int i = e / PQ_ROWS, rr = e - i * PQ_ROWS;
+      if (rr >= rows) continue;
+      double x = 0.0;
+      for (int m = 0; m < n; ++m) {
+        x = fma(qt[rr * n2 + m], zs[m * q + i], x);
+        x = fma(-qt[rr * n2 + n + m], zs[(n + m) * q + i], x);
+      }
+      int j;
+      double sfr;
+      cell_of(x, g.inv_h, g.Nx, g.dNx, g.inv_Nx, j, sfr);
+      const int j1 = (j + 1 == g.Nx) ? 0 : j + 1;
+      const double* ph = phi + (int64_t)i * g.Nx;
+      Y[(int64_t)i * N + base + rr] = fma(sfr, __ldg(ph + j1), (1.0 - sfr) * __ldg(ph + j));
+    }
+  }
+}
+
+// out (d x n2, FP64) = rows idx of a row-format matrix (mode 1 double-float
+// float2, mode 2 FP32 float; N x n2)
+__global__ void k_gather_rows_lp(const void* __restrict__ Q2, int mode, int64_t N, int n2,
+                                 const int32_t* __restrict__ idx, int d, double* __restrict__ out,
+                                 int* status) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * n2; e += gridDim.x * blockDim.x) {
+    const int j = e / n2, m = e - j * n2;
+    const int64_t l = idx[j];
+    if (l < 0 || l >= N) {
+      vp_set_status(status, VP_EINVAL);
+      out[e] = 0.0;
+      continue;
+    }
+    const int64_t a = l * n2 + m;
+    if (mode == 1) {
+      const float2 v = reinterpret_cast<const float2*>(Q2)[a];
+      out[e] = (double)v.x + (double)v.y;
+    } else {
+      out[e] = (double)reinterpret_cast<const float*>(Q2)[a];
+    }
+  }
+}
+
+// One fixed-point round of the DMD-DEIM coefficient stage (eq. grHDD, X part):
+// gX_i = U_X[idx]^T (c (.) F_i(cell of x_i[idx])) / m_p with x_i[idx] =
+// U_X[idx] Ze_i, for sample i = blockIdx.x; Qd holds the d DEIM rows [A | B]
+// of the basis, F the cell field of the DMD potentials (p x Nx).  Returns at
+// once after convergence (done flag).
+__global__ void k_deim_round(GridC g, int n, int p, int d, const double* __restrict__ Qd,
+                             const double* __restrict__ Ze, const double* __restrict__ F,
+                             const double* __restrict__ c, double* __restrict__ gX,
+                             const int* __restrict__ done) {
+  if (*done) return;
+  extern __shared__ double dr[];
+  const int n2 = 2 * n, i = blockIdx.x;
+  double* qd = dr;             // d x n2
+  double* z = qd + d * n2;     // n2
+  double* e = z + n2;          // d
+  for (int t = threadIdx.x; t < d * n2; t += blockDim.x) qd[t] = Qd[t];
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) z[t] = Ze[(int64_t)t * p + i];
+  __syncthreads();
+  const double* Fi = F + (int64_t)i * g.Nx;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    double x = 0.0;
+    for (int m = 0; m < n; ++m) {
+      x = fma(qd[j * n2 + m], z[m], x);
+      x = fma(-qd[j * n2 + n + m], z[n + m], x);
+    }
+    int cell;
+    double sfr;
+    cell_of(x, g.inv_h, g.Nx, g.dNx, g.inv_Nx, cell, sfr);
+    e[j] = c[j] * Fi[cell] / g.mp;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n2; r += blockDim.x) {
+    // U_X row j = [A_j, -B_j]: column r < n reads A, r >= n reads -B
+    const double sg = r < n ? 1.0 : -1.0;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s = fma(qd[j * n2 + r], e[j], s);
+    gX[(int64_t)r * p + i] = sg * s;
+  }
+}
+
+// Gaussian RBF width 0.3 / (mean distance of each node to its nearest other node)
+__global__ void k_rbf_width(int dim, int q, const double* __restrict__ eta_s, double* eps) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < q; i += blockDim.x) {
+    double best = INFINITY;
+    for (int j = 0; j < q; ++j) {
+      if (j == i) continue;
+      double d2 = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        const double dd = eta_s[i * dim + a] - eta_s[j * dim + a];
+        d2 = fma(dd, dd, d2);
+      }
+      best = fmin(best, sqrt(d2));
+    }
+    s += best;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *eps = 0.3 / (t / q);
+  }
+}
+
 }  // namespace
 
 namespace vpk {
@@ -599,43 +940,26 @@ void deim_init() {
   cudaFuncSetAttribute(k_rbf, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_sqrtm, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_phi_at_qz, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_deim_round, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 }  // namespace vpk
 
-extern "C" {
-
-vp_status vp_potential_at_particles(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p,
-                                    const double* X, int64_t ldx, const double* phi, double* Y,
-                                    int64_t ldy, void* stream) {
-  if (!ctx || !grid || !X || !phi || !Y || N < 1 || p < 1 || p > 65535 || ldx < N || ldy < N ||
-      grid->Nx < 3 || grid->Nx > VP_MAX_NX || !(grid->L > 0.0))
-    return VP_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  GridC g = make_gridc(*grid, N);
-  int bx = ceil_div(N, 256);
-  const int want = (4 * ctx->num_sms + p - 1) / p;
-  if (bx > want) bx = want;
-  VP_K(VP_K_SUBSET, (k_phi_at<<<dim3(bx, p), 256, 0, st>>>(g, N, p, X, ldx, phi, Y, ldy)));
-  VP_LAUNCHED();
-  return VP_OK;
+namespace vpk {
+size_t deim_basis_scratch(int sms, int64_t N, int m) {
+  const int tot = m * m;
+  const int gx = std::min<int64_t>(ceil_div(N, YG_ROWS), 2 * sms);
+  return arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
+         arena_bytes(m, 8);
 }
 
-vp_status vp_deim_basis(vp_ctx* ctx, int64_t N, int32_t m, const double* Y, int64_t ldy, int32_t d,
-                        double* Psi, double* sigma, void* stream) {
-  if (!ctx || !Y || !Psi || N < 1 || m < 1 || m > 256 || d < 1 || d > m || d > 128 || ldy < N ||
-      (int64_t)m * d > 25600)
-    return VP_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t ldy, int d,
+                         double* Psi, double* sigma, void* scratch, cudaStream_t st) {
   const int tot = m * m;
-  int gx = std::min<int64_t>(ceil_div(N, YG_ROWS), 2 * ctx->num_sms);
+  const int gx = std::min<int64_t>(ceil_div(N, YG_ROWS), 2 * ctx->num_sms);
   const int gy = ceil_div(tot, 256 * 8);
-  size_t bytes = arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
-                 arena_bytes(m, 8);
-  void* base = nullptr;
-  VP_TRY(vp_workspace(ctx, bytes, &base));
-  Arena a{(char*)base, 0, bytes};
+  const size_t bytes = deim_basis_scratch(ctx->num_sms, N, m);
+  Arena a{(char*)scratch, 0, bytes};
   double* part = a.take<double>((size_t)gx * tot);
   double* G = a.take<double>(tot);
   double2* Gc = a.take<double2>(tot);
@@ -650,71 +974,76 @@ vp_status vp_deim_basis(vp_ctx* ctx, int64_t N, int32_t m, const double* Y, int6
   int bx = std::min<int64_t>(ceil_div(N, 256), 4 * ctx->num_sms);
   VP_K(VP_K_SUBSET, (k_psi<<<bx, 256, sizeof(double) * m * d, st>>>(N, m, d, Y, ldy, Ws, lam, Psi,
                                                                     sigma, ctx->d_status)));
-  VP_LAUNCHED();
   return VP_OK;
 }
 
-vp_status vp_deim_indices(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi, int32_t* idx,
-                          void* stream) {
-  if (!ctx || !Psi || !idx || N < 1 || d < 1 || d > 128 || d > N) return VP_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+size_t deim_indices_scratch(int sms, int64_t N, int d) {
+  const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * sms);
+  return arena_bytes(nb, 8) + arena_bytes(nb, 8) + arena_bytes(128, 8) +
+         arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8) + arena_bytes(d, 4);
+}
+
+vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int32_t* idx,
+                           const double* Psi_prev, int n_up, void* scratch, cudaStream_t st) {
   const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * ctx->num_sms);
-  size_t bytes = arena_bytes(nb, 8) + arena_bytes(nb, 8) + arena_bytes(128, 8);
-  void* base = nullptr;
-  VP_TRY(vp_workspace(ctx, bytes, &base));
-  Arena a{(char*)base, 0, bytes};
+  const size_t bytes = deim_indices_scratch(ctx->num_sms, N, d);
+  Arena a{(char*)scratch, 0, bytes};
   double* pval = a.take<double>(nb);
   int64_t* pidx = a.take<int64_t>(nb);
   double* cvec = a.take<double>(128);
+  double* part = a.take<double>((size_t)nb * d);
+  double* dots = a.take<double>(d);
+  int* renew = a.take<int>(d);
+  const int* rn = nullptr;
+  if (Psi_prev) {  // index update: renew the n_up most rotated positions
+    VP_K(VP_K_SUBSET, (k_rot_dots<<<nb, 256, 0, st>>>(N, d, Psi, Psi_prev, part)));
+    VP_K(VP_K_REDUCE, reduce_partials(nb, d, part, dots, nullptr, st));
+    VP_K(VP_K_SUBSET, (k_renew<<<1, 32, 0, st>>>(d, dots, n_up, renew)));
+    rn = renew;
+  }
   for (int k = 0; k < d; ++k) {
     if (k > 0)
       VP_K(VP_K_SUBSET, (k_deim_small<<<1, 256, sizeof(double) * k * (k + 1), st>>>(
-                            N, k, Psi, idx, cvec, ctx->d_status)));
-    VP_K(VP_K_SUBSET, (k_deim_resid<<<nb, 256, 0, st>>>(N, k, Psi, cvec, pval, pidx)));
-    VP_K(VP_K_SUBSET, (k_deim_pick<<<1, 32, 0, st>>>(nb, pval, pidx, idx, k)));
+                            N, k, Psi, idx, cvec, ctx->d_status, rn)));
+    VP_K(VP_K_SUBSET, (k_deim_resid<<<nb, 256, 0, st>>>(N, k, Psi, cvec, pval, pidx, idx, d, rn)));
+    VP_K(VP_K_SUBSET, (k_deim_pick<<<1, 32, 0, st>>>(nb, pval, pidx, idx, k, rn)));
   }
-  VP_LAUNCHED();
   return VP_OK;
 }
 
-vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi, const int32_t* idx,
-                          double Mq, double* c, void* stream) {
-  if (!ctx || !Psi || !idx || !c || N < 1 || d < 1 || d > 128) return VP_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+size_t deim_weights_scratch(int sms, int64_t N, int d) {
+  const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * sms);
+  return arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8);
+}
+
+vp_status deim_weights_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, const int32_t* idx,
+                           double Mq, double* c, void* scratch, cudaStream_t st) {
   const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * ctx->num_sms);
-  size_t bytes = arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8);
-  void* base = nullptr;
-  VP_TRY(vp_workspace(ctx, bytes, &base));
-  Arena a{(char*)base, 0, bytes};
+  Arena a{(char*)scratch, 0, deim_weights_scratch(ctx->num_sms, N, d)};
   double* part = a.take<double>((size_t)nb * d);
   double* colsum = a.take<double>(d);
   VP_K(VP_K_SUBSET, (k_colsum<<<nb, 256, 0, st>>>(N, d, Psi, part)));
   VP_K(VP_K_REDUCE, reduce_partials(nb, d, part, colsum, nullptr, st));
   VP_K(VP_K_SUBSET, (k_deim_weights<<<1, 256, sizeof(double) * d * (d + 1), st>>>(
                         N, d, Psi, idx, colsum, Mq, c, ctx->d_status)));
-  VP_LAUNCHED();
   return VP_OK;
 }
 
-vp_status vp_dmd_fit(vp_ctx* ctx, int32_t nx, int32_t m, const double* Y, const double* Yp,
-                     double tol, int32_t r_max, int32_t* r_out, double* B, double* Bpinv,
-                     double* A, double* S, double* sigma, void* stream) {
-  if (!ctx || !Y || !Yp || !r_out || !B || !Bpinv || !A || !S || nx < 1 || nx > 4096 || m < 1 ||
-      m > 256 || r_max < 1 || r_max > 64 || !(tol >= 0.0))
-    return VP_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+size_t dmd_fit_scratch(int nx, int m, int r_max) {
+  const int tot = m * m;
+  const int gx = std::max(1, std::min(ceil_div(nx, YG_ROWS), 64));
+  return arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
+         arena_bytes(m, 8) + arena_bytes((size_t)m * r_max, 8) + arena_bytes((size_t)r_max * nx, 8) +
+         2 * arena_bytes((size_t)r_max * r_max, 8);
+}
+
+vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double* Yp, double tol,
+                      int r_max, int* r_out, double* B, double* Bpinv, double* A, double* S,
+                      double* sigma, void* scratch, cudaStream_t st) {
   const int tot = m * m;
   const int gx = std::max(1, std::min(ceil_div(nx, YG_ROWS), 64));
   const int gy = ceil_div(tot, 256 * 8);
-  size_t bytes = arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
-                 arena_bytes(m, 8) + arena_bytes((size_t)m * r_max, 8) +
-                 arena_bytes((size_t)r_max * nx, 8) + 2 * arena_bytes((size_t)r_max * r_max, 8);
-  void* base = nullptr;
-  VP_TRY(vp_workspace(ctx, bytes, &base));
-  Arena a{(char*)base, 0, bytes};
+  Arena a{(char*)scratch, 0, dmd_fit_scratch(nx, m, r_max)};
   double* part = a.take<double>((size_t)gx * tot);
   double* G = a.take<double>(tot);
   double2* Gc = a.take<double2>(tot);
@@ -756,9 +1085,136 @@ vp_status vp_dmd_fit(vp_ctx* ctx, int32_t nx, int32_t m, const double* Y, const 
   // B^+ (r x nx) = BtBi (r x r) * B^T; B is stored as r columns of length nx,
   // i.e. the row-major r x nx matrix B^T
   VP_K(VP_K_SUBSET, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
-  // 4. principal square root of A for half steps
-  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 256, sizeof(double) * (4 * r * r + 2 * r * r), st>>>(
-                        r, A, S, ctx->d_status)));
+  // 4. real part of the principal square root of A for half steps
+  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 32, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
+  return VP_OK;
+}
+
+void dmd_coords_run(int nx, int r, const double* Bpinv, int q, const double* Phi, double* beta,
+                    cudaStream_t st) {
+  // beta (q x r) = Phi (q x nx) Bpinv^T: entry (i, k) = sum_x Phi[i][x] Bpinv[k][x]
+  k_cols_dot<<<ceil_div(q * r, 256), 256, 0, st>>>(nx, q, r, Phi, Bpinv, beta);
+}
+
+void rbf_run(int dim, int q, const double* eta_s, int K, const double* values, int p,
+             const double* eta, double eps, const double* eps_dev, double* out, int* status,
+             cudaStream_t st) {
+  k_rbf<<<1, 256, sizeof(double) * q * (q + K), st>>>(dim, q, eta_s, K, values, p, eta, eps, eps_dev,
+                                                      out, status);
+}
+
+void rbf_width_run(int dim, int q, const double* eta_s, double* eps, cudaStream_t st) {
+  k_rbf_width<<<1, 256, 0, st>>>(dim, q, eta_s, eps);
+}
+
+void dmd_potential_run(int nx, int r, const double* B, const double* A, const double* S, int p,
+                       const double* beta, int ksteps, int half, double* Phi, cudaStream_t st) {
+  k_dmd_eval<<<p, 128, sizeof(double) * 2 * r, st>>>(nx, r, B, A, S, beta, ksteps, half, Phi);
+}
+
+void phi_at_qz(const GridC& g, int64_t N, int n, int q, const double* Q, const double* Zs,
+               const double* phi, double* Y, int sms, cudaStream_t st) {
+  const int bx = std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, PQ_ROWS), 4 * sms));
+  const size_t smem = sizeof(double) * ((size_t)2 * n * q + (size_t)PQ_ROWS * 2 * n);
+  k_phi_at_qz<<<bx, 256, smem, st>>>(g, N, n, q, Q, Zs, phi, Y);
+}
+
+void gather_rows_lp(const void* Q2, int mode, int64_t N, int n2, const int32_t* idx, int d,
+                    double* out, int* status, cudaStream_t st) {
+  k_gather_rows_lp<<<ceil_div(d * n2, 256), 256, 0, st>>>(Q2, mode, N, n2, idx, d, out, status);
+}
+
+void deim_round(const GridC& g, int n, int p, int d, const double* Qd, const double* Ze,
+                const double* F, const double* c, double* gX, const int* done, cudaStream_t st) {
+  const size_t smem = sizeof(double) * ((size_t)d * 2 * n + 2 * n + d);
+  k_deim_round<<<p, 128, smem, st>>>(g, n, p, d, Qd, Ze, F, c, gX, done);
+}
+}  // namespace vpk
+
+extern "C" {
+
+vp_status vp_potential_at_particles(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p,
+                                    const double* X, int64_t ldx, const double* phi, double* Y,
+                                    int64_t ldy, void* stream) {
+  if (!ctx || !grid || !X || !phi || !Y || N < 1 || p < 1 || p > 65535 || ldx < N || ldy < N ||
+      grid->Nx < 3 || grid->Nx > VP_MAX_NX || !(grid->L > 0.0))
+    return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GridC g = make_gridc(*grid, N);
+  int bx = ceil_div(N, 256);
+  const int want = (4 * ctx->num_sms + p - 1) / p;
+  if (bx > want) bx = want;
+  VP_K(VP_K_SUBSET, (k_phi_at<<<dim3(bx, p), 256, 0, st>>>(g, N, p, X, ldx, phi, Y, ldy)));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_deim_basis(vp_ctx* ctx, int64_t N, int32_t m, const double* Y, int64_t ldy, int32_t d,
+                        double* Psi, double* sigma, void* stream) {
+  if (!ctx || !Y || !Psi || N < 1 || m < 1 || m > 256 || d < 1 || d > m || d > 128 || ldy < N ||
+      (int64_t)m * d > 25600)
+    return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, deim_basis_scratch(ctx->num_sms, N, m), &base));
+  VP_TRY(deim_basis_run(ctx, N, m, Y, ldy, d, Psi, sigma, base, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_deim_indices(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi, int32_t* idx,
+                          void* stream) {
+  if (!ctx || !Psi || !idx || N < 1 || d < 1 || d > 128 || d > N) return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, deim_indices_scratch(ctx->num_sms, N, d), &base));
+  VP_TRY(deim_indices_run(ctx, N, d, Psi, idx, nullptr, 0, base, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_deim_indices_update(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi,
+                                 const double* Psi_prev, int32_t n_up, int32_t* idx, void* stream) {
+  if (!ctx || !Psi || !Psi_prev || !idx || N < 1 || d < 1 || d > 128 || d > N || n_up < 0 ||
+      n_up > d)
+    return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, deim_indices_scratch(ctx->num_sms, N, d), &base));
+  VP_TRY(deim_indices_run(ctx, N, d, Psi, idx, Psi_prev, n_up, base, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_deim_weights(vp_ctx* ctx, int64_t N, int32_t d, const double* Psi, const int32_t* idx,
+                          double Mq, double* c, void* stream) {
+  if (!ctx || !Psi || !idx || !c || N < 1 || d < 1 || d > 128) return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, deim_weights_scratch(ctx->num_sms, N, d), &base));
+  VP_TRY(deim_weights_run(ctx, N, d, Psi, idx, Mq, c, base, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_dmd_fit(vp_ctx* ctx, int32_t nx, int32_t m, const double* Y, const double* Yp,
+                     double tol, int32_t r_max, int32_t* r_out, double* B, double* Bpinv,
+                     double* A, double* S, double* sigma, void* stream) {
+  if (!ctx || !Y || !Yp || !r_out || !B || !Bpinv || !A || !S || nx < 1 || nx > 4096 || m < 1 ||
+      m > 256 || r_max < 1 || r_max > 64 || !(tol >= 0.0))
+    return VP_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, dmd_fit_scratch(nx, m, r_max), &base));
+  int r = 0;
+  VP_TRY(dmd_fit_run(ctx, nx, m, Y, Yp, tol, r_max, &r, B, Bpinv, A, S, sigma, base, st));
+  *r_out = r;
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -768,8 +1224,7 @@ vp_status vp_dmd_coords(vp_ctx* ctx, int32_t nx, int32_t r, const double* Bpinv,
   if (!ctx || !Bpinv || !Phi || !beta || nx < 1 || r < 1 || r > 64 || q < 1) return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // beta (q x r) = Phi (q x nx) Bpinv^T: entry (i, k) = sum_x Phi[i][x] Bpinv[k][x]
-  VP_K(VP_K_SUBSET, (k_cols_dot<<<ceil_div(q * r, 256), 256, 0, st>>>(nx, q, r, Phi, Bpinv, beta)));
+  VP_K(VP_K_SUBSET, dmd_coords_run(nx, r, Bpinv, q, Phi, beta, st));
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -782,8 +1237,7 @@ vp_status vp_rbf_interpolate(vp_ctx* ctx, int32_t dim, int32_t q, const double* 
     return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_SUBSET, (k_rbf<<<1, 256, sizeof(double) * q * (q + K), st>>>(
-                        dim, q, eta_s, K, values, p, eta, eps, out, ctx->d_status)));
+  VP_K(VP_K_SUBSET, rbf_run(dim, q, eta_s, K, values, p, eta, eps, nullptr, out, ctx->d_status, st));
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -796,8 +1250,7 @@ vp_status vp_dmd_potential(vp_ctx* ctx, int32_t nx, int32_t r, const double* B, 
     return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_SUBSET, (k_dmd_eval<<<p, 128, sizeof(double) * 2 * r, st>>>(nx, r, B, A, S, beta, ksteps,
-                                                                        half, Phi)));
+  VP_K(VP_K_SUBSET, dmd_potential_run(nx, r, B, A, S, p, beta, ksteps, half, Phi, st));
   VP_LAUNCHED();
   return VP_OK;
 }

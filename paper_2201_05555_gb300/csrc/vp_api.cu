@@ -102,6 +102,7 @@ struct RedWS {
   uint16_t* jcell;    // cell index per (particle, sample), N x p
   float2* frows[5];   // row blocks of the FP32-based step
   float2 *Z2, *Zh2, *F2;
+  double* phi_out = nullptr;  // when set, the FP32-based field also writes the potentials
   int gx_proj, gx_gram;
   // parameter subsample of the basis stages (Sec. 4.1): per-sample buffers
   // for the nsub selected columns; N-row buffers are shared
@@ -354,7 +355,7 @@ struct RedDF {
     a.j = w.jcell;
     a.skip = skip;
     VP_K(VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
-    VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip,
+    VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, w.phi_out, w.F, w.Efield, w.counts, skip,
                                ctx->d_status, st, w.F2, arith));
   }
   void project(const void* Q2, const int* skip) {
@@ -621,6 +622,290 @@ static vp_status basis_update_df(vp_ctx* ctx, Red& R, double* Q, double* Z, doub
   return VP_OK;
 }
 
+// ------------------------------------------ DMD-DEIM reduced dynamics
+// Algorithm 2 on the device: windows, DMD and DEIM operators of one reduced
+// problem (see vp_hyper_* in vp.h).  All buffers are owned by the object
+// (one allocation), apart from the step workspace of the context.
+struct vp_hyper {
+  vp_ctx* ctx = nullptr;
+  vp_grid grid{};
+  GridC g{};
+  int64_t N = 0;
+  int n = 0, p = 0, nsub = 0, dim = 0, T = 0, d = 0, n_up = 0, k_deim = 1, r_max = 0;
+  double dmd_tol = 0.0;
+  void* mem = nullptr;
+  int32_t *sub = nullptr, *idx = nullptr;
+  double *eta = nullptr, *eta_s = nullptr, *eps = nullptr;
+  double* phi_ring = nullptr;  // 2 (T+1) slots of nsub x Nx (each written twice, so
+                               // every window of T+1 consecutive entries is contiguous)
+  double* y_ring = nullptr;    // (T+1) slots of nsub x N (DEIM data; order is immaterial)
+  double *B = nullptr, *Bp = nullptr, *A = nullptr, *S = nullptr, *beta_s = nullptr,
+         *beta = nullptr, *phi_half = nullptr, *F = nullptr, *Psi = nullptr, *Psi_prev = nullptr,
+         *c = nullptr, *Qd = nullptr;
+  void* scratch = nullptr;
+  int64_t entries = 0;  // potentials written to the windows
+  int intervals = 0, hyper_intervals = 0, r = 0;
+};
+
+namespace {
+__global__ void k_gather_eta(int dim, int nsub, const int32_t* __restrict__ sub,
+                             const double* __restrict__ eta, int p, double* __restrict__ eta_s,
+                             int* status) {
+  for (int e = threadIdx.x; e < nsub * dim; e += blockDim.x) {
+    const int i = e / dim, a = e - i * dim;
+    const int c = sub[i];
+    if (c < 0 || c >= p) {
+      vp_set_status(status, VP_EINVAL);
+      eta_s[e] = 0.0;
+    } else {
+      eta_s[e] = eta[c * dim + a];
+    }
+  }
+}
+
+// One interval of Algorithm 2 (see vp.h); S is the step of this call.
+vp_status hyper_interval(vp_hyper* h, Red& R, DFStep& S, double* trace_step, int round_hint,
+                         int* its_out) {
+  vp_ctx* ctx = h->ctx;
+  cudaStream_t st = S.st;
+  RedWS& w = R.w;
+  const int n = h->n, p = h->p, q = h->nsub, Nx = h->grid.Nx, T = h->T;
+  const int64_t N = h->N;
+  const vp_step_opts& o = S.o;
+  // 1. field of the sampled parameters at the entering state writes Phi_{tau-1}
+  const int slot = (int)(h->entries % (T + 1));
+  double* phi_slot = h->phi_ring + (size_t)slot * q * Nx;
+  S.Rs.w.phi_out = phi_slot;
+  VP_TRY(S.pre(trace_step));
+  S.Rs.w.phi_out = nullptr;
+  VP_CUDA(cudaMemcpyAsync(phi_slot + (size_t)(T + 1) * q * Nx, phi_slot, sizeof(double) * q * Nx,
+                          cudaMemcpyDeviceToDevice, st));
+  VP_K(VP_K_HYPER, phi_at_qz(h->g, N, n, q, S.Q, w.sub.Zs, phi_slot,
+                             h->y_ring + (size_t)slot * q * N, ctx->num_sms, st));
+  ++h->entries;
+  const bool hyper = h->entries >= T + 1;
+  if (hyper) {
+    // 3. DMD of the window (oldest entry first), coordinates, RBF, Phi at t + dt/2
+    const int oldest = (int)((h->entries - (T + 1)) % (T + 1));
+    const double* Y = h->phi_ring + (size_t)oldest * q * Nx;
+    int r = 0;
+    VP_TRY(dmd_fit_run(ctx, Nx, T * q, Y, Y + (size_t)q * Nx, h->dmd_tol, h->r_max, &r, h->B, h->Bp,
+                       h->A, h->S, nullptr, h->scratch, st));
+    h->r = r;
+    VP_K(VP_K_HYPER, dmd_coords_run(Nx, r, h->Bp, q, phi_slot, h->beta_s, st));
+    VP_K(VP_K_HYPER, rbf_run(h->dim, q, h->eta_s, r, h->beta_s, p, h->eta, 0.0, h->eps, h->beta,
+                             ctx->d_status, st));
+    VP_K(VP_K_HYPER, dmd_potential_run(Nx, r, h->B, h->A, h->S, p, h->beta, 0, 1, h->phi_half, st));
+    VP_K(VP_K_CELL_GRADIENT, cell_gradient(h->g, p, h->phi_half, h->F, st));
+    // DEIM basis, indices (all, or the n_up most rotated), weights
+    std::swap(h->Psi, h->Psi_prev);
+    VP_TRY(deim_basis_run(ctx, N, (T + 1) * q, h->y_ring, N, h->d, h->Psi, nullptr, h->scratch, st));
+    const bool full = h->hyper_intervals % h->k_deim == 0;
+    VP_TRY(deim_indices_run(ctx, N, h->d, h->Psi, h->idx, full ? nullptr : h->Psi_prev, h->n_up,
+                            h->scratch, st));
+    VP_TRY(deim_weights_run(ctx, N, h->d, h->Psi, h->idx, h->g.Mq, h->c, h->scratch, st));
+    // the d DEIM rows of the basis at the coefficient stage (U_1/2)
+    VP_K(VP_K_HYPER, gather_rows_lp(S.Qm, o.arith, N, 2 * n, h->idx, h->d, h->Qd, ctx->d_status, st));
+    ++h->hyper_intervals;
+  }
+  // fixed point of the coefficient stage
+  int round = round_hint, done_h = 0, total = 0;
+  while (!done_h) {
+    const int rr = std::min(round, o.maxit - total);
+    if (hyper) {
+      for (int k = 0; k < rr; ++k) {
+        VP_K(VP_K_DEIM_ROUND, deim_round(h->g, n, p, h->d, h->Qd, w.Ze, h->F, h->c, w.gX, w.flags, st));
+        VP_K(VP_K_COEFF_UPDATE,
+             coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, S.dt, o.tol, o.maxit, o.stall_floor,
+                          o.stall_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st));
+      }
+    } else {
+      VP_TRY(S.rounds(rr));
+    }
+    total += rr;
+    VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    VP_CUDA(cudaStreamSynchronize(st));
+    if (!ctx->pending.empty()) vp_prof_collect(ctx);
+    done_h = ctx->h_pinned[1];
+    if (!done_h && total >= o.maxit) break;
+    round = 2;
+  }
+  const int its = ctx->h_pinned[2];
+  *its_out = its;
+  if (!done_h || its >= o.maxit) {
+    VP_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_pinned[0] != 0 || !done_h)
+      return vp_fail(ctx, VP_ENOCONV, "fixed point did not converge in %d iterations (interval %d)",
+                     o.maxit, h->intervals);
+  }
+  VP_TRY(S.post());
+  ++h->intervals;
+  return VP_OK;
+}
+}  // namespace
+
+vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          const vp_hyper_opts* opts, vp_hyper** out) {
+  void* stream = nullptr;
+  VP_ENTER();
+  if (!out || !opts) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  *out = nullptr;
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  const vp_hyper_opts& o = *opts;
+  if (o.nsub < n || o.nsub > p || !o.sub_idx)
+    return vp_fail(ctx, VP_EINVAL, "subsample of %d outside [n, p] = [%d, %d] or no indices", o.nsub,
+                   n, p);
+  if (o.dim < 1 || !o.eta) return vp_fail(ctx, VP_EINVAL, "parameters eta (p x dim) are required");
+  if (o.T < 1 || (int64_t)o.T * o.nsub > 256)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "window T = %d with p* = %d: need T >= 1, p* T <= 256", o.T,
+                   o.nsub);
+  const int m = (o.T + 1) * o.nsub;
+  if (o.d < 1 || o.d > 128 || o.d > m || (int64_t)m * o.d > 25600 || o.d > N)
+    return vp_fail(ctx, VP_EINVAL, "d = %d outside [1, min(p* (T+1), 128, N)] or m d > 25600", o.d);
+  if (o.n_up < 0 || o.n_up > o.d || o.k_deim < 1)
+    return vp_fail(ctx, VP_EINVAL, "n_up outside [0, d] or k_deim < 1");
+  if (o.r_max < 1 || o.r_max > 64 || !(o.dmd_tol >= 0.0))
+    return vp_fail(ctx, VP_EINVAL, "r_max outside [1, 64] or dmd_tol < 0");
+  if ((int64_t)o.nsub * (o.nsub + o.r_max) * 8 > 200 * 1024)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "RBF system of p* = %d too large", o.nsub);
+  auto* h = new vp_hyper();
+  h->ctx = ctx;
+  h->grid = *grid;
+  h->g = make_gridc(*grid, N);
+  h->N = N;
+  h->n = n;
+  h->p = p;
+  h->nsub = o.nsub;
+  h->dim = o.dim;
+  h->T = o.T;
+  h->d = o.d;
+  h->n_up = o.n_up;
+  h->k_deim = o.k_deim;
+  h->r_max = o.r_max;
+  h->dmd_tol = o.dmd_tol;
+  const int q = o.nsub, Nx = grid->Nx, n2 = 2 * n, rm = o.r_max;
+  const size_t scratch = std::max(std::max(dmd_fit_scratch(Nx, o.T * q, rm),
+                                           deim_basis_scratch(ctx->num_sms, N, m)),
+                                  std::max(deim_indices_scratch(ctx->num_sms, N, o.d),
+                                           deim_weights_scratch(ctx->num_sms, N, o.d)));
+  const size_t bytes = arena_bytes(q, 4) + arena_bytes(o.d, 4) + arena_bytes((size_t)p * o.dim, 8) +
+                       arena_bytes((size_t)q * o.dim, 8) + arena_bytes(1, 8) +
+                       arena_bytes((size_t)2 * (o.T + 1) * q * Nx, 8) +
+                       arena_bytes((size_t)(o.T + 1) * q * N, 8) + 2 * arena_bytes((size_t)rm * Nx, 8) +
+                       2 * arena_bytes((size_t)rm * rm, 8) + arena_bytes((size_t)q * rm, 8) +
+                       arena_bytes((size_t)p * rm, 8) + 2 * arena_bytes((size_t)p * Nx, 8) +
+                       2 * arena_bytes((size_t)o.d * N, 8) + arena_bytes(o.d, 8) +
+                       arena_bytes((size_t)o.d * n2, 8) + arena_bytes(scratch, 8);
+  cudaError_t e = cudaMalloc(&h->mem, bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    return vp_cuda_check(ctx, e, "cudaMalloc (DMD-DEIM state)");
+  }
+  Arena a{(char*)h->mem, 0, bytes};
+  h->sub = a.take<int32_t>(q);
+  h->idx = a.take<int32_t>(o.d);
+  h->eta = a.take<double>((size_t)p * o.dim);
+  h->eta_s = a.take<double>((size_t)q * o.dim);
+  h->eps = a.take<double>(1);
+  h->phi_ring = a.take<double>((size_t)2 * (o.T + 1) * q * Nx);
+  h->y_ring = a.take<double>((size_t)(o.T + 1) * q * N);
+  h->B = a.take<double>((size_t)rm * Nx);
+  h->Bp = a.take<double>((size_t)rm * Nx);
+  h->A = a.take<double>((size_t)rm * rm);
+  h->S = a.take<double>((size_t)rm * rm);
+  h->beta_s = a.take<double>((size_t)q * rm);
+  h->beta = a.take<double>((size_t)p * rm);
+  h->phi_half = a.take<double>((size_t)p * Nx);
+  h->F = a.take<double>((size_t)p * Nx);
+  h->Psi = a.take<double>((size_t)o.d * N);
+  h->Psi_prev = a.take<double>((size_t)o.d * N);
+  h->c = a.take<double>(o.d);
+  h->Qd = a.take<double>((size_t)o.d * n2);
+  h->scratch = a.take<char>(scratch);
+  cudaStream_t s0 = nullptr;
+  e = cudaMemcpyAsync(h->sub, o.sub_idx, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, s0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->eta, o.eta, sizeof(double) * p * o.dim, cudaMemcpyDeviceToDevice, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->phi_half, 0, sizeof(double) * p * Nx, s0);
+  if (e == cudaSuccess) {
+    k_gather_eta<<<1, 256, 0, s0>>>(o.dim, q, h->sub, h->eta, p, h->eta_s, ctx->d_status);
+    rbf_width_run(o.dim, q, h->eta_s, h->eps, s0);
+    e = cudaStreamSynchronize(s0);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(h->mem);
+    delete h;
+    return vp_cuda_check(ctx, e, "DMD-DEIM set-up");
+  }
+  *out = h;
+  return VP_OK;
+}
+
+vp_status vp_hyper_step(vp_hyper* h, double* Q, double* Z, double dt, int32_t nsteps,
+                        const vp_step_opts* opts, double* trace, int32_t* iters, double* kstate,
+                        void* stream) {
+  if (!h) return VP_EINVAL;
+  vp_ctx* ctx = h->ctx;
+  VP_ENTER();
+  if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
+  if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
+  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 1, 0, 0, nullptr};
+  if (opts) o = *opts;
+  if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
+  if (o.arith < 1 || o.arith > 2)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "the DMD-DEIM step needs arith 1 or 2");
+  if (o.freeze_basis) return vp_fail(ctx, VP_EUNSUPPORTED, "the DMD-DEIM step evolves the basis");
+  const int n = h->n, p = h->p;
+  if ((int64_t)4 * n * n + (int64_t)2 * n * p > 25600)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "4n^2 + 2n p exceeds 25600");
+  o.nsub = h->nsub;
+  o.sub_idx = h->sub;
+  Red R;
+  VP_TRY(red_setup(ctx, &h->grid, h->N, n, p, 0, st, R, true, h->nsub));
+  DFStep S(ctx, R, Q, Z, dt, o, kstate, st);
+  const int64_t tstride = (int64_t)p * 2;
+  int round = 4;
+  for (int step = 0; step < nsteps; ++step) {
+    int its = 0;
+    VP_TRY(hyper_interval(h, R, S, trace ? trace + step * tstride : nullptr, round, &its));
+    if (iters)
+      VP_CUDA(cudaMemcpyAsync(iters + step, R.w.flags + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    round = its > 2 ? its : 2;
+  }
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_hyper_info(vp_hyper* h, int32_t* intervals, int32_t* hyper_intervals, int32_t* r_dmd,
+                        int32_t* idx, double* Phi, void* stream) {
+  if (!h) return VP_EINVAL;
+  vp_ctx* ctx = h->ctx;
+  VP_ENTER();
+  if (intervals) *intervals = h->intervals;
+  if (hyper_intervals) *hyper_intervals = h->hyper_intervals;
+  if (r_dmd) *r_dmd = h->r;
+  if (idx) VP_CUDA(cudaMemcpyAsync(idx, h->idx, sizeof(int32_t) * h->d, cudaMemcpyDeviceToDevice, st));
+  if (Phi)
+    VP_CUDA(cudaMemcpyAsync(Phi, h->phi_half, sizeof(double) * h->p * h->grid.Nx,
+                            cudaMemcpyDeviceToDevice, st));
+  return VP_OK;
+}
+
+vp_status vp_hyper_destroy(vp_hyper* h) {
+  if (!h) return VP_OK;
+  {
+    std::lock_guard<std::mutex> lock(h->ctx->mu);
+    DeviceGuard guard(h->ctx->device);
+    cudaFree(h->mem);
+  }
+  delete h;
+  return VP_OK;
+}
+
 // ------------------------------------------------------------------ tuning
 vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm) {
   if (!ctx || knob < 0 || knob >= TUNE_COUNT || blocks_per_sm < 1 || blocks_per_sm > 32)
@@ -805,7 +1090,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_affine", "k_cell_gradient", "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent",
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
-    "k_init", "k_load", "k_subset"};
+    "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {

@@ -382,6 +382,36 @@ void init_launch_zeta(int64_t N, int p, int n, const double* Q, const double* X,
 void init_launch_zeta_to_Z(int n, int p, const double2* zeta, double* Z, cudaStream_t st);
 void init_kernels_init();  // kernel attributes of init.cu
 void deim_init();          // kernel attributes of deim.cu
+// deim.cu: DEIM construction and DMD on caller-owned scratch (sizes below)
+size_t deim_basis_scratch(int sms, int64_t N, int m);
+vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t ldy, int d,
+                         double* Psi, double* sigma, void* scratch, cudaStream_t st);
+size_t deim_indices_scratch(int sms, int64_t N, int d);
+// Psi_prev == nullptr: all d indices by the greedy rule; else idx holds the
+// previous indices and the n_up most rotated positions are renewed
+vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int32_t* idx,
+                           const double* Psi_prev, int n_up, void* scratch, cudaStream_t st);
+size_t deim_weights_scratch(int sms, int64_t N, int d);
+vp_status deim_weights_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, const int32_t* idx,
+                           double Mq, double* c, void* scratch, cudaStream_t st);
+size_t dmd_fit_scratch(int nx, int m, int r_max);
+vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double* Yp, double tol,
+                      int r_max, int* r_out, double* B, double* Bpinv, double* A, double* S,
+                      double* sigma, void* scratch, cudaStream_t st);
+void dmd_coords_run(int nx, int r, const double* Bpinv, int q, const double* Phi, double* beta,
+                    cudaStream_t st);
+void rbf_run(int dim, int q, const double* eta_s, int K, const double* values, int p,
+             const double* eta, double eps, const double* eps_dev, double* out, int* status,
+             cudaStream_t st);
+void rbf_width_run(int dim, int q, const double* eta_s, double* eps, cudaStream_t st);
+void dmd_potential_run(int nx, int r, const double* B, const double* A, const double* S, int p,
+                       const double* beta, int ksteps, int half, double* Phi, cudaStream_t st);
+void phi_at_qz(const GridC& g, int64_t N, int n, int q, const double* Q, const double* Zs,
+               const double* phi, double* Y, int sms, cudaStream_t st);
+void gather_rows_lp(const void* Q2, int mode, int64_t N, int n2, const int32_t* idx, int d,
+                    double* out, int* status, cudaStream_t st);
+void deim_round(const GridC& g, int n, int p, int d, const double* Qd, const double* Ze,
+                const double* F, const double* c, double* gX, const int* done, cudaStream_t st);
 // Particle loading (load.cu): eta p x 3, X and V p x N; mode 0 quiet start,
 // mode 1 Philox4x32-10 keyed by seed.
 void load_particles(int family, int mode, unsigned long long seed, double k, int64_t N, int p,

@@ -53,6 +53,26 @@ def test_dmd_linear_dynamics_parity(ctx):
     check_fit(ctx, windows, 1e-10, 1e-9)
 
 
+def signed_windows(Nx=40, q=6, T=8, seed=5):
+    """Linear dynamics with a real negative eigenvalue (a mode that changes
+    sign every step), a real positive one and a conjugate pair in the left
+    half plane: half steps take the principal power of each eigenvalue."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam = np.array([-0.8, 0.6, 0.9 * np.exp(2.6j), 0.9 * np.exp(-2.6j)])
+    v = rng.standard_normal((Nx, 4)).astype(complex)
+    v[:, 2] += 1j * rng.standard_normal(Nx)
+    v[:, 3] = v[:, 2].conj()
+    c = rng.standard_normal((q, 4)).astype(complex)
+    c[:, 2] += 1j * rng.standard_normal(q)
+    c[:, 3] = c[:, 2].conj()
+    return [np.stack([np.real(v @ (c[i] * lam ** k)) for k in range(T + 1)], axis=1)
+            for i in range(q)]
+
+
+def test_dmd_negative_real_eigenvalue_parity(ctx):
+    check_fit(ctx, signed_windows(), 1e-10, 1e-8)
+
+
 def test_dmd_reduced_potentials_parity(ctx):
     """Potentials of sampled parameters over six reduced steps of the oracle
     (two-stream), Algorithm 1 with the paper's tolerance."""
