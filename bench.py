@@ -397,6 +397,69 @@ def subsample_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
             "subsample": [int(i) for i in sub.cpu()]}
 
 
+def hyper_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
+    """DMD-DEIM reduced dynamics (Algorithm 2) with the paper's two-stream
+    hyper-reduction settings: p* = 12 sampled parameters, window T = 3,
+    d = 32 DEIM points, 12 indices renewed per interval and all of them every
+    3 intervals, DMD tolerance 1e-5; double-float row work.  The bench
+    workload's sizes (N = 1e5, p = 64, Nx = 128, dt = 0.05) with the quiet
+    start (Hammersley loading) that the paper uses for DMD-DEIM and the rank
+    by tail energy < 1e-8 with 2n in [8, 20] (the quiet start's spectrum falls
+    below 1e-8 sigma_1 before 2n = 20).  Timed intervals follow the windows'
+    fill and a first DMD-DEIM interval; the subsampled reduced step without
+    DMD-DEIM is timed on the same state for comparison."""
+    from paper_2201_05555_gb300 import make_grid
+    from paper_2201_05555_gb300.binding import KERNELS
+    wl = workload()
+    X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=True)
+    Q, Z, _, n = ctx.init_csvd_rank(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev),
+                                    4, wl.n2 // 2, 1e-8)
+    sub = ctx.param_subsample(Z, 12)
+    eta = torch.tensor([[e["v0"]] for e in wl.etas], device=dev, dtype=torch.float64)
+    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(run):
+        ev = _events(torch, steps)
+        for s_ in range(steps):
+            flush.zero_()
+            ev[s_][0].record(stream)
+            run()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    Qr, Zr, Kr = Q.clone(), Z.clone(), torch.zeros_like(Z)
+    for _ in range(3):
+        ctx.basis_update(grid, Qr, Zr, wl.dt, 1, arith=ARITH, kstate=Kr, sub=sub)
+    ms_sub = timed(lambda: ctx.basis_update(grid, Qr, Zr, wl.dt, 1, arith=ARITH, kstate=Kr,
+                                            sub=sub))
+    T_ = 3
+    h = ctx.hyper(grid, wl.N, n, wl.p, sub, eta, T=T_, d=32, n_up=12, k_deim=3, dmd_tol=1e-5)
+    K = torch.zeros_like(Z)
+    h.step(Q, Z, wl.dt, T_ + 2, arith=ARITH, kstate=K)
+    its = []
+    ms = timed(lambda: its.append(h.step(Q, Z, wl.dt, 1, arith=ARITH, kstate=K)[1]))
+    # share of each kernel over three more intervals, every launch timed
+    ctx.profile_reset()
+    ctx.profile_enable(list(range(len(KERNELS))))
+    h.step(Q, Z, wl.dt, 3, arith=ARITH, kstate=K)
+    torch.cuda.synchronize()
+    ctx.profile_enable([])
+    prof = ctx.profile_read()
+    tot = sum(v[2] for v in prof.values()) or 1.0
+    share = sorted(((k, v[2] / tot) for k, v in prof.items() if v[2] > 0), key=lambda x: -x[1])
+    inf = h.info()
+    h.close()
+    return {"workload": f"two-stream, N=1e5, p=64, Nx=128, dt=0.05, quiet start, 2n={2 * n}; "
+                        "DMD-DEIM coefficients (p*=12, T=3, d=32, n_up=12, k_DEIM=3, DMD tol 1e-5)",
+            "value": wl.N * wl.p / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "subsampled_step_ms": ms_sub,
+            "fixed_point_iters": float(np.mean([int(i[0]) for i in its])), "dmd_rank": inf["r"],
+            "kernel_share": {k: round(f, 3) for k, f in share[:8]}}
+
+
 def deim_build_measure(ctx, torch, dev, reps: int = 5) -> dict:
     """DEIM construction (Sec. 4.2) at N = 1e5 particles: m = 8 x 11 snapshot
     columns (8 sampled parameters over a window of 11 steps), d = 32: basis,
@@ -420,6 +483,40 @@ def deim_build_measure(ctx, torch, dev, reps: int = 5) -> dict:
     ms = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
     return {"workload": f"DEIM construction, N=1e5, m={m} snapshot columns, d={d}",
             "ms_per_construction": ms, "snapshot_values_per_s": N * m / (ms / 1e3)}
+
+
+def dmd_measure(ctx, torch, dev, reps: int = 5) -> dict:
+    """DMD of the potential (Sec. 4.2, Algorithm 1) on the two-stream grid
+    Nx = 128: p* = 12 sampled parameters over a window of T = 3 steps
+    (36 data columns), coordinates of the samples, Gaussian RBF interpolation
+    to p = 64 parameters and the predicted potentials at the half step."""
+    nx, ps, T, p = 128, 12, 3, 64
+    g = torch.Generator(device=dev)
+    g.manual_seed(W.BASE_SEED + 7)
+    x = torch.arange(nx, device=dev, dtype=torch.float64) * (2 * np.pi / nx)
+    amp = 1.0 + 0.5 * torch.rand(ps, 1, generator=g, device=dev, dtype=torch.float64)
+    t = torch.arange(T + 1, device=dev, dtype=torch.float64) * 0.05
+    # three growing travelling Fourier modes, one window per sample
+    win = torch.stack([amp * torch.exp(0.1 * k * tk) * torch.cos(k * x + 0.5 * k * tk)
+                       for tk in t for k in (1, 2, 3)]).view(T + 1, 3, ps, nx).sum(1)
+    Y = win[:T].permute(1, 0, 2).reshape(ps * T, nx).contiguous()
+    Yp = win[1:].permute(1, 0, 2).reshape(ps * T, nx).contiguous()
+    last = win[T].contiguous()
+    eta_s = torch.linspace(2.0, 3.0, ps, device=dev, dtype=torch.float64)[:, None].contiguous()
+    eta = torch.linspace(2.0, 3.0, p, device=dev, dtype=torch.float64)[:, None].contiguous()
+    eps = 0.3 / (1.0 / (ps - 1))
+    stream = torch.cuda.current_stream(dev)
+    ev = _events(torch, reps + 1)
+    for r in range(reps + 1):  # first repetition is the warm-up
+        ev[r][0].record(stream)
+        fit = ctx.dmd_fit(Y, Yp, 1e-5, 64)
+        beta = ctx.rbf_interpolate(eta_s, ctx.dmd_coords(fit, last), eta, eps)
+        ctx.dmd_potential(fit, beta, 0, 1)
+        ev[r][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev[1:])[reps // 2]
+    return {"workload": f"DMD fit + coordinates + RBF + potentials, Nx={nx}, p*={ps}, T={T}, p={p}",
+            "rank": fit["r"], "ms_per_fit": ms}
 
 
 def served_measure(args, dev_index: int) -> dict:
@@ -657,7 +754,9 @@ def ours(args, rank, world):
         line["precision_form"] = precision_measure(ctx, torch, dev, flush)
         line["batched"] = batched_measure(args, ctx, torch, dev, flush)
         line["subsampled"] = subsample_measure(ctx, torch, dev, flush)
+        line["hyper"] = hyper_measure(ctx, torch, dev, flush)
         line["deim_build"] = deim_build_measure(ctx, torch, dev)
+        line["dmd"] = dmd_measure(ctx, torch, dev)
         line["served"] = served_measure(args, local)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)

@@ -21,11 +21,6 @@
 #include <cmath>
 #include <vector>
 
-namespace vpk {
-void init_launch_jacobi(int m, double2* A, double2* W, double* lambda, double2* Wout, int* status,
-                        cudaStream_t st);
-}
-
 namespace {
 using namespace vpk;
 
@@ -44,16 +39,31 @@ __global__ void k_phi_at(GridC g, int64_t N, int p, const double* __restrict__ X
   }
 }
 
-// part[blockIdx.x][a][b] = sum over this block's rows of Y_a Y_b (m x m, m <= 256)
+// part[blockIdx.x][e] = sum over this block's rows of Y_a Y_b for the packed
+// lower triangle e = a (a + 1) / 2 + b, b <= a (m (m + 1) / 2 entries, m <= 256)
 #define YG_ROWS 32
+__device__ __forceinline__ void tri_ab(int e, int& a, int& b) {
+  int aa = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while (aa * (aa + 1) / 2 > e) --aa;
+  while ((aa + 1) * (aa + 2) / 2 <= e) ++aa;
+  a = aa;
+  b = e - aa * (aa + 1) / 2;
+}
 __global__ void k_ygram(int64_t N, int m, const double* __restrict__ Y, int64_t ldy,
                         double* __restrict__ part) {
   extern __shared__ double ys[];  // m x YG_ROWS
-  const int tot = m * m;
+  const int tot = m * (m + 1) / 2;
   double acc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  int ea[8], eb[8];
   const int e0 = blockIdx.y * blockDim.x * 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    acc[q] = 0.0;
+    const int e = e0 + q * blockDim.x + threadIdx.x;
+    ea[q] = -1;
+    eb[q] = 0;
+    if (e < tot) tri_ab(e, ea[q], eb[q]);
+  }
   for (int64_t tile = blockIdx.x; tile * YG_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * YG_ROWS;
     const int rows = (int)((int64_t)YG_ROWS < N - base ? (int64_t)YG_ROWS : N - base);
@@ -65,11 +75,11 @@ __global__ void k_ygram(int64_t N, int m, const double* __restrict__ Y, int64_t 
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * blockDim.x + threadIdx.x;
-      if (e < tot) {
-        const int a = e / m, b = e - a * m;
+      if (ea[q] >= 0) {
+        const double* ya = ys + ea[q] * YG_ROWS;
+        const double* yb = ys + eb[q] * YG_ROWS;
         double s = acc[q];
-        for (int r = 0; r < YG_ROWS; ++r) s = fma(ys[a * YG_ROWS + r], ys[b * YG_ROWS + r], s);
+        for (int r = 0; r < YG_ROWS; ++r) s = fma(ya[r], yb[r], s);
         acc[q] = s;
       }
     }
@@ -81,14 +91,128 @@ __global__ void k_ygram(int64_t N, int m, const double* __restrict__ Y, int64_t 
   }
 }
 
-__global__ void k_to_complex(int m, const double* __restrict__ a, double2* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x)
-    out[e] = make_double2(a[e], 0.0);
+// Real symmetric cyclic Jacobi (m <= 256; one block; G given as its packed
+// lower triangle): G = W diag(lambda) W^T
+// with lambda descending and the columns of W (Wout, m x m row-major) in the
+// same order.  Round-robin ordering: the m/2 disjoint pairs of a round are
+// rotated together; a pair is rotated unless |g_jk| <= 1e-15 sqrt|g_jj g_kk|
+// or both diagonal entries are below 1e-14 of the largest one (a pair inside
+// the rounding-level null space, whose rotations would go on forever and
+// change no eigenpair above it).
+// Stops after a sweep without rotations (at most max_sweeps, else
+// VP_ENOCONV).  With m <= JS_SMEM_M, G and W live in shared memory.
+#define JS_SMEM_M 112
+__global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __restrict__ Ag,
+                             double* __restrict__ Wg, double* __restrict__ lambda,
+                             double* __restrict__ Wout, int max_sweeps, int* status) {
+  extern __shared__ double js[];
+  __shared__ double rc[128], rs[128];
+  __shared__ int pj[128], pk[128];
+  __shared__ int nrot;
+  __shared__ double nu;
+  __shared__ int order[256];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const bool sm = m <= JS_SMEM_M;
+  double* A = sm ? js : Ag;
+  double* W = sm ? js + m * m : Wg;
+  for (int e = t; e < m * m; e += nt) {  // Gin: packed lower triangle
+    const int i = e / m, j = e - i * m;
+    const int hi = max(i, j), lo = min(i, j);
+    A[e] = Gin[hi * (hi + 1) / 2 + lo];
+    W[e] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int slots = (m + 1) & ~1, npair = slots / 2;
+  bool conv = false;
+  for (int sweep = 0; sweep < max_sweeps && !conv; ++sweep) {
+    if (t == 0) {
+      nrot = 0;
+      double dm = 0.0;
+      for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(A[j * m + j]));
+      nu = 1e-14 * dm;
+    }
+    __syncthreads();
+    for (int round = 0; round < slots - 1; ++round) {
+      for (int q = t; q < npair; q += nt) {
+        const int a = q, b = slots - 1 - q;
+        const int ia = (a == 0) ? 0 : 1 + (a - 1 + round) % (slots - 1);
+        const int ib = (b == 0) ? 0 : 1 + (b - 1 + round) % (slots - 1);
+        const int j = min(ia, ib), k = max(ia, ib);
+        pj[q] = j;
+        pk[q] = k;
+        double c = 1.0, sn = 0.0;
+        if (k < m) {
+          const double ajk = A[j * m + k], ajj = A[j * m + j], akk = A[k * m + k];
+          if (fabs(ajk) > 1e-15 * sqrt(fabs(ajj * akk)) && fabs(ajk) > 1e-300 &&
+              fmax(fabs(ajj), fabs(akk)) > nu) {
+            atomicAdd(&nrot, 1);
+            const double tau = (akk - ajj) / (2.0 * ajk);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            sn = tt * c;
+          }
+        }
+        rc[q] = c;
+        rs[q] = sn;
+      }
+      __syncthreads();
+      for (int e = t; e < npair * m; e += nt) {  // columns j, k of A and W
+        const int q = e / m, r = e - q * m;
+        const int j = pj[q], k = pk[q];
+        if (k >= m || rs[q] == 0.0) continue;
+        const double c = rc[q], sn = rs[q];
+        const double aj = A[r * m + j], ak = A[r * m + k];
+        A[r * m + j] = c * aj - sn * ak;
+        A[r * m + k] = sn * aj + c * ak;
+        const double wj = W[r * m + j], wk = W[r * m + k];
+        W[r * m + j] = c * wj - sn * wk;
+        W[r * m + k] = sn * wj + c * wk;
+      }
+      __syncthreads();
+      for (int e = t; e < npair * m; e += nt) {  // rows j, k of A
+        const int q = e / m, cidx = e - q * m;
+        const int j = pj[q], k = pk[q];
+        if (k >= m || rs[q] == 0.0) continue;
+        const double c = rc[q], sn = rs[q];
+        const double aj = A[j * m + cidx], ak = A[k * m + cidx];
+        A[j * m + cidx] = c * aj - sn * ak;
+        A[k * m + cidx] = sn * aj + c * ak;
+      }
+      __syncthreads();
+    }
+    conv = nrot == 0;
+    __syncthreads();
+    if (!conv && sweep == max_sweeps - 1 && t == 0) vp_set_status(status, VP_ENOCONV);
+  }
+  if (t == 0) {  // eigenvalues descending (selection order)
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int i = 0; i < m; ++i) {
+      int best = i;
+      for (int j = i + 1; j < m; ++j)
+        if (A[order[j] * m + order[j]] > A[order[best] * m + order[best]]) best = j;
+      const int tmp = order[i];
+      order[i] = order[best];
+      order[best] = tmp;
+    }
+  }
+  __syncthreads();
+  for (int i = t; i < m; i += nt) lambda[i] = A[order[i] * m + order[i]];
+  for (int e = t; e < m * m; e += nt) {
+    const int r = e / m, c = e - r * m;
+    Wout[e] = W[r * m + order[c]];
+  }
 }
+
+static void jacobi_sym(int m, const double* G, double* Ascr, double* Wscr, double* lambda,
+                       double* Wout, int* status, cudaStream_t st) {
+  const size_t smem = m <= JS_SMEM_M ? sizeof(double) * 2 * m * m : 0;
+  k_jacobi_sym<<<1, 512, smem, st>>>(m, G, Ascr, Wscr, lambda, Wout, 60, status);
+}
+
 
 // psi_k = Y w_k / sqrt(lambda_k), k < d; sigma = sqrt(max(lambda, 0)) (m values)
 __global__ void k_psi(int64_t N, int m, int d, const double* __restrict__ Y, int64_t ldy,
-                      const double2* __restrict__ W, const double* __restrict__ lam,
+                      const double* __restrict__ W, const double* __restrict__ lam,
                       double* __restrict__ Psi, double* __restrict__ sigma, int* status) {
   extern __shared__ double cs[];  // m x d coefficients
   for (int e = threadIdx.x; e < m * d; e += blockDim.x) {
@@ -98,7 +222,7 @@ __global__ void k_psi(int64_t N, int m, int d, const double* __restrict__ Y, int
       vp_set_status(status, VP_ENUMERIC);
       cs[e] = 0.0;
     } else {
-      cs[e] = W[a * m + k].x / sqrt(l);
+      cs[e] = W[a * m + k] / sqrt(l);
     }
   }
   if (sigma && blockIdx.x == 0)
@@ -114,95 +238,56 @@ __global__ void k_psi(int64_t N, int m, int d, const double* __restrict__ Y, int
   }
 }
 
-// Solve A c = b for the k x k system A_ij = Psi_j[idx_i], b_i = Psi_k[idx_i]
-// (Gauss-Jordan with partial pivoting, one block, k <= 128): c -> cvec.
-__global__ void k_deim_small(int64_t N, int k, const double* __restrict__ Psi,
-                             const int32_t* __restrict__ idx, double* __restrict__ cvec,
-                             int* status, const int* __restrict__ renew) {
-  if (renew && !renew[k]) return;
-  extern __shared__ double ab[];  // k x (k + 1)
-  __shared__ int piv, ok;
-  const int w = k + 1;
-  for (int e = threadIdx.x; e < k * w; e += blockDim.x) {
-    const int i = e / w, j = e - i * w;
-    ab[e] = Psi[(int64_t)j * N + idx[i]];  // column j < k of the basis, j = k the right side
-  }
-  if (threadIdx.x == 0) ok = 1;
-  __syncthreads();
-  for (int c = 0; c < k; ++c) {
-    if (threadIdx.x == 0) {
-      int b = c;
-      double best = fabs(ab[c * w + c]);
-      for (int r = c + 1; r < k; ++r)
-        if (fabs(ab[r * w + c]) > best) {
-          best = fabs(ab[r * w + c]);
-          b = r;
-        }
-      piv = b;
-      if (!(best > 0.0) || !isfinite(best)) ok = 0;
-    }
-    __syncthreads();
-    if (!ok) break;
-    if (piv != c)
-      for (int j = threadIdx.x; j < w; j += blockDim.x) {
-        const double t = ab[c * w + j];
-        ab[c * w + j] = ab[piv * w + j];
-        ab[piv * w + j] = t;
-      }
-    __syncthreads();
-    const double inv = 1.0 / ab[c * w + c];
-    __syncthreads();
-    for (int j = threadIdx.x; j < w; j += blockDim.x) ab[c * w + j] *= inv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < k * w; e += blockDim.x) {
-      const int r = e / w, j = e - r * w;
-      if (r != c && j != c) ab[e] -= ab[r * w + c] * ab[c * w + j];
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < k; r += blockDim.x)
-      if (r != c) ab[r * w + c] = 0.0;
-    __syncthreads();
-  }
-  if (!ok) {
-    if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) cvec[i] = 0.0;
-    return;
-  }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) cvec[i] = ab[i * w + k];
-}
-
-// |psi_k - sum_{j<k} c_j psi_j| per row; block partial arg-max (lowest row on ties).
-// With renew (the index update): nothing unless position k is renewed, and
-// rows held at another position (inherited, or renewed before k) are skipped.
-__global__ void k_deim_resid(int64_t N, int k, const double* __restrict__ Psi,
-                             const double* __restrict__ cvec, double* __restrict__ pval,
-                             int64_t* __restrict__ pidx, const int32_t* __restrict__ idx, int d,
-                             const int* __restrict__ renew) {
-  if (renew && !renew[k]) return;
-  __shared__ double cs[128];
+// Step k of the greedy DEIM index selection written as Gaussian elimination
+// with row pivoting on the N x d basis: after eliminating the pivots
+// l_1..l_{k-1} from column k, that column is the residual of psi_k after
+// interpolation from psi_1..psi_{k-1} at those rows, so the greedy choice is
+// the row of its largest magnitude (the known equivalence of DEIM with
+// partial-pivoting LU; Drmac and Gugercin, SIAM J. Sci. Comput. 38, 2016).
+// R (d x N) holds the columns being eliminated, prow[j] (j > k-1) the
+// multipliers R_j[l_{k-1}] / R_{k-1}[l_{k-1}] of the previous pivot.  Each
+// block updates its rows of columns k..d-1 and keeps its arg-max of |R_k|
+// (rows held at another position skipped; ties to the lowest row); the last
+// block to finish picks l_k (or keeps the inherited index when renew says
+// so), writes idx[k] and the multipliers of l_k for step k + 1.
+__global__ void k_deim_lu(int64_t N, int d, int k, double* R, double* prow, int32_t* idx,
+                          const int* __restrict__ renew, double* pval, int64_t* pidx, int* ticket,
+                          int* status) {
+  __shared__ double mult[128];
+  __shared__ int32_t held[128];
+  __shared__ int nheld, last;
   __shared__ double bv[32];
   __shared__ int64_t bi[32];
-  __shared__ int32_t held[128];
-  __shared__ int nheld;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = cvec[j];
+  const bool inherit = renew && !renew[k];
   if (threadIdx.x == 0) {
     int c = 0;
-    if (renew)
-      for (int j = 0; j < d; ++j)
-        if (j != k && (j < k || !renew[j])) held[c++] = idx[j];
+    for (int j = 0; j < d; ++j)
+      if (j != k && (j < k || (renew && !renew[j]))) held[c++] = idx[j];
     nheld = c;
   }
+  for (int j = threadIdx.x; j < d; j += blockDim.x) mult[j] = (k > 0 && j >= k) ? prow[j] : 0.0;
   __syncthreads();
   double best = -1.0;
   int64_t bidx = INT64_MAX;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < N;
        l += (int64_t)gridDim.x * blockDim.x) {
+    double rk;
+    if (k > 0) {
+      const double piv = R[(int64_t)(k - 1) * N + l];
+      for (int j = k; j < d; ++j) {
+        double* e = R + (int64_t)j * N + l;
+        const double v = fma(-piv, mult[j], *e);
+        *e = v;
+        if (j == k) rk = v;
+      }
+    } else {
+      rk = R[l];
+    }
+    if (inherit) continue;
     bool skip = false;
     for (int j = 0; j < nheld; ++j) skip |= held[j] == (int32_t)l;
     if (skip) continue;
-    double r = Psi[(int64_t)k * N + l];
-    for (int j = 0; j < k; ++j) r = fma(-cs[j], Psi[(int64_t)j * N + l], r);
-    const double a = fabs(r);
+    const double a = fabs(rk);
     if (a > best || (a == best && l < bidx)) {
       best = a;
       bidx = l;
@@ -221,35 +306,74 @@ __global__ void k_deim_resid(int64_t N, int k, const double* __restrict__ Psi,
     bv[wid] = best;
     bi[wid] = bidx;
   }
+  __threadfence();  // this thread's updates of R before the ticket
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (bv[w] > best || (bv[w] == best && bi[w] < bidx)) {
-        best = bv[w];
-        bidx = bi[w];
+      if (bv[w] > bv[0] || (bv[w] == bv[0] && bi[w] < bi[0])) {
+        bv[0] = bv[w];
+        bi[0] = bi[w];
       }
-    // warp 0's own result is already in best/bidx only for lane 0; fold it in
-    if (bv[0] > best || (bv[0] == best && bi[0] < bidx)) {
-      best = bv[0];
-      bidx = bi[0];
-    }
-    pval[blockIdx.x] = best;
-    pidx[blockIdx.x] = bidx;
+    pval[blockIdx.x] = bv[0];
+    pidx[blockIdx.x] = bi[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
   }
-}
-
-__global__ void k_deim_pick(int nb, const double* __restrict__ pval,
-                            const int64_t* __restrict__ pidx, int32_t* __restrict__ idx, int k,
-                            const int* __restrict__ renew) {
-  if (threadIdx.x != 0 || (renew && !renew[k])) return;
-  double best = -1.0;
-  int64_t b = INT64_MAX;
-  for (int i = 0; i < nb; ++i)
-    if (pval[i] > best || (pval[i] == best && pidx[i] < b)) {
-      best = pval[i];
-      b = pidx[i];
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ int32_t pick;
+  // arg-max over the block partials: strided per thread, then warps, then
+  // the first thread (ties to the lowest row throughout)
+  double vb = -1.0;
+  int64_t ib = INT64_MAX;
+  if (!inherit)
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+      const double v = __ldcg(pval + i);
+      const int64_t ii = __ldcg(pidx + i);
+      if (v > vb || (v == vb && ii < ib)) {
+        vb = v;
+        ib = ii;
+      }
     }
-  idx[k] = (int32_t)b;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, vb, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, ib, o);
+    if (ov > vb || (ov == vb && oi < ib)) {
+      vb = ov;
+      ib = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    bv[wid] = vb;
+    bi[wid] = ib;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *ticket = 0;
+    int64_t b = idx[k];
+    if (!inherit) {
+      double bb = bv[0];
+      b = bi[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (bv[w] > bb || (bv[w] == bb && bi[w] < b)) {
+          bb = bv[w];
+          b = bi[w];
+        }
+    }
+    if (b < 0 || b >= N) {  // nothing left to pick, or a bad inherited index
+      vp_set_status(status, VP_EINVAL);
+      b = 0;
+    }
+    idx[k] = (int32_t)b;
+    pick = (int32_t)b;
+  }
+  __syncthreads();
+  const double pv = __ldcg(R + (int64_t)k * N + pick);
+  if (threadIdx.x == 0 && (!(pv != 0.0) || !isfinite(pv))) vp_set_status(status, VP_ENUMERIC);
+  for (int j = k + 1 + threadIdx.x; j < d; j += blockDim.x)
+    prow[j] = (pv != 0.0 && isfinite(pv)) ? __ldcg(R + (int64_t)j * N + pick) / pv : 0.0;
 }
 
 // block partial dot products psi_k . prev_k (d x N each): part[blockIdx.x][k]
@@ -391,7 +515,7 @@ __global__ void k_cols_dot(int n, int r1, int r2, const double* __restrict__ U,
 }
 
 // C[a][k] = W[a][k] / sigma_k (m x r) from the Jacobi eigenvectors (real parts)
-__global__ void k_dmd_coeff(int m, int r, const double2* __restrict__ W, const double* __restrict__ lam,
+__global__ void k_dmd_coeff(int m, int r, const double* __restrict__ W, const double* __restrict__ lam,
                             double* __restrict__ C, int* status) {
   for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
     const int a = e / r, k = e - a * r;
@@ -400,7 +524,7 @@ __global__ void k_dmd_coeff(int m, int r, const double2* __restrict__ W, const d
       vp_set_status(status, VP_ENUMERIC);
       C[e] = 0.0;
     } else {
-      C[e] = W[a * m + k].x / sqrt(l);
+      C[e] = W[a * m + k] / sqrt(l);
     }
   }
 }
@@ -503,13 +627,13 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
   double2* R = Qm + r * r;   // r x r
   __shared__ double v[64];
   __shared__ double vv;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x, nl = blockDim.x;
   const double eps = 2.220446049250313e-16;
-  for (int e = lane; e < r * r; e += 32) {
+  for (int e = lane; e < r * r; e += nl) {
     H[e] = make_double2(A[e], 0.0);
     Qm[e] = make_double2((e / r == e % r) ? 1.0 : 0.0, 0.0);
   }
-  __syncwarp();
+  __syncthreads();
   // 1. Hessenberg form (A is real: real reflectors)
   for (int k = 0; k + 2 < r; ++k) {
     const int m = r - k - 1;
@@ -520,23 +644,23 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
     }
     if (sx == 0.0) continue;  // column already reduced (same value in every lane)
     const double alpha = -copysign(sqrt(fma(x0, x0, sx)), x0);
-    for (int i = lane; i < m; i += 32) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * r + k].x;
-    __syncwarp();
+    for (int i = lane; i < m; i += nl) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * r + k].x;
+    __syncthreads();
     if (lane == 0) {
       double t = 0.0;
       for (int i = 0; i < m; ++i) t = fma(v[i], v[i], t);
       vv = t;
     }
-    __syncwarp();
+    __syncthreads();
     const double f = 2.0 / vv;
-    for (int j = lane; j < r; j += 32) {  // H <- P H (rows k+1..)
+    for (int j = lane; j < r; j += nl) {  // H <- P H (rows k+1..)
       double w = 0.0;
       for (int i = 0; i < m; ++i) w = fma(v[i], H[(k + 1 + i) * r + j].x, w);
       w *= f;
       for (int i = 0; i < m; ++i) H[(k + 1 + i) * r + j].x -= v[i] * w;
     }
-    __syncwarp();
-    for (int i = lane; i < r; i += 32) {  // H <- H P, Q <- Q P (columns k+1..)
+    __syncthreads();
+    for (int i = lane; i < r; i += nl) {  // H <- H P, Q <- Q P (columns k+1..)
       double w = 0.0, wq = 0.0;
       for (int j = 0; j < m; ++j) {
         w = fma(H[i * r + k + 1 + j].x, v[j], w);
@@ -549,23 +673,34 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
         Qm[i * r + k + 1 + j].x -= wq * v[j];
       }
     }
-    __syncwarp();
-    for (int i = k + 2 + lane; i < r; i += 32) H[i * r + k] = make_double2(0.0, 0.0);
-    __syncwarp();
+    __syncthreads();
+    for (int i = k + 2 + lane; i < r; i += nl) H[i * r + k] = make_double2(0.0, 0.0);
+    __syncthreads();
   }
-  // 2. complex Schur form by implicit single-shift QR sweeps
+  // 2. complex Schur form by implicit single-shift QR sweeps; a subdiagonal
+  // entry deflates below eps times its diagonal neighbours or below eps |A|_F
+  // (a backward-stable perturbation either way)
+  __shared__ double nrm_s;
+  if (lane == 0) {
+    double t = 0.0;
+    for (int e = 0; e < r * r; ++e) t = fma(A[e], A[e], t);
+    nrm_s = sqrt(t);
+  }
+  __syncthreads();
+  const double floor2 = eps * eps * nrm_s * nrm_s;
   int hi = r - 1, it = 0, total = 0;
   bool failed = false;
+  auto abs2 = [](double2 z) { return fma(z.x, z.x, z.y * z.y); };
   while (hi > 0) {
     int l = hi;
-    for (; l > 0; --l) {
-      double sc = c_abs(H[(l - 1) * r + l - 1]) + c_abs(H[l * r + l]);
-      if (sc == 0.0) sc = 1.0;
-      if (c_abs(H[l * r + l - 1]) <= eps * sc) break;
+    for (; l > 0; --l) {  // squared magnitudes: no square roots in the scan
+      const double sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
+      const double sub2 = abs2(H[l * r + l - 1]);
+      if (sub2 <= eps * eps * sc2 || sub2 <= floor2) break;
     }
-    __syncwarp();
+    __syncthreads();
     if (l > 0 && lane == 0) H[l * r + l - 1] = make_double2(0.0, 0.0);
-    __syncwarp();
+    __syncthreads();
     if (l == hi) {
       --hi;
       it = 0;
@@ -585,7 +720,7 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
       const double2 disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
       const double2 m0 = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
       const double2 m1 = cadd(m0, disc), m2 = csub(m0, disc);
-      mu = c_abs(csub(m1, d)) < c_abs(csub(m2, d)) ? m1 : m2;
+      mu = abs2(csub(m1, d)) < abs2(csub(m2, d)) ? m1 : m2;
     }
     for (int k = l; k < hi; ++k) {
       double2 x, y;
@@ -605,23 +740,23 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
       } else if (x.x == 0.0 && x.y == 0.0) {
         cg = 0.0;
         sg = make_double2(1.0, 0.0);
-      } else {
-        const double ax = c_abs(x), nrm = hypot(ax, c_abs(y));
-        cg = ax / nrm;
-        sg = cmul(make_double2(x.x / ax, x.y / ax), make_double2(y.x / nrm, -y.y / nrm));
+      } else {  // cg = |x| / n, sg = (x / |x|) conj(y) / n, n^2 = |x|^2 + |y|^2
+        const double ax2 = abs2(x), ix = rsqrt(ax2), in = rsqrt(ax2 + abs2(y));
+        cg = ax2 * ix * in;
+        sg = cmul(make_double2(x.x * ix, x.y * ix), make_double2(y.x * in, -y.y * in));
       }
-      __syncwarp();
+      __syncthreads();
       const int j0 = k == l ? l : k - 1;
-      for (int j = j0 + lane; j < r; j += 32) {  // rows k, k+1 <- G [rows]
+      for (int j = j0 + lane; j < r; j += nl) {  // rows k, k+1 <- G [rows]
         const double2 h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
         H[k * r + j] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(sg, h1));
         H[(k + 1) * r + j] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(make_double2(sg.x, -sg.y), h0));
       }
-      __syncwarp();
+      __syncthreads();
       if (k > l && lane == 0) H[(k + 1) * r + k - 1] = make_double2(0.0, 0.0);
       const int i1 = min(k + 2, hi) + 1;
       const double2 sc = make_double2(sg.x, -sg.y);
-      for (int i = lane; i < r; i += 32) {  // columns k, k+1 <- [columns] G^H
+      for (int i = lane; i < r; i += nl) {  // columns k, k+1 <- [columns] G^H
         if (i < i1) {
           const double2 h0 = H[i * r + k], h1 = H[i * r + k + 1];
           H[i * r + k] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(h1, sc));
@@ -631,7 +766,7 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
         Qm[i * r + k] = cadd(make_double2(cg * q0.x, cg * q0.y), cmul(q1, sc));
         Qm[i * r + k + 1] = csub(make_double2(cg * q1.x, cg * q1.y), cmul(q0, sg));
       }
-      __syncwarp();
+      __syncthreads();
     }
     ++it;
     ++total;
@@ -642,13 +777,13 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
   }
   // 3. R = T^{1/2} (upper triangular), superdiagonal by superdiagonal
   bool singular = false;
-  for (int e = lane; e < r * r; e += 32) {
+  for (int e = lane; e < r * r; e += nl) {
     const int i = e / r, j = e - i * r;
     R[e] = i == j ? c_sqrt(H[e]) : make_double2(0.0, 0.0);
   }
-  __syncwarp();
+  __syncthreads();
   for (int dd = 1; dd < r; ++dd) {
-    for (int i = lane; i + dd < r; i += 32) {
+    for (int i = lane; i + dd < r; i += nl) {
       const int j = i + dd;
       double2 s = H[i * r + j];
       for (int k = i + 1; k < j; ++k) s = csub(s, cmul(R[i * r + k], R[k * r + j]));
@@ -660,18 +795,18 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
         R[i * r + j] = c_div(s, den);
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
   if (singular) vp_set_status(status, VP_ENUMERIC);
   // 4. S = Re(Q R Q^H): H <- Q R, then S_ij = Re sum_k H_ik conj(Q_jk)
-  for (int e = lane; e < r * r; e += 32) {
+  for (int e = lane; e < r * r; e += nl) {
     const int i = e / r, j = e - i * r;
     double2 s = make_double2(0.0, 0.0);
     for (int k = 0; k <= j; ++k) s = cadd(s, cmul(Qm[i * r + k], R[k * r + j]));
     H[e] = s;
   }
-  __syncwarp();
-  for (int e = lane; e < r * r; e += 32) {
+  __syncthreads();
+  for (int e = lane; e < r * r; e += nl) {
     const int i = e / r, j = e - i * r;
     double s = 0.0;
     for (int k = 0; k < r; ++k) {
@@ -935,7 +1070,7 @@ void deim_init() {
   const int lim = 200 * 1024;
   cudaFuncSetAttribute(k_ygram, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_psi, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_deim_small, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_deim_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_rbf, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_sqrtm, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -949,28 +1084,26 @@ namespace vpk {
 size_t deim_basis_scratch(int sms, int64_t N, int m) {
   const int tot = m * m;
   const int gx = std::min<int64_t>(ceil_div(N, YG_ROWS), 2 * sms);
-  return arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
-         arena_bytes(m, 8);
+  return arena_bytes((size_t)gx * tot, 8) + 4 * arena_bytes(tot, 8) + arena_bytes(m, 8);
 }
 
 vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t ldy, int d,
                          double* Psi, double* sigma, void* scratch, cudaStream_t st) {
-  const int tot = m * m;
+  const int tot = m * m, tri = m * (m + 1) / 2;
   const int gx = std::min<int64_t>(ceil_div(N, YG_ROWS), 2 * ctx->num_sms);
-  const int gy = ceil_div(tot, 256 * 8);
+  const int gy = ceil_div(tri, 256 * 8);
   const size_t bytes = deim_basis_scratch(ctx->num_sms, N, m);
   Arena a{(char*)scratch, 0, bytes};
-  double* part = a.take<double>((size_t)gx * tot);
+  double* part = a.take<double>((size_t)gx * tri);
   double* G = a.take<double>(tot);
-  double2* Gc = a.take<double2>(tot);
-  double2* Wj = a.take<double2>(tot);
-  double2* Ws = a.take<double2>(tot);
+  double* Aj = a.take<double>(tot);
+  double* Wj = a.take<double>(tot);
+  double* Ws = a.take<double>(tot);
   double* lam = a.take<double>(m);
   VP_K(VP_K_SUBSET, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(N, m, Y, ldy,
                                                                                       part)));
-  VP_K(VP_K_REDUCE, reduce_partials(gx, tot, part, G, nullptr, st));
-  VP_K(VP_K_SUBSET, (k_to_complex<<<ceil_div(tot, 256), 256, 0, st>>>(tot, G, Gc)));
-  VP_K(VP_K_INIT, init_launch_jacobi(m, Gc, Wj, lam, Ws, ctx->d_status, st));
+  VP_K(VP_K_REDUCE, reduce_partials(gx, tri, part, G, nullptr, st));
+  VP_K(VP_K_INIT, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
   int bx = std::min<int64_t>(ceil_div(N, 256), 4 * ctx->num_sms);
   VP_K(VP_K_SUBSET, (k_psi<<<bx, 256, sizeof(double) * m * d, st>>>(N, m, d, Y, ldy, Ws, lam, Psi,
                                                                     sigma, ctx->d_status)));
@@ -980,7 +1113,8 @@ vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t
 size_t deim_indices_scratch(int sms, int64_t N, int d) {
   const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * sms);
   return arena_bytes(nb, 8) + arena_bytes(nb, 8) + arena_bytes(128, 8) +
-         arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8) + arena_bytes(d, 4);
+         arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8) + arena_bytes(d, 4) +
+         arena_bytes((size_t)d * N, 8) + arena_bytes(1, 4);
 }
 
 vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int32_t* idx,
@@ -990,10 +1124,12 @@ vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int
   Arena a{(char*)scratch, 0, bytes};
   double* pval = a.take<double>(nb);
   int64_t* pidx = a.take<int64_t>(nb);
-  double* cvec = a.take<double>(128);
+  double* prow = a.take<double>(128);
   double* part = a.take<double>((size_t)nb * d);
   double* dots = a.take<double>(d);
   int* renew = a.take<int>(d);
+  double* R = a.take<double>((size_t)d * N);
+  int* ticket = a.take<int>(1);
   const int* rn = nullptr;
   if (Psi_prev) {  // index update: renew the n_up most rotated positions
     VP_K(VP_K_SUBSET, (k_rot_dots<<<nb, 256, 0, st>>>(N, d, Psi, Psi_prev, part)));
@@ -1001,13 +1137,11 @@ vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int
     VP_K(VP_K_SUBSET, (k_renew<<<1, 32, 0, st>>>(d, dots, n_up, renew)));
     rn = renew;
   }
-  for (int k = 0; k < d; ++k) {
-    if (k > 0)
-      VP_K(VP_K_SUBSET, (k_deim_small<<<1, 256, sizeof(double) * k * (k + 1), st>>>(
-                            N, k, Psi, idx, cvec, ctx->d_status, rn)));
-    VP_K(VP_K_SUBSET, (k_deim_resid<<<nb, 256, 0, st>>>(N, k, Psi, cvec, pval, pidx, idx, d, rn)));
-    VP_K(VP_K_SUBSET, (k_deim_pick<<<1, 32, 0, st>>>(nb, pval, pidx, idx, k, rn)));
-  }
+  VP_CUDA(cudaMemcpyAsync(R, Psi, sizeof(double) * d * N, cudaMemcpyDeviceToDevice, st));
+  VP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
+  for (int k = 0; k < d; ++k)
+    VP_K(VP_K_SUBSET, (k_deim_lu<<<nb, 256, 0, st>>>(N, d, k, R, prow, idx, rn, pval, pidx, ticket,
+                                                     ctx->d_status)));
   return VP_OK;
 }
 
@@ -1032,23 +1166,23 @@ vp_status deim_weights_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, con
 size_t dmd_fit_scratch(int nx, int m, int r_max) {
   const int tot = m * m;
   const int gx = std::max(1, std::min(ceil_div(nx, YG_ROWS), 64));
-  return arena_bytes((size_t)gx * tot, 8) + arena_bytes(tot, 8) + 3 * arena_bytes(tot, 16) +
-         arena_bytes(m, 8) + arena_bytes((size_t)m * r_max, 8) + arena_bytes((size_t)r_max * nx, 8) +
+  return arena_bytes((size_t)gx * tot, 8) + 4 * arena_bytes(tot, 8) + arena_bytes(m, 8) +
+         arena_bytes((size_t)m * r_max, 8) + arena_bytes((size_t)r_max * nx, 8) +
          2 * arena_bytes((size_t)r_max * r_max, 8);
 }
 
 vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double* Yp, double tol,
                       int r_max, int* r_out, double* B, double* Bpinv, double* A, double* S,
                       double* sigma, void* scratch, cudaStream_t st) {
-  const int tot = m * m;
+  const int tot = m * m, tri = m * (m + 1) / 2;
   const int gx = std::max(1, std::min(ceil_div(nx, YG_ROWS), 64));
-  const int gy = ceil_div(tot, 256 * 8);
+  const int gy = ceil_div(tri, 256 * 8);
   Arena a{(char*)scratch, 0, dmd_fit_scratch(nx, m, r_max)};
-  double* part = a.take<double>((size_t)gx * tot);
+  double* part = a.take<double>((size_t)gx * tri);
   double* G = a.take<double>(tot);
-  double2* Gc = a.take<double2>(tot);
-  double2* Wj = a.take<double2>(tot);
-  double2* Ws = a.take<double2>(tot);
+  double* Aj = a.take<double>(tot);
+  double* Wj = a.take<double>(tot);
+  double* Ws = a.take<double>(tot);
   double* lam = a.take<double>(m);
   double* C = a.take<double>((size_t)m * r_max);
   double* U = a.take<double>((size_t)r_max * nx);
@@ -1057,9 +1191,8 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   // 1. Y^T Y and its eigen-decomposition (singular values and right vectors of Y)
   VP_K(VP_K_SUBSET, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(nx, m, Y, nx,
                                                                                        part)));
-  VP_K(VP_K_REDUCE, reduce_partials(gx, tot, part, G, nullptr, st));
-  VP_K(VP_K_SUBSET, (k_to_complex<<<ceil_div(tot, 256), 256, 0, st>>>(tot, G, Gc)));
-  VP_K(VP_K_INIT, init_launch_jacobi(m, Gc, Wj, lam, Ws, ctx->d_status, st));
+  VP_K(VP_K_REDUCE, reduce_partials(gx, tri, part, G, nullptr, st));
+  VP_K(VP_K_INIT, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
   std::vector<double> lh(m);
   VP_CUDA(cudaMemcpyAsync(lh.data(), lam, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
   VP_CUDA(cudaStreamSynchronize(st));
@@ -1086,7 +1219,7 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   // i.e. the row-major r x nx matrix B^T
   VP_K(VP_K_SUBSET, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
   // 4. real part of the principal square root of A for half steps
-  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 32, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
+  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 128, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
   return VP_OK;
 }
 

@@ -61,25 +61,43 @@ __global__ void k_rgram(int64_t N, int p, const double* __restrict__ X, const do
 }
 
 // ------------------------------------------------------- Hermitian Jacobi
+#define JACOBI_SMEM_M 76
 // Diagonalise the Hermitian m x m matrix A (global, overwritten) and
 // accumulate the unitary W (global, m x m): A_in = W diag(lambda) W^H.
 // Writes lambda (descending) and the matching columns of W sorted into Wout
 // (m x m).  m <= 256 (even m uses all slots; odd m adds an idle slot).
-__global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2* Wout,
-                         int max_sweeps, int* status) {
+// With in_smem (m <= JACOBI_SMEM_M) A and W are copied to shared memory and
+// rotated there.  A pair is rotated unless |a_jk| <= 1e-15 sqrt|a_jj a_kk| or
+// both diagonal entries are below 1e-14 of the largest one (a pair inside the
+// rounding-level null space of a rank-deficient matrix, whose rotations would
+// go on forever and change no eigenpair above it).
+__global__ void k_jacobi(int m, double2* A_g, double2* W_g, double* lambda, double2* Wout,
+                         int max_sweeps, int* status, int in_smem) {
+  extern __shared__ double2 jac_sm[];
   __shared__ double2 rot_c[128], rot_s[128];
   __shared__ int pj[128], pk[128];
-  __shared__ double off_s, tot_s;
+  __shared__ double off_s, tot_s, nu_s;
   __shared__ int nrot;
   __shared__ int order[256];
   const int t = threadIdx.x, nt = blockDim.x;
+  double2* A = in_smem ? jac_sm : A_g;
+  double2* W = in_smem ? jac_sm + m * m : W_g;
+  if (in_smem)
+    for (int e = t; e < m * m; e += nt) A[e] = A_g[e];
   for (int e = t; e < m * m; e += nt) W[e] = make_double2((e / m) == (e % m) ? 1.0 : 0.0, 0.0);
   __syncthreads();
   const int slots = (m + 1) & ~1;  // round-robin slots (one idle when m is odd)
   const int npair = slots / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence: off-diagonal mass against the whole
-    if (t == 0) { off_s = 0.0; tot_s = 0.0; nrot = 0; }
+    if (t == 0) {
+      off_s = 0.0;
+      tot_s = 0.0;
+      nrot = 0;
+      double dm = 0.0;
+      for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(A[j * m + j].x));
+      nu_s = 1e-14 * dm;
+    }
     __syncthreads();
     double off = 0.0, tot = 0.0;
     for (int e = t; e < m * m; e += nt) {
@@ -110,7 +128,8 @@ __global__ void k_jacobi(int m, double2* A, double2* W, double* lambda, double2*
           double ajj = A[j * m + j].x, akk = A[k * m + k].x;
           // rotate unless a_jk is below rounding of the diagonal pair (the
           // classical threshold |a_jk| <= eps sqrt|a_jj a_kk|)
-          if (mag > 1e-15 * sqrt(fabs(ajj * akk)) && mag > 1e-300) {
+          if (mag > 1e-15 * sqrt(fabs(ajj * akk)) && mag > 1e-300 &&
+              fmax(fabs(ajj), fabs(akk)) > nu_s) {
             atomicAdd(&nrot, 1);
             double tau = (akk - ajj) / (2.0 * mag);
             double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
@@ -318,6 +337,7 @@ void init_kernels_init() {
   cudaFuncSetAttribute(k_rgram, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_r_times, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_zeta, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 void init_launch_rgram(int64_t N, int p, const double* X, const double* V, double2* part, int gx,
@@ -327,7 +347,9 @@ void init_launch_rgram(int64_t N, int p, const double* X, const double* V, doubl
 }
 void init_launch_jacobi(int m, double2* A, double2* W, double* lambda, double2* Wout, int* status,
                         cudaStream_t st) {
-  k_jacobi<<<1, 512, 0, st>>>(m, A, W, lambda, Wout, 60, status);
+  const int in_smem = m <= JACOBI_SMEM_M;
+  const size_t smem = in_smem ? sizeof(double2) * 2 * m * m : 0;
+  k_jacobi<<<1, 512, smem, st>>>(m, A, W, lambda, Wout, 60, status, in_smem);
 }
 void init_launch_coeff(int p, int n, const double2* W, const double* lambda, double2* C, int* status,
                        cudaStream_t st) {

@@ -444,6 +444,7 @@ struct DFStep {
   cudaStream_t st;
   const void* Qm = nullptr;  // rows the fixed point evaluates at (Q_half, or Q0 when frozen)
   Red Rs;                    // parameter subsample of the basis stages (Rs.p = 0: none)
+  cudaEvent_t field_event = nullptr;  // recorded after the subsample's field, when set
   DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt, double* ks,
          cudaStream_t s);
   vp_status pre(double* trace_step);
@@ -477,6 +478,7 @@ static vp_status basis_stage(DFStep& S, const void* Q2, const double* Zsrc, doub
     VP_K(VP_K_SUBSET, gather_cols(2 * n, S.R.p, Zsrc, S.o.sub_idx, S.Rs.p, S.R.w.sub.Zs,
                                   ctx->d_status, st));
     Ds.field(Q2, S.R.w.sub.Zs, nullptr);
+    if (S.field_event) VP_CUDA(cudaEventRecord(S.field_event, st));
     Ds.basis_velocity(Q2, S.R.w.sub.Zs, scale, M, out);
   } else {
     RedDF D{S.R, ctx, st, S.R.N, n, S.R.p, S.o.arith};
@@ -642,7 +644,11 @@ struct vp_hyper {
   double *B = nullptr, *Bp = nullptr, *A = nullptr, *S = nullptr, *beta_s = nullptr,
          *beta = nullptr, *phi_half = nullptr, *F = nullptr, *Psi = nullptr, *Psi_prev = nullptr,
          *c = nullptr, *Qd = nullptr;
-  void* scratch = nullptr;
+  void* scratch = nullptr;       // DMD scratch (main stream)
+  void* scratch_deim = nullptr;  // DEIM scratch (side stream)
+  cudaStream_t side = nullptr;   // DEIM data and construction
+  cudaStream_t side2 = nullptr;  // DMD chain
+  cudaEvent_t ev_data = nullptr, ev_deim = nullptr, ev_dmd = nullptr;
   int64_t entries = 0;  // potentials written to the windows
   int intervals = 0, hyper_intervals = 0, r = 0;
 };
@@ -672,38 +678,62 @@ vp_status hyper_interval(vp_hyper* h, Red& R, DFStep& S, double* trace_step, int
   const int n = h->n, p = h->p, q = h->nsub, Nx = h->grid.Nx, T = h->T;
   const int64_t N = h->N;
   const vp_step_opts& o = S.o;
-  // 1. field of the sampled parameters at the entering state writes Phi_{tau-1}
+  // 1. field of the sampled parameters at the entering state writes Phi_{tau-1};
+  // the windows and operators below start as soon as it is done (event
+  // ev_data, recorded inside the first basis stage) and overlap the rest of
+  // the stage on two more streams: DEIM data and construction (N-row work)
+  // on `side`, the single-block DMD chain on `side2`
   const int slot = (int)(h->entries % (T + 1));
   double* phi_slot = h->phi_ring + (size_t)slot * q * Nx;
   S.Rs.w.phi_out = phi_slot;
+  S.field_event = h->ev_data;
   VP_TRY(S.pre(trace_step));
   S.Rs.w.phi_out = nullptr;
-  VP_CUDA(cudaMemcpyAsync(phi_slot + (size_t)(T + 1) * q * Nx, phi_slot, sizeof(double) * q * Nx,
-                          cudaMemcpyDeviceToDevice, st));
-  VP_K(VP_K_HYPER, phi_at_qz(h->g, N, n, q, S.Q, w.sub.Zs, phi_slot,
-                             h->y_ring + (size_t)slot * q * N, ctx->num_sms, st));
+  S.field_event = nullptr;
   ++h->entries;
   const bool hyper = h->entries >= T + 1;
+  {
+    cudaStream_t st = h->side;
+    VP_CUDA(cudaStreamWaitEvent(st, h->ev_data, 0));
+    VP_K(VP_K_HYPER, phi_at_qz(h->g, N, n, q, S.Q, w.sub.Zs, phi_slot,
+                               h->y_ring + (size_t)slot * q * N, ctx->num_sms, st));
+    if (hyper) {  // DEIM basis, indices (all, or the n_up most rotated), weights
+      std::swap(h->Psi, h->Psi_prev);
+      VP_TRY(deim_basis_run(ctx, N, (T + 1) * q, h->y_ring, N, h->d, h->Psi, nullptr,
+                            h->scratch_deim, st));
+      const bool full = h->hyper_intervals % h->k_deim == 0;
+      VP_TRY(deim_indices_run(ctx, N, h->d, h->Psi, h->idx, full ? nullptr : h->Psi_prev, h->n_up,
+                              h->scratch_deim, st));
+      VP_TRY(deim_weights_run(ctx, N, h->d, h->Psi, h->idx, h->g.Mq, h->c, h->scratch_deim, st));
+    }
+    VP_CUDA(cudaEventRecord(h->ev_deim, st));
+  }
+  {
+    cudaStream_t st = h->side2;
+    VP_CUDA(cudaStreamWaitEvent(st, h->ev_data, 0));
+    VP_CUDA(cudaMemcpyAsync(phi_slot + (size_t)(T + 1) * q * Nx, phi_slot, sizeof(double) * q * Nx,
+                            cudaMemcpyDeviceToDevice, st));
+    if (hyper) {  // DMD of the window (oldest entry first), coordinates, RBF, Phi at t + dt/2
+      const int oldest = (int)((h->entries - (T + 1)) % (T + 1));
+      const double* Y = h->phi_ring + (size_t)oldest * q * Nx;
+      int r = 0;
+      VP_TRY(dmd_fit_run(ctx, Nx, T * q, Y, Y + (size_t)q * Nx, h->dmd_tol, h->r_max, &r, h->B,
+                         h->Bp, h->A, h->S, nullptr, h->scratch, st));
+      h->r = r;
+      VP_K(VP_K_HYPER, dmd_coords_run(Nx, r, h->Bp, q, phi_slot, h->beta_s, st));
+      VP_K(VP_K_HYPER, rbf_run(h->dim, q, h->eta_s, r, h->beta_s, p, h->eta, 0.0, h->eps, h->beta,
+                               ctx->d_status, st));
+      VP_K(VP_K_HYPER, dmd_potential_run(Nx, r, h->B, h->A, h->S, p, h->beta, 0, 1, h->phi_half,
+                                         st));
+      VP_K(VP_K_CELL_GRADIENT, cell_gradient(h->g, p, h->phi_half, h->F, st));
+    }
+    VP_CUDA(cudaEventRecord(h->ev_dmd, st));
+  }
+  // the main stream continues after both (the side stream reads the
+  // subsample's coefficients, which the last basis stage overwrites)
+  VP_CUDA(cudaStreamWaitEvent(st, h->ev_deim, 0));
+  VP_CUDA(cudaStreamWaitEvent(st, h->ev_dmd, 0));
   if (hyper) {
-    // 3. DMD of the window (oldest entry first), coordinates, RBF, Phi at t + dt/2
-    const int oldest = (int)((h->entries - (T + 1)) % (T + 1));
-    const double* Y = h->phi_ring + (size_t)oldest * q * Nx;
-    int r = 0;
-    VP_TRY(dmd_fit_run(ctx, Nx, T * q, Y, Y + (size_t)q * Nx, h->dmd_tol, h->r_max, &r, h->B, h->Bp,
-                       h->A, h->S, nullptr, h->scratch, st));
-    h->r = r;
-    VP_K(VP_K_HYPER, dmd_coords_run(Nx, r, h->Bp, q, phi_slot, h->beta_s, st));
-    VP_K(VP_K_HYPER, rbf_run(h->dim, q, h->eta_s, r, h->beta_s, p, h->eta, 0.0, h->eps, h->beta,
-                             ctx->d_status, st));
-    VP_K(VP_K_HYPER, dmd_potential_run(Nx, r, h->B, h->A, h->S, p, h->beta, 0, 1, h->phi_half, st));
-    VP_K(VP_K_CELL_GRADIENT, cell_gradient(h->g, p, h->phi_half, h->F, st));
-    // DEIM basis, indices (all, or the n_up most rotated), weights
-    std::swap(h->Psi, h->Psi_prev);
-    VP_TRY(deim_basis_run(ctx, N, (T + 1) * q, h->y_ring, N, h->d, h->Psi, nullptr, h->scratch, st));
-    const bool full = h->hyper_intervals % h->k_deim == 0;
-    VP_TRY(deim_indices_run(ctx, N, h->d, h->Psi, h->idx, full ? nullptr : h->Psi_prev, h->n_up,
-                            h->scratch, st));
-    VP_TRY(deim_weights_run(ctx, N, h->d, h->Psi, h->idx, h->g.Mq, h->c, h->scratch, st));
     // the d DEIM rows of the basis at the coefficient stage (U_1/2)
     VP_K(VP_K_HYPER, gather_rows_lp(S.Qm, o.arith, N, 2 * n, h->idx, h->d, h->Qd, ctx->d_status, st));
     ++h->hyper_intervals;
@@ -787,10 +817,10 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   h->r_max = o.r_max;
   h->dmd_tol = o.dmd_tol;
   const int q = o.nsub, Nx = grid->Nx, n2 = 2 * n, rm = o.r_max;
-  const size_t scratch = std::max(std::max(dmd_fit_scratch(Nx, o.T * q, rm),
-                                           deim_basis_scratch(ctx->num_sms, N, m)),
-                                  std::max(deim_indices_scratch(ctx->num_sms, N, o.d),
-                                           deim_weights_scratch(ctx->num_sms, N, o.d)));
+  const size_t scratch = dmd_fit_scratch(Nx, o.T * q, rm);
+  const size_t scratch_deim = std::max(deim_basis_scratch(ctx->num_sms, N, m),
+                                       std::max(deim_indices_scratch(ctx->num_sms, N, o.d),
+                                                deim_weights_scratch(ctx->num_sms, N, o.d)));
   const size_t bytes = arena_bytes(q, 4) + arena_bytes(o.d, 4) + arena_bytes((size_t)p * o.dim, 8) +
                        arena_bytes((size_t)q * o.dim, 8) + arena_bytes(1, 8) +
                        arena_bytes((size_t)2 * (o.T + 1) * q * Nx, 8) +
@@ -798,7 +828,8 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
                        2 * arena_bytes((size_t)rm * rm, 8) + arena_bytes((size_t)q * rm, 8) +
                        arena_bytes((size_t)p * rm, 8) + 2 * arena_bytes((size_t)p * Nx, 8) +
                        2 * arena_bytes((size_t)o.d * N, 8) + arena_bytes(o.d, 8) +
-                       arena_bytes((size_t)o.d * n2, 8) + arena_bytes(scratch, 8);
+                       arena_bytes((size_t)o.d * n2, 8) + arena_bytes(scratch, 8) +
+                       arena_bytes(scratch_deim, 8);
   cudaError_t e = cudaMalloc(&h->mem, bytes);
   if (e != cudaSuccess) {
     delete h;
@@ -825,6 +856,21 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   h->c = a.take<double>(o.d);
   h->Qd = a.take<double>((size_t)o.d * n2);
   h->scratch = a.take<char>(scratch);
+  h->scratch_deim = a.take<char>(scratch_deim);
+  e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_data, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_deim, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dmd, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (h->ev_deim) cudaEventDestroy(h->ev_deim);
+    if (h->ev_data) cudaEventDestroy(h->ev_data);
+    if (h->side2) cudaStreamDestroy(h->side2);
+    if (h->side) cudaStreamDestroy(h->side);
+    cudaFree(h->mem);
+    delete h;
+    return vp_cuda_check(ctx, e, "DMD-DEIM streams and events");
+  }
   cudaStream_t s0 = nullptr;
   e = cudaMemcpyAsync(h->sub, o.sub_idx, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, s0);
   if (e == cudaSuccess)
@@ -837,6 +883,11 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
+    cudaEventDestroy(h->ev_dmd);
+    cudaEventDestroy(h->ev_deim);
+    cudaEventDestroy(h->ev_data);
+    cudaStreamDestroy(h->side2);
+    cudaStreamDestroy(h->side);
     cudaFree(h->mem);
     delete h;
     return vp_cuda_check(ctx, e, "DMD-DEIM set-up");
@@ -900,6 +951,13 @@ vp_status vp_hyper_destroy(vp_hyper* h) {
   {
     std::lock_guard<std::mutex> lock(h->ctx->mu);
     DeviceGuard guard(h->ctx->device);
+    cudaStreamSynchronize(h->side);
+    cudaStreamSynchronize(h->side2);
+    cudaEventDestroy(h->ev_dmd);
+    cudaEventDestroy(h->ev_deim);
+    cudaEventDestroy(h->ev_data);
+    cudaStreamDestroy(h->side2);
+    cudaStreamDestroy(h->side);
     cudaFree(h->mem);
   }
   delete h;
