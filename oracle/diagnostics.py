@@ -1,6 +1,7 @@
-"""Accuracy diagnostics of the reduced model (Sec. 6.1, eqs. relative_errors,
-relative_errors_complex_SVD; Sec. 6.2, eqs. error_ham_tot, error_ham_tot1) and
-the adaptive-rank error indicator, float64.
+"""Diagnostics of Sec. 6, float64: accuracy of the reduced model (Sec. 6.1,
+eqs. relative_errors, relative_errors_complex_SVD; Sec. 6.2, eqs.
+error_ham_tot, rel_error_Hamiltonian), the adaptive-rank error indicator, and
+damping/growth rates of the electric energy.
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
 CPU legs of bench.py, never by the library.
@@ -18,6 +19,7 @@ CPU legs of bench.py, never by the library.
 * hamiltonian_error_terms: Delta H over one step and the three terms that
   bound it (basis at the end, basis at the start, coefficients), each the
   2-norm over the parameters.
+* fit_rate: exponential rate of the electric energy from its local maxima.
 """
 from __future__ import annotations
 
@@ -76,3 +78,29 @@ def csvd_state(X: np.ndarray, V: np.ndarray, n: int):
     """(U, Z) of the truncated complex SVD of the snapshots (Sec. 3.2)."""
     U, Z, _ = csvd.csvd_init(X, V, n)
     return U, Z
+
+
+def hamiltonian_relative_error(H_full, H_red):
+    """||H(W) - H(UZ)||_2 / ||H(W)||_2 over the p samples (eq. rel_error_Hamiltonian)."""
+    return float(np.linalg.norm(H_full - H_red) / np.linalg.norm(H_full))
+
+
+def local_maxima(y: np.ndarray) -> np.ndarray:
+    """Indices of strict interior local maxima of a 1-D series."""
+    return np.where((y[1:-1] > y[:-2]) & (y[1:-1] >= y[2:]))[0] + 1
+
+
+def fit_rate(t: np.ndarray, E: np.ndarray, t_min: float = -np.inf, t_max: float = np.inf,
+             skip_first: bool = True) -> float:
+    """Exponential rate of the electric energy from a least-squares line through
+    log E at its local maxima in [t_min, t_max], first peak excluded (Sec. 6.2).
+    Returned as the field-amplitude rate, i.e. half the slope of log E (the
+    values the paper prints, -0.287 and 0.078, are amplitude rates)."""
+    pk = local_maxima(E)
+    pk = pk[(t[pk] >= t_min) & (t[pk] <= t_max)]
+    if skip_first:
+        pk = pk[1:]
+    if len(pk) < 2:
+        raise ValueError("not enough peaks")
+    slope = np.polyfit(t[pk], np.log(E[pk]), 1)[0]
+    return 0.5 * float(slope)
