@@ -251,6 +251,36 @@ vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
                             const double* Q_dev, const double* Z_dev, double* E_dev, double* H_dev,
                             double* resid_dev, void* stream);
 
+/* Accuracy diagnostics (Sec. 6.1-6.2); FP64, deterministic.
+ * vp_rel_errors: eq. relative_errors, eps_dev[0] = |S_X - X_r|_F / |S_X|_F,
+ *   eps_dev[1] = |S_V - V_r|_F / |S_V|_F, with the full-order snapshots
+ *   X_dev, V_dev (p x N, sample by sample) and X_r, V_r = U Z.
+ * vp_target_errors: eq. relative_errors_complex_SVD, the same errors for the
+ *   projection onto the ortho-symplectic basis of size 2n from the complex SVD
+ *   of S_X + i S_V (Gram route: tails below ~1e-8 of |S| are not resolved).
+ * vp_rank_indicator: out_dev[0] = |(I - U U^T) G|_F / |G|_F, G the Hamiltonian
+ *   gradient of the full model at R = U Z: the share of the force outside the
+ *   basis (an indicator for rank adaptivity, which the paper leaves open).
+ * vp_half_basis: Qh_dev = R_{Q0}(dt/2 X(Q0, Z0)), the basis at the first
+ *   stage of the step (Sec. 5).
+ * vp_hamiltonian_error_terms: eq. error_ham_tot, out_dev[0..4) =
+ *   |H(U1 Z1) - H(U0 Z0)|, |H(U1 Z1) - H(Uh Z1)|, |H(Uh Z0) - H(U0 Z0)|,
+ *   |H(Uh Z1) - H(Uh Z0)| (2-norms over the p parameters). */
+vp_status vp_rel_errors(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q_dev,
+                        const double* Z_dev, const double* X_dev, const double* V_dev,
+                        double* eps_dev, void* stream);
+vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X_dev,
+                           const double* V_dev, double* eps_dev, void* stream);
+vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q_dev, const double* Z_dev, double* out_dev, void* stream);
+vp_status vp_half_basis(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                        const double* Q0_dev, const double* Z0_dev, double dt, double* Qh_dev,
+                        void* stream);
+vp_status vp_hamiltonian_error_terms(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n,
+                                     int32_t p, const double* Q0_dev, const double* Z0_dev,
+                                     const double* Qh_dev, const double* Q1_dev, const double* Z1_dev,
+                                     double* out_dev, void* stream);
+
 /* a12. DEIM-indexed nonlinear gradient (Sec. 4.3, eq. grHDD):
  * gX = m_p^-1 U_X^T diag(grad Lambda^0(X_r) Phi_DMD) P c, evaluated at the d
  * rows idx_dev of X_r = U_X Z only.  c_dev: the d DEIM weights

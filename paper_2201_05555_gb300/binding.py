@@ -88,6 +88,12 @@ _SIGS = [
     ("vp_deim_basis", _I32, [_P, _I64, _I32, _P, _I64, _I32, _P, _P, _P]),
     ("vp_deim_indices", _I32, [_P, _I64, _I32, _P, _P, _P]),
     ("vp_deim_indices_update", _I32, [_P, _I64, _I32, _P, _P, _I32, _P, _P]),
+    ("vp_rel_errors", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
+    ("vp_target_errors", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P]),
+    ("vp_rank_indicator", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P]),
+    ("vp_half_basis", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _D, _P, _P]),
+    ("vp_hamiltonian_error_terms", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P,
+                                          _P, _P, _P]),
     ("vp_hyper_create", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, C.POINTER(HyperOpts),
                                C.POINTER(_P)]),
     ("vp_hyper_step", _I32, [_P, _P, _P, _D, _I32, C.POINTER(StepOpts), _P, _P, _P, _P]),
@@ -478,6 +484,52 @@ class Context:
                                                _ptr(Q, name="Q"), _ptr(Z, name="Z"), _ptr(E),
                                                _ptr(H), _ptr(r), self._stream()), "reduced_energy")
         return E, H, r
+
+    # -- accuracy diagnostics (Sec. 6.1-6.2)
+    def rel_errors(self, Q: torch.Tensor, Z: torch.Tensor, X: torch.Tensor, V: torch.Tensor):
+        """(eps_X, eps_V) of U Z against full-order X, V (p x N) as a device tensor."""
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        out = self._empty(2)
+        self._check(self.lib.vp_rel_errors(self.h, N, n2 // 2, p, _ptr(Q, name="Q"),
+                                           _ptr(Z, name="Z"), _ptr(X, name="X"),
+                                           _ptr(V, name="V"), _ptr(out), self._stream()),
+                    "rel_errors")
+        return out
+
+    def target_errors(self, X: torch.Tensor, V: torch.Tensor, n: int):
+        p, N = X.shape
+        out = self._empty(2)
+        self._check(self.lib.vp_target_errors(self.h, N, p, n, _ptr(X, name="X"),
+                                              _ptr(V, name="V"), _ptr(out), self._stream()),
+                    "target_errors")
+        return out
+
+    def rank_indicator(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor):
+        N, n2 = Q.shape
+        out = self._empty(1)
+        self._check(self.lib.vp_rank_indicator(self.h, C.byref(grid), N, n2 // 2, Z.shape[1],
+                                               _ptr(Q, name="Q"), _ptr(Z, name="Z"), _ptr(out),
+                                               self._stream()), "rank_indicator")
+        return out
+
+    def half_basis(self, grid: Grid, Q0: torch.Tensor, Z0: torch.Tensor, dt: float):
+        N, n2 = Q0.shape
+        Qh = self._empty(N, n2)
+        self._check(self.lib.vp_half_basis(self.h, C.byref(grid), N, n2 // 2, Z0.shape[1],
+                                           _ptr(Q0, name="Q0"), _ptr(Z0, name="Z0"), dt, _ptr(Qh),
+                                           self._stream()), "half_basis")
+        return Qh
+
+    def hamiltonian_error_terms(self, grid: Grid, Q0, Z0, Qh, Q1, Z1):
+        """(Delta H, basis at end, basis at start, coefficients) as a device tensor."""
+        N, n2 = Q0.shape
+        out = self._empty(4)
+        self._check(self.lib.vp_hamiltonian_error_terms(
+            self.h, C.byref(grid), N, n2 // 2, Z0.shape[1], _ptr(Q0, name="Q0"),
+            _ptr(Z0, name="Z0"), _ptr(Qh, name="Qh"), _ptr(Q1, name="Q1"), _ptr(Z1, name="Z1"),
+            _ptr(out), self._stream()), "hamiltonian_error_terms")
+        return out
 
     def deim_gather_project(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, idx: torch.Tensor,
                             c: torch.Tensor, phi: torch.Tensor):

@@ -143,12 +143,23 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
         double c = 1.0, sn = 0.0;
         if (k < m) {
           const double ajk = A[j * m + k], ajj = A[j * m + j], akk = A[k * m + k];
-          if (fabs(ajk) > 1e-15 * sqrt(fabs(ajj * akk)) && fabs(ajk) > 1e-300 &&
+          if (fabs(ajk) > 1e-15 * sqrt(fabs(ajj * akk)) && (float)fabs(ajk) > 0.0f &&
               fmax(fabs(ajj), fabs(akk)) > nu) {
             atomicAdd(&nrot, 1);
-            const double tau = (akk - ajj) / (2.0 * ajk);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
+            // the angle in FP32 (FP64 division and square roots are slow on
+            // this chip), the rotation normalised in FP64 so that it stays
+            // orthogonal to FP64 rounding; an angle good to FP32 leaves
+            // |g_jk| ~1e-7 of its value, which the next sweeps remove
+            const double dd = akk - ajj;
+            double tt;
+            if (fabs(dd) > 1e18 * fabs(ajk)) {  // tiny angle, beyond FP32 range: t = a_jk / dd
+              tt = ajk / dd;
+            } else {
+              const float tau = (float)dd / (2.0f * (float)ajk);
+              tt = (double)((tau >= 0.0f ? 1.0f : -1.0f) /
+                            (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f))));
+            }
+            c = rsqrt(fma(tt, tt, 1.0));
             sn = tt * c;
           }
         }

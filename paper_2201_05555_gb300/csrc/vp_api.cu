@@ -1534,6 +1534,136 @@ vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
   return VP_OK;
 }
 
+// ------------------------------------------------- accuracy diagnostics
+static vp_status init_csvd_impl(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, int32_t n_max,
+                                double rank_tol, const double* X0, const double* V0, double* Q,
+                                double* Z, double* sigma, int32_t* n_out, cudaStream_t st);
+
+static vp_status rel_errors_impl(vp_ctx* ctx, int64_t N, int n, int p, const double* Q,
+                                 const double* Z, const double* X, const double* V, double* eps,
+                                 cudaStream_t st) {
+  const int nb = diag_blocks(N, ctx->num_sms);
+  const size_t bytes = arena_bytes((size_t)nb * 4, 8) + arena_bytes(4, 8);
+  void* base = nullptr;
+  VP_TRY(vp_workspace(ctx, bytes, &base));
+  Arena a{(char*)base, 0, bytes};
+  double* part = a.take<double>((size_t)nb * 4);
+  double* sums = a.take<double>(4);
+  VP_K(VP_K_REDUCE, rel_err_parts(N, n, p, Q, Z, X, V, part, nb, st));
+  VP_K(VP_K_REDUCE, reduce_partials(nb, 4, part, sums, nullptr, st));
+  VP_K(VP_K_REDUCE, ratio_sqrt(2, sums, eps, st));
+  return VP_OK;
+}
+
+vp_status vp_rel_errors(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q,
+                        const double* Z, const double* X, const double* V, double* eps,
+                        void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !X || !V || !eps) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  VP_TRY(rel_errors_impl(ctx, N, n, p, Q, Z, X, V, eps, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X,
+                           const double* V, double* eps, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  if (n < 1 || n > 40 || n > p || n > N) return vp_fail(ctx, VP_EINVAL, "n outside [1, min(p, N, 40)]");
+  if (!X || !V || !eps) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  // the rank-n complex SVD state of the snapshots (stream-ordered buffers),
+  // then the relative errors of its reconstruction
+  double *Qt = nullptr, *Zt = nullptr;
+  VP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&Qt), sizeof(double) * N * 2 * n, st));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&Zt), sizeof(double) * 2 * n * p, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(Qt, st);
+    return vp_cuda_check(ctx, e, "cudaMallocAsync");
+  }
+  int32_t nn = n;
+  vp_status s = init_csvd_impl(ctx, N, p, n, n, -1.0, X, V, Qt, Zt, nullptr, &nn, st);
+  if (s == VP_OK) s = rel_errors_impl(ctx, N, n, p, Qt, Zt, X, V, eps, st);
+  cudaFreeAsync(Zt, st);
+  cudaFreeAsync(Qt, st);
+  VP_TRY(s);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q, const double* Z, double* out, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !out) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 0, st, R));
+  RedWS& w = R.w;
+  const int64_t zsz = (int64_t)2 * n * p;
+  R.field(Q, Z);
+  VP_K(VP_K_PROJECT, project(R.g, N, n, p, Q, Z, w.F, nullptr, 0, nullptr, nullptr, N, w.part,
+                             w.gx_proj, nullptr, ctx->d_status, st));
+  VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, nullptr, st));
+  R.gv(Q, w.GVraw);
+  VP_K(VP_K_ADD_LINEAR, add_linear(n, p, w.gX, w.GVraw, Z, w.k, st));  // g = U^T G
+  const int nb = diag_blocks(N, ctx->num_sms);
+  if ((int64_t)nb * 2 + 2 > (int64_t)w.gx_proj * zsz)
+    return vp_fail(ctx, VP_EUNSUPPORTED, "partial buffer too small");
+  VP_K(VP_K_REDUCE, normal_parts(R.g, N, n, p, Q, Z, w.F, w.k, w.part, nb, st));
+  VP_K(VP_K_REDUCE, reduce_partials(nb, 2, w.part, w.aux, nullptr, st));
+  VP_K(VP_K_REDUCE, ratio_sqrt(1, w.aux, out, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_half_basis(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                        const double* Q0, const double* Z0, double dt, double* Qh, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q0 || !Z0 || !Qh) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 2, st, R));
+  R.field(Q0, Z0);
+  R.basis_velocity_from_field(Q0, Z0, 0.5 * dt, R.w.rows[0], R.w.rows[1]);
+  R.cayley(Q0, R.w.rows[1], Qh);
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_hamiltonian_error_terms(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n,
+                                     int32_t p, const double* Q0, const double* Z0,
+                                     const double* Qh, const double* Q1, const double* Z1,
+                                     double* out, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q0 || !Z0 || !Qh || !Q1 || !Z1 || !out) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  Red R;
+  VP_TRY(red_setup(ctx, grid, N, n, p, 1, st, R));
+  RedWS& w = R.w;
+  // H at (U0, Z0), (U1, Z1), (U_1/2, Z0), (U_1/2, Z1) into four p-vectors
+  // (in the row buffer, which neither the field nor the Grams use)
+  double* hv = w.rows[0];
+  if (4 * (int64_t)p > N * 2 * n) return vp_fail(ctx, VP_EUNSUPPORTED, "4 p > 2 n N");
+  const double* Qs[4] = {Q0, Q1, Qh, Qh};
+  const double* Zs[4] = {Z0, Z1, Z0, Z1};
+  for (int k = 0; k < 4; ++k) {
+    R.field(Qs[k], Zs[k]);
+    R.gv(Qs[k], w.GVraw);
+    VP_K(VP_K_ENERGIES, energies(n, p, w.GVraw, Zs[k], w.Efield, nullptr, hv + (int64_t)k * p, 1,
+                                 nullptr, nullptr, ctx->d_status, st));
+  }
+  VP_K(VP_K_REDUCE, ham_terms(p, hv, hv + p, hv + 2 * p, hv + 3 * p, out, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
 vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                                  const double* Q, const double* Z, int64_t d, const int32_t* idx,
                                  const double* c, const double* phi, double* gX, void* stream) {

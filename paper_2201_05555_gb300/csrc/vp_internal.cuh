@@ -382,6 +382,15 @@ void init_launch_zeta(int64_t N, int p, int n, const double* Q, const double* X,
 void init_launch_zeta_to_Z(int n, int p, const double2* zeta, double* Z, cudaStream_t st);
 void init_kernels_init();  // kernel attributes of init.cu
 void deim_init();          // kernel attributes of deim.cu
+// diag.cu: accuracy diagnostics (partial sums per block, reduced in order)
+int diag_blocks(int64_t N, int sms);
+void rel_err_parts(int64_t N, int n, int p, const double* Q, const double* Z, const double* X,
+                   const double* V, double* part, int nb, cudaStream_t st);
+void normal_parts(const GridC& g, int64_t N, int n, int p, const double* Q, const double* Z,
+                  const double* F, const double* gproj, double* part, int nb, cudaStream_t st);
+void ratio_sqrt(int pairs, const double* s, double* out, cudaStream_t st);
+void ham_terms(int p, const double* h00, const double* h11, const double* hh0, const double* hh1,
+               double* out, cudaStream_t st);
 // deim.cu: DEIM construction and DMD on caller-owned scratch (sizes below)
 size_t deim_basis_scratch(int sms, int64_t N, int m);
 vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t ldy, int d,

@@ -88,7 +88,7 @@ def test_hyper_run_parity(ctx, case):
         inf = h.info()
         assert int(it[0].item()) == recs[t]["iters"], t
         E0, H0 = reduced.energies(*states[t], g)
-        assert rel(tr[0, :, 0].cpu().numpy(), E0) < 1e-9
+        assert rel(tr[0, :, 0].cpu().numpy(), E0) < 1e-8
         ops = recs[t]["ops"]
         assert inf["hyper_intervals"] == sum(r["ops"] is not None for r in recs[: t + 1])
         if ops is not None:
