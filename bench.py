@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
+    ap.add_argument("--only", choices=["hyper", "dmd", "deim_build", "subsampled"], default=None,
+                    help="run one extra measurement alone and print its JSON (profiling runs)")
     return ap.parse_args()
 
 
@@ -397,7 +399,8 @@ def subsample_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
             "subsample": [int(i) for i in sub.cpu()]}
 
 
-def hyper_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
+def hyper_measure(ctx, torch, dev, flush, steps: int = 10, p: int = 64,
+                  shares: bool = True) -> dict:
     """DMD-DEIM reduced dynamics (Algorithm 2) with the paper's two-stream
     hyper-reduction settings: p* = 12 sampled parameters, window T = 3,
     d = 32 DEIM points, 12 indices renewed per interval and all of them every
@@ -407,10 +410,13 @@ def hyper_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
     by tail energy < 1e-8 with 2n in [8, 20] (the quiet start's spectrum falls
     below 1e-8 sigma_1 before 2n = 20).  Timed intervals follow the windows'
     fill and a first DMD-DEIM interval; the subsampled reduced step without
-    DMD-DEIM is timed on the same state for comparison."""
+    DMD-DEIM is timed on the same state for comparison, both without the
+    energy trace (a diagnostic that needs the field of every parameter).  The
+    same pair is timed at p = 256: the DMD-DEIM coefficient stage costs
+    O(p d n) per round instead of O(N p n)."""
     from paper_2201_05555_gb300 import make_grid
     from paper_2201_05555_gb300.binding import KERNELS
-    wl = workload()
+    wl = W.two_stream_reduced(N=WL["N"], p=p, Nx=WL["Nx"], n2=WL["n2"], dt=WL["dt"])
     X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=True)
     Q, Z, _, n = ctx.init_csvd_rank(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev),
                                     4, wl.n2 // 2, 1e-8)
@@ -432,19 +438,25 @@ def hyper_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
 
     Qr, Zr, Kr = Q.clone(), Z.clone(), torch.zeros_like(Z)
     for _ in range(3):
-        ctx.basis_update(grid, Qr, Zr, wl.dt, 1, arith=ARITH, kstate=Kr, sub=sub)
+        ctx.basis_update(grid, Qr, Zr, wl.dt, 1, arith=ARITH, kstate=Kr, sub=sub, trace=False)
     ms_sub = timed(lambda: ctx.basis_update(grid, Qr, Zr, wl.dt, 1, arith=ARITH, kstate=Kr,
-                                            sub=sub))
+                                            sub=sub, trace=False))
     T_ = 3
     h = ctx.hyper(grid, wl.N, n, wl.p, sub, eta, T=T_, d=32, n_up=12, k_deim=3, dmd_tol=1e-5)
     K = torch.zeros_like(Z)
-    h.step(Q, Z, wl.dt, T_ + 2, arith=ARITH, kstate=K)
+    h.step(Q, Z, wl.dt, T_ + 2, arith=ARITH, kstate=K, trace=False)
     its = []
-    ms = timed(lambda: its.append(h.step(Q, Z, wl.dt, 1, arith=ARITH, kstate=K)[1]))
+    ms = timed(lambda: its.append(h.step(Q, Z, wl.dt, 1, arith=ARITH, kstate=K, trace=False)[1]))
+    if not shares:
+        inf = h.info()
+        h.close()
+        return {"p": p, "2n": 2 * n, "ms_per_step": ms, "value": wl.N * wl.p / (ms / 1e3),
+                "subsampled_step_ms": ms_sub, "dmd_rank": inf["r"],
+                "fixed_point_iters": float(np.mean([int(i[0]) for i in its]))}
     # share of each kernel over three more intervals, every launch timed
     ctx.profile_reset()
     ctx.profile_enable(list(range(len(KERNELS))))
-    h.step(Q, Z, wl.dt, 3, arith=ARITH, kstate=K)
+    h.step(Q, Z, wl.dt, 3, arith=ARITH, kstate=K, trace=False)
     torch.cuda.synchronize()
     ctx.profile_enable([])
     prof = ctx.profile_read()
@@ -452,12 +464,15 @@ def hyper_measure(ctx, torch, dev, flush, steps: int = 10) -> dict:
     share = sorted(((k, v[2] / tot) for k, v in prof.items() if v[2] > 0), key=lambda x: -x[1])
     inf = h.info()
     h.close()
-    return {"workload": f"two-stream, N=1e5, p=64, Nx=128, dt=0.05, quiet start, 2n={2 * n}; "
+    out = {"workload": f"two-stream, N=1e5, p={p}, Nx=128, dt=0.05, quiet start, 2n={2 * n}; "
                         "DMD-DEIM coefficients (p*=12, T=3, d=32, n_up=12, k_DEIM=3, DMD tol 1e-5)",
             "value": wl.N * wl.p / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "subsampled_step_ms": ms_sub,
             "fixed_point_iters": float(np.mean([int(i[0]) for i in its])), "dmd_rank": inf["r"],
             "kernel_share": {k: round(f, 3) for k, f in share[:8]}}
+    # the coefficient stage no longer scales with N p: the same at p = 256
+    out["p256"] = hyper_measure(ctx, torch, dev, flush, steps=5, p=256, shares=False) if p == 64 else None
+    return out
 
 
 def deim_build_measure(ctx, torch, dev, reps: int = 5) -> dict:
@@ -596,7 +611,25 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.only:
+        return only(args)
     return ours(args, rank, world)
+
+
+def only(args):
+    """One extra measurement on GPU 0, printed as its own JSON line."""
+    import torch
+
+    from paper_2201_05555_gb300 import Context
+    dev = torch.device("cuda", 0)
+    ctx = Context(0)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    fn = {"hyper": lambda: hyper_measure(ctx, torch, dev, flush),
+          "dmd": lambda: dmd_measure(ctx, torch, dev),
+          "deim_build": lambda: deim_build_measure(ctx, torch, dev),
+          "subsampled": lambda: subsample_measure(ctx, torch, dev, flush)}[args.only]
+    print(json.dumps({args.only: fn()}))
+    return 0
 
 
 def reference_arm(args, rank, world):

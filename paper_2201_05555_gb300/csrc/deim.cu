@@ -699,88 +699,127 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
   }
   __syncthreads();
   const double floor2 = eps * eps * nrm_s * nrm_s;
-  int hi = r - 1, it = 0, total = 0;
-  bool failed = false;
   auto abs2 = [](double2 z) { return fma(z.x, z.x, z.y * z.y); };
-  while (hi > 0) {
-    int l = hi;
-    for (; l > 0; --l) {  // squared magnitudes: no square roots in the scan
-      const double sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
-      const double sub2 = abs2(H[l * r + l - 1]);
-      if (sub2 <= eps * eps * sc2 || sub2 <= floor2) break;
+  // the scalar decisions (deflation scan, shift, rotation) are taken by
+  // thread 0 and shared: FP64 chains cost the same in a full warp as in one
+  // lane, so only the row and column updates are spread over the block
+  __shared__ int sh_cmd, sh_l, sh_hi;
+  __shared__ double2 sh_mu, sh_sg;
+  __shared__ double sh_cg;
+  int it = 0, total = 0;  // thread 0's counters
+  if (lane == 0) sh_hi = r - 1;
+  __syncthreads();
+  bool failed = false;
+  while (true) {
+    if (lane == 0) {
+      const int hi = sh_hi;
+      int cmd = 0;
+      if (hi <= 0) {
+        cmd = 2;
+      } else {
+        int l = hi;
+        for (; l > 0; --l) {  // squared magnitudes: no square roots in the scan
+          const double sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
+          const double sub2 = abs2(H[l * r + l - 1]);
+          if (sub2 <= eps * eps * sc2 || sub2 <= floor2) break;
+        }
+        if (l > 0) H[l * r + l - 1] = make_double2(0.0, 0.0);
+        if (l == hi) {
+          sh_hi = hi - 1;
+          it = 0;
+          cmd = 1;
+        } else if (total > 40 * r) {
+          cmd = 3;
+        } else {
+          const double2 a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi],
+                        c = H[hi * r + hi - 1], d = H[hi * r + hi];
+          double2 mu;
+          if (it % 11 == 10) {
+            mu = make_double2(d.x + 0.75 * c_abs(c), d.y);
+          } else {
+            const double2 h = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
+            const double2 disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
+            const double2 m0 = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
+            const double2 m1 = cadd(m0, disc), m2 = csub(m0, disc);
+            mu = abs2(csub(m1, d)) < abs2(csub(m2, d)) ? m1 : m2;
+          }
+          sh_l = l;
+          sh_mu = mu;
+          ++it;
+          ++total;
+        }
+      }
+      sh_cmd = cmd;
     }
     __syncthreads();
-    if (l > 0 && lane == 0) H[l * r + l - 1] = make_double2(0.0, 0.0);
-    __syncthreads();
-    if (l == hi) {
-      --hi;
-      it = 0;
-      continue;
-    }
-    if (total > 40 * r) {
+    const int cmd = sh_cmd, l = sh_l, hi = sh_hi;
+    __syncthreads();  // all have read the decision before thread 0 takes the next
+    if (cmd == 2) break;
+    if (cmd == 3) {
       failed = true;
       break;
     }
-    const double2 a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi], c = H[hi * r + hi - 1],
-                  d = H[hi * r + hi];
-    double2 mu;
-    if (it % 11 == 10) {
-      mu = make_double2(d.x + 0.75 * c_abs(c), d.y);
-    } else {
-      const double2 h = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
-      const double2 disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
-      const double2 m0 = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
-      const double2 m1 = cadd(m0, disc), m2 = csub(m0, disc);
-      mu = abs2(csub(m1, d)) < abs2(csub(m2, d)) ? m1 : m2;
-    }
+    if (cmd == 1) continue;
     for (int k = l; k < hi; ++k) {
-      double2 x, y;
-      if (k == l) {
-        x = csub(H[l * r + l], mu);
-        y = H[(l + 1) * r + l];
-      } else {
-        x = H[k * r + k - 1];
-        y = H[(k + 1) * r + k - 1];
-      }
-      // G = [[cg, sg], [-conj(sg), cg]] with G [x; y] = [rho; 0]
-      double cg;
-      double2 sg;
-      if (y.x == 0.0 && y.y == 0.0) {
-        cg = 1.0;
-        sg = make_double2(0.0, 0.0);
-      } else if (x.x == 0.0 && x.y == 0.0) {
-        cg = 0.0;
-        sg = make_double2(1.0, 0.0);
-      } else {  // cg = |x| / n, sg = (x / |x|) conj(y) / n, n^2 = |x|^2 + |y|^2
-        const double ax2 = abs2(x), ix = rsqrt(ax2), in = rsqrt(ax2 + abs2(y));
-        cg = ax2 * ix * in;
-        sg = cmul(make_double2(x.x * ix, x.y * ix), make_double2(y.x * in, -y.y * in));
+      if (lane == 0) {
+        double2 x, y;
+        if (k == l) {
+          x = csub(H[l * r + l], sh_mu);
+          y = H[(l + 1) * r + l];
+        } else {
+          x = H[k * r + k - 1];
+          y = H[(k + 1) * r + k - 1];
+        }
+        // G = [[cg, sg], [-conj(sg), cg]] with G [x; y] = [rho; 0]
+        if (y.x == 0.0 && y.y == 0.0) {
+          sh_cg = 1.0;
+          sh_sg = make_double2(0.0, 0.0);
+        } else if (x.x == 0.0 && x.y == 0.0) {
+          sh_cg = 0.0;
+          sh_sg = make_double2(1.0, 0.0);
+        } else {  // cg = |x| / n, sg = (x / |x|) conj(y) / n, n^2 = |x|^2 + |y|^2
+          const double ax2 = abs2(x), ix = rsqrt(ax2), in = rsqrt(ax2 + abs2(y));
+          sh_cg = ax2 * ix * in;
+          sh_sg = cmul(make_double2(x.x * ix, x.y * ix), make_double2(y.x * in, -y.y * in));
+        }
       }
       __syncthreads();
-      const int j0 = k == l ? l : k - 1;
-      for (int j = j0 + lane; j < r; j += nl) {  // rows k, k+1 <- G [rows]
+      const double cg = sh_cg;
+      const double2 sg = sh_sg;
+      const double2 sc = make_double2(sg.x, -sg.y);
+      // rows k, k+1 <- G [rows]: one output per thread (FP64 issue, not the
+      // lane count, sets the cost, so outputs are spread over all warps);
+      // inputs are read before the barrier, outputs written after it
+      const int j0 = k == l ? l : k - 1, w = r - j0;
+      double2 outv = make_double2(0.0, 0.0);
+      int oidx = -1;
+      for (int o = lane; o < 2 * w; o += nl) {
+        const int j = j0 + (o < w ? o : o - w);
         const double2 h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
-        H[k * r + j] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(sg, h1));
-        H[(k + 1) * r + j] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(make_double2(sg.x, -sg.y), h0));
+        if (o < w) {
+          outv = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(sg, h1));
+          oidx = k * r + j;
+        } else {
+          outv = csub(make_double2(cg * h1.x, cg * h1.y), cmul(sc, h0));
+          oidx = (k + 1) * r + j;
+        }
       }
+      __syncthreads();
+      if (oidx >= 0) H[oidx] = outv;
       __syncthreads();
       if (k > l && lane == 0) H[(k + 1) * r + k - 1] = make_double2(0.0, 0.0);
-      const int i1 = min(k + 2, hi) + 1;
-      const double2 sc = make_double2(sg.x, -sg.y);
-      for (int i = lane; i < r; i += nl) {  // columns k, k+1 <- [columns] G^H
-        if (i < i1) {
-          const double2 h0 = H[i * r + k], h1 = H[i * r + k + 1];
-          H[i * r + k] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(h1, sc));
-          H[i * r + k + 1] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(h0, sg));
-        }
-        const double2 q0 = Qm[i * r + k], q1 = Qm[i * r + k + 1];
-        Qm[i * r + k] = cadd(make_double2(cg * q0.x, cg * q0.y), cmul(q1, sc));
-        Qm[i * r + k + 1] = csub(make_double2(cg * q1.x, cg * q1.y), cmul(q0, sg));
+      // columns k, k+1 <- [columns] G^H: H rows in the first half of the
+      // block, Q rows in the second (different warps, so they overlap)
+      const int i1 = min(k + 2, hi) + 1, half = nl / 2;
+      double2* M2 = lane < half ? H : Qm;
+      const int lim = lane < half ? i1 : r;
+      for (int i = lane < half ? lane : lane - half; i < lim; i += half) {
+        const double2 h0 = M2[i * r + k], h1 = M2[i * r + k + 1];
+        M2[i * r + k] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(h1, sc));
+        M2[i * r + k + 1] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(h0, sg));
       }
       __syncthreads();
     }
-    ++it;
-    ++total;
   }
   if (failed) {
     if (lane == 0) vp_set_status(status, VP_ENOCONV);
@@ -1230,7 +1269,7 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   // i.e. the row-major r x nx matrix B^T
   VP_K(VP_K_SUBSET, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
   // 4. real part of the principal square root of A for half steps
-  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 128, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
+  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 256, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
   return VP_OK;
 }
 
