@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
-    ap.add_argument("--only", choices=["hyper", "dmd", "deim_build", "subsampled"], default=None,
+    ap.add_argument("--only", choices=["hyper", "dmd", "deim_build", "subsampled", "precision"],
+                    default=None,
                     help="run one extra measurement alone and print its JSON (profiling runs)")
     return ap.parse_args()
 
@@ -627,7 +628,8 @@ def only(args):
     fn = {"hyper": lambda: hyper_measure(ctx, torch, dev, flush),
           "dmd": lambda: dmd_measure(ctx, torch, dev),
           "deim_build": lambda: deim_build_measure(ctx, torch, dev),
-          "subsampled": lambda: subsample_measure(ctx, torch, dev, flush)}[args.only]
+          "subsampled": lambda: subsample_measure(ctx, torch, dev, flush),
+          "precision": lambda: precision_measure(ctx, torch, dev, flush)}[args.only]
     print(json.dumps({args.only: fn()}))
     return 0
 

@@ -23,6 +23,7 @@ namespace vpk {
 
 struct ArithDF {
   using V = float2;
+  static constexpr bool kVec4 = false;
   static __device__ __forceinline__ V from(double d) { return df_split(d); }
   static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
@@ -53,6 +54,7 @@ struct ArithDF {
 
 struct ArithF32 {
   using V = float;
+  static constexpr bool kVec4 = true;  // rows of plain floats: float4 loads apply
   static __device__ __forceinline__ V from(double d) { return __double2float_rn(d); }
   static __device__ __forceinline__ V zero() { return 0.f; }
   static __device__ __forceinline__ V neg(V a) { return -a; }
@@ -167,10 +169,24 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   unsigned char* Qs0 = smraw + 16;
   V* Zs = reinterpret_cast<V*>(Qs0 + 2 * qst);
-  const size_t zoff = (16 + 2 * qst + sizeof(V) * n2 * ldz + 15) & ~size_t(15);
+  // FP32 rows with n % 4 == 0: the coefficients also go sample-major (Zt,
+  // rows padded to a multiple of 4) so that both operands of the dot
+  // product arrive as float4 (one shared-memory load per 4 multiply-adds)
+  const bool vec = AR::kVec4 && (n & 3) == 0;
+  const int ldk = n2 + 4;
+  const size_t zto = (16 + 2 * qst + sizeof(V) * n2 * ldz + 15) & ~size_t(15);
+  const size_t zoff = zto + (vec ? ((sizeof(float) * PC * ldk + 15) & ~size_t(15)) : 0);
+  float* Zt = reinterpret_cast<float*>(smraw + zto);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smraw + zoff);
   const int c0 = blockIdx.y * PC;
   load_zc<AR>(Zs, ldz, Zh2, n2, p, c0, PC);
+  if (vec) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2 * PC; e += blockDim.x) {
+      const int k = e / PC, i = e - k * PC;
+      Zt[i * ldk + k] = AR::hi(Zs[k * ldz + i]);
+    }
+  }
   for (int e = threadIdx.x; e < PC * Nx; e += blockDim.x) cnt[e] = 0ull;
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
   const bool active = c0 + ii < p;
@@ -207,13 +223,33 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
     if (active) {
       for (int r = rsub; r < rows; r += RP) {
         const V* q = Qs + r * n2;
-        typename AR::A x;
-        x.zero();
-        for (int k = 0; k < n; ++k) {
-          x.fma2(q[k], Zs[k * ldz + ii]);
-          x.fma2(AR::neg(q[n + k]), Zs[(n + k) * ldz + ii]);
+        V tt;
+        if (vec) {  // x = sum_k A_k a_k - B_k b_k in two partial sums
+          const float4* q4 = reinterpret_cast<const float4*>(q);
+          const float4* z4 = reinterpret_cast<const float4*>(Zt + ii * ldk);
+          const int n4 = n >> 2;
+          float s0 = 0.f, s1 = 0.f;
+          for (int k = 0; k < n4; ++k) {
+            const float4 a = q4[k], za = z4[k], b = q4[n4 + k], zb = z4[n4 + k];
+            s0 = fmaf(a.x, za.x, s0);
+            s1 = fmaf(a.y, za.y, s1);
+            s0 = fmaf(a.z, za.z, s0);
+            s1 = fmaf(a.w, za.w, s1);
+            s0 = fmaf(-b.x, zb.x, s0);
+            s1 = fmaf(-b.y, zb.y, s1);
+            s0 = fmaf(-b.z, zb.z, s0);
+            s1 = fmaf(-b.w, zb.w, s1);
+          }
+          tt = AR::from((double)(s0 + s1));
+        } else {
+          typename AR::A x;
+          x.zero();
+          for (int k = 0; k < n; ++k) {
+            x.fma2(q[k], Zs[k * ldz + ii]);
+            x.fma2(AR::neg(q[n + k]), Zs[(n + k) * ldz + ii]);
+          }
+          tt = x.out();
         }
-        const V tt = x.out();
         int j;
         long long w1;
         cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
@@ -277,6 +313,10 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
              jbytes, &bar[st]);
   };
   const int cc = t % PC, kk0 = t / PC, kstep = blockDim.x / PC;
+  // FP32 rows with n2 % 4 == 0: thread owns contiguous groups of four
+  // columns, read as float4 (one shared-memory load per 4 multiply-adds)
+  const bool vec = AR::kVec4 && (n2 & 3) == 0 && n2 <= 4 * kstep * (MAXACC / 4);
+  auto kof = [&](int a) { return vec ? 4 * (kk0 + (a >> 2) * kstep) + (a & 3) : kk0 + a * kstep; };
   typename AR::A acc[MAXACC];
 #pragma unroll
   for (int a = 0; a < MAXACC; ++a) acc[a].zero();
@@ -305,7 +345,40 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
     __syncthreads();
     // rows in groups of four: the loads of a group are issued together
     int r = 0;
-    for (; r + 4 <= rows; r += 4) {
+    if constexpr (AR::kVec4) {
+      for (; vec && r + 4 <= rows; r += 4) {
+        const float G0 = AR::hi(Gs[r * ldG + cc]), G1 = AR::hi(Gs[(r + 1) * ldG + cc]);
+        const float G2 = AR::hi(Gs[(r + 2) * ldG + cc]), G3 = AR::hi(Gs[(r + 3) * ldG + cc]);
+        const float* Qf = reinterpret_cast<const float*>(Qs);
+#pragma unroll
+        for (int b = 0; b < MAXACC / 4; ++b) {
+          const int k = 4 * (kk0 + b * kstep);
+          if (k < n2) {
+            const float4 q0 = *reinterpret_cast<const float4*>(Qf + r * n2 + k);
+            const float4 q1 = *reinterpret_cast<const float4*>(Qf + (r + 1) * n2 + k);
+            const float4 q2 = *reinterpret_cast<const float4*>(Qf + (r + 2) * n2 + k);
+            const float4 q3 = *reinterpret_cast<const float4*>(Qf + (r + 3) * n2 + k);
+            acc[4 * b + 0].fma2(q0.x, G0);
+            acc[4 * b + 1].fma2(q0.y, G0);
+            acc[4 * b + 2].fma2(q0.z, G0);
+            acc[4 * b + 3].fma2(q0.w, G0);
+            acc[4 * b + 0].fma2(q1.x, G1);
+            acc[4 * b + 1].fma2(q1.y, G1);
+            acc[4 * b + 2].fma2(q1.z, G1);
+            acc[4 * b + 3].fma2(q1.w, G1);
+            acc[4 * b + 0].fma2(q2.x, G2);
+            acc[4 * b + 1].fma2(q2.y, G2);
+            acc[4 * b + 2].fma2(q2.z, G2);
+            acc[4 * b + 3].fma2(q2.w, G2);
+            acc[4 * b + 0].fma2(q3.x, G3);
+            acc[4 * b + 1].fma2(q3.y, G3);
+            acc[4 * b + 2].fma2(q3.z, G3);
+            acc[4 * b + 3].fma2(q3.w, G3);
+          }
+        }
+      }
+    }
+    for (; !vec && r + 4 <= rows; r += 4) {
       const V G0 = Gs[r * ldG + cc], G1 = Gs[(r + 1) * ldG + cc];
       const V G2 = Gs[(r + 2) * ldG + cc], G3 = Gs[(r + 3) * ldG + cc];
 #pragma unroll
@@ -325,7 +398,7 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
       const V G = Gs[r * ldG + cc];
 #pragma unroll
       for (int a = 0; a < MAXACC; ++a) {
-        int k = kk0 + a * kstep;
+        int k = kof(a);
         if (k < n2) acc[a].fma2(Qs[r * n2 + k], G);
       }
     }
@@ -333,7 +406,7 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
   }
 #pragma unroll
   for (int a = 0; a < MAXACC; ++a) {
-    int k = kk0 + a * kstep;
+    int k = kof(a);
     if (k < n2 && c0 + cc < p) {
       double v = acc[a].value();
       part[(int64_t)blockIdx.x * n2 * p + (int64_t)k * p + c0 + cc] = (k < n) ? v : -v;
@@ -343,6 +416,9 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
 
 // -------------------------------------------------------- M = Gamma zeta^H
 // Gamma_li = (q/m) F_i[j_li] + i Im(Q_l zeta_i); M_lk = sum_i Gamma_li conj(zeta_ki).
+// Needs TILE_THREADS = 256 and TILE_ROWS = 64 (the product's thread map).
+#define BM_KJ 5  // columns per thread: k0 + 8 j < n <= 40
+static_assert(TILE_THREADS == 256 && TILE_ROWS == 64, "k_basis_M_lp thread map");
 template <class AR, int MAXACC>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
@@ -357,14 +433,19 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
   V* Gr = Fs + PC * Nx;          // TILE_ROWS x ldG, real part of Gamma
   V* Gi = Gr + TILE_ROWS * ldG;  // imaginary part
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
-  const int npairs = TILE_ROWS * n;
   const int nch = (p + PC - 1) / PC;
+  // product Gamma zeta^H: thread t owns rows r0, r0 + 32 (r0 = t / 8) and
+  // columns k0 + 8 j (k0 = t % 8, j < BM_KJ), so every value read from shared
+  // memory feeds several multiply-adds (register tiling)
+  const int r0 = t >> 3, k0 = t & 7;
   for (int64_t tile = blockIdx.x; tile * TILE_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * TILE_ROWS;
     const int rows = (int)((int64_t)TILE_ROWS < N - base ? (int64_t)TILE_ROWS : N - base);
-    typename AR::A ar[MAXACC], ai[MAXACC];
+    typename AR::A ar[2][BM_KJ], ai[2][BM_KJ];
 #pragma unroll
-    for (int a = 0; a < MAXACC; ++a) { ar[a].zero(); ai[a].zero(); }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < BM_KJ; ++j) { ar[h][j].zero(); ai[h][j].zero(); }
     __syncthreads();
     load_rows(Qs, ldq, Q2, n2, base, rows);
     for (int c0 = 0; c0 < p; c0 += PC) {
@@ -394,33 +475,41 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
       }
       __syncthreads();
       const int pc_eff = min(PC, p - c0);
+      // rows past the tile end hold zeros in Gr, Gi; columns past n are not stored
+      for (int c = 0; c < pc_eff; ++c) {
+        V grc[2], gic[2];
 #pragma unroll
-      for (int a = 0; a < MAXACC; ++a) {
-        int e = t + a * blockDim.x;
-        if (e < npairs) {
-          int r = e / n, k = e - r * n;
-          if (r < rows) {
-            for (int c = 0; c < pc_eff; ++c) {
-              V za = Zs[k * ldz + c], zb = Zs[(n + k) * ldz + c];
-              V grc = Gr[r * ldG + c], gic = Gi[r * ldG + c];
+        for (int h = 0; h < 2; ++h) {
+          grc[h] = Gr[(r0 + 32 * h) * ldG + c];
+          gic[h] = Gi[(r0 + 32 * h) * ldG + c];
+        }
+#pragma unroll
+        for (int j = 0; j < BM_KJ; ++j) {
+          const int k = k0 + 8 * j;
+          if (k < n) {
+            const V za = Zs[k * ldz + c], zb = Zs[(n + k) * ldz + c];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
               // Gamma conj(zeta) = (Gr a + Gi b) + i (Gi a - Gr b)
-              ar[a].fma2(grc, za);
-              ar[a].fma2(gic, zb);
-              ai[a].fma2(gic, za);
-              ai[a].fma2(AR::neg(grc), zb);
+              ar[h][j].fma2(grc[h], za);
+              ar[h][j].fma2(gic[h], zb);
+              ai[h][j].fma2(gic[h], za);
+              ai[h][j].fma2(AR::neg(grc[h]), zb);
             }
           }
         }
       }
     }
 #pragma unroll
-    for (int a = 0; a < MAXACC; ++a) {
-      int e = t + a * blockDim.x;
-      if (e < npairs) {
-        int r = e / n, k = e - r * n;
-        if (r < rows) {
-          M[(base + r) * n2 + k] = ar[a].out();
-          M[(base + r) * n2 + n + k] = ai[a].out();
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + 32 * h;
+      if (r >= rows) continue;
+#pragma unroll
+      for (int j = 0; j < BM_KJ; ++j) {
+        const int k = k0 + 8 * j;
+        if (k < n) {
+          M[(base + r) * n2 + k] = ar[h][j].out();
+          M[(base + r) * n2 + n + k] = ai[h][j].out();
         }
       }
     }
@@ -778,7 +867,9 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     case LP_DEPOSIT: {
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
+      const bool vec = AR::kVec4 && (n & 3) == 0;
       size_t smem = ((16 + 2 * qst + sizeof(V) * n2 * (PC + 1) + 15) & ~size_t(15)) +
+                    (vec ? ((sizeof(float) * PC * (n2 + 4) + 15) & ~size_t(15)) : 0) +
                     sizeof(unsigned long long) * PC * g.Nx;
       int gx = grid_bps(ceil_div(N, TILE_ROWS), ch, (A.tune ? A.tune : kTuneDefault)[TUNE_DEPOSIT], A.num_sms);
       k_deposit_lp<AR><<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
