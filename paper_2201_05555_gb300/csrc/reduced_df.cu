@@ -426,12 +426,17 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
              const uint16_t* __restrict__ jin, typename AR::V* __restrict__ M) {
   using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int n2 = 2 * n, ldq = n2 + 1, ldz = PC + 1, Nx = g.Nx, ldG = PC + 1;
+  // FP32 rows with n % 4 == 0: unpadded Q rows and a sample-major copy of
+  // the coefficient chunk (Zt), so that V_r = Im(Q zeta) reads float4 operands
+  const bool vec = AR::kVec4 && (n & 3) == 0;
+  const int n2 = 2 * n, ldq = vec ? n2 : n2 + 1, ldz = PC + 1, Nx = g.Nx, ldG = PC + 1;
+  const int ldk = n2 + 4;
   V* Qs = reinterpret_cast<V*>(smraw);
   V* Zs = Qs + TILE_ROWS * ldq;
-  V* Fs = Zs + n2 * ldz;
-  V* Gr = Fs + PC * Nx;          // TILE_ROWS x ldG, real part of Gamma
+  V* Gr = Zs + n2 * ldz;         // TILE_ROWS x ldG, real part of Gamma
   V* Gi = Gr + TILE_ROWS * ldG;  // imaginary part
+  float* Zt = reinterpret_cast<float*>(
+      smraw + ((reinterpret_cast<unsigned char*>(Gi + TILE_ROWS * ldG) - smraw + 15) & ~size_t(15)));
   const int t = threadIdx.x, ii = t & (PC - 1), rsub = t / PC, RP = blockDim.x / PC;
   const int nch = (p + PC - 1) / PC;
   // product Gamma zeta^H: thread t owns rows r0, r0 + 32 (r0 = t / 8) and
@@ -451,24 +456,47 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
     for (int c0 = 0; c0 < p; c0 += PC) {
       __syncthreads();
       load_zc<AR>(Zs, ldz, Z2, n2, p, c0, PC);
-      for (int e = t; e < PC * Nx; e += blockDim.x) {
-        int c = e / Nx;
-        Fs[e] = (c0 + c < p) ? F2[(int64_t)(c0 + c) * Nx + (e - c * Nx)] : AR::zero();
-      }
       __syncthreads();
+      if (vec) {
+        for (int e = t; e < n2 * PC; e += blockDim.x) {
+          const int k = e / PC, i = e - k * PC;
+          Zt[i * ldk + k] = AR::hi(Zs[k * ldz + i]);
+        }
+        __syncthreads();
+      }
       const bool active = c0 + ii < p;
       for (int r = rsub; r < rows; r += RP) {
         V gr = AR::zero(), gi = AR::zero();
         if (active) {
           const V* q = Qs + r * ldq;
-          typename AR::A v;
-          v.zero();
-          for (int k = 0; k < n; ++k) {
-            v.fma2(q[n + k], Zs[k * ldz + ii]);   // B a
-            v.fma2(q[k], Zs[(n + k) * ldz + ii]); // A b
+          if (vec) {  // v = sum_k B_k a_k + A_k b_k
+            const float4* q4 = reinterpret_cast<const float4*>(q);
+            const float4* z4 = reinterpret_cast<const float4*>(Zt + ii * ldk);
+            const int n4 = n >> 2;
+            float s0 = 0.f, s1 = 0.f;
+            for (int k = 0; k < n4; ++k) {
+              const float4 qa = q4[k], qb = q4[n4 + k], za = z4[k], zb = z4[n4 + k];
+              s0 = fmaf(qb.x, za.x, s0);
+              s1 = fmaf(qb.y, za.y, s1);
+              s0 = fmaf(qb.z, za.z, s0);
+              s1 = fmaf(qb.w, za.w, s1);
+              s0 = fmaf(qa.x, zb.x, s0);
+              s1 = fmaf(qa.y, zb.y, s1);
+              s0 = fmaf(qa.z, zb.z, s0);
+              s1 = fmaf(qa.w, zb.w, s1);
+            }
+            gi = AR::from((double)(s0 + s1));
+          } else {
+            typename AR::A v;
+            v.zero();
+            for (int k = 0; k < n; ++k) {
+              v.fma2(q[n + k], Zs[k * ldz + ii]);   // B a
+              v.fma2(q[k], Zs[(n + k) * ldz + ii]); // A b
+            }
+            gi = v.out();
           }
-          gr = Fs[ii * Nx + jin[jt_block(tile, c0 / PC, nch, PC) + r * PC + ii]];
-          gi = v.out();
+          // the chunk's field rows (PC x Nx) stay in L1 across the tiles
+          gr = __ldg(F2 + (int64_t)(c0 + ii) * Nx + jin[jt_block(tile, c0 / PC, nch, PC) + r * PC + ii]);
         }
         Gr[r * ldG + ii] = gr;
         Gi[r * ldG + ii] = gi;
@@ -914,8 +942,8 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
           break;
         }
       }
-      size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + PC * g.Nx +
-                                 2 * TILE_ROWS * (PC + 1));
+      size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + 2 * TILE_ROWS * (PC + 1)) +
+                    ((AR::kVec4 && (n & 3) == 0) ? 16 + sizeof(float) * PC * (n2 + 4) : 0);
       int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_BASIS_M], A.num_sms);
       if (TILE_ROWS * n <= 4 * TILE_THREADS)
         k_basis_M_lp<AR, 4><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
