@@ -23,6 +23,17 @@ GridC make_gridc(const vp_grid& gr, int64_t N) {
   g.S = fixed_point_bits(N);
   g.fp_scale = ldexp(1.0, g.S);
   g.fp_inv = ldexp(1.0, -g.S);
+  // packed FP32 deposit: the weight sums of a cell stay below 2^(Sp + bl)
+  // and the count below 2^bl (bl = bit length of N), so Sp + 2 bl <= 63
+  int bl = 0;
+  while (bl < 62 && (int64_t(1) << bl) <= N) ++bl;
+  g.Sp = std::min(24, 63 - 2 * bl);
+  if (g.Sp < 8) {
+    g.Sp = 0;
+    g.Kp = 0;
+  } else {
+    g.Kp = g.Sp + bl;
+  }
   return g;
 }
 
@@ -161,9 +172,28 @@ __global__ void k_poisson(GridC g, const double* __restrict__ rho,
   __shared__ double red[32];
   const int i = blockIdx.x, Nx = g.Nx;
   const int64_t base = (int64_t)i * Nx;
-  for (int c = threadIdx.x; c < Nx; c += blockDim.x) {
-    double r = rho ? rho[base + c] : g.Mq * ((double)counts[base + c] * g.fp_inv) + g.bg_load;
-    a[c] = r;
+  if (!rho && f2mode == 2 && g.Kp > 0) {
+    // packed FP32 counts: node count_c = n_c 2^Sp - W_c + W_{c-1} (periodic)
+    const unsigned long long mask = (1ull << g.Kp) - 1ull;
+    for (int c = threadIdx.x; c < Nx; c += blockDim.x) {
+      const unsigned long long P = counts[base + c];
+      a[c] = (double)(P >> g.Kp);
+      tmp[c] = (double)(P & mask);
+    }
+    __syncthreads();
+    const double one = ldexp(1.0, g.Sp), inv = ldexp(1.0, -g.Sp);
+    double nc[VP_MAX_NX / 256 + 1];
+    int q = 0;
+    for (int c = threadIdx.x; c < Nx; c += blockDim.x, ++q)
+      nc[q] = fma(a[c], one, tmp[c == 0 ? Nx - 1 : c - 1] - tmp[c]);  // exact integers
+    __syncthreads();
+    q = 0;
+    for (int c = threadIdx.x; c < Nx; c += blockDim.x, ++q) a[c] = g.Mq * (nc[q] * inv) + g.bg_load;
+  } else {
+    for (int c = threadIdx.x; c < Nx; c += blockDim.x) {
+      double r = rho ? rho[base + c] : g.Mq * ((double)counts[base + c] * g.fp_inv) + g.bg_load;
+      a[c] = r;
+    }
   }
   __syncthreads();
   if (zero_counts)

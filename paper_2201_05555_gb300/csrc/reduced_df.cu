@@ -192,6 +192,9 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
   const bool active = c0 + ii < p;
   const long long one = 1ll << g.S;
   const float scale = (float)g.fp_scale, inv_Nx = (float)g.inv_Nx;
+  const bool pack = AR::kVec4 && g.Kp > 0;  // the Poisson solve decodes the same form
+  const float pscale = (float)(1 << (g.Sp > 0 ? g.Sp : 0));
+  const unsigned long long pbit = g.Kp > 0 ? (1ull << g.Kp) : 0ull;
   unsigned long long* mycnt = cnt + ii * Nx;
   const int64_t ntiles = (N + TILE_ROWS - 1) / TILE_ROWS;
   if (t == 0) {
@@ -251,11 +254,25 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
           tt = x.out();
         }
         int j;
-        long long w1;
-        cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
-        int j1 = (j + 1 == Nx) ? 0 : j + 1;
-        atomicAdd(mycnt + j, (unsigned long long)(one - w1));
-        atomicAdd(mycnt + j1, (unsigned long long)w1);
+        if (pack) {
+          // FP32 rows: cell and fraction in FP32 (both exact), one packed
+          // count (1 << Kp) + round(frac 2^Sp) into the particle's cell
+          const float th = AR::hi(tt), fl = floorf(th);
+          const int q = __float2int_rn((th - fl) * pscale);
+          int jr = (int)fl;
+          const int wq = (int)floorf((float)jr * inv_Nx);
+          jr -= wq * Nx;
+          if (jr < 0) jr += Nx;
+          if (jr >= Nx) jr -= Nx;
+          j = jr;
+          atomicAdd(mycnt + j, pbit + (unsigned long long)q);
+        } else {
+          long long w1;
+          cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
+          int j1 = (j + 1 == Nx) ? 0 : j + 1;
+          atomicAdd(mycnt + j, (unsigned long long)(one - w1));
+          atomicAdd(mycnt + j1, (unsigned long long)w1);
+        }
         if (jout) jout[jt_block(tile, blockIdx.y, gridDim.y, PC) + r * PC + ii] = (uint16_t)j;
       }
     }

@@ -242,6 +242,10 @@ struct GridC {
   int Nx;
   double L, h, inv_h, inv_Nx, dNx, Mq, mp, qm, bg_load, fp_scale, fp_inv;  // fp_*: 2^S, 2^-S
   int S;
+  // FP32 row form: one packed count per particle, (1 << Kp) + round(frac 2^Sp)
+  // into its cell (the count field above bit Kp, the weight sum below it);
+  // Kp = 0 when N is too large for packing
+  int Sp, Kp;
 };
 GridC make_gridc(const vp_grid& g, int64_t N);
 
