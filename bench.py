@@ -650,6 +650,23 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The timed region's duration as the slowest rank saw it (every rank runs
+    its own replica; the job ends with the last one)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job particle-steps/s: the units all ranks processed over the
+    slowest rank's time."""
+    return units_per_step * steps * world / (ms / 1e3)
+
+
 def config_dict(world):
     return {"workload": "two-stream reduced model, N=1e5 particles x p=64 samples, 2n=20, "
                         "Nx=128, dt=0.05, FP64",
@@ -722,10 +739,7 @@ def ours(args, rank, world):
     total_launches = sum(v[0] for v in prof.values())
     ctx.sync_status()
     its = [int(i[0]) for i in iters]
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
 
     # ---- end to end through host buffers: H2D state, one step, D2H state
     Qh = Q.cpu().pin_memory()
@@ -747,14 +761,11 @@ def ours(args, rank, world):
         e2e_ev[s][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
 
     units_step = wl.N * wl.p
-    value = units_step * args.steps * world / (ms / 1e3)
-    e2e_value = units_step * args.steps * world / (e2e_ms / 1e3)
+    value = job_throughput(units_step, args.steps, world, ms)
+    e2e_value = job_throughput(units_step, args.steps, world, e2e_ms)
     state_bytes = Q.numel() * 8 + Z.numel() * 8
 
     # ---- roofline of the dominant kernel (k_project: FP64 ALU bound)
