@@ -436,7 +436,7 @@ k_project_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
 // Needs TILE_THREADS = 256 and TILE_ROWS = 64 (the product's thread map).
 #define BM_KJ 5  // columns per thread: k0 + 8 j < n <= 40
 static_assert(TILE_THREADS == 256 && TILE_ROWS == 64, "k_basis_M_lp thread map");
-template <class AR, int MAXACC>
+template <class AR>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __restrict__ Q2,
              const typename AR::V* __restrict__ Z2, const typename AR::V* __restrict__ F2,
@@ -962,14 +962,9 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       size_t smem = sizeof(V) * (TILE_ROWS * (n2 + 1) + n2 * (PC + 1) + 2 * TILE_ROWS * (PC + 1)) +
                     ((AR::kVec4 && (n & 3) == 0) ? 16 + sizeof(float) * PC * (n2 + 4) : 0);
       int gx = grid_bps(ceil_div(N, TILE_ROWS), 1, (A.tune ? A.tune : kTuneDefault)[TUNE_BASIS_M], A.num_sms);
-      if (TILE_ROWS * n <= 4 * TILE_THREADS)
-        k_basis_M_lp<AR, 4><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
-                                                            (const V*)A.v1, (const V*)A.v2, A.j,
-                                                            (V*)A.v3);
-      else
-        k_basis_M_lp<AR, 16><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
-                                                             (const V*)A.v1, (const V*)A.v2, A.j,
-                                                             (V*)A.v3);
+      k_basis_M_lp<AR><<<gx, TILE_THREADS, smem, st>>>(g, N, n, p, PC, (const V*)A.v0,
+                                                       (const V*)A.v1, (const V*)A.v2, A.j,
+                                                       (V*)A.v3);
       break;
     }
     case LP_GRAM: {
@@ -1013,8 +1008,7 @@ static void set_attrs() {
   cudaFuncSetAttribute(k_deposit_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_project_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_project_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_basis_M_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_basis_M_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_basis_M_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_basis_M2_lp<AR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_basis_M2_lp<AR, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_gram_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
