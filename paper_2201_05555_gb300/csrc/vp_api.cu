@@ -871,15 +871,14 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
     delete h;
     return vp_cuda_check(ctx, e, "DMD-DEIM streams and events");
   }
-  cudaStream_t s0 = nullptr;
-  e = cudaMemcpyAsync(h->sub, o.sub_idx, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, s0);
+  e = cudaMemcpyAsync(h->sub, o.sub_idx, sizeof(int32_t) * q, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->eta, o.eta, sizeof(double) * p * o.dim, cudaMemcpyDeviceToDevice, s0);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->phi_half, 0, sizeof(double) * p * Nx, s0);
+    e = cudaMemcpyAsync(h->eta, o.eta, sizeof(double) * p * o.dim, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->phi_half, 0, sizeof(double) * p * Nx, st);
   if (e == cudaSuccess) {
-    k_gather_eta<<<1, 256, 0, s0>>>(o.dim, q, h->sub, h->eta, p, h->eta_s, ctx->d_status);
-    rbf_width_run(o.dim, q, h->eta_s, h->eps, s0);
-    e = cudaStreamSynchronize(s0);
+    k_gather_eta<<<1, 256, 0, st>>>(o.dim, q, h->sub, h->eta, p, h->eta_s, ctx->d_status);
+    rbf_width_run(o.dim, q, h->eta_s, h->eps, st);
+    e = cudaStreamSynchronize(st);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
