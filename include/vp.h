@@ -639,7 +639,8 @@ typedef enum vp_kernel {
   VP_K_AFFINE, VP_K_CELL_GRADIENT, VP_K_SMALL_BASIS, VP_K_SMALL_CAYLEY, VP_K_SMALL_TANGENT,
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
-  VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_COUNT
+  VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
+  VP_K_JACOBI_SYM, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

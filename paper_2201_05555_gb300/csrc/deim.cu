@@ -1150,12 +1150,12 @@ vp_status deim_basis_run(vp_ctx* ctx, int64_t N, int m, const double* Y, int64_t
   double* Wj = a.take<double>(tot);
   double* Ws = a.take<double>(tot);
   double* lam = a.take<double>(m);
-  VP_K(VP_K_SUBSET, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(N, m, Y, ldy,
+  VP_K(VP_K_DEIM, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(N, m, Y, ldy,
                                                                                       part)));
   VP_K(VP_K_REDUCE, reduce_partials(gx, tri, part, G, nullptr, st));
-  VP_K(VP_K_INIT, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
+  VP_K(VP_K_JACOBI_SYM, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
   int bx = std::min<int64_t>(ceil_div(N, 256), 4 * ctx->num_sms);
-  VP_K(VP_K_SUBSET, (k_psi<<<bx, 256, sizeof(double) * m * d, st>>>(N, m, d, Y, ldy, Ws, lam, Psi,
+  VP_K(VP_K_DEIM, (k_psi<<<bx, 256, sizeof(double) * m * d, st>>>(N, m, d, Y, ldy, Ws, lam, Psi,
                                                                     sigma, ctx->d_status)));
   return VP_OK;
 }
@@ -1182,15 +1182,15 @@ vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int
   int* ticket = a.take<int>(1);
   const int* rn = nullptr;
   if (Psi_prev) {  // index update: renew the n_up most rotated positions
-    VP_K(VP_K_SUBSET, (k_rot_dots<<<nb, 256, 0, st>>>(N, d, Psi, Psi_prev, part)));
+    VP_K(VP_K_DEIM, (k_rot_dots<<<nb, 256, 0, st>>>(N, d, Psi, Psi_prev, part)));
     VP_K(VP_K_REDUCE, reduce_partials(nb, d, part, dots, nullptr, st));
-    VP_K(VP_K_SUBSET, (k_renew<<<1, 32, 0, st>>>(d, dots, n_up, renew)));
+    VP_K(VP_K_DEIM, (k_renew<<<1, 32, 0, st>>>(d, dots, n_up, renew)));
     rn = renew;
   }
   VP_CUDA(cudaMemcpyAsync(R, Psi, sizeof(double) * d * N, cudaMemcpyDeviceToDevice, st));
   VP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
   for (int k = 0; k < d; ++k)
-    VP_K(VP_K_SUBSET, (k_deim_lu<<<nb, 256, 0, st>>>(N, d, k, R, prow, idx, rn, pval, pidx, ticket,
+    VP_K(VP_K_DEIM, (k_deim_lu<<<nb, 256, 0, st>>>(N, d, k, R, prow, idx, rn, pval, pidx, ticket,
                                                      ctx->d_status)));
   return VP_OK;
 }
@@ -1206,9 +1206,9 @@ vp_status deim_weights_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, con
   Arena a{(char*)scratch, 0, deim_weights_scratch(ctx->num_sms, N, d)};
   double* part = a.take<double>((size_t)nb * d);
   double* colsum = a.take<double>(d);
-  VP_K(VP_K_SUBSET, (k_colsum<<<nb, 256, 0, st>>>(N, d, Psi, part)));
+  VP_K(VP_K_DEIM, (k_colsum<<<nb, 256, 0, st>>>(N, d, Psi, part)));
   VP_K(VP_K_REDUCE, reduce_partials(nb, d, part, colsum, nullptr, st));
-  VP_K(VP_K_SUBSET, (k_deim_weights<<<1, 256, sizeof(double) * d * (d + 1), st>>>(
+  VP_K(VP_K_DEIM, (k_deim_weights<<<1, 256, sizeof(double) * d * (d + 1), st>>>(
                         N, d, Psi, idx, colsum, Mq, c, ctx->d_status)));
   return VP_OK;
 }
@@ -1239,10 +1239,10 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   double* BtB = a.take<double>((size_t)r_max * r_max);
   double* BtBi = a.take<double>((size_t)r_max * r_max);
   // 1. Y^T Y and its eigen-decomposition (singular values and right vectors of Y)
-  VP_K(VP_K_SUBSET, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(nx, m, Y, nx,
+  VP_K(VP_K_DMD, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(nx, m, Y, nx,
                                                                                        part)));
   VP_K(VP_K_REDUCE, reduce_partials(gx, tri, part, G, nullptr, st));
-  VP_K(VP_K_INIT, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
+  VP_K(VP_K_JACOBI_SYM, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
   std::vector<double> lh(m);
   VP_CUDA(cudaMemcpyAsync(lh.data(), lam, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
   VP_CUDA(cudaStreamSynchronize(st));
@@ -1255,21 +1255,21 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
     if (lh[k] > 0.0 && std::sqrt(lh[k]) > tol_eff * s1) ++r;
   if (r < 1) return vp_fail(ctx, VP_ENUMERIC, "DMD data matrix is zero");
   *r_out = r;
-  if (sigma) VP_K(VP_K_INIT, sqrt_nonneg(m, lam, sigma, st));
+  if (sigma) VP_K(VP_K_DMD, sqrt_nonneg(m, lam, sigma, st));
   // 3. C = V_r S_r^-1; U_r = Y C, B = Y' C; A = U_r^T B; B^+ = (B^T B)^-1 B^T
-  VP_K(VP_K_SUBSET, (k_dmd_coeff<<<1, 256, 0, st>>>(m, r, Ws, lam, C, ctx->d_status)));
+  VP_K(VP_K_DMD, (k_dmd_coeff<<<1, 256, 0, st>>>(m, r, Ws, lam, C, ctx->d_status)));
   const int gcols = std::max(1, std::min(ceil_div((int64_t)nx * r, 256), 4 * ctx->num_sms));
-  VP_K(VP_K_SUBSET, (k_cols_times<<<gcols, 256, 0, st>>>(nx, m, r, Y, C, U)));
-  VP_K(VP_K_SUBSET, (k_cols_times<<<gcols, 256, 0, st>>>(nx, m, r, Yp, C, B)));
-  VP_K(VP_K_SUBSET, (k_cols_dot<<<ceil_div(r * r, 256), 256, 0, st>>>(nx, r, r, U, B, A)));
-  VP_K(VP_K_SUBSET, (k_cols_dot<<<ceil_div(r * r, 256), 256, 0, st>>>(nx, r, r, B, B, BtB)));
-  VP_K(VP_K_SUBSET, (k_inverse<<<1, 256, sizeof(double) * 2 * r * r, st>>>(r, BtB, BtBi,
+  VP_K(VP_K_DMD, (k_cols_times<<<gcols, 256, 0, st>>>(nx, m, r, Y, C, U)));
+  VP_K(VP_K_DMD, (k_cols_times<<<gcols, 256, 0, st>>>(nx, m, r, Yp, C, B)));
+  VP_K(VP_K_DMD, (k_cols_dot<<<ceil_div(r * r, 256), 256, 0, st>>>(nx, r, r, U, B, A)));
+  VP_K(VP_K_DMD, (k_cols_dot<<<ceil_div(r * r, 256), 256, 0, st>>>(nx, r, r, B, B, BtB)));
+  VP_K(VP_K_DMD, (k_inverse<<<1, 256, sizeof(double) * 2 * r * r, st>>>(r, BtB, BtBi,
                                                                            ctx->d_status)));
   // B^+ (r x nx) = BtBi (r x r) * B^T; B is stored as r columns of length nx,
   // i.e. the row-major r x nx matrix B^T
-  VP_K(VP_K_SUBSET, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
+  VP_K(VP_K_DMD, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
   // 4. real part of the principal square root of A for half steps
-  VP_K(VP_K_SUBSET, (k_sqrtm<<<1, 256, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
+  VP_K(VP_K_DMD, (k_sqrtm<<<1, 256, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
   return VP_OK;
 }
 
@@ -1328,7 +1328,7 @@ vp_status vp_potential_at_particles(vp_ctx* ctx, const vp_grid* grid, int64_t N,
   int bx = ceil_div(N, 256);
   const int want = (4 * ctx->num_sms + p - 1) / p;
   if (bx > want) bx = want;
-  VP_K(VP_K_SUBSET, (k_phi_at<<<dim3(bx, p), 256, 0, st>>>(g, N, p, X, ldx, phi, Y, ldy)));
+  VP_K(VP_K_DEIM, (k_phi_at<<<dim3(bx, p), 256, 0, st>>>(g, N, p, X, ldx, phi, Y, ldy)));
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -1407,7 +1407,7 @@ vp_status vp_dmd_coords(vp_ctx* ctx, int32_t nx, int32_t r, const double* Bpinv,
   if (!ctx || !Bpinv || !Phi || !beta || nx < 1 || r < 1 || r > 64 || q < 1) return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_SUBSET, dmd_coords_run(nx, r, Bpinv, q, Phi, beta, st));
+  VP_K(VP_K_DMD, dmd_coords_run(nx, r, Bpinv, q, Phi, beta, st));
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -1420,7 +1420,7 @@ vp_status vp_rbf_interpolate(vp_ctx* ctx, int32_t dim, int32_t q, const double* 
     return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_SUBSET, rbf_run(dim, q, eta_s, K, values, p, eta, eps, nullptr, out, ctx->d_status, st));
+  VP_K(VP_K_DMD, rbf_run(dim, q, eta_s, K, values, p, eta, eps, nullptr, out, ctx->d_status, st));
   VP_LAUNCHED();
   return VP_OK;
 }
@@ -1433,7 +1433,7 @@ vp_status vp_dmd_potential(vp_ctx* ctx, int32_t nx, int32_t r, const double* B, 
     return VP_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  VP_K(VP_K_SUBSET, dmd_potential_run(nx, r, B, A, S, p, beta, ksteps, half, Phi, st));
+  VP_K(VP_K_DMD, dmd_potential_run(nx, r, B, A, S, p, beta, ksteps, half, Phi, st));
   VP_LAUNCHED();
   return VP_OK;
 }

@@ -98,6 +98,26 @@ __device__ __forceinline__ void cell_fixed(float th, float tl, int Nx, float inv
   w1 = q;
 }
 
+// register-resident coefficients in the deposit: instances for n up to each
+// bound (double-float rows; FP32 rows with n % 4 == 0), the smallest that
+// holds n is launched so that small ranks keep a small register count
+static constexpr int kDepNrDF[2] = {4, 10};
+static constexpr int kDepNrF32[3] = {8, 16, 32};
+
+// the register bound launched for rank n, 0 for the shared-memory operands
+template <class AR>
+static inline int dep_nr(int n) {
+  if constexpr (AR::kVec4) {
+    if (n & 3) return 0;
+    for (int b : kDepNrF32)
+      if (n <= b) return b;
+  } else {
+    for (int b : kDepNrDF)
+      if (n <= b) return b;
+  }
+  return 0;
+}
+
 static inline int chunk_w(int p, int Nx) {
   int pc = 1;
   while (pc < p && pc < 32) pc <<= 1;
@@ -153,8 +173,12 @@ __device__ __forceinline__ void load_zc(typename AR::V* Zs, int ldz,
 // shared memory (int64, order-free) and go to the global counts once per
 // block.  Full tiles of Q rows arrive by bulk copies into two stages, the
 // copy of the block's next tile running during the current one; a partial
-// last tile is read with plain loads.
-template <class AR>
+// last tile is read with plain loads.  With NR > 0 (n <= NR; for FP32 rows
+// also n % 4 == 0) each thread keeps its sample's coefficients in registers
+// for the whole launch, so the dot product reads only Q from shared memory
+// (broadcast within the warp); the terms are summed in the same order as
+// with the shared-memory operands.
+template <class AR, int NR>
 __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
                              const typename AR::V* __restrict__ Q2,
                              const typename AR::V* __restrict__ Zh2,
@@ -173,14 +197,15 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
   // rows padded to a multiple of 4) so that both operands of the dot
   // product arrive as float4 (one shared-memory load per 4 multiply-adds)
   const bool vec = AR::kVec4 && (n & 3) == 0;
+  const bool zt = vec && NR == 0;  // Zt only when the coefficients stay in shared memory
   const int ldk = n2 + 4;
   const size_t zto = (16 + 2 * qst + sizeof(V) * n2 * ldz + 15) & ~size_t(15);
-  const size_t zoff = zto + (vec ? ((sizeof(float) * PC * ldk + 15) & ~size_t(15)) : 0);
+  const size_t zoff = zto + (zt ? ((sizeof(float) * PC * ldk + 15) & ~size_t(15)) : 0);
   float* Zt = reinterpret_cast<float*>(smraw + zto);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smraw + zoff);
   const int c0 = blockIdx.y * PC;
   load_zc<AR>(Zs, ldz, Zh2, n2, p, c0, PC);
-  if (vec) {
+  if (zt) {
     __syncthreads();
     for (int e = threadIdx.x; e < n2 * PC; e += blockDim.x) {
       const int k = e / PC, i = e - k * PC;
@@ -203,6 +228,15 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
     mbar_fence_init();
   }
   __syncthreads();
+  // registers: za[k] = a_k / h, zb[k] = b_k / h of sample c0 + ii
+  V za[NR > 0 ? NR : 1], zb[NR > 0 ? NR : 1];
+  if constexpr (NR > 0) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      za[k] = k < n ? Zs[k * ldz + ii] : AR::zero();
+      zb[k] = k < n ? Zs[(n + k) * ldz + ii] : AR::zero();
+    }
+  }
   auto issue = [&](int64_t tl, int st) {
     if (t != 0 || tl >= ntiles || (tl + 1) * TILE_ROWS > N) return;
     fence_proxy_async_smem();
@@ -227,7 +261,25 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
       for (int r = rsub; r < rows; r += RP) {
         const V* q = Qs + r * n2;
         V tt;
-        if (vec) {  // x = sum_k A_k a_k - B_k b_k in two partial sums
+        if constexpr (NR > 0 && AR::kVec4) {  // x = sum_k A_k a_k - B_k b_k, coefficients in registers
+          const float4* q4 = reinterpret_cast<const float4*>(q);
+          const int n4 = n >> 2;
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < NR / 4; ++k)
+            if (k < n4) {
+              const float4 a = q4[k], b = q4[n4 + k];
+              s0 = fmaf(a.x, za[4 * k], s0);
+              s1 = fmaf(a.y, za[4 * k + 1], s1);
+              s0 = fmaf(a.z, za[4 * k + 2], s0);
+              s1 = fmaf(a.w, za[4 * k + 3], s1);
+              s0 = fmaf(-b.x, zb[4 * k], s0);
+              s1 = fmaf(-b.y, zb[4 * k + 1], s1);
+              s0 = fmaf(-b.z, zb[4 * k + 2], s0);
+              s1 = fmaf(-b.w, zb[4 * k + 3], s1);
+            }
+          tt = AR::from((double)(s0 + s1));
+        } else if (vec) {  // x = sum_k A_k a_k - B_k b_k in two partial sums
           const float4* q4 = reinterpret_cast<const float4*>(q);
           const float4* z4 = reinterpret_cast<const float4*>(Zt + ii * ldk);
           const int n4 = n >> 2;
@@ -244,6 +296,16 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
             s1 = fmaf(-b.w, zb.w, s1);
           }
           tt = AR::from((double)(s0 + s1));
+        } else if constexpr (NR > 0) {
+          typename AR::A x;
+          x.zero();
+#pragma unroll
+          for (int k = 0; k < NR; ++k)
+            if (k < n) {
+              x.fma2(q[k], za[k]);
+              x.fma2(AR::neg(q[n + k]), zb[k]);
+            }
+          tt = x.out();
         } else {
           typename AR::A x;
           x.zero();
@@ -913,11 +975,21 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
       const bool vec = AR::kVec4 && (n & 3) == 0;
+      const int nr = dep_nr<AR>(n);
       size_t smem = ((16 + 2 * qst + sizeof(V) * n2 * (PC + 1) + 15) & ~size_t(15)) +
-                    (vec ? ((sizeof(float) * PC * (n2 + 4) + 15) & ~size_t(15)) : 0) +
+                    ((vec && nr == 0) ? ((sizeof(float) * PC * (n2 + 4) + 15) & ~size_t(15)) : 0) +
                     sizeof(unsigned long long) * PC * g.Nx;
       int gx = grid_bps(ceil_div(N, TILE_ROWS), ch, (A.tune ? A.tune : kTuneDefault)[TUNE_DEPOSIT], A.num_sms);
-      k_deposit_lp<AR><<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
+      auto kern = k_deposit_lp<AR, 0>;
+      if constexpr (AR::kVec4) {
+        if (nr == kDepNrF32[0]) kern = k_deposit_lp<AR, kDepNrF32[0]>;
+        if (nr == kDepNrF32[1]) kern = k_deposit_lp<AR, kDepNrF32[1]>;
+        if (nr == kDepNrF32[2]) kern = k_deposit_lp<AR, kDepNrF32[2]>;
+      } else {
+        if (nr == kDepNrDF[0]) kern = k_deposit_lp<AR, kDepNrDF[0]>;
+        if (nr == kDepNrDF[1]) kern = k_deposit_lp<AR, kDepNrDF[1]>;
+      }
+      kern<<<dim3(gx, ch), TILE_THREADS, smem, st>>>(
           g, N, n, p, PC, (const V*)A.v0, (const V*)A.v1, A.counts, A.j, A.skip, A.status);
       break;
     }
@@ -1005,7 +1077,15 @@ void lp_launch(int arith, LpOp op, const LpArgs& a, cudaStream_t st) {
 template <class AR>
 static void set_attrs() {
   const int big = 220 * 1024;
-  cudaFuncSetAttribute(k_deposit_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_deposit_lp<AR, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if constexpr (AR::kVec4) {
+    cudaFuncSetAttribute(k_deposit_lp<AR, kDepNrF32[0]>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_deposit_lp<AR, kDepNrF32[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_deposit_lp<AR, kDepNrF32[2]>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  } else {
+    cudaFuncSetAttribute(k_deposit_lp<AR, kDepNrDF[0]>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_deposit_lp<AR, kDepNrDF[1]>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  }
   cudaFuncSetAttribute(k_project_lp<AR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_project_lp<AR, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_basis_M_lp<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

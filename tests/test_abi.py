@@ -58,3 +58,18 @@ def test_host_validation_without_gpu(lib):
     # a NULL context is rejected on the host before any CUDA call
     lib.vp_deposit_cic.restype = ctypes.c_int32
     assert lib.vp_deposit_cic(None, None, 10, 1, None, 10, None, None) == 1  # VP_EINVAL
+
+
+def test_kernel_names_match_the_binding(lib):
+    # the profiling ids of include/vp.h, the library's name table and the
+    # binding's list agree entry by entry (bench kernel shares use the names)
+    from paper_2201_05555_gb300.binding import KERNELS
+
+    text = open(os.path.join(ROOT, "include", "vp.h")).read()
+    body = re.search(r"typedef enum vp_kernel \{(.*?)\} vp_kernel;", text, flags=re.S).group(1)
+    ids = [t.strip().split("=")[0].strip() for t in body.split(",") if t.strip()]
+    assert ids[-1] == "VP_K_COUNT" and len(ids) - 1 == len(KERNELS)
+    lib.vp_kernel_name.restype = ctypes.c_char_p
+    lib.vp_kernel_name.argtypes = [ctypes.c_int32]
+    assert [lib.vp_kernel_name(i).decode() for i in range(len(KERNELS))] == KERNELS
+    assert lib.vp_kernel_name(len(KERNELS)) == b"unknown"
