@@ -715,8 +715,9 @@ def ours(args, rank, world):
 
     # ---- timed region: device-resident state
     KP = "k_project_lp" if ARITH else "k_project"
+    KD = "k_deposit_lp" if ARITH else "k_deposit_reduced"
     ctx.profile_reset()
-    ctx.profile_enable([KP])
+    ctx.profile_enable([KD, KP])
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -768,21 +769,30 @@ def ours(args, rank, world):
     e2e_value = job_throughput(units_step, args.steps, world, e2e_ms)
     state_bytes = Q.numel() * 8 + Z.numel() * 8
 
-    # ---- roofline of the dominant kernel (k_project: FP64 ALU bound)
-    l, timed, pms = prof[KP]
-    real = sum(its)  # launches that did work (the rest exit on the converged flag)
-    # algorithmic FP64 flop per launch: projection 2n FMA per particle-sample
-    # (+ 2n for the position when it is recomputed in FP64)
-    flop_per_launch = units_step * (4 if ARITH == 1 else 8) * n
-    achieved = flop_per_launch * real / (pms / 1e3) / 1e12 if pms > 0 else None
+    # ---- roofline of the dominant kernel (the deposit, largest share of the
+    # step in the launch list) and of the projection beside it; both ALU bound
     peak = DF_PEAK_TFLOPS if ARITH == 1 else FP64_PEAK_TFLOPS
     basis = ("double-float Dot2: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 flop / 12 FP32 "
              "instructions per emulated FP64 FMA" if ARITH == 1 else
              "FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2.07 GHz, measured 1.19 TFLOP/s")
-    roof = {"bound": "alu", "kernel": KP, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(KP),
-            "launches": l, "working_launches": real, "ms_total": pms, "peak_basis": basis,
-            "flop_per_launch": flop_per_launch}
+
+    def kernel_roof(kern, flop_per_launch, real):
+        l, _, kms = prof[kern]
+        achieved = flop_per_launch * real / (kms / 1e3) / 1e12 if kms > 0 else None
+        return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": profiled_traffic(kern), "launches": l, "working_launches": real,
+                "ms_total": kms, "peak_basis": basis, "flop_per_launch": flop_per_launch}
+
+    # algorithmic FP64 flop per launch, per particle-sample: the deposit's
+    # position 2n FMA; the projection 2n FMA (+ 2n for the position when the
+    # FP64 form recomputes it).  Working launches: every fixed-point round that
+    # did work (the rest exit on the converged flag) and, for the deposit, the
+    # two other field evaluations of each step (entering state, stage 3)
+    rounds = sum(its)
+    roof = kernel_roof(KD, units_step * 4 * n,
+                       rounds + 2 * args.steps if ARITH == 1 else prof[KD][0])
+    roof_proj = kernel_roof(KP, units_step * (4 if ARITH == 1 else 8) * n, rounds)
     clocks = clk.summary()
     if rank != 0:
         return 0
@@ -792,7 +802,8 @@ def ours(args, rank, world):
             "config": config_dict(world),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + trh.numel() * 8},
-            "gpu_launches": total_launches, "roofline": roof, "clocks": clocks,
+            "gpu_launches": total_launches, "roofline": roof, "roofline_project": roof_proj,
+            "clocks": clocks,
             "autotuned_blocks_per_sm": tuned,
             "fixed_point_iters": its}
     if not args.no_extras and world == 1:
