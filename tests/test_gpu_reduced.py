@@ -222,6 +222,22 @@ def test_prk2_large_rank_parity(ctx, sh, arith):
     assert rel(UZ, Uo @ Zo) < (TOL if arith < 2 else 1e-5)
 
 
+@pytest.mark.parametrize("arith,n", [(1, 4), (1, 9), (1, 11), (2, 4), (2, 8), (2, 12), (2, 6)])
+def test_deposit_register_bounds_parity(ctx, arith, n):
+    """The deposit keeps a sample's coefficients in registers up to a bound on n
+    (double-float: 4, 10; FP32 rows with n % 4 == 0: 8, 16, 32) and reads them
+    from shared memory above it or for other FP32 ranks: ranks at and beside
+    each bound, one step against the oracle (1e-10; FP32 rows 1e-5 on UZ)."""
+    g, grid, U, Z = state(N=3001, p=37, n=n, Nx=64)
+    dt = 0.05
+    Qd, Zd = T(q_storage(U)), T(Z)
+    ctx.basis_update(grid, Qd, Zd, dt, 1, arith=arith, reortho=arith == 2)
+    ctx.sync_status()
+    Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
+    UZ = U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy()
+    assert rel(UZ, Uo @ Zo) < (TOL if arith < 2 else 1e-5)
+
+
 # ------------------------------------------------------- parameter subsample
 @pytest.mark.parametrize("p,pmax,tol", [(37, 9, 0.0), (64, 64, 0.0), (200, 50, 0.3), (5, 3, 0.0)])
 def test_param_subsample_parity(ctx, p, pmax, tol):
