@@ -299,12 +299,26 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
         } else if constexpr (NR > 0) {
           typename AR::A x;
           x.zero();
+          if ((n & 1) == 0) {  // n even: two terms of A and of B per 16-byte load
+            static_assert(NR % 2 == 0, "pairs of terms");
 #pragma unroll
-          for (int k = 0; k < NR; ++k)
-            if (k < n) {
-              x.fma2(q[k], za[k]);
-              x.fma2(AR::neg(q[n + k]), zb[k]);
-            }
+            for (int k = 0; k < NR; k += 2)
+              if (k < n) {
+                const float4 qa = *reinterpret_cast<const float4*>(q + k);
+                const float4 qb = *reinterpret_cast<const float4*>(q + n + k);
+                x.fma2(make_float2(qa.x, qa.y), za[k]);
+                x.fma2(AR::neg(make_float2(qb.x, qb.y)), zb[k]);
+                x.fma2(make_float2(qa.z, qa.w), za[k + 1]);
+                x.fma2(AR::neg(make_float2(qb.z, qb.w)), zb[k + 1]);
+              }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+              if (k < n) {
+                x.fma2(q[k], za[k]);
+                x.fma2(AR::neg(q[n + k]), zb[k]);
+              }
+          }
           tt = x.out();
         } else {
           typename AR::A x;
