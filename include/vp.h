@@ -632,7 +632,12 @@ vp_status vp_batch_destroy(vp_batch* b);
 vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
 
 /* ------------------------------------------------------------ profiling */
-/* Kernels of the library, for launch counts and event timing. */
+/* Kernels of the library, for launch counts and event timing.  One id may
+ * cover a family of kernels: VP_K_DEIM the DEIM basis, indices, weights and
+ * snapshot columns; VP_K_DMD the DMD fit, coordinates, RBF interpolation and
+ * predicted potentials; VP_K_JACOBI_SYM the real symmetric Jacobi of both;
+ * VP_K_HYPER the per-interval window and operator work of vp_hyper_step;
+ * VP_K_INIT the complex-SVD start and the re-orthonormalisation factor. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
