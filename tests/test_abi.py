@@ -73,3 +73,17 @@ def test_kernel_names_match_the_binding(lib):
     lib.vp_kernel_name.argtypes = [ctypes.c_int32]
     assert [lib.vp_kernel_name(i).decode() for i in range(len(KERNELS))] == KERNELS
     assert lib.vp_kernel_name(len(KERNELS)) == b"unknown"
+
+
+def test_no_fallback_without_the_library_or_a_gpu(monkeypatch, tmp_path):
+    # the binding has no CPU path: a missing library and host tensors are errors
+    import torch
+
+    from paper_2201_05555_gb300 import binding
+
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB", str(tmp_path / "libvp.so"))
+    with pytest.raises(ImportError, match="missing"):
+        binding.load_library()
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        binding._ptr(torch.zeros(4, dtype=torch.float64), name="Q")
