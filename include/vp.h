@@ -80,13 +80,18 @@ typedef struct vp_step_opts {
   double tol;      /* fixed-point stop: |k_{m+1} - k_m|_F <= tol |k_{m+1}|_F (Sec. 6.1: 1e-9) */
   int32_t maxit;   /* iteration cap; exceeding it gives VP_ENOCONV */
   int32_t freeze_basis; /* 1: keep U fixed (global symplectic reduced basis, Sec. 3.1) */
-  /* Stagnation stop (the PIC force jumps at the nodes, so the fixed-point map
-   * is discontinuous and can end in a cycle of cell flips above tol): stop at
-   * iteration m >= 3 when the relative update r_m <= stall_floor and
-   * r_m >= stall_ratio min(r_{m-1}, r_{m-2}).  stall_floor = 0 disables it.
-   * Defaults 1e-3 and 0.5. */
-  double stall_floor;
-  double stall_ratio;
+  /* Two-cycle stop.  The PIC force is piecewise constant in each particle
+   * position (it jumps at the nodes), so the fixed-point map is discontinuous
+   * and the iteration can settle on a cycle of two iterates that differ by a
+   * few cell flips, above tol.  Stop at iteration m >= 2 when
+   *   |k_m - k_{m-2}|_F <= tol |k_m|_F                (back where it was),
+   *   |k_m - k_{m-2}|_F <= cycle_ratio |k_m - k_{m-1}|_F (not a converging
+   *       oscillation, which returns only to |1/c - 1| of its update), and
+   *   |k_m - k_{m-1}|_F <= cycle_max |k_m|_F           (a small cycle);
+   * k_m, a member of the cycle, is the result.  cycle_max = 0 disables it.
+   * Defaults 1e-3 and 1e-2. */
+  double cycle_max;
+  double cycle_ratio;
   /* Arithmetic of the N-row work (deposit, projection, Gamma zeta^H, Gram
    * matrices, affine row updates):
    * 0 = FP64;
@@ -191,7 +196,7 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
 /* a9. nsteps partitioned RK2 steps (Sec. 5, eqs. pRK_Z .. pRK_U_ktilde):
  * explicit midpoint + Cayley retraction for U, implicit midpoint (fixed point
  * from k = 0) for Z, in place on Q_dev (N x 2n) and Z_dev (2n x p).
- * opts NULL = {1e-9, 100, 0, 1e-3, 0.5, 0, 0, 0, NULL}.  trace_dev (nullable): (nsteps x p x 2)
+ * opts NULL = {1e-9, 100, 0, 1e-3, 1e-2, 0, 0, 0, NULL}.  trace_dev (nullable): (nsteps x p x 2)
  * electric energy and reduced Hamiltonian 1/2|V_r|^2 + E (eq.
  * nonlinear_hamiltonian) of the state entering each step, taken from the
  * step's first field evaluation (no extra work; with arith = 2 from an extra

@@ -16,11 +16,15 @@ update to k is below tol times the norm of k (Sec. 6.1, tol = 1e-9).
 
 The PIC force is piecewise constant in each particle position (the P1 hat
 gradients jump at the nodes), so the fixed-point map is discontinuous: the
-iteration can end in a cycle of cell flips above 1e-9, at a level that
-shrinks as N grows (3.5e-7 for N = 1e5, p = 64; 1.0e-5 for N = 1e4, p = 32).
-The iteration therefore also stops on stagnation: at iteration m >= 3 a
-relative update r_m <= stall_floor (1e-3) that is not below stall_ratio (0.5)
-times min(r_{m-1}, r_{m-2}), i.e. no halving over the last two iterations.
+iteration can settle on a cycle of two iterates that differ by a few cell
+flips, with a relative update above 1e-9 that never shrinks (3.5e-7 for
+N = 1e5, p = 64).  The iteration therefore also stops on such a two-cycle:
+at iteration m >= 2 when k_m is back where it was two iterations ago,
+|k_m - k_{m-2}| <= tol |k_m|, that return distance is at most cycle_ratio
+(1e-2) times the update |k_m - k_{m-1}| (an oscillating iteration that
+converges with factor -c returns only to |1/c - 1| of its update), and the
+update is at most cycle_max (1e-3) times |k_m| (a small cycle).  k_m is the
+result.  Any other non-convergence ends in NoConvergence at maxit.
 """
 from __future__ import annotations
 
@@ -194,13 +198,13 @@ def param_subsample(Z0: np.ndarray, p_max: int, tol: float = 0.0) -> np.ndarray:
 
 def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
               tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
-              retract=retraction, grad_fn=None, stall_floor: float = 1e-3,
-              stall_ratio: float = 0.5, k_init: np.ndarray | None = None,
+              retract=retraction, grad_fn=None, cycle_max: float = 1e-3,
+              cycle_ratio: float = 1e-2, k_init: np.ndarray | None = None,
               sub: np.ndarray | None = None, coeff_grad=None):
     """One step (U0, Z0) -> (U1, Z1).  Returns (U1, Z1, info).
 
     info: 'iters' (fixed-point evaluations), 'resid' (last relative update),
-    'stalled' (stopped on stagnation), 'U_half', 'k2', 'E0' (electric
+    'cycle' (stopped on a two-cycle), 'U_half', 'k2', 'E0' (electric
     energies at (U0, Z0); PIC gradient only), 'kh1' (basis velocity at the start).
     grad_fn: optional map R -> G replacing the PIC gradient (any Hamiltonian).
     k_init: initial guess of the fixed point (the paper leaves it unstated);
@@ -227,8 +231,8 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
     info["kh1"] = kh1
     info["U_half"] = U_half
     k = np.zeros_like(Z0) if k_init is None else np.array(k_init, dtype=np.float64, copy=True)
-    r_prev = [np.inf, np.inf]  # r_{m-1}, r_{m-2}
-    stalled = False
+    k_back = None  # k_{m-2}
+    cycle = False
     for it in range(1, maxit + 1):
         if coeff_grad is None:
             G = _gradient(U_half, Z0 + 0.5 * dt * k, g, grad_fn)
@@ -237,19 +241,19 @@ def prk2_step(U0: np.ndarray, Z0: np.ndarray, dt: float, g: pic.Grid,
             k_new = apply_J(coeff_grad(U_half, Z0 + 0.5 * dt * k))
         diff = np.linalg.norm(k_new - k)
         nk = np.linalg.norm(k_new)
-        k = k_new
+        ret = np.inf if k_back is None else np.linalg.norm(k_new - k_back)
+        k_back, k = k, k_new
         if diff <= tol * nk:
             break
-        r = diff / nk
-        if it >= 3 and r <= stall_floor and r >= stall_ratio * min(r_prev):
-            stalled = True
+        if (cycle_max > 0 and ret <= tol * nk and ret <= cycle_ratio * diff
+                and diff <= cycle_max * nk):
+            cycle = True
             break
-        r_prev = [r, r_prev[0]]
     else:
         raise NoConvergence(f"fixed point did not converge in {maxit} iterations")
     info["iters"] = it
     info["resid"] = diff / nk if nk > 0 else 0.0
-    info["stalled"] = stalled
+    info["cycle"] = cycle
     info["k2"] = k
     Z1 = Z0 + dt * k
     if freeze_basis:

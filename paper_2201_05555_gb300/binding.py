@@ -35,8 +35,8 @@ class Grid(C.Structure):
 
 
 class StepOpts(C.Structure):
-    _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32), ("stall_floor", _D),
-                ("stall_ratio", _D), ("arith", _I32), ("reortho", _I32), ("nsub", _I32),
+    _fields_ = [("tol", _D), ("maxit", _I32), ("freeze_basis", _I32), ("cycle_max", _D),
+                ("cycle_ratio", _D), ("arith", _I32), ("reortho", _I32), ("nsub", _I32),
                 ("sub_idx", _P)]
 
 
@@ -323,8 +323,8 @@ class Context:
 
     def basis_update(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int,
                      tol: float = 1e-9, maxit: int = 100, freeze_basis: bool = False,
-                     trace: bool = True, iters: bool = True, stall_floor: float = 1e-3,
-                     stall_ratio: float = 0.5, arith: int = 0,
+                     trace: bool = True, iters: bool = True, cycle_max: float = 1e-3,
+                     cycle_ratio: float = 1e-2, arith: int = 0,
                      kstate: torch.Tensor | None = None, reortho: bool = False,
                      sub: torch.Tensor | None = None):
         """nsteps partitioned RK2 steps in place on Q (N x 2n) and Z (2n x p).
@@ -334,7 +334,7 @@ class Context:
         p = Z.shape[1]
         tr = self._empty(max(nsteps, 1), p, 2) if trace else None
         it = self._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
-        opts = StepOpts(tol, maxit, int(freeze_basis), stall_floor, stall_ratio, int(arith),
+        opts = StepOpts(tol, maxit, int(freeze_basis), cycle_max, cycle_ratio, int(arith),
                         int(reortho), 0 if sub is None else sub.numel(),
                         _ptr(sub, torch.int32, "sub"))
         self._check(self.lib.vp_basis_update(self.h, C.byref(grid), N, n2 // 2, p,
@@ -757,13 +757,13 @@ class Hyper:
 
     def step(self, Q: torch.Tensor, Z: torch.Tensor, dt: float, nsteps: int, tol: float = 1e-9,
              maxit: int = 100, arith: int = 1, reortho: bool = False, trace: bool = True,
-             iters: bool = True, kstate: torch.Tensor | None = None, stall_floor: float = 1e-3,
-             stall_ratio: float = 0.5):
+             iters: bool = True, kstate: torch.Tensor | None = None, cycle_max: float = 1e-3,
+             cycle_ratio: float = 1e-2):
         """nsteps intervals in place on Q (N x 2n) and Z (2n x p); returns (trace, iters)."""
         ctx = self.ctx
         tr = ctx._empty(max(nsteps, 1), self.p, 2) if trace else None
         it = ctx._empty(max(nsteps, 1), dtype=torch.int32) if iters else None
-        opts = StepOpts(tol, maxit, 0, stall_floor, stall_ratio, int(arith), int(reortho), 0, None)
+        opts = StepOpts(tol, maxit, 0, cycle_max, cycle_ratio, int(arith), int(reortho), 0, None)
         ctx._check(ctx.lib.vp_hyper_step(self.h, _ptr(Q, name="Q"), _ptr(Z, name="Z"), dt, nsteps,
                                          C.byref(opts), _ptr(tr), _ptr(it, torch.int32),
                                          _ptr(kstate, name="kstate"), ctx._stream()), "hyper_step")

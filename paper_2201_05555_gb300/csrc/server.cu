@@ -145,7 +145,7 @@ void vp_server::run(Job* j, Slot* sl) {
     cudaMemsetAsync(K, 0, sizeof(double) * n2 * p, st);
     const double L = 2.0 * 3.141592653589793 / family_k(q.family);
     vp_grid grid{q.Nx, L, -L / (double)N, L / (double)N, 1.0};
-    vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, q.arith, q.arith == 2 ? 1 : 0};
+    vp_step_opts o{1e-9, 100, 0, 1e-3, 1e-2, q.arith, q.arith == 2 ? 1 : 0};
     const int chunk = 16;
     for (int s0 = 0; s0 < q.nsteps && s == VP_OK; s0 += chunk) {
       {

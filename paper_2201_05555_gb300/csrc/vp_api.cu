@@ -94,9 +94,9 @@ vp_status check_n(vp_ctx* ctx, int32_t n, int64_t N) {
 // Workspace of the reduced-model calls.
 struct RedWS {
   unsigned long long* counts;
-  double *F, *Efield, *part, *gX, *k, *Ze, *Z0, *Z1, *GVraw, *aux;
+  double *F, *Efield, *part, *gX, *k, *kp, *Ze, *Z0, *Z1, *GVraw, *aux;
   double2 *grams, *cay, *C, *tmp;
-  int* flags;  // [0] done, [1] iters
+  int* flags;  // [0] done, [1] iters, [2] ticket, [3] stopped on a two-cycle
   double* rows[5];
   float2 *Q2a, *Q2b;  // row-format shadows of Q0 and Q_half (float2 or float)
   uint16_t* jcell;    // cell index per (particle, sample), N x p
@@ -146,8 +146,8 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
                                    std::max<size_t>((size_t)gg * 12 * nn * 2, (size_t)gg * n2 * n2));
   size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
   return arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
-         arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)n2 * n2, 8) +
-         arena_bytes((size_t)n2 * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
+         arena_bytes((size_t)n2 * p, 8) * 6 + arena_bytes((size_t)n2 * n2, 8) +
+         arena_bytes((size_t)(n2 + 3) * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
          arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
@@ -174,11 +174,12 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.part = a.take<double>(part_d);
   w.gX = a.take<double>((size_t)n2 * p);
   w.k = a.take<double>((size_t)n2 * p);
+  w.kp = a.take<double>((size_t)n2 * p);
   w.Ze = a.take<double>((size_t)n2 * p);
   w.Z0 = a.take<double>((size_t)n2 * p);
   w.Z1 = a.take<double>((size_t)n2 * p);
   w.GVraw = a.take<double>((size_t)n2 * n2);
-  w.aux = a.take<double>((size_t)n2 * p + 64);
+  w.aux = a.take<double>((size_t)(n2 + 3) * p + 64);
   w.grams = a.take<double2>(12 * nn);
   w.cay = a.take<double2>(4 * nn);
   w.C = a.take<double2>(4 * nn);
@@ -528,8 +529,7 @@ vp_status DFStep::pre(double* trace_step) {
     VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
     VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
   }
-  VP_CUDA(cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), st));
-  VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
+  VP_CUDA(cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
   LpArgs a = D.base();  // Ze in row format for the first round's deposit
   a.dsrc = w.Ze;
   a.v0 = w.Z2;
@@ -550,8 +550,8 @@ vp_status DFStep::rounds(int count) {
     D.field(Qm, w.Ze, w.flags, true);
     D.project(Qm, w.flags);
     VP_K(VP_K_COEFF_UPDATE,
-         coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit, o.stall_floor,
-                      o.stall_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st, w.part,
+         coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.kp, w.Ze, dt, o.tol, o.maxit,
+                      o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st, w.part,
                       w.gx_proj, w.Z2, w.Zh2, R.g.inv_h, o.arith));
   }
   return VP_OK;
@@ -746,8 +746,8 @@ vp_status hyper_interval(vp_hyper* h, Red& R, DFStep& S, double* trace_step, int
       for (int k = 0; k < rr; ++k) {
         VP_K(VP_K_DEIM_ROUND, deim_round(h->g, n, p, h->d, h->Qd, w.Ze, h->F, h->c, w.gX, w.flags, st));
         VP_K(VP_K_COEFF_UPDATE,
-             coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, S.dt, o.tol, o.maxit, o.stall_floor,
-                          o.stall_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st));
+             coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kp, w.Ze, S.dt, o.tol, o.maxit,
+                          o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st));
       }
     } else {
       VP_TRY(S.rounds(rr));
@@ -903,7 +903,7 @@ vp_status vp_hyper_step(vp_hyper* h, double* Q, double* Z, double dt, int32_t ns
   VP_ENTER();
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 1, 0, 0, nullptr};
+  vp_step_opts o{1e-9, 100, 0, 1e-3, 1e-2, 1, 0, 0, nullptr};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
   if (o.arith < 1 || o.arith > 2)
@@ -1810,7 +1810,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
-  vp_step_opts o{1e-9, 100, 0, 1e-3, 0.5, 0, 0, 0, nullptr};
+  vp_step_opts o{1e-9, 100, 0, 1e-3, 1e-2, 0, 0, 0, nullptr};
   if (opts) o = *opts;
   if (!(o.tol >= 0.0) || o.maxit < 1) return vp_fail(ctx, VP_EINVAL, "tol < 0 or maxit < 1");
   if (o.arith < 0 || o.arith > 2) return vp_fail(ctx, VP_EINVAL, "arith must be 0, 1 or 2");
@@ -1858,8 +1858,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
       VP_CUDA(cudaMemcpyAsync(w.Ze, Z, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
       VP_CUDA(cudaMemsetAsync(w.k, 0, sizeof(double) * zsz, st));
     }
-    VP_CUDA(cudaMemsetAsync(w.flags, 0, 3 * sizeof(int), st));
-    VP_CUDA(cudaMemsetAsync(w.aux, 0, 2 * sizeof(double), st));
+    VP_CUDA(cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
     int done_h = 0, total = 0;
     while (!done_h) {
       for (int r = 0; r < round && total < o.maxit; ++r, ++total) {
@@ -1867,8 +1866,8 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
         VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
                                    w.part, w.gx_proj, w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
-        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.Ze, dt, o.tol, o.maxit,
-                                             o.stall_floor, o.stall_ratio, w.aux, w.flags,
+        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kp, w.Ze, dt, o.tol,
+                                             o.maxit, o.cycle_max, o.cycle_ratio, w.aux, w.flags,
                                              w.flags + 1, ctx->d_status, st));
       }
       VP_CUDA(cudaMemcpyAsync(ctx->h_pinned + 1, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));

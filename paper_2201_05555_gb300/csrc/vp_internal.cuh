@@ -343,12 +343,13 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
 // gX: the projection (2n x p), or nullptr with `part` (nparts x 2n x p block
-// partials of it, summed here in block order).  Z2/Zh2 (nullable): the new
-// evaluation point Ze and Ze / h in the row format `zmode` (1 double-float,
-// 2 FP32) for the next deposit.
+// partials of it, summed here in block order).  kp (2n x p): the iterate two
+// iterations back (no initial value needed).  partials: 3 p doubles.
+// Z2/Zh2 (nullable): the new evaluation point Ze and Ze / h in the row format
+// `zmode` (1 double-float, 2 FP32) for the next deposit.
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
-                  double* Ze, double dt, double tol, int maxit, double stall_floor,
-                  double stall_ratio, double* rstate, int* done, int* iters, int* status,
+                  double* kp, double* Ze, double dt, double tol, int maxit, double cycle_max,
+                  double cycle_ratio, double* partials, int* done, int* iters, int* status,
                   cudaStream_t st, const double* part = nullptr, int nparts = 0,
                   void* Z2 = nullptr, void* Zh2 = nullptr, double inv_h = 0.0, int zmode = 0);
 void axpy(int64_t m, double a, const double* x, const double* y, double* out, cudaStream_t st);

@@ -227,3 +227,114 @@ def test_prk2_with_full_subsample_is_unchanged():
     a = reduced.prk2_step(U, Z, 0.05, g)
     b = reduced.prk2_step(U, Z, 0.05, g, sub=np.arange(7))
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------- fixed-point stopping rule
+def _orthosymplectic(N, n, seed):
+    rng = np.random.default_rng(seed)
+    Qc = rng.standard_normal((N, n)) + 1j * rng.standard_normal((N, n))
+    Qc, _ = np.linalg.qr(Qc)
+    return csvd.U_from_Q(Qc)
+
+
+def test_fixed_point_contraction_07_runs_to_tol():
+    """H = 1/2 R^T A R with A = U B U^T and B = diag(b, -b) (a saddle):
+    with the basis frozen the fixed-point map is affine, k -> J B (Z + dt/2 k),
+    and its linear part dt/2 J B has the real eigenvalues +0.7 and -0.7.  The
+    iteration converges linearly with factor 0.7, monotone along one direction
+    and oscillating along the other; the two-cycle test must not stop it, so
+    it runs to the paper's relative update 1e-9 and reaches the exact solution
+    of (I - dt/2 J B) k = J B Z to about 0.7 / 0.3 of that."""
+    N, n, p, dt, c = 40, 2, 3, 0.1, 0.7
+    U = _orthosymplectic(N, n, 3)
+    b = 2 * c / dt
+    B = np.diag(np.r_[np.full(n, b), np.full(n, -b)])
+    A = U @ B @ U.T
+    Z0 = np.random.default_rng(4).standard_normal((2 * n, p))
+    g = pic.make_grid(N, 8, 1.0)
+    Jn = reduced.J(2 * n)
+    eig = np.sort(np.linalg.eigvals(0.5 * dt * Jn @ B).real)
+    np.testing.assert_allclose(eig, [-c, -c, c, c], atol=1e-12)
+    U1, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, grad_fn=lambda R: A @ R)
+    assert not info["cycle"]
+    assert info["resid"] <= 1e-9
+    assert info["iters"] > 50  # 0.7^m falls to ~1e-9 only after ~60 iterations
+    k_exact = np.linalg.solve(np.eye(2 * n) - 0.5 * dt * Jn @ B, Jn @ B @ Z0)
+    assert np.linalg.norm(info["k2"] - k_exact) <= 3e-9 * np.linalg.norm(k_exact)
+
+
+def _flip_hamiltonian(U, K, eps, theta):
+    """G(R) = U h(U^T R) with h(z) = (K + eps sign(z_2 - theta)) e_1 on the
+    first coefficient pair: a force that jumps across z_2 = theta, like the P1
+    force at a node.  With the basis frozen, k = J h(Z + dt/2 k) moves only
+    z_2, by -(K + eps s) dt/2."""
+    def grad_fn(R):
+        z = U.T @ R
+        h = np.zeros_like(z)
+        h[0] = K + eps * np.where(z[1] - theta >= 0, 1.0, -1.0)
+        return U @ h
+    return grad_fn
+
+
+def test_fixed_point_stops_on_constructed_two_cycle():
+    """Z_2 - theta = dt/2 K + delta with |delta| < dt/2 eps: from k = 0 the
+    iterates are k_1 = -(K + eps) e_2, k_2 = -(K - eps) e_2, k_3 = k_1, ...
+    an exact two-cycle of relative amplitude 2 eps / K.  The rule stops at
+    m = 3 (k_3 = k_1), not before (k_2 is far from k_0 = 0), on k_3."""
+    N, dt, K, eps = 20, 0.1, 1.0, 1e-6
+    U = _orthosymplectic(N, 1, 7)
+    theta, delta = 0.3, 0.25 * 0.5 * dt * eps
+    Z0 = np.array([[0.2], [theta + 0.5 * dt * K + delta]])
+    g = pic.make_grid(N, 8, 1.0)
+    _, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True,
+                                    grad_fn=_flip_hamiltonian(U, K, eps, theta))
+    assert info["cycle"] and info["iters"] == 3
+    np.testing.assert_allclose(info["k2"], [[0.0], [-(K + eps)]], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(info["resid"], 2 * eps / (K + eps), rtol=1e-8)
+    np.testing.assert_allclose(Z1, Z0 + dt * info["k2"], rtol=0, atol=0)
+
+
+def test_fixed_point_large_cycle_is_not_accepted():
+    """The same construction with eps / K = 0.1: a cycle of relative amplitude
+    0.2 > cycle_max = 1e-3 is no solution, so the iteration runs out."""
+    N, dt, K, eps = 20, 0.1, 1.0, 0.1
+    U = _orthosymplectic(N, 1, 7)
+    theta, delta = 0.3, 0.25 * 0.5 * dt * eps
+    Z0 = np.array([[0.2], [theta + 0.5 * dt * K + delta]])
+    g = pic.make_grid(N, 8, 1.0)
+    with pytest.raises(reduced.NoConvergence):
+        reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, maxit=30,
+                          grad_fn=_flip_hamiltonian(U, K, eps, theta))
+
+
+def test_fixed_point_two_cycle_on_tiny_pic():
+    """A tiny PIC case (N = 64, p = 4, Nx = 8, dt = 0.5, basis frozen) whose
+    iteration settles on a cycle of cell flips with relative amplitude
+    ~3.5e-3.  With cycle_max = 1e-3 that cycle is refused (NoConvergence);
+    with cycle_max = 1e-2 the iteration stops on it, and the result is a
+    member of a true two-cycle of the fixed-point map F (checked by applying
+    F here): F(F(k)) = k to the tolerance while F(k) differs from k by the
+    cycle's amplitude."""
+    N, p, n, Nx, L, dt = 64, 4, 2, 8, 4 * np.pi, 0.5
+    g = pic.make_grid(N, Nx, L)
+    X0 = W.random_positions(p, N, L, seed=4)
+    V0 = W.random_velocities(p, N, seed=1004)
+    U0, Z0, _ = csvd.csvd_init(X0, V0, n)
+    with pytest.raises(reduced.NoConvergence):
+        reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60)
+    _, _, info = reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60, cycle_max=1e-2)
+    assert info["cycle"]
+    k = info["k2"]
+
+    def F(k):
+        return reduced.apply_J(U0.T @ reduced.full_gradient(U0, Z0 + 0.5 * dt * k, g)[0])
+
+    k1 = F(k)
+    k2 = F(k1)
+    nk = np.linalg.norm(k)
+    assert np.linalg.norm(k2 - k) <= 1e-9 * nk
+    assert 1e-3 < np.linalg.norm(k1 - k) / nk < 1e-2
+    # the two members place some particle in different cells
+    cells = [np.floor(np.mod(reduced.reconstruct(U0, Z0 + 0.5 * dt * kk)[0], L) / g.h)
+             for kk in (k, k1)]
+    assert np.any(cells[0] != cells[1])
