@@ -674,7 +674,7 @@ def config_dict(world):
             "loading": "seeded per sample", "parallelism": f"replicas x{world}",
             "arithmetic": ("FP64 storage; particle loops in double-float (Dot2), small dense "
                            "and reductions FP64" if ARITH == 1 else "FP64"),
-            "fixed_point": "tol 1e-9, or a two-cycle (|k_m - k_m-2| <= 1e-9 |k_m|, <= 1e-2 |k_m - k_m-1|, amplitude <= 1e-3), warm start from k2",
+            "fixed_point": "tol 1e-9, or a q-cycle, q in 2..4 (|k_m - k_m-q| <= 1e-9 |k_m| and <= 1e-2 |k_m - k_m-1|, amplitude <= 1e-3), warm start from k2",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 

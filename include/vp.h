@@ -77,19 +77,26 @@ typedef struct vp_grid {
 
 /* Options of the partitioned RK2 step (Sec. 5). */
 typedef struct vp_step_opts {
-  double tol;      /* fixed-point stop: |k_{m+1} - k_m|_F <= tol |k_{m+1}|_F (Sec. 6.1: 1e-9) */
+  double tol;      /* fixed-point stop: |k_{m+1} - k_m|_F <= tol |k_{m+1}|_F (Sec. 6.1: 1e-9).
+                    * With arith = 2 (FP32 rows) a tol below 1e-6 is raised to 1e-6: the
+                    * map is then evaluated in FP32, whose updates stop shrinking near the
+                    * FP32 rounding level (~1e-7 relative). */
   int32_t maxit;   /* iteration cap; exceeding it gives VP_ENOCONV */
   int32_t freeze_basis; /* 1: keep U fixed (global symplectic reduced basis, Sec. 3.1) */
-  /* Two-cycle stop.  The PIC force is piecewise constant in each particle
-   * position (it jumps at the nodes), so the fixed-point map is discontinuous
-   * and the iteration can settle on a cycle of two iterates that differ by a
-   * few cell flips, above tol.  Stop at iteration m >= 2 when
-   *   |k_m - k_{m-2}|_F <= tol |k_m|_F                (back where it was),
-   *   |k_m - k_{m-2}|_F <= cycle_ratio |k_m - k_{m-1}|_F (not a converging
-   *       oscillation, which returns only to |1/c - 1| of its update), and
-   *   |k_m - k_{m-1}|_F <= cycle_max |k_m|_F           (a small cycle);
-   * k_m, a member of the cycle, is the result.  cycle_max = 0 disables it.
-   * Defaults 1e-3 and 1e-2. */
+  /* Stops for a discontinuous map.  The PIC force is piecewise constant in
+   * each particle position (it jumps at the nodes), so the fixed-point map is
+   * discontinuous and its updates need not fall to tol.  While the relative
+   * update r_m = |k_m - k_{m-1}|_F / |k_m|_F is at most cycle_max, the
+   * iteration also stops at iteration m
+   * - on a short cycle, for the shortest period q in 2..4 with q <= m and
+   *     |k_m - k_{m-q}|_F <= tol |k_m|_F                (back where it was),
+   *     |k_m - k_{m-q}|_F <= cycle_ratio |k_m - k_{m-1}|_F (not a converging
+   *     iteration, which returns only to a sizeable fraction of its update);
+   * - on a plateau, when m > 8 and r_m >= r_{m-8} / 2: the update has not
+   *   halved over 8 iterations (iterates wandering among configurations that
+   *   differ by a few cell flips; a linear contraction triggers this only
+   *   with a factor above 0.917).
+   * k_m is the result.  cycle_max = 0 disables both.  Defaults 1e-3, 1e-2. */
   double cycle_max;
   double cycle_ratio;
   /* Arithmetic of the N-row work (deposit, projection, Gamma zeta^H, Gram
@@ -443,10 +450,14 @@ vp_status vp_hyper_destroy(vp_hyper* h);
  * the library until the process exits.  Nothing is allocated: no cudaMalloc,
  * cudaFree or allocating library routine.
  * - Limit: p * Nx <= 131072; larger requests return VP_EUNSUPPORTED and
- *   launch nothing.  Invalid arguments return VP_EINVAL.
- * - Works on the caller's current device.  The first call on each device
- *   looks up the array's device address (cudaGetSymbolAddress); make that
- *   first call before any stream capture.
+ *   launch nothing.
+ * - Works on the caller's current device, in its primary context (the one
+ *   the CUDA runtime uses).  The first call on each device looks up the
+ *   array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ * - Invalid arguments (a non-finite L, mp, Mq or background included) return
+ *   VP_EINVAL; a failed launch returns VP_ECUDA for this call's own launches
+ *   only.
  * - All calls on a device share the array.  Each call clears the part it uses
  *   before depositing, but calls whose work overlaps on the GPU (two streams,
  *   two host threads) race on it and give wrong results: serialise them. */
@@ -642,7 +653,9 @@ vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
  * snapshot columns; VP_K_DMD the DMD fit, coordinates, RBF interpolation and
  * predicted potentials; VP_K_JACOBI_SYM the real symmetric Jacobi of both;
  * VP_K_HYPER the per-interval window and operator work of vp_hyper_step;
- * VP_K_INIT the complex-SVD start and the re-orthonormalisation factor. */
+ * VP_K_INIT the complex-SVD start and the re-orthonormalisation factor;
+ * VP_K_DEPOSIT_DIAG the double-float deposit of the FP64-accurate energy
+ * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
@@ -650,7 +663,7 @@ typedef enum vp_kernel {
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
-  VP_K_JACOBI_SYM, VP_K_COUNT
+  VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

@@ -139,7 +139,8 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_small_basis_coeffs", "k_small_cayley", "k_small_tangent", "k_coeff_update",
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
-           "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd", "k_jacobi_sym"]
+           "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd", "k_jacobi_sym",
+           "k_deposit_lp_diag"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -612,7 +613,13 @@ def deposit_cic_noalloc(grid: Grid, X: torch.Tensor, rho: torch.Tensor) -> torch
     may not allocate device memory (no context; rho must be given).  Runs on
     X's device and the current torch stream of that device."""
     lib = load_library()
+    if X.dim() != 2:
+        raise ValueError(f"X must be p x N, got shape {tuple(X.shape)}")
     p, N = X.shape
+    if tuple(rho.shape) != (p, grid.Nx):
+        raise ValueError(f"rho must be p x Nx = {(p, grid.Nx)}, got {tuple(rho.shape)}")
+    if rho.device != X.device:
+        raise ValueError(f"rho is on {rho.device}, X on {X.device}")
     with torch.cuda.device(X.device):
         st = C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream)
         s = lib.vp_deposit_cic_noalloc(C.byref(grid), N, p, _ptr(X, name="X"), N,
@@ -815,7 +822,7 @@ class Batch:
                                _ptr(it, torch.int32, "iters"))
         self._arr = arr
         ro = (arith == 2) if reortho is None else reortho
-        opts = StepOpts(tol, maxit, 0, 1e-3, 0.5, arith, int(ro), 0, None)
+        opts = StepOpts(tol, maxit, 0, 1e-3, 1e-2, arith, int(ro), 0, None)
         h = _P()
         s = self.lib.vp_batch_create(C.byref(h), device, C.cast(arr, _P), len(instances),
                                      C.byref(opts), rounds_first, rounds_more,

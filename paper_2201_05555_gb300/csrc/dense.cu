@@ -424,24 +424,31 @@ __device__ double block_sum2(double v, double* red) {
 // Fixed-point update of the coefficient stage, spread over blocks of
 // sample columns: block b owns columns [b CW, (b+1) CW) and writes
 // k_new = J (gX + G_V Ze) and Ze = Z0 + dt/2 k_new for them (a column depends
-// only on its own column of Ze).  kp holds the iterate two iterations back.
-// Each block leaves its sums |k_new - k|^2, |k_new|^2, |k_new - kp|^2 in
-// `partials`; the last block to finish (ticket counter) adds them in block
-// order (deterministic), counts the iteration and decides: converged
-// (relative update <= tol), on a two-cycle (see vp_step_opts), non-finite
+// only on its own column of Ze).  kr is a ring of the iterates two to
+// CU_QMAX iterations back (iterate j in slot j mod (CU_QMAX - 1)).  Each
+// block leaves its sums |k_new - k|^2, |k_new|^2 and |k_new - k_{m-q}|^2
+// (q = 2 .. CU_QMAX) in `partials`; the last block to finish (ticket counter)
+// adds them in block order (deterministic), counts the iteration and decides:
+// converged (relative update <= tol), on a q-cycle or a plateau (see
+// vp_step_opts; rhist keeps the last CU_PW relative updates), non-finite
 // (VP_ENUMERIC) or out of iterations (VP_ENOCONV).  Every later launch of the
 // step returns at once through `done`.
 #define CU_CW 1
+#define CU_QMAX 4                 // longest cycle the stop rule recognises
+#define CU_NP (2 + CU_QMAX - 1)   // partial sums per block
+#define CU_PW 8                   // plateau window (iterations)
 __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
                                const double* __restrict__ GVraw, const double* __restrict__ Z0,
-                               double* k, double* kp, double* Ze, double dt, double tol,
+                               double* k, double* kr, double* Ze, double dt, double tol,
                                int maxit, double cycle_max, double cycle_ratio, int* done,
-                               int* iters, int* ticket, double* partials, int* status,
+                               int* iters, int* ticket, double* partials, double* rhist,
+                               int* status,
                                const double* __restrict__ part, int nparts, void* Z2, void* Zh2,
                                double inv_h, int zmode) {
   if (*done) return;
-  // iteration number of this launch; kp is defined from the second on
-  const bool have_kp = *iters >= 1;
+  // iteration number of this launch; iterate m - q exists for q <= m
+  const int m_it = *iters + 1;
+  const int64_t zsz = (int64_t)2 * n * p;
   extern __shared__ double cu_sm[];
   __shared__ double red[32];
   __shared__ int last;
@@ -495,7 +502,9 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
     }
   }
   __syncthreads();
-  double d2 = 0.0, k2 = 0.0, c2 = 0.0;
+  double d2 = 0.0, k2 = 0.0, c2[CU_QMAX - 1];
+#pragma unroll
+  for (int q = 0; q < CU_QMAX - 1; ++q) c2[q] = 0.0;
   // k_new[r] = g[n + r] (r < n), k_new[n + r] = -g[r], g = gX + G_V Ze
   for (int e = threadIdx.x; e < n2 * cw; e += blockDim.x) {
     int r = e / cw, c = e - r * cw;
@@ -509,22 +518,28 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
     double dk = kn - kold;
     d2 = fma(dk, dk, d2);
     k2 = fma(kn, kn, k2);
-    if (have_kp) {
-      const double dc = kn - kp[o];
-      c2 = fma(dc, dc, c2);
-    }
-    kp[o] = kold;
+#pragma unroll
+    for (int q = 2; q <= CU_QMAX; ++q)
+      if (q <= m_it) {
+        const double dc = kn - kr[(int64_t)((m_it - q) % (CU_QMAX - 1)) * zsz + o];
+        c2[q - 2] = fma(dc, dc, c2[q - 2]);
+      }
+    // iterate m - 1 takes the slot of iterate m - CU_QMAX, read just above
+    kr[(int64_t)((m_it - 1) % (CU_QMAX - 1)) * zsz + o] = kold;
     k[o] = kn;
     const double ze = fma(0.5 * dt, kn, Z0[o]);
     Ze[o] = ze;
     if (Z2) store_lp(Z2, o, ze, zmode);
     if (Zh2) store_lp(Zh2, o, ze * inv_h, zmode);
   }
-  double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red), C2 = block_sum2(c2, red);
+  double D2 = block_sum2(d2, red), K2 = block_sum2(k2, red), C2[CU_QMAX - 1];
+#pragma unroll
+  for (int q = 0; q < CU_QMAX - 1; ++q) C2[q] = block_sum2(c2[q], red);
   if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x] = D2;
-    partials[3 * blockIdx.x + 1] = K2;
-    partials[3 * blockIdx.x + 2] = C2;
+    partials[CU_NP * blockIdx.x] = D2;
+    partials[CU_NP * blockIdx.x + 1] = K2;
+#pragma unroll
+    for (int q = 0; q < CU_QMAX - 1; ++q) partials[CU_NP * blockIdx.x + 2 + q] = C2[q];
     __threadfence();
     last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
   }
@@ -535,34 +550,50 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
   // adds the lanes by a fixed butterfly (its order does not depend on timing)
   D2 = 0.0;
   K2 = 0.0;
-  C2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < CU_QMAX - 1; ++q) C2[q] = 0.0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-    D2 += __ldcg(partials + 3 * b);
-    K2 += __ldcg(partials + 3 * b + 1);
-    C2 += __ldcg(partials + 3 * b + 2);
+    D2 += __ldcg(partials + CU_NP * b);
+    K2 += __ldcg(partials + CU_NP * b + 1);
+#pragma unroll
+    for (int q = 0; q < CU_QMAX - 1; ++q) C2[q] += __ldcg(partials + CU_NP * b + 2 + q);
   }
   for (int o = 16; o > 0; o >>= 1) {
     D2 += __shfl_xor_sync(0xffffffffu, D2, o);
     K2 += __shfl_xor_sync(0xffffffffu, K2, o);
-    C2 += __shfl_xor_sync(0xffffffffu, C2, o);
+#pragma unroll
+    for (int q = 0; q < CU_QMAX - 1; ++q) C2[q] += __shfl_xor_sync(0xffffffffu, C2[q], o);
   }
   if (threadIdx.x != 0) return;
   *ticket = 0;
   int it = *iters + 1;
   *iters = it;
-  const double diff = sqrt(D2), nk = sqrt(K2), ret = sqrt(C2);
+  const double diff = sqrt(D2), nk = sqrt(K2);
   bool conv = diff <= tol * nk;
-  // two-cycle: the iterate is back where it was two iterations ago (to tol),
-  // the return distance is small against the update (an oscillating but
-  // converging iteration returns only to |1/c - 1| of its update), and the
-  // cycle's relative amplitude is at most cycle_max
-  const bool cycle = it >= 2 && cycle_max > 0.0 && ret <= tol * nk &&
-                     ret <= cycle_ratio * diff && diff <= cycle_max * nk;
-  if (!isfinite(D2) || !isfinite(K2) || !isfinite(C2)) {
+  // q-cycle: the iterate is back where it was q iterations ago (to tol), the
+  // return distance is small against the update (a converging iteration
+  // returns only to a sizeable fraction of its update), and the cycle's
+  // relative amplitude is at most cycle_max; the shortest such q
+  int cycle = 0;
+  bool finite = isfinite(D2) && isfinite(K2);
+  for (int q = 2; q <= CU_QMAX; ++q) {
+    const double ret = sqrt(C2[q - 2]);
+    finite = finite && isfinite(C2[q - 2]);
+    if (!cycle && q <= it && cycle_max > 0.0 && ret <= tol * nk && ret <= cycle_ratio * diff &&
+        diff <= cycle_max * nk)
+      cycle = q;
+  }
+  // plateau: the relative update has not halved over CU_PW iterations
+  // (r_m >= r_{m-CU_PW} / 2; r_j lives in rhist[j % CU_PW])
+  const double r = nk > 0.0 ? diff / nk : 0.0;
+  const bool plateau = !conv && !cycle && cycle_max > 0.0 && r <= cycle_max && it > CU_PW &&
+                       r >= 0.5 * rhist[it % CU_PW];
+  rhist[it % CU_PW] = r;
+  if (!finite) {
     vp_set_status(status, VP_ENUMERIC);
     *done = 1;
-  } else if (conv || cycle) {
-    if (cycle) done[3] = 1;
+  } else if (conv || cycle || plateau) {
+    done[3] = conv ? 0 : (cycle ? cycle : 1);
     *done = 1;
   } else if (it >= maxit) {
     vp_set_status(status, VP_ENOCONV);
@@ -571,18 +602,20 @@ __global__ void k_coeff_update(int n, int p, const double* __restrict__ gX,
 }
 
 // flags: [0] done, [1] iterations, [2] ticket (zero between launches),
-// [3] 1 when the iteration stopped on a two-cycle; kp: 2n x p, the iterate
-// two iterations back; partials: 3 doubles per block (p blocks).
+// [3] how it stopped: 0 converged, 1 plateau, q >= 2 a q-cycle;
+// kr: (CU_QMAX - 1) x 2n x p ring of earlier iterates; partials: CU_NP
+// doubles per block (p blocks), then the CU_PW relative updates.
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
-                  double* kp, double* Ze, double dt, double tol, int maxit, double cycle_max,
+                  double* kr, double* Ze, double dt, double tol, int maxit, double cycle_max,
                   double cycle_ratio, double* partials, int* done, int* iters, int* status,
                   cudaStream_t st, const double* part, int nparts, void* Z2, void* Zh2,
                   double inv_h, int zmode) {
   const int nb = (p + CU_CW - 1) / CU_CW;
   // GV, Zs, Gs and the slice sums (at most max(blockDim, 2n CU_CW) of them)
   size_t smem = sizeof(double) * (4 * n * n + 4 * (size_t)n * CU_CW + 256 + 2 * (size_t)n * CU_CW);
-  k_coeff_update<<<nb, 256, smem, st>>>(n, p, gX, GVraw, Z0, k, kp, Ze, dt, tol, maxit, cycle_max,
-                                        cycle_ratio, done, iters, done + 2, partials, status, part,
+  k_coeff_update<<<nb, 256, smem, st>>>(n, p, gX, GVraw, Z0, k, kr, Ze, dt, tol, maxit, cycle_max,
+                                        cycle_ratio, done, iters, done + 2, partials,
+                                        partials + (size_t)CU_NP * nb, status, part,
                                         nparts, Z2, Zh2, inv_h, zmode);
 }
 

@@ -11,6 +11,7 @@
 #include "vp_internal.cuh"
 
 #include <atomic>
+#include <cmath>
 
 // p * Nx must not exceed this many counts (2^17 int64 = 1 MiB).
 #define VP_NOALLOC_MAX_COUNTS 131072
@@ -21,7 +22,10 @@ static __device__ __align__(256) unsigned long long g_noalloc_counts[VP_NOALLOC_
 namespace {
 // Device address of g_noalloc_counts on each device, looked up once with
 // that device current.  In host code the symbol name itself is only a
-// host-side stand-in and must never be handed to a kernel.
+// host-side stand-in and must never be handed to a kernel.  The address is
+// that of the device's primary context (the one the CUDA runtime uses); a
+// caller that makes another context current with the driver API must not use
+// this entry point.
 std::atomic<unsigned long long*> g_counts_addr[VP_NOALLOC_MAX_DEVICES];
 std::atomic<int> g_sms[VP_NOALLOC_MAX_DEVICES];
 
@@ -52,7 +56,11 @@ extern "C" vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int3
                                             const double* X_dev, int64_t ldx, double* rho_dev,
                                             void* stream) {
   if (!grid || !X_dev || !rho_dev || ldx < N) return VP_EINVAL;
-  if (grid->Nx < 3 || grid->Nx > VP_MAX_NX || !(grid->L > 0.0) || !(grid->mp > 0.0))
+  // the grid checks of vp_deposit_cic: an infinite L or mp, or a non-finite
+  // Mq or background, would give a silently wrong rho
+  if (grid->Nx < 3 || grid->Nx > VP_MAX_NX || !(grid->L > 0.0) || !std::isfinite(grid->L) ||
+      !(grid->mp > 0.0) || !std::isfinite(grid->mp) || !std::isfinite(grid->Mq) ||
+      !std::isfinite(grid->background))
     return VP_EINVAL;
   if (N < 1 || N >= (int64_t(1) << 31) || p < 1 || p > 65535) return VP_EINVAL;
   if ((int64_t)p * grid->Nx > VP_NOALLOC_MAX_COUNTS) return VP_EUNSUPPORTED;
@@ -72,9 +80,11 @@ extern "C" vp_status vp_deposit_cic_noalloc(const vp_grid* grid, int64_t N, int3
     return VP_ECUDA;
   }
   const vpk::GridC g = vpk::make_gridc(*grid, N);
-  vpk::deposit_samples(g, N, p, X_dev, ldx, counts, sms, st);
-  vpk::counts_to_rho(g, p, counts, rho_dev, st);
-  if (cudaGetLastError() != cudaSuccess) return VP_ECUDA;
+  if (vpk::deposit_samples_launch(g, N, p, X_dev, ldx, counts, sms, st) != cudaSuccess ||
+      vpk::counts_to_rho_launch(g, p, counts, rho_dev, st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return VP_ECUDA;
+  }
   return VP_OK;
 }
 

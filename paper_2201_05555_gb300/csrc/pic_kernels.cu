@@ -158,6 +158,37 @@ void counts_to_rho(const GridC& g, int p, const unsigned long long* counts, doub
   k_counts_to_rho<<<ceil_div(n, 256), 256, 0, st>>>(g, p, counts, rho);
 }
 
+// The same two launches through cudaLaunchKernel, whose return value is the
+// launch's own error (the allocation-free deposit reports it without reading
+// an error that earlier, unrelated work left pending on the thread).
+cudaError_t deposit_samples_launch(const GridC& g, int64_t N, int p, const double* X, int64_t ldx,
+                                   unsigned long long* counts, int num_sms, cudaStream_t st) {
+  const int bs = 256;
+  int bx = ceil_div(N, bs * 8);
+  int want = (2 * num_sms + p - 1) / p;
+  if (bx > want) bx = want;
+  if (bx < 1) bx = 1;
+  GridC ga = g;
+  int64_t Na = N, lda = ldx;
+  const double* Xa = X;
+  unsigned long long* ca = counts;
+  void* args[] = {&ga, &Na, &Xa, &lda, &ca};
+  return cudaLaunchKernel((const void*)k_deposit, dim3(bx, p), dim3(bs),
+                          args, g.Nx * sizeof(unsigned long long), st);
+}
+
+cudaError_t counts_to_rho_launch(const GridC& g, int p, const unsigned long long* counts,
+                                 double* rho, cudaStream_t st) {
+  const int64_t n = (int64_t)p * g.Nx;
+  GridC ga = g;
+  int pa = p;
+  const unsigned long long* ca = counts;
+  double* ra = rho;
+  void* args[] = {&ga, &pa, &ca, &ra};
+  return cudaLaunchKernel((const void*)k_counts_to_rho, dim3((unsigned)ceil_div(n, 256)), dim3(256),
+                          args, 0, st);
+}
+
 // ---------------------------------------------------------------- Poisson
 // One block per sample.  Input either rho (double) or fixed-point counts.
 // F2 (nullable): (q/m) F also in the row format f2mode of the FP32-based

@@ -883,7 +883,11 @@ __global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restric
 
 // ------------------------------------------------------------------ affine
 // out_l = sum_t X_t,l C_t (C_t n x n complex FP64, converted once per block);
-// written as FP64 rows (out_d) and/or rows of the policy (out_v).
+// written as FP64 rows (out_d) and/or rows of the policy (out_v).  With
+// a.base (FP64 rows of term 0), out_d = base + sum_t X_t C_t - X_0: the
+// increment (C_0 less the identity) in the policy's arithmetic, the sum with
+// the FP64 base in FP64, so out_d keeps FP64 accuracy where the increment
+// is small (a retraction over one time step).
 template <class AR>
 __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __restrict__ C,
                             double* __restrict__ out_d, typename AR::V* __restrict__ out_v,
@@ -901,6 +905,7 @@ __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __r
   const int64_t ntiles = (N + TR - 1) / TR;
   for (int e = t; e < a.nterms * nn; e += blockDim.x) {
     double2 c = C[e];
+    if (a.base && e < nn && e / n == e % n) c.x -= 1.0;  // term 0: C_0 - I
     Cr[e] = AR::from(c.x);
     Ci[e] = AR::from(c.y);
   }
@@ -955,8 +960,13 @@ __global__ void k_affine_lp(int64_t N, int n, AffineArgsLP a, const double2* __r
       }
       const int64_t o = (base + r) * n2;
       if (out_d) {
-        out_d[o + k] = re.value();
-        out_d[o + n + k] = im.value();
+        double vr = re.value(), vi = im.value();
+        if (a.base) {
+          vr += a.base[o + k];
+          vi += a.base[o + n + k];
+        }
+        out_d[o + k] = vr;
+        out_d[o + n + k] = vi;
       }
       if (out_v) {
         out_v[o + k] = re.out();

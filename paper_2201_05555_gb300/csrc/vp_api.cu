@@ -94,9 +94,9 @@ vp_status check_n(vp_ctx* ctx, int32_t n, int64_t N) {
 // Workspace of the reduced-model calls.
 struct RedWS {
   unsigned long long* counts;
-  double *F, *Efield, *part, *gX, *k, *kp, *Ze, *Z0, *Z1, *GVraw, *aux;
+  double *F, *Efield, *part, *gX, *k, *kr, *Ze, *Z0, *Z1, *GVraw, *aux;
   double2 *grams, *cay, *C, *tmp;
-  int* flags;  // [0] done, [1] iters, [2] ticket, [3] stopped on a two-cycle
+  int* flags;  // [0] done, [1] iters, [2] ticket, [3] period of the cycle stopped on
   double* rows[5];
   float2 *Q2a, *Q2b;  // row-format shadows of Q0 and Q_half (float2 or float)
   uint16_t* jcell;    // cell index per (particle, sample), N x p
@@ -146,8 +146,8 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
                                    std::max<size_t>((size_t)gg * 12 * nn * 2, (size_t)gg * n2 * n2));
   size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
   return arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
-         arena_bytes((size_t)n2 * p, 8) * 6 + arena_bytes((size_t)n2 * n2, 8) +
-         arena_bytes((size_t)(n2 + 3) * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
+         arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)3 * n2 * p, 8) +
+         arena_bytes((size_t)n2 * n2, 8) + arena_bytes((size_t)(n2 + 5) * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
          arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
@@ -174,12 +174,12 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.part = a.take<double>(part_d);
   w.gX = a.take<double>((size_t)n2 * p);
   w.k = a.take<double>((size_t)n2 * p);
-  w.kp = a.take<double>((size_t)n2 * p);
+  w.kr = a.take<double>((size_t)3 * n2 * p);  // ring of earlier fixed-point iterates
   w.Ze = a.take<double>((size_t)n2 * p);
   w.Z0 = a.take<double>((size_t)n2 * p);
   w.Z1 = a.take<double>((size_t)n2 * p);
   w.GVraw = a.take<double>((size_t)n2 * n2);
-  w.aux = a.take<double>((size_t)(n2 + 3) * p + 64);
+  w.aux = a.take<double>((size_t)(n2 + 5) * p + 64);
   w.grams = a.take<double2>(12 * nn);
   w.cay = a.take<double2>(4 * nn);
   w.C = a.take<double2>(4 * nn);
@@ -326,6 +326,7 @@ struct RedDF {
   cudaStream_t st;
   int64_t N;
   int n, p, arith;
+  bool diag = false;  // the FP64-accurate energy diagnostic of the FP32 form (own profiling id)
   LpArgs base() const {
     LpArgs a;
     a.g = &R.g;
@@ -355,7 +356,7 @@ struct RedDF {
     a.counts = w.counts;
     a.j = w.jcell;
     a.skip = skip;
-    VP_K(VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
+    VP_K(diag ? VP_K_DEPOSIT_DIAG : VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
     VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, w.phi_out, w.F, w.Efield, w.counts, skip,
                                ctx->d_status, st, w.F2, arith));
   }
@@ -392,9 +393,11 @@ struct RedDF {
     VP_K(VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
   }
-  void comb(std::initializer_list<const void*> xs, const double2* C, double* out_d, void* out_v) {
+  void comb(std::initializer_list<const void*> xs, const double2* C, double* out_d, void* out_v,
+            const double* base_d = nullptr) {
     LpArgs a = base();
     for (const void* x : xs) a.aff.X[a.aff.nterms++] = x;
+    a.aff.base = base_d;
     a.C = C;
     a.dout = out_d;
     a.v0 = out_v;
@@ -421,19 +424,23 @@ struct RedDF {
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
     comb({M, Q2}, w.C, nullptr, out);
   }
-  // Cayley retraction of Q0 along xi; leaves G0, P, XX in w.cay
-  void cayley(const void* Q0, const void* xi, double* out_d, void* out_v) {
+  // Cayley retraction of Q0 along xi; leaves G0, P, XX in w.cay.  Q0d (FP64
+  // rows of Q0, nullable): out_d = Q0d + the increment (see AffineArgsLP)
+  void cayley(const void* Q0, const void* xi, double* out_d, void* out_v,
+              const double* Q0d = nullptr) {
     RedWS& w = R.w;
     grams({Q0, xi}, {{0, 0}, {0, 1}, {1, 1}}, w.cay);
     const int nn = n * n;
     VP_K(VP_K_SMALL_CAYLEY, small_cayley_coeffs(n, w.cay, w.cay + nn, w.cay + 2 * nn, w.C, w.tmp,
                                                 ctx->d_status, st));
-    comb({Q0, xi}, w.C, out_d, out_v);
+    comb({Q0, xi}, w.C, out_d, out_v, Q0d);
   }
 };
 }  // namespace
 
 namespace {
+// Lowest fixed-point tolerance of the FP32 form (about 8 FP32 ulps).
+constexpr double kTolFP32 = 1e-6;
 struct DFStep {
   vp_ctx* ctx;
   Red& R;
@@ -463,6 +470,10 @@ struct DFStep {
 DFStep::DFStep(vp_ctx* c, Red& r, double* q, double* z, double d, const vp_step_opts& opt,
                double* ks, cudaStream_t s)
     : ctx(c), R(r), Q(q), Z(z), dt(d), o(opt), kstate(ks), st(s) {
+  // the FP32 form evaluates the fixed-point map with FP32 rows: its updates
+  // stop shrinking near the FP32 rounding level (~1e-7 relative), so the stop
+  // tolerance is at least kTolFP32
+  if (o.arith == 2 && o.tol < kTolFP32) o.tol = kTolFP32;
   Rs = sub_red(R);
   Rs.w.sub.idx = opt.sub_idx;
 }
@@ -494,7 +505,7 @@ vp_status DFStep::pre(double* trace_step) {
   const int n = R.n, p = R.p;
   const int64_t N = R.N;
   RedDF D{R, ctx, st, N, n, p, o.arith};
-  RedDF DD{R, ctx, st, N, n, p, 1};  // double-float diagnostics
+  RedDF DD{R, ctx, st, N, n, p, 1, true};  // double-float diagnostics
   void *Q0 = w.Q2a, *M = w.frows[0], *xih = w.frows[1], *Qh = w.frows[2];
   const int64_t zsz = (int64_t)2 * n * p;
   if (trace_step && o.arith == 2) {  // FP64-accurate diagnostic in the precision form
@@ -550,7 +561,7 @@ vp_status DFStep::rounds(int count) {
     D.field(Qm, w.Ze, w.flags, true);
     D.project(Qm, w.flags);
     VP_K(VP_K_COEFF_UPDATE,
-         coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.kp, w.Ze, dt, o.tol, o.maxit,
+         coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.kr, w.Ze, dt, o.tol, o.maxit,
                       o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st, w.part,
                       w.gx_proj, w.Z2, w.Zh2, R.g.inv_h, o.arith));
   }
@@ -575,7 +586,10 @@ vp_status DFStep::post() {
     VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
                                                   ctx->d_status, st));
     D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
-    D.cayley(Q0, xi1, Q, nullptr);             // Q_1 = R_Q0(xi_1) in FP64
+    // Q_1 = R_Q0(xi_1) in FP64; in the FP32 form as Q_0 + (Q_1 - Q_0), the
+    // increment from FP32 rows added to the FP64 Q_0, so that Q does not take
+    // an FP32 rounding error every step
+    D.cayley(Q0, xi1, Q, nullptr, o.arith == 2 ? Q : nullptr);
     if (o.reortho) {                           // Q <- Q (Q^H Q)^-1/2
       DD.split(Q, w.Q2b);
       DD.grams({w.Q2b}, {{0, 0}}, w.grams);
@@ -746,7 +760,7 @@ vp_status hyper_interval(vp_hyper* h, Red& R, DFStep& S, double* trace_step, int
       for (int k = 0; k < rr; ++k) {
         VP_K(VP_K_DEIM_ROUND, deim_round(h->g, n, p, h->d, h->Qd, w.Ze, h->F, h->c, w.gX, w.flags, st));
         VP_K(VP_K_COEFF_UPDATE,
-             coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kp, w.Ze, S.dt, o.tol, o.maxit,
+             coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kr, w.Ze, S.dt, o.tol, o.maxit,
                           o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st));
       }
     } else {
@@ -1148,7 +1162,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd",
-    "k_jacobi_sym"};
+    "k_jacobi_sym", "k_deposit_lp_diag"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1866,7 +1880,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
         VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
                                    w.part, w.gx_proj, w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
-        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kp, w.Ze, dt, o.tol,
+        VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kr, w.Ze, dt, o.tol,
                                              o.maxit, o.cycle_max, o.cycle_ratio, w.aux, w.flags,
                                              w.flags + 1, ctx->d_status, st));
       }

@@ -268,6 +268,10 @@ struct GramArgsLP {
 struct AffineArgsLP {
   const void* X[4];
   int nterms;
+  // FP64 rows of term 0 (nullable): the FP64 output is then written as
+  // base + sum_t X_t C_t - X_0, i.e. term 0's coefficient less the identity
+  // in the row arithmetic and the base added in FP64 (increment form)
+  const double* base = nullptr;
 };
 enum LpOp { LP_SPLIT, LP_PREP, LP_DEPOSIT, LP_PROJECT, LP_BASIS_M, LP_GRAM, LP_GRAM_REAL, LP_AFFINE };
 struct LpArgs {
@@ -303,6 +307,11 @@ void deposit_samples(const GridC& g, int64_t N, int p, const double* X, int64_t 
                      unsigned long long* counts, int num_sms, cudaStream_t st);
 void counts_to_rho(const GridC& g, int p, const unsigned long long* counts, double* rho,
                    cudaStream_t st);
+// the same launches, returning the launch's own error
+cudaError_t deposit_samples_launch(const GridC& g, int64_t N, int p, const double* X, int64_t ldx,
+                                   unsigned long long* counts, int num_sms, cudaStream_t st);
+cudaError_t counts_to_rho_launch(const GridC& g, int p, const unsigned long long* counts,
+                                 double* rho, cudaStream_t st);
 void poisson(const GridC& g, int p, const double* rho, const unsigned long long* counts,
              double* phi, double* F, double* energy, unsigned long long* zero_counts,
              const int* skip, int* status, cudaStream_t st, void* F2 = nullptr, int f2mode = 0);
@@ -343,12 +352,13 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
                           double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
 // gX: the projection (2n x p), or nullptr with `part` (nparts x 2n x p block
-// partials of it, summed here in block order).  kp (2n x p): the iterate two
-// iterations back (no initial value needed).  partials: 3 p doubles.
+// partials of it, summed here in block order).  kr (3 x 2n x p): ring of
+// the iterates two to four iterations back (no initial value needed).
+// partials: 5 p + 8 doubles (block sums, then the last 8 relative updates).
 // Z2/Zh2 (nullable): the new evaluation point Ze and Ze / h in the row format
 // `zmode` (1 double-float, 2 FP32) for the next deposit.
 void coeff_update(int n, int p, const double* gX, const double* GVraw, const double* Z0, double* k,
-                  double* kp, double* Ze, double dt, double tol, int maxit, double cycle_max,
+                  double* kr, double* Ze, double dt, double tol, int maxit, double cycle_max,
                   double cycle_ratio, double* partials, int* done, int* iters, int* status,
                   cudaStream_t st, const double* part = nullptr, int nparts = 0,
                   void* Z2 = nullptr, void* Zh2 = nullptr, double inv_h = 0.0, int zmode = 0);

@@ -87,3 +87,20 @@ def test_no_fallback_without_the_library_or_a_gpu(monkeypatch, tmp_path):
         binding.load_library()
     with pytest.raises(ValueError, match="CUDA tensor"):
         binding._ptr(torch.zeros(4, dtype=torch.float64), name="Q")
+
+
+def test_noalloc_binding_checks_shapes_before_the_call(lib):
+    # an undersized rho would be written past its end on the device: the
+    # binding refuses mismatched shapes on the host
+    import torch
+
+    from paper_2201_05555_gb300 import make_grid
+    from paper_2201_05555_gb300.binding import deposit_cic_noalloc
+
+    grid = make_grid(10, 16, 1.0)
+    with pytest.raises(ValueError, match="p x Nx"):
+        deposit_cic_noalloc(grid, torch.zeros(2, 10, dtype=torch.float64),
+                            torch.zeros(2, 15, dtype=torch.float64))
+    with pytest.raises(ValueError, match="p x N"):
+        deposit_cic_noalloc(grid, torch.zeros(20, dtype=torch.float64),
+                            torch.zeros(2, 16, dtype=torch.float64))

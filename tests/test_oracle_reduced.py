@@ -237,15 +237,17 @@ def _orthosymplectic(N, n, seed):
     return csvd.U_from_Q(Qc)
 
 
-def test_fixed_point_contraction_07_runs_to_tol():
+@pytest.mark.parametrize("c", [0.7, 0.9])
+def test_fixed_point_contraction_runs_to_tol(c):
     """H = 1/2 R^T A R with A = U B U^T and B = diag(b, -b) (a saddle):
     with the basis frozen the fixed-point map is affine, k -> J B (Z + dt/2 k),
     and its linear part dt/2 J B has the real eigenvalues +0.7 and -0.7.  The
     iteration converges linearly with factor 0.7, monotone along one direction
-    and oscillating along the other; the two-cycle test must not stop it, so
-    it runs to the paper's relative update 1e-9 and reaches the exact solution
-    of (I - dt/2 J B) k = J B Z to about 0.7 / 0.3 of that."""
-    N, n, p, dt, c = 40, 2, 3, 0.1, 0.7
+    and oscillating along the other (also with 0.9); neither the cycle test nor
+    the plateau test (0.9^8 = 0.43 < 1/2) may stop it, so it runs to the
+    paper's relative update 1e-9 and reaches the exact solution of
+    (I - dt/2 J B) k = J B Z to about c / (1 - c) of that."""
+    N, n, p, dt = 40, 2, 3, 0.1
     U = _orthosymplectic(N, n, 3)
     b = 2 * c / dt
     B = np.diag(np.r_[np.full(n, b), np.full(n, -b)])
@@ -255,66 +257,122 @@ def test_fixed_point_contraction_07_runs_to_tol():
     Jn = reduced.J(2 * n)
     eig = np.sort(np.linalg.eigvals(0.5 * dt * Jn @ B).real)
     np.testing.assert_allclose(eig, [-c, -c, c, c], atol=1e-12)
-    U1, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, grad_fn=lambda R: A @ R)
-    assert not info["cycle"]
+    U1, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, grad_fn=lambda R: A @ R,
+                                     maxit=400)
+    assert info["cycle"] == 0 and not info["plateau"]
     assert info["resid"] <= 1e-9
-    assert info["iters"] > 50  # 0.7^m falls to ~1e-9 only after ~60 iterations
+    # c^m falls to ~1e-9 only after log(1e-9) / log(c) iterations
+    assert info["iters"] > 0.9 * np.log(1e-9) / np.log(c)
     k_exact = np.linalg.solve(np.eye(2 * n) - 0.5 * dt * Jn @ B, Jn @ B @ Z0)
-    assert np.linalg.norm(info["k2"] - k_exact) <= 3e-9 * np.linalg.norm(k_exact)
+    assert np.linalg.norm(info["k2"] - k_exact) <= 2e-9 * c / (1 - c) * np.linalg.norm(k_exact)
 
 
-def _flip_hamiltonian(U, K, eps, theta):
-    """G(R) = U h(U^T R) with h(z) = (K + eps sign(z_2 - theta)) e_1 on the
-    first coefficient pair: a force that jumps across z_2 = theta, like the P1
-    force at a node.  With the basis frozen, k = J h(Z + dt/2 k) moves only
-    z_2, by -(K + eps s) dt/2."""
+def _staircase_hamiltonian(U, levels, dt, eps):
+    """G(R) = U h(U^T R) with h(z) = (phi(z_2), 0) on one coefficient pair and
+    phi a staircase: a force that jumps across thresholds of z_2, like the P1
+    force at the nodes.  With the basis frozen, Z0 = 0 and dt/2 = 0.05,
+    k = J h(Z0 + dt/2 k) moves only z_2: k_2 = -phi(0.05 k_2).  With
+    v_j = 1 + j eps (j < P = levels), phi = -v_{j+1 mod P} on the interval of
+    half-width 0.05 eps / 2 around 0.05 v_j (the outer intervals extended to
+    infinity), so from k = 0 the iterates are v_1, v_2, ..., v_{P-1}, v_0,
+    v_1, ...: an exact P-cycle of relative amplitude about eps."""
+    v = 1.0 + eps * np.arange(levels)
+    edges = 0.5 * dt * (v[:-1] + 0.5 * eps)  # upper ends of intervals 0 .. P-2
+
     def grad_fn(R):
         z = U.T @ R
+        j = np.searchsorted(edges, z[1], side="right")
         h = np.zeros_like(z)
-        h[0] = K + eps * np.where(z[1] - theta >= 0, 1.0, -1.0)
+        h[0] = -v[(j + 1) % levels]
         return U @ h
-    return grad_fn
+    return grad_fn, v
 
 
-def test_fixed_point_stops_on_constructed_two_cycle():
-    """Z_2 - theta = dt/2 K + delta with |delta| < dt/2 eps: from k = 0 the
-    iterates are k_1 = -(K + eps) e_2, k_2 = -(K - eps) e_2, k_3 = k_1, ...
-    an exact two-cycle of relative amplitude 2 eps / K.  The rule stops at
-    m = 3 (k_3 = k_1), not before (k_2 is far from k_0 = 0), on k_3."""
-    N, dt, K, eps = 20, 0.1, 1.0, 1e-6
+@pytest.mark.parametrize("period", [2, 3, 4])
+def test_fixed_point_stops_on_constructed_cycle(period):
+    """The staircase with P = 2, 3, 4 levels: the iterates return exactly at
+    m = P + 1 (k_{P+1} = k_1), where the rule stops with period P on k_1's
+    value; no shorter period matches on the way."""
+    N, dt, eps = 20, 0.1, 1e-5
     U = _orthosymplectic(N, 1, 7)
-    theta, delta = 0.3, 0.25 * 0.5 * dt * eps
-    Z0 = np.array([[0.2], [theta + 0.5 * dt * K + delta]])
+    Z0 = np.zeros((2, 1))
     g = pic.make_grid(N, 8, 1.0)
-    _, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True,
-                                    grad_fn=_flip_hamiltonian(U, K, eps, theta))
-    assert info["cycle"] and info["iters"] == 3
-    np.testing.assert_allclose(info["k2"], [[0.0], [-(K + eps)]], rtol=0, atol=1e-14)
-    np.testing.assert_allclose(info["resid"], 2 * eps / (K + eps), rtol=1e-8)
+    grad_fn, v = _staircase_hamiltonian(U, period, dt, eps)
+    _, Z1, info = reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, grad_fn=grad_fn)
+    assert info["cycle"] == period and info["iters"] == period + 1
+    # J (h_1, 0) = (0, -h_1): k = (0, v_1)
+    np.testing.assert_allclose(info["k2"], [[0.0], [v[1 % period]]], rtol=0, atol=1e-14)
     np.testing.assert_allclose(Z1, Z0 + dt * info["k2"], rtol=0, atol=0)
 
 
-def test_fixed_point_large_cycle_is_not_accepted():
-    """The same construction with eps / K = 0.1: a cycle of relative amplitude
-    0.2 > cycle_max = 1e-3 is no solution, so the iteration runs out."""
-    N, dt, K, eps = 20, 0.1, 1.0, 0.1
+def test_fixed_point_cycle_longer_than_four_stops_on_the_plateau():
+    """A five-cycle is beyond the periods of the cycle test (2 to 4); its
+    updates repeat, so it stops on the plateau test instead, at m = 10 (the
+    first iteration whose update r_10 = 4 eps is compared with r_2 = eps)."""
+    N, dt, eps = 20, 0.1, 1e-5
     U = _orthosymplectic(N, 1, 7)
-    theta, delta = 0.3, 0.25 * 0.5 * dt * eps
-    Z0 = np.array([[0.2], [theta + 0.5 * dt * K + delta]])
     g = pic.make_grid(N, 8, 1.0)
+    grad_fn, _ = _staircase_hamiltonian(U, 5, dt, eps)
+    _, _, info = reduced.prk2_step(U, np.zeros((2, 1)), dt, g, freeze_basis=True, maxit=40,
+                                   grad_fn=grad_fn)
+    assert info["cycle"] == 0 and info["plateau"] and info["iters"] == 10
+    # without the plateau test it runs out; with longer periods allowed it
+    # stops at m = 6 on the cycle
     with pytest.raises(reduced.NoConvergence):
-        reduced.prk2_step(U, Z0, dt, g, freeze_basis=True, maxit=30,
-                          grad_fn=_flip_hamiltonian(U, K, eps, theta))
+        reduced.prk2_step(U, np.zeros((2, 1)), dt, g, freeze_basis=True, maxit=40,
+                          grad_fn=grad_fn, plateau_window=1000)
+    _, _, info = reduced.prk2_step(U, np.zeros((2, 1)), dt, g, freeze_basis=True, maxit=40,
+                                   grad_fn=grad_fn, cycle_qmax=5)
+    assert info["cycle"] == 5 and info["iters"] == 6
 
 
-def test_fixed_point_two_cycle_on_tiny_pic():
+def test_fixed_point_stops_on_a_wandering_plateau():
+    """A force with many small pseudo-random jumps: k_2 = -(1 + eps u(j)) with
+    j the cell of width delta = eps / 400 holding z_2 = 0.05 k_2 and u(j) in
+    [-1, 1] from a hash of j.  The iterates wander among values within eps of
+    1 without settling or repeating within the window; the plateau test stops
+    them, on a value inside that band, well before maxit."""
+    N, dt, eps = 20, 0.1, 1e-5
+    U = _orthosymplectic(N, 1, 7)
+    g = pic.make_grid(N, 8, 1.0)
+    delta = 0.05 * eps / 400
+
+    def u(j):
+        return 2.0 * ((np.asarray(j, dtype=np.int64) * 2654435761 % 4294967296) / 4294967296.0) - 1.0
+
+    def grad_fn(R):
+        z = U.T @ R
+        h = np.zeros_like(z)
+        h[0] = 1.0 + eps * u(np.floor(z[1] / delta).astype(np.int64))
+        return U @ h
+
+    _, _, info = reduced.prk2_step(U, np.zeros((2, 1)), dt, g, freeze_basis=True, maxit=60,
+                                   grad_fn=grad_fn)
+    assert info["plateau"] and info["cycle"] == 0 and 10 <= info["iters"] <= 30
+    assert abs(abs(info["k2"][1, 0]) - 1.0) <= eps
+    assert eps / 100 < info["resid"] <= 2 * eps
+
+
+def test_fixed_point_large_cycle_is_not_accepted():
+    """The two-level staircase with eps = 0.1: a cycle of relative amplitude
+    about 0.1 > cycle_max = 1e-3 is no solution, so the iteration runs out."""
+    N, dt = 20, 0.1
+    U = _orthosymplectic(N, 1, 7)
+    g = pic.make_grid(N, 8, 1.0)
+    grad_fn, _ = _staircase_hamiltonian(U, 2, dt, 0.1)
+    with pytest.raises(reduced.NoConvergence):
+        reduced.prk2_step(U, np.zeros((2, 1)), dt, g, freeze_basis=True, maxit=30,
+                          grad_fn=grad_fn)
+
+
+def test_fixed_point_cycle_on_tiny_pic():
     """A tiny PIC case (N = 64, p = 4, Nx = 8, dt = 0.5, basis frozen) whose
     iteration settles on a cycle of cell flips with relative amplitude
     ~3.5e-3.  With cycle_max = 1e-3 that cycle is refused (NoConvergence);
     with cycle_max = 1e-2 the iteration stops on it, and the result is a
-    member of a true two-cycle of the fixed-point map F (checked by applying
-    F here): F(F(k)) = k to the tolerance while F(k) differs from k by the
-    cycle's amplitude."""
+    member of a true q-cycle of the fixed-point map F (checked by applying F
+    here q times): F^q(k) = k to the tolerance while F(k) differs from k by
+    the cycle's amplitude.  The plateau test stops it earlier, on the way."""
     N, p, n, Nx, L, dt = 64, 4, 2, 8, 4 * np.pi, 0.5
     g = pic.make_grid(N, Nx, L)
     X0 = W.random_positions(p, N, L, seed=4)
@@ -322,18 +380,28 @@ def test_fixed_point_two_cycle_on_tiny_pic():
     U0, Z0, _ = csvd.csvd_init(X0, V0, n)
     with pytest.raises(reduced.NoConvergence):
         reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60)
-    _, _, info = reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60, cycle_max=1e-2)
-    assert info["cycle"]
+    # the cycle test alone (plateau test off)
+    _, _, info = reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60, cycle_max=1e-2,
+                                   plateau_window=1000)
+    q = info["cycle"]
+    assert 2 <= q <= 4
     k = info["k2"]
 
     def F(k):
         return reduced.apply_J(U0.T @ reduced.full_gradient(U0, Z0 + 0.5 * dt * k, g)[0])
 
-    k1 = F(k)
-    k2 = F(k1)
+    orbit = [k]
+    for _ in range(q):
+        orbit.append(F(orbit[-1]))
+    k1 = orbit[1]
     nk = np.linalg.norm(k)
-    assert np.linalg.norm(k2 - k) <= 1e-9 * nk
+    assert np.linalg.norm(orbit[q] - k) <= 1e-9 * nk
     assert 1e-3 < np.linalg.norm(k1 - k) / nk < 1e-2
+    # with the plateau test as well it stops no later, once the updates stop
+    # shrinking at the cycle's amplitude
+    _, _, info2 = reduced.prk2_step(U0, Z0, dt, g, freeze_basis=True, maxit=60, cycle_max=1e-2)
+    assert info2["plateau"] or info2["cycle"]
+    assert info2["iters"] <= info["iters"] and 1e-3 < info2["resid"] < 1e-2
     # the two members place some particle in different cells
     cells = [np.floor(np.mod(reduced.reconstruct(U0, Z0 + 0.5 * dt * kk)[0], L) / g.h)
              for kk in (k, k1)]
