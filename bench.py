@@ -1,13 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the reduced-model hot path on GB300.
 
-Workload (two-stream instability, dynamical reduced model): N = 1e5
-particles per sample, p = 64 samples (v0 on a Hammersley set in [2, 3]),
-rank 2n = 20, Nx = 128, dt = 0.05, FP64.  One step is one partitioned RK2
-step (Sec. 5): basis velocity, Cayley retraction, the fixed-point
-coefficient stage (deposit, Poisson, gather, projection per iteration),
-the tangent velocity and the second retraction, plus the FP64 energy
-diagnostics.  Metric: particle-steps/s = N * p * steps / time.
+Headline workload (the largest configuration on one GPU): the precision form
+of the dynamical reduced model on bump-on-tail, N = 1e6 particles per sample,
+p = 256 samples (beam velocity on a Hammersley set in [4, 5]), Nx = 256,
+dt = 0.1, rank 2n in [16, 64] chosen at t = 0 by the complex-SVD tail energy
+(< 1e-8, capped at 64), Philox-seeded loading on the device.  One step is
+one partitioned RK2 step (Sec. 5): basis velocity, Cayley retraction, the
+fixed-point coefficient stage (deposit, Poisson, gather, projection per
+iteration), the tangent velocity, the second retraction and the FP64
+re-orthonormalisation, plus the FP64-accurate energy check of the entering
+state.  Row work (reconstruction, deposit, projection, Gamma zeta^H, Grams,
+row updates) in FP32; cross-block reductions, small dense algebra,
+re-orthonormalisation factor and energies in FP64.  Metric:
+particle-steps/s = N * p * steps / time.
+
+Extra lines: the two-stream workload (N = 1e5, p = 64, 2n = 20) in FP64 and
+in double-float arithmetic, each with its error against the oracle after
+one step from the same start; the FP64 and double-float forms at the
+headline size; full-order, batched, served, subsampled, DMD-DEIM, DEIM and
+DMD measurements.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,14 +48,22 @@ import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s (N*p per step)"
 UNIT = "particle-steps/s"
+# headline: bump-on-tail precision form
+HEAD = dict(N=1_000_000, p=256, Nx=256, dt=0.1, n_min=8, n_max=32, rank_tol=1e-8,
+            vb=(4.0, 5.0), alpha=0.04, sigma_b=0.5)
+# oracle sample of the headline workload: the same samples and rank on fewer particles
+CPU_SAMPLE_N = 20_000
+# two-stream reduced workload of the extra FP64 and double-float lines
 WL = dict(name="two_stream_reduced", N=100_000, p=64, n2=20, Nx=128, dt=0.05)
 L2_BYTES = 129 * 2**20
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM clock
+# FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Double-float particle loops: one emulated FMA (Dot2 term: a product, its
 # exact error from three FMAs, a TwoSum and two error additions) costs 12 FP32
 # instructions, so the derived peak is 152 SMs x 128 lanes x 2.07 GHz x 2 / 12.
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
-ARITH = 1
+ARITH = 1  # arithmetic of the two-stream subsample and DMD-DEIM lines (double-float)
 # served form: Poisson arrivals; N log-uniform, p uniform in [1, 64], horizon T
 SERVE = dict(rate=50.0, seconds=10.0, N=(1e3, 1e4), T=4.0, slots=16, arith=2,
              budget=150 << 30)
@@ -69,7 +89,7 @@ def parse():
     ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
-    ap.add_argument("--only", choices=["hyper", "dmd", "deim_build", "subsampled", "precision"],
+    ap.add_argument("--only", choices=["head", "hyper", "dmd", "deim_build", "subsampled", "forms"],
                     default=None,
                     help="run one extra measurement alone and print its JSON (profiling runs)")
     return ap.parse_args()
@@ -165,41 +185,105 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def cpu_baseline(steps: int) -> dict:
-    """The FP64 oracle, as it stands, on one host thread (BLAS pinned to 1
-    thread): `steps` PRK2 steps of the full workload."""
-    code = f"""
-import json, os, sys, time
+def _oracle_proc(code: str, one_thread: bool, timeout: int = 1800) -> dict:
+    """Run `code` (which prints one JSON line last) in a fresh interpreter;
+    one_thread pins BLAS and OpenMP to one host thread."""
+    env = dict(os.environ)
+    if one_thread:
+        env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError((r.stderr.strip().splitlines() or ["no output"])[-1])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_head_sample(n_part: int, steps: int, warmup: int, path: str) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the headline
+    workload: the same 256 bump-on-tail samples and rank 2n = 64 on n_part
+    particles per sample (host loading, seeded per sample).  The start
+    (truncated complex SVD) runs in its own process on all host threads and
+    is not timed; then `warmup` untimed and `steps` timed PRK2 steps on one
+    host thread (BLAS pinned), the fixed point warm-started as on the device."""
+    pre = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import workloads as W
+from oracle import csvd, pic, reduced
+N, p, n, Nx, dt = {n_part}, {HEAD['p']}, {HEAD['n_max']}, {HEAD['Nx']}, {HEAD['dt']}
+"""
+    init = pre + f"""
+etas = W.hammersley_params(p, {{"vb": {HEAD['vb']}}}, {{"alpha": {HEAD['alpha']}, "sigma_b": {HEAD['sigma_b']}}})
+X0, V0 = W.load_batch(W.BUMP_ON_TAIL, etas, N, quiet=False)
+U, Z, _ = csvd.csvd_init(X0, V0, n)
+np.savez({path!r}, U=U, Z=Z)
+print(json.dumps({{"ok": 1}}))
+"""
+    step = pre + f"""
+d = np.load({path!r})
+U, Z = d["U"], d["Z"]
+g = pic.make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+k = None
+its = []
+for _ in range({warmup}):
+    U, Z, info = reduced.prk2_step(U, Z, dt, g, k_init=k)
+    k = info["k2"]
+t = time.perf_counter()
+for _ in range({steps}):
+    U, Z, info = reduced.prk2_step(U, Z, dt, g, k_init=k)
+    k = info["k2"]
+    its.append(info["iters"])
+print(json.dumps({{"seconds": time.perf_counter() - t, "iters": its}}))
+"""
+    _oracle_proc(init, one_thread=False)
+    out = _oracle_proc(step, one_thread=True)
+    units = n_part * HEAD["p"] * steps
+    return {"value": units / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{steps} PRK2 step(s) after {warmup} untimed, of the bump-on-tail workload "
+                       f"on N={n_part} of its particles per sample, p={HEAD['p']}, "
+                       f"2n={2 * HEAD['n_max']}, Nx={HEAD['Nx']}, dt={HEAD['dt']}; numpy float64, "
+                       f"BLAS on 1 thread; fixed-point iterations {out['iters']}"),
+            "seconds": out["seconds"], "steps": steps}
+
+
+def oracle_two_stream_step(path: str) -> dict:
+    """The oracle's start (truncated complex SVD of the host-loaded two-stream
+    workload, all host threads) and one cold PRK2 step from it on one host
+    thread.  Writes U0, Z0, U1, Z1 to `path` for the device's error against
+    it; returns the step's timing."""
+    pre = f"""
+import json, sys, time
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 import workloads as W
 from oracle import csvd, pic, reduced
 wl = W.two_stream_reduced(N={WL['N']}, p={WL['p']}, Nx={WL['Nx']}, n2={WL['n2']}, dt={WL['dt']})
+"""
+    init = pre + f"""
 X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet)
 U, Z, _ = csvd.csvd_init(X0, V0, wl.n2 // 2)
-g = pic.make_grid(wl.N, wl.Nx, wl.family.L)
-
-t = time.perf_counter()
-its = []
-for _ in range({steps}):
-    U, Z, info = reduced.prk2_step(U, Z, wl.dt, g)
-    its.append(info["iters"])
-dt = time.perf_counter() - t
-print(json.dumps({{"seconds": dt, "iters": its}}))
+np.savez({path!r}, U=U, Z=Z)
+print(json.dumps({{"ok": 1}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=1800)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "error": r.stderr.strip().splitlines()[-1:]}
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    units = WL["N"] * WL["p"] * steps
-    return {"value": units / out["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} PRK2 steps of the full workload (N={WL['N']}, p={WL['p']}, "
-                      f"2n={WL['n2']}) numpy float64, BLAS 1 thread; "
-                      f"fixed-point iterations {out['iters']}",
-            "seconds": out["seconds"]}
+    step = pre + f"""
+d = np.load({path!r})
+U, Z = d["U"], d["Z"]
+g = pic.make_grid(wl.N, wl.Nx, wl.family.L)
+t = time.perf_counter()
+U1, Z1, info = reduced.prk2_step(U, Z, wl.dt, g)
+dt_ = time.perf_counter() - t
+np.savez({path!r}, U=U, Z=Z, U1=U1, Z1=Z1)
+print(json.dumps({{"seconds": dt_, "iters": info["iters"]}}))
+"""
+    _oracle_proc(init, one_thread=False)
+    out = _oracle_proc(step, one_thread=True)
+    return {"value": WL["N"] * WL["p"] / out["seconds"], "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": (f"one cold PRK2 step of the two-stream workload (N={WL['N']}, p={WL['p']}, "
+                       f"2n={WL['n2']}), numpy float64, BLAS on 1 thread; fixed-point "
+                       f"iterations {out['iters']}"),
+            "seconds": out["seconds"], "iters": out["iters"]}
 
 
 # ------------------------------------------------------ extra measurements
@@ -235,65 +319,6 @@ def full_order_measure(ctx, torch, dev, flush, reps: int = 5) -> dict:
             "value": units / (med / 1e3), "unit": UNIT, "us_per_step": med * 1e3 / wl.steps,
             "ms_per_200_steps_median": med, "reps": reps,
             "bound": "latency (state 640 KB, on-chip); HBM fraction not meaningful"}
-
-
-def precision_measure(ctx, torch, dev, flush, steps: int = 4, warm: int = 1) -> dict:
-    """Precision form on the bump-on-tail workload: N = 1e6, p = 256,
-    Nx = 256, dt = 0.1, Philox-seeded loading on the device, rank 2n in [16, 64] chosen
-    at t = 0 by tail energy < 1e-8.  The same start is stepped with FP32 row
-    work (arith 2, FP64 re-orthonormalisation and energies) and with
-    double-float row work (arith 1, FP64-accurate); errors compare the two
-    energy traces."""
-    from paper_2201_05555_gb300 import make_grid
-    N, p, Nx, dt = 1_000_000, 256, 256, 0.1
-    etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
-    rows = torch.tensor([[e["vb"], e["alpha"], e["sigma_b"]] for e in etas], device=dev)
-    X, V = ctx.load_particles(2, N, rows, mode=1, seed=W.BASE_SEED)
-    Q, Z, sig, n = ctx.init_csvd_rank(X, V, 8, 32, 1e-8)
-    Q, Z = Q.clone(), Z.clone()
-    ctx.sync_status()
-    del X, V
-    torch.cuda.empty_cache()
-    grid = make_grid(N, Nx, W.BUMP_ON_TAIL.L)
-    stream = torch.cuda.current_stream(dev)
-    out, traces = {}, {}
-    for arith in (1, 2):
-        Qa, Za, Ka = Q.clone(), Z.clone(), torch.zeros_like(Z)
-        trs = []
-        for _ in range(warm):
-            tr, _ = ctx.basis_update(grid, Qa, Za, dt, 1, arith=arith, kstate=Ka,
-                                     reortho=arith == 2)
-            trs.append(tr)
-        ev = _events(torch, steps)
-        its = []
-        for s_ in range(steps):
-            flush.zero_()
-            ev[s_][0].record(stream)
-            tr, it = ctx.basis_update(grid, Qa, Za, dt, 1, arith=arith, kstate=Ka,
-                                      reortho=arith == 2)
-            ev[s_][1].record(stream)
-            trs.append(tr)
-            its.append(it)
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        traces[arith] = torch.cat(trs).cpu().numpy()
-        out[arith] = {"value": N * p * steps / (ms / 1e3), "ms_per_step": ms / steps,
-                      "fixed_point_iters": [int(i[0]) for i in its]}
-        del Qa, Za, Ka
-    ref, lo = traces[1], traces[2]
-    errE = float(np.max(np.abs(lo[..., 0] - ref[..., 0]) / np.abs(ref[..., 0])))
-    errH = float(np.max(np.abs(lo[..., 1] - ref[..., 1]) / np.abs(ref[..., 1])))
-    return {"workload": f"bump-on-tail precision form, N=1e6 x p=256, Nx=256, dt=0.1, "
-                        f"Philox-seeded loading, 2n={2 * n} (tail energy < 1e-8 in [16, 64])",
-            "value": out[2]["value"], "unit": UNIT, "ms_per_step": out[2]["ms_per_step"],
-            "arith": "FP32 N-row work, FP64 Grams/small dense/re-orthonormalisation/energies",
-            "fixed_point_iters": out[2]["fixed_point_iters"],
-            "fp64_form": {"value": out[1]["value"], "ms_per_step": out[1]["ms_per_step"],
-                          "arith": "double-float N-row work (FP64-accurate)",
-                          "fixed_point_iters": out[1]["fixed_point_iters"]},
-            "speedup_vs_fp64_form": out[2]["value"] / out[1]["value"],
-            "max_rel_err_E": errE, "max_rel_err_H": errH,
-            "err_steps": warm + steps, "rank_2n": 2 * n}
 
 
 def batched_measure(args, ctx, torch, dev, flush) -> dict:
@@ -618,31 +643,48 @@ def main():
 
 
 def only(args):
-    """One extra measurement on GPU 0, printed as its own JSON line."""
+    """One measurement on GPU 0, printed as its own JSON line (profiling runs)."""
     import torch
 
     from paper_2201_05555_gb300 import Context
     dev = torch.device("cuda", 0)
     ctx = Context(0)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.only == "head":
+        Q, Z, n, grid = head_setup(ctx, torch, dev, 0)
+        ctx.autotune(grid, Q, Z, arith=2, reps=3)
+        K = torch.zeros_like(Z)
+        for _ in range(max(args.warmup, 1) + args.steps):
+            ctx.basis_update(grid, Q, Z, HEAD["dt"], 1, trace=True, arith=2, kstate=K,
+                             reortho=True)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        print(json.dumps({"head": {"steps": max(args.warmup, 1) + args.steps, "rank_2n": 2 * n}}))
+        return 0
     fn = {"hyper": lambda: hyper_measure(ctx, torch, dev, flush),
           "dmd": lambda: dmd_measure(ctx, torch, dev),
           "deim_build": lambda: deim_build_measure(ctx, torch, dev),
           "subsampled": lambda: subsample_measure(ctx, torch, dev, flush),
-          "precision": lambda: precision_measure(ctx, torch, dev, flush)}[args.only]
+          "forms": lambda: head_forms_measure(ctx, torch, dev, flush)}[args.only]
     print(json.dumps({args.only: fn()}))
     return 0
 
 
 def reference_arm(args, rank, world):
+    """The oracle timed on the host cores on the headline's metric and unit:
+    each step is a PRK2 step of a bounded sample of the headline workload
+    (fewer particles per sample, sized so that warm-up and timed steps take
+    about two and a half minutes of one host thread)."""
     if rank != 0:
         return 0
-    res = cpu_baseline(max(1, args.steps if args.steps <= 3 else 2))
+    n_part = int(max(2000, min(CPU_SAMPLE_N, 1.5e5 / max(1, args.steps + args.warmup))))
+    with tempfile.TemporaryDirectory() as td:
+        res = oracle_head_sample(n_part, args.steps, args.warmup, os.path.join(td, "s.npz"))
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": (WL["N"] * WL["p"] / res["value"] * 1e3) if res.get("value") else None,
+            "n_gpus": args.gpus, "steps": res["steps"], "warmup": args.warmup,
+            "ms_per_step": res["seconds"] / res["steps"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(world),
+            "data": "synthetic", "config": config_dict(world, 2 * HEAD["n_max"]),
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -667,21 +709,200 @@ def job_throughput(units_per_step: float, steps: int, world: int, ms: float) -> 
     return units_per_step * steps * world / (ms / 1e3)
 
 
-def config_dict(world):
-    return {"workload": "two-stream reduced model, N=1e5 particles x p=64 samples, 2n=20, "
-                        "Nx=128, dt=0.05, FP64",
-            "N": WL["N"], "p": WL["p"], "rank_2n": WL["n2"], "Nx": WL["Nx"], "dt": WL["dt"],
-            "loading": "seeded per sample", "parallelism": f"replicas x{world}",
-            "arithmetic": ("FP64 storage; particle loops in double-float (Dot2), small dense "
-                           "and reductions FP64" if ARITH == 1 else "FP64"),
-            "fixed_point": "tol 1e-9, or a q-cycle, q in 2..4 (|k_m - k_m-q| <= 1e-9 |k_m| and <= 1e-2 |k_m - k_m-1|, amplitude <= 1e-3), warm start from k2",
-            "l2": "flushed between timed steps (256 MiB write)"}
+FIXED_POINT = ("tol 1e-9 (raised to 1e-6 for FP32 rows), or a q-cycle, q in 2..4 "
+               "(|k_m - k_m-q| <= tol |k_m| and <= 1e-2 |k_m - k_m-1|), or a plateau (update "
+               "not halved over 8 iterations), both at an update <= 1e-3; warm start from k2")
+
+
+def config_dict(world, n2):
+    return {"workload": (f"bump-on-tail reduced model, precision form: N=1e6 particles x p=256 "
+                         f"samples, 2n={n2} (tail energy < 1e-8, 2n in [16, 64]), Nx=256, dt=0.1"),
+            "N": HEAD["N"], "p": HEAD["p"], "rank_2n": n2, "Nx": HEAD["Nx"], "dt": HEAD["dt"],
+            "loading": "Philox-seeded per sample on the device (beam velocity on a Hammersley "
+                       "set in [4, 5], alpha 0.04, beam width 0.5)",
+            "parallelism": f"replicas x{world}",
+            "arithmetic": ("FP32 row work (reconstruction, deposit, projection, Gamma zeta^H, Grams, "
+                           "row updates); FP64 storage of Q and Z, cross-block reductions, small "
+                           "dense algebra, re-orthonormalisation factor and the energy check"),
+            "fixed_point": FIXED_POINT,
+            "l2": "flushed between timed steps (256 MiB write); Q (512 MB) exceeds L2"}
+
+
+def head_setup(ctx, torch, dev, rank):
+    """Headline state on the device: Philox-seeded loading, truncated complex
+    SVD start with the rank chosen by tail energy (input preparation, not
+    timed)."""
+    from paper_2201_05555_gb300 import make_grid
+    etas = W.hammersley_params(HEAD["p"], {"vb": HEAD["vb"]},
+                               {"alpha": HEAD["alpha"], "sigma_b": HEAD["sigma_b"]})
+    rows = torch.tensor([[e["vb"], e["alpha"], e["sigma_b"]] for e in etas], device=dev)
+    X, V = ctx.load_particles(2, HEAD["N"], rows, mode=1, seed=W.BASE_SEED + 1000 * rank)
+    Q, Z, _, n = ctx.init_csvd_rank(X, V, HEAD["n_min"], HEAD["n_max"], HEAD["rank_tol"])
+    Q, Z = Q.clone(), Z.clone()
+    ctx.sync_status()
+    del X, V
+    torch.cuda.empty_cache()
+    return Q, Z, n, make_grid(HEAD["N"], HEAD["Nx"], W.BUMP_ON_TAIL.L)
+
+
+def kernel_flop(kern, N, n, p):
+    """Algorithmic flop per launch of the particle kernels (per particle-sample:
+    the position Re(Q_l zeta_i), 2n multiply-adds, for the deposit; the
+    projection's 2n multiply-adds, plus 2n for the FP64 form, which recomputes
+    the position; Gamma zeta^H: V_r (2n) and the complex product (4n))."""
+    per = {"k_deposit_lp": 4 * n, "k_deposit_lp_diag": 4 * n, "k_deposit_reduced": 4 * n,
+           "k_project_lp": 4 * n, "k_project": 8 * n, "k_basis_M_lp": 12 * n,
+           "k_basis_M": 12 * n}.get(kern)
+    return None if per is None else N * p * per
+
+
+def working_launches(kern, rounds, steps, launches):
+    """Launches of `kern` that did work: every fixed-point round (later rounds
+    exit at once on the converged flag) and, for the deposit, the field at the
+    entering state and at the third stage of every step; the basis kernel twice
+    per step."""
+    if kern in ("k_deposit_lp", "k_deposit_reduced"):
+        return rounds + 2 * steps
+    if kern in ("k_project_lp", "k_project"):
+        return rounds
+    if kern in ("k_basis_M_lp", "k_basis_M"):
+        return 2 * steps
+    return launches
+
+
+def kernel_roof(prof, kern, N, n, p, rounds, steps, peak, basis):
+    l, _, kms = prof[kern]
+    fl = kernel_flop(kern, N, n, p)
+    real = working_launches(kern, rounds, steps, l)
+    achieved = fl * real / (kms / 1e3) / 1e12 if (fl and kms > 0) else None
+    return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": profiled_traffic(kern), "launches": l, "working_launches": real,
+            "ms_total": kms, "ms_per_working_launch": kms / real if real else None,
+            "peak_basis": basis, "flop_per_launch": fl}
+
+
+def kernel_shares(ctx, run):
+    """Share of each kernel in the event-timed launches of `run()` (every
+    launch timed; a profiling pass outside the timed region)."""
+    from paper_2201_05555_gb300.binding import KERNELS
+    ctx.profile_reset()
+    ctx.profile_enable(list(range(len(KERNELS))))
+    run()
+    ctx.profile_enable([])
+    prof = ctx.profile_read()
+    tot = sum(v[2] for v in prof.values()) or 1.0
+    return sorted(((k, v[2] / tot) for k, v in prof.items() if v[2] > 0), key=lambda x: -x[1])
+
+
+def timed_form(ctx, torch, dev, flush, grid, Q, Z, dt, arith, steps, warm, reortho, trace=True,
+               after_warmup=None):
+    """`warm` untimed then `steps` timed warm-started steps of one form, each
+    bracketed by CUDA events on the launch stream (L2 flushed before each);
+    after_warmup() runs between the two."""
+    stream = torch.cuda.current_stream(dev)
+    K = torch.zeros_like(Z)
+    for _ in range(warm):
+        ctx.basis_update(grid, Q, Z, dt, 1, trace=trace, arith=arith, kstate=K, reortho=reortho)
+    if after_warmup:
+        torch.cuda.synchronize()
+        after_warmup()
+    ev = _events(torch, steps)
+    its = []
+    for s_ in range(steps):
+        flush.zero_()
+        ev[s_][0].record(stream)
+        _, it = ctx.basis_update(grid, Q, Z, dt, 1, trace=trace, arith=arith, kstate=K,
+                                 reortho=reortho)
+        ev[s_][1].record(stream)
+        its.append(it)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return ms, [int(i[0]) for i in its]
+
+
+def head_forms_measure(ctx, torch, dev, flush, steps: int = 2) -> dict:
+    """The headline state stepped in the FP64 form (arith 0) and in the
+    double-float form (arith 1), FP64-accurate, from the same start as the
+    precision form; CUDA events per step."""
+    Q0, Z0, n, grid = head_setup(ctx, torch, dev, 0)
+    out = {}
+    for arith, name in ((0, "fp64_form"), (1, "double_float_form")):
+        Q, Z = Q0.clone(), Z0.clone()
+        ms, its = timed_form(ctx, torch, dev, flush, grid, Q, Z, HEAD["dt"], arith, steps, 1,
+                             False)
+        out[name] = {"value": HEAD["N"] * HEAD["p"] / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms, "steps": steps, "fixed_point_iters": its,
+                     "dtype": "f64" if arith == 0 else "df64",
+                     "arith": ("FP64 throughout" if arith == 0 else
+                               "double-float row work (pairs of FP32, Dot2), FP64 small dense")}
+        del Q, Z
+        torch.cuda.empty_cache()
+    return out
+
+
+def two_stream_measure(ctx, torch, dev, flush, arith, start, steps: int = 20) -> dict:
+    """The two-stream reduced workload (N = 1e5, p = 64, 2n = 20, Nx = 128,
+    dt = 0.05) in the FP64 form (arith 0) or the double-float form (arith 1):
+    warm-started steps timed with CUDA events, the roofline of the deposit, and
+    the error of one cold step from the oracle's start against the oracle."""
+    from paper_2201_05555_gb300 import make_grid
+    wl = W.two_stream_reduced(N=WL["N"], p=WL["p"], Nx=WL["Nx"], n2=WL["n2"], dt=WL["dt"])
+    n = wl.n2 // 2
+    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    out = {}
+    if start is not None:  # (U0, Z0, U1, Z1) of the oracle
+        U0, Z0, U1, Z1 = start
+        N = wl.N
+        Q = torch.tensor(np.ascontiguousarray(np.hstack([U0[:N, :n], U0[N:, :n]])), device=dev)
+        Z = torch.tensor(np.ascontiguousarray(Z0), device=dev)
+        ctx.basis_update(grid, Q, Z, wl.dt, 1, trace=False, arith=arith)
+        ctx.sync_status()
+        Qh, Zh = Q.cpu().numpy(), Z.cpu().numpy()
+        Xg = Qh[:, :n] @ Zh[:n] - Qh[:, n:] @ Zh[n:]
+        Vg = Qh[:, n:] @ Zh[:n] + Qh[:, :n] @ Zh[n:]
+        Xo, Vo = U1[:N] @ Z1, U1[N:] @ Z1
+        out["error_vs_oracle_one_step"] = {
+            "UZ_rel": float(np.sqrt((np.linalg.norm(Xg - Xo) ** 2 + np.linalg.norm(Vg - Vo) ** 2)
+                                    / (np.linalg.norm(Xo) ** 2 + np.linalg.norm(Vo) ** 2))),
+            "Z_rel": float(np.linalg.norm(Zh - Z1) / np.linalg.norm(Z1)),
+            "how": "one cold PRK2 step from the oracle's complex-SVD start, device vs oracle"}
+    else:
+        X0, V0 = W.load_batch(wl.family, wl.etas, wl.N, quiet=wl.quiet, seed=W.BASE_SEED)
+        Q, Z, _ = ctx.init_csvd(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev), n)
+    if arith:
+        ctx.autotune(grid, Q, Z, arith=arith, reps=5)
+    KD = "k_deposit_lp" if arith else "k_deposit_reduced"
+
+    def profile_on():
+        ctx.profile_reset()
+        ctx.profile_enable([KD])
+
+    ms, its = timed_form(ctx, torch, dev, flush, grid, Q, Z, wl.dt, arith, steps, 3, False,
+                         after_warmup=profile_on)
+    ctx.profile_enable([])
+    prof = ctx.profile_read()
+    peak = DF_PEAK_TFLOPS if arith == 1 else FP64_PEAK_TFLOPS
+    basis = ("double-float Dot2: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 flop / 12 FP32 "
+             "instructions per emulated FP64 FMA" if arith == 1 else
+             "FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2.07 GHz, measured 1.19 TFLOP/s")
+    roof = kernel_roof(prof, KD, wl.N, n, wl.p, sum(its), steps, peak, basis)
+    out.update({"workload": ("two-stream reduced model, N=1e5 particles x p=64 samples, 2n=20, "
+                             "Nx=128, dt=0.05, seeded loading per sample"),
+                "dtype": "f64" if arith == 0 else "df64",
+                "arith": ("FP64 throughout" if arith == 0 else
+                          "double-float row work (pairs of FP32, Dot2, ~48 significant bits), "
+                          "FP64 storage, reductions and small dense algebra"),
+                "value": wl.N * wl.p / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                "steps": steps, "fixed_point_iters": its, "roofline": roof})
+    return out
 
 
 def ours(args, rank, world):
     import torch
 
-    from paper_2201_05555_gb300 import Context, make_grid
+    from paper_2201_05555_gb300 import Context
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -691,44 +912,39 @@ def ours(args, rank, world):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     ctx = Context(local)
+    N, p, dt = HEAD["N"], HEAD["p"], HEAD["dt"]
 
-    wl, X0, V0 = initial_state(rank)
-    n = wl.n2 // 2
-    # truncated complex SVD start on the device (setup, not timed)
-    Q, Z, _ = ctx.init_csvd(torch.tensor(X0, device=dev), torch.tensor(V0, device=dev), n)
-    ctx.sync_status()
-    grid = make_grid(wl.N, wl.Nx, wl.family.L)
+    Q, Z, n, grid = head_setup(ctx, torch, dev, rank)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-
     # launch shapes of the particle kernels chosen on this state (setup, not timed)
-    tuned = ctx.autotune(grid, Q, Z, arith=ARITH, reps=5) if ARITH else None
+    tuned = ctx.autotune(grid, Q, Z, arith=2, reps=3)
     kstate = torch.zeros_like(Z)  # warm start of the fixed point (previous step's k2)
 
-    def step(Qt, Zt, trace=True, arith=ARITH):
-        return ctx.basis_update(grid, Qt, Zt, wl.dt, 1, trace=trace, iters=True, arith=arith,
-                                kstate=kstate)
+    def step(Qt, Zt, Kt):
+        return ctx.basis_update(grid, Qt, Zt, dt, 1, trace=True, iters=True, arith=2,
+                                kstate=Kt, reortho=True)
 
     for _ in range(args.warmup):
-        step(Q, Z)
+        step(Q, Z, kstate)
     torch.cuda.synchronize()
+    # kernel shares of one step (every launch event-timed; outside the timed region)
+    shares = kernel_shares(ctx, lambda: step(Q, Z, kstate))
+    roof_kernels = [k for k, _ in shares if kernel_flop(k, N, n, p)][:3]
 
     # ---- timed region: device-resident state
-    KP = "k_project_lp" if ARITH else "k_project"
-    KD = "k_deposit_lp" if ARITH else "k_deposit_reduced"
     ctx.profile_reset()
-    ctx.profile_enable([KD, KP])
+    ctx.profile_enable(roof_kernels)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    ev = _events(torch, args.steps)
     iters = []
     with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.zero_()
             ev[s][0].record(stream)
-            _, it = step(Q, Z)
+            _, it = step(Q, Z, kstate)
             ev[s][1].record(stream)
             iters.append(it)
         torch.cuda.synchronize()
@@ -742,73 +958,82 @@ def ours(args, rank, world):
     its = [int(i[0]) for i in iters]
     ms = max_over_ranks(ms, dist, dev)
 
-    # ---- end to end through host buffers: H2D state, one step, D2H state
+    # ---- end to end through host buffers: H2D state, one step, D2H state and energies
     Qh = Q.cpu().pin_memory()
     Zh = Z.cpu().pin_memory()
-    Qd, Zd = torch.empty_like(Q), torch.empty_like(Z)
-    trh = torch.empty((1, wl.p, 2), dtype=torch.float64).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+    Kh = kstate.cpu().pin_memory()
+    Qd, Zd, Kd = torch.empty_like(Q), torch.empty_like(Z), torch.empty_like(kstate)
+    trh = torch.empty((1, p, 2), dtype=torch.float64).pin_memory()
+    e2e_ev = _events(torch, args.steps)
+    e2e_its = []
     torch.cuda.synchronize()
     for s in range(args.steps):
         flush.zero_()
         e2e_ev[s][0].record(stream)
         Qd.copy_(Qh, non_blocking=True)
         Zd.copy_(Zh, non_blocking=True)
-        tr, _ = step(Qd, Zd)
+        Kd.copy_(Kh, non_blocking=True)
+        tr, it = step(Qd, Zd, Kd)
         Qh.copy_(Qd, non_blocking=True)
         Zh.copy_(Zd, non_blocking=True)
+        Kh.copy_(Kd, non_blocking=True)
         trh.copy_(tr, non_blocking=True)
         e2e_ev[s][1].record(stream)
+        e2e_its.append(it)
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e_its = [int(i[0]) for i in e2e_its]
 
-    units_step = wl.N * wl.p
+    units_step = N * p
     value = job_throughput(units_step, args.steps, world, ms)
     e2e_value = job_throughput(units_step, args.steps, world, e2e_ms)
-    state_bytes = Q.numel() * 8 + Z.numel() * 8
+    state_bytes = (Q.numel() + Z.numel() + kstate.numel()) * 8
 
-    # ---- roofline of the dominant kernel (the deposit, largest share of the
-    # step in the launch list) and of the projection beside it; both ALU bound
-    peak = DF_PEAK_TFLOPS if ARITH == 1 else FP64_PEAK_TFLOPS
-    basis = ("double-float Dot2: 152 SMs x 128 FP32 lanes x 2.07 GHz x 2 flop / 12 FP32 "
-             "instructions per emulated FP64 FMA" if ARITH == 1 else
-             "FP64: 152 SMs x 4 flop/clk/SM (2 DFMA) x 2.07 GHz, measured 1.19 TFLOP/s")
-
-    def kernel_roof(kern, flop_per_launch, real):
-        l, _, kms = prof[kern]
-        achieved = flop_per_launch * real / (kms / 1e3) / 1e12 if kms > 0 else None
-        return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": profiled_traffic(kern), "launches": l, "working_launches": real,
-                "ms_total": kms, "peak_basis": basis, "flop_per_launch": flop_per_launch}
-
-    # algorithmic FP64 flop per launch, per particle-sample: the deposit's
-    # position 2n FMA; the projection 2n FMA (+ 2n for the position when the
-    # FP64 form recomputes it).  Working launches: every fixed-point round that
-    # did work (the rest exit on the converged flag) and, for the deposit, the
-    # two other field evaluations of each step (entering state, stage 3)
+    # ---- roofline of the dominant kernel (largest share of the step among the
+    # particle kernels) and of the next two; FP32 SIMT, ALU bound
+    basis = "FP32: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz"
     rounds = sum(its)
-    roof = kernel_roof(KD, units_step * 4 * n,
-                       rounds + 2 * args.steps if ARITH == 1 else prof[KD][0])
-    roof_proj = kernel_roof(KP, units_step * (4 if ARITH == 1 else 8) * n, rounds)
+    roofs = [kernel_roof(prof, k, N, n, p, rounds, args.steps, FP32_PEAK_TFLOPS, basis)
+             for k in roof_kernels]
     clocks = clk.summary()
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(world),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(world, 2 * n),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes + trh.numel() * 8},
-            "gpu_launches": total_launches, "roofline": roof, "roofline_project": roof_proj,
-            "clocks": clocks,
-            "autotuned_blocks_per_sm": tuned,
-            "fixed_point_iters": its}
+                    "d2h_bytes_per_step": state_bytes + trh.numel() * 8,
+                    "ms_per_step": e2e_ms / args.steps, "fixed_point_iters": e2e_its},
+            "gpu_launches": total_launches, "roofline": roofs[0] if roofs else None,
+            "roofline_next": roofs[1:],
+            "kernel_share": {k: round(f, 3) for k, f in shares[:10]},
+            "clocks": clocks, "autotuned_blocks_per_sm": tuned, "fixed_point_iters": its,
+            "accuracy": ("FP32 form against the FP64 oracle (tests/test_gpu_precision.py): "
+                         "relative H and E errors <= 5e-7 after one step; over 200 steps H "
+                         "within 1.4e-5 and E within 2.2e-6 of its largest value")}
+    del Qd, Zd, Kd
     if not args.no_extras and world == 1:
+        del Q, Z, kstate
+        torch.cuda.empty_cache()
+        forms = head_forms_measure(ctx, torch, dev, flush)
+        line["fp64_form"] = forms["fp64_form"]
+        line["double_float_form"] = forms["double_float_form"]
+        line["speedup_vs_fp64_form"] = value / forms["fp64_form"]["value"]
+        line["speedup_vs_double_float_form"] = value / forms["double_float_form"]["value"]
+        start, c2_cpu = None, None
+        if not args.no_cpu_baseline:
+            with tempfile.TemporaryDirectory() as td:
+                path = os.path.join(td, "c2.npz")
+                c2_cpu = oracle_two_stream_step(path)
+                d = np.load(path)
+                start = (d["U"], d["Z"], d["U1"], d["Z1"])
+        line["two_stream_fp64"] = two_stream_measure(ctx, torch, dev, flush, 0, start)
+        line["two_stream_double_float"] = two_stream_measure(ctx, torch, dev, flush, 1, start)
+        if c2_cpu:
+            line["two_stream_cpu_baseline"] = c2_cpu
         line["full_order"] = full_order_measure(ctx, torch, dev, flush)
-        line["precision_form"] = precision_measure(ctx, torch, dev, flush)
         line["batched"] = batched_measure(args, ctx, torch, dev, flush)
         line["subsampled"] = subsample_measure(ctx, torch, dev, flush)
         line["hyper"] = hyper_measure(ctx, torch, dev, flush)
@@ -816,7 +1041,9 @@ def ours(args, rank, world):
         line["dmd"] = dmd_measure(ctx, torch, dev)
         line["served"] = served_measure(args, local)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        with tempfile.TemporaryDirectory() as td:
+            line["cpu_baseline"] = oracle_head_sample(CPU_SAMPLE_N, 1, 0,
+                                                      os.path.join(td, "s.npz"))
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
