@@ -89,6 +89,13 @@ def parse():
     ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
+    ap.add_argument("--sharded", action="store_true",
+                    help="with N > 1 ranks: one particle-sharded problem of N x 1e6 particles per "
+                         "sample (vp_ctx_set_comm over NCCL) instead of N replicas")
+    ap.add_argument("--no-tc", action="store_true",
+                    help="FP32 SIMT kernels only (no tensor-core kernels)")
+    ap.add_argument("--head-n", type=int, default=HEAD["N"],
+                    help="particles per sample of the headline workload in --only head")
     ap.add_argument("--only", choices=["head", "hyper", "dmd", "deim_build", "subsampled", "forms"],
                     default=None,
                     help="run one extra measurement alone and print its JSON (profiling runs)")
@@ -650,7 +657,10 @@ def only(args):
     dev = torch.device("cuda", 0)
     ctx = Context(0)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.no_tc:
+        ctx.tensor_cores(False)
     if args.only == "head":
+        HEAD["N"] = args.head_n
         Q, Z, n, grid = head_setup(ctx, torch, dev, 0)
         ctx.autotune(grid, Q, Z, arith=2, reps=3)
         K = torch.zeros_like(Z)
@@ -728,6 +738,29 @@ def config_dict(world, n2):
             "l2": "flushed between timed steps (256 MiB write); Q (512 MB) exceeds L2"}
 
 
+def head_setup_sharded(ctx, torch, dev, rank, world, dist):
+    """Particle-sharded headline state: every rank loads N particles per sample
+    of its own (seeded by rank) and takes its truncated complex SVD at the
+    headline's rank; the stacked blocks Q_r / sqrt(world) form an orthonormal
+    basis of the whole problem, and zeta = sum_r Q_r^H R0_r / sqrt(world) its
+    coefficients (summed over the ranks once, at set-up)."""
+    from paper_2201_05555_gb300 import make_grid
+    etas = W.hammersley_params(HEAD["p"], {"vb": HEAD["vb"]},
+                               {"alpha": HEAD["alpha"], "sigma_b": HEAD["sigma_b"]})
+    rows = torch.tensor([[e["vb"], e["alpha"], e["sigma_b"]] for e in etas], device=dev)
+    X, V = ctx.load_particles(2, HEAD["N"], rows, mode=1, seed=W.BASE_SEED + 1000 * rank)
+    n = HEAD["n_max"]
+    Q, Z, _ = ctx.init_csvd(X, V, n)
+    ctx.sync_status()
+    Q = Q / world ** 0.5
+    dist.all_reduce(Z)
+    Z = Z / world ** 0.5
+    del X, V
+    torch.cuda.empty_cache()
+    return Q.contiguous(), Z.contiguous(), n, make_grid(HEAD["N"] * world, HEAD["Nx"],
+                                                        W.BUMP_ON_TAIL.L)
+
+
 def head_setup(ctx, torch, dev, rank):
     """Headline state on the device: Philox-seeded loading, truncated complex
     SVD start with the rank chosen by tail energy (input preparation, not
@@ -750,9 +783,9 @@ def kernel_flop(kern, N, n, p):
     the position Re(Q_l zeta_i), 2n multiply-adds, for the deposit; the
     projection's 2n multiply-adds, plus 2n for the FP64 form, which recomputes
     the position; Gamma zeta^H: V_r (2n) and the complex product (4n))."""
-    per = {"k_deposit_lp": 4 * n, "k_deposit_lp_diag": 4 * n, "k_deposit_reduced": 4 * n,
-           "k_project_lp": 4 * n, "k_project": 8 * n, "k_basis_M_lp": 12 * n,
-           "k_basis_M": 12 * n}.get(kern)
+    per = {"k_deposit_lp": 4 * n, "k_deposit_tc": 4 * n, "k_deposit_lp_diag": 4 * n,
+           "k_deposit_reduced": 4 * n, "k_project_lp": 4 * n, "k_project_tc": 4 * n,
+           "k_project": 8 * n, "k_basis_M_lp": 12 * n, "k_basis_M": 12 * n}.get(kern)
     return None if per is None else N * p * per
 
 
@@ -761,9 +794,9 @@ def working_launches(kern, rounds, steps, launches):
     exit at once on the converged flag) and, for the deposit, the field at the
     entering state and at the third stage of every step; the basis kernel twice
     per step."""
-    if kern in ("k_deposit_lp", "k_deposit_reduced"):
+    if kern in ("k_deposit_lp", "k_deposit_tc", "k_deposit_reduced"):
         return rounds + 2 * steps
-    if kern in ("k_project_lp", "k_project"):
+    if kern in ("k_project_lp", "k_project_tc", "k_project"):
         return rounds
     if kern in ("k_basis_M_lp", "k_basis_M"):
         return 2 * steps
@@ -907,18 +940,27 @@ def ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
-    if world > 1:
+    if world > 1 or args.sharded:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     ctx = Context(local)
+    if args.no_tc:
+        ctx.tensor_cores(False)
     N, p, dt = HEAD["N"], HEAD["p"], HEAD["dt"]
 
-    Q, Z, n, grid = head_setup(ctx, torch, dev, rank)
+    sharded = args.sharded and dist is not None
+    if sharded:
+        Q, Z, n, grid = head_setup_sharded(ctx, torch, dev, rank, world, dist)
+    else:
+        Q, Z, n, grid = head_setup(ctx, torch, dev, rank)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     # launch shapes of the particle kernels chosen on this state (setup, not timed)
-    tuned = ctx.autotune(grid, Q, Z, arith=2, reps=3)
+    tuned = None if sharded else ctx.autotune(grid, Q, Z, arith=2, reps=3)
+    if sharded:  # sums over the ranks' particles through NCCL
+        from paper_2201_05555_gb300.binding import RankComm
+        RankComm(lambda t: dist.all_reduce(t), HEAD["N"] * world).attach(ctx)
     kstate = torch.zeros_like(Z)  # warm start of the fixed point (previous step's k2)
 
     def step(Qt, Zt, Kt):
@@ -1002,7 +1044,9 @@ def ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(world, 2 * n),
+            "config": dict(config_dict(world, 2 * n), **(
+                {"parallelism": f"particle-sharded x{world} (N={HEAD['N']} per rank, sums over "
+                                f"ranks by NCCL all-reduce)"} if sharded else {})),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes + trh.numel() * 8,
                     "ms_per_step": e2e_ms / args.steps, "fixed_point_iters": e2e_its},
@@ -1014,7 +1058,7 @@ def ours(args, rank, world):
                          "relative H and E errors <= 5e-7 after one step; over 200 steps H "
                          "within 1.4e-5 and E within 2.2e-6 of its largest value")}
     del Qd, Zd, Kd
-    if not args.no_extras and world == 1:
+    if not args.no_extras and world == 1 and not sharded:
         del Q, Z, kstate
         torch.cuda.empty_cache()
         forms = head_forms_measure(ctx, torch, dev, flush)

@@ -60,7 +60,8 @@ typedef enum vp_status {
   VP_ENUMERIC = 7,     /* non-finite value or singular small system */
   VP_EDRIFT = 8,       /* basis left the ortho-symplectic manifold */
   VP_ECUDA = 9,        /* a CUDA runtime call failed */
-  VP_EUNSUPPORTED = 10 /* size outside the compiled limits */
+  VP_EUNSUPPORTED = 10, /* size outside the compiled limits, or a call not available */
+  VP_ECOMM = 11         /* a sum of the attached communicator (vp_ctx_set_comm) failed */
 } vp_status;
 
 typedef struct vp_ctx vp_ctx;
@@ -134,6 +135,40 @@ vp_status vp_ctx_sync_status(vp_ctx* ctx, void* stream);
 /* Bytes of workspace currently held by the context. */
 size_t vp_ctx_workspace_bytes(const vp_ctx* ctx);
 int32_t vp_version(void);
+
+/* --------------------------------------------------- particle sharding */
+/* The reduced model shards over particles (Sec. 3.2: every N-row quantity
+ * of the reduced vector field -- X_r = U_X Z, the deposit, the gather, the
+ * projection U^T G, Gamma zeta^H and the row updates of the Cayley
+ * retraction -- is a sum or a map over the rows of U).  A rank holds the rows
+ * of its own particles; the sums over rows are the only exchange:
+ * the p x Nx charge counts (int64 fixed point, exact in any order), the
+ * 2n x p projection and the small Gram matrices of the basis stages, of the
+ * retraction and of the tangent velocity (FP64).  Poisson, the small dense
+ * algebra, the fixed-point decision and the coefficient update then run
+ * redundantly and identically on every rank. */
+typedef struct vp_comm {
+  /* In-place sum over the ranks of `count` values at the device pointer buf
+   * (FP64, or the unsigned 64-bit charge counts), ordered on `stream` (a
+   * cudaStream_t as void*): the library's earlier work on stream has written
+   * buf, and its later work reads the sum.  Called on the host thread that
+   * called the library, the same number of times and with the same counts on
+   * every rank.  Returns 0 on success. */
+  int (*sum_f64)(void* user, double* buf, int64_t count, void* stream);
+  int (*sum_u64)(void* user, uint64_t* buf, int64_t count, void* stream);
+  void* user;        /* passed back to both */
+  int64_t n_global;  /* particles per sample over all ranks (fixed-point scales) */
+} vp_comm;
+
+/* Attach a communicator to ctx (copied; comm = NULL detaches).  With one
+ * attached, vp_basis_update and vp_reduced_energy take Q_dev as this rank's
+ * N rows and Z as the full (replicated) coefficients, and give on every rank
+ * the results of the whole problem (n_global particles per sample): Q_dev
+ * this rank's rows of the new basis, Z, traces, energies and iteration counts
+ * identical on every rank.  The parameter subsample (nsub) is supported; the
+ * other reduced-model and hyper-reduction calls return VP_EUNSUPPORTED while a
+ * communicator is attached.  A failed sum makes the call return VP_ECOMM. */
+vp_status vp_ctx_set_comm(vp_ctx* ctx, const vp_comm* comm);
 
 /* ------------------------------------------------------ particle-grid maps */
 /* a2. rho = Lambda^0(X)^T M_q + b for each of p samples (Sec. 2.1,
@@ -581,6 +616,13 @@ typedef enum vp_tune_knob {
   VP_TUNE_AFFINE_LP, VP_TUNE_COUNT
 } vp_tune_knob;
 vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm);
+/* enable = 1 (default): in the FP32 form (arith = 2) the projection g_X =
+ * U_X^T G (Sec. 3.2, eq. grads) and the reconstruction X_r = U_X Z of the
+ * deposit run on the tensor cores (tcgen05, TF32 operands split in two, FP32
+ * accumulation in tensor memory) when 2n <= 64 (the deposit: 2n a multiple
+ * of 4) and the sample chunk of the particle kernels is 16 or 32 wide;
+ * enable = 0: always the FP32 SIMT kernels.  Other values: VP_EINVAL. */
+vp_status vp_tensor_cores(vp_ctx* ctx, int32_t enable);
 vp_status vp_tune_get(vp_ctx* ctx, int32_t knob, int32_t* blocks_per_sm);
 /* Autotuner: on the caller's state (Q N x 2n, Z 2n x p; read only) times
  * every knob's kernel at 1, 2, 3, 4, 6 and 8 blocks per SM (`reps` launches
@@ -655,7 +697,9 @@ vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
  * VP_K_HYPER the per-interval window and operator work of vp_hyper_step;
  * VP_K_INIT the complex-SVD start and the re-orthonormalisation factor;
  * VP_K_DEPOSIT_DIAG the double-float deposit of the FP64-accurate energy
- * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits. */
+ * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits;
+ * VP_K_PROJECT_TC the projection and VP_K_DEPOSIT_TC the deposit of the FP32
+ * form with their contractions on the tensor cores. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
@@ -663,7 +707,7 @@ typedef enum vp_kernel {
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
-  VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_COUNT
+  VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_PROJECT_TC, VP_K_DEPOSIT_TC, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

@@ -1,6 +1,6 @@
 """Geometric particle-in-cell discretisation (Sec. 2.1) in float64.
 
-Conventions (readings of the paper where it is silent, each listed in DESIGN):
+Conventions (the readings taken where the paper is silent):
 * nodes x_j = j h, j = 0..Nx-1, h = L/Nx, periodic P1 hats
   lambda_j(x) = max(0, 1 - dist_per(x, x_j)/h);
 * a particle at wrapped position x~ lies in cell j = floor(x~/h) (a particle

@@ -20,7 +20,7 @@ _I32, _I64, _D, _SZ = C.c_int32, C.c_int64, C.c_double, C.c_size_t
 
 STATUS = {0: "VP_OK", 1: "VP_EINVAL", 2: "VP_ENOMEM", 3: "VP_EBUSY", 4: "VP_EAGAIN",
           5: "VP_ETIMEDOUT", 6: "VP_ENOCONV", 7: "VP_ENUMERIC", 8: "VP_EDRIFT", 9: "VP_ECUDA",
-          10: "VP_EUNSUPPORTED"}
+          10: "VP_EUNSUPPORTED", 11: "VP_ECOMM"}
 
 
 class VPError(RuntimeError):
@@ -78,6 +78,8 @@ _SIGS = [
     ("vp_deim_gather_project", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _I64, _P,
                                       _P, _P, _P, _P]),
     ("vp_deposit_cic_noalloc", _I32, [C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P]),
+    ("vp_tensor_cores", _I32, [_P, _I32]),
+    ("vp_ctx_set_comm", _I32, [_P, _P]),
     ("vp_init_csvd", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_profile_enable", _I32, [_P, C.c_uint64]),
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
@@ -140,7 +142,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
            "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd", "k_jacobi_sym",
-           "k_deposit_lp_diag"]
+           "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -222,6 +224,10 @@ class Context:
         return int(self.lib.vp_ctx_workspace_bytes(self.h))
 
     # -- profiling (launch counters, CUDA-event timers on the launch stream)
+    def tensor_cores(self, enable: bool):
+        """Use the tcgen05 kernels of the FP32 form where they apply (default on)."""
+        self._check(self.lib.vp_tensor_cores(self.h, int(bool(enable))), "tensor_cores")
+
     def profile_enable(self, kernels=()):
         mask = 0
         for k in kernels:
@@ -627,6 +633,93 @@ def deposit_cic_noalloc(grid: Grid, X: torch.Tensor, rho: torch.Tensor) -> torch
     if s != 0:
         raise VPError(s, "vp_deposit_cic_noalloc")
     return rho
+
+
+# ------------------------------------------------------- particle sharding
+_SUM = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
+
+
+class _CommStruct(C.Structure):
+    """vp_comm: sums over the ranks, called by the library."""
+    _fields_ = [("sum_f64", _SUM), ("sum_u64", _SUM), ("user", _P), ("n_global", _I64)]
+
+
+class _DeviceView:
+    """`count` values at a device pointer, for torch.as_tensor (CUDA array
+    interface); no copy."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+class RankComm:
+    """Particle sharding of a Context (vp_ctx_set_comm): `allreduce(t)` must
+    sum the CUDA tensor t in place over the ranks, ordered after the work
+    queued on the current stream and before the work queued after it (as
+    torch.distributed.all_reduce on an NCCL group does).  The library hands it
+    views of its own buffers: FP64 sums, and the int64 fixed-point charge
+    counts viewed as int64 (two's-complement sums equal the unsigned ones).
+    n_global: particles per sample over all ranks."""
+
+    def __init__(self, allreduce, n_global: int):
+        def f64(user, buf, count, stream):
+            try:
+                allreduce(torch.as_tensor(_DeviceView(buf, count, "<f8"), device="cuda"))
+                return 0
+            except Exception:  # the library reports VP_ECOMM
+                return 1
+
+        def u64(user, buf, count, stream):
+            try:
+                allreduce(torch.as_tensor(_DeviceView(buf, count, "<i8"), device="cuda"))
+                return 0
+            except Exception:
+                return 1
+
+        self._cb = (_SUM(f64), _SUM(u64))  # the library keeps the pointers: keep them alive
+        self.struct = _CommStruct(self._cb[0], self._cb[1], None, int(n_global))
+
+    def attach(self, ctx: "Context"):
+        ctx._comm = self
+        ctx._check(ctx.lib.vp_ctx_set_comm(ctx.h, C.byref(self.struct)), "ctx_set_comm")
+
+    @staticmethod
+    def detach(ctx: "Context"):
+        ctx._check(ctx.lib.vp_ctx_set_comm(ctx.h, None), "ctx_set_comm")
+        ctx._comm = None
+
+
+class LoopbackGroup:
+    """Sums over `world` ranks that are host threads of one process, each with
+    its own Context and stream (one GPU, or one per rank): a rank's sum
+    synchronises its stream and waits at a host barrier for the others; rank
+    0 then adds the buffers in rank order on its stream, writes the sum back
+    to each and synchronises before the barrier is released.  Kernels never
+    wait on one another; the waiting is on the host, between launches.  A
+    barrier that times out fails the sum (the library returns VP_ECOMM)."""
+
+    def __init__(self, world: int, timeout: float = 60.0):
+        import threading
+        self.world = world
+        self.barrier = threading.Barrier(world, timeout=timeout)
+        self.slots = [None] * world
+
+    def allreduce_for(self, rank: int):
+        def allreduce(t):
+            torch.cuda.current_stream().synchronize()
+            self.slots[rank] = t
+            self.barrier.wait()
+            if rank == 0:
+                acc = self.slots[0].clone()
+                for r in range(1, self.world):
+                    acc += self.slots[r]
+                for r in range(self.world):
+                    self.slots[r].copy_(acc)
+                torch.cuda.current_stream().synchronize()
+            self.barrier.wait()
+        return allreduce
 
 
 _default: dict[int, Context] = {}

@@ -19,6 +19,8 @@
 // at the same (Q, zeta).
 #include "vp_internal.cuh"
 
+#include <algorithm>
+
 namespace vpk {
 
 struct ArithDF {
@@ -996,6 +998,16 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_DEPOSIT: {
+      if constexpr (AR::kVec4) {  // FP32 rows: reconstruction on the tensor cores
+        if (A.tc && deposit_tc_supported(n, p, g.Nx, g.Kp)) {
+          const int ch = ceil_div(p, chunk_w(p, g.Nx));
+          const int64_t tiles = ceil_div(N, 128);
+          const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, A.num_sms / ch));
+          deposit_tc(g, N, n, p, (const float*)A.v0, (const float*)A.v1, A.counts, A.j, gx,
+                     A.skip, A.status, st);
+          break;
+        }
+      }
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
       const bool vec = AR::kVec4 && (n & 3) == 0;
@@ -1018,6 +1030,13 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_PROJECT: {
+      if constexpr (AR::kVec4) {  // FP32 rows: tensor cores where the shapes allow
+        if (A.tc && project_tc_supported(n, p, g.Nx)) {
+          project_tc(g, N, n, p, (const float*)A.v0, (const float*)A.v1, A.j, A.part, A.gridx,
+                     A.skip, A.status, st);
+          break;
+        }
+      }
       int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
       const size_t jst = (sizeof(uint16_t) * TILE_ROWS * PC + 15) & ~size_t(15);

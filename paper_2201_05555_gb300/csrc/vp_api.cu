@@ -46,6 +46,16 @@ vp_status vp_workspace(vp_ctx* ctx, size_t bytes, void** out) {
   return VP_OK;
 }
 
+void comm_sum_f64(vp_ctx* ctx, double* buf, int64_t count, cudaStream_t st) {
+  if (!ctx->comm_on || ctx->comm_failed || count <= 0) return;
+  if (ctx->comm.sum_f64(ctx->comm.user, buf, count, (void*)st) != 0) ctx->comm_failed = true;
+}
+void comm_sum_u64(vp_ctx* ctx, unsigned long long* buf, int64_t count, cudaStream_t st) {
+  if (!ctx->comm_on || ctx->comm_failed || count <= 0) return;
+  if (ctx->comm.sum_u64(ctx->comm.user, reinterpret_cast<uint64_t*>(buf), count, (void*)st) != 0)
+    ctx->comm_failed = true;
+}
+
 namespace {
 struct DeviceGuard {
   int prev = -1;
@@ -66,6 +76,13 @@ struct DeviceGuard {
   DeviceGuard guard_(ctx->device);                              \
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);     \
   (void)st;
+
+// Reduced-model calls that do not sum over ranks refuse while a communicator
+// is attached (their results would be this rank's rows only).
+#define VP_NO_COMM()                                                                  \
+  if (ctx->comm_on)                                                                   \
+    return vp_fail(ctx, VP_EUNSUPPORTED, "%s: not available with a communicator attached", \
+                   __func__)
 
 vp_status check_grid(vp_ctx* ctx, const vp_grid* g) {
   if (!g) return vp_fail(ctx, VP_EINVAL, "grid is NULL");
@@ -225,6 +242,7 @@ struct Red {
              const float2* Q2 = nullptr) {
     (void)Q2;
     VP_K(VP_K_DEPOSIT_REDUCED, deposit_reduced(g, N, n, p, Q, Z, w.counts, skip, ctx->num_sms, st));
+    comm_sum_u64(ctx, w.counts, (int64_t)p * g.Nx, st);
     VP_K(VP_K_POISSON, poisson(g, p, nullptr, w.counts, nullptr, w.F, w.Efield, w.counts, skip, ctx->d_status, st));
   }
   // Grams out_s = blk[pa]^H blk[pb] into `out` (npairs x n x n double2)
@@ -242,10 +260,12 @@ struct Red {
     VP_K(VP_K_GRAM, gram(N, n, a, reinterpret_cast<double2*>(w.part), w.gx_gram, st));
     VP_K(VP_K_REDUCE, reduce_partials(w.gx_gram, (int64_t)a.npairs * n * n * 2, w.part,
                     reinterpret_cast<double*>(out), nullptr, st));
+    comm_sum_f64(ctx, reinterpret_cast<double*>(out), (int64_t)a.npairs * n * n * 2, st);
   }
   void gv(const double* Q, double* GVraw) {
     VP_K(VP_K_GRAM_REAL, gram_real(N, 2 * n, Q, w.part, w.gx_gram, st));
     VP_K(VP_K_REDUCE, reduce_partials(w.gx_gram, (int64_t)4 * n * n, w.part, GVraw, nullptr, st));
+    comm_sum_f64(ctx, GVraw, (int64_t)4 * n * n, st);
   }
   void comb(std::initializer_list<const double*> xs, const double2* C, double* out) {
     AffineArgs a{};
@@ -288,7 +308,8 @@ vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, i
   R.n = n;
   R.p = p;
   R.st = st;
-  if (grid) R.g = make_gridc(*grid, N);
+  // fixed-point scales bound the sums over all ranks' particles
+  if (grid) R.g = make_gridc(*grid, ctx->comm_on ? ctx->comm.n_global : N);
   VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df, nsub));
   if (grid) VP_CUDA(cudaMemsetAsync(R.w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
   if (grid && R.w.sub.nsub)
@@ -336,6 +357,7 @@ struct RedDF {
     a.num_sms = ctx->num_sms;
     a.tune = ctx->tune;
     a.status = ctx->d_status;
+    a.tc = ctx->tensor_cores != 0;
     return a;
   }
   // field at (Q2, Z): Z2 = Z and Zh2 = Z / h in row format (skipped when the
@@ -356,7 +378,10 @@ struct RedDF {
     a.counts = w.counts;
     a.j = w.jcell;
     a.skip = skip;
-    VP_K(diag ? VP_K_DEPOSIT_DIAG : VP_K_DEPOSIT_LP, lp_launch(arith, LP_DEPOSIT, a, st));
+    const bool tc = a.tc && arith == 2 && deposit_tc_supported(n, p, R.g.Nx, R.g.Kp);
+    VP_K(diag ? VP_K_DEPOSIT_DIAG : (tc ? VP_K_DEPOSIT_TC : VP_K_DEPOSIT_LP),
+         lp_launch(arith, LP_DEPOSIT, a, st));
+    comm_sum_u64(ctx, w.counts, (int64_t)p * R.g.Nx, st);
     VP_K(VP_K_POISSON, poisson(R.g, p, nullptr, w.counts, w.phi_out, w.F, w.Efield, w.counts, skip,
                                ctx->d_status, st, w.F2, arith));
   }
@@ -368,7 +393,8 @@ struct RedDF {
     a.part = R.w.part;
     a.gridx = R.w.gx_proj;
     a.skip = skip;
-    VP_K(VP_K_PROJECT_LP, lp_launch(arith, LP_PROJECT, a, st));
+    const bool tc = a.tc && arith == 2 && project_tc_supported(n, p, R.g.Nx);
+    VP_K(tc ? VP_K_PROJECT_TC : VP_K_PROJECT_LP, lp_launch(arith, LP_PROJECT, a, st));
   }
   void grams(std::initializer_list<const void*> blks,
              std::initializer_list<std::pair<int, int>> pairs, double2* out) {
@@ -384,6 +410,7 @@ struct RedDF {
     VP_K(VP_K_GRAM_LP, lp_launch(arith, LP_GRAM, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)a.gram.npairs * n * n * 2, R.w.part,
                                       reinterpret_cast<double*>(out), nullptr, st));
+    comm_sum_f64(ctx, reinterpret_cast<double*>(out), (int64_t)a.gram.npairs * n * n * 2, st);
   }
   void gv(const void* Q2, double* GVraw) {
     LpArgs a = base();
@@ -392,6 +419,7 @@ struct RedDF {
     a.gridx = R.w.gx_gram;
     VP_K(VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
+    comm_sum_f64(ctx, GVraw, (int64_t)4 * n * n, st);
   }
   void comb(std::initializer_list<const void*> xs, const double2* C, double* out_d, void* out_v,
             const double* base_d = nullptr) {
@@ -560,6 +588,15 @@ vp_status DFStep::rounds(int count) {
   for (int r = 0; r < count; ++r) {
     D.field(Qm, w.Ze, w.flags, true);
     D.project(Qm, w.flags);
+    if (ctx->comm_on) {  // the projection summed over the ranks before the update
+      VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
+      comm_sum_f64(ctx, w.gX, zsz, st);
+      VP_K(VP_K_COEFF_UPDATE,
+           coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kr, w.Ze, dt, o.tol, o.maxit,
+                        o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status,
+                        st, nullptr, 0, w.Z2, w.Zh2, R.g.inv_h, o.arith));
+      continue;
+    }
     VP_K(VP_K_COEFF_UPDATE,
          coeff_update(n, p, nullptr, w.GVraw, w.Z0, w.k, w.kr, w.Ze, dt, o.tol, o.maxit,
                       o.cycle_max, o.cycle_ratio, w.aux, w.flags, w.flags + 1, ctx->d_status, st, w.part,
@@ -793,6 +830,7 @@ vp_status vp_hyper_create(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
                           const vp_hyper_opts* opts, vp_hyper** out) {
   void* stream = nullptr;
   VP_ENTER();
+  VP_NO_COMM();
   if (!out || !opts) return vp_fail(ctx, VP_EINVAL, "null pointer");
   *out = nullptr;
   VP_TRY(check_grid(ctx, grid));
@@ -915,6 +953,7 @@ vp_status vp_hyper_step(vp_hyper* h, double* Q, double* Z, double dt, int32_t ns
   if (!h) return VP_EINVAL;
   vp_ctx* ctx = h->ctx;
   VP_ENTER();
+  VP_NO_COMM();
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
   if (nsteps < 0 || !std::isfinite(dt)) return vp_fail(ctx, VP_EINVAL, "nsteps < 0 or dt not finite");
   vp_step_opts o{1e-9, 100, 0, 1e-3, 1e-2, 1, 0, 0, nullptr};
@@ -978,6 +1017,29 @@ vp_status vp_hyper_destroy(vp_hyper* h) {
 }
 
 // ------------------------------------------------------------------ tuning
+vp_status vp_ctx_set_comm(vp_ctx* ctx, const vp_comm* comm) {
+  if (!ctx) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (!comm) {
+    ctx->comm_on = false;
+    ctx->comm = vp_comm{};
+    return VP_OK;
+  }
+  if (!comm->sum_f64 || !comm->sum_u64 || comm->n_global < 1)
+    return vp_fail(ctx, VP_EINVAL, "communicator needs sum_f64, sum_u64 and n_global >= 1");
+  ctx->comm = *comm;
+  ctx->comm_on = true;
+  ctx->comm_failed = false;
+  return VP_OK;
+}
+
+vp_status vp_tensor_cores(vp_ctx* ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return VP_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->tensor_cores = enable;
+  return VP_OK;
+}
+
 vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm) {
   if (!ctx || knob < 0 || knob >= TUNE_COUNT || blocks_per_sm < 1 || blocks_per_sm > 32)
     return VP_EINVAL;
@@ -1000,6 +1062,7 @@ vp_status vp_autotune(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, in
                       const double* Q, const double* Z, int32_t arith, int32_t reps,
                       int32_t* chosen, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1162,7 +1225,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd",
-    "k_jacobi_sym", "k_deposit_lp_diag"};
+    "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1321,7 +1384,8 @@ const char* vp_status_string(vp_status s) {
     case VP_ENUMERIC: return "non-finite value or singular system";
     case VP_EDRIFT: return "basis left the ortho-symplectic manifold";
     case VP_ECUDA: return "CUDA error";
-    case VP_EUNSUPPORTED: return "unsupported size";
+    case VP_EUNSUPPORTED: return "unsupported size or call";
+    case VP_ECOMM: return "sum over the ranks failed";
   }
   return "unknown status";
 }
@@ -1348,6 +1412,8 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   reduced_init();
   dense_init();
   df_init();
+  tc_init();
+  tc_deposit_init();
   init_kernels_init();
   deim_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -1465,6 +1531,7 @@ vp_status vp_reconstruct(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const dou
 vp_status vp_project_grad(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const double* Q,
                           const double* GX, const double* Z, double* g_out, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z || !g_out) return vp_fail(ctx, VP_EINVAL, "Q, Z and g are required");
@@ -1485,6 +1552,7 @@ vp_status vp_project_grad(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const do
 vp_status vp_basis_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                             const double* Q, const double* Z, double* Xi, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1500,6 +1568,7 @@ vp_status vp_basis_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
 vp_status vp_cayley_retract(vp_ctx* ctx, int64_t N, int32_t n, const double* Q0, const double* xi,
                             double* Qout, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_np(ctx, N, 1));
   VP_TRY(check_n(ctx, n, N));
   if (!Q0 || !xi || !Qout) return vp_fail(ctx, VP_EINVAL, "Q0, xi and Qout are required");
@@ -1514,6 +1583,7 @@ vp_status vp_tangent_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32
                               const double* Q0, const double* xi, const double* Z, double* Y,
                               void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1537,6 +1607,9 @@ vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z) return vp_fail(ctx, VP_EINVAL, "Q and Z are required");
+  if (ctx->comm_on && N > ctx->comm.n_global)
+    return vp_fail(ctx, VP_EINVAL, "N = %lld rows exceed n_global", (long long)N);
+  ctx->comm_failed = false;
   Red R;
   VP_TRY(red_setup(ctx, grid, N, n, p, 0, st, R));
   R.field(Q, Z);
@@ -1545,6 +1618,7 @@ vp_status vp_reduced_energy(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
   VP_K(VP_K_ENERGIES, energies(n, p, R.w.GVraw, Z, R.w.Efield, E, H, 1, resid ? R.w.grams : nullptr, resid,
            ctx->d_status, st));
   VP_LAUNCHED();
+  if (ctx->comm_failed) return vp_fail(ctx, VP_ECOMM, "a sum over the ranks failed");
   return VP_OK;
 }
 
@@ -1573,6 +1647,7 @@ vp_status vp_rel_errors(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const doub
                         const double* Z, const double* X, const double* V, double* eps,
                         void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
   if (!Q || !Z || !X || !V || !eps) return vp_fail(ctx, VP_EINVAL, "null pointer");
@@ -1584,6 +1659,7 @@ vp_status vp_rel_errors(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const doub
 vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X,
                            const double* V, double* eps, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_np(ctx, N, p));
   if (n < 1 || n > 40 || n > p || n > N) return vp_fail(ctx, VP_EINVAL, "n outside [1, min(p, N, 40)]");
   if (!X || !V || !eps) return vp_fail(ctx, VP_EINVAL, "null pointer");
@@ -1609,6 +1685,7 @@ vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const d
 vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                             const double* Q, const double* Z, double* out, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1636,6 +1713,7 @@ vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
 vp_status vp_half_basis(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                         const double* Q0, const double* Z0, double dt, double* Qh, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1654,6 +1732,7 @@ vp_status vp_hamiltonian_error_terms(vp_ctx* ctx, const vp_grid* grid, int64_t N
                                      const double* Qh, const double* Q1, const double* Z1,
                                      double* out, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1682,6 +1761,7 @@ vp_status vp_deim_gather_project(vp_ctx* ctx, const vp_grid* grid, int64_t N, in
                                  const double* Q, const double* Z, int64_t d, const int32_t* idx,
                                  const double* c, const double* phi, double* gX, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1787,6 +1867,7 @@ static vp_status init_csvd_impl(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min
 vp_status vp_init_csvd(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const double* X0,
                        const double* V0, double* Q, double* Z, double* sigma, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   return init_csvd_impl(ctx, N, p, 1, n, -1.0, X0, V0, Q, Z, sigma, nullptr, st);
 }
 
@@ -1808,6 +1889,7 @@ vp_status vp_init_csvd_rank(vp_ctx* ctx, int64_t N, int32_t p, int32_t n_min, in
                             double tail_tol, const double* X0, const double* V0, double* Q,
                             double* Z, double* sigma, int32_t* n_out, void* stream) {
   VP_ENTER();
+  VP_NO_COMM();
   if (!(tail_tol >= 0.0)) return vp_fail(ctx, VP_EINVAL, "tail_tol must be >= 0");
   return init_csvd_impl(ctx, N, p, n_min, n_max, tail_tol, X0, V0, Q, Z, sigma, n_out, st);
 }
@@ -1838,10 +1920,17 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
       return vp_fail(ctx, VP_EINVAL, "subsample of %d columns outside [n, p] = [%d, %d] or no indices",
                      o.nsub, n, p);
   }
+  if (ctx->comm_on && N > ctx->comm.n_global)
+    return vp_fail(ctx, VP_EINVAL, "N = %lld rows exceed n_global", (long long)N);
+  ctx->comm_failed = false;
   const bool df = o.arith != 0;
   Red R;
   VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df, o.nsub));
-  if (df) return basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st);
+  if (df) {
+    VP_TRY(basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st));
+    if (ctx->comm_failed) return vp_fail(ctx, VP_ECOMM, "a sum over the ranks failed");
+    return VP_OK;
+  }
   RedWS& w = R.w;
   double *M = w.rows[0], *xih = w.rows[1], *Qh = w.rows[2], *Xp = w.rows[3], *xi1 = w.rows[4];
   const int64_t zsz = (int64_t)2 * n * p;
@@ -1880,6 +1969,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
         VP_K(VP_K_PROJECT, project(R.g, N, n, p, Qmid, w.Ze, w.F, nullptr, 0, nullptr, nullptr, N,
                                    w.part, w.gx_proj, w.flags, ctx->d_status, st));
         VP_K(VP_K_REDUCE, reduce_partials(w.gx_proj, zsz, w.part, w.gX, w.flags, st));
+        comm_sum_f64(ctx, w.gX, zsz, st);
         VP_K(VP_K_COEFF_UPDATE, coeff_update(n, p, w.gX, w.GVraw, w.Z0, w.k, w.kr, w.Ze, dt, o.tol,
                                              o.maxit, o.cycle_max, o.cycle_ratio, w.aux, w.flags,
                                              w.flags + 1, ctx->d_status, st));
@@ -1916,6 +2006,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
     VP_CUDA(cudaMemcpyAsync(Z, w.Z1, sizeof(double) * zsz, cudaMemcpyDeviceToDevice, st));
   }
   VP_LAUNCHED();
+  if (ctx->comm_failed) return vp_fail(ctx, VP_ECOMM, "a sum over the ranks failed");
   return VP_OK;
 }
 

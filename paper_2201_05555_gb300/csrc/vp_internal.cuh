@@ -43,7 +43,18 @@ struct vp_ctx {
   std::vector<cudaEvent_t> event_pool;
   int tune[TUNE_COUNT] = {kTuneDefault[0], kTuneDefault[1], kTuneDefault[2], kTuneDefault[3],
                          kTuneDefault[4]};
+  int tensor_cores = 1;  // vp_tensor_cores: tcgen05 kernels where they apply
+  // particle sharding (vp_ctx_set_comm): sums over the rows of all ranks
+  vp_comm comm{};
+  bool comm_on = false;
+  bool comm_failed = false;
 };
+
+// Sum over the ranks of the attached communicator, in place on the device
+// buffer, ordered on st; no-op without one.  A failure is recorded in the
+// context (the entry point then returns VP_ECOMM).
+void comm_sum_f64(vp_ctx* ctx, double* buf, int64_t count, cudaStream_t st);
+void comm_sum_u64(vp_ctx* ctx, unsigned long long* buf, int64_t count, cudaStream_t st);
 
 // Blocks of a grid sized for `bps` resident blocks per SM over `chunks`
 // column chunks, at most one per tile.
@@ -292,6 +303,7 @@ struct LpArgs {
   double* dout = nullptr;
   const int* tune = nullptr;  // vp_ctx::tune (null: defaults)
   int* status = nullptr;      // device status word
+  bool tc = false;            // tensor-core kernels where they apply (FP32 rows)
 };
 
 // Cell indices of the FP32-based path are stored tile by tile: for row tile
@@ -380,6 +392,18 @@ void pic_init();
 // reduced_df.cu: arith 1 = double-float, 2 = FP32
 void lp_launch(int arith, LpOp op, const LpArgs& a, cudaStream_t st);
 void df_init();
+// tc_project.cu: projection of the FP32 form on the tensor cores
+bool project_tc_supported(int n, int p, int Nx);
+void project_tc(const GridC& g, int64_t N, int n, int p, const float* Q2, const float* F2,
+                const uint16_t* jt, double* part, int gridx, const int* skip, int* status,
+                cudaStream_t st);
+void tc_init();
+// tc_deposit.cu: deposit of the FP32 form with the reconstruction on the tensor cores
+bool deposit_tc_supported(int n, int p, int Nx, int Kp);
+void deposit_tc(const GridC& g, int64_t N, int n, int p, const float* Q2, const float* Zh2,
+                unsigned long long* counts, uint16_t* jout, int gridx, const int* skip,
+                int* status, cudaStream_t st);
+void tc_deposit_init();
 
 // init.cu (complex SVD start)
 void init_launch_rgram(int64_t N, int p, const double* X, const double* V, double2* part, int gx,

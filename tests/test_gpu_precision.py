@@ -163,3 +163,44 @@ def test_precision_form_200_steps_against_oracle(ctx, family):
     assert err["H_step1"] <= GATE and err["E_step1"] <= GATE, err
     assert err["H_max_rel"] <= FP32_200["H"] and err["E_max_rel"] <= FP32_200["E"], err
     assert err["manifold"] < 1e-12
+
+
+@pytest.mark.parametrize("shape", [dict(N=20_000, p=64, n=32, Nx=256),
+                                   dict(N=7_001, p=40, n=10, Nx=128),
+                                   dict(N=3_001, p=256, n=16, Nx=256)])
+def test_tensor_core_kernels_match_simt(ctx, shape):
+    """The FP32 form with its projection and its deposit's reconstruction on
+    the tensor cores (tcgen05, TF32 operands split in two, FP32 accumulation in
+    tensor memory) against the same step with the FP32 SIMT kernels and
+    against the FP64 oracle: one step from the same start; the tensor-core
+    kernels must have run, and only they."""
+    from paper_2201_05555_gb300 import make_grid
+    N, p, n, Nx = shape["N"], shape["p"], shape["n"], shape["Nx"]
+    etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
+    X0, V0 = W.load_batch(W.BUMP_ON_TAIL, etas, N, quiet=False)
+    U, Z, _ = csvd.csvd_init(X0, V0, n)
+    g = pic.make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+    grid = make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+    dt = 0.1
+    out = {}
+    for tc in (True, False):
+        ctx.tensor_cores(tc)
+        Qd, Zd = T(q_storage(U)), T(Z)
+        ctx.profile_reset()
+        ctx.profile_enable(["k_project_tc", "k_project_lp", "k_deposit_tc", "k_deposit_lp"])
+        ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, reortho=True, trace=False)
+        ctx.sync_status()
+        prof = ctx.profile_read()
+        ctx.profile_enable([])
+        out[tc] = (U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy(), prof)
+    ctx.tensor_cores(True)
+    for k in ("project", "deposit"):
+        assert out[True][1][f"k_{k}_tc"][0] > 0 and out[True][1][f"k_{k}_lp"][0] == 0
+        assert out[False][1][f"k_{k}_tc"][0] == 0 and out[False][1][f"k_{k}_lp"][0] > 0
+    Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
+    ref = Uo @ Zo
+    e_tc, e_simt = rel(out[True][0], ref), rel(out[False][0], ref)
+    print("tensor-core kernels", json.dumps(shape), "UZ rel: tc %.2e simt %.2e diff %.2e"
+          % (e_tc, e_simt, rel(out[True][0], out[False][0])))
+    assert e_tc < 1e-5 and e_simt < 1e-5
+    assert rel(out[True][0], out[False][0]) < 1e-5
