@@ -14,10 +14,10 @@
 // remainder v_lo = v - v_hi; x_li = D[l][i] + D[l][PC + i], the product at
 // the accuracy of FP32 row arithmetic (FP32 accumulation in tensor memory).
 //
-// Warp roles (13 warps): warps 8-11 stage the Q tiles (split, K-major
-// canonical layout, two stages); warp 12 allocates tensor memory and its lane
-// 0 issues the MMAs into one of two accumulators; warps 0-7 read an
-// accumulator (warp w: lanes 32 (w % 4) .. + 31, samples of half w / 4),
+// Warp roles (21 warps): warps 16-19 stage the Q tiles (split, K-major
+// canonical layout, two stages); warp 20 allocates tensor memory and its lane
+// 0 issues the MMAs into one of two accumulators; warps 0-15 read an
+// accumulator (warp w: lanes 32 (w % 4) .. + 31, samples of quarter w / 4),
 // release it and deposit.  Counts accumulate in shared memory (int64,
 // order-free) and go to the global counts once per CTA.  Every mbarrier wait
 // is bounded (VP_ETIMEDOUT; the kernel then runs to its end and frees its
@@ -28,7 +28,7 @@ namespace vpk {
 namespace {
 
 constexpr int kDepRows = 128;  // MMA M: particles per tile
-constexpr int kDepWarps = 13;
+constexpr int kDepWarps = 21;  // 16 epilogue, 4 producer, 1 MMA
 constexpr int kDepThreads = 32 * kDepWarps;
 constexpr int kDepStages = 2;
 
@@ -42,10 +42,10 @@ __global__ void __launch_bounds__(kDepThreads, 1)
 k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
              const float* __restrict__ Zh2, unsigned long long* __restrict__ counts,
              uint16_t* __restrict__ jout, const int* skip, int* status) {
-  static_assert(PC == 16 || PC == 32, "two halves of PC / 2 samples");
+  static_assert(PC == 16 || PC == 32, "four quarters of PC / 4 samples");
   if (skip && *skip) return;
   constexpr int NB = 2 * PC;  // MMA N: [z_hi | z_lo]
-  constexpr int HALF = PC / 2;
+  constexpr int SUB = PC / 4;  // samples per epilogue warp
   const int n2 = 2 * n, kp = (n2 + 7) & ~7, Nx = g.Nx;
   const uint32_t aBytes = (uint32_t)kDepRows * kp * 4;  // Q_hi or Q_lo tile
   const uint32_t bBytes = (uint32_t)NB * kp * 4;
@@ -57,7 +57,7 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
   uint64_t* full = bars;       // [2] tile staged (128 producer arrivals)
   uint64_t* afree = bars + 2;  // [2] stage read by the MMAs (commit)
   uint64_t* dfull = bars + 4;  // [2] accumulator ready (commit)
-  uint64_t* dfree = bars + 6;  // [2] accumulator drained (256 epilogue arrivals)
+  uint64_t* dfree = bars + 6;  // [2] accumulator drained (512 epilogue arrivals)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 8);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nch = gridDim.y, chunk = blockIdx.y, c0 = chunk * PC;
@@ -82,11 +82,11 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
       mbar_init(&full[s], 128);
       mbar_init(&afree[s], 1);
       mbar_init(&dfull[s], 1);
-      mbar_init(&dfree[s], 256);
+      mbar_init(&dfree[s], 512);
     }
     mbar_fence_init();
   }
-  if (warp == 12) tc_alloc(tslot, 4 * PC);  // two accumulators of 2 PC columns
+  if (warp == 20) tc_alloc(tslot, 4 * PC);  // two accumulators of 2 PC columns
   fence_proxy_async_smem();                  // B written by the generic proxy
   tc_fence_before();
   __syncthreads();
@@ -95,38 +95,47 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
   const int64_t ntiles = (N + kDepRows - 1) / kDepRows;
   const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
 
-  if (warp >= 8 && warp < 12) {
-    // ---- producers: warp pw stages rows 32 pw .. 32 pw + 31 of the tile, two
-    // consecutive rows per load instruction (lane l: row 2 i + l / 16, float4
-    // column l % 16), all sixteen loads in flight before the splits and stores
-    const int pw = warp - 8, q = lane & 15, rsub = lane >> 4, nq = kp / 4;
+  if (warp >= 16 && warp < 20) {
+    // ---- producers: warp pw stages rows 32 pw .. 32 pw + 31 of the tile.  In
+    // iteration i lane l takes row 32 pw + 8 (i % 4) + l % 8 and float4 column
+    // 4 (i / 4) + l / 8: the warp's stores fill one contiguous 512-byte run of
+    // the canonical layout (conflict-free), its loads 8 rows x 64 bytes; all
+    // loads are in flight before the splits and stores
+    const int pw = warp - 16, nq = kp / 4;
     for (int it = 0; it < my_tiles; ++it) {
       const int s = it & 1;
       if (it >= 2) mbar_wait(&afree[s], (uint32_t)(((it >> 1) - 1) & 1), status);
       const int64_t base = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * kDepRows;
       unsigned char* Ah = A0 + s * 2 * aBytes;
       unsigned char* Al = Ah + aBytes;
-      float4 v[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int64_t R = base + 32 * pw + 2 * i + rsub;
-        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < nq && R < N && 4 * q < n2) v[i] = __ldg(reinterpret_cast<const float4*>(Q2 + R * n2) + q);
-      }
-      if (q < nq) {
+      for (int ph = 0; ph < 2; ++ph) {  // two phases of eight loads in flight
+        float4 v[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int r = 32 * pw + 2 * i + rsub;
-          const float2 a = tf32_split(v[i].x), b = tf32_split(v[i].y), c = tf32_split(v[i].z),
-                       d = tf32_split(v[i].w);
-          *reinterpret_cast<float4*>(Ah + cmk_off(r, 4 * q, kp)) = make_float4(a.x, b.x, c.x, d.x);
-          *reinterpret_cast<float4*>(Al + cmk_off(r, 4 * q, kp)) = make_float4(a.y, b.y, c.y, d.y);
+        for (int i2 = 0; i2 < 8; ++i2) {
+          const int i = 8 * ph + i2;
+          const int r = 32 * pw + 8 * (i & 3) + (lane & 7), q = 4 * (i >> 2) + (lane >> 3);
+          const int64_t R = base + r;
+          v[i2] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (q < nq && R < N && 4 * q < n2)
+            v[i2] = __ldg(reinterpret_cast<const float4*>(Q2 + R * n2) + q);
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 8; ++i2) {
+          const int i = 8 * ph + i2;
+          const int r = 32 * pw + 8 * (i & 3) + (lane & 7), q = 4 * (i >> 2) + (lane >> 3);
+          if (q < nq) {
+            const float2 a = tf32_split(v[i2].x), b = tf32_split(v[i2].y),
+                         c = tf32_split(v[i2].z), d = tf32_split(v[i2].w);
+            *reinterpret_cast<float4*>(Ah + cmk_off(r, 4 * q, kp)) = make_float4(a.x, b.x, c.x, d.x);
+            *reinterpret_cast<float4*>(Al + cmk_off(r, 4 * q, kp)) = make_float4(a.y, b.y, c.y, d.y);
+          }
         }
       }
       fence_proxy_async_smem();
       mbar_arrive(&full[s]);
     }
-  } else if (warp == 12) {
+  } else if (warp == 20) {
     // ---- MMA issue
     if (lane == 0) {
       const uint32_t idesc = tc_idesc_tf32(kDepRows, NB);
@@ -150,8 +159,8 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31, samples of half w / 4
-    const int half = warp >> 2, row = 32 * (warp & 3) + lane;
+    // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31, samples of quarter w / 4
+    const int quarter = warp >> 2, row = 32 * (warp & 3) + lane;
     const long long one = 1ll << g.Sp;
     const float pscale = (float)one, inv_Nx = (float)g.inv_Nx;
     const unsigned long long pbit = 1ull << g.Kp;
@@ -159,20 +168,26 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
       const int d = it & 1;
       mbar_wait(&dfull[d], (uint32_t)((it >> 1) & 1), status);
       tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * NB + half * HALF);
-      uint32_t vh[16], vl[16];
-      tc_ld16(ta, vh);        // z_hi part of samples half * HALF ..
-      tc_ld16(ta + PC, vl);   // z_lo part
+      const uint32_t ta =
+          tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * NB + quarter * SUB);
+      uint32_t vh[SUB], vl[SUB];
+      if constexpr (SUB == 8) {
+        tc_ld8(ta, vh);       // z_hi part of samples quarter * SUB ..
+        tc_ld8(ta + PC, vl);  // z_lo part
+      } else {
+        tc_ld4(ta, vh);
+        tc_ld4(ta + PC, vl);
+      }
       tc_wait_ld();
       tc_fence_before();
       mbar_arrive(&dfree[d]);
       const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
       const int64_t R = tile * kDepRows + row;
       if (R < N) {
-        uint16_t js[HALF];
+        uint32_t js[SUB / 2];
 #pragma unroll
-        for (int u = 0; u < HALF; ++u) {
-          const int c = half * HALF + u;
+        for (int u = 0; u < SUB; ++u) {
+          const int c = quarter * SUB + u;
           // cell and fraction in FP32 (both exact), as the FP32 SIMT deposit
           const float th = __uint_as_float(vh[u]) + __uint_as_float(vl[u]);
           const float fl = floorf(th);
@@ -182,38 +197,23 @@ k_deposit_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
           jr -= wq * Nx;
           if (jr < 0) jr += Nx;
           if (jr >= Nx) jr -= Nx;
-          js[u] = (uint16_t)jr;
+          if (u & 1) js[u >> 1] |= (uint32_t)jr << 16;
+          else js[u >> 1] = (uint32_t)jr;
           if (c < pc_eff) atomicAdd(cnt + c * Nx + jr, pbit + (unsigned long long)q);
         }
         const int64_t tl = R / TILE_ROWS;
-        uint16_t* dst = jout + jt_block(tl, chunk, nch, PC) + (R - tl * TILE_ROWS) * PC + half * HALF;
-        if constexpr (HALF == 16) {
-          uint4 w0, w1;
-          w0.x = js[0] | ((uint32_t)js[1] << 16);
-          w0.y = js[2] | ((uint32_t)js[3] << 16);
-          w0.z = js[4] | ((uint32_t)js[5] << 16);
-          w0.w = js[6] | ((uint32_t)js[7] << 16);
-          w1.x = js[8] | ((uint32_t)js[9] << 16);
-          w1.y = js[10] | ((uint32_t)js[11] << 16);
-          w1.z = js[12] | ((uint32_t)js[13] << 16);
-          w1.w = js[14] | ((uint32_t)js[15] << 16);
-          reinterpret_cast<uint4*>(dst)[0] = w0;
-          reinterpret_cast<uint4*>(dst)[1] = w1;
-        } else {
-          uint4 w0;
-          w0.x = js[0] | ((uint32_t)js[1] << 16);
-          w0.y = js[2] | ((uint32_t)js[3] << 16);
-          w0.z = js[4] | ((uint32_t)js[5] << 16);
-          w0.w = js[6] | ((uint32_t)js[7] << 16);
-          reinterpret_cast<uint4*>(dst)[0] = w0;
-        }
+        uint16_t* dst = jout + jt_block(tl, chunk, nch, PC) + (R - tl * TILE_ROWS) * PC + quarter * SUB;
+        if constexpr (SUB == 8)
+          *reinterpret_cast<uint4*>(dst) = make_uint4(js[0], js[1], js[2], js[3]);
+        else
+          *reinterpret_cast<uint2*>(dst) = make_uint2(js[0], js[1]);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 12) tc_dealloc(tmem, 4 * PC);
+  if (warp == 20) tc_dealloc(tmem, 4 * PC);
   for (int e = t; e < PC * Nx; e += kDepThreads) {
     const int c = e / Nx;
     if (c < pc_eff && cnt[e]) atomicAdd(&counts[(int64_t)(c0 + c) * Nx + (e - c * Nx)], cnt[e]);
