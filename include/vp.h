@@ -196,6 +196,40 @@ vp_status vp_gather_E(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, co
                       int64_t ldx, const double* F_dev, const int32_t* idx_dev, int64_t d,
                       double* GX_dev, void* stream);
 
+/* ------------------------------------------- typed per-step calls (vp_dtype)
+ * The calls a2, a4, a1 and a5 above on N-row inputs of a stated element type
+ * (positions, gradients and basis rows; grids, Z and g stay FP64), with
+ * explicit leading dimensions.  FP64 inputs give the results of the calls
+ * above.  Positions are converted to FP64 before their cell and weight are
+ * taken, so the deposit and the gather equal the FP64 calls on the rounded
+ * positions (the deposit exactly; the gather up to the rounding of its
+ * output to the type).  The reconstruction and the projection multiply and
+ * accumulate in FP32 for FP32 and BF16 inputs (FP64 for FP64), per-block
+ * partial sums added in FP64.  Pointers must be aligned to their element
+ * type; a bad dtype, flag or alignment returns VP_EINVAL. */
+typedef enum vp_dtype { VP_F64 = 0, VP_F32 = 1, VP_BF16 = 2 } vp_dtype;
+/* Deposit flag: charge accumulated as int64 fixed point (order-independent,
+ * bit-identical on repetition).  It is the only accumulation the library
+ * implements, so flags = 0 means the same. */
+#define VP_DEPOSIT_FIXEDPOINT 1
+/* a2 (Sec. 2.1, eq. PoissonSystem): rho = Lambda^0(X)^T M_q + b. */
+vp_status vp_deposit_cic_t(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const void* X_dev,
+                           int64_t ldx, int32_t dtype, double* rho_dev, int32_t flags, void* stream);
+/* a4 (eq. VPHamEqn): GX_dev (p x N, or p x d with idx_dev) in dtype. */
+vp_status vp_gather_E_t(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const void* X_dev,
+                        int64_t ldx, int32_t dtype, const double* F_dev, const int32_t* idx_dev,
+                        int64_t d, void* GX_dev, void* stream);
+/* a1 (Sec. 3.2): Q_dev N rows of ldq >= 2n elements; X_dev, V_dev (nullable)
+ * p x N with leading dimension ldx >= N, in dtype. */
+vp_status vp_reconstruct_t(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const void* Q_dev,
+                           int64_t ldq, int32_t dtype, const double* Z_dev, void* X_dev,
+                           void* V_dev, int64_t ldx, void* stream);
+/* a5 (eq. grads): g_dev (2n x p, FP64) = U^T [GX; V_r], GX_dev p x N with
+ * leading dimension ldg >= N (nullable: the V part alone). */
+vp_status vp_project_grad_t(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const void* Q_dev,
+                            int64_t ldq, int32_t dtype, const void* GX_dev, int64_t ldg,
+                            const double* Z_dev, double* g_dev, void* stream);
+
 /* a10. nsteps Stormer-Verlet steps of the full-order model for each sample
  * (Sec. 5, eq. sv_full_order), in place on X_dev, V_dev (p x N, ld N).
  * trace_dev (nullable): (nsteps x p x 2) electric energy and Hamiltonian
@@ -603,8 +637,12 @@ vp_status vp_serve_cancel(vp_server* srv, uint64_t ticket);
 /* Counters (each nullable). */
 vp_status vp_server_stats(vp_server* srv, int64_t* submitted, int64_t* completed, int32_t* active,
                           int32_t* pending, size_t* used_bytes);
-/* Drop waiting queries, cancel running ones, join every thread, free. */
-vp_status vp_server_destroy(vp_server* srv);
+/* Let waiting and running queries finish for up to drain_timeout_ms (0: not
+ * at all), then drop the waiting ones, cancel the running ones at their next
+ * 16-step boundary, join every thread and free.  Returns VP_ETIMEDOUT when
+ * queries were still waiting or running at the timeout (the server is freed
+ * all the same), VP_EINVAL for a negative timeout. */
+vp_status vp_server_destroy(vp_server* srv, int32_t drain_timeout_ms);
 
 /* ---------------------------------------------------------------- tuning */
 /* Launch shape of the FP32-based particle kernels (arith 1 and 2): each

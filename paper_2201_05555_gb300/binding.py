@@ -80,6 +80,11 @@ _SIGS = [
     ("vp_deposit_cic_noalloc", _I32, [C.POINTER(Grid), _I64, _I32, _P, _I64, _P, _P]),
     ("vp_tensor_cores", _I32, [_P, _I32]),
     ("vp_ctx_set_comm", _I32, [_P, _P]),
+    ("vp_deposit_cic_t", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _I64, _I32, _P, _I32, _P]),
+    ("vp_gather_E_t", _I32, [_P, C.POINTER(Grid), _I64, _I32, _P, _I64, _I32, _P, _P, _I64, _P,
+                             _P]),
+    ("vp_reconstruct_t", _I32, [_P, _I64, _I32, _I32, _P, _I64, _I32, _P, _P, _P, _I64, _P]),
+    ("vp_project_grad_t", _I32, [_P, _I64, _I32, _I32, _P, _I64, _I32, _P, _I64, _P, _P, _P]),
     ("vp_init_csvd", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_profile_enable", _I32, [_P, C.c_uint64]),
     ("vp_profile_read", _I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
@@ -120,7 +125,7 @@ _SIGS = [
     ("vp_serve_cancel", _I32, [_P, C.c_uint64]),
     ("vp_server_stats", _I32, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32),
                                C.POINTER(_I32), C.POINTER(_SZ)]),
-    ("vp_server_destroy", _I32, [_P]),
+    ("vp_server_destroy", _I32, [_P, _I32]),
     ("vp_selftest_wait", _I32, [_P, _I32, _P]),
     ("vp_tune_set", _I32, [_P, _I32, _I32]),
     ("vp_tune_get", _I32, [_P, _I32, C.POINTER(_I32)]),
@@ -180,6 +185,19 @@ def _ptr(t: torch.Tensor | None, dtype=torch.float64, name: str = "tensor"):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t.data_ptr()
+
+
+# element types of the typed per-step calls (vp_dtype)
+DTYPES = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
+DEPOSIT_FIXEDPOINT = 1
+
+
+def _dtype_of(*ts):
+    """The vp_dtype shared by the given tensors (None entries skipped)."""
+    dt = {t.dtype for t in ts if t is not None}
+    if len(dt) != 1 or next(iter(dt)) not in DTYPES:
+        raise ValueError(f"tensors must share one of float64, float32, bfloat16; got {dt}")
+    return next(iter(dt))
 
 
 class Context:
@@ -254,6 +272,54 @@ class Context:
         self._check(self.lib.vp_deposit_cic(self.h, C.byref(grid), N, p, _ptr(X, name="X"), N,
                                             _ptr(rho, name="rho"), self._stream()), "deposit")
         return rho
+
+    def deposit_cic_t(self, grid: Grid, X: torch.Tensor, flags: int = DEPOSIT_FIXEDPOINT):
+        """vp_deposit_cic_t: X (p x N) float64, float32 or bfloat16; rho FP64."""
+        dt = _dtype_of(X)
+        p, N = X.shape
+        rho = self._empty(p, grid.Nx)
+        self._check(self.lib.vp_deposit_cic_t(self.h, C.byref(grid), N, p, _ptr(X, dt, "X"),
+                                              X.stride(0), DTYPES[dt], _ptr(rho, name="rho"),
+                                              flags, self._stream()), "deposit_cic_t")
+        return rho
+
+    def gather_E_t(self, grid: Grid, X: torch.Tensor, F: torch.Tensor,
+                   idx: torch.Tensor | None = None):
+        """vp_gather_E_t: GX in the dtype of X."""
+        dt = _dtype_of(X)
+        p, N = X.shape
+        d = N if idx is None else idx.numel()
+        GX = torch.empty((p, d), dtype=dt, device=X.device)
+        self._check(self.lib.vp_gather_E_t(self.h, C.byref(grid), N, p, _ptr(X, dt, "X"),
+                                           X.stride(0), DTYPES[dt], _ptr(F, name="F"),
+                                           _ptr(idx, torch.int32, "idx"), d, _ptr(GX, dt),
+                                           self._stream()), "gather_E_t")
+        return GX
+
+    def reconstruct_t(self, Q: torch.Tensor, Z: torch.Tensor, want_v: bool = True):
+        """vp_reconstruct_t: X, V (p x N) in the dtype of Q."""
+        dt = _dtype_of(Q)
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        X = torch.empty((p, N), dtype=dt, device=Q.device)
+        V = torch.empty((p, N), dtype=dt, device=Q.device) if want_v else None
+        self._check(self.lib.vp_reconstruct_t(self.h, N, n2 // 2, p, _ptr(Q, dt, "Q"), Q.stride(0),
+                                              DTYPES[dt], _ptr(Z, name="Z"), _ptr(X, dt),
+                                              _ptr(V, dt), N, self._stream()), "reconstruct_t")
+        return X, V
+
+    def project_grad_t(self, Q: torch.Tensor, GX: torch.Tensor | None, Z: torch.Tensor):
+        """vp_project_grad_t: Q and GX of one dtype; g (2n x p) FP64."""
+        dt = _dtype_of(Q, GX)
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        g = self._empty(n2, p)
+        self._check(self.lib.vp_project_grad_t(self.h, N, n2 // 2, p, _ptr(Q, dt, "Q"), Q.stride(0),
+                                               DTYPES[dt], _ptr(GX, dt, "GX"),
+                                               GX.stride(0) if GX is not None else N,
+                                               _ptr(Z, name="Z"), _ptr(g), self._stream()),
+                    "project_grad_t")
+        return g
 
     def poisson(self, grid: Grid, rho: torch.Tensor, want_phi: bool = True):
         p = rho.shape[0]
@@ -814,11 +880,16 @@ class Server:
         return {"submitted": sub.value, "completed": com.value, "active": act.value,
                 "pending": pen.value, "used_bytes": used.value}
 
-    def close(self):
+    def close(self, drain_timeout_ms: int = 0) -> int:
+        """Destroy the server after letting its queries finish for up to
+        drain_timeout_ms; returns the status (VP_ETIMEDOUT = 5 when some had
+        to be cancelled)."""
+        s = 0
         if getattr(self, "h", None):
-            self.lib.vp_server_destroy(self.h)
+            s = self.lib.vp_server_destroy(self.h, int(drain_timeout_ms))
             self.h = None
             self._held.clear()
+        return s
 
     def __del__(self):
         try:

@@ -385,8 +385,15 @@ vp_status vp_server_stats(vp_server* s, int64_t* submitted, int64_t* completed, 
   return VP_OK;
 }
 
-vp_status vp_server_destroy(vp_server* s) {
-  if (!s) return VP_EINVAL;
+vp_status vp_server_destroy(vp_server* s, int32_t drain_timeout_ms) {
+  if (!s || drain_timeout_ms < 0) return VP_EINVAL;
+  // let waiting and running queries finish for up to drain_timeout_ms
+  bool drained = true;
+  if (drain_timeout_ms > 0) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    drained = s->cv_done.wait_for(lk, std::chrono::milliseconds(drain_timeout_ms),
+                                  [&] { return s->pending.empty() && s->active == 0; });
+  }
   std::vector<std::thread> ths;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -406,7 +413,7 @@ vp_status vp_server_destroy(vp_server* s) {
   }
   if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
-  return VP_OK;
+  return drained ? VP_OK : VP_ETIMEDOUT;
 }
 
 // ------------------------------------------------------------- checkpoint

@@ -1549,6 +1549,95 @@ vp_status vp_project_grad(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const do
   return VP_OK;
 }
 
+// ------------------------------------------------- typed per-step calls
+static vp_status check_dtype(vp_ctx* ctx, int32_t dtype, std::initializer_list<const void*> ptrs) {
+  if (dtype < VP_F64 || dtype > VP_BF16) return vp_fail(ctx, VP_EINVAL, "dtype %d", dtype);
+  const uintptr_t a = (uintptr_t)vp_dtype_size(dtype);
+  for (const void* q : ptrs)
+    if (q && ((uintptr_t)q % a)) return vp_fail(ctx, VP_EINVAL, "pointer not aligned to its dtype");
+  return VP_OK;
+}
+
+vp_status vp_deposit_cic_t(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const void* X,
+                           int64_t ldx, int32_t dtype, double* rho, int32_t flags, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  if (!X || !rho || ldx < N) return vp_fail(ctx, VP_EINVAL, "null pointer or ldx < N");
+  if (flags & ~VP_DEPOSIT_FIXEDPOINT) return vp_fail(ctx, VP_EINVAL, "unknown deposit flags");
+  VP_TRY(check_dtype(ctx, dtype, {X}));
+  GridC g = make_gridc(*grid, N);
+  void* base;
+  size_t cb = sizeof(unsigned long long) * p * grid->Nx;
+  VP_TRY(vp_workspace(ctx, cb, &base));
+  auto* counts = (unsigned long long*)base;
+  VP_CUDA(cudaMemsetAsync(counts, 0, cb, st));
+  VP_K(VP_K_DEPOSIT, deposit_typed(g, N, p, X, ldx, dtype, counts, ctx->num_sms, st));
+  VP_K(VP_K_RHO, counts_to_rho(g, p, counts, rho, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_gather_E_t(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t p, const void* X,
+                        int64_t ldx, int32_t dtype, const double* F, const int32_t* idx, int64_t d,
+                        void* GX, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_grid(ctx, grid));
+  VP_TRY(check_np(ctx, N, p));
+  if (!X || !F || !GX || ldx < N) return vp_fail(ctx, VP_EINVAL, "null pointer or ldx < N");
+  if (idx && (d < 1 || d > N)) return vp_fail(ctx, VP_EINVAL, "d = %lld outside [1, N]", (long long)d);
+  VP_TRY(check_dtype(ctx, dtype, {X, GX}));
+  GridC g = make_gridc(*grid, N);
+  VP_K(VP_K_GATHER, gather_typed(g, N, p, X, ldx, dtype, F, idx, d, GX, ctx->num_sms,
+                                 ctx->d_status, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_reconstruct_t(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const void* Q,
+                           int64_t ldq, int32_t dtype, const double* Z, void* X, void* V,
+                           int64_t ldx, void* stream) {
+  VP_ENTER();
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !X) return vp_fail(ctx, VP_EINVAL, "Q, Z and X are required");
+  if (ldq < 2 * n || ldx < N) return vp_fail(ctx, VP_EINVAL, "ldq < 2n or ldx < N");
+  VP_TRY(check_dtype(ctx, dtype, {Q, X, V}));
+  VP_K(VP_K_RECONSTRUCT, reconstruct_typed(N, n, p, Q, ldq, dtype, Z, X, V, ldx, ctx->num_sms, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_project_grad_t(vp_ctx* ctx, int64_t N, int32_t n, int32_t p, const void* Q,
+                            int64_t ldq, int32_t dtype, const void* GX, int64_t ldg,
+                            const double* Z, double* g_out, void* stream) {
+  VP_ENTER();
+  VP_NO_COMM();
+  VP_TRY(check_np(ctx, N, p));
+  VP_TRY(check_n(ctx, n, N));
+  if (!Q || !Z || !g_out) return vp_fail(ctx, VP_EINVAL, "Q, Z and g are required");
+  if (ldq < 2 * n || (GX && ldg < N)) return vp_fail(ctx, VP_EINVAL, "ldq < 2n or ldg < N");
+  VP_TRY(check_dtype(ctx, dtype, {Q, GX}));
+  const int n2 = 2 * n, ch = ceil_div(p, 32);
+  const int gp = typed_grid_x(N, ch, ctx->num_sms), gg = typed_grid_x(N, 1, ctx->num_sms);
+  const size_t zsz = (size_t)n2 * p, gsz = (size_t)n2 * n2;
+  const size_t part = std::max((size_t)gp * zsz, (size_t)gg * gsz);
+  void* base;
+  VP_TRY(vp_workspace(ctx, sizeof(double) * (part + zsz + gsz), &base));
+  double* P = (double*)base;
+  double* gX = P + part;
+  double* GV = gX + zsz;
+  if (GX) {
+    VP_K(VP_K_PROJECT, project_typed(N, n, p, Q, ldq, dtype, GX, ldg, P, gp, st));
+    VP_K(VP_K_REDUCE, reduce_partials(gp, (int64_t)zsz, P, gX, nullptr, st));
+  }
+  VP_K(VP_K_GRAM_REAL, gram_real_typed(N, n2, Q, ldq, dtype, P, gg, st));
+  VP_K(VP_K_REDUCE, reduce_partials(gg, (int64_t)gsz, P, GV, nullptr, st));
+  VP_K(VP_K_ADD_LINEAR, add_linear(n, p, GX ? gX : nullptr, GV, Z, g_out, st));
+  VP_LAUNCHED();
+  return VP_OK;
+}
+
 vp_status vp_basis_velocity(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                             const double* Q, const double* Z, double* Xi, void* stream) {
   VP_ENTER();

@@ -404,6 +404,21 @@ void deposit_tc(const GridC& g, int64_t N, int n, int p, const float* Q2, const 
                 unsigned long long* counts, uint16_t* jout, int gridx, const int* skip,
                 int* status, cudaStream_t st);
 void tc_deposit_init();
+// typed.cu: per-step calls on FP64 / FP32 / BF16 inputs (dtype 0 / 1 / 2)
+int vp_dtype_size(int dtype);
+void deposit_typed(const GridC& g, int64_t N, int p, const void* X, int64_t ldx, int dtype,
+                   unsigned long long* counts, int num_sms, cudaStream_t st);
+void gather_typed(const GridC& g, int64_t N, int p, const void* X, int64_t ldx, int dtype,
+                  const double* F, const int32_t* idx, int64_t d, void* GX, int num_sms,
+                  int* status, cudaStream_t st);
+void reconstruct_typed(int64_t N, int n, int p, const void* Q, int64_t ldq, int dtype,
+                       const double* Z, void* X, void* V, int64_t ldx, int num_sms,
+                       cudaStream_t st);
+void project_typed(int64_t N, int n, int p, const void* Q, int64_t ldq, int dtype, const void* GX,
+                   int64_t ldg, double* part, int gridx, cudaStream_t st);
+void gram_real_typed(int64_t N, int m, const void* Q, int64_t ldq, int dtype, double* part,
+                     int gridx, cudaStream_t st);
+int typed_grid_x(int64_t N, int chunks, int num_sms);
 
 // init.cu (complex SVD start)
 void init_launch_rgram(int64_t N, int p, const double* X, const double* V, double2* part, int gx,

@@ -204,3 +204,44 @@ def test_tensor_core_kernels_match_simt(ctx, shape):
           % (e_tc, e_simt, rel(out[True][0], out[False][0])))
     assert e_tc < 1e-5 and e_simt < 1e-5
     assert rel(out[True][0], out[False][0]) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def headline_shape_reference():
+    """One oracle step at the headline's shape on N = 3e4 particles."""
+    N, p, n, Nx, dt = 30_000, 256, 32, 256, 0.1
+    etas = W.hammersley_params(p, {"vb": (4.0, 5.0)}, {"alpha": 0.04, "sigma_b": 0.5})
+    X0, V0 = W.load_batch(W.BUMP_ON_TAIL, etas, N, quiet=False)
+    U, Z, _ = csvd.csvd_init(X0, V0, n)
+    g = pic.make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+    U1, Z1, info = reduced.prk2_step(U, Z, dt, g)
+    E1, H1 = reduced.energies(U1, Z1, g)
+    return (N, p, n, Nx, dt), U, Z, g, U1, Z1, E1, H1, info
+
+
+@pytest.mark.parametrize("tc", [True, False])
+def test_precision_form_at_headline_shape(ctx, headline_shape_reference, tc):
+    """The kernel instances the headline runs (2n = 64, p = 256, Nx = 256:
+    the tensor-core deposit and projection, or the FP32 SIMT deposit with its
+    register-resident coefficients, and the chunked Gamma zeta^H), one step of
+    the FP32 form with re-orthonormalisation against the FP64 oracle: the
+    one-step gate of 1e-6 in H and E, 1e-5 in UZ."""
+    from paper_2201_05555_gb300 import make_grid
+    (N, p, n, Nx, dt), U, Z, g, U1, Z1, E1, H1, info = headline_shape_reference
+    grid = make_grid(N, Nx, W.BUMP_ON_TAIL.L)
+    ctx.tensor_cores(tc)
+    try:
+        Qd, Zd = T(q_storage(U)), T(Z)
+        ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, reortho=True, trace=False)
+        Eg, Hg, r = ctx.reduced_energy(grid, Qd, Zd)
+        ctx.sync_status()
+    finally:
+        ctx.tensor_cores(True)
+    Ug, Zg = U_of(Qd.cpu().numpy()), Zd.cpu().numpy()
+    err = {"UZ": rel(Ug @ Zg, U1 @ Z1), "Z": rel(Zg, Z1),
+           "E": float(np.max(np.abs(Eg.cpu().numpy() - E1) / np.abs(E1))),
+           "H": float(np.max(np.abs(Hg.cpu().numpy() - H1) / np.abs(H1))),
+           "manifold": float(r.cpu()), "oracle_iters": info["iters"]}
+    print("headline shape, tensor cores", tc, json.dumps(err))
+    assert err["UZ"] < 1e-5 and err["E"] <= 1e-6 and err["H"] <= 1e-6, err
+    assert err["manifold"] < 1e-12

@@ -239,3 +239,22 @@ def test_serve_timeout_cancel_invalid():
     with pytest.raises(VPError):
         s.submit(7, rows, **long_q)
     s.close()
+
+
+def test_serve_destroy_drains_then_cancels():
+    """vp_server_destroy with a drain timeout: short queries finish within it
+    (VP_OK); a long one is still running at a short timeout, is cancelled at
+    its next 16-step boundary and the call reports VP_ETIMEDOUT."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_05555_gb300 import Server
+    rows, _ = eta_rows(1, 16)
+    s = Server(0, hbm_budget=8 << 30, max_slots=2)
+    for _ in range(3):
+        s.submit(1, rows, N=20_000, Nx=128, n_max=5, dt=0.05, nsteps=32, arith=1)
+    assert s.close(drain_timeout_ms=120_000) == 0
+    s = Server(0, hbm_budget=8 << 30, max_slots=1)
+    s.submit(1, rows, N=200_000, Nx=128, n_max=6, dt=0.05, nsteps=4000, arith=1)
+    t = time.perf_counter()
+    assert s.close(drain_timeout_ms=300) == 5  # VP_ETIMEDOUT
+    assert time.perf_counter() - t < 60
