@@ -736,7 +736,8 @@ vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
  * VP_K_INIT the complex-SVD start and the re-orthonormalisation factor;
  * VP_K_DEPOSIT_DIAG the double-float deposit of the FP64-accurate energy
  * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits;
- * VP_K_PROJECT_TC the projection and VP_K_DEPOSIT_TC the deposit of the FP32
+ * VP_K_PROJECT_TC the projection, VP_K_DEPOSIT_TC the deposit and
+ * VP_K_GRAM_TC the Gram matrices (complex pairs and the real G_V) of the FP32
  * form with their contractions on the tensor cores. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
@@ -745,7 +746,8 @@ typedef enum vp_kernel {
   VP_K_COEFF_UPDATE, VP_K_AXPY, VP_K_ADD_LINEAR, VP_K_ENERGIES, VP_K_SPLIT, VP_K_DEPOSIT_LP,
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
-  VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_PROJECT_TC, VP_K_DEPOSIT_TC, VP_K_COUNT
+  VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_PROJECT_TC, VP_K_DEPOSIT_TC,
+  VP_K_GRAM_TC, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

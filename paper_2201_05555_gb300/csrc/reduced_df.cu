@@ -1083,6 +1083,13 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_GRAM: {
+      if constexpr (AR::kVec4) {
+        if (A.tc && gram_tc_supported(n, A.gram.nblk, A.gram.npairs) &&
+            (int64_t)(A.gridx - 1) * 32 < N) {
+          gram_tc(N, n, A.gram, 0, A.part, A.gridx, A.status, st);
+          break;
+        }
+      }
       int total = A.gram.npairs * n * n;
       int gy = ceil_div(total, TILE_THREADS * GDF_EPT);
       size_t smem = 16 + 2 * sizeof(V) * A.gram.nblk * GDF_ROWS * n2;
@@ -1091,6 +1098,16 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_GRAM_REAL: {
+      if constexpr (AR::kVec4) {
+        if (A.tc && gram_tc_supported(n, 1, 1) && (int64_t)(A.gridx - 1) * 32 < N) {
+          GramArgsLP gr{};
+          gr.blk[0] = A.v0;
+          gr.nblk = 1;
+          gr.npairs = 1;
+          gram_tc(N, n, gr, 1, A.part, A.gridx, A.status, st);
+          break;
+        }
+      }
       int m = n2;
       int gy = ceil_div(m * m, TILE_THREADS * GDF_EPT);
       size_t smem = sizeof(V) * GDF_ROWS * (m + 1);

@@ -396,6 +396,14 @@ struct RedDF {
     const bool tc = a.tc && arith == 2 && project_tc_supported(n, p, R.g.Nx);
     VP_K(tc ? VP_K_PROJECT_TC : VP_K_PROJECT_LP, lp_launch(arith, LP_PROJECT, a, st));
   }
+  // one or two CTAs per SM (shared memory), at most one per 32-row tile and
+  // within the partial buffer
+  int gram_tc_grid(int nblk) const {
+    int64_t g = (int64_t)ctx->num_sms * (nblk <= 2 ? 2 : 1);
+    g = std::min<int64_t>(g, (N + 31) / 32);
+    g = std::min<int64_t>(g, R.w.gx_gram);
+    return (int)std::max<int64_t>(g, 1);
+  }
   void grams(std::initializer_list<const void*> blks,
              std::initializer_list<std::pair<int, int>> pairs, double2* out) {
     LpArgs a = base();
@@ -406,9 +414,10 @@ struct RedDF {
       ++a.gram.npairs;
     }
     a.part = R.w.part;
-    a.gridx = R.w.gx_gram;
-    VP_K(VP_K_GRAM_LP, lp_launch(arith, LP_GRAM, a, st));
-    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)a.gram.npairs * n * n * 2, R.w.part,
+    const bool tc = a.tc && arith == 2 && gram_tc_supported(n, a.gram.nblk, a.gram.npairs);
+    a.gridx = tc ? gram_tc_grid(a.gram.nblk) : R.w.gx_gram;
+    VP_K(tc ? VP_K_GRAM_TC : VP_K_GRAM_LP, lp_launch(arith, LP_GRAM, a, st));
+    VP_K(VP_K_REDUCE, reduce_partials(a.gridx, (int64_t)a.gram.npairs * n * n * 2, R.w.part,
                                       reinterpret_cast<double*>(out), nullptr, st));
     comm_sum_f64(ctx, reinterpret_cast<double*>(out), (int64_t)a.gram.npairs * n * n * 2, st);
   }
@@ -416,9 +425,10 @@ struct RedDF {
     LpArgs a = base();
     a.v0 = const_cast<void*>(Q2);
     a.part = R.w.part;
-    a.gridx = R.w.gx_gram;
-    VP_K(VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
-    VP_K(VP_K_REDUCE, reduce_partials(R.w.gx_gram, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
+    const bool tc = a.tc && arith == 2 && gram_tc_supported(n, 1, 1);
+    a.gridx = tc ? gram_tc_grid(1) : R.w.gx_gram;
+    VP_K(tc ? VP_K_GRAM_TC : VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
+    VP_K(VP_K_REDUCE, reduce_partials(a.gridx, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
     comm_sum_f64(ctx, GVraw, (int64_t)4 * n * n, st);
   }
   void comb(std::initializer_list<const void*> xs, const double2* C, double* out_d, void* out_v,
@@ -1225,7 +1235,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd",
-    "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc"};
+    "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1414,6 +1424,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   df_init();
   tc_init();
   tc_deposit_init();
+  tc_gram_init();
   init_kernels_init();
   deim_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {

@@ -404,6 +404,13 @@ void deposit_tc(const GridC& g, int64_t N, int n, int p, const float* Q2, const 
                 unsigned long long* counts, uint16_t* jout, int gridx, const int* skip,
                 int* status, cudaStream_t st);
 void tc_deposit_init();
+// Gram matrices of the FP32 rows on the tensor cores: the complex pairs of
+// a GramArgsLP (real_out = 0) or the real Gram of block 0 (real_out = 1),
+// per-block partials in the layout of the SIMT kernels.
+bool gram_tc_supported(int n, int nblk, int npairs);
+void gram_tc(int64_t N, int n, const GramArgsLP& a, int real_out, double* part, int gridx,
+             int* status, cudaStream_t st);
+void tc_gram_init();
 // typed.cu: per-step calls on FP64 / FP32 / BF16 inputs (dtype 0 / 1 / 2)
 int vp_dtype_size(int dtype);
 void deposit_typed(const GridC& g, int64_t N, int p, const void* X, int64_t ldx, int dtype,

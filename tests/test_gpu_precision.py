@@ -169,9 +169,10 @@ def test_precision_form_200_steps_against_oracle(ctx, family):
                                    dict(N=7_001, p=40, n=10, Nx=128),
                                    dict(N=3_001, p=256, n=16, Nx=256)])
 def test_tensor_core_kernels_match_simt(ctx, shape):
-    """The FP32 form with its projection and its deposit's reconstruction on
-    the tensor cores (tcgen05, TF32 operands split in two, FP32 accumulation in
-    tensor memory) against the same step with the FP32 SIMT kernels and
+    """The FP32 form with its projection, its deposit's reconstruction and its
+    Gram matrices on the tensor cores (tcgen05, TF32 operands split in two,
+    FP32 accumulation in tensor memory) against the same step with the FP32
+    SIMT kernels and
     against the FP64 oracle: one step from the same start; the tensor-core
     kernels must have run, and only they."""
     from paper_2201_05555_gb300 import make_grid
@@ -187,16 +188,19 @@ def test_tensor_core_kernels_match_simt(ctx, shape):
         ctx.tensor_cores(tc)
         Qd, Zd = T(q_storage(U)), T(Z)
         ctx.profile_reset()
-        ctx.profile_enable(["k_project_tc", "k_project_lp", "k_deposit_tc", "k_deposit_lp"])
+        ctx.profile_enable(["k_project_tc", "k_project_lp", "k_deposit_tc", "k_deposit_lp",
+                            "k_gram_tc", "k_gram_lp"])
         ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, reortho=True, trace=False)
         ctx.sync_status()
         prof = ctx.profile_read()
         ctx.profile_enable([])
         out[tc] = (U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy(), prof)
     ctx.tensor_cores(True)
-    for k in ("project", "deposit"):
-        assert out[True][1][f"k_{k}_tc"][0] > 0 and out[True][1][f"k_{k}_lp"][0] == 0
-        assert out[False][1][f"k_{k}_tc"][0] == 0 and out[False][1][f"k_{k}_lp"][0] > 0
+    for k in ("project", "deposit", "gram"):
+        # the Gram of the re-orthonormalisation stays double-float (one launch)
+        rest = 1 if k == "gram" else 0
+        assert out[True][1][f"k_{k}_tc"][0] > 0 and out[True][1][f"k_{k}_lp"][0] == rest
+        assert out[False][1][f"k_{k}_tc"][0] == 0 and out[False][1][f"k_{k}_lp"][0] > rest
     Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
     ref = Uo @ Zo
     e_tc, e_simt = rel(out[True][0], ref), rel(out[False][0], ref)
