@@ -809,7 +809,8 @@ def kernel_flop(kern, N, n, p):
     the position; Gamma zeta^H: V_r (2n) and the complex product (4n))."""
     per = {"k_deposit_lp": 4 * n, "k_deposit_tc": 4 * n, "k_deposit_lp_diag": 4 * n,
            "k_deposit_reduced": 4 * n, "k_project_lp": 4 * n, "k_project_tc": 4 * n,
-           "k_project": 8 * n, "k_basis_M_lp": 12 * n, "k_basis_M": 12 * n}.get(kern)
+           "k_project": 8 * n, "k_basis_M_lp": 12 * n, "k_basis_M_tc": 12 * n,
+           "k_basis_M": 12 * n}.get(kern)
     return None if per is None else N * p * per
 
 
@@ -822,7 +823,7 @@ def working_launches(kern, rounds, steps, launches):
         return rounds + 2 * steps
     if kern in ("k_project_lp", "k_project_tc", "k_project"):
         return rounds
-    if kern in ("k_basis_M_lp", "k_basis_M"):
+    if kern in ("k_basis_M_lp", "k_basis_M_tc", "k_basis_M"):
         return 2 * steps
     return launches
 

@@ -737,8 +737,9 @@ vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
  * VP_K_DEPOSIT_DIAG the double-float deposit of the FP64-accurate energy
  * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits;
  * VP_K_PROJECT_TC the projection, VP_K_DEPOSIT_TC the deposit and
- * VP_K_GRAM_TC the Gram matrices (complex pairs and the real G_V) of the FP32
- * form with their contractions on the tensor cores. */
+ * VP_K_GRAM_TC the Gram matrices (complex pairs and the real G_V) and
+ * VP_K_BASIS_M_TC the basis velocity product Gamma zeta^H of the FP32 form
+ * with their contractions on the tensor cores. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
@@ -747,7 +748,7 @@ typedef enum vp_kernel {
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
   VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_PROJECT_TC, VP_K_DEPOSIT_TC,
-  VP_K_GRAM_TC, VP_K_COUNT
+  VP_K_GRAM_TC, VP_K_BASIS_M_TC, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

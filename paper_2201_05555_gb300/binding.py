@@ -147,7 +147,8 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp", "k_project_lp",
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
            "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd", "k_jacobi_sym",
-           "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc"]
+           "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc",
+           "k_basis_M_tc"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None

@@ -1051,6 +1051,13 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_BASIS_M: {
       int PC = chunk_w(p, g.Nx);
+      if constexpr (AR::kVec4) {
+        if (A.tc && A.bop && basis_tc_supported(n, p)) {
+          basis_tc(g, N, n, p, PC, (const float*)A.v0, (const float*)A.v1, (const float*)A.v2,
+                   A.j, (float*)A.v3, A.bop, A.num_sms, A.status, st);
+          break;
+        }
+      }
       {
         const int nch = ceil_div(p, PC);
         const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);

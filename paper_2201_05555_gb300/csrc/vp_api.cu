@@ -117,6 +117,7 @@ struct RedWS {
   double* rows[5];
   float2 *Q2a, *Q2b;  // row-format shadows of Q0 and Q_half (float2 or float)
   uint16_t* jcell;    // cell index per (particle, sample), N x p
+  float* bop;         // the tensor-core Gamma zeta^H operand (FP32 form)
   float2* frows[5];   // row blocks of the FP32-based step
   float2 *Z2, *Zh2, *F2;
   double* phi_out = nullptr;  // when set, the FP32-based field also writes the potentials
@@ -169,7 +170,7 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
                    2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) +
-                   sub_ws_bytes(N, n, nsub, Nx)
+                   arena_bytes(basis_tc_bop_floats(n, p), 4) + sub_ws_bytes(N, n, nsub, Nx)
              : 0);
 }
 
@@ -210,6 +211,7 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.F2 = df ? a.take<float2>(pn) : nullptr;
+  w.bop = df ? a.take<float>(basis_tc_bop_floats(n, p)) : nullptr;
   w.sub = RedWS::Sub();
   if (df && nsub > 0) {
     const size_t ps = (size_t)nsub * (Nx > 0 ? Nx : 1), zs = (size_t)n2 * nsub;
@@ -457,7 +459,9 @@ struct RedDF {
     a.v2 = w.F2;
     a.v3 = M;
     a.j = w.jcell;
-    VP_K(VP_K_BASIS_M_LP, lp_launch(arith, LP_BASIS_M, a, st));
+    a.bop = w.bop;
+    const bool tc = a.tc && arith == 2 && w.bop && basis_tc_supported(n, p);
+    VP_K(tc ? VP_K_BASIS_M_TC : VP_K_BASIS_M_LP, lp_launch(arith, LP_BASIS_M, a, st));
     grams({Q2, M}, {{0, 1}}, w.grams);
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
     comb({M, Q2}, w.C, nullptr, out);
@@ -1235,7 +1239,8 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_coeff_update", "k_axpy", "k_add_linear", "k_energies", "k_split", "k_deposit_lp",
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd",
-    "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc"};
+    "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc",
+    "k_basis_M_tc"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1425,6 +1430,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   tc_init();
   tc_deposit_init();
   tc_gram_init();
+  tc_basis_init();
   init_kernels_init();
   deim_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {

@@ -304,6 +304,7 @@ struct LpArgs {
   const int* tune = nullptr;  // vp_ctx::tune (null: defaults)
   int* status = nullptr;      // device status word
   bool tc = false;            // tensor-core kernels where they apply (FP32 rows)
+  float* bop = nullptr;       // scratch of the tensor-core Gamma zeta^H (basis_tc_bop_floats)
 };
 
 // Cell indices of the FP32-based path are stored tile by tile: for row tile
@@ -411,6 +412,14 @@ bool gram_tc_supported(int n, int nblk, int npairs);
 void gram_tc(int64_t N, int n, const GramArgsLP& a, int real_out, double* part, int gridx,
              int* status, cudaStream_t st);
 void tc_gram_init();
+// M = Gamma zeta^H of the FP32 rows on the tensor cores (the split form
+// [Q | G] [W ; a^T | -b^T]); bop holds basis_tc_bop_floats(n, p) floats.
+bool basis_tc_supported(int n, int p);
+size_t basis_tc_bop_floats(int n, int p);
+void basis_tc(const GridC& g, int64_t N, int n, int p, int PC, const float* Q2, const float* Z2,
+              const float* F2, const uint16_t* jt, float* M, float* bop, int num_sms,
+              int* status, cudaStream_t st);
+void tc_basis_init();
 // typed.cu: per-step calls on FP64 / FP32 / BF16 inputs (dtype 0 / 1 / 2)
 int vp_dtype_size(int dtype);
 void deposit_typed(const GridC& g, int64_t N, int p, const void* X, int64_t ldx, int dtype,

@@ -169,8 +169,8 @@ def test_precision_form_200_steps_against_oracle(ctx, family):
                                    dict(N=7_001, p=40, n=10, Nx=128),
                                    dict(N=3_001, p=256, n=16, Nx=256)])
 def test_tensor_core_kernels_match_simt(ctx, shape):
-    """The FP32 form with its projection, its deposit's reconstruction and its
-    Gram matrices on the tensor cores (tcgen05, TF32 operands split in two,
+    """The FP32 form with its projection, its deposit's reconstruction, its
+    Gram matrices and its basis velocity Gamma zeta^H on the tensor cores (tcgen05, TF32 operands split in two,
     FP32 accumulation in tensor memory) against the same step with the FP32
     SIMT kernels and
     against the FP64 oracle: one step from the same start; the tensor-core
@@ -189,14 +189,14 @@ def test_tensor_core_kernels_match_simt(ctx, shape):
         Qd, Zd = T(q_storage(U)), T(Z)
         ctx.profile_reset()
         ctx.profile_enable(["k_project_tc", "k_project_lp", "k_deposit_tc", "k_deposit_lp",
-                            "k_gram_tc", "k_gram_lp"])
+                            "k_gram_tc", "k_gram_lp", "k_basis_M_tc", "k_basis_M_lp"])
         ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, reortho=True, trace=False)
         ctx.sync_status()
         prof = ctx.profile_read()
         ctx.profile_enable([])
         out[tc] = (U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy(), prof)
     ctx.tensor_cores(True)
-    for k in ("project", "deposit", "gram"):
+    for k in ("project", "deposit", "gram", "basis_M"):
         # the Gram of the re-orthonormalisation stays double-float (one launch)
         rest = 1 if k == "gram" else 0
         assert out[True][1][f"k_{k}_tc"][0] > 0 and out[True][1][f"k_{k}_lp"][0] == rest
