@@ -654,13 +654,26 @@ typedef enum vp_tune_knob {
   VP_TUNE_AFFINE_LP, VP_TUNE_COUNT
 } vp_tune_knob;
 vp_status vp_tune_set(vp_ctx* ctx, int32_t knob, int32_t blocks_per_sm);
-/* enable = 1 (default): in the FP32 form (arith = 2) the projection g_X =
- * U_X^T G (Sec. 3.2, eq. grads) and the reconstruction X_r = U_X Z of the
- * deposit run on the tensor cores (tcgen05, TF32 operands split in two, FP32
- * accumulation in tensor memory) when 2n <= 64 (the deposit: 2n a multiple
- * of 4) and the sample chunk of the particle kernels is 16 or 32 wide;
- * enable = 0: always the FP32 SIMT kernels.  Other values: VP_EINVAL. */
-vp_status vp_tensor_cores(vp_ctx* ctx, int32_t enable);
+/* Tensor-core kernels of the FP32 form (arith = 2; tcgen05, kind::tf32, FP32
+ * values split into TF32 pieces, FP32 accumulation in tensor memory), one
+ * bit each: the reconstruction X_r = U_X Z of the deposit (Sec. 3.2; 2n <= 64
+ * a multiple of 4, sample chunks of 16 or 32), the projection g_X = U_X^T G
+ * (eq. grads; 2n <= 64), the Gram matrices X^H Y and U_V^T U_V (2n <= 64),
+ * the basis velocity Gamma zeta^H (Sec. 3.2, 5; 2n <= 64) and the row
+ * combinations sum_t X_t C_t of the basis velocity, the Cayley retraction and
+ * the tangent velocity (2n <= 64).  A kernel whose bit is clear, or whose
+ * shape does not apply, runs on the FP32 CUDA cores. */
+typedef enum vp_tc_kernel {
+  VP_TC_DEPOSIT = 1, VP_TC_PROJECT = 2, VP_TC_GRAM = 4, VP_TC_BASIS_M = 8, VP_TC_AFFINE = 16,
+  VP_TC_ALL = 31,
+  /* the default leaves the deposit on the CUDA cores: its cell and weight
+   * come from the position, whose two-piece TF32 split (2^-22 of each
+   * operand) measurably adds to the energy error of a step */
+  VP_TC_DEFAULT = VP_TC_PROJECT | VP_TC_GRAM | VP_TC_BASIS_M | VP_TC_AFFINE
+} vp_tc_kernel;
+/* mask: an OR of vp_tc_kernel bits (default VP_TC_DEFAULT; 0: all SIMT).
+ * Values outside [0, VP_TC_ALL]: VP_EINVAL. */
+vp_status vp_tensor_cores(vp_ctx* ctx, int32_t mask);
 vp_status vp_tune_get(vp_ctx* ctx, int32_t knob, int32_t* blocks_per_sm);
 /* Autotuner: on the caller's state (Q N x 2n, Z 2n x p; read only) times
  * every knob's kernel at 1, 2, 3, 4, 6 and 8 blocks per SM (`reps` launches
@@ -737,9 +750,10 @@ vp_status vp_selftest_wait(vp_ctx* ctx, int32_t spins, void* stream);
  * VP_K_DEPOSIT_DIAG the double-float deposit of the FP64-accurate energy
  * diagnostic in the FP32 form (arith = 2), apart from its FP32 deposits;
  * VP_K_PROJECT_TC the projection, VP_K_DEPOSIT_TC the deposit and
- * VP_K_GRAM_TC the Gram matrices (complex pairs and the real G_V) and
- * VP_K_BASIS_M_TC the basis velocity product Gamma zeta^H of the FP32 form
- * with their contractions on the tensor cores. */
+ * VP_K_GRAM_TC the Gram matrices (complex pairs and the real G_V),
+ * VP_K_BASIS_M_TC the basis velocity product Gamma zeta^H and VP_K_AFFINE_TC
+ * the row combinations sum_t X_t C_t of the FP32 form with their
+ * contractions on the tensor cores. */
 typedef enum vp_kernel {
   VP_K_DEPOSIT = 0, VP_K_RHO, VP_K_POISSON, VP_K_GATHER, VP_K_FULL_STEP, VP_K_RECONSTRUCT,
   VP_K_DEPOSIT_REDUCED, VP_K_PROJECT, VP_K_BASIS_M, VP_K_GRAM, VP_K_GRAM_REAL, VP_K_REDUCE,
@@ -748,7 +762,7 @@ typedef enum vp_kernel {
   VP_K_PROJECT_LP, VP_K_BASIS_M_LP, VP_K_PREP_LP, VP_K_GRAM_LP, VP_K_GRAM_REAL_LP, VP_K_AFFINE_LP,
   VP_K_INIT, VP_K_LOAD, VP_K_SUBSET, VP_K_HYPER, VP_K_DEIM_ROUND, VP_K_DEIM, VP_K_DMD,
   VP_K_JACOBI_SYM, VP_K_DEPOSIT_DIAG, VP_K_PROJECT_TC, VP_K_DEPOSIT_TC,
-  VP_K_GRAM_TC, VP_K_BASIS_M_TC, VP_K_COUNT
+  VP_K_GRAM_TC, VP_K_BASIS_M_TC, VP_K_AFFINE_TC, VP_K_COUNT
 } vp_kernel;
 
 /* Every launch is counted per kernel.  Kernels whose bit (1 << vp_kernel) is

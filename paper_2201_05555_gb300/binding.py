@@ -140,6 +140,11 @@ _SIGS = [
 ]
 
 # vp_kernel ids (include/vp.h)
+# vp_tc_kernel bits of vp_tensor_cores
+TC_KERNELS = {"deposit": 1, "project": 2, "gram": 4, "basis_M": 8, "affine": 16}
+TC_ALL = 31
+TC_DEFAULT = 30  # all but the deposit
+
 KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step",
            "k_reconstruct", "k_deposit_reduced", "k_project", "k_basis_M", "k_gram",
            "k_gram_real", "k_reduce_partials", "k_affine", "k_cell_gradient",
@@ -148,7 +153,7 @@ KERNELS = ["k_deposit", "k_counts_to_rho", "k_poisson", "k_gather", "k_full_step
            "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp", "k_init",
            "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd", "k_jacobi_sym",
            "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc",
-           "k_basis_M_tc"]
+           "k_basis_M_tc", "k_affine_tc"]
 KID = {k: i for i, k in enumerate(KERNELS)}
 
 _lib = None
@@ -243,9 +248,19 @@ class Context:
         return int(self.lib.vp_ctx_workspace_bytes(self.h))
 
     # -- profiling (launch counters, CUDA-event timers on the launch stream)
-    def tensor_cores(self, enable: bool):
-        """Use the tcgen05 kernels of the FP32 form where they apply (default on)."""
-        self._check(self.lib.vp_tensor_cores(self.h, int(bool(enable))), "tensor_cores")
+    def tensor_cores(self, enable=True):
+        """Which tcgen05 kernels of the FP32 form run where they apply: True
+        (the library default, TC_DEFAULT), False (none), an int mask of
+        vp_tc_kernel bits, or names from TC_KERNELS."""
+        if enable is True or enable is False:
+            mask = TC_DEFAULT if enable else 0
+        elif isinstance(enable, int):
+            mask = enable
+        else:
+            mask = 0
+            for name in enable:
+                mask |= TC_KERNELS[name]
+        self._check(self.lib.vp_tensor_cores(self.h, mask), "tensor_cores")
 
     def profile_enable(self, kernels=()):
         mask = 0

@@ -999,7 +999,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_DEPOSIT: {
       if constexpr (AR::kVec4) {  // FP32 rows: reconstruction on the tensor cores
-        if (A.tc && deposit_tc_supported(n, p, g.Nx, g.Kp)) {
+        if ((A.tc & VP_TC_DEPOSIT) && deposit_tc_supported(n, p, g.Nx, g.Kp)) {
           const int ch = ceil_div(p, chunk_w(p, g.Nx));
           const int64_t tiles = ceil_div(N, 128);
           const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, A.num_sms / ch));
@@ -1031,7 +1031,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_PROJECT: {
       if constexpr (AR::kVec4) {  // FP32 rows: tensor cores where the shapes allow
-        if (A.tc && project_tc_supported(n, p, g.Nx)) {
+        if ((A.tc & VP_TC_PROJECT) && project_tc_supported(n, p, g.Nx)) {
           project_tc(g, N, n, p, (const float*)A.v0, (const float*)A.v1, A.j, A.part, A.gridx,
                      A.skip, A.status, st);
           break;
@@ -1052,7 +1052,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     case LP_BASIS_M: {
       int PC = chunk_w(p, g.Nx);
       if constexpr (AR::kVec4) {
-        if (A.tc && A.bop && basis_tc_supported(n, p)) {
+        if ((A.tc & VP_TC_BASIS_M) && A.bop && basis_tc_supported(n, p)) {
           basis_tc(g, N, n, p, PC, (const float*)A.v0, (const float*)A.v1, (const float*)A.v2,
                    A.j, (float*)A.v3, A.bop, A.num_sms, A.status, st);
           break;
@@ -1091,7 +1091,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_GRAM: {
       if constexpr (AR::kVec4) {
-        if (A.tc && gram_tc_supported(n, A.gram.nblk, A.gram.npairs) &&
+        if ((A.tc & VP_TC_GRAM) && gram_tc_supported(n, A.gram.nblk, A.gram.npairs) &&
             (int64_t)(A.gridx - 1) * 32 < N) {
           gram_tc(N, n, A.gram, 0, A.part, A.gridx, A.status, st);
           break;
@@ -1106,7 +1106,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
     }
     case LP_GRAM_REAL: {
       if constexpr (AR::kVec4) {
-        if (A.tc && gram_tc_supported(n, 1, 1) && (int64_t)(A.gridx - 1) * 32 < N) {
+        if ((A.tc & VP_TC_GRAM) && gram_tc_supported(n, 1, 1) && (int64_t)(A.gridx - 1) * 32 < N) {
           GramArgsLP gr{};
           gr.blk[0] = A.v0;
           gr.nblk = 1;
@@ -1122,6 +1122,12 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
       break;
     }
     case LP_AFFINE: {
+      if constexpr (AR::kVec4) {
+        if ((A.tc & VP_TC_AFFINE) && A.bop && affine_tc_supported(n, A.aff.nterms)) {
+          affine_tc(g, N, n, A.aff, A.C, A.dout, (float*)A.v0, A.bop, A.num_sms, A.status, st);
+          break;
+        }
+      }
       // rows per tile: 64, or fewer when two stages of every term would not fit
       int TR = TILE_ROWS;
       auto smem_for = [&](int tr) {

@@ -74,10 +74,27 @@ static __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// TF32 part of x (low 13 mantissa bits cleared) and the exact remainder
+// x (finite) rounded to the nearest TF32 value, ties away from zero: half a
+// unit of the 13 dropped mantissa bits is added to the magnitude bits (a
+// carry into the exponent is the correct rounding up) and the 13 bits are
+// cleared; two integer operations instead of a conversion
+static __device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+// x as hi + lo with both parts TF32: hi = x rounded to TF32, lo = the exact
+// remainder x - hi rounded to TF32, so that |x - hi - lo| <= 2^-22 |x| (the
+// tensor cores read only the TF32 bits of an operand: a remainder left in
+// FP32 would lose its low bits to truncation there, up to 2^-20 |x|)
 static __device__ __forceinline__ float2 tf32_split(float x) {
-  const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  return make_float2(h, x - h);
+  const float h = tf32_rna(x);
+  return make_float2(h, tf32_rna(x - h));
+}
+// x as the exact sum of three TF32 values (11 + 11 + the remaining <= 2
+// significant bits): x - a1 and (x - a1) - a2 are exact in FP32
+static __device__ __forceinline__ float3 tf32_split3(float x) {
+  const float a1 = tf32_rna(x), r1 = x - a1;
+  const float a2 = tf32_rna(r1);
+  return make_float3(a1, a2, tf32_rna(r1 - a2));
 }
 
 // 16 consecutive columns of this warp's 32 lanes: v[j] = D[lane][col + j]

@@ -10,8 +10,8 @@
 // strided set of tiles):
 //   D (128 x 2 PC) = Q_hi [z_hi | z_lo] + Q_lo [z_hi | z_lo]   (K = 2n),
 // with z = zeta / h and the B half of its rows negated, every FP32 value v
-// split into its TF32 part v_hi (low 13 mantissa bits cleared) and the
-// remainder v_lo = v - v_hi; x_li = D[l][i] + D[l][PC + i], the product at
+// split into v_hi = v rounded to TF32 and v_lo = v - v_hi rounded to TF32
+// (|v - v_hi - v_lo| <= 2^-22 |v|); x_li = D[l][i] + D[l][PC + i], close to
 // the accuracy of FP32 row arithmetic (FP32 accumulation in tensor memory).
 //
 // Warp roles (21 warps): warps 16-19 stage the Q tiles (split, K-major

@@ -7,9 +7,10 @@
 // All of them come from the real product P = [Xr Xi]^T [Yr Yi] (2n x 2n):
 // X^H Y = (P11 + P22) + i (P12 - P21).  Per CTA (a strided set of 32-row
 // tiles) and pair s the accumulator D_s (128 x 64) = [X_hi; X_lo]^T (Y_hi +
-// Y_lo) lives in tensor memory (64 columns per pair), with every FP32 value v
-// split into its TF32 part v_hi and the remainder v_lo = v - v_hi; rows c and
-// c + 64 of D_s add up, in FP64, to P's row c.  2n <= 64, zero-padded.
+// Y_lo) lives in tensor memory (64 columns per pair), with every FP32 value
+// v split into v_hi = v rounded to TF32 and v_lo = v - v_hi rounded to TF32;
+// rows c and c + 64 of D_s add up, in FP64, to P's row c.  2n <= 64,
+// zero-padded.
 //
 // One staged buffer per row block and stage, [hi | lo] in the K-major
 // no-swizzle canonical layout (element (c, k) of the hi half at byte

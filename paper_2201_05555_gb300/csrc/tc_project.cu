@@ -8,12 +8,12 @@
 // accumulator D lives in tensor memory for the CTA's whole life:
 //   D (128 x PC) = A (128 x K) B (K x PC),
 //   A = [Q_hi^T; Q_lo^T]  (rows 0..63: the FP32 row Q_l split as
-//                          Q_hi = Q with its low 13 mantissa bits cleared, the
-//                          TF32 part; rows 64..127: Q_lo = Q - Q_hi),
+//                          Q_hi = Q rounded to TF32; rows 64..127: Q_lo =
+//                          Q - Q_hi rounded to TF32, tf32_split),
 //   B = G_hi + G_lo       (two MMAs with the same A, G split the same way),
 // so rows m and m + 64 of D hold Q_hi G and Q_lo G, whose sum (taken in FP64
-// in the epilogue) is Q G up to the TF32 rounding of Q_lo G_lo and of G_lo and
-// the FP32 accumulation: the accuracy of FP32 row arithmetic.  2n <= 64
+// in the epilogue) is Q G up to the split (2^-22 of each operand) and the
+// FP32 accumulation: close to the accuracy of FP32 row arithmetic.  2n <= 64
 // (zero-padded to 64).
 //
 // Operands are staged by all 256 threads in the K-major, no-swizzle canonical

@@ -117,7 +117,7 @@ struct RedWS {
   double* rows[5];
   float2 *Q2a, *Q2b;  // row-format shadows of Q0 and Q_half (float2 or float)
   uint16_t* jcell;    // cell index per (particle, sample), N x p
-  float* bop;         // the tensor-core Gamma zeta^H operand (FP32 form)
+  float* bop;         // operand of the tensor-core row products (FP32 form)
   float2* frows[5];   // row blocks of the FP32-based step
   float2 *Z2, *Zh2, *F2;
   double* phi_out = nullptr;  // when set, the FP32-based field also writes the potentials
@@ -170,7 +170,7 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
                    2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) +
-                   arena_bytes(basis_tc_bop_floats(n, p), 4) + sub_ws_bytes(N, n, nsub, Nx)
+                   arena_bytes(rows_tc_bop_floats(n, p), 4) + sub_ws_bytes(N, n, nsub, Nx)
              : 0);
 }
 
@@ -211,7 +211,7 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.F2 = df ? a.take<float2>(pn) : nullptr;
-  w.bop = df ? a.take<float>(basis_tc_bop_floats(n, p)) : nullptr;
+  w.bop = df ? a.take<float>(rows_tc_bop_floats(n, p)) : nullptr;
   w.sub = RedWS::Sub();
   if (df && nsub > 0) {
     const size_t ps = (size_t)nsub * (Nx > 0 ? Nx : 1), zs = (size_t)n2 * nsub;
@@ -359,7 +359,7 @@ struct RedDF {
     a.num_sms = ctx->num_sms;
     a.tune = ctx->tune;
     a.status = ctx->d_status;
-    a.tc = ctx->tensor_cores != 0;
+    a.tc = ctx->tensor_cores;
     return a;
   }
   // field at (Q2, Z): Z2 = Z and Zh2 = Z / h in row format (skipped when the
@@ -380,7 +380,7 @@ struct RedDF {
     a.counts = w.counts;
     a.j = w.jcell;
     a.skip = skip;
-    const bool tc = a.tc && arith == 2 && deposit_tc_supported(n, p, R.g.Nx, R.g.Kp);
+    const bool tc = (a.tc & VP_TC_DEPOSIT) && arith == 2 && deposit_tc_supported(n, p, R.g.Nx, R.g.Kp);
     VP_K(diag ? VP_K_DEPOSIT_DIAG : (tc ? VP_K_DEPOSIT_TC : VP_K_DEPOSIT_LP),
          lp_launch(arith, LP_DEPOSIT, a, st));
     comm_sum_u64(ctx, w.counts, (int64_t)p * R.g.Nx, st);
@@ -395,7 +395,7 @@ struct RedDF {
     a.part = R.w.part;
     a.gridx = R.w.gx_proj;
     a.skip = skip;
-    const bool tc = a.tc && arith == 2 && project_tc_supported(n, p, R.g.Nx);
+    const bool tc = (a.tc & VP_TC_PROJECT) && arith == 2 && project_tc_supported(n, p, R.g.Nx);
     VP_K(tc ? VP_K_PROJECT_TC : VP_K_PROJECT_LP, lp_launch(arith, LP_PROJECT, a, st));
   }
   // one or two CTAs per SM (shared memory), at most one per 32-row tile and
@@ -416,7 +416,7 @@ struct RedDF {
       ++a.gram.npairs;
     }
     a.part = R.w.part;
-    const bool tc = a.tc && arith == 2 && gram_tc_supported(n, a.gram.nblk, a.gram.npairs);
+    const bool tc = (a.tc & VP_TC_GRAM) && arith == 2 && gram_tc_supported(n, a.gram.nblk, a.gram.npairs);
     a.gridx = tc ? gram_tc_grid(a.gram.nblk) : R.w.gx_gram;
     VP_K(tc ? VP_K_GRAM_TC : VP_K_GRAM_LP, lp_launch(arith, LP_GRAM, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(a.gridx, (int64_t)a.gram.npairs * n * n * 2, R.w.part,
@@ -427,7 +427,7 @@ struct RedDF {
     LpArgs a = base();
     a.v0 = const_cast<void*>(Q2);
     a.part = R.w.part;
-    const bool tc = a.tc && arith == 2 && gram_tc_supported(n, 1, 1);
+    const bool tc = (a.tc & VP_TC_GRAM) && arith == 2 && gram_tc_supported(n, 1, 1);
     a.gridx = tc ? gram_tc_grid(1) : R.w.gx_gram;
     VP_K(tc ? VP_K_GRAM_TC : VP_K_GRAM_REAL_LP, lp_launch(arith, LP_GRAM_REAL, a, st));
     VP_K(VP_K_REDUCE, reduce_partials(a.gridx, (int64_t)4 * n * n, R.w.part, GVraw, nullptr, st));
@@ -441,7 +441,9 @@ struct RedDF {
     a.C = C;
     a.dout = out_d;
     a.v0 = out_v;
-    VP_K(VP_K_AFFINE_LP, lp_launch(arith, LP_AFFINE, a, st));
+    a.bop = R.w.bop;
+    const bool tc = (a.tc & VP_TC_AFFINE) && arith == 2 && R.w.bop && affine_tc_supported(n, a.aff.nterms);
+    VP_K(tc ? VP_K_AFFINE_TC : VP_K_AFFINE_LP, lp_launch(arith, LP_AFFINE, a, st));
   }
   void split(const double* Q, void* Q2) {
     LpArgs a = base();
@@ -460,7 +462,7 @@ struct RedDF {
     a.v3 = M;
     a.j = w.jcell;
     a.bop = w.bop;
-    const bool tc = a.tc && arith == 2 && w.bop && basis_tc_supported(n, p);
+    const bool tc = (a.tc & VP_TC_BASIS_M) && arith == 2 && w.bop && basis_tc_supported(n, p);
     VP_K(tc ? VP_K_BASIS_M_TC : VP_K_BASIS_M_LP, lp_launch(arith, LP_BASIS_M, a, st));
     grams({Q2, M}, {{0, 1}}, w.grams);
     VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
@@ -1047,10 +1049,10 @@ vp_status vp_ctx_set_comm(vp_ctx* ctx, const vp_comm* comm) {
   return VP_OK;
 }
 
-vp_status vp_tensor_cores(vp_ctx* ctx, int32_t enable) {
-  if (!ctx || (enable != 0 && enable != 1)) return VP_EINVAL;
+vp_status vp_tensor_cores(vp_ctx* ctx, int32_t mask) {
+  if (!ctx || mask < 0 || mask > VP_TC_ALL) return VP_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
-  ctx->tensor_cores = enable;
+  ctx->tensor_cores = mask;
   return VP_OK;
 }
 
@@ -1240,7 +1242,7 @@ static const char* kKernelNames[VP_K_COUNT] = {
     "k_project_lp", "k_basis_M_lp", "k_prep_lp", "k_gram_lp", "k_gram_real_lp", "k_affine_lp",
     "k_init", "k_load", "k_subset", "k_hyper", "k_deim_round", "k_deim", "k_dmd",
     "k_jacobi_sym", "k_deposit_lp_diag", "k_project_tc", "k_deposit_tc", "k_gram_tc",
-    "k_basis_M_tc"};
+    "k_basis_M_tc", "k_affine_tc"};
 
 static cudaEvent_t take_event(vp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -1430,7 +1432,7 @@ vp_status vp_ctx_create(vp_ctx** out, int device, size_t scratch_bytes) {
   tc_init();
   tc_deposit_init();
   tc_gram_init();
-  tc_basis_init();
+  tc_rows_init();
   init_kernels_init();
   deim_init();
   if (cudaDeviceSynchronize() != cudaSuccess) {

@@ -43,7 +43,7 @@ struct vp_ctx {
   std::vector<cudaEvent_t> event_pool;
   int tune[TUNE_COUNT] = {kTuneDefault[0], kTuneDefault[1], kTuneDefault[2], kTuneDefault[3],
                          kTuneDefault[4]};
-  int tensor_cores = 1;  // vp_tensor_cores: tcgen05 kernels where they apply
+  int tensor_cores = VP_TC_DEFAULT;  // vp_tensor_cores mask: tcgen05 kernels where they apply
   // particle sharding (vp_ctx_set_comm): sums over the rows of all ranks
   vp_comm comm{};
   bool comm_on = false;
@@ -303,8 +303,8 @@ struct LpArgs {
   double* dout = nullptr;
   const int* tune = nullptr;  // vp_ctx::tune (null: defaults)
   int* status = nullptr;      // device status word
-  bool tc = false;            // tensor-core kernels where they apply (FP32 rows)
-  float* bop = nullptr;       // scratch of the tensor-core Gamma zeta^H (basis_tc_bop_floats)
+  int tc = 0;                 // vp_tc_kernel mask: tensor-core kernels where they apply
+  float* bop = nullptr;       // scratch of the tensor-core row products (rows_tc_bop_floats)
 };
 
 // Cell indices of the FP32-based path are stored tile by tile: for row tile
@@ -412,14 +412,19 @@ bool gram_tc_supported(int n, int nblk, int npairs);
 void gram_tc(int64_t N, int n, const GramArgsLP& a, int real_out, double* part, int gridx,
              int* status, cudaStream_t st);
 void tc_gram_init();
-// M = Gamma zeta^H of the FP32 rows on the tensor cores (the split form
-// [Q | G] [W ; a^T | -b^T]); bop holds basis_tc_bop_floats(n, p) floats.
+// Row-block products of the FP32 rows on the tensor cores: M = Gamma zeta^H
+// (the split form [Q | G] [W ; a^T | -b^T]) and the combinations
+// sum_t X_t C_t of LP_AFFINE; bop holds rows_tc_bop_floats(n, p) floats.
 bool basis_tc_supported(int n, int p);
-size_t basis_tc_bop_floats(int n, int p);
+bool affine_tc_supported(int n, int nterms);
+size_t rows_tc_bop_floats(int n, int p);
 void basis_tc(const GridC& g, int64_t N, int n, int p, int PC, const float* Q2, const float* Z2,
               const float* F2, const uint16_t* jt, float* M, float* bop, int num_sms,
               int* status, cudaStream_t st);
-void tc_basis_init();
+void affine_tc(const GridC& g, int64_t N, int n, const AffineArgsLP& aff, const double2* C,
+               double* out_d, float* out_v, float* bop, int num_sms, int* status,
+               cudaStream_t st);
+void tc_rows_init();
 // typed.cu: per-step calls on FP64 / FP32 / BF16 inputs (dtype 0 / 1 / 2)
 int vp_dtype_size(int dtype);
 void deposit_typed(const GridC& g, int64_t N, int p, const void* X, int64_t ldx, int dtype,

@@ -75,6 +75,25 @@ def test_kernel_names_match_the_binding(lib):
     assert lib.vp_kernel_name(len(KERNELS)) == b"unknown"
 
 
+def test_tensor_core_bits_match_the_binding(lib):
+    # vp_tc_kernel of include/vp.h and the binding's masks agree; the context
+    # rejects masks outside [0, VP_TC_ALL] on the host (NULL context: EINVAL)
+    from paper_2201_05555_gb300.binding import TC_ALL, TC_DEFAULT, TC_KERNELS
+
+    text = open(os.path.join(ROOT, "include", "vp.h")).read()
+    body = re.search(r"typedef enum vp_tc_kernel \{(.*?)\} vp_tc_kernel;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    vals = dict(re.findall(r"(VP_TC_\w+)\s*=\s*(\d+)", body))
+    names = {"deposit": "VP_TC_DEPOSIT", "project": "VP_TC_PROJECT", "gram": "VP_TC_GRAM",
+             "basis_M": "VP_TC_BASIS_M", "affine": "VP_TC_AFFINE"}
+    assert {k: int(vals[v]) for k, v in names.items()} == TC_KERNELS
+    assert int(vals["VP_TC_ALL"]) == TC_ALL == sum(TC_KERNELS.values())
+    assert TC_DEFAULT == TC_ALL & ~TC_KERNELS["deposit"]
+    assert "VP_TC_DEFAULT = VP_TC_PROJECT | VP_TC_GRAM | VP_TC_BASIS_M | VP_TC_AFFINE" in body
+    lib.vp_tensor_cores.restype = ctypes.c_int32
+    assert lib.vp_tensor_cores(None, 1) == 1  # VP_EINVAL
+
+
 def test_no_fallback_without_the_library_or_a_gpu(monkeypatch, tmp_path):
     # the binding has no CPU path: a missing library and host tensors are errors
     import torch

@@ -10,6 +10,7 @@ import pytest
 import workloads as W
 from oracle import csvd, pic, reduced
 from tests.helpers import U_of, q_storage, rel
+from paper_2201_05555_gb300.binding import TC_ALL
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -170,7 +171,8 @@ def test_precision_form_200_steps_against_oracle(ctx, family):
                                    dict(N=3_001, p=256, n=16, Nx=256)])
 def test_tensor_core_kernels_match_simt(ctx, shape):
     """The FP32 form with its projection, its deposit's reconstruction, its
-    Gram matrices and its basis velocity Gamma zeta^H on the tensor cores (tcgen05, TF32 operands split in two,
+    Gram matrices, its basis velocity Gamma zeta^H and its row combinations
+    on the tensor cores (tcgen05, TF32 operands split in two,
     FP32 accumulation in tensor memory) against the same step with the FP32
     SIMT kernels and
     against the FP64 oracle: one step from the same start; the tensor-core
@@ -185,20 +187,22 @@ def test_tensor_core_kernels_match_simt(ctx, shape):
     dt = 0.1
     out = {}
     for tc in (True, False):
-        ctx.tensor_cores(tc)
+        ctx.tensor_cores(TC_ALL if tc else 0)
         Qd, Zd = T(q_storage(U)), T(Z)
         ctx.profile_reset()
         ctx.profile_enable(["k_project_tc", "k_project_lp", "k_deposit_tc", "k_deposit_lp",
-                            "k_gram_tc", "k_gram_lp", "k_basis_M_tc", "k_basis_M_lp"])
+                            "k_gram_tc", "k_gram_lp", "k_basis_M_tc", "k_basis_M_lp",
+                            "k_affine_tc", "k_affine_lp"])
         ctx.basis_update(grid, Qd, Zd, dt, 1, arith=2, reortho=True, trace=False)
         ctx.sync_status()
         prof = ctx.profile_read()
         ctx.profile_enable([])
         out[tc] = (U_of(Qd.cpu().numpy()) @ Zd.cpu().numpy(), prof)
     ctx.tensor_cores(True)
-    for k in ("project", "deposit", "gram", "basis_M"):
-        # the Gram of the re-orthonormalisation stays double-float (one launch)
-        rest = 1 if k == "gram" else 0
+    for k in ("project", "deposit", "gram", "basis_M", "affine"):
+        # the Gram and the combination of the re-orthonormalisation stay
+        # double-float (one launch each)
+        rest = 1 if k in ("gram", "affine") else 0
         assert out[True][1][f"k_{k}_tc"][0] > 0 and out[True][1][f"k_{k}_lp"][0] == rest
         assert out[False][1][f"k_{k}_tc"][0] == 0 and out[False][1][f"k_{k}_lp"][0] > rest
     Uo, Zo, _ = reduced.prk2_step(U, Z, dt, g)
@@ -226,10 +230,12 @@ def headline_shape_reference():
 @pytest.mark.parametrize("tc", [True, False])
 def test_precision_form_at_headline_shape(ctx, headline_shape_reference, tc):
     """The kernel instances the headline runs (2n = 64, p = 256, Nx = 256:
-    the tensor-core deposit and projection, or the FP32 SIMT deposit with its
-    register-resident coefficients, and the chunked Gamma zeta^H), one step of
-    the FP32 form with re-orthonormalisation against the FP64 oracle: the
-    one-step gate of 1e-6 in H and E, 1e-5 in UZ."""
+    the default tensor-core set, i.e. the FP32 SIMT deposit with its
+    register-resident coefficients and the projection, Grams, Gamma zeta^H
+    and row combinations on the tensor cores; or every kernel on the CUDA
+    cores, with the chunked Gamma zeta^H), one step of the FP32 form with
+    re-orthonormalisation against the FP64 oracle: the one-step gate of 1e-6
+    in H and E, 1e-5 in UZ."""
     from paper_2201_05555_gb300 import make_grid
     (N, p, n, Nx, dt), U, Z, g, U1, Z1, E1, H1, info = headline_shape_reference
     grid = make_grid(N, Nx, W.BUMP_ON_TAIL.L)
