@@ -91,47 +91,32 @@ __global__ void k_ygram(int64_t N, int m, const double* __restrict__ Y, int64_t 
   }
 }
 
-// Real symmetric cyclic Jacobi (m <= 256; one block; G given as its packed
-// lower triangle): G = W diag(lambda) W^T
-// with lambda descending and the columns of W (Wout, m x m row-major) in the
-// same order.  Round-robin ordering: the m/2 disjoint pairs of a round are
-// rotated together; a pair is rotated unless |g_jk| <= 1e-15 sqrt|g_jj g_kk|
-// or both diagonal entries are below 1e-14 of the largest one (a pair inside
-// the rounding-level null space, whose rotations would go on forever and
-// change no eigenpair above it).
-// Stops after a sweep without rotations (at most max_sweeps, else
-// VP_ENOCONV).  With m <= JS_SMEM_M, G and W live in shared memory.
-#define JS_SMEM_M 112
-__global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __restrict__ Ag,
-                             double* __restrict__ Wg, double* __restrict__ lambda,
-                             double* __restrict__ Wout, int max_sweeps, int* status) {
-  extern __shared__ double js[];
-  __shared__ double rc[128], rs[128];
-  __shared__ int pj[128], pk[128];
-  __shared__ int nrot;
-  __shared__ double nu;
-  __shared__ int order[256];
+// Round-robin sweeps of the cyclic Jacobi method on a symmetric m x m matrix A
+// (shared memory, row-major) with the rotations accumulated into W (A <- J^T A J,
+// W <- W J).  The m/2 disjoint pairs of a round rotate together; a pair
+// (j, k) rotates unless |a_jk| <= rel sqrt|a_jj a_kk|, |a_jk| <= floor_rel
+// max_i |a_ii|, or both diagonal entries are below null_rel max_i |a_ii| (a
+// pair inside the rounding-level null space, whose rotations would go on
+// forever and change no eigenpair above it).  Returns after a sweep without
+// rotations (true) or after max_sweeps (false).  The rotation angle comes from
+// an FP32 tangent (FP64 division and square roots are slow on this part),
+// normalised in the working precision R so that the rotation stays orthogonal
+// to R's rounding.  All threads of the block call it.
+template <class R>
+__device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_rel, R null_rel,
+                              R* rc, R* rs, int* pj, int* pk, int* nrot, R* nu_fl) {
   const int t = threadIdx.x, nt = blockDim.x;
-  const bool sm = m <= JS_SMEM_M;
-  double* A = sm ? js : Ag;
-  double* W = sm ? js + m * m : Wg;
-  for (int e = t; e < m * m; e += nt) {  // Gin: packed lower triangle
-    const int i = e / m, j = e - i * m;
-    const int hi = max(i, j), lo = min(i, j);
-    A[e] = Gin[hi * (hi + 1) / 2 + lo];
-    W[e] = i == j ? 1.0 : 0.0;
-  }
-  __syncthreads();
   const int slots = (m + 1) & ~1, npair = slots / 2;
-  bool conv = false;
-  for (int sweep = 0; sweep < max_sweeps && !conv; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (t == 0) {
-      nrot = 0;
-      double dm = 0.0;
+      *nrot = 0;
+      R dm = 0;
       for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(A[j * m + j]));
-      nu = 1e-14 * dm;
+      nu_fl[0] = null_rel * dm;
+      nu_fl[1] = floor_rel * dm;
     }
     __syncthreads();
+    const R nu = nu_fl[0], fl = nu_fl[1];
     for (int round = 0; round < slots - 1; ++round) {
       for (int q = t; q < npair; q += nt) {
         const int a = q, b = slots - 1 - q;
@@ -140,26 +125,21 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
         const int j = min(ia, ib), k = max(ia, ib);
         pj[q] = j;
         pk[q] = k;
-        double c = 1.0, sn = 0.0;
+        R c = 1, sn = 0;
         if (k < m) {
-          const double ajk = A[j * m + k], ajj = A[j * m + j], akk = A[k * m + k];
-          if (fabs(ajk) > 1e-15 * sqrt(fabs(ajj * akk)) && (float)fabs(ajk) > 0.0f &&
-              fmax(fabs(ajj), fabs(akk)) > nu) {
-            atomicAdd(&nrot, 1);
-            // the angle in FP32 (FP64 division and square roots are slow on
-            // this chip), the rotation normalised in FP64 so that it stays
-            // orthogonal to FP64 rounding; an angle good to FP32 leaves
-            // |g_jk| ~1e-7 of its value, which the next sweeps remove
-            const double dd = akk - ajj;
-            double tt;
-            if (fabs(dd) > 1e18 * fabs(ajk)) {  // tiny angle, beyond FP32 range: t = a_jk / dd
+          const R ajk = A[j * m + k], ajj = A[j * m + j], akk = A[k * m + k];
+          if (fabs(ajk) > rel * sqrt(fabs(ajj * akk)) && fabs(ajk) > fl &&
+              (float)fabs(ajk) > 0.0f && fmax(fabs(ajj), fabs(akk)) > nu) {
+            atomicAdd(nrot, 1);
+            const R dd = akk - ajj;
+            R tt;
+            if (fabs(dd) > (R)1e18 * fabs(ajk)) {  // tiny angle, beyond FP32 range: t = a_jk / dd
               tt = ajk / dd;
             } else {
               const float tau = (float)dd / (2.0f * (float)ajk);
-              tt = (double)((tau >= 0.0f ? 1.0f : -1.0f) /
-                            (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f))));
+              tt = (R)((tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f))));
             }
-            c = rsqrt(fma(tt, tt, 1.0));
+            c = rsqrt(fma(tt, tt, (R)1));
             sn = tt * c;
           }
         }
@@ -170,12 +150,12 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
       for (int e = t; e < npair * m; e += nt) {  // columns j, k of A and W
         const int q = e / m, r = e - q * m;
         const int j = pj[q], k = pk[q];
-        if (k >= m || rs[q] == 0.0) continue;
-        const double c = rc[q], sn = rs[q];
-        const double aj = A[r * m + j], ak = A[r * m + k];
+        if (k >= m || rs[q] == (R)0) continue;
+        const R c = rc[q], sn = rs[q];
+        const R aj = A[r * m + j], ak = A[r * m + k];
         A[r * m + j] = c * aj - sn * ak;
         A[r * m + k] = sn * aj + c * ak;
-        const double wj = W[r * m + j], wk = W[r * m + k];
+        const R wj = W[r * m + j], wk = W[r * m + k];
         W[r * m + j] = c * wj - sn * wk;
         W[r * m + k] = sn * wj + c * wk;
       }
@@ -183,18 +163,39 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
       for (int e = t; e < npair * m; e += nt) {  // rows j, k of A
         const int q = e / m, cidx = e - q * m;
         const int j = pj[q], k = pk[q];
-        if (k >= m || rs[q] == 0.0) continue;
-        const double c = rc[q], sn = rs[q];
-        const double aj = A[j * m + cidx], ak = A[k * m + cidx];
+        if (k >= m || rs[q] == (R)0) continue;
+        const R c = rc[q], sn = rs[q];
+        const R aj = A[j * m + cidx], ak = A[k * m + cidx];
         A[j * m + cidx] = c * aj - sn * ak;
         A[k * m + cidx] = sn * aj + c * ak;
       }
       __syncthreads();
     }
-    conv = nrot == 0;
+    const bool conv = *nrot == 0;
     __syncthreads();
-    if (!conv && sweep == max_sweeps - 1 && t == 0) vp_set_status(status, VP_ENOCONV);
+    if (conv) return true;
   }
+  return false;
+}
+
+// C = op(X) Y for m x m row-major matrices in shared memory, op(X) = X or X^T
+__device__ void small_mm(int m, const double* X, bool xt, const double* Y, double* C) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    double s = 0.0;
+    if (xt)
+      for (int k = 0; k < m; ++k) s = fma(X[k * m + i], Y[k * m + j], s);
+    else
+      for (int k = 0; k < m; ++k) s = fma(X[i * m + k], Y[k * m + j], s);
+    C[e] = s;
+  }
+}
+
+// lambda (descending) and the columns of W in the same order (Wout, m x m
+// row-major) from the diagonal of the converged A
+__device__ void jacobi_output(int m, const double* A, const double* W, double* lambda,
+                              double* Wout, int* order) {
+  const int t = threadIdx.x, nt = blockDim.x;
   if (t == 0) {  // eigenvalues descending (selection order)
     for (int i = 0; i < m; ++i) order[i] = i;
     for (int i = 0; i < m; ++i) {
@@ -214,8 +215,110 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
   }
 }
 
+// G (packed lower triangle) into the full m x m A and W = I
+__device__ void jacobi_load(int m, const double* Gin, double* A, double* W) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    const int hi = max(i, j), lo = min(i, j);
+    A[e] = Gin[hi * (hi + 1) / 2 + lo];
+    W[e] = i == j ? 1.0 : 0.0;
+  }
+}
+
+// Real symmetric cyclic Jacobi in FP64 (m <= 256; one block; G given as its
+// packed lower triangle): G = W diag(lambda) W^T with lambda descending and
+// the columns of W (Wout, m x m row-major) in the same order.  Pairs rotate
+// unless |g_jk| <= 1e-15 sqrt|g_jj g_kk| or both diagonal entries are below
+// 1e-14 of the largest one; stops after a sweep without rotations (at most
+// max_sweeps, else VP_ENOCONV).  With m <= JS_SMEM_M, A and W live in shared
+// memory.
+#define JS_SMEM_M 112
+__global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __restrict__ Ag,
+                             double* __restrict__ Wg, double* __restrict__ lambda,
+                             double* __restrict__ Wout, int max_sweeps, int* status) {
+  extern __shared__ double js[];
+  __shared__ double rc[128], rs[128], nu[2];
+  __shared__ int pj[128], pk[128], nrot, order[256];
+  const bool sm = m <= JS_SMEM_M;
+  double* A = sm ? js : Ag;
+  double* W = sm ? js + m * m : Wg;
+  jacobi_load(m, Gin, A, W);
+  __syncthreads();
+  const bool conv = jacobi_sweeps<double>(m, A, W, max_sweeps, 1e-15, 0.0, 1e-14, rc, rs, pj, pk,
+                                          &nrot, nu);
+  if (!conv && threadIdx.x == 0) vp_set_status(status, VP_ENOCONV);
+  jacobi_output(m, A, W, lambda, Wout, order);
+}
+
+// The same eigen-decomposition in mixed precision for m <= JS_MP_M: FP32
+// sweeps on G rounded to FP32 take the rotations down to the FP32 level
+// (pairs with |a_jk| <= 1e-6 sqrt|a_jj a_kk| or <= 2e-7 max|a_ii| stay, at
+// most 30 sweeps), at the FP32 issue rate; then, in FP64, one Newton-Schulz
+// step re-orthonormalises their product, W <- W (3 I - W^T W) / 2, A = W^T G W
+// (symmetrised) is diagonal up to ~1e-7 of its norm, and the FP64 sweeps
+// above finish it (quadratic convergence: about two sweeps with rotations).
+// The result is the FP64 decomposition up to rounding.
+#define JS_MP_M 64
+__global__ void k_jacobi_sym_mp(int m, const double* __restrict__ Gin, double* __restrict__ lambda,
+                                double* __restrict__ Wout, int max_sweeps, int* status) {
+  extern __shared__ double js[];
+  __shared__ double rc[128], rs[128], nu[2];
+  __shared__ int pj[128], pk[128], nrot, order[256];
+  const int mm = m * m;
+  double* G = js;
+  double* A = G + mm;
+  double* W = A + mm;
+  double* Tm = W + mm;
+  float* A32 = reinterpret_cast<float*>(Tm + mm);
+  float* W32 = A32 + mm;
+  jacobi_load(m, Gin, G, W);
+  __syncthreads();
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+    A32[e] = (float)G[e];
+    W32[e] = (float)W[e];
+  }
+  __syncthreads();
+  jacobi_sweeps<float>(m, A32, W32, 30, 1e-6f, 2e-7f, 1e-6f, reinterpret_cast<float*>(rc),
+                       reinterpret_cast<float*>(rs), pj, pk, &nrot, reinterpret_cast<float*>(nu));
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) W[e] = (double)W32[e];
+  __syncthreads();
+  small_mm(m, W, true, W, Tm);  // W^T W
+  __syncthreads();
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    Tm[e] = (i == j ? 1.5 : 0.0) - 0.5 * Tm[e];
+  }
+  __syncthreads();
+  small_mm(m, W, false, Tm, A);  // W (3 I - W^T W) / 2
+  __syncthreads();
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) W[e] = A[e];
+  __syncthreads();
+  small_mm(m, G, false, W, Tm);  // G W
+  __syncthreads();
+  small_mm(m, W, true, Tm, A);  // W^T G W
+  __syncthreads();
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    if (i < j) {
+      const double v = 0.5 * (A[i * m + j] + A[j * m + i]);
+      A[i * m + j] = v;
+      A[j * m + i] = v;
+    }
+  }
+  __syncthreads();
+  const bool conv = jacobi_sweeps<double>(m, A, W, max_sweeps, 1e-15, 0.0, 1e-14, rc, rs, pj, pk,
+                                          &nrot, nu);
+  if (!conv && threadIdx.x == 0) vp_set_status(status, VP_ENOCONV);
+  jacobi_output(m, A, W, lambda, Wout, order);
+}
+
 static void jacobi_sym(int m, const double* G, double* Ascr, double* Wscr, double* lambda,
                        double* Wout, int* status, cudaStream_t st) {
+  if (m <= JS_MP_M) {
+    const size_t smem = (sizeof(double) * 4 + sizeof(float) * 2) * m * m;
+    k_jacobi_sym_mp<<<1, 512, smem, st>>>(m, G, lambda, Wout, 60, status);
+    return;
+  }
   const size_t smem = m <= JS_SMEM_M ? sizeof(double) * 2 * m * m : 0;
   k_jacobi_sym<<<1, 512, smem, st>>>(m, G, Ascr, Wscr, lambda, Wout, 60, status);
 }
@@ -1121,6 +1224,7 @@ void deim_init() {
   cudaFuncSetAttribute(k_ygram, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_psi, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_jacobi_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi_sym_mp, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_deim_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_rbf, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_sqrtm, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);

@@ -259,8 +259,55 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
       for (int e = t; e < rows * n2; e += blockDim.x) Qs[e] = Q2[base * n2 + e];
       __syncthreads();
     }
+    // cell and weight of position tt (cell units) of row r: charge counts and
+    // the stored cell index
+    auto put = [&](int r, V tt) {
+      int j;
+      if (pack) {
+        // FP32 rows: cell and fraction in FP32 (both exact), one packed
+        // count (1 << Kp) + round(frac 2^Sp) into the particle's cell
+        const float th = AR::hi(tt), fl = floorf(th);
+        const int q = __float2int_rn((th - fl) * pscale);
+        int jr = (int)fl;
+        const int wq = (int)floorf((float)jr * inv_Nx);
+        jr -= wq * Nx;
+        if (jr < 0) jr += Nx;
+        if (jr >= Nx) jr -= Nx;
+        j = jr;
+        atomicAdd(mycnt + j, pbit + (unsigned long long)q);
+      } else {
+        long long w1;
+        cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
+        int j1 = (j + 1 == Nx) ? 0 : j + 1;
+        atomicAdd(mycnt + j, (unsigned long long)(one - w1));
+        atomicAdd(mycnt + j1, (unsigned long long)w1);
+      }
+      if (jout) jout[jt_block(tile, blockIdx.y, gridDim.y, PC) + r * PC + ii] = (uint16_t)j;
+    };
     if (active) {
-      for (int r = rsub; r < rows; r += RP) {
+      int r0 = rsub;
+      if constexpr (NR == 0 && !AR::kVec4) {
+        // double-float rows with the coefficients in shared memory: two rows
+        // per pass share every coefficient load, each row summed in the same
+        // order as the loop below
+        for (; r0 + RP < rows; r0 += 2 * RP) {
+          const V* qa = Qs + r0 * n2;
+          const V* qb = Qs + (r0 + RP) * n2;
+          typename AR::A x, y;
+          x.zero();
+          y.zero();
+          for (int k = 0; k < n; ++k) {
+            const V za = Zs[k * ldz + ii], zb = Zs[(n + k) * ldz + ii];
+            x.fma2(qa[k], za);
+            y.fma2(qb[k], za);
+            x.fma2(AR::neg(qa[n + k]), zb);
+            y.fma2(AR::neg(qb[n + k]), zb);
+          }
+          put(r0, x.out());
+          put(r0 + RP, y.out());
+        }
+      }
+      for (int r = r0; r < rows; r += RP) {
         const V* q = Qs + r * n2;
         V tt;
         if constexpr (NR > 0 && AR::kVec4) {  // x = sum_k A_k a_k - B_k b_k, coefficients in registers
@@ -331,27 +378,7 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
           }
           tt = x.out();
         }
-        int j;
-        if (pack) {
-          // FP32 rows: cell and fraction in FP32 (both exact), one packed
-          // count (1 << Kp) + round(frac 2^Sp) into the particle's cell
-          const float th = AR::hi(tt), fl = floorf(th);
-          const int q = __float2int_rn((th - fl) * pscale);
-          int jr = (int)fl;
-          const int wq = (int)floorf((float)jr * inv_Nx);
-          jr -= wq * Nx;
-          if (jr < 0) jr += Nx;
-          if (jr >= Nx) jr -= Nx;
-          j = jr;
-          atomicAdd(mycnt + j, pbit + (unsigned long long)q);
-        } else {
-          long long w1;
-          cell_fixed(AR::hi(tt), AR::lo(tt), Nx, inv_Nx, scale, g.S, one, j, w1);
-          int j1 = (j + 1 == Nx) ? 0 : j + 1;
-          atomicAdd(mycnt + j, (unsigned long long)(one - w1));
-          atomicAdd(mycnt + j1, (unsigned long long)w1);
-        }
-        if (jout) jout[jt_block(tile, blockIdx.y, gridDim.y, PC) + r * PC + ii] = (uint16_t)j;
+        put(r, tt);
       }
     }
     __syncthreads();
@@ -772,6 +799,46 @@ k_basis_M2_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __
 // Full 32-row tiles of every block arrive by bulk copies into two stages (the
 // next tile's copies run during the current tile); a partial last tile is
 // read with plain loads.
+// Entries of a Gram launch, enumerated compactly: per pair s its full n x n
+// block, or for a Hermitian pair (pa == pb) only k1 <= k2, the lower half
+// written as the conjugate.  gram_entries: their count.
+__host__ __device__ __forceinline__ int gram_entries(const GramArgsLP& a, int n) {
+  int c = 0;
+  for (int s = 0; s < a.npairs; ++s) c += (a.pa[s] == a.pb[s]) ? n * (n + 1) / 2 : n * n;
+  return c;
+}
+// index e < n (n + 1) / 2 of the upper triangle, row by row -> (k1, k2),
+// k1 <= k2: row k1 holds the n - k1 entries k2 = k1 .. n - 1 from start(k1)
+__device__ __forceinline__ void tri_entry(int n, int e, int& k1, int& k2) {
+  auto start = [n](int k) { return k * n - k * (k - 1) / 2; };
+  const float b = (float)(2 * n + 1);
+  int r = (int)(0.5f * (b - sqrtf(b * b - 8.0f * (float)e)));
+  r = r < 0 ? 0 : (r > n - 1 ? n - 1 : r);
+  while (r > 0 && start(r) > e) --r;
+  while (r + 1 < n && start(r + 1) <= e) ++r;
+  k1 = r;
+  k2 = r + (e - start(r));
+}
+// compact index e -> (s, k1, k2); false past the last entry
+__device__ __forceinline__ bool gram_entry(const GramArgsLP& a, int n, int e, int& s, int& k1,
+                                           int& k2) {
+  for (s = 0; s < a.npairs; ++s) {
+    const bool herm = a.pa[s] == a.pb[s];
+    const int cnt = herm ? n * (n + 1) / 2 : n * n;
+    if (e < cnt) {
+      if (herm) {
+        tri_entry(n, e, k1, k2);
+      } else {
+        k1 = e / n;
+        k2 = e - k1 * n;
+      }
+      return true;
+    }
+    e -= cnt;
+  }
+  return false;
+}
+
 template <class AR>
 __global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ part, int* status) {
   using V = typename AR::V;
@@ -781,13 +848,18 @@ __global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ 
   const size_t sst = (size_t)bbytes * a.nblk;                     // one stage, 16-aligned
   uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
   unsigned char* S0 = smraw + 16;
-  const int total = a.npairs * n * n;
+  const int total = a.npairs * n * n;  // entries of the partial layout
   const int e0 = blockIdx.y * blockDim.x * GDF_EPT;
   const int t = threadIdx.x;
   const int64_t ntiles = (N + GDF_ROWS - 1) / GDF_ROWS;
   typename AR::A re[GDF_EPT], im[GDF_EPT];
+  int es[GDF_EPT], ek1[GDF_EPT], ek2[GDF_EPT];
 #pragma unroll
-  for (int q = 0; q < GDF_EPT; ++q) { re[q].zero(); im[q].zero(); }
+  for (int q = 0; q < GDF_EPT; ++q) {
+    re[q].zero();
+    im[q].zero();
+    if (!gram_entry(a, n, e0 + q * blockDim.x + t, es[q], ek1[q], ek2[q])) es[q] = -1;
+  }
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -821,9 +893,8 @@ __global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ 
     }
 #pragma unroll
     for (int q = 0; q < GDF_EPT; ++q) {
-      int e = e0 + q * blockDim.x + t;
-      if (e < total) {
-        int s = e / (n * n), rem = e - s * n * n, k1 = rem / n, k2 = rem - k1 * n;
+      if (es[q] >= 0) {
+        const int s = es[q], k1 = ek1[q], k2 = ek2[q];
         const V* X = sm + a.pa[s] * GDF_ROWS * n2;
         const V* Y = sm + a.pb[s] * GDF_ROWS * n2;
         for (int r = 0; r < rows; ++r) {
@@ -841,8 +912,13 @@ __global__ void k_gram_lp(int64_t N, int n, GramArgsLP a, double2* __restrict__ 
   }
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) {
-    int e = e0 + q * blockDim.x + t;
-    if (e < total) part[(int64_t)blockIdx.x * total + e] = make_double2(re[q].value(), im[q].value());
+    if (es[q] >= 0) {
+      const int s = es[q], k1 = ek1[q], k2 = ek2[q];
+      double2* o = part + (int64_t)blockIdx.x * total + (int64_t)s * n * n;
+      const double vr = re[q].value(), vi = im[q].value();
+      o[k1 * n + k2] = make_double2(vr, vi);
+      if (a.pa[s] == a.pb[s] && k1 != k2) o[k2 * n + k1] = make_double2(vr, -vi);
+    }
   }
 }
 
@@ -853,11 +929,18 @@ __global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restric
   using V = typename AR::V;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
-  const int ldb = m + 1, total = m * m;
+  // the upper triangle k1 <= k2 only (the Gram is symmetric), mirrored on output
+  const int ldb = m + 1, total = m * m, tri = m * (m + 1) / 2;
   const int e0 = blockIdx.y * blockDim.x * GDF_EPT;
   typename AR::A acc[GDF_EPT];
+  int ek1[GDF_EPT], ek2[GDF_EPT];
 #pragma unroll
-  for (int q = 0; q < GDF_EPT; ++q) acc[q].zero();
+  for (int q = 0; q < GDF_EPT; ++q) {
+    acc[q].zero();
+    const int e = e0 + q * blockDim.x + threadIdx.x;
+    if (e < tri) tri_entry(m, e, ek1[q], ek2[q]);
+    else ek1[q] = -1;
+  }
   for (int64_t tile = blockIdx.x; tile * GDF_ROWS < N; tile += gridDim.x) {
     const int64_t base = tile * GDF_ROWS;
     const int rows = (int)((int64_t)GDF_ROWS < N - base ? (int64_t)GDF_ROWS : N - base);
@@ -869,17 +952,20 @@ __global__ void k_gram_real_lp(int64_t N, int m, const typename AR::V* __restric
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < GDF_EPT; ++q) {
-      int e = e0 + q * blockDim.x + threadIdx.x;
-      if (e < total) {
-        int k1 = e / m, k2 = e - k1 * m;
+      if (ek1[q] >= 0) {
+        const int k1 = ek1[q], k2 = ek2[q];
         for (int r = 0; r < rows; ++r) acc[q].fma2(sm[r * ldb + k1], sm[r * ldb + k2]);
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < GDF_EPT; ++q) {
-    int e = e0 + q * blockDim.x + threadIdx.x;
-    if (e < total) part[(int64_t)blockIdx.x * total + e] = acc[q].value();
+    if (ek1[q] >= 0) {
+      const int k1 = ek1[q], k2 = ek2[q];
+      const double v = acc[q].value();
+      part[(int64_t)blockIdx.x * total + k1 * m + k2] = v;
+      if (k1 != k2) part[(int64_t)blockIdx.x * total + k2 * m + k1] = v;
+    }
   }
 }
 
@@ -1097,8 +1183,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
           break;
         }
       }
-      int total = A.gram.npairs * n * n;
-      int gy = ceil_div(total, TILE_THREADS * GDF_EPT);
+      int gy = ceil_div(gram_entries(A.gram, n), TILE_THREADS * GDF_EPT);
       size_t smem = 16 + 2 * sizeof(V) * A.gram.nblk * GDF_ROWS * n2;
       k_gram_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, n, A.gram, (double2*)A.part,
                                                                    A.status);
@@ -1116,7 +1201,7 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
         }
       }
       int m = n2;
-      int gy = ceil_div(m * m, TILE_THREADS * GDF_EPT);
+      int gy = ceil_div(m * (m + 1) / 2, TILE_THREADS * GDF_EPT);
       size_t smem = sizeof(V) * GDF_ROWS * (m + 1);
       k_gram_real_lp<AR><<<dim3(A.gridx, gy), TILE_THREADS, smem, st>>>(N, m, (const V*)A.v0, A.part);
       break;
