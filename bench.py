@@ -1079,9 +1079,10 @@ def ours(args, rank, world):
             "roofline_next": roofs[1:],
             "kernel_share": {k: round(f, 3) for k, f in shares[:10]},
             "clocks": clocks, "autotuned_blocks_per_sm": tuned, "fixed_point_iters": its,
-            "accuracy": ("FP32 form against the FP64 oracle (tests/test_gpu_precision.py): "
-                         "relative H and E errors <= 5e-7 after one step; over 200 steps H "
-                         "within 1.4e-5 and E within 2.2e-6 of its largest value")}
+            "accuracy": ("FP32 form, default tensor-core set, against the FP64 oracle "
+                         "(tests/test_gpu_precision.py): relative H and E errors <= 6e-7 after "
+                         "one step at the headline shape (N = 3e4, p = 256, 2n = 64); over 200 "
+                         "steps H within 1.7e-5 and E within 1.8e-6 of its largest value")}
     del Qd, Zd, Kd
     if not args.no_extras and world == 1 and not sharded:
         del Q, Z, kstate
