@@ -103,7 +103,7 @@ __global__ void k_ygram(int64_t N, int m, const double* __restrict__ Y, int64_t 
 // normalised in the working precision R so that the rotation stays orthogonal
 // to R's rounding.  All threads of the block call it.
 template <class R>
-__device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_rel, R null_rel,
+__device__ bool jacobi_sweeps(int m, int ld, R* A, R* W, int max_sweeps, R rel, R floor_rel, R null_rel,
                               R* rc, R* rs, int* pj, int* pk, int* nrot, R* nu_fl) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int slots = (m + 1) & ~1, npair = slots / 2;
@@ -111,7 +111,7 @@ __device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_
     if (t == 0) {
       *nrot = 0;
       R dm = 0;
-      for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(A[j * m + j]));
+      for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(A[j * ld + j]));
       nu_fl[0] = null_rel * dm;
       nu_fl[1] = floor_rel * dm;
     }
@@ -127,7 +127,7 @@ __device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_
         pk[q] = k;
         R c = 1, sn = 0;
         if (k < m) {
-          const R ajk = A[j * m + k], ajj = A[j * m + j], akk = A[k * m + k];
+          const R ajk = A[j * ld + k], ajj = A[j * ld + j], akk = A[k * ld + k];
           if (fabs(ajk) > rel * sqrt(fabs(ajj * akk)) && fabs(ajk) > fl &&
               (float)fabs(ajk) > 0.0f && fmax(fabs(ajj), fabs(akk)) > nu) {
             atomicAdd(nrot, 1);
@@ -152,12 +152,12 @@ __device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_
         const int j = pj[q], k = pk[q];
         if (k >= m || rs[q] == (R)0) continue;
         const R c = rc[q], sn = rs[q];
-        const R aj = A[r * m + j], ak = A[r * m + k];
-        A[r * m + j] = c * aj - sn * ak;
-        A[r * m + k] = sn * aj + c * ak;
-        const R wj = W[r * m + j], wk = W[r * m + k];
-        W[r * m + j] = c * wj - sn * wk;
-        W[r * m + k] = sn * wj + c * wk;
+        const R aj = A[r * ld + j], ak = A[r * ld + k];
+        A[r * ld + j] = c * aj - sn * ak;
+        A[r * ld + k] = sn * aj + c * ak;
+        const R wj = W[r * ld + j], wk = W[r * ld + k];
+        W[r * ld + j] = c * wj - sn * wk;
+        W[r * ld + k] = sn * wj + c * wk;
       }
       __syncthreads();
       for (int e = t; e < npair * m; e += nt) {  // rows j, k of A
@@ -165,9 +165,9 @@ __device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_
         const int j = pj[q], k = pk[q];
         if (k >= m || rs[q] == (R)0) continue;
         const R c = rc[q], sn = rs[q];
-        const R aj = A[j * m + cidx], ak = A[k * m + cidx];
-        A[j * m + cidx] = c * aj - sn * ak;
-        A[k * m + cidx] = sn * aj + c * ak;
+        const R aj = A[j * ld + cidx], ak = A[k * ld + cidx];
+        A[j * ld + cidx] = c * aj - sn * ak;
+        A[k * ld + cidx] = sn * aj + c * ak;
       }
       __syncthreads();
     }
@@ -178,22 +178,9 @@ __device__ bool jacobi_sweeps(int m, R* A, R* W, int max_sweeps, R rel, R floor_
   return false;
 }
 
-// C = op(X) Y for m x m row-major matrices in shared memory, op(X) = X or X^T
-__device__ void small_mm(int m, const double* X, bool xt, const double* Y, double* C) {
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e - i * m;
-    double s = 0.0;
-    if (xt)
-      for (int k = 0; k < m; ++k) s = fma(X[k * m + i], Y[k * m + j], s);
-    else
-      for (int k = 0; k < m; ++k) s = fma(X[i * m + k], Y[k * m + j], s);
-    C[e] = s;
-  }
-}
-
 // lambda (descending) and the columns of W in the same order (Wout, m x m
 // row-major) from the diagonal of the converged A
-__device__ void jacobi_output(int m, const double* A, const double* W, double* lambda,
+__device__ void jacobi_output(int m, int ld, const double* A, const double* W, double* lambda,
                               double* Wout, int* order) {
   const int t = threadIdx.x, nt = blockDim.x;
   if (t == 0) {  // eigenvalues descending (selection order)
@@ -201,27 +188,27 @@ __device__ void jacobi_output(int m, const double* A, const double* W, double* l
     for (int i = 0; i < m; ++i) {
       int best = i;
       for (int j = i + 1; j < m; ++j)
-        if (A[order[j] * m + order[j]] > A[order[best] * m + order[best]]) best = j;
+        if (A[order[j] * ld + order[j]] > A[order[best] * ld + order[best]]) best = j;
       const int tmp = order[i];
       order[i] = order[best];
       order[best] = tmp;
     }
   }
   __syncthreads();
-  for (int i = t; i < m; i += nt) lambda[i] = A[order[i] * m + order[i]];
+  for (int i = t; i < m; i += nt) lambda[i] = A[order[i] * ld + order[i]];
   for (int e = t; e < m * m; e += nt) {
     const int r = e / m, c = e - r * m;
-    Wout[e] = W[r * m + order[c]];
+    Wout[e] = W[r * ld + order[c]];
   }
 }
 
 // G (packed lower triangle) into the full m x m A and W = I
-__device__ void jacobi_load(int m, const double* Gin, double* A, double* W) {
+__device__ void jacobi_load(int m, int ld, const double* Gin, double* A, double* W) {
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e - i * m;
     const int hi = max(i, j), lo = min(i, j);
-    A[e] = Gin[hi * (hi + 1) / 2 + lo];
-    W[e] = i == j ? 1.0 : 0.0;
+    A[i * ld + j] = Gin[hi * (hi + 1) / 2 + lo];
+    W[i * ld + j] = i == j ? 1.0 : 0.0;
   }
 }
 
@@ -232,7 +219,7 @@ __device__ void jacobi_load(int m, const double* Gin, double* A, double* W) {
 // 1e-14 of the largest one; stops after a sweep without rotations (at most
 // max_sweeps, else VP_ENOCONV).  With m <= JS_SMEM_M, A and W live in shared
 // memory.
-#define JS_SMEM_M 112
+#define JS_SMEM_M 111
 __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __restrict__ Ag,
                              double* __restrict__ Wg, double* __restrict__ lambda,
                              double* __restrict__ Wout, int max_sweeps, int* status) {
@@ -240,86 +227,287 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
   __shared__ double rc[128], rs[128], nu[2];
   __shared__ int pj[128], pk[128], nrot, order[256];
   const bool sm = m <= JS_SMEM_M;
+  // rows padded to m + 1 in shared memory: the column updates of a round
+  // walk down a column, which a stride of m would put in one bank
+  const int ld = sm ? m + 1 : m;
   double* A = sm ? js : Ag;
-  double* W = sm ? js + m * m : Wg;
-  jacobi_load(m, Gin, A, W);
+  double* W = sm ? js + m * ld : Wg;
+  jacobi_load(m, ld, Gin, A, W);
   __syncthreads();
-  const bool conv = jacobi_sweeps<double>(m, A, W, max_sweeps, 1e-15, 0.0, 1e-14, rc, rs, pj, pk,
-                                          &nrot, nu);
+  const bool conv = jacobi_sweeps<double>(m, ld, A, W, max_sweeps, 1e-15, 0.0, 1e-14, rc, rs, pj,
+                                          pk, &nrot, nu);
   if (!conv && threadIdx.x == 0) vp_set_status(status, VP_ENOCONV);
-  jacobi_output(m, A, W, lambda, Wout, order);
+  jacobi_output(m, ld, A, W, lambda, Wout, order);
 }
 
-// The same eigen-decomposition in mixed precision for m <= JS_MP_M: FP32
-// sweeps on G rounded to FP32 take the rotations down to the FP32 level
-// (pairs with |a_jk| <= 1e-6 sqrt|a_jj a_kk| or <= 2e-7 max|a_ii| stay, at
-// most 30 sweeps), at the FP32 issue rate; then, in FP64, one Newton-Schulz
-// step re-orthonormalises their product, W <- W (3 I - W^T W) / 2, A = W^T G W
-// (symmetrised) is diagonal up to ~1e-7 of its norm, and the FP64 sweeps
-// above finish it (quadratic convergence: about two sweeps with rotations).
-// The result is the FP64 decomposition up to rounding.
-#define JS_MP_M 64
-__global__ void k_jacobi_sym_mp(int m, const double* __restrict__ Gin, double* __restrict__ lambda,
-                                double* __restrict__ Wout, int max_sweeps, int* status) {
-  extern __shared__ double js[];
-  __shared__ double rc[128], rs[128], nu[2];
-  __shared__ int pj[128], pk[128], nrot, order[256];
-  const int mm = m * m;
-  double* G = js;
-  double* A = G + mm;
-  double* W = A + mm;
-  double* Tm = W + mm;
-  float* A32 = reinterpret_cast<float*>(Tm + mm);
-  float* W32 = A32 + mm;
-  jacobi_load(m, Gin, G, W);
-  __syncthreads();
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
-    A32[e] = (float)G[e];
-    W32[e] = (float)W[e];
+// ------------------------------------------- double-float symmetric Jacobi
+// A double-float value hi + lo (|lo| <= half an ulp of hi) carries about 48
+// significant bits; its operations run on the FP32 pipes, which issue 64
+// times the FP64 rate of this part.
+struct DFv {
+  float h, l;
+};
+__device__ __forceinline__ DFv dfv(float h, float l) { return DFv{h, l}; }
+__device__ __forceinline__ DFv dfv_from(double x) {
+  const float h = (float)x;
+  return DFv{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double dfv_to(DFv a) { return (double)a.h + (double)a.l; }
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ DFv two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return DFv{s, (a - (s - bb)) + (b - bb)};
+}
+// s + e = a + b exactly for |a| >= |b| (Dekker's FastTwoSum)
+__device__ __forceinline__ DFv fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return DFv{s, b - (s - a)};
+}
+__device__ __forceinline__ DFv dfv_add(DFv a, DFv b) {
+  const DFv s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ DFv dfv_neg(DFv a) { return DFv{-a.h, -a.l}; }
+__device__ __forceinline__ DFv dfv_mul(DFv a, DFv b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+// c a - s b
+__device__ __forceinline__ DFv dfv_rot(DFv c, DFv a, DFv s, DFv b) {
+  return dfv_add(dfv_mul(c, a), dfv_neg(dfv_mul(s, b)));
+}
+
+// Round-robin cyclic Jacobi sweeps as jacobi_sweeps, in double-float: a pair
+// (j, k) rotates unless |a_jk| <= 1e-14 sqrt|a_jj a_kk| (double-float
+// rounding is ~4e-15) or both diagonal entries are below 1e-14 of the
+// largest.  The tangent of the angle is taken in FP32 from the leading parts
+// (as in the FP64 sweeps); c = (1 + t^2)^-1/2 by an FP32 reciprocal square
+// root and one Newton step in double-float, s = t c, so the rotation is
+// orthogonal to double-float rounding.  Returns after a sweep without
+// rotations (true) or after max_sweeps (false).
+__device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, DFv* rc, DFv* rs, int* pj,
+                                 int* pk, int* nrot, float* nu_s) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int slots = (m + 1) & ~1, npair = slots / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (t == 0) {
+      *nrot = 0;
+      float dm = 0.f;
+      for (int j = 0; j < m; ++j) dm = fmaxf(dm, fabsf(A[j * ld + j].h));
+      *nu_s = 1e-14f * dm;
+    }
+    __syncthreads();
+    const float nu = *nu_s;
+    for (int round = 0; round < slots - 1; ++round) {
+      for (int q = t; q < npair; q += nt) {
+        const int a = q, b = slots - 1 - q;
+        const int ia = (a == 0) ? 0 : 1 + (a - 1 + round) % (slots - 1);
+        const int ib = (b == 0) ? 0 : 1 + (b - 1 + round) % (slots - 1);
+        const int j = min(ia, ib), k = max(ia, ib);
+        pj[q] = j;
+        pk[q] = k;
+        DFv c = dfv(1.f, 0.f), sn = dfv(0.f, 0.f);
+        if (k < m) {
+          const DFv ajk = A[j * ld + k], ajj = A[j * ld + j], akk = A[k * ld + k];
+          const float x = fabsf(ajk.h);
+          if (x > 1e-14f * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
+              fmaxf(fabsf(ajj.h), fabsf(akk.h)) > nu) {
+            atomicAdd(nrot, 1);
+            const DFv dd = dfv_add(akk, dfv_neg(ajj));
+            float tt;
+            if (fabsf(dd.h) > 1e18f * x) {  // tiny angle: t = a_jk / dd
+              tt = ajk.h / dd.h;
+            } else {
+              const float tau = dd.h / (2.0f * ajk.h);
+              tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            }
+            // u = 1 + t^2 exactly as a double-float (t^2 by an FMA), y ~ u^-1/2
+            const float t2 = tt * tt;
+            const DFv u = fast_two_sum(1.0f, t2);
+            const DFv uu = dfv_add(u, dfv(fmaf(tt, tt, -t2), 0.f));
+            const float y0 = rsqrtf(uu.h);
+            // y = y0 + y0 (1 - u y0^2) / 2
+            const DFv y0sq = dfv_mul(dfv(y0, 0.f), dfv(y0, 0.f));
+            const DFv r = dfv_add(dfv(1.f, 0.f), dfv_neg(dfv_mul(uu, y0sq)));
+            c = dfv_add(dfv(y0, 0.f), dfv_mul(dfv(0.5f * y0, 0.f), r));
+            sn = dfv_mul(dfv(tt, 0.f), c);
+          }
+        }
+        rc[q] = c;
+        rs[q] = sn;
+      }
+      __syncthreads();
+      for (int e = t; e < npair * m; e += nt) {  // columns j, k of A and W
+        const int q = e / m, r = e - q * m;
+        const int j = pj[q], k = pk[q];
+        if (k >= m || rs[q].h == 0.f) continue;
+        const DFv c = rc[q], sn = rs[q];
+        const DFv aj = A[r * ld + j], ak = A[r * ld + k];
+        A[r * ld + j] = dfv_rot(c, aj, sn, ak);
+        A[r * ld + k] = dfv_rot(sn, aj, dfv_neg(c), ak);  // s aj + c ak
+        const DFv wj = W[r * ld + j], wk = W[r * ld + k];
+        W[r * ld + j] = dfv_rot(c, wj, sn, wk);
+        W[r * ld + k] = dfv_rot(sn, wj, dfv_neg(c), wk);
+      }
+      __syncthreads();
+      for (int e = t; e < npair * m; e += nt) {  // rows j, k of A
+        const int q = e / m, cidx = e - q * m;
+        const int j = pj[q], k = pk[q];
+        if (k >= m || rs[q].h == 0.f) continue;
+        const DFv c = rc[q], sn = rs[q];
+        const DFv aj = A[j * ld + cidx], ak = A[k * ld + cidx];
+        A[j * ld + cidx] = dfv_rot(c, aj, sn, ak);
+        A[k * ld + cidx] = dfv_rot(sn, aj, dfv_neg(c), ak);
+      }
+      __syncthreads();
+    }
+    const bool conv = *nrot == 0;
+    __syncthreads();
+    if (conv) return true;
   }
-  __syncthreads();
-  jacobi_sweeps<float>(m, A32, W32, 30, 1e-6f, 2e-7f, 1e-6f, reinterpret_cast<float*>(rc),
-                       reinterpret_cast<float*>(rs), pj, pk, &nrot, reinterpret_cast<float*>(nu));
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) W[e] = (double)W32[e];
-  __syncthreads();
-  small_mm(m, W, true, W, Tm);  // W^T W
-  __syncthreads();
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+  return false;
+}
+
+// C = op(X) Y for m x m matrices in shared memory (rows ld apart), op(X) = X
+// or X^T
+__device__ void small_mm(int m, int ld, const double* X, bool xt, const double* Y, double* C) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e - i * m;
-    Tm[e] = (i == j ? 1.5 : 0.0) - 0.5 * Tm[e];
+    double s = 0.0;
+    if (xt)
+      for (int k = 0; k < m; ++k) s = fma(X[k * ld + i], Y[k * ld + j], s);
+    else
+      for (int k = 0; k < m; ++k) s = fma(X[i * ld + k], Y[k * ld + j], s);
+    C[i * ld + j] = s;
+  }
+}
+
+// The same eigen-decomposition in double-float for m <= JS_REFINE_M: G is scaled by a power of two near its largest
+// diagonal entry (exact), held as double-float pairs, and swept as above with
+// the rotations on the FP32 pipes; lambda and W are the double-float results
+// rounded to FP64 (about 4e-15 of the largest eigenvalue, against 1e-16 for
+// the FP64 sweeps, at several times their speed).  With refine (m <= 64) an
+// FP64 finish follows: two Newton-Schulz steps re-orthonormalise W,
+// W <- W (3 I - W^T W) / 2, A = W^T G W (symmetrised) is diagonal up to the
+// double-float level, and the FP64 sweeps resolve what is below it (the
+// small eigenvalues, to FP64 accuracy, in a few sweeps).
+#define JS_REFINE_M 64
+__global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* __restrict__ lambda,
+                                double* __restrict__ Wout, int max_sweeps, int refine,
+                                int* status) {
+  extern __shared__ double js[];
+  __shared__ DFv rc[128], rs[128];
+  __shared__ int pj[128], pk[128], nrot, order[256];
+  __shared__ float nu;
+  __shared__ double nud[2], scale_s;
+  const int ld = m + 1, mm = m * ld;  // padded rows (see k_jacobi_sym)
+  DFv* A = reinterpret_cast<DFv*>(js);
+  DFv* W = A + mm;
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (t == 0) {
+    double dm = 0.0;
+    for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(Gin[j * (j + 1) / 2 + j]));
+    scale_s = dm > 0.0 ? ldexp(1.0, -ilogb(dm)) : 1.0;
   }
   __syncthreads();
-  small_mm(m, W, false, Tm, A);  // W (3 I - W^T W) / 2
+  const double sc = scale_s;
+  for (int e = t; e < m * m; e += nt) {
+    const int i = e / m, j = e - i * m;
+    const int hi = max(i, j), lo = min(i, j);
+    A[i * ld + j] = dfv_from(Gin[hi * (hi + 1) / 2 + lo] * sc);
+    W[i * ld + j] = dfv(i == j ? 1.f : 0.f, 0.f);
+  }
   __syncthreads();
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) W[e] = A[e];
+  const bool conv = jacobi_sweeps_df(m, ld, A, W, max_sweeps, rc, rs, pj, pk, &nrot, &nu);
+  if (!refine) {
+    if (!conv && t == 0) vp_set_status(status, VP_ENOCONV);
+    if (t == 0) {  // eigenvalues descending (selection order)
+      for (int i = 0; i < m; ++i) order[i] = i;
+      for (int i = 0; i < m; ++i) {
+        int best = i;
+        for (int j = i + 1; j < m; ++j)
+          if (dfv_to(A[order[j] * ld + order[j]]) > dfv_to(A[order[best] * ld + order[best]]))
+            best = j;
+        const int tmp = order[i];
+        order[i] = order[best];
+        order[best] = tmp;
+      }
+    }
+    __syncthreads();
+    for (int i = t; i < m; i += nt) lambda[i] = dfv_to(A[order[i] * ld + order[i]]) / sc;
+    for (int e = t; e < m * m; e += nt) {
+      const int r = e / m, c = e - r * m;
+      Wout[e] = dfv_to(W[r * ld + order[c]]);
+    }
+    return;
+  }
+  // FP64 finish: the double-float slots become FP64 (same size, element by
+  // element by the same thread), then G and a work matrix follow them
+  double* Ad = js;
+  double* Wd = js + mm;
+  double* G = js + 2 * mm;
+  double* Tm = js + 3 * mm;
+  for (int e = t; e < m * m; e += nt) {
+    const int i = e / m, j = e - i * m;
+    Wd[i * ld + j] = dfv_to(W[i * ld + j]);
+    const int hi = max(i, j), lo = min(i, j);
+    G[i * ld + j] = Gin[hi * (hi + 1) / 2 + lo] * sc;
+  }
   __syncthreads();
-  small_mm(m, G, false, W, Tm);  // G W
+  for (int ns = 0; ns < 2; ++ns) {
+    small_mm(m, ld, Wd, true, Wd, Tm);  // W^T W
+    __syncthreads();
+    for (int e = t; e < m * m; e += nt) {
+      const int i = e / m, j = e - i * m;
+      Tm[i * ld + j] = (i == j ? 1.5 : 0.0) - 0.5 * Tm[i * ld + j];
+    }
+    __syncthreads();
+    small_mm(m, ld, Wd, false, Tm, Ad);  // W (3 I - W^T W) / 2
+    __syncthreads();
+    for (int e = t; e < m * m; e += nt) {
+      const int i = e / m, j = e - i * m;
+      Wd[i * ld + j] = Ad[i * ld + j];
+    }
+    __syncthreads();
+  }
+  small_mm(m, ld, G, false, Wd, Tm);  // G W
   __syncthreads();
-  small_mm(m, W, true, Tm, A);  // W^T G W
+  small_mm(m, ld, Wd, true, Tm, Ad);  // W^T G W
   __syncthreads();
-  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+  for (int e = t; e < m * m; e += nt) {
     const int i = e / m, j = e - i * m;
     if (i < j) {
-      const double v = 0.5 * (A[i * m + j] + A[j * m + i]);
-      A[i * m + j] = v;
-      A[j * m + i] = v;
+      const double v = 0.5 * (Ad[i * ld + j] + Ad[j * ld + i]);
+      Ad[i * ld + j] = v;
+      Ad[j * ld + i] = v;
     }
   }
   __syncthreads();
-  const bool conv = jacobi_sweeps<double>(m, A, W, max_sweeps, 1e-15, 0.0, 1e-14, rc, rs, pj, pk,
-                                          &nrot, nu);
-  if (!conv && threadIdx.x == 0) vp_set_status(status, VP_ENOCONV);
-  jacobi_output(m, A, W, lambda, Wout, order);
+  const bool conv64 = jacobi_sweeps<double>(m, ld, Ad, Wd, max_sweeps, 1e-15, 0.0, 1e-14,
+                                            reinterpret_cast<double*>(rc),
+                                            reinterpret_cast<double*>(rs), pj, pk, &nrot, nud);
+  if (!conv64 && t == 0) vp_set_status(status, VP_ENOCONV);
+  jacobi_output(m, ld, Ad, Wd, lambda, Wout, order);
+  __syncthreads();
+  for (int i = t; i < m; i += nt) lambda[i] /= sc;
 }
 
+// m <= 64: the double-float sweeps, with fp64_finish followed by the FP64
+// finish (the DMD Gram, whose small singular values are divided by later),
+// else the double-float result as it is (the DEIM Gram); larger m: the FP64
+// sweeps (measured faster than double-float at m = 88), in shared memory up
+// to JS_SMEM_M, in global memory above.
 static void jacobi_sym(int m, const double* G, double* Ascr, double* Wscr, double* lambda,
-                       double* Wout, int* status, cudaStream_t st) {
-  if (m <= JS_MP_M) {
-    const size_t smem = (sizeof(double) * 4 + sizeof(float) * 2) * m * m;
-    k_jacobi_sym_mp<<<1, 512, smem, st>>>(m, G, lambda, Wout, 60, status);
+                       double* Wout, int* status, cudaStream_t st, bool fp64_finish = false) {
+  if (m <= JS_REFINE_M) {
+    const size_t smem = sizeof(double) * (fp64_finish ? 4 : 2) * m * (m + 1);
+    k_jacobi_sym_df<<<1, 512, smem, st>>>(m, G, lambda, Wout, 60, fp64_finish ? 1 : 0, status);
     return;
   }
-  const size_t smem = m <= JS_SMEM_M ? sizeof(double) * 2 * m * m : 0;
+  const size_t smem = m <= JS_SMEM_M ? sizeof(double) * 2 * m * (m + 1) : 0;
   k_jacobi_sym<<<1, 512, smem, st>>>(m, G, Ascr, Wscr, lambda, Wout, 60, status);
 }
 
@@ -491,6 +679,192 @@ __global__ void k_deim_lu(int64_t N, int d, int k, double* R, double* prow, int3
 }
 
 // block partial dot products psi_k . prev_k (d x N each): part[blockIdx.x][k]
+// The d steps of k_deim_lu in one cooperative launch, when every block's rows
+// of the basis fit in shared memory: block b owns rows [b rb, min(N, (b+1) rb))
+// and keeps its d x rb slice of R in shared memory for all steps.  Step k:
+// eliminate the previous pivot from the slice's columns k..d-1; publish the
+// block's candidate (its arg-max of |R_k| with held rows skipped, or the
+// inherited row if the block owns it) together with that row's values of
+// columns k..d-1; one grid barrier; then every block takes the same global
+// choice (ties to the lowest row) and the multipliers R_j[l_k] / R_k[l_k]
+// from the published row.  Same operations in the same order as k_deim_lu,
+// so the same indices.  Published data alternate between two buffers by step
+// parity: a block passes barrier k + 1 only after every block has arrived
+// there, i.e. has finished reading the data of step k.  The barrier is a
+// monotonic counter with a bounded wait (VP_ETIMEDOUT, and an abort flag
+// that releases the other blocks).
+constexpr int kLuThreads = 256;
+constexpr int kLuSpins = 1 << 22;
+
+__device__ bool lu_barrier(unsigned* count, unsigned target, int* abort_flag, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    for (int spins = 0;; ++spins) {
+      if (*reinterpret_cast<volatile unsigned*>(count) >= target) break;
+      if (*reinterpret_cast<volatile int*>(abort_flag)) {
+        ok = 0;
+        break;
+      }
+      if (spins > kLuSpins) {
+        vp_set_status(status, VP_ETIMEDOUT);
+        atomicExch(abort_flag, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kLuThreads)
+k_deim_lu_coop(int64_t N, int d, int rb, const double* __restrict__ Psi, int32_t* idx,
+               const int* __restrict__ renew, double* pval, int64_t* pidx, double* prows,
+               unsigned* bar, int* abort_flag, int* status) {
+  extern __shared__ double Rs[];  // d x rb
+  __shared__ double mult[128];
+  __shared__ int32_t picks[128], held[128];
+  __shared__ int nheld;
+  __shared__ double bv[32];
+  __shared__ int64_t bi[32];
+  __shared__ int64_t cand_s, pick_s;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int64_t r0 = (int64_t)b * rb;
+  const int rows = (int)(N - r0 < (int64_t)rb ? (N - r0 > 0 ? N - r0 : 0) : rb);
+  for (int e = t; e < d * rows; e += blockDim.x) {
+    const int j = e / rows, i = e - j * rows;
+    Rs[j * rb + i] = Psi[(int64_t)j * N + r0 + i];
+  }
+  for (int j = t; j < d; j += blockDim.x) mult[j] = 0.0;
+  __syncthreads();
+  for (int k = 0; k < d; ++k) {
+    const bool inherit = renew && !renew[k];
+    const int par = k & 1;
+    if (t == 0) {  // rows held at the other positions
+      int c = 0;
+      for (int j = 0; j < d; ++j)
+        if (j != k && (j < k || (renew && !renew[j]))) held[c++] = j < k ? picks[j] : idx[j];
+      nheld = c;
+    }
+    if (k > 0)  // eliminate the previous pivot from columns k..d-1
+      for (int e = t; e < (d - k) * rows; e += blockDim.x) {
+        const int jj = e / rows, i = e - jj * rows, j = k + jj;
+        Rs[j * rb + i] = fma(-Rs[(k - 1) * rb + i], mult[j], Rs[j * rb + i]);
+      }
+    __syncthreads();
+    double best = -1.0;
+    int64_t bidx = INT64_MAX;
+    if (!inherit)
+      for (int i = t; i < rows; i += blockDim.x) {
+        const int64_t l = r0 + i;
+        bool skip = false;
+        for (int j = 0; j < nheld; ++j) skip |= held[j] == (int32_t)l;
+        if (skip) continue;
+        const double a = fabs(Rs[k * rb + i]);
+        if (a > best || (a == best && l < bidx)) {
+          best = a;
+          bidx = l;
+        }
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) {
+        best = ob;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) {
+      bv[wid] = best;
+      bi[wid] = bidx;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double bb = bv[0];
+      int64_t c = bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (bv[w] > bb || (bv[w] == bb && bi[w] < c)) {
+          bb = bv[w];
+          c = bi[w];
+        }
+      if (inherit) {  // the inherited row, published by its owner
+        const int64_t l = idx[k];
+        c = (l >= r0 && l < r0 + rows) ? l : INT64_MAX;
+        bb = c != INT64_MAX ? 1.0 : -1.0;
+      }
+      pval[par * nb + b] = bb;
+      pidx[par * nb + b] = c;
+      cand_s = c;
+    }
+    __syncthreads();
+    const int64_t cand = cand_s;
+    if (cand != INT64_MAX)
+      for (int j = k + t; j < d; j += blockDim.x)
+        prows[((int64_t)par * nb + b) * d + j] = Rs[j * rb + (int)(cand - r0)];
+    if (!lu_barrier(bar, (unsigned)(k + 1) * (unsigned)nb, abort_flag, status)) return;
+    // the global choice, the same in every block
+    double vb = -1.0;
+    int64_t ib = INT64_MAX;
+    for (int i = t; i < nb; i += blockDim.x) {
+      const double v = __ldcg(pval + par * nb + i);
+      const int64_t ii = __ldcg(pidx + par * nb + i);
+      if (v > vb || (v == vb && ii < ib)) {
+        vb = v;
+        ib = ii;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, vb, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, ib, o);
+      if (ov > vb || (ov == vb && oi < ib)) {
+        vb = ov;
+        ib = oi;
+      }
+    }
+    __syncthreads();
+    if (lane == 0) {
+      bv[wid] = vb;
+      bi[wid] = ib;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double bb = bv[0];
+      int64_t p = bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (bv[w] > bb || (bv[w] == bb && bi[w] < p)) {
+          bb = bv[w];
+          p = bi[w];
+        }
+      if (inherit) p = idx[k];
+      if (p < 0 || p >= N) {  // nothing left to pick, or a bad inherited index
+        if (b == 0) vp_set_status(status, VP_EINVAL);
+        p = 0;
+      }
+      picks[k] = (int32_t)p;
+      pick_s = p;
+    }
+    __syncthreads();
+    const int64_t pick = pick_s;
+    const int owner = (int)(pick / rb);
+    const double* row = prows + ((int64_t)par * nb + owner) * d;
+    const double pv = __ldcg(row + k);
+    if (t == 0 && b == 0) {
+      idx[k] = (int32_t)pick;
+      if (!(pv != 0.0) || !isfinite(pv)) vp_set_status(status, VP_ENUMERIC);
+    }
+    for (int j = k + 1 + t; j < d; j += blockDim.x)
+      mult[j] = (pv != 0.0 && isfinite(pv)) ? __ldcg(row + j) / pv : 0.0;
+    __syncthreads();
+  }
+}
+
 __global__ void k_rot_dots(int64_t N, int d, const double* __restrict__ Psi,
                            const double* __restrict__ Prev, double* __restrict__ part) {
   __shared__ double red[32];
@@ -704,78 +1078,94 @@ __global__ void k_inverse(int r, const double* __restrict__ G, double* __restric
 }
 
 // ---------------------------------------------- half-step power of A
-__device__ __forceinline__ double c_abs(double2 a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ double2 c_div(double2 a, double2 b) {  // Smith's algorithm
+// complex helpers in FP64 (double2) and FP32 (float2)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float c_abs(float2 a) { return hypotf(a.x, a.y); }
+template <class C> struct CplxT;
+template <> struct CplxT<double2> {
+  using R = double;
+  static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <> struct CplxT<float2> {
+  using R = float;
+  static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+  static constexpr float eps = 1.1920929e-7f;
+};
+template <class C>
+__device__ __forceinline__ C c_div(C a, C b) {  // Smith's algorithm
+  using R = typename CplxT<C>::R;
   if (fabs(b.x) >= fabs(b.y)) {
-    const double q = b.y / b.x, den = b.x + b.y * q;
-    return make_double2((a.x + a.y * q) / den, (a.y - a.x * q) / den);
+    const R q = b.y / b.x, den = b.x + b.y * q;
+    return CplxT<C>::make((a.x + a.y * q) / den, (a.y - a.x * q) / den);
   }
-  const double q = b.x / b.y, den = b.x * q + b.y;
-  return make_double2((a.x * q + a.y) / den, (a.y * q - a.x) / den);
+  const R q = b.x / b.y, den = b.x * q + b.y;
+  return CplxT<C>::make((a.x * q + a.y) / den, (a.y * q - a.x) / den);
 }
 // principal square root, branch cut on the negative real axis (the sign of
 // the imaginary part, zero included, picks the side)
-__device__ __forceinline__ double2 c_sqrt(double2 z) {
-  if (z.x == 0.0 && z.y == 0.0) return make_double2(0.0, 0.0);
-  const double t = sqrt(0.5 * (c_abs(z) + fabs(z.x)));
-  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
-  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+template <class C>
+__device__ __forceinline__ C c_sqrt(C z) {
+  using R = typename CplxT<C>::R;
+  if (z.x == (R)0 && z.y == (R)0) return CplxT<C>::make(0, 0);
+  const R t = sqrt((R)0.5 * (c_abs(z) + fabs(z.x)));
+  if (z.x >= (R)0) return CplxT<C>::make(t, z.y / ((R)2 * t));
+  return CplxT<C>::make(fabs(z.y) / ((R)2 * t), copysign(t, z.y));
 }
 
-// S = Re(A^{1/2}) with the principal power of every eigenvalue (A real, r x r,
-// r <= 64), i.e. Re(W Lambda^{1/2} W^-1) for A = W Lambda W^-1: the half-step
-// factor of exact DMD.  An eigenvalue on the negative real axis (a mode that
-// changes sign every step) contributes +-i |lambda|^{1/2} times a real
-// projector, whose real part is zero on either side of the cut.
-// Method: complex Schur form A = Q T Q^H (Householder reduction to Hessenberg
-// form, then implicit single-shift QR sweeps with Wilkinson shifts, Givens
-// rotations and deflation; every tenth sweep of an eigenvalue uses an ad hoc
-// shift), the upper-triangular square root R of T by the recurrence
-// R_ii = T_ii^{1/2}, (R_ii + R_jj) R_ij = T_ij - sum_{i<k<j} R_ik R_kj (Bjorck
-// and Hammarling, 1983), then S = Re(Q R Q^H).  One warp; the QR sweeps stop
-// after 40 r in total (VP_ENOCONV).
-__global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict__ S, int* status) {
-  extern __shared__ double2 sq[];
-  double2* H = sq;           // r x r, becomes T, then Q R
-  double2* Qm = H + r * r;   // r x r
-  double2* R = Qm + r * r;   // r x r
-  __shared__ double v[64];
-  __shared__ double vv;
+// Complex Schur form A = Q T Q^H of the real r x r matrix A (r <= 64) in the
+// precision of C, then the upper-triangular square root Rm of T with the
+// principal power of every diagonal entry: Householder reduction to
+// Hessenberg form, implicit single-shift QR sweeps with Wilkinson shifts,
+// Givens rotations and deflation (every eleventh sweep of an eigenvalue uses an
+// ad hoc shift), then R_ii = T_ii^{1/2}, (R_ii + R_jj) R_ij = T_ij -
+// sum_{i<k<j} R_ik R_kj (Bjorck and Hammarling, 1983).  On return H holds T,
+// Qm the Schur vectors; false when the QR sweeps did not finish within 40 r
+// in total (VP_ENOCONV); a zero R_ii + R_jj sets VP_ENUMERIC.
+template <class C>
+__device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* Rm, int* status) {
+  using R = typename CplxT<C>::R;
+  using CT = CplxT<C>;
+  __shared__ R v[64];
+  __shared__ R vv;
   const int lane = threadIdx.x, nl = blockDim.x;
-  const double eps = 2.220446049250313e-16;
+  const R eps = CT::eps;
   for (int e = lane; e < r * r; e += nl) {
-    H[e] = make_double2(A[e], 0.0);
-    Qm[e] = make_double2((e / r == e % r) ? 1.0 : 0.0, 0.0);
+    H[e] = CT::make((R)A[e], 0);
+    Qm[e] = CT::make((e / r == e % r) ? 1 : 0, 0);
   }
   __syncthreads();
   // 1. Hessenberg form (A is real: real reflectors)
   for (int k = 0; k + 2 < r; ++k) {
     const int m = r - k - 1;
-    double sx = 0.0, x0 = H[(k + 1) * r + k].x;
+    R sx = 0, x0 = H[(k + 1) * r + k].x;
     for (int i = 1; i < m; ++i) {
-      const double t = H[(k + 1 + i) * r + k].x;
+      const R t = H[(k + 1 + i) * r + k].x;
       sx = fma(t, t, sx);
     }
-    if (sx == 0.0) continue;  // column already reduced (same value in every lane)
-    const double alpha = -copysign(sqrt(fma(x0, x0, sx)), x0);
+    if (sx == (R)0) continue;  // column already reduced (same value in every lane)
+    const R alpha = -copysign(sqrt(fma(x0, x0, sx)), x0);
     for (int i = lane; i < m; i += nl) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * r + k].x;
     __syncthreads();
     if (lane == 0) {
-      double t = 0.0;
+      R t = 0;
       for (int i = 0; i < m; ++i) t = fma(v[i], v[i], t);
       vv = t;
     }
     __syncthreads();
-    const double f = 2.0 / vv;
+    const R f = (R)2 / vv;
     for (int j = lane; j < r; j += nl) {  // H <- P H (rows k+1..)
-      double w = 0.0;
+      R w = 0;
       for (int i = 0; i < m; ++i) w = fma(v[i], H[(k + 1 + i) * r + j].x, w);
       w *= f;
       for (int i = 0; i < m; ++i) H[(k + 1 + i) * r + j].x -= v[i] * w;
     }
     __syncthreads();
     for (int i = lane; i < r; i += nl) {  // H <- H P, Q <- Q P (columns k+1..)
-      double w = 0.0, wq = 0.0;
+      R w = 0, wq = 0;
       for (int j = 0; j < m; ++j) {
         w = fma(H[i * r + k + 1 + j].x, v[j], w);
         wq = fma(Qm[i * r + k + 1 + j].x, v[j], wq);
@@ -788,27 +1178,27 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
       }
     }
     __syncthreads();
-    for (int i = k + 2 + lane; i < r; i += nl) H[i * r + k] = make_double2(0.0, 0.0);
+    for (int i = k + 2 + lane; i < r; i += nl) H[i * r + k] = CT::make(0, 0);
     __syncthreads();
   }
   // 2. complex Schur form by implicit single-shift QR sweeps; a subdiagonal
   // entry deflates below eps times its diagonal neighbours or below eps |A|_F
   // (a backward-stable perturbation either way)
-  __shared__ double nrm_s;
+  __shared__ R nrm_s;
   if (lane == 0) {
     double t = 0.0;
     for (int e = 0; e < r * r; ++e) t = fma(A[e], A[e], t);
-    nrm_s = sqrt(t);
+    nrm_s = (R)sqrt(t);
   }
   __syncthreads();
-  const double floor2 = eps * eps * nrm_s * nrm_s;
-  auto abs2 = [](double2 z) { return fma(z.x, z.x, z.y * z.y); };
+  const R floor2 = eps * eps * nrm_s * nrm_s;
+  auto abs2 = [](C z) { return fma(z.x, z.x, z.y * z.y); };
   // the scalar decisions (deflation scan, shift, rotation) are taken by
   // thread 0 and shared: FP64 chains cost the same in a full warp as in one
   // lane, so only the row and column updates are spread over the block
   __shared__ int sh_cmd, sh_l, sh_hi;
-  __shared__ double2 sh_mu, sh_sg;
-  __shared__ double sh_cg;
+  __shared__ C sh_mu, sh_sg;
+  __shared__ R sh_cg;
   int it = 0, total = 0;  // thread 0's counters
   if (lane == 0) sh_hi = r - 1;
   __syncthreads();
@@ -822,11 +1212,11 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
       } else {
         int l = hi;
         for (; l > 0; --l) {  // squared magnitudes: no square roots in the scan
-          const double sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
-          const double sub2 = abs2(H[l * r + l - 1]);
+          const R sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
+          const R sub2 = abs2(H[l * r + l - 1]);
           if (sub2 <= eps * eps * sc2 || sub2 <= floor2) break;
         }
-        if (l > 0) H[l * r + l - 1] = make_double2(0.0, 0.0);
+        if (l > 0) H[l * r + l - 1] = CT::make(0, 0);
         if (l == hi) {
           sh_hi = hi - 1;
           it = 0;
@@ -834,16 +1224,16 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
         } else if (total > 40 * r) {
           cmd = 3;
         } else {
-          const double2 a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi],
+          const C a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi],
                         c = H[hi * r + hi - 1], d = H[hi * r + hi];
-          double2 mu;
+          C mu;
           if (it % 11 == 10) {
-            mu = make_double2(d.x + 0.75 * c_abs(c), d.y);
+            mu = CT::make(d.x + (R)0.75 * c_abs(c), d.y);
           } else {
-            const double2 h = make_double2(0.5 * (a.x - d.x), 0.5 * (a.y - d.y));
-            const double2 disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
-            const double2 m0 = make_double2(0.5 * (a.x + d.x), 0.5 * (a.y + d.y));
-            const double2 m1 = cadd(m0, disc), m2 = csub(m0, disc);
+            const C h = CT::make((R)0.5 * (a.x - d.x), (R)0.5 * (a.y - d.y));
+            const C disc = c_sqrt(cadd(cmul(h, h), cmul(b, c)));
+            const C m0 = CT::make((R)0.5 * (a.x + d.x), (R)0.5 * (a.y + d.y));
+            const C m1 = cadd(m0, disc), m2 = csub(m0, disc);
             mu = abs2(csub(m1, d)) < abs2(csub(m2, d)) ? m1 : m2;
           }
           sh_l = l;
@@ -865,7 +1255,7 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
     if (cmd == 1) continue;
     for (int k = l; k < hi; ++k) {
       if (lane == 0) {
-        double2 x, y;
+        C x, y;
         if (k == l) {
           x = csub(H[l * r + l], sh_mu);
           y = H[(l + 1) * r + l];
@@ -874,99 +1264,155 @@ __global__ void k_sqrtm(int r, const double* __restrict__ A, double* __restrict_
           y = H[(k + 1) * r + k - 1];
         }
         // G = [[cg, sg], [-conj(sg), cg]] with G [x; y] = [rho; 0]
-        if (y.x == 0.0 && y.y == 0.0) {
-          sh_cg = 1.0;
-          sh_sg = make_double2(0.0, 0.0);
-        } else if (x.x == 0.0 && x.y == 0.0) {
-          sh_cg = 0.0;
-          sh_sg = make_double2(1.0, 0.0);
+        if (y.x == (R)0 && y.y == (R)0) {
+          sh_cg = 1;
+          sh_sg = CT::make(0, 0);
+        } else if (x.x == (R)0 && x.y == (R)0) {
+          sh_cg = 0;
+          sh_sg = CT::make(1, 0);
         } else {  // cg = |x| / n, sg = (x / |x|) conj(y) / n, n^2 = |x|^2 + |y|^2
-          const double ax2 = abs2(x), ix = rsqrt(ax2), in = rsqrt(ax2 + abs2(y));
+          const R ax2 = abs2(x), ix = rsqrt(ax2), in = rsqrt(ax2 + abs2(y));
           sh_cg = ax2 * ix * in;
-          sh_sg = cmul(make_double2(x.x * ix, x.y * ix), make_double2(y.x * in, -y.y * in));
+          sh_sg = cmul(CT::make(x.x * ix, x.y * ix), CT::make(y.x * in, -y.y * in));
         }
       }
       __syncthreads();
-      const double cg = sh_cg;
-      const double2 sg = sh_sg;
-      const double2 sc = make_double2(sg.x, -sg.y);
+      const R cg = sh_cg;
+      const C sg = sh_sg;
+      const C sc = CT::make(sg.x, -sg.y);
       // rows k, k+1 <- G [rows]: one output per thread (FP64 issue, not the
       // lane count, sets the cost, so outputs are spread over all warps);
       // inputs are read before the barrier, outputs written after it
       const int j0 = k == l ? l : k - 1, w = r - j0;
-      double2 outv = make_double2(0.0, 0.0);
+      C outv = CT::make(0, 0);
       int oidx = -1;
       for (int o = lane; o < 2 * w; o += nl) {
         const int j = j0 + (o < w ? o : o - w);
-        const double2 h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
+        const C h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
         if (o < w) {
-          outv = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(sg, h1));
+          outv = cadd(CT::make(cg * h0.x, cg * h0.y), cmul(sg, h1));
           oidx = k * r + j;
         } else {
-          outv = csub(make_double2(cg * h1.x, cg * h1.y), cmul(sc, h0));
+          outv = csub(CT::make(cg * h1.x, cg * h1.y), cmul(sc, h0));
           oidx = (k + 1) * r + j;
         }
       }
       __syncthreads();
       if (oidx >= 0) H[oidx] = outv;
       __syncthreads();
-      if (k > l && lane == 0) H[(k + 1) * r + k - 1] = make_double2(0.0, 0.0);
+      if (k > l && lane == 0) H[(k + 1) * r + k - 1] = CT::make(0, 0);
       // columns k, k+1 <- [columns] G^H: H rows in the first half of the
       // block, Q rows in the second (different warps, so they overlap)
       const int i1 = min(k + 2, hi) + 1, half = nl / 2;
-      double2* M2 = lane < half ? H : Qm;
+      C* M2 = lane < half ? H : Qm;
       const int lim = lane < half ? i1 : r;
       for (int i = lane < half ? lane : lane - half; i < lim; i += half) {
-        const double2 h0 = M2[i * r + k], h1 = M2[i * r + k + 1];
-        M2[i * r + k] = cadd(make_double2(cg * h0.x, cg * h0.y), cmul(h1, sc));
-        M2[i * r + k + 1] = csub(make_double2(cg * h1.x, cg * h1.y), cmul(h0, sg));
+        const C h0 = M2[i * r + k], h1 = M2[i * r + k + 1];
+        M2[i * r + k] = cadd(CT::make(cg * h0.x, cg * h0.y), cmul(h1, sc));
+        M2[i * r + k + 1] = csub(CT::make(cg * h1.x, cg * h1.y), cmul(h0, sg));
       }
       __syncthreads();
     }
   }
   if (failed) {
     if (lane == 0) vp_set_status(status, VP_ENOCONV);
-    return;
+    return false;
   }
   // 3. R = T^{1/2} (upper triangular), superdiagonal by superdiagonal
   bool singular = false;
   for (int e = lane; e < r * r; e += nl) {
     const int i = e / r, j = e - i * r;
-    R[e] = i == j ? c_sqrt(H[e]) : make_double2(0.0, 0.0);
+    Rm[e] = i == j ? c_sqrt(H[e]) : CT::make(0, 0);
   }
   __syncthreads();
   for (int dd = 1; dd < r; ++dd) {
     for (int i = lane; i + dd < r; i += nl) {
       const int j = i + dd;
-      double2 s = H[i * r + j];
-      for (int k = i + 1; k < j; ++k) s = csub(s, cmul(R[i * r + k], R[k * r + j]));
-      const double2 den = cadd(R[i * r + i], R[j * r + j]);
-      if (den.x == 0.0 && den.y == 0.0) {
+      C s = H[i * r + j];
+      for (int k = i + 1; k < j; ++k) s = csub(s, cmul(Rm[i * r + k], Rm[k * r + j]));
+      const C den = cadd(Rm[i * r + i], Rm[j * r + j]);
+      if (den.x == (R)0 && den.y == (R)0) {
         singular = true;
-        R[i * r + j] = make_double2(0.0, 0.0);
+        Rm[i * r + j] = CT::make(0, 0);
       } else {
-        R[i * r + j] = c_div(s, den);
+        Rm[i * r + j] = c_div(s, den);
       }
     }
     __syncthreads();
   }
   if (singular) vp_set_status(status, VP_ENUMERIC);
-  // 4. S = Re(Q R Q^H): H <- Q R, then S_ij = Re sum_k H_ik conj(Q_jk)
-  for (int e = lane; e < r * r; e += nl) {
-    const int i = e / r, j = e - i * r;
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k <= j; ++k) s = cadd(s, cmul(Qm[i * r + k], R[k * r + j]));
-    H[e] = s;
-  }
+  return true;
+}
+
+// ------------------------------------------ mixed-precision half-step power
+// Re(A^{1/2}) with the Schur form and the triangular root in FP32, then one
+// Newton step in FP64: with X0 = Q R Q^H (Q, R the FP32 factors, in FP64),
+// the correction F of X0 F + F X0 = A - X0^2 is Q Y Q^H with
+// R Y + Y R = Q^H (A - X0^2) Q (a triangular Sylvester equation), since
+// Q^H Q = I to FP32 rounding; X1 = X0 + F is the principal root to FP64
+// rounding (the error of X0, ~1e-7, squared, plus 1e-7 of the correction).
+// k_sqrtm_schur32: the FP32 factors, written as FP64 complex r x r (r <= 64).
+__global__ void k_sqrtm_schur32(int r, const double* __restrict__ A, double2* __restrict__ Qd,
+                                double2* __restrict__ Rd, int* status) {
+  extern __shared__ float2 sq32[];
+  float2* H = sq32;
+  float2* Qm = H + r * r;
+  float2* Rm = Qm + r * r;
+  if (!schur_sqrt<float2>(r, A, H, Qm, Rm, status)) return;
   __syncthreads();
-  for (int e = lane; e < r * r; e += nl) {
-    const int i = e / r, j = e - i * r;
-    double s = 0.0;
-    for (int k = 0; k < r; ++k) {
-      const double2 h = H[i * r + k], q = Qm[j * r + k];
-      s = fma(h.x, q.x, fma(h.y, q.y, s));  // Re(h conj(q))
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    Qd[e] = make_double2(Qm[e].x, Qm[e].y);
+    Rd[e] = make_double2(Rm[e].x, Rm[e].y);
+  }
+}
+
+// One row per block (r blocks of 64 threads, thread j: column j) of
+// op(P) op(Qm) with op = identity or conjugate transpose (FP64 complex,
+// r x r row-major).  mode 0: out = op(P) op(Qm); mode 1: out = A - op(P) op(Qm)
+// with A real; mode 2: S = Re(Z + op(P) op(Qm)) (real output).
+__global__ void k_cmm_row(int r, const double2* __restrict__ P, int ph,
+                          const double2* __restrict__ Qm, int qh, int mode,
+                          const double* __restrict__ A, const double2* __restrict__ Z,
+                          double2* __restrict__ out, double* __restrict__ S) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= r) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int k = 0; k < r; ++k) {
+    const double2 p = ph ? make_double2(P[k * r + i].x, -P[k * r + i].y) : P[i * r + k];
+    const double2 q = qh ? make_double2(Qm[j * r + k].x, -Qm[j * r + k].y) : Qm[k * r + j];
+    s = cadd(s, cmul(p, q));
+  }
+  const int e = i * r + j;
+  if (mode == 0) out[e] = s;
+  else if (mode == 1) out[e] = make_double2(A[e] - s.x, -s.y);
+  else S[e] = Z[e].x + s.x;
+}
+
+// R Y + Y R = C for upper-triangular R (r x r, FP64 complex), Y full: entry
+// (i, j) needs Y_kj (k > i) and Y_ik (k < j), so the anti-diagonals
+// d = j - i are solved in increasing order; each entry's sum is spread over a
+// warp.  A zero R_ii + R_jj leaves Y_ij = 0 (the FP32 phase has flagged it).
+__global__ void k_sylv_tri(int r, const double2* __restrict__ Rm, const double2* __restrict__ C,
+                           double2* __restrict__ Y) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int d = -(r - 1); d <= r - 1; ++d) {
+    const int i0 = d < 0 ? -d : 0, cnt = r - (d < 0 ? -d : d);
+    for (int q = warp; q < cnt; q += nw) {
+      const int i = i0 + q, j = i + d;
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = i + 1 + lane; k < r; k += 32) s = cadd(s, cmul(Rm[i * r + k], Y[k * r + j]));
+      for (int k = lane; k < j; k += 32) s = cadd(s, cmul(Y[i * r + k], Rm[k * r + j]));
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        const double2 den = cadd(Rm[i * r + i], Rm[j * r + j]);
+        Y[i * r + j] = (den.x == 0.0 && den.y == 0.0) ? make_double2(0.0, 0.0)
+                                                     : c_div(csub(C[i * r + j], s), den);
+      }
     }
-    S[e] = s;
+    __syncthreads();
   }
 }
 
@@ -1224,10 +1670,11 @@ void deim_init() {
   cudaFuncSetAttribute(k_ygram, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_psi, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_jacobi_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_jacobi_sym_mp, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_jacobi_sym_df, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_deim_lu_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_deim_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_rbf, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_sqrtm, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_sqrtm_schur32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_phi_at_qz, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_deim_round, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -1268,7 +1715,33 @@ size_t deim_indices_scratch(int sms, int64_t N, int d) {
   const int nb = std::min<int64_t>(ceil_div(N, 256), 2 * sms);
   return arena_bytes(nb, 8) + arena_bytes(nb, 8) + arena_bytes(128, 8) +
          arena_bytes((size_t)nb * d, 8) + arena_bytes(d, 8) + arena_bytes(d, 4) +
-         arena_bytes((size_t)d * N, 8) + arena_bytes(1, 4);
+         arena_bytes((size_t)d * N, 8) + arena_bytes(1, 4) +
+         // the cooperative form: two parities of per-block candidates and rows, barrier words
+         2 * arena_bytes((size_t)2 * sms, 8) + arena_bytes((size_t)2 * sms * d, 8) +
+         arena_bytes(2, 4);
+}
+
+// The cooperative form of the index selection when every block's slice of
+// the basis fits in shared memory (one block per SM); false: not launched.
+static bool deim_lu_coop(vp_ctx* ctx, int64_t N, int d, const double* Psi, int32_t* idx,
+                         const int* renew, double* pval, int64_t* pidx, double* prows,
+                         unsigned* bar, cudaStream_t st) {
+  const int nb = ctx->num_sms;
+  const int64_t rb64 = (N + nb - 1) / nb;
+  const size_t smem = sizeof(double) * (size_t)d * (size_t)rb64;
+  if (d > 128 || N < nb || smem > 200 * 1024) return false;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_deim_lu_coop, kLuThreads, smem) !=
+          cudaSuccess ||
+      per < 1)
+    return false;
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return false;
+  int rb = (int)rb64;
+  int* abort_flag = reinterpret_cast<int*>(bar + 1);
+  int* status = ctx->d_status;
+  void* args[] = {&N, &d, &rb, &Psi, &idx, &renew, &pval, &pidx, &prows, &bar, &abort_flag, &status};
+  return cudaLaunchCooperativeKernel((const void*)k_deim_lu_coop, nb, kLuThreads, args, smem, st) ==
+         cudaSuccess;
 }
 
 vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int32_t* idx,
@@ -1284,6 +1757,10 @@ vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int
   int* renew = a.take<int>(d);
   double* R = a.take<double>((size_t)d * N);
   int* ticket = a.take<int>(1);
+  double* cval = a.take<double>((size_t)2 * ctx->num_sms);
+  int64_t* cidx = a.take<int64_t>((size_t)2 * ctx->num_sms);
+  double* crows = a.take<double>((size_t)2 * ctx->num_sms * d);
+  unsigned* cbar = a.take<unsigned>(2);
   const int* rn = nullptr;
   if (Psi_prev) {  // index update: renew the n_up most rotated positions
     VP_K(VP_K_DEIM, (k_rot_dots<<<nb, 256, 0, st>>>(N, d, Psi, Psi_prev, part)));
@@ -1291,6 +1768,9 @@ vp_status deim_indices_run(vp_ctx* ctx, int64_t N, int d, const double* Psi, int
     VP_K(VP_K_DEIM, (k_renew<<<1, 32, 0, st>>>(d, dots, n_up, renew)));
     rn = renew;
   }
+  bool coop = false;
+  VP_K(VP_K_DEIM, coop = deim_lu_coop(ctx, N, d, Psi, idx, rn, cval, cidx, crows, cbar, st));
+  if (coop) return VP_OK;
   VP_CUDA(cudaMemcpyAsync(R, Psi, sizeof(double) * d * N, cudaMemcpyDeviceToDevice, st));
   VP_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int), st));
   for (int k = 0; k < d; ++k)
@@ -1322,7 +1802,7 @@ size_t dmd_fit_scratch(int nx, int m, int r_max) {
   const int gx = std::max(1, std::min(ceil_div(nx, YG_ROWS), 64));
   return arena_bytes((size_t)gx * tot, 8) + 4 * arena_bytes(tot, 8) + arena_bytes(m, 8) +
          arena_bytes((size_t)m * r_max, 8) + arena_bytes((size_t)r_max * nx, 8) +
-         2 * arena_bytes((size_t)r_max * r_max, 8);
+         2 * arena_bytes((size_t)r_max * r_max, 8) + 7 * arena_bytes((size_t)r_max * r_max, 16);
 }
 
 vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double* Yp, double tol,
@@ -1342,11 +1822,13 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   double* U = a.take<double>((size_t)r_max * nx);
   double* BtB = a.take<double>((size_t)r_max * r_max);
   double* BtBi = a.take<double>((size_t)r_max * r_max);
+  double2* sq[7];  // half-step power: Q, R, two products, X, residual, Y
+  for (int i = 0; i < 7; ++i) sq[i] = a.take<double2>((size_t)r_max * r_max);
   // 1. Y^T Y and its eigen-decomposition (singular values and right vectors of Y)
   VP_K(VP_K_DMD, (k_ygram<<<dim3(gx, gy), 256, sizeof(double) * m * YG_ROWS, st>>>(nx, m, Y, nx,
                                                                                        part)));
   VP_K(VP_K_REDUCE, reduce_partials(gx, tri, part, G, nullptr, st));
-  VP_K(VP_K_JACOBI_SYM, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st));
+  VP_K(VP_K_JACOBI_SYM, jacobi_sym(m, G, Aj, Wj, lam, Ws, ctx->d_status, st, true));
   std::vector<double> lh(m);
   VP_CUDA(cudaMemcpyAsync(lh.data(), lam, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
   VP_CUDA(cudaStreamSynchronize(st));
@@ -1372,8 +1854,19 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   // B^+ (r x nx) = BtBi (r x r) * B^T; B is stored as r columns of length nx,
   // i.e. the row-major r x nx matrix B^T
   VP_K(VP_K_DMD, (k_mm<<<gcols, 256, 0, st>>>(r, r, nx, BtBi, B, Bpinv)));
-  // 4. real part of the principal square root of A for half steps
-  VP_K(VP_K_DMD, (k_sqrtm<<<1, 256, sizeof(double2) * 3 * r * r, st>>>(r, A, S, ctx->d_status)));
+  // 4. real part of the principal square root of A for half steps: FP32
+  // Schur form and triangular root, one FP64 Newton step
+  double2 *Qd = sq[0], *Rd = sq[1], *M1 = sq[2], *X = sq[3], *E = sq[4], *Cm = sq[5], *Ys = sq[6];
+  VP_K(VP_K_DMD, (k_sqrtm_schur32<<<1, 256, sizeof(float2) * 3 * r * r, st>>>(r, A, Qd, Rd,
+                                                                              ctx->d_status)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 0, Rd, 0, 0, nullptr, nullptr, M1, nullptr)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 1, 0, nullptr, nullptr, X, nullptr)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, X, 0, X, 0, 1, A, nullptr, E, nullptr)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 1, E, 0, 0, nullptr, nullptr, M1, nullptr)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 0, 0, nullptr, nullptr, Cm, nullptr)));
+  VP_K(VP_K_DMD, (k_sylv_tri<<<1, 256, 0, st>>>(r, Rd, Cm, Ys)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 0, Ys, 0, 0, nullptr, nullptr, M1, nullptr)));
+  VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 1, 2, nullptr, X, nullptr, S)));
   return VP_OK;
 }
 
