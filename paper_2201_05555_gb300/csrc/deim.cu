@@ -281,15 +281,17 @@ __device__ __forceinline__ DFv dfv_rot(DFv c, DFv a, DFv s, DFv b) {
 }
 
 // Round-robin cyclic Jacobi sweeps as jacobi_sweeps, in double-float: a pair
-// (j, k) rotates unless |a_jk| <= 1e-14 sqrt|a_jj a_kk| (double-float
-// rounding is ~4e-15) or both diagonal entries are below 1e-14 of the
-// largest.  The tangent of the angle is taken in FP32 from the leading parts
+// (j, k) rotates unless |a_jk| <= rel sqrt|a_jj a_kk| or both diagonal
+// entries are below 1e-14 of the largest.  rel must stay well above the
+// double-float rounding of ~4e-15 per operation, which the entries
+// accumulate over the sweeps: at 1e-14 pairs near that level went on
+// rotating until the sweep cap.  The tangent of the angle is taken in FP32 from the leading parts
 // (as in the FP64 sweeps); c = (1 + t^2)^-1/2 by an FP32 reciprocal square
 // root and one Newton step in double-float, s = t c, so the rotation is
 // orthogonal to double-float rounding.  Returns after a sweep without
 // rotations (true) or after max_sweeps (false).
-__device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, DFv* rc, DFv* rs, int* pj,
-                                 int* pk, int* nrot, float* nu_s) {
+__device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, float rel, DFv* rc,
+                                 DFv* rs, int* pj, int* pk, int* nrot, float* nu_s) {
   const int t = threadIdx.x, nt = blockDim.x;
   const int slots = (m + 1) & ~1, npair = slots / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -313,7 +315,7 @@ __device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, 
         if (k < m) {
           const DFv ajk = A[j * ld + k], ajj = A[j * ld + j], akk = A[k * ld + k];
           const float x = fabsf(ajk.h);
-          if (x > 1e-14f * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
+          if (x > rel * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
               fmaxf(fabsf(ajj.h), fabsf(akk.h)) > nu) {
             atomicAdd(nrot, 1);
             const DFv dd = dfv_add(akk, dfv_neg(ajj));
@@ -422,7 +424,10 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
     W[i * ld + j] = dfv(i == j ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
-  const bool conv = jacobi_sweeps_df(m, ld, A, W, max_sweeps, rc, rs, pj, pk, &nrot, &nu);
+  // 1e-13 for the result as it is; 1e-12 before the FP64 finish, which takes
+  // the rest
+  const bool conv = jacobi_sweeps_df(m, ld, A, W, max_sweeps, refine ? 1e-12f : 1e-13f, rc, rs, pj,
+                                     pk, &nrot, &nu);
   if (!refine) {
     if (!conv && t == 0) vp_set_status(status, VP_ENOCONV);
     if (t == 0) {  // eigenvalues descending (selection order)
@@ -1123,7 +1128,8 @@ __device__ __forceinline__ C c_sqrt(C z) {
 // Qm the Schur vectors; false when the QR sweeps did not finish within 40 r
 // in total (VP_ENOCONV); a zero R_ii + R_jj sets VP_ENUMERIC.
 template <class C>
-__device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* Rm, int* status) {
+__device__ bool schur_sqrt(int r, int ld, const double* __restrict__ A, C* H, C* Qm, C* Rm,
+                           int* status) {
   using R = typename CplxT<C>::R;
   using CT = CplxT<C>;
   __shared__ R v[64];
@@ -1131,21 +1137,22 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
   const int lane = threadIdx.x, nl = blockDim.x;
   const R eps = CT::eps;
   for (int e = lane; e < r * r; e += nl) {
-    H[e] = CT::make((R)A[e], 0);
-    Qm[e] = CT::make((e / r == e % r) ? 1 : 0, 0);
+    const int i = e / r, j = e - i * r;
+    H[i * ld + j] = CT::make((R)A[e], 0);
+    Qm[i * ld + j] = CT::make(i == j ? 1 : 0, 0);
   }
   __syncthreads();
   // 1. Hessenberg form (A is real: real reflectors)
   for (int k = 0; k + 2 < r; ++k) {
     const int m = r - k - 1;
-    R sx = 0, x0 = H[(k + 1) * r + k].x;
+    R sx = 0, x0 = H[(k + 1) * ld + k].x;
     for (int i = 1; i < m; ++i) {
-      const R t = H[(k + 1 + i) * r + k].x;
+      const R t = H[(k + 1 + i) * ld + k].x;
       sx = fma(t, t, sx);
     }
     if (sx == (R)0) continue;  // column already reduced (same value in every lane)
     const R alpha = -copysign(sqrt(fma(x0, x0, sx)), x0);
-    for (int i = lane; i < m; i += nl) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * r + k].x;
+    for (int i = lane; i < m; i += nl) v[i] = i == 0 ? x0 - alpha : H[(k + 1 + i) * ld + k].x;
     __syncthreads();
     if (lane == 0) {
       R t = 0;
@@ -1156,26 +1163,26 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
     const R f = (R)2 / vv;
     for (int j = lane; j < r; j += nl) {  // H <- P H (rows k+1..)
       R w = 0;
-      for (int i = 0; i < m; ++i) w = fma(v[i], H[(k + 1 + i) * r + j].x, w);
+      for (int i = 0; i < m; ++i) w = fma(v[i], H[(k + 1 + i) * ld + j].x, w);
       w *= f;
-      for (int i = 0; i < m; ++i) H[(k + 1 + i) * r + j].x -= v[i] * w;
+      for (int i = 0; i < m; ++i) H[(k + 1 + i) * ld + j].x -= v[i] * w;
     }
     __syncthreads();
     for (int i = lane; i < r; i += nl) {  // H <- H P, Q <- Q P (columns k+1..)
       R w = 0, wq = 0;
       for (int j = 0; j < m; ++j) {
-        w = fma(H[i * r + k + 1 + j].x, v[j], w);
-        wq = fma(Qm[i * r + k + 1 + j].x, v[j], wq);
+        w = fma(H[i * ld + k + 1 + j].x, v[j], w);
+        wq = fma(Qm[i * ld + k + 1 + j].x, v[j], wq);
       }
       w *= f;
       wq *= f;
       for (int j = 0; j < m; ++j) {
-        H[i * r + k + 1 + j].x -= w * v[j];
-        Qm[i * r + k + 1 + j].x -= wq * v[j];
+        H[i * ld + k + 1 + j].x -= w * v[j];
+        Qm[i * ld + k + 1 + j].x -= wq * v[j];
       }
     }
     __syncthreads();
-    for (int i = k + 2 + lane; i < r; i += nl) H[i * r + k] = CT::make(0, 0);
+    for (int i = k + 2 + lane; i < r; i += nl) H[i * ld + k] = CT::make(0, 0);
     __syncthreads();
   }
   // 2. complex Schur form by implicit single-shift QR sweeps; a subdiagonal
@@ -1209,11 +1216,11 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
       } else {
         int l = hi;
         for (; l > 0; --l) {  // squared magnitudes: no square roots in the scan
-          const R sc2 = abs2(H[(l - 1) * r + l - 1]) + abs2(H[l * r + l]);
-          const R sub2 = abs2(H[l * r + l - 1]);
+          const R sc2 = abs2(H[(l - 1) * ld + l - 1]) + abs2(H[l * ld + l]);
+          const R sub2 = abs2(H[l * ld + l - 1]);
           if (sub2 <= eps * eps * sc2 || sub2 <= floor2) break;
         }
-        if (l > 0) H[l * r + l - 1] = CT::make(0, 0);
+        if (l > 0) H[l * ld + l - 1] = CT::make(0, 0);
         if (l == hi) {
           sh_hi = hi - 1;
           it = 0;
@@ -1221,8 +1228,8 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
         } else if (total > 40 * r) {
           cmd = 3;
         } else {
-          const C a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi],
-                        c = H[hi * r + hi - 1], d = H[hi * r + hi];
+          const C a = H[(hi - 1) * ld + hi - 1], b = H[(hi - 1) * ld + hi],
+                        c = H[hi * ld + hi - 1], d = H[hi * ld + hi];
           C mu;
           if (it % 11 == 10) {
             mu = CT::make(d.x + (R)0.75 * c_abs(c), d.y);
@@ -1254,11 +1261,11 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
       if (lane == 0) {
         C x, y;
         if (k == l) {
-          x = csub(H[l * r + l], sh_mu);
-          y = H[(l + 1) * r + l];
+          x = csub(H[l * ld + l], sh_mu);
+          y = H[(l + 1) * ld + l];
         } else {
-          x = H[k * r + k - 1];
-          y = H[(k + 1) * r + k - 1];
+          x = H[k * ld + k - 1];
+          y = H[(k + 1) * ld + k - 1];
         }
         // G = [[cg, sg], [-conj(sg), cg]] with G [x; y] = [rho; 0]
         if (y.x == (R)0 && y.y == (R)0) {
@@ -1285,28 +1292,28 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
       int oidx = -1;
       for (int o = lane; o < 2 * w; o += nl) {
         const int j = j0 + (o < w ? o : o - w);
-        const C h0 = H[k * r + j], h1 = H[(k + 1) * r + j];
+        const C h0 = H[k * ld + j], h1 = H[(k + 1) * ld + j];
         if (o < w) {
           outv = cadd(CT::make(cg * h0.x, cg * h0.y), cmul(sg, h1));
-          oidx = k * r + j;
+          oidx = k * ld + j;
         } else {
           outv = csub(CT::make(cg * h1.x, cg * h1.y), cmul(sc, h0));
-          oidx = (k + 1) * r + j;
+          oidx = (k + 1) * ld + j;
         }
       }
       __syncthreads();
       if (oidx >= 0) H[oidx] = outv;
       __syncthreads();
-      if (k > l && lane == 0) H[(k + 1) * r + k - 1] = CT::make(0, 0);
+      if (k > l && lane == 0) H[(k + 1) * ld + k - 1] = CT::make(0, 0);
       // columns k, k+1 <- [columns] G^H: H rows in the first half of the
       // block, Q rows in the second (different warps, so they overlap)
       const int i1 = min(k + 2, hi) + 1, half = nl / 2;
       C* M2 = lane < half ? H : Qm;
       const int lim = lane < half ? i1 : r;
       for (int i = lane < half ? lane : lane - half; i < lim; i += half) {
-        const C h0 = M2[i * r + k], h1 = M2[i * r + k + 1];
-        M2[i * r + k] = cadd(CT::make(cg * h0.x, cg * h0.y), cmul(h1, sc));
-        M2[i * r + k + 1] = csub(CT::make(cg * h1.x, cg * h1.y), cmul(h0, sg));
+        const C h0 = M2[i * ld + k], h1 = M2[i * ld + k + 1];
+        M2[i * ld + k] = cadd(CT::make(cg * h0.x, cg * h0.y), cmul(h1, sc));
+        M2[i * ld + k + 1] = csub(CT::make(cg * h1.x, cg * h1.y), cmul(h0, sg));
       }
       __syncthreads();
     }
@@ -1319,20 +1326,20 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
   bool singular = false;
   for (int e = lane; e < r * r; e += nl) {
     const int i = e / r, j = e - i * r;
-    Rm[e] = i == j ? c_sqrt(H[e]) : CT::make(0, 0);
+    Rm[i * ld + j] = i == j ? c_sqrt(H[i * ld + j]) : CT::make(0, 0);
   }
   __syncthreads();
   for (int dd = 1; dd < r; ++dd) {
     for (int i = lane; i + dd < r; i += nl) {
       const int j = i + dd;
-      C s = H[i * r + j];
-      for (int k = i + 1; k < j; ++k) s = csub(s, cmul(Rm[i * r + k], Rm[k * r + j]));
-      const C den = cadd(Rm[i * r + i], Rm[j * r + j]);
+      C s = H[i * ld + j];
+      for (int k = i + 1; k < j; ++k) s = csub(s, cmul(Rm[i * ld + k], Rm[k * ld + j]));
+      const C den = cadd(Rm[i * ld + i], Rm[j * ld + j]);
       if (den.x == (R)0 && den.y == (R)0) {
         singular = true;
-        Rm[i * r + j] = CT::make(0, 0);
+        Rm[i * ld + j] = CT::make(0, 0);
       } else {
-        Rm[i * r + j] = c_div(s, den);
+        Rm[i * ld + j] = c_div(s, den);
       }
     }
     __syncthreads();
@@ -1352,14 +1359,16 @@ __device__ bool schur_sqrt(int r, const double* __restrict__ A, C* H, C* Qm, C* 
 __global__ void k_sqrtm_schur32(int r, const double* __restrict__ A, double2* __restrict__ Qd,
                                 double2* __restrict__ Rd, int* status) {
   extern __shared__ float2 sq32[];
+  const int ld = r + 1;  // padded rows: column sweeps of a stride r share banks
   float2* H = sq32;
-  float2* Qm = H + r * r;
-  float2* Rm = Qm + r * r;
-  if (!schur_sqrt<float2>(r, A, H, Qm, Rm, status)) return;
+  float2* Qm = H + r * ld;
+  float2* Rm = Qm + r * ld;
+  if (!schur_sqrt<float2>(r, ld, A, H, Qm, Rm, status)) return;
   __syncthreads();
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    Qd[e] = make_double2(Qm[e].x, Qm[e].y);
-    Rd[e] = make_double2(Rm[e].x, Rm[e].y);
+    const int i = e / r, j = e - i * r;
+    Qd[e] = make_double2(Qm[i * ld + j].x, Qm[i * ld + j].y);
+    Rd[e] = make_double2(Rm[i * ld + j].x, Rm[i * ld + j].y);
   }
 }
 
@@ -1390,16 +1399,25 @@ __global__ void k_cmm_row(int r, const double2* __restrict__ P, int ph,
 // d = j - i are solved in increasing order; each entry's sum is spread over a
 // warp (1024 threads: one entry per warp for r <= 32).  A zero R_ii + R_jj
 // leaves Y_ij = 0 (the FP32 phase has flagged it).
-__global__ void k_sylv_tri(int r, const double2* __restrict__ Rm, const double2* __restrict__ C,
-                           double2* __restrict__ Y) {
+__global__ void k_sylv_tri(int r, const double2* __restrict__ Rg, const double2* __restrict__ C,
+                           double2* __restrict__ Yg) {
+  extern __shared__ double2 sy[];  // R and Y, rows padded to r + 1
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ld = r + 1;
+  double2* Rm = sy;
+  double2* Y = sy + r * ld;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e - i * r;
+    Rm[i * ld + j] = Rg[e];
+  }
+  __syncthreads();
   for (int d = -(r - 1); d <= r - 1; ++d) {
     const int i0 = d < 0 ? -d : 0, cnt = r - (d < 0 ? -d : d);
     for (int q = warp; q < cnt; q += nw) {
       const int i = i0 + q, j = i + d;
       double2 s = make_double2(0.0, 0.0);
-      for (int k = i + 1 + lane; k < r; k += 32) s = cadd(s, cmul(Rm[i * r + k], Y[k * r + j]));
-      for (int k = lane; k < j; k += 32) s = cadd(s, cmul(Y[i * r + k], Rm[k * r + j]));
+      for (int k = i + 1 + lane; k < r; k += 32) s = cadd(s, cmul(Rm[i * ld + k], Y[k * ld + j]));
+      for (int k = lane; k < j; k += 32) s = cadd(s, cmul(Y[i * ld + k], Rm[k * ld + j]));
       for (int o = 16; o > 0; o >>= 1) {
         s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
         s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
@@ -1407,21 +1425,25 @@ __global__ void k_sylv_tri(int r, const double2* __restrict__ Rm, const double2*
       if (lane == 0) {
         // (C - s) / den as (C - s) conj(den) / |den|^2, the reciprocal of
         // |den|^2 from FP32 by two Newton steps in FP64 (FP64 accurate)
-        const double2 den = cadd(Rm[i * r + i], Rm[j * r + j]);
+        const double2 den = cadd(Rm[i * ld + i], Rm[j * ld + j]);
         const double dn = fma(den.x, den.x, den.y * den.y);
         double2 y = make_double2(0.0, 0.0);
         if (dn > 0.0 && dn < 1e300) {
-          double q = (double)(1.0f / (float)dn);
-          if (q == 0.0 || !isfinite(q)) q = 1.0 / dn;  // outside the FP32 range
-          q = q * fma(-dn, q, 2.0);
-          q = q * fma(-dn, q, 2.0);
+          double inv = (double)(1.0f / (float)dn);
+          if (inv == 0.0 || !isfinite(inv)) inv = 1.0 / dn;  // outside the FP32 range
+          inv = inv * fma(-dn, inv, 2.0);
+          inv = inv * fma(-dn, inv, 2.0);
           const double2 num = cmul(csub(C[i * r + j], s), make_double2(den.x, -den.y));
-          y = make_double2(num.x * q, num.y * q);
+          y = make_double2(num.x * inv, num.y * inv);
         }
-        Y[i * r + j] = y;
+        Y[i * ld + j] = y;
       }
     }
     __syncthreads();
+  }
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e / r, j = e - i * r;
+    Yg[e] = Y[i * ld + j];
   }
 }
 
@@ -1684,6 +1706,7 @@ void deim_init() {
   cudaFuncSetAttribute(k_deim_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_rbf, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_sqrtm_schur32, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_sylv_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_phi_at_qz, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_deim_round, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -1866,14 +1889,14 @@ vp_status dmd_fit_run(vp_ctx* ctx, int nx, int m, const double* Y, const double*
   // 4. real part of the principal square root of A for half steps: FP32
   // Schur form and triangular root, one FP64 Newton step
   double2 *Qd = sq[0], *Rd = sq[1], *M1 = sq[2], *X = sq[3], *E = sq[4], *Cm = sq[5], *Ys = sq[6];
-  VP_K(VP_K_DMD, (k_sqrtm_schur32<<<1, 256, sizeof(float2) * 3 * r * r, st>>>(r, A, Qd, Rd,
-                                                                              ctx->d_status)));
+  VP_K(VP_K_DMD, (k_sqrtm_schur32<<<1, 256, sizeof(float2) * 3 * r * (r + 1), st>>>(
+                      r, A, Qd, Rd, ctx->d_status)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 0, Rd, 0, 0, nullptr, nullptr, M1, nullptr)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 1, 0, nullptr, nullptr, X, nullptr)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, X, 0, X, 0, 1, A, nullptr, E, nullptr)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 1, E, 0, 0, nullptr, nullptr, M1, nullptr)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 0, 0, nullptr, nullptr, Cm, nullptr)));
-  VP_K(VP_K_DMD, (k_sylv_tri<<<1, 1024, 0, st>>>(r, Rd, Cm, Ys)));
+  VP_K(VP_K_DMD, (k_sylv_tri<<<1, 1024, sizeof(double2) * 2 * r * (r + 1), st>>>(r, Rd, Cm, Ys)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, Qd, 0, Ys, 0, 0, nullptr, nullptr, M1, nullptr)));
   VP_K(VP_K_DMD, (k_cmm_row<<<r, 64, 0, st>>>(r, M1, 0, Qd, 1, 2, nullptr, X, nullptr, S)));
   return VP_OK;
