@@ -130,7 +130,7 @@ __device__ bool jacobi_sweeps(int m, int ld, R* A, R* W, int max_sweeps, R rel, 
           const R ajk = A[j * ld + k], ajj = A[j * ld + j], akk = A[k * ld + k];
           if (fabs(ajk) > rel * sqrt(fabs(ajj * akk)) && fabs(ajk) > fl &&
               (float)fabs(ajk) > 0.0f && fmax(fabs(ajj), fabs(akk)) > nu) {
-            atomicAdd(nrot, 1);
+            *nrot = 1;  // any rotation this sweep (the same value from every writer)
             const R dd = akk - ajj;
             R tt;
             if (fabs(dd) > (R)1e18 * fabs(ajk)) {  // tiny angle, beyond FP32 range: t = a_jk / dd
@@ -317,7 +317,7 @@ __device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, 
           const float x = fabsf(ajk.h);
           if (x > rel * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
               fmaxf(fabsf(ajj.h), fabsf(akk.h)) > nu) {
-            atomicAdd(nrot, 1);
+            *nrot = 1;  // any rotation this sweep (the same value from every writer)
             const DFv dd = dfv_add(akk, dfv_neg(ajj));
             float tt;
             if (fabsf(dd.h) > 1e18f * x) {  // tiny angle: t = a_jk / dd
@@ -510,7 +510,7 @@ static void jacobi_sym(int m, const double* G, double* Ascr, double* Wscr, doubl
                        double* Wout, int* status, cudaStream_t st, bool fp64_finish = false) {
   if (m <= JS_REFINE_M) {
     const size_t smem = sizeof(double) * (fp64_finish ? 4 : 2) * m * (m + 1);
-    k_jacobi_sym_df<<<1, 512, smem, st>>>(m, G, lambda, Wout, 60, fp64_finish ? 1 : 0, status);
+    k_jacobi_sym_df<<<1, 1024, smem, st>>>(m, G, lambda, Wout, 60, fp64_finish ? 1 : 0, status);
     return;
   }
   const size_t smem = m <= JS_SMEM_M ? sizeof(double) * 2 * m * (m + 1) : 0;

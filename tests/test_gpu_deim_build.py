@@ -55,9 +55,11 @@ def test_deim_basis_parity(ctx, N, m, d):
     assert np.all(np.abs(cos - 1.0) < 1e-8)
 
 
-@pytest.mark.parametrize("N,d", [(20_000, 12), (5001, 30), (64, 64)])
+@pytest.mark.parametrize("N,d", [(20_000, 12), (5001, 30), (64, 64), (200_000, 24)])
 def test_deim_indices_and_weights_parity(ctx, N, d):
-    """On the oracle's basis: indices exact, weights to 1e-10."""
+    """On the oracle's basis: indices exact, weights to 1e-10.  N = 64 and
+    N = 2e5 take the multi-launch elimination (fewer rows than SMs; per-block
+    slices beyond shared memory), the others the cooperative one."""
     Y = synthetic_snapshots(N, max(d, 40) if N > 64 else 64, seed=N)
     Psi_o, _ = deim.deim_basis(Y, d)
     idx = ctx.deim_indices(T(Psi_o.T)).cpu().numpy()
