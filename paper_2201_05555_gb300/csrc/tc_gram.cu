@@ -65,20 +65,29 @@ k_gram_tc(int64_t N, int n, GramArgsLP a, int real_out, double* __restrict__ par
   // thread roles: column c = t % 64, row groups (t / 64) + {0, 4} of the tile
   const int c = t & 63;
   float qv[kGMaxBlocks][2][4];
+  // 32-bit offsets within a tile: row 4 kq + u, column c
+  const int co = 4 * (t >> 6) * n2 + c;
   auto load = [&](int64_t tile) {
     const int64_t r0 = tile * kGRows;
+    const int rows = N - r0 < (int64_t)kGRows ? (int)(N - r0) : kGRows;  // >= 1
 #pragma unroll
-    for (int b = 0; b < kGMaxBlocks; ++b)
+    for (int b = 0; b < kGMaxBlocks; ++b) {
+      if (b >= nb) {  // blocks past nb stage zeros
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kq = (t >> 6) + 4 * h;
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) qv[b][h][u] = 0.f;
+        continue;
+      }
+      const float* x = static_cast<const float*>(a.blk[b]) + r0 * n2 + co;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int64_t R = r0 + 4 * kq + u;
-          qv[b][h][u] = (b < nb && c < n2 && R < N)
-                            ? __ldg(static_cast<const float*>(a.blk[b]) + R * n2 + c) : 0.f;
+          const int r = 4 * ((t >> 6) + 4 * h) + u;
+          qv[b][h][u] = (c < n2 && r < rows) ? __ldg(x + (16 * h + u) * n2) : 0.f;
         }
-      }
+    }
   };
   if (blockIdx.x < ntiles) load(blockIdx.x);
   int it = 0;

@@ -95,26 +95,29 @@ k_project_tc(GridC g, int64_t N, int n, int p, const float* __restrict__ Q2,
   const int bc = t % PC, bkq = t / PC;
   float qa[2][4];
   uint16_t jb[4];
+  // per-thread offsets within a tile, 32-bit: Q row 4 kq + u of column m,
+  // and the cell of row 4 bkq + u, sample bc, inside the tile's index block
+  // (a 32-row tile lies in one TILE_ROWS-row block of the cell layout)
+  const int qo = 4 * (t >> 6) * n2 + m;
+  const bool q_role = m < n2, j_role = b_role && bc < pc_eff;
   auto load = [&](int64_t tile) {
     const int64_t r0 = tile * kTcRows;
+    const int rows = N - r0 < (int64_t)kTcRows ? (int)(N - r0) : kTcRows;  // >= 1
+    const float* q = Q2 + r0 * n2 + qo;
+    const int64_t tl = r0 / TILE_ROWS;
+    const uint16_t* jp =
+        jt + jt_block(tl, chunk, nch, PC) + ((int)(r0 - tl * TILE_ROWS) + 4 * bkq) * PC + bc;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int kq = (t >> 6) + 4 * h;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int64_t R = r0 + 4 * kq + u;
-        qa[h][u] = (m < n2 && R < N) ? __ldg(Q2 + R * n2 + m) : 0.f;
+        const int r = 4 * ((t >> 6) + 4 * h) + u;
+        qa[h][u] = (q_role && r < rows) ? __ldg(q + (16 * h + u) * n2) : 0.f;
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t R = r0 + 4 * bkq + u;
-      jb[u] = 0xFFFFu;
-      if (b_role && R < N && bc < pc_eff) {
-        const int64_t tl = R / TILE_ROWS;
-        jb[u] = __ldg(jt + jt_block(tl, chunk, nch, PC) + (R - tl * TILE_ROWS) * PC + bc);
-      }
-    }
+    for (int u = 0; u < 4; ++u)
+      jb[u] = (j_role && 4 * bkq + u < rows) ? __ldg(jp + u * PC) : (uint16_t)0xFFFFu;
   };
   if (blockIdx.x < ntiles) load(blockIdx.x);
   int it = 0;

@@ -224,11 +224,9 @@ __device__ __forceinline__ void rows_tc_body(const GridC& g, int64_t N, int n, i
           jj[e] = J[(((k >> pcs) << 6) + (r & 63)) * PC + (k & (PC - 1))];
         }
       }
+      const float* f = a.F2 + i0 * Nx;  // p x Nx field rows: offsets fit 32 bits
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int i = i0 + e;
-        o[e] = (R < N && i < p) ? __ldg(a.F2 + (size_t)i * Nx + jj[e]) : 0.f;
-      }
+      for (int e = 0; e < 8; ++e) o[e] = (R < N && i0 + e < p) ? __ldg(f + e * Nx + jj[e]) : 0.f;
     }
   };
   // warps 0-3: rows 32 w + lane of local tile tl from accumulator tl % 2
