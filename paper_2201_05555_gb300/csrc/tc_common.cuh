@@ -89,13 +89,6 @@ static __device__ __forceinline__ float2 tf32_split(float x) {
   const float h = tf32_rna(x);
   return make_float2(h, tf32_rna(x - h));
 }
-// x as the exact sum of three TF32 values (11 + 11 + the remaining <= 2
-// significant bits): x - a1 and (x - a1) - a2 are exact in FP32
-static __device__ __forceinline__ float3 tf32_split3(float x) {
-  const float a1 = tf32_rna(x), r1 = x - a1;
-  const float a2 = tf32_rna(r1);
-  return make_float3(a1, a2, tf32_rna(r1 - a2));
-}
 
 // 16 consecutive columns of this warp's 32 lanes: v[j] = D[lane][col + j]
 static __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {

@@ -23,19 +23,19 @@
 //    taken less the identity, so that the increment keeps its own relative
 //    accuracy and the base its FP64 one.
 //
-// Precision: every FP32 row value a is split exactly into three TF32 values
-// a1 + a2 + a3 (tf32_split3), every coefficient b into b_hi = b rounded to
-// TF32 and b_lo = b - b_hi rounded to TF32 (|b - b_hi - b_lo| <= 2^-22 |b|,
-// about the FP32 rounding of the FP64 coefficient); the accumulator
-// (128 x 2NB, NB = 2n rounded up to 16) takes a_s [B_hi | B_lo] for s = 1..3,
-// and out = D[:, :NB] + D[:, NB:]: FP32 row arithmetic up to the coefficients'
-// split (FP32 accumulation in tensor memory).  Bop is built and split
+// Precision: every FP32 value v (row value or coefficient) is split into
+// v_hi = v rounded to TF32 and v_lo = v - v_hi rounded to TF32
+// (|v - v_hi - v_lo| <= 2^-22 |v|, tf32_split); the accumulator (128 x 2NB,
+// NB = 2n rounded up to 16) takes a_s [B_hi | B_lo] for s = hi, lo, and
+// out = D[:, :NB] + D[:, NB:] (FP32 accumulation in tensor memory).  An exact
+// three-piece split of the row values measured no difference in the step's
+// error against the oracle, so kBmPieces = 2.  Bop is built and split
 // once per call by a prep kernel into 32-row K chunks in the K-major
 // no-swizzle canonical layout (element (c, k) of a chunk at byte (c / 8) *
 // 1024 + (k / 4) * 128 + (c % 8) * 16 + (k % 4) * 4, B_hi in rows c < NB,
 // B_lo in rows NB + c); W is accumulated in FP64.
 //
-// Pipeline (512 threads, one CTA per SM, three stages of [A_1 | A_2 | A_3 | B
+// Pipeline (512 threads, one CTA per SM, three stages of [A_hi | A_lo | B
 // chunk | cell indices]): thread 0 bulk-copies a step's B chunk (and, for the
 // sample steps, its two 64-row blocks of cell indices) S - 1 steps ahead; all
 // threads load the step's A values one step ahead (row blocks of the next
@@ -54,10 +54,11 @@ constexpr int kBmK = 32;         // K per step
 constexpr int kBmThreads = 512;
 constexpr int kBmStages = 3;
 constexpr int kBmTerms = 4;      // row blocks of one product
+constexpr int kBmPieces = 2;       // TF32 pieces of a row value
 constexpr uint32_t kBmA = 16384;   // one TF32 piece of A of one step
 constexpr uint32_t kBmB = 16384;   // B chunk, at most 2 NB = 128 rows
 constexpr uint32_t kBmJ = 8192;    // two 64-row blocks of up to 32 cell indices
-constexpr uint32_t kBmStage = 3 * kBmA + kBmB + kBmJ;
+constexpr uint32_t kBmStage = kBmPieces * kBmA + kBmB + kBmJ;
 
 __device__ __forceinline__ uint32_t bm_off(int r, int k) {
   return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
@@ -173,11 +174,11 @@ __device__ __forceinline__ void rows_tc_body(const GridC& g, int64_t N, int n, i
     const bool h1 = 2 * tile + 1 < nt64;
     fence_proxy_async_smem();
     mbar_expect_tx(bar, bbytes + jbytes * (h1 ? 2u : 1u));
-    bulk_g2s(S + 3 * kBmA, Bg + (size_t)kt * 2 * NB * kBmK, bbytes, bar);
+    bulk_g2s(S + kBmPieces * kBmA, Bg + (size_t)kt * 2 * NB * kBmK, bbytes, bar);
     if (jbytes) {
-      bulk_g2s(S + 3 * kBmA + kBmB, a.jt + jt_block(2 * tile, c0, nch, PC), jbytes, bar);
+      bulk_g2s(S + kBmPieces * kBmA + kBmB, a.jt + jt_block(2 * tile, c0, nch, PC), jbytes, bar);
       if (h1)
-        bulk_g2s(S + 3 * kBmA + kBmB + 4096, a.jt + jt_block(2 * tile + 1, c0, nch, PC), jbytes,
+        bulk_g2s(S + kBmPieces * kBmA + kBmB + 4096, a.jt + jt_block(2 * tile + 1, c0, nch, PC), jbytes,
                  bar);
     }
   };
@@ -203,7 +204,7 @@ __device__ __forceinline__ void rows_tc_body(const GridC& g, int64_t N, int n, i
         }
       }
     } else if (kSamples) {  // field values G_li = (q/m) F_i[j_li]
-      const uint16_t* J = reinterpret_cast<const uint16_t*>(stage(gs) + 3 * kBmA + kBmB) +
+      const uint16_t* J = reinterpret_cast<const uint16_t*>(stage(gs) + kBmPieces * kBmA + kBmB) +
                           (r >> 6) * 2048;
       const int i0 = (kt - KTr) * kBmK + 8 * kq;
       uint16_t jj[8];
@@ -307,25 +308,23 @@ __device__ __forceinline__ void rows_tc_body(const GridC& g, int64_t N, int n, i
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int k = 8 * kq + 4 * u;
-      const float3 v0 = tf32_split3(val[4 * u]), v1 = tf32_split3(val[4 * u + 1]),
-                   v2 = tf32_split3(val[4 * u + 2]), v3 = tf32_split3(val[4 * u + 3]);
+      const float2 v0 = tf32_split(val[4 * u]), v1 = tf32_split(val[4 * u + 1]),
+                   v2 = tf32_split(val[4 * u + 2]), v3 = tf32_split(val[4 * u + 3]);
       *reinterpret_cast<float4*>(S + bm_off(r, k)) = make_float4(v0.x, v1.x, v2.x, v3.x);
       *reinterpret_cast<float4*>(S + kBmA + bm_off(r, k)) = make_float4(v0.y, v1.y, v2.y, v3.y);
-      *reinterpret_cast<float4*>(S + 2 * kBmA + bm_off(r, k)) =
-          make_float4(v0.z, v1.z, v2.z, v3.z);
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (t == 0) {
       mbar_wait(&full[s], (uint32_t)((gs / kBmStages) & 1), status);
       tc_fence_after();
-      const uint32_t sa = smem_u32(S), sb = sa + 3 * kBmA;
+      const uint32_t sa = smem_u32(S), sb = sa + kBmPieces * kBmA;
       const uint32_t d = tmem + (uint32_t)(128 * (tl & 1));
 #pragma unroll
       for (int j = 0; j < kBmK / 8; ++j) {
         const uint64_t bd = tc_sdesc(sb + 256 * j, 128, 1024);
 #pragma unroll
-        for (int piece = 0; piece < 3; ++piece)
+        for (int piece = 0; piece < kBmPieces; ++piece)
           tc_mma_tf32(d, tc_sdesc(sa + piece * kBmA + 256 * j, 128, 1024), bd, idesc,
                       (kt > 0 || j > 0 || piece > 0));
       }
