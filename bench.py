@@ -90,8 +90,11 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
     ap.add_argument("--sharded", action="store_true",
-                    help="with N > 1 ranks: one particle-sharded problem of N x 1e6 particles per "
-                         "sample (vp_ctx_set_comm over NCCL) instead of N replicas")
+                    help="the particle-sharded form even on one rank (a one-rank NCCL group); "
+                         "with N > 1 ranks it is the default")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 ranks: N independent replicas of the headline instead of "
+                         "one particle-sharded problem")
     ap.add_argument("--no-tc", action="store_true",
                     help="FP32 SIMT kernels only (no tensor-core kernels)")
     ap.add_argument("--head-n", type=int, default=HEAD["N"],
@@ -968,21 +971,27 @@ def ours(args, rank, world):
     if world > 1 or args.sharded:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    # N > 1 ranks: one particle-sharded problem (N x 1e6 particles per sample,
+    # sums over the ranks by NCCL all-reduce) unless --replicas
     dev = torch.device("cuda", local)
     ctx = Context(local)
     if args.no_tc:
         ctx.tensor_cores(False)
     N, p, dt = HEAD["N"], HEAD["p"], HEAD["dt"]
 
-    sharded = args.sharded and dist is not None
+    sharded = dist is not None and (args.sharded or not args.replicas)
     if sharded:
         Q, Z, n, grid = head_setup_sharded(ctx, torch, dev, rank, world, dist)
     else:
         Q, Z, n, grid = head_setup(ctx, torch, dev, rank)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # launch shapes of the particle kernels chosen on this state (setup, not timed)
-    tuned = None if sharded else ctx.autotune(grid, Q, Z, arith=2, reps=3)
+    # launch shapes of the particle kernels chosen on this state (setup, not
+    # timed; sharded: on the rank's own rows, before the sums are attached)
+    if sharded:
+        from paper_2201_05555_gb300 import make_grid
+        grid_local = make_grid(HEAD["N"], HEAD["Nx"], W.BUMP_ON_TAIL.L)
+    tuned = ctx.autotune(grid_local if sharded else grid, Q, Z, arith=2, reps=3)
     if sharded:  # sums over the ranks' particles through NCCL
         from paper_2201_05555_gb300.binding import RankComm
         RankComm(lambda t: dist.all_reduce(t), HEAD["N"] * world).attach(ctx)
