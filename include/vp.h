@@ -354,6 +354,23 @@ vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const d
                            const double* V_dev, double* eps_dev, void* stream);
 vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                             const double* Q_dev, const double* Z_dev, double* out_dev, void* stream);
+/* Re-initialisation at a larger rank (Sec. 6.4, two-stream instability in the
+ * nonlinear regime: the reduced model restarts from the complex SVD of the
+ * full-order solutions of all samples at the restart time, with a larger
+ * basis).  The trigger is a reading: the rank indicator of the current state
+ * (Q_dev N x 2n, Z_dev 2n x p, as vp_rank_indicator) above `threshold`
+ * (threshold < 0 always restarts, +inf never does, a NaN indicator restarts).
+ * On a restart, Q_new_dev (N x 2 n_new) and Z_new_dev (2 n_new x p) receive
+ * the start of vp_init_csvd from the full-order states X_dev, V_dev (p x N,
+ * ld N, unwrapped positions), 1 <= n_new <= min(p, N, 40); otherwise they are
+ * not written.  *indicator (host, nullable) receives the indicator,
+ * *restarted (host) 1 or 0.  Synchronises `stream` once: the decision is
+ * taken on the host.  The caller owns every buffer; a NaN threshold, a null
+ * pointer or an n_new out of range is VP_EINVAL. */
+vp_status vp_restart_csvd(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          const double* Q_dev, const double* Z_dev, const double* X_dev,
+                          const double* V_dev, double threshold, int32_t n_new, double* Q_new_dev,
+                          double* Z_new_dev, double* indicator, int32_t* restarted, void* stream);
 vp_status vp_half_basis(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
                         const double* Q0_dev, const double* Z0_dev, double dt, double* Qh_dev,
                         void* stream);

@@ -98,6 +98,8 @@ _SIGS = [
     ("vp_rel_errors", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     ("vp_target_errors", _I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P]),
     ("vp_rank_indicator", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P]),
+    ("vp_restart_csvd", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P, _D, _I32,
+                                _P, _P, C.POINTER(_D), C.POINTER(_I32), _P]),
     ("vp_half_basis", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _D, _P, _P]),
     ("vp_hamiltonian_error_terms", _I32, [_P, C.POINTER(Grid), _I64, _I32, _I32, _P, _P, _P, _P,
                                           _P, _P, _P]),
@@ -601,6 +603,26 @@ class Context:
                                                _ptr(Q, name="Q"), _ptr(Z, name="Z"), _ptr(out),
                                                self._stream()), "rank_indicator")
         return out
+
+    def restart_csvd(self, grid: Grid, Q: torch.Tensor, Z: torch.Tensor, X: torch.Tensor,
+                     V: torch.Tensor, threshold: float, n_new: int):
+        """(restarted, indicator, Q_new, Z_new): the start of rank n_new from the
+        full-order states X, V (p x N) when the rank indicator of (Q, Z) exceeds
+        `threshold` (Sec. 6.4); Q_new, Z_new are None without a restart."""
+        N, n2 = Q.shape
+        p = Z.shape[1]
+        Qn = self._empty(N, 2 * n_new)
+        Zn = self._empty(2 * n_new, p)
+        ind, flag = _D(0.0), _I32(0)
+        self._check(self.lib.vp_restart_csvd(self.h, C.byref(grid), N, n2 // 2, p,
+                                             _ptr(Q, name="Q"), _ptr(Z, name="Z"),
+                                             _ptr(X, name="X"), _ptr(V, name="V"),
+                                             float(threshold), n_new, _ptr(Qn), _ptr(Zn),
+                                             C.byref(ind), C.byref(flag), self._stream()),
+                    "restart_csvd")
+        if flag.value:
+            return True, ind.value, Qn, Zn
+        return False, ind.value, None, None
 
     def half_basis(self, grid: Grid, Q0: torch.Tensor, Z0: torch.Tensor, dt: float):
         N, n2 = Q0.shape

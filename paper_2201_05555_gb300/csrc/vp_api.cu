@@ -1790,10 +1790,9 @@ vp_status vp_target_errors(vp_ctx* ctx, int64_t N, int32_t p, int32_t n, const d
   return VP_OK;
 }
 
-vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
-                            const double* Q, const double* Z, double* out, void* stream) {
-  VP_ENTER();
-  VP_NO_COMM();
+static vp_status rank_indicator_impl(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n,
+                                     int32_t p, const double* Q, const double* Z, double* out,
+                                     cudaStream_t st) {
   VP_TRY(check_grid(ctx, grid));
   VP_TRY(check_np(ctx, N, p));
   VP_TRY(check_n(ctx, n, N));
@@ -1815,6 +1814,44 @@ vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t
   VP_K(VP_K_REDUCE, reduce_partials(nb, 2, w.part, w.aux, nullptr, st));
   VP_K(VP_K_REDUCE, ratio_sqrt(1, w.aux, out, st));
   VP_LAUNCHED();
+  return VP_OK;
+}
+
+vp_status vp_rank_indicator(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                            const double* Q, const double* Z, double* out, void* stream) {
+  VP_ENTER();
+  VP_NO_COMM();
+  return rank_indicator_impl(ctx, grid, N, n, p, Q, Z, out, st);
+}
+
+// Re-initialisation at a larger rank (Sec. 6.4): the indicator of the current
+// reduced state decides on the host; the new start is the truncated complex
+// SVD of the full-order states, as at t = 0.
+vp_status vp_restart_csvd(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n, int32_t p,
+                          const double* Q, const double* Z, const double* X, const double* V,
+                          double threshold, int32_t n_new, double* Q_new, double* Z_new,
+                          double* indicator, int32_t* restarted, void* stream) {
+  VP_ENTER();
+  VP_NO_COMM();
+  if (!restarted || !X || !V || !Q_new || !Z_new) return vp_fail(ctx, VP_EINVAL, "null pointer");
+  if (threshold != threshold) return vp_fail(ctx, VP_EINVAL, "threshold is NaN");
+  *restarted = 0;
+  double* d_ind = nullptr;
+  VP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_ind), sizeof(double), st));
+  vp_status s = rank_indicator_impl(ctx, grid, N, n, p, Q, Z, d_ind, st);
+  double ind = 0.0;
+  if (s == VP_OK) {
+    cudaError_t e = cudaMemcpyAsync(&ind, d_ind, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = vp_cuda_check(ctx, e, "indicator read");
+  }
+  cudaFreeAsync(d_ind, st);
+  VP_TRY(s);
+  if (indicator) *indicator = ind;
+  if (!(ind <= threshold)) {  // a NaN indicator (a broken state) restarts as well
+    VP_TRY(init_csvd_impl(ctx, N, p, 1, n_new, -1.0, X, V, Q_new, Z_new, nullptr, nullptr, st));
+    *restarted = 1;
+  }
   return VP_OK;
 }
 
