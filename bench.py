@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=SERVE["slots"])
     ap.add_argument("--serve-arith", type=int, default=SERVE["arith"])
     ap.add_argument("--batch-size", type=int, default=512)
-    ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e5))
+    ap.add_argument("--batch-n", type=float, nargs=2, default=(1e4, 1e6))
     ap.add_argument("--batch-steps", type=int, default=4)
     ap.add_argument("--batch-rounds", type=int, default=8)
     ap.add_argument("--sharded", action="store_true",
@@ -100,7 +100,7 @@ def parse():
     ap.add_argument("--head-n", type=int, default=HEAD["N"],
                     help="particles per sample of the headline workload in --only head")
     ap.add_argument("--only", choices=["head", "hyper", "dmd", "deim_build", "subsampled", "forms",
-                                       "served_c5"],
+                                       "served_c5", "batched"],
                     default=None,
                     help="run one extra measurement alone and print its JSON (profiling runs)")
     return ap.parse_args()
@@ -702,7 +702,8 @@ def only(args):
           "deim_build": lambda: deim_build_measure(ctx, torch, dev),
           "subsampled": lambda: subsample_measure(ctx, torch, dev, flush),
           "forms": lambda: head_forms_measure(ctx, torch, dev, flush),
-          "served_c5": lambda: served_c5_measure(args, 0)}[args.only]
+          "served_c5": lambda: served_c5_measure(args, 0),
+          "batched": lambda: batched_measure(args, ctx, torch, dev, flush)}[args.only]
     print(json.dumps({args.only: fn()}))
     return 0
 
@@ -1115,7 +1116,11 @@ def ours(args, rank, world):
         if c2_cpu:
             line["two_stream_cpu_baseline"] = c2_cpu
         line["full_order"] = full_order_measure(ctx, torch, dev, flush)
-        line["batched"] = batched_measure(args, ctx, torch, dev, flush)
+        try:
+            line["batched"] = batched_measure(args, ctx, torch, dev, flush)
+        except RuntimeError as e:  # VPError (e.g. VP_ENOMEM) or a torch allocation
+            line["batched"] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
         line["subsampled"] = subsample_measure(ctx, torch, dev, flush)
         line["hyper"] = hyper_measure(ctx, torch, dev, flush)
         line["deim_build"] = deim_build_measure(ctx, torch, dev)

@@ -149,8 +149,11 @@ static size_t sub_ws_bytes(int64_t N, int n, int nsub, int Nx) {
          2 * arena_bytes(zn, 8) + arena_bytes(pn, 8) + arena_bytes(jcell_count(N, nsub, Nx), 2);
 }
 
+// f32rows: the FP32 form (arith 2) keeps its row blocks (Q2a, frows) as FP32,
+// half the double-float size; the double-float shadow Q2b of its energy
+// check and re-orthonormalisation keeps the full size.
 size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df, int* gx_proj,
-                    int* gx_gram, const int* tune = nullptr, int nsub = 0) {
+                    int* gx_gram, const int* tune = nullptr, int nsub = 0, bool f32rows = false) {
   const int n2 = 2 * n, nn = n * n;
   const int chunks = project_chunks(p, Nx > 0 ? Nx : 3);
   // the FP32-based path sizes its grids by the context's launch-shape knobs
@@ -168,18 +171,20 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
          arena_bytes((size_t)n2 * n2, 8) + arena_bytes((size_t)(n2 + 5) * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
          arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
-         (df ? 7 * arena_bytes((size_t)N * n2, 8) + arena_bytes(jcell_count(N, p, Nx), 2) +
+         (df ? arena_bytes((size_t)N * n2, 8) + 6 * arena_bytes((size_t)N * n2, f32rows ? 4 : 8) +
+                   arena_bytes(jcell_count(N, p, Nx), 2) +
                    2 * arena_bytes((size_t)n2 * p, 8) + arena_bytes(pn, 8) +
                    arena_bytes(rows_tc_bop_floats(n, p), 4) + sub_ws_bytes(N, n, nsub, Nx)
              : 0);
 }
 
 vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS& w,
-                 bool df = false, int nsub = 0) {
+                 bool df = false, int nsub = 0, bool f32rows = false) {
   const int n2 = 2 * n, nn = n * n;
   size_t pn = (size_t)p * (Nx > 0 ? Nx : 1);
+  f32rows = f32rows && df;
   size_t bytes = red_ws_bytes(ctx->num_sms, N, n, p, Nx, nrows, df, &w.gx_proj, &w.gx_gram,
-                              ctx->tune, df ? nsub : 0);
+                              ctx->tune, df ? nsub : 0, f32rows);
   size_t part_d = std::max<size_t>((size_t)w.gx_proj * n2 * p,
                                    std::max<size_t>((size_t)w.gx_gram * 12 * nn * 2,
                                                     (size_t)w.gx_gram * n2 * n2));
@@ -204,10 +209,17 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.tmp = a.take<double2>(10 * nn);
   w.flags = a.take<int>(8);
   for (int r = 0; r < 5; ++r) w.rows[r] = r < nrows ? a.take<double>((size_t)N * n2) : nullptr;
-  w.Q2a = df ? a.take<float2>((size_t)N * n2) : nullptr;
+  // the row blocks of the df / FP32 step: float2 (double-float) elements, or
+  // float with f32rows, N x 2n each
+  auto rowblk = [&]() -> float2* {
+    if (!df) return nullptr;
+    if (f32rows) return reinterpret_cast<float2*>(a.take<float>((size_t)N * n2));
+    return a.take<float2>((size_t)N * n2);
+  };
+  w.Q2a = rowblk();
+  for (int r = 0; r < 5; ++r) w.frows[r] = rowblk();
   w.Q2b = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.jcell = df ? a.take<uint16_t>(jcell_count(N, p, Nx)) : nullptr;
-  for (int r = 0; r < 5; ++r) w.frows[r] = df ? a.take<float2>((size_t)N * n2) : nullptr;
   w.Z2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.Zh2 = df ? a.take<float2>((size_t)n2 * p) : nullptr;
   w.F2 = df ? a.take<float2>(pn) : nullptr;
@@ -303,7 +315,8 @@ struct Red {
 };
 
 vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, int nrows,
-                    cudaStream_t st, Red& R, bool df = false, int nsub = 0) {
+                    cudaStream_t st, Red& R, bool df = false, int nsub = 0,
+                    bool f32rows = false) {
   R.ctx = ctx;
   R.df = df;
   R.N = N;
@@ -312,7 +325,7 @@ vp_status red_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, i
   R.st = st;
   // fixed-point scales bound the sums over all ranks' particles
   if (grid) R.g = make_gridc(*grid, ctx->comm_on ? ctx->comm.n_global : N);
-  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df, nsub));
+  VP_TRY(red_ws(ctx, N, n, p, grid ? grid->Nx : 0, nrows, R.w, df, nsub, f32rows));
   if (grid) VP_CUDA(cudaMemsetAsync(R.w.counts, 0, sizeof(unsigned long long) * p * grid->Nx, st));
   if (grid && R.w.sub.nsub)
     VP_CUDA(cudaMemsetAsync(R.w.sub.counts, 0, sizeof(unsigned long long) * nsub * grid->Nx, st));
@@ -1214,7 +1227,7 @@ vp_status step_setup(vp_ctx* ctx, const vp_grid* grid, int64_t N, int n, int p, 
     delete is;
     return vp_fail(ctx, VP_EINVAL, "subsample outside [n, p] or no indices");
   }
-  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, is->R, true, opts->nsub);
+  vp_status s = red_setup(ctx, grid, N, n, p, 0, st, is->R, true, opts->nsub, opts->arith == 2);
   if (s != VP_OK) {
     delete is;
     return s;
@@ -1335,7 +1348,8 @@ size_t init_ws_bytes(int sms, int64_t N, int p, int n, int* gx_out) {
 size_t vp_query_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int arith) {
   const bool df = arith != 0;
   return std::max(init_ws_bytes(sms, N, p, n, nullptr),
-                  red_ws_bytes(sms, N, n, p, Nx, df ? 0 : 5, df, nullptr, nullptr));
+                  red_ws_bytes(sms, N, n, p, Nx, df ? 0 : 5, df, nullptr, nullptr, nullptr, 0,
+                               arith == 2));
 }
 
 // Free a context's workspace arena (synchronises the device).
@@ -2070,7 +2084,7 @@ vp_status vp_basis_update(vp_ctx* ctx, const vp_grid* grid, int64_t N, int32_t n
   ctx->comm_failed = false;
   const bool df = o.arith != 0;
   Red R;
-  VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df, o.nsub));
+  VP_TRY(red_setup(ctx, grid, N, n, p, df ? 0 : 5, st, R, df, o.nsub, o.arith == 2));
   if (df) {
     VP_TRY(basis_update_df(ctx, R, Q, Z, dt, nsteps, o, trace, iters, kstate, st));
     if (ctx->comm_failed) return vp_fail(ctx, VP_ECOMM, "a sum over the ranks failed");

@@ -109,11 +109,13 @@ def server():
     s.close()
 
 
-def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps, loading=0, seed=0):
+def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps, loading=0, seed=0,
+                 fp32_start=False):
     """The served pipeline on the oracle: quiet start, complex SVD start with
     n = the smallest k <= n_max whose relative tail energy is below rank_tol,
     then warm-started PRK2 steps; returns n, the (E, H) trace of the states
-    entering each step and the final Z."""
+    entering each step and the final Z.  fp32_start rounds the start's Z to
+    FP32 (the oracle's sensitivity to that rounding)."""
     fam = FAM[family]
     if loading == 0:
         X0, V0 = W.load_batch(fam, recs, N, quiet=True)
@@ -127,6 +129,8 @@ def oracle_query(family, rows, recs, N, Nx, n_max, rank_tol, dt, nsteps, loading
         n -= 1
     if n < n_max:
         U, Z, sig = csvd.csvd_init(X0, V0, n)
+    if fp32_start:
+        Z = Z.astype(np.float32).astype(np.float64)
     g = pic.make_grid(N, Nx, fam.L)
     E0, H0 = reduced.energies(U, Z, g)
     U, Z, tr, _ = reduced.run(U, Z, dt, nsteps, g, warm_start=True)
@@ -150,6 +154,36 @@ def test_serve_matches_oracle(server, family, loading):
     assert rel(tr, tr_o) < 1e-9
     # Z is fixed up to an ortho-symplectic change of basis: compare Z^T Z
     assert rel(zeta.T @ zeta, Z_o.T @ Z_o) < 1e-9
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_serve_precision_form_matches_oracle(server, family):
+    """A served query in the FP32 form (arith 2) against the FP64 oracle, quiet
+    start: per-step H of the states entering each step within the precision
+    gate of 1e-6.  E (relative to the sample's largest E) is held to the gate
+    or to twice the oracle's own deviation when its start is rounded to FP32,
+    whichever is larger: with a quiet start the field energy is that of a
+    small perturbation, and FP32 rounding of the state alone moves it by
+    ~2e-4 on two-stream and ~6e-6 on bump-on-tail at these sizes."""
+    N, p, Nx, n_max, tol_rank, dt, nsteps = 20_000, 16, 128, 4, 1e-7, 0.05, 5
+    rows, recs = eta_rows(family, p)
+    t = server.submit(family, rows, N, Nx, n_max, dt, nsteps, arith=2, rank_tol=tol_rank)
+    r, tr, zeta = server.wait(t)
+    assert r.status == 0 and r.steps_done == nsteps
+    n, tr_o, Z_o = oracle_query(family, rows, recs, N, Nx, n_max, tol_rank, dt, nsteps)
+    _, tr_p, _ = oracle_query(family, rows, recs, N, Nx, n_max, tol_rank, dt, nsteps,
+                              fp32_start=True)
+    assert r.n == n
+
+    def dev(a):
+        return (np.abs(a[:, :, 1] - tr_o[:, :, 1]) / np.abs(tr_o[:, :, 1]),
+                np.abs(a[:, :, 0] - tr_o[:, :, 0]) / np.abs(tr_o[:, :, 0]).max(axis=0))
+    eH, eE = dev(tr)
+    sH, sE = dev(tr_p)
+    print("served FP32 form", family, float(eH.max()), float(eE.max()), "oracle sensitivity",
+          float(sH.max()), float(sE.max()))
+    assert eH.max() <= 1e-6
+    assert eE.max() <= max(1e-6, 2.0 * sE.max())
 
 
 def test_serve_alone_equals_mix(server):
