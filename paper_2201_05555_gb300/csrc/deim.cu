@@ -280,96 +280,286 @@ __device__ __forceinline__ DFv dfv_rot(DFv c, DFv a, DFv s, DFv b) {
   return dfv_add(dfv_mul(c, a), dfv_neg(dfv_mul(s, b)));
 }
 
-// Round-robin cyclic Jacobi sweeps as jacobi_sweeps, in double-float: a pair
-// (j, k) rotates unless |a_jk| <= rel sqrt|a_jj a_kk| or both diagonal
-// entries are below 1e-14 of the largest.  rel must stay well above the
-// double-float rounding of ~4e-15 per operation, which the entries
-// accumulate over the sweeps: at 1e-14 pairs near that level went on
-// rotating until the sweep cap.  The tangent of the angle is taken in FP32 from the leading parts
-// (as in the FP64 sweeps); c = (1 + t^2)^-1/2 by an FP32 reciprocal square
-// root and one Newton step in double-float, s = t c, so the rotation is
-// orthogonal to double-float rounding.  Returns after a sweep without
-// rotations (true) or after max_sweeps (false).
-__device__ bool jacobi_sweeps_df(int m, int ld, DFv* A, DFv* W, int max_sweeps, float rel, DFv* rc,
-                                 DFv* rs, int* pj, int* pk, int* nrot, float* nu_s) {
+// ------------------------ cyclic Jacobi with one block barrier per round
+// The sweeps of the double-float kernel and of its FP64 finish (m <= 64).
+// The same rotations as jacobi_sweeps (round-robin pairs, the same
+// thresholds, the column update of a round before its row update), laid out
+// so that a round needs one barrier instead of three:
+// - A is double-buffered: a thread owns a 2 x 2 block (the rows of pair q1,
+//   the columns of pair q2), reads it from the current copy, applies the
+//   column rotation of q2 and then the row rotation of q1, and writes the
+//   other copy; W's columns are rotated in place (each entry by one task);
+// - the rotations of the next round are computed in the same phase by the
+//   first warp, from the three entries of each next pair that this round
+//   produces, evaluated by the same operations as the block update.
+// At the start of a sweep the null-space threshold is taken from the
+// diagonal and the first round's rotations from A itself (two more
+// barriers).  Element operations of a rotation: c a - s b and s a + c b.
+__device__ __forceinline__ double jrot(double c, double a, double s, double b) {
+  return fma(c, a, -(s * b));
+}
+__device__ __forceinline__ double jrotp(double s, double a, double c, double b) {
+  return fma(s, a, c * b);
+}
+__device__ __forceinline__ DFv jrot(DFv c, DFv a, DFv s, DFv b) { return dfv_rot(c, a, s, b); }
+__device__ __forceinline__ DFv jrotp(DFv s, DFv a, DFv c, DFv b) {
+  return dfv_rot(s, a, dfv_neg(c), b);
+}
+__device__ __forceinline__ bool jmoving(double s) { return s != 0.0; }
+__device__ __forceinline__ bool jmoving(DFv s) { return s.h != 0.f; }
+__device__ __forceinline__ void jident(double& c, double& sn) {
+  c = 1.0;
+  sn = 0.0;
+}
+__device__ __forceinline__ void jident(DFv& c, DFv& sn) {
+  c = dfv(1.f, 0.f);
+  sn = dfv(0.f, 0.f);
+}
+__device__ __forceinline__ double jlead(double a) { return a; }
+__device__ __forceinline__ double jlead(DFv a) { return (double)a.h; }
+
+// The rotation (c, s) of a pair from a_jj, a_kk, a_jk, or false (c = 1,
+// s = 0) below the thresholds of jacobi_sweeps: |a_jk| <= rel sqrt|a_jj a_kk|,
+// |a_jk| <= fl, or both diagonal entries at most nu.  FP64: an FP32 tangent,
+// c = (1 + t^2)^-1/2 in FP64.
+__device__ bool jparams(double ajj, double akk, double ajk, double rel, double fl, double nu,
+                        double& c, double& sn) {
+  c = 1.0;
+  sn = 0.0;
+  if (!(fabs(ajk) > rel * sqrt(fabs(ajj * akk)) && fabs(ajk) > fl && (float)fabs(ajk) > 0.0f &&
+        fmax(fabs(ajj), fabs(akk)) > nu))
+    return false;
+  const double dd = akk - ajj;
+  double tt;
+  if (fabs(dd) > 1e18 * fabs(ajk)) {  // tiny angle, beyond FP32 range: t = a_jk / dd
+    tt = ajk / dd;
+  } else {
+    const float tau = (float)dd / (2.0f * (float)ajk);
+    tt = (double)((tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f))));
+  }
+  c = rsqrt(fma(tt, tt, 1.0));
+  sn = tt * c;
+  return true;
+}
+// Double-float: the thresholds on the leading parts (rel must stay well above
+// the double-float rounding of ~4e-15 per operation, which the entries
+// accumulate over the sweeps); the tangent in FP32 from the leading parts,
+// c = (1 + t^2)^-1/2 by an FP32 reciprocal square root and one Newton step
+// in double-float, s = t c, so that the rotation is orthogonal to
+// double-float rounding.
+__device__ bool jparams(DFv ajj, DFv akk, DFv ajk, double rel_d, double fl, double nu_d, DFv& c,
+                        DFv& sn) {
+  (void)fl;
+  const float rel = (float)rel_d, nu = (float)nu_d;
+  c = dfv(1.f, 0.f);
+  sn = dfv(0.f, 0.f);
+  const float x = fabsf(ajk.h);
+  if (!(x > rel * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
+        fmaxf(fabsf(ajj.h), fabsf(akk.h)) > nu))
+    return false;
+  const DFv dd = dfv_add(akk, dfv_neg(ajj));
+  float tt;
+  if (fabsf(dd.h) > 1e18f * x) {  // tiny angle: t = a_jk / dd
+    tt = ajk.h / dd.h;
+  } else {
+    const float tau = dd.h / (2.0f * ajk.h);
+    tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  }
+  // u = 1 + t^2 exactly as a double-float (t^2 by an FMA), y ~ u^-1/2
+  const float t2 = tt * tt;
+  const DFv u = fast_two_sum(1.0f, t2);
+  const DFv uu = dfv_add(u, dfv(fmaf(tt, tt, -t2), 0.f));
+  const float y0 = rsqrtf(uu.h);
+  // y = y0 + y0 (1 - u y0^2) / 2
+  const DFv y0sq = dfv_mul(dfv(y0, 0.f), dfv(y0, 0.f));
+  const DFv r = dfv_add(dfv(1.f, 0.f), dfv_neg(dfv_mul(uu, y0sq)));
+  c = dfv_add(dfv(y0, 0.f), dfv_mul(dfv(0.5f * y0, 0.f), r));
+  sn = dfv_mul(dfv(tt, 0.f), c);
+  return true;
+}
+
+// Pair q of round r of the round-robin schedule over `slots` (even) indices:
+// slot 0 stays, the others turn; j < k (k == m is the padding of odd m).
+__device__ __forceinline__ void rr_pair(int slots, int r, int q, int& j, int& k) {
+  const int a = q, b = slots - 1 - q;
+  const int ia = (a == 0) ? 0 : 1 + (a - 1 + r) % (slots - 1);
+  const int ib = (b == 0) ? 0 : 1 + (b - 1 + r) % (slots - 1);
+  j = min(ia, ib);
+  k = max(ia, ib);
+}
+// The entry (x, y) of A after a round, by the operations of the block
+// update: the column pass of y's pair (moving my, rotation cy, sy) on rows x
+// and, if x's pair moves, its partner; then the row pass of x's pair.
+template <class T>
+__device__ __forceinline__ T jnew(const T* A, int ld, int x, int xp, bool xk, bool mx, T cx, T sx,
+                                  int y, int yp, bool yk, bool my, T cy, T sy) {
+  auto col = [&](int i) -> T {
+    if (!my) return A[i * ld + y];
+    const T aj = A[i * ld + (yk ? yp : y)], ak = A[i * ld + (yk ? y : yp)];
+    return yk ? jrotp(sy, aj, cy, ak) : jrot(cy, aj, sy, ak);
+  };
+  const T tx = col(x);
+  if (!mx) return tx;
+  const T tp = col(xp);
+  const T tj = xk ? tp : tx, tk = xk ? tx : tp;
+  return xk ? jrotp(sx, tj, cx, tk) : jrot(cx, tj, sx, tk);
+}
+
+// The schedule of every round (the same in each sweep), in shared memory:
+// pair q of round r is (pj, pk)[r * 32 + q]; index x of round r belongs to
+// pair pq[r * 64 + x] >> 1, as its larger index when the low bit is set.
+// Task tables: block e = (q1, q2) and W task e = (q, row), one byte each.
+struct JacTabs {
+  uint8_t pj[63 * 32], pk[63 * 32], pq[63 * 64];
+  uint16_t blk[32 * 32], wt[64 * 32];
+};
+__device__ void jacobi_tabs(int m, JacTabs* tb) {
+  const int slots = (m + 1) & ~1, npair = slots / 2, R = slots - 1;
+  for (int e = threadIdx.x; e < R * npair; e += blockDim.x) {
+    const int r = e / npair, q = e - r * npair;
+    int j, k;
+    rr_pair(slots, r, q, j, k);
+    tb->pj[r * 32 + q] = (uint8_t)j;
+    tb->pk[r * 32 + q] = (uint8_t)k;
+    tb->pq[r * 64 + j] = (uint8_t)(2 * q);
+    if (k < m) tb->pq[r * 64 + k] = (uint8_t)(2 * q + 1);
+  }
+  for (int e = threadIdx.x; e < npair * npair; e += blockDim.x)
+    tb->blk[e] = (uint16_t)(((e / npair) << 8) | (e % npair));
+  for (int e = threadIdx.x; e < m * npair; e += blockDim.x)
+    tb->wt[e] = (uint16_t)(((e / m) << 8) | (e % m));
+}
+
+// Sweeps as jacobi_sweeps for m <= 64 with blockDim.x >= 64: A (rows ld
+// apart) and its second copy A2, W, all in shared memory; tb from
+// jacobi_tabs; rc, rs hold 2 x 32 rotations, flag 2 ints, thr 2 doubles
+// (shared).  On return A points to the copy that holds the result.  Returns
+// after a sweep without rotations (true) or after max_sweeps (false).
+template <class T>
+__device__ bool jacobi_sweeps_1b(int m, int ld, T*& A, T* A2, T* W, int max_sweeps, double rel,
+                                 double floor_rel, double null_rel, const JacTabs* tb, T* rc, T* rs,
+                                 int* flag, double* thr) {
   const int t = threadIdx.x, nt = blockDim.x;
-  const int slots = (m + 1) & ~1, npair = slots / 2;
+  const int slots = (m + 1) & ~1, npair = slots / 2, R = slots - 1;
+  const int nblk = npair * npair, ntask = nblk + m * npair;
+  T* Ac = A;
+  T* An = A2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    const int fs = sweep & 1;
     if (t == 0) {
-      *nrot = 0;
-      float dm = 0.f;
-      for (int j = 0; j < m; ++j) dm = fmaxf(dm, fabsf(A[j * ld + j].h));
-      *nu_s = 1e-14f * dm;
+      double dm = 0.0;
+      for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(jlead(Ac[j * ld + j])));
+      thr[0] = null_rel * dm;
+      thr[1] = floor_rel * dm;
+      flag[fs] = 0;
     }
     __syncthreads();
-    const float nu = *nu_s;
-    for (int round = 0; round < slots - 1; ++round) {
-      for (int q = t; q < npair; q += nt) {
-        const int a = q, b = slots - 1 - q;
-        const int ia = (a == 0) ? 0 : 1 + (a - 1 + round) % (slots - 1);
-        const int ib = (b == 0) ? 0 : 1 + (b - 1 + round) % (slots - 1);
-        const int j = min(ia, ib), k = max(ia, ib);
-        pj[q] = j;
-        pk[q] = k;
-        DFv c = dfv(1.f, 0.f), sn = dfv(0.f, 0.f);
-        if (k < m) {
-          const DFv ajk = A[j * ld + k], ajj = A[j * ld + j], akk = A[k * ld + k];
-          const float x = fabsf(ajk.h);
-          if (x > rel * sqrtf(fabsf(ajj.h) * fabsf(akk.h)) && x > 0.f &&
-              fmaxf(fabsf(ajj.h), fabsf(akk.h)) > nu) {
-            *nrot = 1;  // any rotation this sweep (the same value from every writer)
-            const DFv dd = dfv_add(akk, dfv_neg(ajj));
-            float tt;
-            if (fabsf(dd.h) > 1e18f * x) {  // tiny angle: t = a_jk / dd
-              tt = ajk.h / dd.h;
-            } else {
-              const float tau = dd.h / (2.0f * ajk.h);
-              tt = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    const double nu = thr[0], fl = thr[1];
+    for (int q = t; q < npair; q += nt) {  // round 0's rotations from A itself
+      const int j = tb->pj[q], k = tb->pk[q];
+      T c, sn;
+      jident(c, sn);  // the padding pair of odd m never rotates
+      const bool mv = k < m && jparams(Ac[j * ld + j], Ac[k * ld + k], Ac[j * ld + k], rel, fl, nu,
+                                       c, sn);
+      if (mv) flag[fs] = 1;  // any rotation this sweep (the same value from every writer)
+      rc[q] = c;
+      rs[q] = sn;
+    }
+    __syncthreads();
+    for (int r = 0; r < R; ++r) {
+      const T* rcc = rc + (r & 1) * 32;
+      const T* rsc = rs + (r & 1) * 32;
+      if (t < 32) {
+        if (r + 1 < R) {  // rotations of round r + 1 from the entries this round produces
+          T* rcn = rc + ((r + 1) & 1) * 32;
+          T* rsn = rs + ((r + 1) & 1) * 32;
+          for (int q = t; q < npair; q += 32) {
+            const int u = tb->pj[(r + 1) * 32 + q], v = tb->pk[(r + 1) * 32 + q];
+            T c, sn;
+            jident(c, sn);
+            bool mv = false;
+            if (v < m) {
+              // pairs with the padding index carry the identity, so a moving
+              // pair has both indices below m
+              const int pu = tb->pq[r * 64 + u], pv = tb->pq[r * 64 + v];
+              const int qa = pu >> 1, qb = pv >> 1;
+              const bool uk = pu & 1, vk = pv & 1;
+              const int up = uk ? tb->pj[r * 32 + qa] : tb->pk[r * 32 + qa];
+              const int vp = vk ? tb->pj[r * 32 + qb] : tb->pk[r * 32 + qb];
+              const bool ma = jmoving(rsc[qa]);
+              const bool mb = jmoving(rsc[qb]);
+              const T ca = rcc[qa], sa = rsc[qa], cb = rcc[qb], sb = rsc[qb];
+              const T auu = jnew(Ac, ld, u, up, uk, ma, ca, sa, u, up, uk, ma, ca, sa);
+              const T avv = jnew(Ac, ld, v, vp, vk, mb, cb, sb, v, vp, vk, mb, cb, sb);
+              const T auv = jnew(Ac, ld, u, up, uk, ma, ca, sa, v, vp, vk, mb, cb, sb);
+              mv = jparams(auu, avv, auv, rel, fl, nu, c, sn);
             }
-            // u = 1 + t^2 exactly as a double-float (t^2 by an FMA), y ~ u^-1/2
-            const float t2 = tt * tt;
-            const DFv u = fast_two_sum(1.0f, t2);
-            const DFv uu = dfv_add(u, dfv(fmaf(tt, tt, -t2), 0.f));
-            const float y0 = rsqrtf(uu.h);
-            // y = y0 + y0 (1 - u y0^2) / 2
-            const DFv y0sq = dfv_mul(dfv(y0, 0.f), dfv(y0, 0.f));
-            const DFv r = dfv_add(dfv(1.f, 0.f), dfv_neg(dfv_mul(uu, y0sq)));
-            c = dfv_add(dfv(y0, 0.f), dfv_mul(dfv(0.5f * y0, 0.f), r));
-            sn = dfv_mul(dfv(tt, 0.f), c);
+            if (mv) flag[fs] = 1;
+            rcn[q] = c;
+            rsn[q] = sn;
           }
         }
-        rc[q] = c;
-        rs[q] = sn;
+      } else {
+        for (int e = t - 32; e < ntask; e += nt - 32) {
+          if (e < nblk) {  // block (rows of pair q1, columns of pair q2) into the other copy
+            const int bq = tb->blk[e], q1 = bq >> 8, q2 = bq & 255;
+            const int j1 = tb->pj[r * 32 + q1], k1 = tb->pk[r * 32 + q1];
+            const int j2 = tb->pj[r * 32 + q2], k2 = tb->pk[r * 32 + q2];
+            const bool v1 = k1 < m, v2 = k2 < m;
+            const bool m1 = v1 && jmoving(rsc[q1]), m2 = v2 && jmoving(rsc[q2]);
+            T a00 = Ac[j1 * ld + j2], a01 = a00, a10 = a00, a11 = a00;
+            if (v2) a01 = Ac[j1 * ld + k2];
+            if (v1) a10 = Ac[k1 * ld + j2];
+            if (v1 && v2) a11 = Ac[k1 * ld + k2];
+            if (m2) {  // columns j2, k2
+              const T c = rcc[q2], sn = rsc[q2];
+              const T x0 = jrot(c, a00, sn, a01), y0 = jrotp(sn, a00, c, a01);
+              a00 = x0;
+              a01 = y0;
+              if (v1) {
+                const T x1 = jrot(c, a10, sn, a11), y1 = jrotp(sn, a10, c, a11);
+                a10 = x1;
+                a11 = y1;
+              }
+            }
+            if (m1) {  // rows j1, k1
+              const T c = rcc[q1], sn = rsc[q1];
+              const T x0 = jrot(c, a00, sn, a10), y0 = jrotp(sn, a00, c, a10);
+              a00 = x0;
+              a10 = y0;
+              if (v2) {
+                const T x1 = jrot(c, a01, sn, a11), y1 = jrotp(sn, a01, c, a11);
+                a01 = x1;
+                a11 = y1;
+              }
+            }
+            An[j1 * ld + j2] = a00;
+            if (v2) An[j1 * ld + k2] = a01;
+            if (v1) An[k1 * ld + j2] = a10;
+            if (v1 && v2) An[k1 * ld + k2] = a11;
+          } else {  // columns j, k of W in place
+            const int wq = tb->wt[e - nblk], q = wq >> 8, row = wq & 255;
+            const int j = tb->pj[r * 32 + q], k = tb->pk[r * 32 + q];
+            if (k < m && jmoving(rsc[q])) {
+              const T c = rcc[q], sn = rsc[q];
+              const T wj = W[row * ld + j], wk = W[row * ld + k];
+              W[row * ld + j] = jrot(c, wj, sn, wk);
+              W[row * ld + k] = jrotp(sn, wj, c, wk);
+            }
+          }
+        }
       }
       __syncthreads();
-      for (int e = t; e < npair * m; e += nt) {  // columns j, k of A and W
-        const int q = e / m, r = e - q * m;
-        const int j = pj[q], k = pk[q];
-        if (k >= m || rs[q].h == 0.f) continue;
-        const DFv c = rc[q], sn = rs[q];
-        const DFv aj = A[r * ld + j], ak = A[r * ld + k];
-        A[r * ld + j] = dfv_rot(c, aj, sn, ak);
-        A[r * ld + k] = dfv_rot(sn, aj, dfv_neg(c), ak);  // s aj + c ak
-        const DFv wj = W[r * ld + j], wk = W[r * ld + k];
-        W[r * ld + j] = dfv_rot(c, wj, sn, wk);
-        W[r * ld + k] = dfv_rot(sn, wj, dfv_neg(c), wk);
-      }
-      __syncthreads();
-      for (int e = t; e < npair * m; e += nt) {  // rows j, k of A
-        const int q = e / m, cidx = e - q * m;
-        const int j = pj[q], k = pk[q];
-        if (k >= m || rs[q].h == 0.f) continue;
-        const DFv c = rc[q], sn = rs[q];
-        const DFv aj = A[j * ld + cidx], ak = A[k * ld + cidx];
-        A[j * ld + cidx] = dfv_rot(c, aj, sn, ak);
-        A[k * ld + cidx] = dfv_rot(sn, aj, dfv_neg(c), ak);
-      }
-      __syncthreads();
+      T* tmp = Ac;
+      Ac = An;
+      An = tmp;
     }
-    const bool conv = *nrot == 0;
-    __syncthreads();
-    if (conv) return true;
+    if (flag[fs] == 0) {
+      A = Ac;
+      return true;
+    }
   }
+  A = Ac;
   return false;
 }
 
@@ -398,23 +588,28 @@ __device__ void small_mm(int m, int ld, const double* X, bool xt, const double* 
 // double-float level, and the FP64 sweeps resolve what is below it (the
 // small eigenvalues, to FP64 accuracy, in a few sweeps).
 #define JS_REFINE_M 64
-__global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* __restrict__ lambda,
+__global__ void __launch_bounds__(1024) k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* __restrict__ lambda,
                                 double* __restrict__ Wout, int max_sweeps, int refine,
                                 int* status) {
   extern __shared__ double js[];
-  __shared__ DFv rc[128], rs[128];
-  __shared__ int pj[128], pk[128], nrot, order[256];
-  __shared__ float nu;
-  __shared__ double nud[2], scale_s;
+  __shared__ DFv rcf[64], rsf[64];
+  __shared__ double rcd[64], rsd[64], thr[2];
+  __shared__ int flag[2], order[JS_REFINE_M], pj[64], pk[64], nrot;
+  __shared__ double scale_s;
+  __shared__ JacTabs tabs;
   const int ld = m + 1, mm = m * ld;  // padded rows (see k_jacobi_sym)
+  // double-float phase: A, W, the second copy of A; FP64 finish: A, W, G, and
+  // a work matrix that is also the second copy of A
   DFv* A = reinterpret_cast<DFv*>(js);
   DFv* W = A + mm;
+  DFv* A2 = A + 2 * mm;
   const int t = threadIdx.x, nt = blockDim.x;
   if (t == 0) {
     double dm = 0.0;
     for (int j = 0; j < m; ++j) dm = fmax(dm, fabs(Gin[j * (j + 1) / 2 + j]));
     scale_s = dm > 0.0 ? ldexp(1.0, -ilogb(dm)) : 1.0;
   }
+  jacobi_tabs(m, &tabs);
   __syncthreads();
   const double sc = scale_s;
   for (int e = t; e < m * m; e += nt) {
@@ -426,8 +621,9 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
   __syncthreads();
   // 1e-13 for the result as it is; 1e-12 before the FP64 finish, which takes
   // the rest
-  const bool conv = jacobi_sweeps_df(m, ld, A, W, max_sweeps, refine ? 1e-12f : 1e-13f, rc, rs, pj,
-                                     pk, &nrot, &nu);
+  DFv* Af = A;
+  const bool conv = jacobi_sweeps_1b<DFv>(m, ld, Af, A2, W, max_sweeps, refine ? 1e-12 : 1e-13,
+                                          0.0, 1e-14, &tabs, rcf, rsf, flag, thr);
   if (!refine) {
     if (!conv && t == 0) vp_set_status(status, VP_ENOCONV);
     if (t == 0) {  // eigenvalues descending (selection order)
@@ -435,7 +631,7 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
       for (int i = 0; i < m; ++i) {
         int best = i;
         for (int j = i + 1; j < m; ++j)
-          if (dfv_to(A[order[j] * ld + order[j]]) > dfv_to(A[order[best] * ld + order[best]]))
+          if (dfv_to(Af[order[j] * ld + order[j]]) > dfv_to(Af[order[best] * ld + order[best]]))
             best = j;
         const int tmp = order[i];
         order[i] = order[best];
@@ -443,15 +639,15 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
       }
     }
     __syncthreads();
-    for (int i = t; i < m; i += nt) lambda[i] = dfv_to(A[order[i] * ld + order[i]]) / sc;
+    for (int i = t; i < m; i += nt) lambda[i] = dfv_to(Af[order[i] * ld + order[i]]) / sc;
     for (int e = t; e < m * m; e += nt) {
       const int r = e / m, c = e - r * m;
       Wout[e] = dfv_to(W[r * ld + order[c]]);
     }
     return;
   }
-  // FP64 finish: the double-float slots become FP64 (same size, element by
-  // element by the same thread), then G and a work matrix follow them
+  // FP64 finish: the double-float W becomes FP64 in place (same size,
+  // element by element by the same thread), then G and a work matrix follow
   double* Ad = js;
   double* Wd = js + mm;
   double* G = js + 2 * mm;
@@ -492,9 +688,10 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
     }
   }
   __syncthreads();
-  const bool conv64 = jacobi_sweeps<double>(m, ld, Ad, Wd, max_sweeps, 1e-15, 0.0, 1e-14,
-                                            reinterpret_cast<double*>(rc),
-                                            reinterpret_cast<double*>(rs), pj, pk, &nrot, nud);
+  // few pairs rotate in these sweeps: the in-place passes, which skip the
+  // pairs that do not rotate, cost less than copying A every round
+  const bool conv64 = jacobi_sweeps<double>(m, ld, Ad, Wd, max_sweeps, 1e-15, 0.0, 1e-14, rcd, rsd,
+                                            pj, pk, &nrot, thr);
   if (!conv64 && t == 0) vp_set_status(status, VP_ENOCONV);
   jacobi_output(m, ld, Ad, Wd, lambda, Wout, order);
   __syncthreads();
@@ -509,7 +706,7 @@ __global__ void k_jacobi_sym_df(int m, const double* __restrict__ Gin, double* _
 static void jacobi_sym(int m, const double* G, double* Ascr, double* Wscr, double* lambda,
                        double* Wout, int* status, cudaStream_t st, bool fp64_finish = false) {
   if (m <= JS_REFINE_M) {
-    const size_t smem = sizeof(double) * (fp64_finish ? 4 : 2) * m * (m + 1);
+    const size_t smem = sizeof(double) * (fp64_finish ? 4 : 3) * m * (m + 1);
     k_jacobi_sym_df<<<1, 1024, smem, st>>>(m, G, lambda, Wout, 60, fp64_finish ? 1 : 0, status);
     return;
   }
