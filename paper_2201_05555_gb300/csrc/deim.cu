@@ -16,6 +16,7 @@
 // init.cu), so directions of singular values below ~1e-8 sigma_1 are not
 // resolved; the interpolation indices need only the leading ones.
 #include "vp_internal.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -241,40 +242,6 @@ __global__ void k_jacobi_sym(int m, const double* __restrict__ Gin, double* __re
 }
 
 // ------------------------------------------- double-float symmetric Jacobi
-// A double-float value hi + lo (|lo| <= half an ulp of hi) carries about 48
-// significant bits; its operations run on the FP32 pipes, which issue 64
-// times the FP64 rate of this part.
-struct DFv {
-  float h, l;
-};
-__device__ __forceinline__ DFv dfv(float h, float l) { return DFv{h, l}; }
-__device__ __forceinline__ DFv dfv_from(double x) {
-  const float h = (float)x;
-  return DFv{h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ double dfv_to(DFv a) { return (double)a.h + (double)a.l; }
-// s + e = a + b exactly (Knuth's TwoSum)
-__device__ __forceinline__ DFv two_sum(float a, float b) {
-  const float s = a + b, bb = s - a;
-  return DFv{s, (a - (s - bb)) + (b - bb)};
-}
-// s + e = a + b exactly for |a| >= |b| (Dekker's FastTwoSum)
-__device__ __forceinline__ DFv fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return DFv{s, b - (s - a)};
-}
-__device__ __forceinline__ DFv dfv_add(DFv a, DFv b) {
-  const DFv s = two_sum(a.h, b.h);
-  return fast_two_sum(s.h, s.l + (a.l + b.l));
-}
-__device__ __forceinline__ DFv dfv_neg(DFv a) { return DFv{-a.h, -a.l}; }
-__device__ __forceinline__ DFv dfv_mul(DFv a, DFv b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return fast_two_sum(p, e);
-}
 // c a - s b
 __device__ __forceinline__ DFv dfv_rot(DFv c, DFv a, DFv s, DFv b) {
   return dfv_add(dfv_mul(c, a), dfv_neg(dfv_mul(s, b)));

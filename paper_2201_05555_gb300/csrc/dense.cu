@@ -3,6 +3,10 @@
 // Gauss-Jordan solves with partial pivoting, and the per-step coefficient
 // updates.  Complex n x n matrices are row-major double2 in global memory.
 #include "vp_internal.cuh"
+#include "dfloat.cuh"
+
+#include <cstddef>
+#include <type_traits>
 
 namespace vpk {
 
@@ -10,43 +14,116 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// ---------------------------------------------- element types of the kernels
+// The small dense kernels run on a complex element type CT: double2 (FP64),
+// or DC, real and imaginary parts as double-float pairs (16 bytes like
+// double2, so the shared-memory layouts are the same).  This part issues
+// FP64 at 1/64 of the FP32 rate, and one block of these kernels is bound by
+// it; the double-float operations run on the FP32 pipes at about five times
+// the FP64 throughput, with ~1e-14 relative rounding per operation instead
+// of ~1e-16, and run on 1024 threads (the FP64 ones on 256: more warps do
+// not raise the FP64 rate).  Inputs and outputs in global memory stay double2.
+struct DC {
+  DFv re, im;
+};
+__device__ __forceinline__ DC cadd(DC a, DC b) { return DC{dfv_add(a.re, b.re), dfv_add(a.im, b.im)}; }
+__device__ __forceinline__ DC csub(DC a, DC b) {
+  return DC{dfv_add(a.re, dfv_neg(b.re)), dfv_add(a.im, dfv_neg(b.im))};
+}
+__device__ __forceinline__ DC cmul(DC a, DC b) {
+  return DC{dfv_add(dfv_mul(a.re, b.re), dfv_neg(dfv_mul(a.im, b.im))),
+            dfv_add(dfv_mul(a.re, b.im), dfv_mul(a.im, b.re))};
+}
+__device__ __forceinline__ DC cconj(DC a) { return DC{a.re, dfv_neg(a.im)}; }
+__device__ __forceinline__ DC cscale(DC a, double s) {
+  const DFv f = dfv_from(s);
+  return DC{dfv_mul(a.re, f), dfv_mul(a.im, f)};
+}
+// a real factor in the working precision, converted once outside the loops
+// (a conversion from FP64 runs on the FP64 pipe)
+__device__ __forceinline__ double cfac(double2*, double s) { return s; }
+__device__ __forceinline__ DFv cfac(DC*, double s) { return dfv_from(s); }
+__device__ __forceinline__ DC cscale(DC a, DFv f) { return DC{dfv_mul(a.re, f), dfv_mul(a.im, f)}; }
+// conversions from and to the global double2 layout
+template <class CT>
+__device__ __forceinline__ CT cload(double2 a);
+template <>
+__device__ __forceinline__ double2 cload<double2>(double2 a) { return a; }
+template <>
+__device__ __forceinline__ DC cload<DC>(double2 a) { return DC{dfv_from(a.x), dfv_from(a.y)}; }
+template <class CT>
+__device__ __forceinline__ CT cload(DC a);
+template <>
+__device__ __forceinline__ DC cload<DC>(DC a) { return a; }
+__device__ __forceinline__ double2 cto(double2 a) { return a; }
+__device__ __forceinline__ double2 cto(DC a) { return make_double2(dfv_to(a.re), dfv_to(a.im)); }
+template <class CT>
+__device__ __forceinline__ CT cval(double re, double im) {
+  return cload<CT>(make_double2(re, im));
+}
+__device__ __forceinline__ double cabs2(DC a) { return cabs2(cto(a)); }
+// a + d (real d)
+__device__ __forceinline__ double2 cadd_re(double2 a, double d) {
+  a.x += d;
+  return a;
+}
+__device__ __forceinline__ DC cadd_re(DC a, double d) { return DC{dfv_add(a.re, dfv_from(d)), a.im}; }
+// conj(p) / |p|^2 with |p|^2 = a2, formed in FP64
+__device__ __forceinline__ double2 cinv_a2(double2 pv, double a2) { return cscale(cconj(pv), 1.0 / a2); }
+__device__ __forceinline__ DC cinv_a2(DC pv, double a2) {
+  return cload<DC>(cscale(cconj(cto(pv)), 1.0 / a2));
+}
+
 // out = alpha * op(A) op(B) + beta * out (all n x n); op = 0 plain, 1 conj-transpose.
 // out must not alias A or B.  Ends with __syncthreads().
-__device__ void cmm(double2* out, const double2* A, int opA, const double2* B, int opB,
-                    double2 alpha, double beta, int n) {
+template <class CT, class TA, class TB>
+__device__ void cmm(CT* out, const TA* A, int opA, const TB* B, int opB, CT alpha, double beta,
+                    int n) {
+  const CT zero = cval<CT>(0.0, 0.0);
+  const auto fb = cfac(out, beta);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int r = e / n, c = e - r * n;
-    double2 s = make_double2(0.0, 0.0);
+    CT s = zero;
     for (int k = 0; k < n; ++k) {
-      double2 a = opA ? cconj(A[k * n + r]) : A[r * n + k];
-      double2 b = opB ? cconj(B[c * n + k]) : B[k * n + c];
+      CT a = opA ? cconj(cload<CT>(A[k * n + r])) : cload<CT>(A[r * n + k]);
+      CT b = opB ? cconj(cload<CT>(B[c * n + k])) : cload<CT>(B[k * n + c]);
       s = cadd(s, cmul(a, b));
     }
-    double2 v = cmul(alpha, s);
-    out[e] = beta == 0.0 ? v : cadd(v, cscale(out[e], beta));
+    CT v = cmul(alpha, s);
+    out[e] = beta == 0.0 ? v : cadd(v, cscale(out[e], fb));
   }
   __syncthreads();
 }
 
 // out = a*A + b*op(B) + d*I (elementwise), n x n.  out may alias A.
-__device__ void cadd_mat(double2* out, double a, const double2* A, double b, const double2* B,
-                         int opB, double d, int n) {
+template <class CT, class TA, class TB>
+__device__ void cadd_mat(CT* out, double a, const TA* A, double b, const TB* B, int opB, double d,
+                         int n) {
+  const CT zero = cval<CT>(0.0, 0.0);
+  const auto fa = cfac(out, a), fb = cfac(out, b);
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int r = e / n, c = e - r * n;
-    double2 x = A ? cscale(A[e], a) : make_double2(0.0, 0.0);
-    if (B) x = cadd(x, cscale(opB ? cconj(B[c * n + r]) : B[e], b));
-    if (r == c) x.x += d;
+    CT x = A ? cscale(cload<CT>(A[e]), fa) : zero;
+    if (B) x = cadd(x, cscale(opB ? cconj(cload<CT>(B[c * n + r])) : cload<CT>(B[e]), fb));
+    if (r == c) x = cadd_re(x, d);
     out[e] = x;
   }
   __syncthreads();
+}
+template <class CT, class TA>
+__device__ void cadd_mat(CT* out, double a, const TA* A, double b, std::nullptr_t, int opB,
+                         double d, int n) {
+  cadd_mat(out, a, A, b, static_cast<const CT*>(nullptr), opB, d, n);
 }
 
 // Solve A X = B in place (A: n x n, lda; B: n x m, ldb; both in shared
 // memory) by Gauss-Jordan with partial pivoting.  Returns false if a pivot
 // vanishes.  Pivot ties resolve to the lowest row (deterministic).
-__device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m, double2* col) {
+template <class CT>
+__device__ bool gj_solve(CT* A, int lda, CT* B, int ldb, int n, int m, CT* col) {
   __shared__ int piv;
   __shared__ int ok;
+  __shared__ CT inv_s;
   if (threadIdx.x == 0) ok = 1;
   __syncthreads();
   for (int c = 0; c < n; ++c) {
@@ -72,19 +149,22 @@ __device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m,
     const int pr = piv;
     if (pr != c) {
       for (int j = threadIdx.x; j < n + m; j += blockDim.x) {
-        double2* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
-        double2* b = j < n ? &A[pr * lda + j] : &B[pr * ldb + j - n];
-        double2 t = *a;
+        CT* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
+        CT* b = j < n ? &A[pr * lda + j] : &B[pr * ldb + j - n];
+        CT t = *a;
         *a = *b;
         *b = t;
       }
       __syncthreads();
     }
-    const double2 pv = A[c * lda + c];
-    const double2 inv = cscale(cconj(pv), 1.0 / cabs2(pv));
+    if (threadIdx.x == 0) {  // the inverse of the pivot, once (FP64)
+      const CT pv = A[c * lda + c];
+      inv_s = cinv_a2(pv, cabs2(pv));
+    }
     __syncthreads();
+    const CT inv = inv_s;
     for (int j = threadIdx.x; j < n + m; j += blockDim.x) {
-      double2* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
+      CT* a = j < n ? &A[c * lda + j] : &B[c * ldb + j - n];
       *a = cmul(*a, inv);
     }
     for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = A[r * lda + c];
@@ -92,7 +172,7 @@ __device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m,
     for (int e = threadIdx.x; e < n * (n + m); e += blockDim.x) {
       int r = e / (n + m), j = e - r * (n + m);
       if (r == c) continue;
-      double2 f = col[r];
+      CT f = col[r];
       if (j < n) A[r * lda + j] = csub(A[r * lda + j], cmul(f, A[c * lda + j]));
       else B[r * ldb + j - n] = csub(B[r * ldb + j - n], cmul(f, B[c * ldb + j - n]));
     }
@@ -112,7 +192,8 @@ __device__ bool gj_solve(double2* A, int lda, double2* B, int ldb, int n, int m,
 // is undefined.  Returns false (M undefined) when a pivot falls below 1e-14
 // times the largest initial diagonal entry or is not finite; callers then
 // rebuild M and use gj_solve.
-__device__ bool gj_np(double2* M, int ld, int n, int w, double2* work, double2* rowc) {
+template <class CT>
+__device__ bool gj_np(CT* M, int ld, int n, int w, CT* work, CT* rowc) {
   __shared__ int bad;
   __shared__ double dscale;
   if (threadIdx.x == 0) {
@@ -122,23 +203,25 @@ __device__ bool gj_np(double2* M, int ld, int n, int w, double2* work, double2* 
     bad = !(d > 0.0) || !isfinite(d);
   }
   __syncthreads();
-  double2* src = M;
-  double2* dst = work;
+  CT* src = M;
+  CT* dst = work;
   int lds = ld, ldd = w;
   for (int c = 0; c < n; ++c) {
-    const double2 pv = src[c * lds + c];
-    const double a2 = cabs2(pv);
-    if (threadIdx.x == 0 && (!(a2 > 1e-28 * dscale) || !isfinite(a2))) bad = 1;
-    const double2 inv = cscale(cconj(pv), 1.0 / a2);
     const int w1 = w - c - 1;  // columns c+1 .. w-1
-    for (int j = threadIdx.x; j < w1; j += blockDim.x) rowc[j] = cmul(src[c * lds + c + 1 + j], inv);
+    if (threadIdx.x < w1 || threadIdx.x == 0) {  // the threads that scale the pivot row
+      const CT pv = src[c * lds + c];
+      const double a2 = cabs2(pv);
+      if (threadIdx.x == 0 && (!(a2 > 1e-28 * dscale) || !isfinite(a2))) bad = 1;
+      const CT inv = cinv_a2(pv, a2);
+      for (int j = threadIdx.x; j < w1; j += blockDim.x) rowc[j] = cmul(src[c * lds + c + 1 + j], inv);
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < n * w1; e += blockDim.x) {
       const int r = e / w1, jj = e - r * w1, j = c + 1 + jj;
       dst[r * ldd + j] = (r == c) ? rowc[jj] : csub(src[r * lds + j], cmul(src[r * lds + c], rowc[jj]));
     }
     __syncthreads();
-    double2* t = src;
+    CT* t = src;
     src = dst;
     dst = t;
     const int tl = lds;
@@ -155,14 +238,43 @@ __device__ bool gj_np(double2* M, int ld, int n, int w, double2* work, double2* 
   return !bad;
 }
 
-// Hermitian H = zeta zeta^H (n x n) from Z = [a; b] (2n x p).
-__device__ void zeta_gram(double2* H, const double* Z, int n, int p) {
+// Hermitian H = zeta zeta^H (n x n) from Z = [a; b] (2n x p).  In
+// double-float, Z is converted once, in chunks of ZG_CHUNK columns staged in
+// zs (2n x ZG_CHUNK double-float pairs of shared memory), since a conversion
+// from FP64 runs on the FP64 pipe.
+#define ZG_CHUNK 32
+template <class CT>
+__device__ void zeta_gram(CT* H, const double* Z, int n, int p, DFv* zs = nullptr) {
+  if constexpr (!std::is_same<CT, double2>::value) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) H[e] = cval<CT>(0.0, 0.0);
+    for (int i0 = 0; i0 < p; i0 += ZG_CHUNK) {
+      const int w = min(ZG_CHUNK, p - i0);
+      __syncthreads();  // the previous chunk is used up
+      for (int e = threadIdx.x; e < 2 * n * w; e += blockDim.x) {
+        const int r = e / w, i = e - r * w;
+        zs[r * ZG_CHUNK + i] = dfv_from(Z[(int64_t)r * p + i0 + i]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        CT s = H[e];
+        for (int i = 0; i < w; ++i) {
+          const CT zr = CT{zs[r * ZG_CHUNK + i], zs[(n + r) * ZG_CHUNK + i]};
+          const CT zc = CT{zs[c * ZG_CHUNK + i], zs[(n + c) * ZG_CHUNK + i]};
+          s = cadd(s, cmul(zr, cconj(zc)));
+        }
+        H[e] = s;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int r = e / n, c = e - r * n;
-    double2 s = make_double2(0.0, 0.0);
+    CT s = cval<CT>(0.0, 0.0);
     for (int i = 0; i < p; ++i) {
-      double2 zr = make_double2(Z[(int64_t)r * p + i], Z[(int64_t)(n + r) * p + i]);
-      double2 zc = make_double2(Z[(int64_t)c * p + i], Z[(int64_t)(n + c) * p + i]);
+      CT zr = cval<CT>(Z[(int64_t)r * p + i], Z[(int64_t)(n + r) * p + i]);
+      CT zc = cval<CT>(Z[(int64_t)c * p + i], Z[(int64_t)(n + c) * p + i]);
       s = cadd(s, cmul(zr, cconj(zc)));
     }
     H[e] = s;
@@ -174,28 +286,32 @@ __device__ void zeta_gram(double2* H, const double* Z, int n, int p) {
 // X(Q, zeta) = -i (M - Q (Q^H M)) H^-1 = M C0 + Q C1 (times scale), with
 // H = zeta zeta^H, C0 = -i scale H^-1, C1 = i scale (Q^H M) H^-1.
 // Shared: aug n x 3n.  Output C (2 x n x n).
+template <class CT>
 __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ QhM,
                                      const double* __restrict__ Z, double scale, double2* C,
                                      double2* tmp, int* status, int in_smem) {
-  extern __shared__ double2 aug[];
+  extern __shared__ double2 aug_raw[];
+  CT* aug = reinterpret_cast<CT*>(aug_raw);
   const int ld = 3 * n;
-  double2* H = in_smem ? aug + n * ld : tmp;  // n x n
-  double2* work = aug + n * ld + n * n;        // n x 3n (in_smem)
-  __shared__ double2 rowc[128];
-  zeta_gram(H, Z, n, p);
+  CT* H = in_smem ? aug + n * ld : reinterpret_cast<CT*>(tmp);  // n x n
+  CT* work = aug + n * ld + n * n;                               // n x 3n (in_smem)
+  __shared__ CT rowc[128];
+  // double-float: the staging of Z follows the work matrix in shared memory
+  zeta_gram(H, Z, n, p, reinterpret_cast<DFv*>(work + n * ld));
+  const CT one = cval<CT>(1.0, 0.0), zero = cval<CT>(0.0, 0.0);
   auto build = [&]() {
     for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
       int r = e / ld, c = e - r * ld;
-      double2 v;
+      CT v;
       if (c < n) v = H[r * n + c];
-      else if (c < 2 * n) v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
-      else v = cconj(QhM[(c - 2 * n) * n + r]);  // (Q^H M)^H
+      else if (c < 2 * n) v = c - n == r ? one : zero;
+      else v = cconj(cload<CT>(QhM[(c - 2 * n) * n + r]));  // (Q^H M)^H
       aug[e] = v;
     }
     __syncthreads();
   };
   build();
-  __shared__ double2 col[64];
+  __shared__ CT col[64];
   bool ok = in_smem && gj_np(aug, ld, n, ld, work, rowc);
   if (!ok) {
     build();
@@ -206,17 +322,21 @@ __global__ void k_small_basis_coeffs(int n, int p, const double2* __restrict__ Q
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int r = e / n, c = e - r * n;
-    double2 hinv = aug[r * ld + n + c];              // H^-1
-    double2 y = cconj(aug[c * ld + 2 * n + r]);      // ((H^-1 (Q^H M)^H)^H)[r][c] = (Q^H M H^-1)[r][c]
+    double2 hinv = cto(aug[r * ld + n + c]);          // H^-1
+    double2 y = cconj(cto(aug[c * ld + 2 * n + r]));  // ((H^-1 (Q^H M)^H)^H)[r][c] = (Q^H M H^-1)[r][c]
     C[e] = make_double2(scale * hinv.y, -scale * hinv.x);          // -i s H^-1
     C[n * n + e] = make_double2(-scale * y.y, scale * y.x);        // +i s (Q^H M) H^-1
   }
 }
 
 void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
-                        double2* C, double2* tmp, int* status, cudaStream_t st) {
+                        double2* C, double2* tmp, int* status, cudaStream_t st, bool df) {
   size_t smem = sizeof(double2) * n * 7 * n;
-  k_small_basis_coeffs<<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status, 1);
+  if (df) smem += sizeof(DFv) * 2 * n * ZG_CHUNK;
+  if (df)
+    k_small_basis_coeffs<DC><<<1, 1024, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status, 1);
+  else
+    k_small_basis_coeffs<double2><<<1, 256, smem, st>>>(n, p, QhM, Z, scale, C, tmp, status, 1);
 }
 
 // ------------------------------------------------------- Cayley retraction
@@ -226,56 +346,67 @@ void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, doubl
 // K = D^H C = [[Q0^H W, -G0], [W^H W, -W^H Q0]],
 // Q0^H W = P - G0 P / 2,  W^H W = XX - P^H P + P^H G0 P / 4.
 // Output C (2 x n x n): coefficient of Q0, coefficient of xi.
+template <class CT>
 __global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const double2* __restrict__ Pg,
                                const double2* __restrict__ XXg, double2* C, double2* tmp,
                                int* status, int in_smem, int fast) {
-  extern __shared__ double2 aug[];  // 2n x 3n, then (in_smem) G0, P, XX, T, QW, WW
+  extern __shared__ double2 aug_raw[];  // 2n x 3n, then (in_smem) G0, P, XX, T, QW, WW
+  CT* aug = reinterpret_cast<CT*>(aug_raw);
   const int nn = n * n, ld = 3 * n;
-  double2* sb = aug + 6 * nn;
-  const double2* G0 = G0g;
-  const double2* P = Pg;
-  const double2* XX = XXg;
-  double2* T = in_smem ? sb + 3 * nn : tmp;            // G0 P
-  double2* QW = in_smem ? sb + 4 * nn : tmp + nn;      // Q0^H W
-  double2* WW = in_smem ? sb + 5 * nn : tmp + 2 * nn;  // W^H W
-  if (in_smem) {
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-      sb[e] = G0g[e];
-      sb[nn + e] = Pg[e];
-      sb[2 * nn + e] = XXg[e];
-    }
-    __syncthreads();
-    G0 = sb;
-    P = sb + nn;
-    XX = sb + 2 * nn;
+  CT* sb = aug + 6 * nn;
+  CT* tb = reinterpret_cast<CT*>(tmp);
+  // inputs in the working type: shared memory, or after the temporaries in tmp
+  CT* ib = in_smem ? sb : tb + 3 * nn;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    ib[e] = cload<CT>(G0g[e]);
+    ib[nn + e] = cload<CT>(Pg[e]);
+    ib[2 * nn + e] = cload<CT>(XXg[e]);
   }
-  const double2 one = make_double2(1.0, 0.0);
+  __syncthreads();
+  const CT* G0 = ib;
+  const CT* P = ib + nn;
+  const CT* XX = ib + 2 * nn;
+  CT* T = in_smem ? sb + 3 * nn : tb;            // G0 P
+  CT* QW = in_smem ? sb + 4 * nn : tb + nn;      // Q0^H W
+  CT* WW = in_smem ? sb + 5 * nn : tb + 2 * nn;  // W^H W
+  const CT one = cval<CT>(1.0, 0.0);
   cmm(T, G0, 0, P, 0, one, 0.0, n);
   cadd_mat(QW, 1.0, P, -0.5, T, 0, 0.0, n);
-  cmm(WW, P, 1, P, 0, make_double2(-1.0, 0.0), 0.0, n);
-  cmm(WW, P, 1, T, 0, make_double2(0.25, 0.0), 1.0, n);
+  cmm(WW, P, 1, P, 0, cval<CT>(-1.0, 0.0), 0.0, n);
+  cmm(WW, P, 1, T, 0, cval<CT>(0.25, 0.0), 1.0, n);
   cadd_mat(WW, 1.0, WW, 1.0, XX, 0, 0.0, n);
+  const auto fhalf = cfac(aug, 0.5), fmhalf = cfac(aug, -0.5);
   auto build = [&]() {
     for (int e = threadIdx.x; e < 2 * n * ld; e += blockDim.x) {
       int r = e / ld, c = e - r * ld;
       int rb = r >= n, cb = c / n, rr = r - rb * n, cc = c - cb * n;
-      double2 v;
-      double d = (rr == cc) ? 1.0 : 0.0;
-      if (!rb && cb == 0) v = make_double2(d - 0.5 * QW[rr * n + cc].x, -0.5 * QW[rr * n + cc].y);
-      else if (!rb && cb == 1) v = cscale(G0[rr * n + cc], 0.5);
-      else if (!rb && cb == 2) v = G0[rr * n + cc];
-      else if (rb && cb == 0) v = cscale(WW[rr * n + cc], -0.5);
-      else {  // W^H Q0 = (Q0^H W)^H
-        double2 wq = cconj(QW[cc * n + rr]);
-        v = (cb == 1) ? make_double2(d + 0.5 * wq.x, 0.5 * wq.y) : wq;
+      CT v;
+      const bool dg = rr == cc;
+      if (!rb && cb == 0) {
+        v = cscale(QW[rr * n + cc], fmhalf);
+        if (dg) v = cadd_re(v, 1.0);
+      } else if (!rb && cb == 1) {
+        v = cscale(G0[rr * n + cc], fhalf);
+      } else if (!rb && cb == 2) {
+        v = G0[rr * n + cc];
+      } else if (rb && cb == 0) {
+        v = cscale(WW[rr * n + cc], fmhalf);
+      } else {  // W^H Q0 = (Q0^H W)^H
+        CT wq = cconj(QW[cc * n + rr]);
+        if (cb == 1) {
+          v = cscale(wq, fhalf);
+          if (dg) v = cadd_re(v, 1.0);
+        } else {
+          v = wq;
+        }
       }
       aug[e] = v;
     }
     __syncthreads();
   };
   build();
-  __shared__ double2 col[128];
-  __shared__ double2 rowc[256];
+  __shared__ CT col[128];
+  __shared__ CT rowc[256];
   bool ok = fast && gj_np(aug, ld, 2 * n, ld, aug + 12 * nn, rowc);
   if (!ok) {
     build();
@@ -284,7 +415,7 @@ __global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const dou
       return;
     }
   }
-  // copy Yt, Yb to global scratch (reuse T, QW)
+  // copy Yt, Yb out of the system (reuse T, QW)
   for (int e = threadIdx.x; e < nn; e += blockDim.x) {
     int r = e / n, c = e - r * n;
     T[e] = aug[r * ld + 2 * n + c];         // Yt
@@ -292,18 +423,25 @@ __global__ void k_small_cayley(int n, const double2* __restrict__ G0g, const dou
   }
   __syncthreads();
   // alpha = I - P Yt / 2 - Yb ; beta = Yt
-  cmm(C, P, 0, T, 0, make_double2(-0.5, 0.0), 0.0, n);
-  cadd_mat(C, 1.0, C, -1.0, QW, 0, 1.0, n);
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) C[nn + e] = T[e];
+  CT* alpha = WW;
+  cmm(alpha, P, 0, T, 0, cval<CT>(-0.5, 0.0), 0.0, n);
+  cadd_mat(alpha, 1.0, alpha, -1.0, QW, 0, 1.0, n);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    C[e] = cto(alpha[e]);
+    C[nn + e] = cto(T[e]);
+  }
 }
 
 void small_cayley_coeffs(int n, const double2* G0, const double2* P, const double2* XX, double2* C,
-                         double2* tmp, int* status, cudaStream_t st) {
+                         double2* tmp, int* status, cudaStream_t st, bool df) {
   size_t full = sizeof(double2) * 12 * n * n;
   int in_smem = full <= 200 * 1024;
   int fast = in_smem && sizeof(double2) * 18 * n * n <= 200 * 1024;  // + work for gj_np
   size_t smem = fast ? sizeof(double2) * 18 * n * n : in_smem ? full : sizeof(double2) * 6 * n * n;
-  k_small_cayley<<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem, fast);
+  if (df)
+    k_small_cayley<DC><<<1, 1024, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem, fast);
+  else
+    k_small_cayley<double2><<<1, 256, smem, st>>>(n, G0, P, XX, C, tmp, status, in_smem, fast);
 }
 
 // ------------------------------------------------------- tangent velocity
@@ -316,94 +454,114 @@ void small_cayley_coeffs(int n, const double2* G0, const double2* P, const doubl
 //   c = u3 - T2 (R^H Ups + Q0^H Ups) - (Q0^H Ups)^H,
 // where A1 = Q0^H Xp, A2 = xi^H Xp, A3 = Q0^H R, A4 = R^H Xp, A5 = R^H xi.
 // grams: [A1, A2, A3, A4, A5] (5 x n x n); output C = scale * [u1, u2, c]
-// (coefficients of Xp, xi, Q0).
+// (coefficients of Xp, xi, Q0).  Inputs are read in place (global) unless
+// they fit in shared memory.
+template <class CT>
 __global__ void k_small_tangent(int n, const double2* __restrict__ grams_g,
                                 const double2* __restrict__ G0g, const double2* __restrict__ Pg,
                                 double scale, double2* C, double2* tmp, int* status, int in_smem,
                                 int fast) {
-  extern __shared__ double2 aug[];  // n x 2n, then (in_smem) 7 inputs and 8 temporaries
+  extern __shared__ double2 aug_raw[];  // n x 2n, then (in_smem) 7 inputs and 8 temporaries
+  CT* aug = reinterpret_cast<CT*>(aug_raw);
   const int nn = n * n, ld = 2 * n;
-  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
-  double2* sb = aug + 2 * nn;
-  const double2* grams = grams_g;
-  const double2* G0 = G0g;
-  const double2* P = Pg;
-  double2* tb = in_smem ? sb + 7 * nn : tmp;
+  const CT one = cval<CT>(1.0, 0.0), mone = cval<CT>(-1.0, 0.0), zero = cval<CT>(0.0, 0.0);
+  CT* sb = aug + 2 * nn;
+  CT* tb = in_smem ? sb + 7 * nn : reinterpret_cast<CT*>(tmp);
   if (in_smem) {
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-      for (int q = 0; q < 5; ++q) sb[q * nn + e] = grams_g[q * nn + e];
-      sb[5 * nn + e] = G0g[e];
-      sb[6 * nn + e] = Pg[e];
+      for (int q = 0; q < 5; ++q) sb[q * nn + e] = cload<CT>(grams_g[q * nn + e]);
+      sb[5 * nn + e] = cload<CT>(G0g[e]);
+      sb[6 * nn + e] = cload<CT>(Pg[e]);
     }
     __syncthreads();
-    grams = sb;
-    G0 = sb + 5 * nn;
-    P = sb + 6 * nn;
   }
-  const double2 *A1 = grams, *A2 = grams + nn, *A3 = grams + 2 * nn, *A4 = grams + 3 * nn,
-                *A5 = grams + 4 * nn;
-  double2 *T1 = tb, *u1 = tb + nn, *u2 = tb + 2 * nn, *u3 = tb + 3 * nn, *W1 = tb + 4 * nn,
-          *QU = tb + 5 * nn, *RU = tb + 6 * nn, *W2 = tb + 7 * nn;
-  auto build = [&]() {
-    for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
-      int r = e / ld, c = e - r * ld;
-      double2 v;
-      if (c < n) { v = A3[r * n + c]; if (r == c) v.x += 1.0; }
-      else v = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
-      aug[e] = v;
-    }
-    __syncthreads();
-  };
-  build();
-  __shared__ double2 col[64];
-  __shared__ double2 rowc[128];
-  bool ok = fast && gj_np(aug, ld, n, ld, aug + 17 * nn, rowc);
-  if (!ok) {
+  CT *T1 = tb, *u1 = tb + nn, *u2 = tb + 2 * nn, *u3 = tb + 3 * nn, *W1 = tb + 4 * nn,
+     *QU = tb + 5 * nn, *RU = tb + 6 * nn, *W2 = tb + 7 * nn;
+  __shared__ CT col[64];
+  __shared__ CT rowc[128];
+  // the rest, on inputs of type TI (CT in shared memory, or double2 in global)
+  auto body = [&](auto grams, auto G0, auto P) {
+    auto A1 = grams, A2 = grams + nn, A3 = grams + 2 * nn, A4 = grams + 3 * nn, A5 = grams + 4 * nn;
+    auto build = [&]() {
+      for (int e = threadIdx.x; e < n * ld; e += blockDim.x) {
+        int r = e / ld, c = e - r * ld;
+        CT v;
+        if (c < n) { v = cload<CT>(A3[r * n + c]); if (r == c) v = cadd_re(v, 1.0); }
+        else v = c - n == r ? one : zero;
+        aug[e] = v;
+      }
+      __syncthreads();
+    };
     build();
-    if (!gj_solve(aug, ld, aug + n, ld, n, n, col)) {
-      if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
-      return;
+    bool ok = fast && gj_np(aug, ld, n, ld, aug + 17 * nn, rowc);
+    if (!ok) {
+      build();
+      if (!gj_solve(aug, ld, aug + n, ld, n, n, col)) {
+        if (threadIdx.x == 0) vp_set_status(status, VP_ENUMERIC);
+        return;
+      }
     }
-  }
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    int r = e / n, c = e - r * n;
-    T1[e] = aug[r * ld + n + c];
-  }
-  __syncthreads();
-  cadd_mat(u1, 2.0, T1, 0.0, nullptr, 0, 0.0, n);
-  cmm(u2, A1, 0, T1, 0, mone, 0.0, n);
-  // W1 = P A1 / 2 + A2 - P^H A1 / 2
-  cmm(W1, P, 0, A1, 0, make_double2(0.5, 0.0), 0.0, n);
-  cmm(W1, P, 1, A1, 0, make_double2(-0.5, 0.0), 1.0, n);
-  cadd_mat(W1, 1.0, W1, 1.0, A2, 0, 0.0, n);
-  cmm(u3, W1, 0, T1, 0, one, 0.0, n);
-  // QU = A1 u1 + P u2 + G0 u3
-  cmm(QU, A1, 0, u1, 0, one, 0.0, n);
-  cmm(QU, P, 0, u2, 0, one, 1.0, n);
-  cmm(QU, G0, 0, u3, 0, one, 1.0, n);
-  // RU = A4 u1 + A5 u2 + A3^H u3
-  cmm(RU, A4, 0, u1, 0, one, 0.0, n);
-  cmm(RU, A5, 0, u2, 0, one, 1.0, n);
-  cmm(RU, A3, 1, u3, 0, one, 1.0, n);
-  // c = u3 - T1^H (RU + QU) - QU^H
-  cadd_mat(W2, 1.0, RU, 1.0, QU, 0, 0.0, n);
-  cmm(W1, T1, 1, W2, 0, one, 0.0, n);
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    int r = e / n, c = e - r * n;
-    double2 cc = csub(csub(u3[e], W1[e]), cconj(QU[c * n + r]));
-    C[e] = cscale(u1[e], scale);
-    C[nn + e] = cscale(u2[e], scale);
-    C[2 * nn + e] = cscale(cc, scale);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      int r = e / n, c = e - r * n;
+      T1[e] = aug[r * ld + n + c];
+    }
+    __syncthreads();
+    cadd_mat(u1, 2.0, T1, 0.0, nullptr, 0, 0.0, n);
+    cmm(u2, A1, 0, T1, 0, mone, 0.0, n);
+    // W1 = P A1 / 2 + A2 - P^H A1 / 2
+    cmm(W1, P, 0, A1, 0, cval<CT>(0.5, 0.0), 0.0, n);
+    cmm(W1, P, 1, A1, 0, cval<CT>(-0.5, 0.0), 1.0, n);
+    cadd_mat(W1, 1.0, W1, 1.0, A2, 0, 0.0, n);
+    cmm(u3, W1, 0, T1, 0, one, 0.0, n);
+    // QU = A1 u1 + P u2 + G0 u3
+    cmm(QU, A1, 0, u1, 0, one, 0.0, n);
+    cmm(QU, P, 0, u2, 0, one, 1.0, n);
+    cmm(QU, G0, 0, u3, 0, one, 1.0, n);
+    // RU = A4 u1 + A5 u2 + A3^H u3
+    cmm(RU, A4, 0, u1, 0, one, 0.0, n);
+    cmm(RU, A5, 0, u2, 0, one, 1.0, n);
+    cmm(RU, A3, 1, u3, 0, one, 1.0, n);
+    // c = u3 - T1^H (RU + QU) - QU^H
+    cadd_mat(W2, 1.0, RU, 1.0, QU, 0, 0.0, n);
+    cmm(W1, T1, 1, W2, 0, one, 0.0, n);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      int r = e / n, c = e - r * n;
+      CT cc = csub(csub(u3[e], W1[e]), cconj(QU[c * n + r]));
+      C[e] = cscale(cto(u1[e]), scale);
+      C[nn + e] = cscale(cto(u2[e]), scale);
+      C[2 * nn + e] = cscale(cto(cc), scale);
+    }
+  };
+  if (in_smem) {
+    body(static_cast<const CT*>(sb), static_cast<const CT*>(sb + 5 * nn),
+         static_cast<const CT*>(sb + 6 * nn));
+  } else if constexpr (std::is_same<CT, double2>::value) {
+    body(grams_g, G0g, Pg);
+  } else {  // double-float: the inputs converted once, after the temporaries in tmp
+    CT* ib = tb + 8 * nn;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      for (int q = 0; q < 5; ++q) ib[q * nn + e] = cload<CT>(grams_g[q * nn + e]);
+      ib[5 * nn + e] = cload<CT>(G0g[e]);
+      ib[6 * nn + e] = cload<CT>(Pg[e]);
+    }
+    __syncthreads();
+    body(static_cast<const CT*>(ib), static_cast<const CT*>(ib + 5 * nn),
+         static_cast<const CT*>(ib + 6 * nn));
   }
 }
 
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
-                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st) {
+                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st,
+                          bool df) {
   size_t full = sizeof(double2) * 17 * n * n;
   int in_smem = full <= 200 * 1024;
   int fast = in_smem && sizeof(double2) * 19 * n * n <= 200 * 1024;  // + work for gj_np
   size_t smem = fast ? sizeof(double2) * 19 * n * n : in_smem ? full : sizeof(double2) * 2 * n * n;
-  k_small_tangent<<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem, fast);
+  if (df)
+    k_small_tangent<DC><<<1, 1024, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem, fast);
+  else
+    k_small_tangent<double2><<<1, 256, smem, st>>>(n, grams, G0, P, scale, C, tmp, status, in_smem,
+                                                   fast);
 }
 
 // ------------------------------------------------- fixed-point iteration
@@ -857,9 +1015,12 @@ void energies(int n, int p, const double* GVraw, const double* Z, const double* 
 }
 
 void dense_init() {
-  cudaFuncSetAttribute(k_small_basis_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_small_cayley, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_small_tangent, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_basis_coeffs<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_cayley<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_tangent<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_basis_coeffs<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_cayley<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_small_tangent<DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_coeff_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_lowdin, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

@@ -169,7 +169,7 @@ size_t red_ws_bytes(int sms, int64_t N, int n, int p, int Nx, int nrows, bool df
   return arena_bytes(pn, 8) * 2 + arena_bytes(p, 8) + arena_bytes(part_d, 8) +
          arena_bytes((size_t)n2 * p, 8) * 5 + arena_bytes((size_t)3 * n2 * p, 8) +
          arena_bytes((size_t)n2 * n2, 8) + arena_bytes((size_t)(n2 + 5) * p + 64, 8) + arena_bytes(12 * nn, 16) + arena_bytes(4 * nn, 16) +
-         arena_bytes(4 * nn, 16) + arena_bytes(10 * nn, 16) + arena_bytes(8, 4) +
+         arena_bytes(4 * nn, 16) + arena_bytes(17 * nn, 16) + arena_bytes(8, 4) +
          (size_t)nrows * arena_bytes((size_t)N * n2, 8) +
          (df ? arena_bytes((size_t)N * n2, 8) + 6 * arena_bytes((size_t)N * n2, f32rows ? 4 : 8) +
                    arena_bytes(jcell_count(N, p, Nx), 2) +
@@ -206,7 +206,7 @@ vp_status red_ws(vp_ctx* ctx, int64_t N, int n, int p, int Nx, int nrows, RedWS&
   w.grams = a.take<double2>(12 * nn);
   w.cay = a.take<double2>(4 * nn);
   w.C = a.take<double2>(4 * nn);
-  w.tmp = a.take<double2>(10 * nn);
+  w.tmp = a.take<double2>(17 * nn);  // small dense scratch (see dense.cu)
   w.flags = a.take<int>(8);
   for (int r = 0; r < 5; ++r) w.rows[r] = r < nrows ? a.take<double>((size_t)N * n2) : nullptr;
   // the row blocks of the df / FP32 step: float2 (double-float) elements, or
@@ -478,7 +478,8 @@ struct RedDF {
     const bool tc = (a.tc & VP_TC_BASIS_M) && arith == 2 && w.bop && basis_tc_supported(n, p);
     VP_K(tc ? VP_K_BASIS_M_TC : VP_K_BASIS_M_LP, lp_launch(arith, LP_BASIS_M, a, st));
     grams({Q2, M}, {{0, 1}}, w.grams);
-    VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st));
+    VP_K(VP_K_SMALL_BASIS, small_basis_coeffs(n, p, w.grams, Z, scale, w.C, w.tmp, ctx->d_status, st,
+                                              arith == 2));
     comb({M, Q2}, w.C, nullptr, out);
   }
   // Cayley retraction of Q0 along xi; leaves G0, P, XX in w.cay.  Q0d (FP64
@@ -489,7 +490,7 @@ struct RedDF {
     grams({Q0, xi}, {{0, 0}, {0, 1}, {1, 1}}, w.cay);
     const int nn = n * n;
     VP_K(VP_K_SMALL_CAYLEY, small_cayley_coeffs(n, w.cay, w.cay + nn, w.cay + 2 * nn, w.C, w.tmp,
-                                                ctx->d_status, st));
+                                                ctx->d_status, st, arith == 2));
     comb({Q0, xi}, w.C, out_d, out_v, Q0d);
   }
 };
@@ -650,7 +651,7 @@ vp_status DFStep::post() {
     D.grams({Q0, xih, Qh, Xp}, {{0, 3}, {1, 3}, {0, 2}, {2, 3}, {2, 1}}, w.grams);
     const int nn = n * n;
     VP_K(VP_K_SMALL_TANGENT, small_tangent_coeffs(n, w.grams, w.cay, w.cay + nn, dt, w.C, w.tmp,
-                                                  ctx->d_status, st));
+                                                  ctx->d_status, st, o.arith == 2));
     D.comb({Xp, xih, Q0}, w.C, nullptr, xi1);  // xi_1 = dt Y(xi_half, Z_mid)
     // Q_1 = R_Q0(xi_1) in FP64; in the FP32 form as Q_0 + (Q_1 - Q_0), the
     // increment from FP32 rows added to the FP64 Q_0, so that Q does not take

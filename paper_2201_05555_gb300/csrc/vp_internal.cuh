@@ -357,13 +357,15 @@ void affine(int64_t N, int n, const AffineArgs& a, const double2* C, double* out
 void cell_gradient(const GridC& g, int p, const double* phi, double* F, cudaStream_t st);
 void reduced_init();
 
-// dense.cu (single-block FP64 small dense algebra)
+// dense.cu (single-block small dense algebra, FP64; df: in double-float on
+// the FP32 pipes, for the FP32 form)
 void small_basis_coeffs(int n, int p, const double2* QhM, const double* Z, double scale,
-                        double2* C, double2* tmp, int* status, cudaStream_t st);
+                        double2* C, double2* tmp, int* status, cudaStream_t st, bool df = false);
 void small_cayley_coeffs(int n, const double2* G0, const double2* P, const double2* XX, double2* C,
-                         double2* tmp, int* status, cudaStream_t st);
+                         double2* tmp, int* status, cudaStream_t st, bool df = false);
 void small_tangent_coeffs(int n, const double2* grams, const double2* G0, const double2* P,
-                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st);
+                          double scale, double2* C, double2* tmp, int* status, cudaStream_t st,
+                          bool df = false);
 // gX: the projection (2n x p), or nullptr with `part` (nparts x 2n x p block
 // partials of it, summed here in block order).  kr (3 x 2n x p): ring of
 // the iterates two to four iterations back (no initial value needed).
