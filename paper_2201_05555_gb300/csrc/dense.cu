@@ -974,28 +974,32 @@ void sqrt_nonneg(int m, const double* x, double* out, cudaStream_t st) {
 
 // --------------------------------------------------------------- energies
 // E_out[i] = Efield[i], H_out[i] = 1/2 Z_i^T G_V Z_i + Efield[i];
-// resid = |Q^H Q - I|_F from the complex Gram QhQ (nullable).
-__global__ void k_energies(int n, int p, const double* __restrict__ GVraw,
-                           const double* __restrict__ Z, const double* __restrict__ Efield,
-                           double* E_out, double* H_out, int64_t stride,
-                           const double2* __restrict__ QhQ, double* resid, int* status) {
-  const int n2 = 2 * n;
-  for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    double kin = 0.0;
-    for (int a = 0; a < n2; ++a) {
-      double za = Z[(int64_t)a * p + i];
-      double s = 0.0;
-      for (int b = 0; b < n2; ++b) s = fma(GVraw[vperm(a, n) * n2 + vperm(b, n)], Z[(int64_t)b * p + i], s);
-      kin = fma(za, s, kin);
-    }
-    double E = Efield[i];
-    double H = 0.5 * kin + E;
+// resid = |Q^H Q - I|_F from the complex Gram QhQ (nullable).  Block i takes
+// sample i (the FP64 work spread over the SMs): thread a forms
+// s_a = sum_b G_V[a][b] z_b in order, and the block adds z_a s_a in a fixed
+// tree (deterministic).  Block 0 also forms the residual.
+#define EN_THREADS 128
+__global__ void __launch_bounds__(EN_THREADS)
+k_energies(int n, int p, const double* __restrict__ GVraw, const double* __restrict__ Z,
+           const double* __restrict__ Efield, double* E_out, double* H_out, int64_t stride,
+           const double2* __restrict__ QhQ, double* resid, int* status) {
+  __shared__ double red[32];
+  const int n2 = 2 * n, i = blockIdx.x;
+  double part = 0.0;
+  for (int a = threadIdx.x; a < n2 && i < p; a += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < n2; ++b) s = fma(GVraw[vperm(a, n) * n2 + vperm(b, n)], Z[(int64_t)b * p + i], s);
+    part = fma(Z[(int64_t)a * p + i], s, part);
+  }
+  const double kin = block_sum2(part, red);
+  if (threadIdx.x == 0 && i < p) {
+    const double E = Efield[i];
+    const double H = 0.5 * kin + E;
     if (E_out) E_out[i * stride] = E;
     if (H_out) H_out[i * stride] = H;
     if (!isfinite(H)) vp_set_status(status, VP_ENUMERIC);
   }
-  if (QhQ && resid) {
-    __shared__ double red[32];
+  if (QhQ && resid && blockIdx.x == 0) {
     double s = 0.0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       int r = e / n, c = e - r * n;
@@ -1011,7 +1015,8 @@ __global__ void k_energies(int n, int p, const double* __restrict__ GVraw,
 void energies(int n, int p, const double* GVraw, const double* Z, const double* Efield,
               double* E_out, double* H_out, int64_t stride, const double2* QhQ, double* resid,
               int* status, cudaStream_t st) {
-  k_energies<<<1, 256, 0, st>>>(n, p, GVraw, Z, Efield, E_out, H_out, stride, QhQ, resid, status);
+  k_energies<<<p > 0 ? p : 1, EN_THREADS, 0, st>>>(n, p, GVraw, Z, Efield, E_out, H_out, stride, QhQ, resid,
+                                       status);
 }
 
 void dense_init() {

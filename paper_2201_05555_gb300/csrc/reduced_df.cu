@@ -26,7 +26,9 @@ namespace vpk {
 struct ArithDF {
   using V = float2;
   static constexpr bool kVec4 = false;
-  static __device__ __forceinline__ V from(double d) { return df_split(d); }
+  static __device__ __forceinline__ V from(double d) { return df_split_bits(d); }
+  // an FP32 value as V, without the FP64 pipe: (f, 0)
+  static __device__ __forceinline__ V from_f(float f) { return make_float2(f, 0.f); }
   static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
   static __device__ __forceinline__ float hi(V a) { return a.x; }
@@ -57,7 +59,8 @@ struct ArithDF {
 struct ArithF32 {
   using V = float;
   static constexpr bool kVec4 = true;  // rows of plain floats: float4 loads apply
-  static __device__ __forceinline__ V from(double d) { return __double2float_rn(d); }
+  static __device__ __forceinline__ V from(double d) { return df_split_bits(d).x; }
+  static __device__ __forceinline__ V from_f(float f) { return f; }
   static __device__ __forceinline__ V zero() { return 0.f; }
   static __device__ __forceinline__ V neg(V a) { return -a; }
   static __device__ __forceinline__ float hi(V a) { return a; }
@@ -327,7 +330,7 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
               s0 = fmaf(-b.z, zb[4 * k + 2], s0);
               s1 = fmaf(-b.w, zb[4 * k + 3], s1);
             }
-          tt = AR::from((double)(s0 + s1));
+          tt = AR::from_f(s0 + s1);
         } else if (vec) {  // x = sum_k A_k a_k - B_k b_k in two partial sums
           const float4* q4 = reinterpret_cast<const float4*>(q);
           const float4* z4 = reinterpret_cast<const float4*>(Zt + ii * ldk);
@@ -344,7 +347,7 @@ __global__ void k_deposit_lp(GridC g, int64_t N, int n, int p, int PC,
             s0 = fmaf(-b.z, zb.z, s0);
             s1 = fmaf(-b.w, zb.w, s1);
           }
-          tt = AR::from((double)(s0 + s1));
+          tt = AR::from_f(s0 + s1);
         } else if constexpr (NR > 0) {
           typename AR::A x;
           x.zero();
@@ -607,7 +610,7 @@ k_basis_M_lp(GridC g, int64_t N, int n, int p, int PC, const typename AR::V* __r
               s0 = fmaf(qa.z, zb.z, s0);
               s1 = fmaf(qa.w, zb.w, s1);
             }
-            gi = AR::from((double)(s0 + s1));
+            gi = AR::from_f(s0 + s1);
           } else {
             typename AR::A v;
             v.zero();

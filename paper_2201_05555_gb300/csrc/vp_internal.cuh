@@ -178,6 +178,34 @@ __device__ __forceinline__ float2 df_split(double d) {
   float l = __double2float_rn(d - (double)h);
   return make_float2(h, l);
 }
+// The same split by integer operations on the bit pattern, for an exponent
+// of d in [-70, 126]: this part issues FP64 conversions at 1/64 of the FP32
+// rate, and the row splits of the FP32-based forms were bound by them.
+// hi = d rounded to 24 significant bits (to nearest, ties to even); the
+// remainder r = d - hi, an integer multiple of 2^(e-52) with |r| <= 2^(e-24),
+// is rounded to FP32 by the int-to-float conversion and scaled by a power of
+// two (exact).  The same bits as df_split; zero, tiny, huge and non-finite d
+// take df_split.
+__device__ __forceinline__ float2 df_split_bits(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((u >> 52) & 0x7ffull) - 1023;
+  if (e < -70 || e > 126) return df_split(d);
+  const unsigned long long mant = u & ((1ull << 52) - 1);
+  const unsigned int low = (unsigned int)(mant & ((1ull << 29) - 1));
+  unsigned int m23 = (unsigned int)(mant >> 29);
+  const unsigned int up = (low > (1u << 28) || (low == (1u << 28) && (m23 & 1u))) ? 1u : 0u;
+  const int r = (int)low - (int)(up << 29);
+  m23 += up;
+  unsigned int fe = (unsigned int)(e + 127);
+  if (m23 == (1u << 23)) {
+    m23 = 0;
+    fe += 1;
+  }
+  const unsigned int sgn = (unsigned int)(u >> 63);
+  const float hi = __uint_as_float((sgn << 31) | (fe << 23) | m23);
+  const float lo = (float)(sgn ? -r : r) * __uint_as_float((unsigned int)(e - 52 + 127) << 23);
+  return make_float2(hi, lo);
+}
 // Store d in the row format of the FP32-based forms: mode 1 double-float
 // (float2), mode 2 FP32 (float).
 __device__ __forceinline__ void store_lp(void* base, int64_t e, double d, int mode) {
