@@ -11,8 +11,9 @@ fixed-point coefficient stage (deposit, Poisson, gather, projection per
 iteration), the tangent velocity, the second retraction and the FP64
 re-orthonormalisation, plus the FP64-accurate energy check of the entering
 state.  Row work (reconstruction, deposit, projection, Gamma zeta^H, Grams,
-row updates) in FP32; cross-block reductions, small dense algebra,
-re-orthonormalisation factor and energies in FP64.  Metric:
+row updates) in FP32; cross-block reductions, re-orthonormalisation factor
+and energies in FP64; the small dense algebra (n x n and 2n x 2n solves and
+products) in double-float.  Metric:
 particle-steps/s = N * p * steps / time.
 
 Extra lines: the two-stream workload (N = 1e5, p = 64, 2n = 20) in FP64 and
