@@ -1097,7 +1097,13 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
           break;
         }
       }
-      int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
+      int PC = chunk_w(p, g.Nx);
+      // double-float rows that store no cell indices (the energy check of the
+      // FP32 form): 16-sample chunks, so that two blocks fit an SM (the 32-
+      // sample counts and Q stages take 145 KB); the counts are exact sums, so
+      // the chunking does not change them
+      if (!AR::kVec4 && !A.j && PC > 16) PC = 16;
+      const int ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
       const bool vec = AR::kVec4 && (n & 3) == 0;
       const int nr = dep_nr<AR>(n);
@@ -1126,7 +1132,13 @@ static void launch_all(LpOp op, const LpArgs& A, cudaStream_t st) {
           break;
         }
       }
-      int PC = chunk_w(p, g.Nx), ch = ceil_div(p, PC);
+      int PC = chunk_w(p, g.Nx);
+      // double-float rows that store no cell indices (the energy check of the
+      // FP32 form): 16-sample chunks, so that two blocks fit an SM (the 32-
+      // sample counts and Q stages take 145 KB); the counts are exact sums, so
+      // the chunking does not change them
+      if (!AR::kVec4 && !A.j && PC > 16) PC = 16;
+      const int ch = ceil_div(p, PC);
       const size_t qst = (sizeof(V) * TILE_ROWS * n2 + 15) & ~size_t(15);
       const size_t jst = (sizeof(uint16_t) * TILE_ROWS * PC + 15) & ~size_t(15);
       size_t smem = 16 + 2 * qst + 2 * jst + sizeof(V) * (PC * g.Nx + TILE_ROWS * (PC + 1));

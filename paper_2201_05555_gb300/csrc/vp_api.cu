@@ -391,7 +391,9 @@ struct RedDF {
     a.v0 = const_cast<void*>(Q2);
     a.v1 = w.Zh2;
     a.counts = w.counts;
-    a.j = w.jcell;
+    // the energy check's cell indices would be overwritten unread by the
+    // step's own field evaluation: not stored
+    a.j = diag ? nullptr : w.jcell;
     a.skip = skip;
     const bool tc = (a.tc & VP_TC_DEPOSIT) && arith == 2 && deposit_tc_supported(n, p, R.g.Nx, R.g.Kp);
     VP_K(diag ? VP_K_DEPOSIT_DIAG : (tc ? VP_K_DEPOSIT_TC : VP_K_DEPOSIT_LP),
